@@ -1,0 +1,1047 @@
+/*
+ * sdref.c -- plain FP64 CPU oracle of the SD MHD+GLM method (arXiv 2502.17805).
+ *
+ * TEST INFRASTRUCTURE ONLY: used by the tests, the smoke check and the CPU
+ * baseline of the benchmark; never by the product path.  It shares no code
+ * with the CUDA library.  Every loop is written in the order the method
+ * states it; nothing is blocked, fused or reordered for speed (the only
+ * concession is an OpenMP loop over independent elements, which changes no
+ * arithmetic).
+ *
+ * Readings of passages the paper leaves open (each also listed in the design notes):
+ *  R1 flux points: the N+1 points {0, roots of the Legendre polynomial P_{N-1}
+ *     mapped to [0,1], 1}; the paper's "N-th degree" would give N+2 points,
+ *     contradicting the N+1 flux points per line it requires (Sec. SD Method).
+ *  R2 flux reconstruction sums run over the N+1 flux points of the family's
+ *     own direction (Sec. SD Method, reconstruction of F, G, H).
+ *  R3 energy flux GLM term: c_h psi B (a vector); induction flux of B in
+ *     direction n: (U.n)B - (B.n)U + c_h psi n; psi flux c_h B (Eq. invF).
+ *  R4 the damping rate a of psi is the parameter glm_alpha (source M).
+ *  R5 c_h is a parameter; the driver sets it to lambda_max each step.
+ *  R6 Rusanov wave speed: max(|u_n| + c_f(n) on both sides, c_h), c_f the
+ *     fast magnetosonic speed along n.
+ *  R7 the divergence of B in the Powell terms is the discrete SD divergence
+ *     with the BR1 face average of the normal field.
+ *  R8 no GLM terms beyond those printed (no advection of psi).
+ *  R9 inviscid wall ghost: rho, p, psi, E copied; u -> u - 2(u.n)n;
+ *     conducting: B -> B - 2(B.n)n; radial: B -> 2(B.n)n - B.
+ *  R10 transfinite map: edge-based Gordon-Hall blend (three bilinear edge
+ *     projectors minus twice the trilinear corner projector); constant-radius
+ *     edges are great-circle arcs, radial edges straight; the geometry is the
+ *     degree-p = floor(N/2) tensor interpolant of that map at Chebyshev-Lobatto
+ *     nodes, and S^d = rows of adj(J) as cross products of its derivatives.
+ *  R11 time stepping: Shu-Osher SSP-RK3 (the SSPRK(5,3) table the paper
+ *     cites is not given in the paper).
+ *  R12 shell initial noise and dipole (see sdref_state_init).
+ */
+#include "sdref.h"
+
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define MAXN 8
+#define MAXP 4
+
+static __thread char g_err[512];
+static void set_err(const char* msg) { snprintf(g_err, sizeof g_err, "%s", msg); }
+const char* sdref_last_error(void) { return g_err; }
+
+static int g_threads = 0;
+void sdref_set_threads(int n) { g_threads = n; }
+int sdref_get_threads(void) {
+#ifdef _OPENMP
+  return g_threads > 0 ? g_threads : omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+/* ------------------------------------------------------------------ */
+/* 1D nodes and Lagrange operators (Sec. SD Method)                    */
+/* ------------------------------------------------------------------ */
+
+/* Legendre P_M(x) and its derivative by the three-term recurrence. */
+static void legendre_eval(int M, double x, double* P, double* dP) {
+  double p0 = 1.0, p1 = x;
+  if (M == 0) { *P = 1.0; *dP = 0.0; return; }
+  for (int n = 1; n < M; ++n) {
+    double p2 = ((2.0 * n + 1.0) * x * p1 - n * p0) / (n + 1.0);
+    p0 = p1;
+    p1 = p2;
+  }
+  *P = p1;
+  *dP = M * (x * p1 - p0) / (x * x - 1.0);
+}
+
+/* Roots of P_M on [-1,1] in ascending order, with Gauss-Legendre weights. */
+static void legendre_roots(int M, double* root, double* wgl) {
+  for (int k = 0; k < M; ++k) {
+    double x = cos(M_PI * (k + 0.75) / (M + 0.5));
+    for (int it = 0; it < 100; ++it) {
+      double P, dP;
+      legendre_eval(M, x, &P, &dP);
+      double dx = P / dP;
+      x -= dx;
+      if (fabs(dx) < 1e-17) break;
+    }
+    double P, dP;
+    legendre_eval(M, x, &P, &dP);
+    root[M - 1 - k] = x;
+    if (wgl) wgl[M - 1 - k] = 2.0 / ((1.0 - x * x) * dP * dP);
+  }
+}
+
+/* h_i(x): Lagrange basis over the N solution points. */
+static double lagrange(const double* nodes, int n, int i, double x) {
+  double v = 1.0;
+  for (int s = 0; s < n; ++s)
+    if (s != i) v *= (x - nodes[s]) / (nodes[i] - nodes[s]);
+  return v;
+}
+
+/* derivative of the Lagrange basis function i over n nodes, at x */
+static double lagrange_deriv(const double* nodes, int n, int i, double x) {
+  double sum = 0.0;
+  for (int m = 0; m < n; ++m) {
+    if (m == i) continue;
+    double prod = 1.0 / (nodes[i] - nodes[m]);
+    for (int s = 0; s < n; ++s)
+      if (s != i && s != m) prod *= (x - nodes[s]) / (nodes[i] - nodes[s]);
+    sum += prod;
+  }
+  return sum;
+}
+
+int sdref_nodes(int N, double* xs, double* xf, double* E, double* D, double* w) {
+  if (N < 2 || N > MAXN) { set_err("order N must be in [2,8]"); return 1; }
+  /* solution points: Chebyshev-Gauss, X_{s,n} = (1 - cos((2n-1) pi / (2N))) / 2 */
+  for (int n = 1; n <= N; ++n) xs[n - 1] = 0.5 * (1.0 - cos((2.0 * n - 1.0) / (2.0 * N) * M_PI));
+  /* flux points (reading R1): {0, roots of P_{N-1}, 1} */
+  double r[MAXN + 1];
+  xf[0] = 0.0;
+  if (N - 1 > 0) legendre_roots(N - 1, r, NULL);
+  for (int k = 0; k < N - 1; ++k) xf[k + 1] = 0.5 * (1.0 + r[k]);
+  xf[N] = 1.0;
+  /* E[f][i] = h_i(X_f) */
+  for (int f = 0; f <= N; ++f)
+    for (int i = 0; i < N; ++i) E[f * N + i] = lagrange(xs, N, i, xf[f]);
+  /* D[i][f] = l_f'(X_s,i) */
+  for (int i = 0; i < N; ++i)
+    for (int f = 0; f <= N; ++f) D[i * (N + 1) + f] = lagrange_deriv(xf, N + 1, f, xs[i]);
+  /* w_i = int_0^1 h_i, by a Gauss-Legendre rule exact for degree 2N+3 */
+  int M = N + 2;
+  double t[MAXN + 2], wg[MAXN + 2];
+  legendre_roots(M, t, wg);
+  for (int i = 0; i < N; ++i) {
+    double s = 0.0;
+    for (int q = 0; q < M; ++q) s += 0.5 * wg[q] * lagrange(xs, N, i, 0.5 * (1.0 + t[q]));
+    w[i] = s;
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Mesh                                                                */
+/* ------------------------------------------------------------------ */
+
+struct sdref_mesh {
+  int N, p;
+  double xs[MAXN], xf[MAXN + 1], E[(MAXN + 1) * MAXN], D[MAXN * (MAXN + 1)], w[MAXN];
+  double yl[MAXP + 1]; /* Chebyshev-Lobatto nodes of the polynomial map */
+  int64_t n_e, n_v;
+  double* verts;
+  int64_t* hex;
+  double per[3];
+  int geom;
+  double r_in, r_out;
+  int bc_in, bc_out;
+  int64_t* nb_e;   /* [n_e*6] neighbour element or -1 */
+  int32_t* nb_f;   /* [n_e*6] neighbour face */
+  int32_t* owner;  /* [n_e*6] 1 if this side computes the common flux */
+  int32_t* code;   /* [n_e*6] orientation code */
+  int32_t* bc;     /* [n_e*6] boundary condition of a boundary face */
+  int64_t n_bf, n_if;
+  double h_min;
+  double** gcache; /* per element geometry block */
+};
+
+/* local corner (s,t) of face F -> hex corner index */
+static int face_corner(int F, int s, int t) {
+  switch (F) {
+    case 0: return 0 + 2 * s + 4 * t;
+    case 1: return 1 + 2 * s + 4 * t;
+    case 2: return s + 0 + 4 * t;
+    case 3: return s + 2 + 4 * t;
+    case 4: return s + 2 * t + 0;
+    default: return s + 2 * t + 4;
+  }
+}
+
+/* corner c of element e, unwrapped across periodic directions so that every
+ * corner lies within half a period of corner 0 */
+static void corner_xyz(const sdref_mesh* m, int64_t e, int c, double* X) {
+  const double* v = m->verts + 3 * m->hex[8 * e + c];
+  const double* v0 = m->verts + 3 * m->hex[8 * e + 0];
+  for (int d = 0; d < 3; ++d) {
+    X[d] = v[d];
+    if (m->per[d] > 0.0) X[d] += m->per[d] * round((v0[d] - v[d]) / m->per[d]);
+  }
+}
+
+typedef struct {
+  int64_t key[4];
+  int64_t e;
+  int F;
+} face_rec;
+
+static int cmp_face(const void* A, const void* B) {
+  const face_rec* a = (const face_rec*)A;
+  const face_rec* b = (const face_rec*)B;
+  for (int i = 0; i < 4; ++i) {
+    if (a->key[i] < b->key[i]) return -1;
+    if (a->key[i] > b->key[i]) return 1;
+  }
+  if (a->e != b->e) return a->e < b->e ? -1 : 1;
+  return a->F - b->F;
+}
+
+static int cmp_i64(const void* A, const void* B) {
+  int64_t a = *(const int64_t*)A, b = *(const int64_t*)B;
+  return a < b ? -1 : (a > b ? 1 : 0);
+}
+
+/* orientation code of the map from this side's face point (a,b) to the
+ * neighbour's (a',b'), found by matching the face corners' vertex ids */
+static int face_code(const sdref_mesh* m, int64_t e1, int F1, int64_t e2, int F2) {
+  int64_t v2[2][2];
+  for (int s = 0; s < 2; ++s)
+    for (int t = 0; t < 2; ++t) v2[s][t] = m->hex[8 * e2 + face_corner(F2, s, t)];
+  int st[3][2];
+  const int probe[3][2] = {{0, 0}, {1, 0}, {0, 1}};
+  for (int q = 0; q < 3; ++q) {
+    int64_t v = m->hex[8 * e1 + face_corner(F1, probe[q][0], probe[q][1])];
+    st[q][0] = st[q][1] = -1;
+    for (int s = 0; s < 2; ++s)
+      for (int t = 0; t < 2; ++t)
+        if (v2[s][t] == v) { st[q][0] = s; st[q][1] = t; }
+    if (st[q][0] < 0) return -1;
+  }
+  int swap = (st[1][0] == st[0][0]); /* moving along own s leaves neighbour s' fixed */
+  int flipA = (st[0][0] == 1), flipB = (st[0][1] == 1);
+  return (swap << 2) | (flipA << 1) | flipB;
+}
+
+static void map_point(int code, int N, int a, int b, int* a2, int* b2) {
+  int swap = (code >> 2) & 1, flipA = (code >> 1) & 1, flipB = code & 1;
+  int u = swap ? b : a, v = swap ? a : b;
+  *a2 = flipA ? N - 1 - u : u;
+  *b2 = flipB ? N - 1 - v : v;
+}
+
+static double dist3(const double* a, const double* b) {
+  double dx = a[0] - b[0], dy = a[1] - b[1], dz = a[2] - b[2];
+  return sqrt(dx * dx + dy * dy + dz * dz);
+}
+
+sdref_mesh* sdref_mesh_create(int N, int64_t n_v, const double* verts, int64_t n_e, const int64_t* hex,
+                              const double* periodic, int geom, double r_in, double r_out, int bc_in,
+                              int bc_out) {
+  if (N < 2 || N > MAXN) { set_err("order N must be in [2,8]"); return NULL; }
+  if (n_e <= 0 || n_v <= 0 || !verts || !hex) { set_err("empty mesh"); return NULL; }
+  sdref_mesh* m = (sdref_mesh*)calloc(1, sizeof(sdref_mesh));
+  m->N = N;
+  m->p = N / 2;
+  sdref_nodes(N, m->xs, m->xf, m->E, m->D, m->w);
+  for (int a = 0; a <= m->p; ++a) m->yl[a] = 0.5 * (1.0 - cos(M_PI * a / m->p));
+  m->n_e = n_e;
+  m->n_v = n_v;
+  m->verts = (double*)malloc(sizeof(double) * 3 * n_v);
+  memcpy(m->verts, verts, sizeof(double) * 3 * n_v);
+  m->hex = (int64_t*)malloc(sizeof(int64_t) * 8 * n_e);
+  memcpy(m->hex, hex, sizeof(int64_t) * 8 * n_e);
+  for (int64_t i = 0; i < 8 * n_e; ++i)
+    if (hex[i] < 0 || hex[i] >= n_v) { set_err("vertex index out of range"); sdref_mesh_destroy(m); return NULL; }
+  for (int d = 0; d < 3; ++d) m->per[d] = periodic ? periodic[d] : 0.0;
+  m->geom = geom;
+  m->r_in = r_in;
+  m->r_out = r_out;
+  m->bc_in = bc_in;
+  m->bc_out = bc_out;
+  m->nb_e = (int64_t*)malloc(sizeof(int64_t) * 6 * n_e);
+  m->nb_f = (int32_t*)calloc(6 * n_e, sizeof(int32_t));
+  m->owner = (int32_t*)calloc(6 * n_e, sizeof(int32_t));
+  m->code = (int32_t*)calloc(6 * n_e, sizeof(int32_t));
+  m->bc = (int32_t*)calloc(6 * n_e, sizeof(int32_t));
+  m->gcache = (double**)calloc(n_e, sizeof(double*));
+  for (int64_t i = 0; i < 6 * n_e; ++i) m->nb_e[i] = -1;
+
+  /* match faces by their sorted corner vertex ids */
+  face_rec* fr = (face_rec*)malloc(sizeof(face_rec) * 6 * n_e);
+  for (int64_t e = 0; e < n_e; ++e) {
+    for (int F = 0; F < 6; ++F) {
+      face_rec* r = &fr[6 * e + F];
+      for (int s = 0; s < 2; ++s)
+        for (int t = 0; t < 2; ++t) r->key[2 * t + s] = hex[8 * e + face_corner(F, s, t)];
+      qsort(r->key, 4, sizeof(int64_t), cmp_i64);
+      r->e = e;
+      r->F = F;
+    }
+  }
+  qsort(fr, 6 * n_e, sizeof(face_rec), cmp_face);
+  int64_t i = 0;
+  while (i < 6 * n_e) {
+    int64_t j = i + 1;
+    while (j < 6 * n_e && memcmp(fr[j].key, fr[i].key, sizeof fr[i].key) == 0) ++j;
+    if (j - i > 2) { set_err("face shared by more than two elements"); free(fr); sdref_mesh_destroy(m); return NULL; }
+    if (j - i == 2) {
+      int64_t e1 = fr[i].e, e2 = fr[i + 1].e;
+      int F1 = fr[i].F, F2 = fr[i + 1].F;
+      int c12 = face_code(m, e1, F1, e2, F2), c21 = face_code(m, e2, F2, e1, F1);
+      if (c12 < 0 || c21 < 0) { set_err("face corners do not match"); free(fr); sdref_mesh_destroy(m); return NULL; }
+      m->nb_e[6 * e1 + F1] = e2; m->nb_f[6 * e1 + F1] = F2; m->code[6 * e1 + F1] = c12; m->owner[6 * e1 + F1] = 1;
+      m->nb_e[6 * e2 + F2] = e1; m->nb_f[6 * e2 + F2] = F1; m->code[6 * e2 + F2] = c21; m->owner[6 * e2 + F2] = 0;
+      m->n_if++;
+    } else {
+      int64_t e = fr[i].e;
+      int F = fr[i].F;
+      int bcv = bc_in;
+      if (geom == 1) {
+        double c[3] = {0, 0, 0}, X[3];
+        for (int s = 0; s < 2; ++s)
+          for (int t = 0; t < 2; ++t) {
+            corner_xyz(m, e, face_corner(F, s, t), X);
+            for (int d = 0; d < 3; ++d) c[d] += 0.25 * X[d];
+          }
+        double rc = sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+        bcv = rc < 0.5 * (r_in + r_out) ? bc_in : bc_out;
+      }
+      if (bcv == SDREF_BC_PERIODIC) { set_err("unmatched face with periodic boundary condition"); free(fr); sdref_mesh_destroy(m); return NULL; }
+      m->bc[6 * e + F] = bcv;
+      m->n_bf++;
+    }
+    i = j;
+  }
+  free(fr);
+
+  /* smallest element edge (chord) for the time-step rule */
+  static const int edges[12][2] = {{0, 1}, {2, 3}, {4, 5}, {6, 7}, {0, 2}, {1, 3},
+                                   {4, 6}, {5, 7}, {0, 4}, {1, 5}, {2, 6}, {3, 7}};
+  double hmin = INFINITY;
+  for (int64_t e = 0; e < n_e; ++e) {
+    double X[8][3];
+    for (int c = 0; c < 8; ++c) corner_xyz(m, e, c, X[c]);
+    for (int k = 0; k < 12; ++k) {
+      double l = dist3(X[edges[k][0]], X[edges[k][1]]);
+      if (l < hmin) hmin = l;
+    }
+  }
+  m->h_min = hmin;
+  return m;
+}
+
+void sdref_mesh_destroy(sdref_mesh* m) {
+  if (!m) return;
+  if (m->gcache)
+    for (int64_t e = 0; e < m->n_e; ++e) free(m->gcache[e]);
+  free(m->gcache);
+  free(m->verts); free(m->hex); free(m->nb_e); free(m->nb_f); free(m->owner); free(m->code); free(m->bc);
+  free(m);
+}
+
+int sdref_mesh_info(const sdref_mesh* m, int64_t* n_bfaces, int64_t* n_ifaces, double* h_min) {
+  if (n_bfaces) *n_bfaces = m->n_bf;
+  if (n_ifaces) *n_ifaces = m->n_if;
+  if (h_min) *h_min = m->h_min;
+  return 0;
+}
+
+int sdref_mesh_faces(const sdref_mesh* m, int64_t e, int64_t* nb_e, int32_t* nb_f, int32_t* owner, int32_t* code) {
+  if (e < 0 || e >= m->n_e) { set_err("element out of range"); return 1; }
+  for (int F = 0; F < 6; ++F) {
+    nb_e[F] = m->nb_e[6 * e + F];
+    nb_f[F] = m->nb_f[6 * e + F];
+    owner[F] = m->owner[6 * e + F];
+    code[F] = m->code[6 * e + F];
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Transfinite mapping and metrics (Sec. SD Method; reading R10)       */
+/* ------------------------------------------------------------------ */
+
+/* point at parameter t on the edge from A to B */
+static void edge_point(const double* A, const double* B, double t, int geom, double* out) {
+  if (geom == 0) {
+    for (int d = 0; d < 3; ++d) out[d] = (1.0 - t) * A[d] + t * B[d];
+    return;
+  }
+  double ra = sqrt(A[0] * A[0] + A[1] * A[1] + A[2] * A[2]);
+  double rb = sqrt(B[0] * B[0] + B[1] * B[1] + B[2] * B[2]);
+  double da[3], db[3];
+  for (int d = 0; d < 3; ++d) { da[d] = A[d] / ra; db[d] = B[d] / rb; }
+  double cr[3] = {da[1] * db[2] - da[2] * db[1], da[2] * db[0] - da[0] * db[2], da[0] * db[1] - da[1] * db[0]};
+  double th = atan2(sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]), da[0] * db[0] + da[1] * db[1] + da[2] * db[2]);
+  double r = (1.0 - t) * ra + t * rb;
+  double dir[3];
+  if (th < 1e-12) {
+    double nn = 0.0;
+    for (int d = 0; d < 3; ++d) { dir[d] = (1.0 - t) * da[d] + t * db[d]; nn += dir[d] * dir[d]; }
+    nn = sqrt(nn);
+    for (int d = 0; d < 3; ++d) dir[d] /= nn;
+  } else {
+    double sa = sin((1.0 - t) * th) / sin(th), sb = sin(t * th) / sin(th);
+    for (int d = 0; d < 3; ++d) dir[d] = sa * da[d] + sb * db[d];
+  }
+  for (int d = 0; d < 3; ++d) out[d] = r * dir[d];
+}
+
+/* X = P_{xi eta} + P_{eta zeta} + P_{xi zeta} - 2 P_{xi eta zeta} built from the 12 edges */
+static void tfi(const double V[8][3], int geom, double xi, double eta, double zeta, double* X) {
+  double phx[2] = {1.0 - xi, xi}, phy[2] = {1.0 - eta, eta}, phz[2] = {1.0 - zeta, zeta};
+  double P[3];
+  for (int d = 0; d < 3; ++d) X[d] = 0.0;
+  for (int j = 0; j < 2; ++j)
+    for (int k = 0; k < 2; ++k) {
+      edge_point(V[0 + 2 * j + 4 * k], V[1 + 2 * j + 4 * k], xi, geom, P);
+      for (int d = 0; d < 3; ++d) X[d] += phy[j] * phz[k] * P[d];
+    }
+  for (int i = 0; i < 2; ++i)
+    for (int k = 0; k < 2; ++k) {
+      edge_point(V[i + 0 + 4 * k], V[i + 2 + 4 * k], eta, geom, P);
+      for (int d = 0; d < 3; ++d) X[d] += phx[i] * phz[k] * P[d];
+    }
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j) {
+      edge_point(V[i + 2 * j], V[i + 2 * j + 4], zeta, geom, P);
+      for (int d = 0; d < 3; ++d) X[d] += phx[i] * phy[j] * P[d];
+    }
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j)
+      for (int k = 0; k < 2; ++k)
+        for (int d = 0; d < 3; ++d) X[d] -= 2.0 * phx[i] * phy[j] * phz[k] * V[i + 2 * j + 4 * k][d];
+}
+
+/* geometry block layout */
+static int64_t gsz_S(const sdref_mesh* m) { return 3LL * (m->N + 1) * m->N * m->N * 3; }
+static int64_t gsz_J(const sdref_mesh* m) { return (int64_t)m->N * m->N * m->N; }
+static int64_t gsz_Xp(const sdref_mesh* m) { return 3LL * (m->p + 1) * (m->p + 1) * (m->p + 1); }
+
+/* derivative of the polynomial map: dX/d(dir) at (xi, eta, zeta) */
+static void map_deriv(const sdref_mesh* m, const double* Xp, int dir, const double* pt, double* out) {
+  int p1 = m->p + 1;
+  out[0] = out[1] = out[2] = 0.0;
+  for (int c = 0; c < p1; ++c)
+    for (int b = 0; b < p1; ++b)
+      for (int a = 0; a < p1; ++a) {
+        double la = dir == 0 ? lagrange_deriv(m->yl, p1, a, pt[0]) : lagrange(m->yl, p1, a, pt[0]);
+        double lb = dir == 1 ? lagrange_deriv(m->yl, p1, b, pt[1]) : lagrange(m->yl, p1, b, pt[1]);
+        double lc = dir == 2 ? lagrange_deriv(m->yl, p1, c, pt[2]) : lagrange(m->yl, p1, c, pt[2]);
+        double wgt = la * lb * lc;
+        const double* x = Xp + 3 * (a + p1 * (b + p1 * c));
+        for (int d = 0; d < 3; ++d) out[d] += wgt * x[d];
+      }
+}
+
+static void map_value(const sdref_mesh* m, const double* Xp, const double* pt, double* out) {
+  int p1 = m->p + 1;
+  out[0] = out[1] = out[2] = 0.0;
+  for (int c = 0; c < p1; ++c)
+    for (int b = 0; b < p1; ++b)
+      for (int a = 0; a < p1; ++a) {
+        double wgt = lagrange(m->yl, p1, a, pt[0]) * lagrange(m->yl, p1, b, pt[1]) * lagrange(m->yl, p1, c, pt[2]);
+        const double* x = Xp + 3 * (a + p1 * (b + p1 * c));
+        for (int d = 0; d < 3; ++d) out[d] += wgt * x[d];
+      }
+}
+
+static void cross3(const double* a, const double* b, double* c) {
+  c[0] = a[1] * b[2] - a[2] * b[1];
+  c[1] = a[2] * b[0] - a[0] * b[2];
+  c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+/* computational coordinates of point (f, a, b) of flux family d */
+static void family_point(const sdref_mesh* m, int d, int f, int a, int b, double* pt) {
+  if (d == 0) { pt[0] = m->xf[f]; pt[1] = m->xs[a]; pt[2] = m->xs[b]; }
+  else if (d == 1) { pt[0] = m->xs[a]; pt[1] = m->xf[f]; pt[2] = m->xs[b]; }
+  else { pt[0] = m->xs[a]; pt[1] = m->xs[b]; pt[2] = m->xf[f]; }
+}
+
+static int compute_geometry(sdref_mesh* m, int64_t e) {
+  if (m->gcache[e]) return 0;
+  int N = m->N, p1 = m->p + 1;
+  int64_t nS = gsz_S(m), nJ = gsz_J(m), nXp = gsz_Xp(m);
+  double* g = (double*)malloc(sizeof(double) * (nS + nJ + 3 * nJ + nXp));
+  double *S = g, *J = g + nS, *X = J + nJ, *Xp = X + 3 * nJ;
+  double V[8][3];
+  for (int c = 0; c < 8; ++c) corner_xyz(m, e, c, V[c]);
+  for (int c = 0; c < p1; ++c)
+    for (int b = 0; b < p1; ++b)
+      for (int a = 0; a < p1; ++a) tfi(V, m->geom, m->yl[a], m->yl[b], m->yl[c], Xp + 3 * (a + p1 * (b + p1 * c)));
+  int bad = 0;
+  for (int d = 0; d < 3; ++d)
+    for (int b = 0; b < N; ++b)
+      for (int a = 0; a < N; ++a)
+        for (int f = 0; f <= N; ++f) {
+          double pt[3], x1[3], x2[3];
+          family_point(m, d, f, a, b, pt);
+          /* S^xi = x_eta x x_zeta, S^eta = x_zeta x x_xi, S^zeta = x_xi x x_eta */
+          map_deriv(m, Xp, (d + 1) % 3, pt, x1);
+          map_deriv(m, Xp, (d + 2) % 3, pt, x2);
+          cross3(x1, x2, S + 3 * (((int64_t)d * (N + 1) * N * N) + f + (N + 1) * (a + N * b)));
+        }
+  for (int k = 0; k < N; ++k)
+    for (int j = 0; j < N; ++j)
+      for (int i = 0; i < N; ++i) {
+        int n = i + N * (j + N * k);
+        double pt[3] = {m->xs[i], m->xs[j], m->xs[k]}, xa[3], xb[3], xc[3], cr[3];
+        map_deriv(m, Xp, 0, pt, xa);
+        map_deriv(m, Xp, 1, pt, xb);
+        map_deriv(m, Xp, 2, pt, xc);
+        cross3(xb, xc, cr);
+        J[n] = xa[0] * cr[0] + xa[1] * cr[1] + xa[2] * cr[2];
+        if (!(J[n] > 0.0)) bad = 1;
+        map_value(m, Xp, pt, X + 3 * n);
+      }
+  if (bad) { free(g); set_err("non-positive Jacobian"); return 2; }
+  m->gcache[e] = g;
+  return 0;
+}
+
+static const double* geo_S(const sdref_mesh* m, int64_t e, int d, int f, int a, int b) {
+  int N = m->N;
+  return m->gcache[e] + 3 * (((int64_t)d * (N + 1) * N * N) + f + (N + 1) * (a + N * b));
+}
+static double geo_J(const sdref_mesh* m, int64_t e, int n) { return m->gcache[e][gsz_S(m) + n]; }
+static const double* geo_X(const sdref_mesh* m, int64_t e, int n) { return m->gcache[e] + gsz_S(m) + gsz_J(m) + 3 * n; }
+
+int sdref_geometry(sdref_mesh* m, int64_t e, double* S, double* J, double* X, double* Xp) {
+  if (e < 0 || e >= m->n_e) { set_err("element out of range"); return 1; }
+  int rc = compute_geometry(m, e);
+  if (rc) return rc;
+  const double* g = m->gcache[e];
+  int64_t nS = gsz_S(m), nJ = gsz_J(m), nXp = gsz_Xp(m);
+  if (S) memcpy(S, g, sizeof(double) * nS);
+  if (J) memcpy(J, g + nS, sizeof(double) * nJ);
+  if (X) memcpy(X, g + nS + nJ, sizeof(double) * 3 * nJ);
+  if (Xp) memcpy(Xp, g + nS + 4 * nJ, sizeof(double) * nXp);
+  return 0;
+}
+
+/* compute geometry for every element flagged in need[] (distinct slots: safe in parallel) */
+static int ensure_geometry(sdref_mesh* m, const char* need) {
+  int err = 0;
+#pragma omp parallel for schedule(dynamic, 16) num_threads(sdref_get_threads())
+  for (int64_t e = 0; e < m->n_e; ++e) {
+    if (need && !need[e]) continue;
+    if (!m->gcache[e] && compute_geometry(m, e)) {
+#pragma omp atomic write
+      err = 1;
+    }
+  }
+  if (err) { set_err("non-positive Jacobian"); return 2; }
+  return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Physics: Eq. (invF), fast speed, Rusanov (readings R3, R6, R8)      */
+/* ------------------------------------------------------------------ */
+
+static double pressure(const double* q, double gam) {
+  double rho = q[0];
+  double ke = 0.5 * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) / rho;
+  double me = 0.5 * (q[5] * q[5] + q[6] * q[6] + q[7] * q[7]);
+  return (gam - 1.0) * (q[4] - ke - me - 0.5 * q[8] * q[8]);
+}
+
+/* flux of Q through a surface with (not necessarily unit) normal n */
+void sdref_flux(const double* q, const double* n, double gam, double ch, double* F) {
+  double rho = q[0];
+  double u[3] = {q[1] / rho, q[2] / rho, q[3] / rho};
+  const double* B = q + 5;
+  double psi = q[8];
+  double p = pressure(q, gam);
+  double B2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
+  double e = q[4] - 0.5 * psi * psi; /* E = e + psi^2/2, Eq. (energy) */
+  double un = u[0] * n[0] + u[1] * n[1] + u[2] * n[2];
+  double Bn = B[0] * n[0] + B[1] * n[1] + B[2] * n[2];
+  double uB = u[0] * B[0] + u[1] * B[1] + u[2] * B[2];
+  double pt = p + 0.5 * B2;
+  F[0] = rho * un;
+  for (int d = 0; d < 3; ++d) F[1 + d] = rho * u[d] * un + pt * n[d] - B[d] * Bn;
+  F[4] = un * (e + pt) - Bn * uB + ch * psi * Bn;
+  for (int d = 0; d < 3; ++d) F[5 + d] = un * B[d] - Bn * u[d] + ch * psi * n[d];
+  F[8] = ch * Bn;
+}
+
+/* fast magnetosonic speed along the unit normal n */
+double sdref_fast_speed(const double* q, const double* n, double gam) {
+  double rho = q[0];
+  double p = pressure(q, gam);
+  double a2 = gam * p / rho;
+  double b2 = (q[5] * q[5] + q[6] * q[6] + q[7] * q[7]) / rho;
+  double Bn = q[5] * n[0] + q[6] * n[1] + q[7] * n[2];
+  double bn2 = Bn * Bn / rho;
+  double s = a2 + b2;
+  double disc = s * s - 4.0 * a2 * bn2;
+  if (disc < 0.0) disc = 0.0;
+  return sqrt(0.5 * (s + sqrt(disc)));
+}
+
+void sdref_rusanov(const double* qL, const double* qR, const double* n, double gam, double ch, double* F) {
+  double FL[9], FR[9];
+  sdref_flux(qL, n, gam, ch, FL);
+  sdref_flux(qR, n, gam, ch, FR);
+  double unL = (qL[1] * n[0] + qL[2] * n[1] + qL[3] * n[2]) / qL[0];
+  double unR = (qR[1] * n[0] + qR[2] * n[1] + qR[3] * n[2]) / qR[0];
+  double lam = fabs(unL) + sdref_fast_speed(qL, n, gam);
+  double lR = fabs(unR) + sdref_fast_speed(qR, n, gam);
+  if (lR > lam) lam = lR;
+  if (ch > lam) lam = ch;
+  for (int v = 0; v < 9; ++v) F[v] = 0.5 * (FL[v] + FR[v]) - 0.5 * lam * (qR[v] - qL[v]);
+}
+
+/* wall / far-field ghost state (reading R9) */
+static void ghost_state(const double* q, const double* n, int bc, const sdref_phys* ph, double* g) {
+  if (bc == SDREF_BC_FARFIELD) {
+    for (int v = 0; v < 9; ++v) g[v] = ph->farfield[v];
+    return;
+  }
+  for (int v = 0; v < 9; ++v) g[v] = q[v];
+  double mn = q[1] * n[0] + q[2] * n[1] + q[3] * n[2];
+  for (int d = 0; d < 3; ++d) g[1 + d] = q[1 + d] - 2.0 * mn * n[d];
+  double Bn = q[5] * n[0] + q[6] * n[1] + q[7] * n[2];
+  if (bc == SDREF_BC_WALL_CONDUCTING) {
+    for (int d = 0; d < 3; ++d) g[5 + d] = q[5 + d] - 2.0 * Bn * n[d];
+  } else {
+    for (int d = 0; d < 3; ++d) g[5 + d] = 2.0 * Bn * n[d] - q[5 + d];
+  }
+}
+
+/* ------------------------------------------------------------------ */
+/* Residual (Sec. SD Method: extrapolate, flux, common flux, derive)   */
+/* ------------------------------------------------------------------ */
+
+static inline int sol_index(int N, int d, int i, int a, int b) {
+  if (d == 0) return i + N * (a + N * b);
+  if (d == 1) return a + N * (i + N * b);
+  return a + N * (b + N * i);
+}
+
+static inline double qat(const sdref_mesh* m, const double* q, int v, int64_t e, int n) {
+  int64_t N3 = (int64_t)m->N * m->N * m->N;
+  return q[((int64_t)v * m->n_e + e) * N3 + n];
+}
+
+/* value of element e's solution extrapolated to point (a,b) of its face F */
+static void face_value(const sdref_mesh* m, const double* q, int64_t e, int F, int a, int b, double* Q) {
+  int N = m->N, d = F / 2, f = (F & 1) ? N : 0;
+  for (int v = 0; v < 9; ++v) {
+    double s = 0.0;
+    for (int i = 0; i < N; ++i) s += m->E[f * N + i] * qat(m, q, v, e, sol_index(N, d, i, a, b));
+    Q[v] = s;
+  }
+}
+
+/* common contravariant flux at point (a,b) of face F of element e, given this side's value Qown.
+ * Ft[9] receives S^d . F* (the family-d contravariant flux), Bt the BR1 value S^d . B*. */
+static void common_flux(const sdref_mesh* m, const sdref_phys* ph, const double* q, int64_t e, int F, int a,
+                        int b, const double* Qown, double* Ft, double* Bt) {
+  int N = m->N, d = F / 2, side = F & 1, f = side ? N : 0;
+  double sgn = side ? 1.0 : -1.0; /* S^d points along increasing d: outward on the d=1 face */
+  int64_t k = 6 * e + F;
+  double Fs[9], Bn, mag;
+  if (m->nb_e[k] < 0) {
+    const double* S = geo_S(m, e, d, f, a, b);
+    mag = sqrt(S[0] * S[0] + S[1] * S[1] + S[2] * S[2]);
+    double n[3] = {sgn * S[0] / mag, sgn * S[1] / mag, sgn * S[2] / mag};
+    double g[9];
+    ghost_state(Qown, n, m->bc[k], ph, g);
+    sdref_rusanov(Qown, g, n, ph->gamma, ph->c_h, Fs);
+    Bn = 0.5 * ((Qown[5] + g[5]) * n[0] + (Qown[6] + g[6]) * n[1] + (Qown[7] + g[7]) * n[2]);
+  } else {
+    int64_t e2 = m->nb_e[k];
+    int F2 = m->nb_f[k], a2, b2;
+    map_point(m->code[k], N, a, b, &a2, &b2);
+    double Q2[9];
+    face_value(m, q, e2, F2, a2, b2, Q2);
+    if (m->owner[k]) {
+      const double* S = geo_S(m, e, d, f, a, b);
+      mag = sqrt(S[0] * S[0] + S[1] * S[1] + S[2] * S[2]);
+      double n[3] = {sgn * S[0] / mag, sgn * S[1] / mag, sgn * S[2] / mag};
+      sdref_rusanov(Qown, Q2, n, ph->gamma, ph->c_h, Fs);
+      Bn = 0.5 * ((Qown[5] + Q2[5]) * n[0] + (Qown[6] + Q2[6]) * n[1] + (Qown[7] + Q2[7]) * n[2]);
+    } else {
+      /* the owner (neighbour) side defines the normal: F* computed with the owner as left state */
+      int d2 = F2 / 2, f2 = (F2 & 1) ? N : 0;
+      double sgn2 = (F2 & 1) ? 1.0 : -1.0;
+      const double* S = geo_S(m, e2, d2, f2, a2, b2);
+      mag = sqrt(S[0] * S[0] + S[1] * S[1] + S[2] * S[2]);
+      double n[3] = {sgn2 * S[0] / mag, sgn2 * S[1] / mag, sgn2 * S[2] / mag};
+      sdref_rusanov(Q2, Qown, n, ph->gamma, ph->c_h, Fs);
+      Bn = 0.5 * ((Q2[5] + Qown[5]) * n[0] + (Q2[6] + Qown[6]) * n[1] + (Q2[7] + Qown[7]) * n[2]);
+      for (int v = 0; v < 9; ++v) Fs[v] = -Fs[v]; /* this side's outward normal is -n */
+      Bn = -Bn;
+    }
+  }
+  for (int v = 0; v < 9; ++v) Ft[v] = sgn * mag * Fs[v];
+  *Bt = sgn * mag * Bn;
+}
+
+/* source vector M (Sec. MHD Governing Equations); mag[] gets the sum of |terms| */
+static void sources(const sdref_phys* ph, const double* Q, double divB, const double* x, double* M, double* mag) {
+  double rho = Q[0];
+  const double* m = Q + 1;
+  const double* B = Q + 5;
+  double u[3] = {m[0] / rho, m[1] / rho, m[2] / rho};
+  for (int v = 0; v < 9; ++v) { M[v] = 0.0; mag[v] = 0.0; }
+  if (ph->gravity) {
+    double r = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+    double g[3] = {-ph->GM * x[0] / (r * r * r), -ph->GM * x[1] / (r * r * r), -ph->GM * x[2] / (r * r * r)};
+    for (int d = 0; d < 3; ++d) { M[1 + d] += rho * g[d]; mag[1 + d] += fabs(rho * g[d]); }
+    double w = m[0] * g[0] + m[1] * g[1] + m[2] * g[2];
+    M[4] += w;
+    mag[4] += fabs(w);
+  }
+  if (ph->coriolis) {
+    /* -2 rho Omega x U with Omega = Omega z: (2 Omega rho v, -2 Omega rho u, 0) */
+    double cx = 2.0 * ph->omega * m[1], cy = -2.0 * ph->omega * m[0];
+    M[1] += cx; M[2] += cy;
+    mag[1] += fabs(cx); mag[2] += fabs(cy);
+  }
+  if (ph->powell) {
+    double uB = u[0] * B[0] + u[1] * B[1] + u[2] * B[2];
+    for (int d = 0; d < 3; ++d) { M[1 + d] -= divB * B[d]; mag[1 + d] += fabs(divB * B[d]); }
+    M[4] -= divB * uB;
+    mag[4] += fabs(divB * uB);
+    for (int d = 0; d < 3; ++d) { M[5 + d] -= divB * u[d]; mag[5 + d] += fabs(divB * u[d]); }
+  }
+  M[8] -= ph->glm_alpha * Q[8];
+  mag[8] += fabs(ph->glm_alpha * Q[8]);
+}
+
+/* residual of one element: out[9][N^3]; divb[N^3] (may be NULL); smax[9] running max of scale */
+static void residual_element(const sdref_mesh* m, const sdref_phys* ph, const double* q, int64_t e, double* out,
+                             double* divb, double* smax) {
+  int N = m->N, N3 = N * N * N;
+  double Qe[9][MAXN * MAXN * MAXN];
+  double div[9][MAXN * MAXN * MAXN], mag[9][MAXN * MAXN * MAXN], dB[MAXN * MAXN * MAXN];
+  for (int v = 0; v < 9; ++v)
+    for (int n = 0; n < N3; ++n) { Qe[v][n] = qat(m, q, v, e, n); div[v][n] = 0.0; mag[v][n] = 0.0; }
+  for (int n = 0; n < N3; ++n) dB[n] = 0.0;
+
+  for (int d = 0; d < 3; ++d)
+    for (int b = 0; b < N; ++b)
+      for (int a = 0; a < N; ++a) {
+        double Qf[MAXN + 1][9], Ft[MAXN + 1][9], Bt[MAXN + 1];
+        /* extrapolate the solution along the line to the family-d flux points */
+        for (int f = 0; f <= N; ++f)
+          for (int v = 0; v < 9; ++v) {
+            double s = 0.0;
+            for (int i = 0; i < N; ++i) s += m->E[f * N + i] * Qe[v][sol_index(N, d, i, a, b)];
+            Qf[f][v] = s;
+          }
+        /* interior flux points: contravariant flux S^d . F(Q) */
+        for (int f = 1; f < N; ++f) {
+          const double* S = geo_S(m, e, d, f, a, b);
+          sdref_flux(Qf[f], S, ph->gamma, ph->c_h, Ft[f]);
+          Bt[f] = S[0] * Qf[f][5] + S[1] * Qf[f][6] + S[2] * Qf[f][7];
+        }
+        /* element-boundary flux points: common (Rusanov / BR1) values */
+        common_flux(m, ph, q, e, 2 * d + 0, a, b, Qf[0], Ft[0], &Bt[0]);
+        common_flux(m, ph, q, e, 2 * d + 1, a, b, Qf[N], Ft[N], &Bt[N]);
+        /* derivative of the flux polynomial at the solution points */
+        for (int i = 0; i < N; ++i) {
+          int n = sol_index(N, d, i, a, b);
+          for (int v = 0; v < 9; ++v) {
+            double s = 0.0, sa = 0.0;
+            for (int f = 0; f <= N; ++f) {
+              double t = m->D[i * (N + 1) + f] * Ft[f][v];
+              s += t;
+              sa += fabs(t);
+            }
+            div[v][n] += s;
+            mag[v][n] += sa;
+          }
+          double s = 0.0;
+          for (int f = 0; f <= N; ++f) s += m->D[i * (N + 1) + f] * Bt[f];
+          dB[n] += s;
+        }
+      }
+
+  for (int n = 0; n < N3; ++n) {
+    double J = geo_J(m, e, n);
+    double divB = dB[n] / J;
+    double Q[9], M[9], Mm[9];
+    for (int v = 0; v < 9; ++v) Q[v] = Qe[v][n];
+    sources(ph, Q, divB, geo_X(m, e, n), M, Mm);
+    for (int v = 0; v < 9; ++v) {
+      out[(int64_t)v * N3 + n] = -div[v][n] / J + M[v];
+      double sc = mag[v][n] / J + Mm[v];
+      if (smax && sc > smax[v]) smax[v] = sc;
+    }
+    if (divb) divb[n] = divB;
+  }
+}
+
+static int check_inputs(const sdref_mesh* m, const sdref_phys* ph, const double* q) {
+  if (!m || !ph || !q) { set_err("null argument"); return 1; }
+  return 0;
+}
+
+int sdref_residual(sdref_mesh* m, const sdref_phys* ph, const double* q, double* dqdt, double* divb, double* scale) {
+  if (check_inputs(m, ph, q) || !dqdt) return 1;
+  if (ensure_geometry(m, NULL)) return 2;
+  int N = m->N;
+  int64_t N3 = (int64_t)N * N * N;
+  int nth = sdref_get_threads();
+  double* sc = (double*)calloc(9 * (size_t)(nth > 0 ? nth : 1), sizeof(double));
+#pragma omp parallel num_threads(nth)
+  {
+    int tid = 0;
+#ifdef _OPENMP
+    tid = omp_get_thread_num();
+#endif
+    double* buf = (double*)malloc(sizeof(double) * 9 * N3);
+    double* db = (double*)malloc(sizeof(double) * N3);
+#pragma omp for schedule(dynamic, 8)
+    for (int64_t e = 0; e < m->n_e; ++e) {
+      residual_element(m, ph, q, e, buf, db, sc + 9 * tid);
+      for (int v = 0; v < 9; ++v)
+        for (int64_t n = 0; n < N3; ++n) dqdt[((int64_t)v * m->n_e + e) * N3 + n] = buf[v * N3 + n];
+      if (divb)
+        for (int64_t n = 0; n < N3; ++n) divb[e * N3 + n] = db[n];
+    }
+    free(buf);
+    free(db);
+  }
+  if (scale) {
+    for (int v = 0; v < 9; ++v) {
+      scale[v] = 0.0;
+      for (int t = 0; t < nth; ++t)
+        if (sc[9 * t + v] > scale[v]) scale[v] = sc[9 * t + v];
+    }
+  }
+  free(sc);
+  return 0;
+}
+
+int sdref_residual_elements(sdref_mesh* m, const sdref_phys* ph, const double* q, int64_t n_list,
+                            const int64_t* elems, double* out, double* scale) {
+  if (check_inputs(m, ph, q) || !elems || !out) return 1;
+  char* need = (char*)calloc(m->n_e, 1);
+  for (int64_t l = 0; l < n_list; ++l) {
+    int64_t e = elems[l];
+    if (e < 0 || e >= m->n_e) { free(need); set_err("element out of range"); return 1; }
+    need[e] = 1;
+    for (int F = 0; F < 6; ++F)
+      if (m->nb_e[6 * e + F] >= 0) need[m->nb_e[6 * e + F]] = 1;
+  }
+  int rc = ensure_geometry(m, need);
+  free(need);
+  if (rc) return rc;
+  int64_t N3 = (int64_t)m->N * m->N * m->N;
+  double smax[9] = {0};
+  for (int64_t l = 0; l < n_list; ++l) residual_element(m, ph, q, elems[l], out + l * 9 * N3, NULL, smax);
+  if (scale)
+    for (int v = 0; v < 9; ++v) scale[v] = smax[v];
+  return 0;
+}
+
+/* Shu-Osher SSP-RK3 stage (reading R11) */
+int sdref_rk_stage(sdref_mesh* m, const sdref_phys* ph, int stage, double dt, const double* q_n, const double* q_in,
+                   double* q_out) {
+  static const double A[3] = {0.0, 0.75, 1.0 / 3.0};
+  static const double Bc[3] = {1.0, 0.25, 2.0 / 3.0};
+  if (stage < 0 || stage > 2) { set_err("stage must be 0, 1 or 2"); return 1; }
+  int64_t tot = 9LL * m->n_e * m->N * m->N * m->N;
+  double* R = (double*)malloc(sizeof(double) * tot);
+  int rc = sdref_residual(m, ph, q_in, R, NULL, NULL);
+  if (rc) { free(R); return rc; }
+  for (int64_t i = 0; i < tot; ++i) {
+    double qn = stage == 0 ? 0.0 : q_n[i];
+    q_out[i] = A[stage] * qn + Bc[stage] * (q_in[i] + dt * R[i]);
+  }
+  free(R);
+  return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Diagnostics (Sec. Results: KE, E_B)                                 */
+/* ------------------------------------------------------------------ */
+
+int sdref_diagnostics(sdref_mesh* m, const sdref_phys* ph, const double* q, sdref_diag* out) {
+  if (check_inputs(m, ph, q) || !out) return 1;
+  int N = m->N;
+  int64_t N3 = (int64_t)N * N * N, tot = 9 * m->n_e * N3;
+  double* R = (double*)malloc(sizeof(double) * tot);
+  double* divb = (double*)malloc(sizeof(double) * m->n_e * N3);
+  int rc = sdref_residual(m, ph, q, R, divb, NULL);
+  free(R);
+  if (rc) { free(divb); return rc; }
+  double ke = 0, eb = 0, mass = 0, en = 0, vol = 0, mdb = 0, lmax = 0, minr = INFINITY, minp = INFINITY;
+  for (int64_t e = 0; e < m->n_e; ++e)
+    for (int k = 0; k < N; ++k)
+      for (int j = 0; j < N; ++j)
+        for (int i = 0; i < N; ++i) {
+          int n = i + N * (j + N * k);
+          double Q[9];
+          for (int v = 0; v < 9; ++v) Q[v] = qat(m, q, v, e, n);
+          double wq = m->w[i] * m->w[j] * m->w[k] * geo_J(m, e, n);
+          double rho = Q[0];
+          double m2 = Q[1] * Q[1] + Q[2] * Q[2] + Q[3] * Q[3];
+          double B2 = Q[5] * Q[5] + Q[6] * Q[6] + Q[7] * Q[7];
+          ke += wq * 0.5 * m2 / rho;
+          eb += wq * 0.5 * B2;
+          mass += wq * rho;
+          en += wq * Q[4];
+          vol += wq;
+          double p = pressure(Q, ph->gamma);
+          double cmax = sqrt(ph->gamma * p / rho + B2 / rho);
+          double lam = sqrt(m2) / rho + cmax;
+          if (lam > lmax || lam != lam) lmax = lam;
+          double ad = fabs(divb[e * N3 + n]);
+          if (ad > mdb || ad != ad) mdb = ad;
+          if (rho < minr || rho != rho) minr = rho;
+          if (p < minp || p != p) minp = p;
+        }
+  free(divb);
+  out->ke = ke / vol;
+  out->eb = eb / vol;
+  out->max_divb = mdb;
+  out->mass = mass;
+  out->energy = en;
+  out->lambda_max = lmax;
+  out->min_rho = minr;
+  out->min_p = minp;
+  out->volume = vol;
+  return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Initial states (Sec. Initial Conditions; reading R12)               */
+/* ------------------------------------------------------------------ */
+
+/* SplitMix64 (Steele, Lea, Flood 2014; Vigna's reference): the (index+1)-th output of the
+ * generator whose state starts at seed. */
+uint64_t sdref_splitmix64(uint64_t seed, uint64_t index) {
+  uint64_t z = seed + (index + 1) * 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+double sdref_uniform(uint64_t seed, uint64_t index) {
+  return 2.0 * ((double)(sdref_splitmix64(seed, index) >> 11) * 0x1.0p-53) - 1.0;
+}
+
+int sdref_polytrope(double r, double N_rho, double r_b, double r_t, double rho_b, double R_gas, double gam,
+                    double GM, double* rho, double* p, double* T) {
+  double Cp = gam * R_gas / (gam - 1.0);
+  double Phi = -GM / r, Phi_b = -GM / r_b, Phi_t = -GM / r_t;
+  double Tb = (Phi_t - Phi_b) / (Cp * (1.0 - exp(-(gam - 1.0) * N_rho)));
+  double pb = rho_b * R_gas * Tb;
+  double z = 1.0 - (Phi - Phi_b) / (Cp * Tb);
+  if (rho) *rho = rho_b * pow(z, 1.0 / (gam - 1.0));
+  if (p) *p = pb * pow(z, gam / (gam - 1.0));
+  if (T) *T = Tb * z;
+  return 0;
+}
+
+static void prim_to_cons(double rho, const double* u, double p, const double* B, double psi, double gam, double* Q) {
+  Q[0] = rho;
+  for (int d = 0; d < 3; ++d) Q[1 + d] = rho * u[d];
+  Q[4] = p / (gam - 1.0) + 0.5 * rho * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]) +
+         0.5 * (B[0] * B[0] + B[1] * B[1] + B[2] * B[2]) + 0.5 * psi * psi;
+  for (int d = 0; d < 3; ++d) Q[5 + d] = B[d];
+  Q[8] = psi;
+}
+
+int sdref_state_init(sdref_mesh* m, const sdref_phys* ph, int kind, const double* P, uint64_t seed, double* q,
+                     double* qbg) {
+  if (!m || !ph || !P || !q) { set_err("null argument"); return 1; }
+  if (ensure_geometry(m, NULL)) return 2;
+  int N = m->N;
+  int64_t N3 = (int64_t)N * N * N;
+  double gam = ph->gamma;
+  double B0dip = 0.0;
+  if (kind == SDREF_INIT_SHELL_POLYTROPE) {
+    /* dipole amplitude: int 1/2 |B|^2 dV = ratio * int p0/(gamma-1) dV over the ideal shell
+     * (reading R12: the kinetic energy is zero at t = 0, so the internal energy is the reference) */
+    double Nr = P[0], rb = P[1], rt = P[2], rhob = P[3], Rg = P[4], ratio = P[6];
+    double IB = 8.0 * M_PI * (pow(rb, -3.0) - pow(rt, -3.0)) / 3.0;
+    double t[64], wg[64], Ip = 0.0;
+    legendre_roots(64, t, wg);
+    for (int qd = 0; qd < 64; ++qd) {
+      double r = 0.5 * (rb + rt) + 0.5 * (rt - rb) * t[qd], pr;
+      sdref_polytrope(r, Nr, rb, rt, rhob, Rg, gam, ph->GM, NULL, &pr, NULL);
+      Ip += 0.5 * (rt - rb) * wg[qd] * pr * r * r;
+    }
+    Ip *= 4.0 * M_PI / (gam - 1.0);
+    B0dip = sqrt(2.0 * ratio * Ip / IB);
+  } else if (kind < 0 || kind > SDREF_INIT_SINB) {
+    set_err("unknown initial state kind");
+    return 1;
+  }
+  for (int64_t e = 0; e < m->n_e; ++e)
+    for (int64_t n = 0; n < N3; ++n) {
+      const double* x = geo_X(m, e, (int)n);
+      double Q[9], Qb[9] = {0};
+      double zero3[3] = {0, 0, 0};
+      if (kind == SDREF_INIT_UNIFORM) {
+        double u[3] = {P[1], P[2], P[3]}, B[3] = {P[5], P[6], P[7]};
+        prim_to_cons(P[0], u, P[4], B, P[8], gam, Q);
+      } else if (kind == SDREF_INIT_ALFVEN) {
+        /* circularly polarised Alfven wave along k with B0 parallel to k */
+        double rho = P[0], p = P[1], B0 = P[2], amp = P[3], k[3] = {P[4], P[5], P[6]}, tt = P[7];
+        double kn = sqrt(k[0] * k[0] + k[1] * k[1] + k[2] * k[2]);
+        double kh[3] = {k[0] / kn, k[1] / kn, k[2] / kn}, zh[3] = {0, 0, 1}, xh[3] = {1, 0, 0}, e1[3], e2[3];
+        cross3(kh, zh, e1);
+        double n1 = sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
+        if (n1 < 1e-8) { cross3(xh, kh, e1); n1 = sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]); }
+        for (int d = 0; d < 3; ++d) e1[d] /= n1;
+        cross3(kh, e1, e2);
+        double om = kn * B0 / sqrt(rho);
+        double ph_ = k[0] * x[0] + k[1] * x[1] + k[2] * x[2] - om * tt;
+        double B[3], u[3];
+        for (int d = 0; d < 3; ++d) {
+          double dB = amp * (cos(ph_) * e1[d] + sin(ph_) * e2[d]);
+          B[d] = B0 * kh[d] + dB;
+          u[d] = -dB / sqrt(rho);
+        }
+        prim_to_cons(rho, u, p, B, 0.0, gam, Q);
+      } else if (kind == SDREF_INIT_SHELL_POLYTROPE) {
+        double Nr = P[0], rb = P[1], rt = P[2], rhob = P[3], Rg = P[4], amp = P[5];
+        double r = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+        double rho0, p0;
+        sdref_polytrope(r, Nr, rb, rt, rhob, Rg, gam, ph->GM, &rho0, &p0, NULL);
+        /* entropy noise: density perturbed at fixed pressure, tapered to zero at both walls */
+        double xi = sdref_uniform(seed, (uint64_t)(e * N3 + n));
+        double rho = rho0 * (1.0 - amp * xi * sin(M_PI * (r - rb) / (rt - rb)));
+        /* dipole B = B0 (3 (z.rhat) rhat - z) / r^3 */
+        double rh[3] = {x[0] / r, x[1] / r, x[2] / r}, B[3];
+        for (int d = 0; d < 3; ++d) B[d] = B0dip * (3.0 * rh[2] * rh[d] - (d == 2 ? 1.0 : 0.0)) / (r * r * r);
+        prim_to_cons(rho, zero3, p0, B, 0.0, gam, Q);
+        prim_to_cons(rho0, zero3, p0, zero3, 0.0, gam, Qb);
+      } else if (kind == SDREF_INIT_DIVB_PULSE) {
+        double rho = P[0], p = P[1], amp = P[2], c[3] = {P[3], P[4], P[5]}, sg = P[6];
+        double r2 = (x[0] - c[0]) * (x[0] - c[0]) + (x[1] - c[1]) * (x[1] - c[1]) + (x[2] - c[2]) * (x[2] - c[2]);
+        double B[3] = {amp * exp(-r2 / (2.0 * sg * sg)), 0.0, 0.0};
+        prim_to_cons(rho, zero3, p, B, 0.0, gam, Q);
+      } else { /* SINB: B = (b sin(2 pi x), 0, 0), uniform rho, p, u */
+        double u[3] = {P[2], P[3], P[4]}, B[3] = {P[5] * sin(2.0 * M_PI * x[0]), 0.0, 0.0};
+        prim_to_cons(P[0], u, P[1], B, 0.0, gam, Q);
+      }
+      for (int v = 0; v < 9; ++v) {
+        q[((int64_t)v * m->n_e + e) * N3 + n] = Q[v];
+        if (qbg) qbg[((int64_t)v * m->n_e + e) * N3 + n] = Qb[v];
+      }
+    }
+  return 0;
+}
