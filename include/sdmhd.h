@@ -1,0 +1,213 @@
+/*
+ * sdmhd.h -- C ABI of the GB300 spectral-difference (SD) MHD+GLM library.
+ *
+ * The library computes, on one GPU, the SD residual and the explicit SSP
+ * Runge-Kutta update of ideal compressible MHD with GLM divergence cleaning
+ * on curved hexahedra (arXiv 2502.17805, "Fully Compressible
+ * Magnetohydrodynamic Simulations of Solar Convection Zones with CHORUS++"):
+ *
+ *   dQ/dt + div F(Q) = M(Q)                     Eq. (1), Sec. MHD Governing Equations
+ *   Q = (rho, rho U, E, B, psi)                 Eq. (2); E as Eq. (3)
+ *   F = inviscid MHD + GLM flux                 Eq. (invF)
+ *   M = gravity, Coriolis, Powell, -a psi       source vector M, same section
+ *   cubed-sphere shell mesh                     Sec. Meshing
+ *   transfinite map, |J|, contravariant flux    Sec. Spectral Difference Method
+ *   Chebyshev-Gauss solution points, Legendre
+ *   flux points, Lagrange extrapolation and
+ *   derivative, BR1 average, Rusanov flux       Sec. Spectral Difference Method
+ *   polytropic hydrostatic initial state        Sec. Initial Conditions
+ *   wall boundary conditions                    Sec. Problem Formulation and Boundary Conditions
+ *   KE and E_B volume averages                  Sec. Results
+ *
+ * Conventions (all calls)
+ *   - State arrays are device pointers to FP64 data in the layout
+ *       q[v * 9-plane][e * elem_stride + n],  n = i + N*(j + N*k),
+ *     v in (rho, rho u, rho v, rho w, E, Bx, By, Bz, psi), i along xi;
+ *     one plane holds n_elements * elem_stride values, elem_stride >= N^3 is
+ *     rounded up so every element starts on a 16-byte boundary
+ *     (see sd_mesh_query).  Q is the physical state (not |J|-weighted).
+ *   - The caller owns every state buffer.  The library owns the mesh,
+ *     geometry, background tables and its scratch buffers.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Work is
+ *     stream-ordered and asynchronous, except where a call says it
+ *     synchronises.
+ *   - No call aborts, prints or exits.  Every failure returns a status and
+ *     leaves a message for sd_last_error().  Device-side waits are bounded.
+ *   - Functions are not thread-safe on one mesh object; distinct mesh objects
+ *     may be used from distinct host threads.
+ */
+#ifndef SDMHD_H
+#define SDMHD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SD_OK = 0,
+  SD_ERR_INVALID_ARGUMENT = 1, /* null pointer, bad size, bad enum value, misaligned buffer */
+  SD_ERR_UNSUPPORTED = 2,      /* order N outside [2, 8] */
+  SD_ERR_MESH_TOPOLOGY = 3,    /* non-conforming mesh: a face shared by >2 elements, corners that do not match */
+  SD_ERR_MESH_GEOMETRY = 4,    /* |J| <= 0 somewhere in an element */
+  SD_ERR_OUT_OF_MEMORY = 5,    /* a device or host allocation failed */
+  SD_ERR_CUDA = 6,             /* a CUDA runtime call or kernel launch failed */
+  SD_ERR_NONPHYSICAL = 7,      /* rho <= 0, p <= 0 or NaN met by sd_diagnostics */
+  SD_ERR_TIMEOUT = 8           /* a bounded device-side wait ran out */
+} sd_status;
+
+typedef enum { SD_FP64 = 0, SD_FP32_MIXED = 1 } sd_precision;
+
+/* Boundary conditions of unmatched faces (Sec. Problem Formulation and Boundary
+ * Conditions).  Walls are impenetrable (U.n = 0); the inviscid ghost state
+ * copies rho, p, psi and E, reflects U, and for the magnetic field either
+ * reflects B (perfectly conducting, B_n -> -B_n) or reverses the tangential
+ * field (perfectly radial, B_t -> -B_t).  FARFIELD uses sd_phys.farfield as
+ * the ghost state (for tests).  PERIODIC is only valid for matched faces. */
+typedef enum { SD_BC_PERIODIC = 0, SD_BC_WALL_CONDUCTING = 1, SD_BC_WALL_RADIAL = 2, SD_BC_FARFIELD = 3 } sd_bc;
+
+/* Initial states (sd_init.kind) and their params[]:
+ *  SD_INIT_UNIFORM         rho, u, v, w, p, Bx, By, Bz, psi
+ *  SD_INIT_ALFVEN          rho, p, |B0|, amplitude, kx, ky, kz, t: circularly polarised
+ *                          Alfven wave along k, B0 parallel to k, U = -dB/sqrt(rho)
+ *  SD_INIT_SHELL_POLYTROPE N_rho, r_b, r_t, rho_b, R_gas, noise amplitude, dipole ratio:
+ *                          polytrope of Sec. Initial Conditions (Eq. polytrop eqns, T_b), gamma and
+ *                          GM from sd_phys; density noise at fixed pressure,
+ *                          rho0 (1 - A xi sin(pi (r - r_b)/(r_t - r_b))), xi = SplitMix64 draw in
+ *                          [-1, 1) keyed by (seed, e*N^3 + n); dipole B0 (3 (z.r)r - z)/r^3 scaled
+ *                          so that its magnetic energy is `ratio` times the internal energy
+ *  SD_INIT_DIVB_PULSE      rho, p, amplitude, cx, cy, cz, sigma: Bx Gaussian bump, U = 0 */
+typedef enum { SD_INIT_UNIFORM = 0, SD_INIT_ALFVEN = 1, SD_INIT_SHELL_POLYTROPE = 2, SD_INIT_DIVB_PULSE = 3 } sd_init_kind;
+
+typedef struct {
+  int32_t order;              /* N: solution points per direction, 2..8 (Sec. SD Method) */
+  int32_t geom;               /* 0: straight edges (trilinear); 1: spherical shell about the origin */
+  int64_t n_vertices;
+  const double* vertices;     /* host [n_vertices][3] */
+  int64_t n_elements;
+  const int64_t* hex;         /* host [n_elements][8]; corner (i,j,k) -> i + 2j + 4k, right-handed */
+  const double* periodic_lengths; /* host [3] or NULL; entries > 0 make that direction periodic */
+  double r_inner, r_outer;    /* shell radii (geom = 1): classify boundary faces as inner / outer */
+  int32_t bc_inner, bc_outer; /* sd_bc of inner / outer boundary faces (geom 0: bc_inner for all) */
+} sd_mesh_desc;
+
+typedef struct {
+  double gamma;     /* ratio of specific heats */
+  double GM;        /* gravity g = -GM x / |x|^3 (source M) */
+  double omega;     /* rotation rate about z (Coriolis -2 rho Omega x U) */
+  double glm_alpha; /* damping a of the GLM source -a psi */
+  double c_h;       /* GLM speed used in the flux and the Rusanov speed */
+  int32_t powell;   /* 1: Powell terms -(div B)(B, U.B, U) in M */
+  int32_t gravity;  /* 1: rho g and rho U.g in M */
+  int32_t coriolis; /* 1: Coriolis force in M */
+  int32_t pad_;
+  double farfield[9]; /* conserved ghost state of SD_BC_FARFIELD faces */
+} sd_phys;
+
+typedef struct {
+  int32_t kind; /* sd_init_kind */
+  int32_t pad_;
+  double params[16];
+  uint64_t seed;
+} sd_init;
+
+typedef struct {
+  double ke;         /* (1/V) int 1/2 rho |U|^2 dV        (Sec. Results, KE) */
+  double eb;         /* (1/V) int 1/2 |B|^2 dV            (Sec. Results, E_B) */
+  double max_divb;   /* max over solution points of |div B| (discrete SD divergence, BR1 faces) */
+  double mass;       /* int rho dV */
+  double energy;     /* int E dV */
+  double lambda_max; /* max over solution points of |U| + sqrt(gamma p / rho + |B|^2 / rho) */
+  double min_rho, min_p;
+  double volume;     /* int dV */
+} sd_diag;
+
+typedef struct {
+  int32_t order;
+  int32_t p_map;           /* degree of the polynomial geometry map, floor(N/2) */
+  int64_t n_elements;
+  int64_t n_points;        /* n_elements * N^3: the degrees of freedom per variable (Sec. Meshing) */
+  int64_t elem_stride;     /* values between consecutive elements in one variable plane */
+  int64_t state_bytes;     /* bytes of one state array: 9 * n_elements * elem_stride * 8 */
+  int64_t n_boundary_faces;
+  int64_t n_interior_faces;
+  double h_min;            /* smallest element edge chord, for the time-step rule */
+  int64_t device_bytes;    /* bytes the library holds on the device for this mesh */
+} sd_mesh_info;
+
+typedef struct sd_mesh sd_mesh;
+typedef struct sd_background sd_background;
+
+/* Last error message of the calling host thread ("" when none). */
+const char* sd_last_error(void);
+
+/* Build a mesh on the current device: copies the host description, matches
+ * faces (sorted corner ids; periodic directions unwrap corners by the period),
+ * computes orientation codes, then runs the geometry kernel: the transfinite
+ * map of each hexahedron (bilinear edge projectors minus twice the trilinear
+ * corner projector, Sec. SD Method) sampled at Chebyshev-Lobatto nodes as a
+ * degree-floor(N/2) polynomial map, its contravariant metrics S^d = |J| grad xi_d
+ * at the flux points, |J| and x at the solution points.  Synchronises `stream`.
+ * Errors: SD_ERR_INVALID_ARGUMENT, SD_ERR_UNSUPPORTED, SD_ERR_MESH_TOPOLOGY,
+ * SD_ERR_MESH_GEOMETRY, SD_ERR_OUT_OF_MEMORY, SD_ERR_CUDA.  *out is NULL on error. */
+sd_status sd_mesh_create(const sd_mesh_desc* desc, void* stream, sd_mesh** out);
+sd_status sd_mesh_destroy(sd_mesh* mesh);
+sd_status sd_mesh_query(const sd_mesh* mesh, sd_mesh_info* out);
+
+/* Write the initial state (Sec. Initial Conditions) at the solution points.
+ * q: device state (layout above).  q_background: device state or NULL; for
+ * SD_INIT_SHELL_POLYTROPE it receives the noise-free, field-free polytrope
+ * (rho0, 0, p0/(gamma-1), 0, 0), otherwise zeros.  Asynchronous. */
+sd_status sd_state_init(const sd_mesh* mesh, const sd_phys* phys, const sd_init* init, double* q,
+                        double* q_background, void* stream);
+
+/* Prepare the FP32-mixed precision path around a hydrostatic background Q0
+ * (device state, only rho and E are read; U = B = psi = 0 is assumed):
+ * rounds rho0 and p0 to FP32, computes in FP64 the background residual R0
+ * (pressure gradient with central face average, plus rho0 g) and the FP64 jumps
+ * of the background across faces.  The handle stays valid while the mesh
+ * lives.  Synchronises `stream`. */
+sd_status sd_background_create(const sd_mesh* mesh, const sd_phys* phys, const double* q_background, void* stream,
+                               sd_background** out);
+sd_status sd_background_destroy(sd_background* bg);
+
+/* dqdt = -div F / |J| + M at every solution point (Sec. SD Method: extrapolate to
+ * the flux points, contravariant flux, Rusanov / BR1 common values at element
+ * faces, derivative of the flux polynomials).  q and dqdt: device states.
+ * SD_FP64: every step in FP64.  SD_FP32_MIXED: needs `bg`; the perturbation
+ * about the background is carried through the SD operators in FP32 and added
+ * to the FP64 background residual.  Asynchronous. */
+sd_status sd_residual(const sd_mesh* mesh, const sd_phys* phys, sd_precision prec, const double* q,
+                      const sd_background* bg, double* dqdt, void* stream);
+
+/* One stage of the Shu-Osher SSP-RK3 scheme with the residual fused in:
+ *   stage 0: q_out = q_in + dt R(q_in)                       (q_n ignored)
+ *   stage 1: q_out = 3/4 q_n + 1/4 (q_in + dt R(q_in))
+ *   stage 2: q_out = 1/3 q_n + 2/3 (q_in + dt R(q_in))
+ * The RK combination is always FP64.  q_out may alias q_in or q_n.  Stage 0
+ * recomputes the face traces of q_in; stages 1 and 2 reuse the traces the
+ * previous stage wrote for its q_out when q_in is that buffer, so the
+ * intermediate states must not be changed outside the library between the
+ * stages of one step.  Asynchronous. */
+sd_status sd_rk_stage(const sd_mesh* mesh, const sd_phys* phys, sd_precision prec, int32_t stage, double dt,
+                      const double* q_n, const double* q_in, double* q_out, const sd_background* bg, void* stream);
+
+/* One full SSP-RK3 step with device-side step control: lambda_max of q (max of
+ * |U| + fast speed over the solution points), dt = cfl * h_min / (N lambda_max),
+ * c_h = lambda_max when phys->c_h <= 0 (else phys->c_h), then the three fused
+ * stages.  q (in/out) and work: device states; dt_out: device double[2] or NULL,
+ * receives (dt, c_h).  No host synchronisation.  Asynchronous. */
+sd_status sd_step(const sd_mesh* mesh, const sd_phys* phys, sd_precision prec, double cfl, double* q, double* work,
+                  const sd_background* bg, double* dt_out, void* stream);
+
+/* Global diagnostics of q in FP64 (Sec. Results: KE, E_B), with the discrete
+ * div B of the residual (BR1 face average) for max|div B|.  Sums run in a fixed
+ * order (deterministic).  Synchronises `stream`; returns SD_ERR_NONPHYSICAL
+ * (with *out filled) when rho <= 0, p <= 0 or a NaN is found. */
+sd_status sd_diagnostics(const sd_mesh* mesh, const sd_phys* phys, const double* q, sd_diag* out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SDMHD_H */

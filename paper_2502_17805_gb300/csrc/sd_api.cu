@@ -1,0 +1,762 @@
+// sd_api.cu -- host side of the C ABI declared in include/sdmhd.h.
+//
+// Mesh construction (face matching, orientation codes, boundary tagging,
+// operator tables) runs on the host; everything per solution point or flux
+// point runs in the CUDA kernels of this library.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <array>
+#include <string>
+#include <vector>
+
+#include "sd_internal.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+sd_status fail(sd_status st, const std::string& msg) {
+  g_err = msg;
+  return st;
+}
+
+sd_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(SD_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define SD_CUDA(call)                                          \
+  do {                                                         \
+    cudaError_t e_ = (call);                                   \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);        \
+  } while (0)
+
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) {
+      ok = false;
+      return;
+    }
+    if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+  }
+  ~DeviceGuard() {
+    int cur;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+// ---------------------------------------------------------------- 1D operators
+
+// Legendre polynomial P_M and its derivative at x (Bonnet recurrence)
+void legendre(int M, double x, double* P, double* dP) {
+  double a = 1.0, b = x;
+  if (M == 0) {
+    *P = 1.0;
+    *dP = 0.0;
+    return;
+  }
+  for (int k = 2; k <= M; ++k) {
+    const double c = ((2.0 * k - 1.0) * x * b - (k - 1.0) * a) / k;
+    a = b;
+    b = c;
+  }
+  *P = b;
+  *dP = M * (a - x * b) / (1.0 - x * x);
+}
+
+// Gauss-Legendre nodes (ascending) and weights on [-1, 1] by Newton iteration
+void gauss_legendre(int M, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(M, 0.0);
+  w.assign(M, 0.0);
+  for (int k = 0; k < M; ++k) {
+    double t = -cos(M_PI * (k + 0.75) / (M + 0.5));
+    for (int it = 0; it < 60; ++it) {
+      double P, dP;
+      legendre(M, t, &P, &dP);
+      const double step = P / dP;
+      t -= step;
+      if (fabs(step) < 1e-16) break;
+    }
+    double P, dP;
+    legendre(M, t, &P, &dP);
+    x[k] = t;
+    w[k] = 2.0 / ((1.0 - t * t) * dP * dP);
+  }
+  std::sort(x.begin(), x.end());
+  for (int k = 0; k < M; ++k) {
+    double P, dP;
+    legendre(M, x[k], &P, &dP);
+    w[k] = 2.0 / ((1.0 - x[k] * x[k]) * dP * dP);
+  }
+}
+
+double lagr(const double* z, int n, int i, double t) {
+  double v = 1.0;
+  for (int s = 0; s < n; ++s)
+    if (s != i) v *= (t - z[s]) / (z[i] - z[s]);
+  return v;
+}
+
+double lagr_d(const double* z, int n, int i, double t) {
+  double sum = 0.0;
+  for (int m = 0; m < n; ++m) {
+    if (m == i) continue;
+    double pr = 1.0 / (z[i] - z[m]);
+    for (int s = 0; s < n; ++s)
+      if (s != i && s != m) pr *= (t - z[s]) / (z[i] - z[s]);
+    sum += pr;
+  }
+  return sum;
+}
+
+// Solution points: Chebyshev-Gauss, X_s,n = (1 - cos((2n-1) pi / 2N)) / 2.
+// Flux points: 0, the N-1 roots of P_{N-1} mapped to [0, 1], and 1 (N+1 points).
+void build_ops(int N, sd::Ops<double>& o) {
+  memset(&o, 0, sizeof(o));
+  for (int n = 0; n < N; ++n) o.xs[n] = 0.5 * (1.0 - cos((2.0 * n + 1.0) * M_PI / (2.0 * N)));
+  std::vector<double> r, wr;
+  gauss_legendre(N - 1, r, wr);
+  o.xf[0] = 0.0;
+  for (int k = 0; k < N - 1; ++k) o.xf[k + 1] = 0.5 * (r[k] + 1.0);
+  o.xf[N] = 1.0;
+  for (int f = 0; f <= N; ++f)
+    for (int i = 0; i < N; ++i) o.E[f * N + i] = lagr(o.xs, N, i, o.xf[f]);
+  for (int i = 0; i < N; ++i)
+    for (int f = 0; f <= N; ++f) o.D[i * (N + 1) + f] = lagr_d(o.xf, N + 1, f, o.xs[i]);
+  std::vector<double> g, gw;
+  gauss_legendre(N + 3, g, gw);
+  for (int i = 0; i < N; ++i) {
+    double s = 0.0;
+    for (int k = 0; k < N + 3; ++k) s += 0.5 * gw[k] * lagr(o.xs, N, i, 0.5 * (g[k] + 1.0));
+    o.w[i] = s;
+  }
+}
+
+void ops_to_f32(const sd::Ops<double>& a, sd::Ops<float>& b) {
+  for (int i = 0; i < (sd::kMaxN + 1) * sd::kMaxN; ++i) {
+    b.E[i] = (float)a.E[i];
+    b.D[i] = (float)a.D[i];
+  }
+  for (int i = 0; i < sd::kMaxN; ++i) {
+    b.w[i] = (float)a.w[i];
+    b.xs[i] = (float)a.xs[i];
+  }
+  for (int i = 0; i <= sd::kMaxN; ++i) b.xf[i] = (float)a.xf[i];
+}
+
+// ---------------------------------------------------------------- mesh topology
+
+// corner of face F at face-local corner (s, t); the face-local axes are the two
+// remaining directions in increasing order
+int face_corner(int F, int s, int t) {
+  const int d = F >> 1, side = F & 1;
+  int c[3];
+  c[d] = side;
+  c[d == 0 ? 1 : 0] = s;
+  c[d == 2 ? 1 : 2] = t;
+  return c[0] + 2 * c[1] + 4 * c[2];
+}
+
+// orientation code of the map (a, b) on face F1 of e1 -> (a', b') on face F2 of e2
+int orientation(const int64_t* hex, int64_t e1, int F1, int64_t e2, int F2) {
+  int s0 = -1, t0 = -1, s1 = -1, t1 = -1, s2 = -1, t2 = -1;
+  const int64_t v00 = hex[8 * e1 + face_corner(F1, 0, 0)];
+  const int64_t v10 = hex[8 * e1 + face_corner(F1, 1, 0)];
+  const int64_t v01 = hex[8 * e1 + face_corner(F1, 0, 1)];
+  for (int s = 0; s < 2; ++s)
+    for (int t = 0; t < 2; ++t) {
+      const int64_t v = hex[8 * e2 + face_corner(F2, s, t)];
+      if (v == v00) { s0 = s; t0 = t; }
+      if (v == v10) { s1 = s; t1 = t; }
+      if (v == v01) { s2 = s; t2 = t; }
+    }
+  if (s0 < 0 || s1 < 0 || s2 < 0) return -1;
+  // the second face must be reached consistently: the two probed axes must differ
+  if ((s1 != s0) == (s2 != s0)) return -1;
+  if (s1 != s0) {
+    if (t1 != t0 || s2 != s0 || t2 == t0) return -1;
+    return (0 << 2) | ((s0 == 1) << 1) | (t0 == 1);
+  }
+  if (t1 == t0 || s2 == s0 || t2 != t0) return -1;
+  return (1 << 2) | ((s0 == 1) << 1) | (t0 == 1);
+}
+
+int64_t round_stride(int N) {
+  const int64_t n3 = (int64_t)N * N * N;
+  return (n3 + 1) / 2 * 2;  // 16-byte aligned element starts for FP64
+}
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count, int64_t* bytes) {
+  *bytes += (int64_t)(count * sizeof(T));
+  return cudaMalloc((void**)p, count * sizeof(T) + 16);
+}
+
+void free_mesh(sd_mesh* m) {
+  if (!m) return;
+  void* ptrs[] = {m->Sfam64, m->invJ64, m->X64, m->Sfam32, m->invJ32, m->X32, m->nbr, m->meta,
+                  m->tr64[0], m->tr64[1], m->tr32[0], m->tr32[1], m->dyn, m->diag_part, m->diag_out, m->divb};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (m->host_diag) cudaFreeHost(m->host_diag);
+  delete m;
+}
+
+sd_status check_state_ptr(const void* p, const char* name) {
+  if (!p) return fail(SD_ERR_INVALID_ARGUMENT, std::string(name) + " is NULL");
+  if (((uintptr_t)p & 15) != 0) return fail(SD_ERR_INVALID_ARGUMENT, std::string(name) + " is not 16-byte aligned");
+  return SD_OK;
+}
+
+sd::StageParams base_params(const sd_mesh* m, const sd_phys* ph, int prec) {
+  sd::StageParams P;
+  memset(&P, 0, sizeof(P));
+  P.n_e = m->n_e;
+  P.stride = m->stride;
+  P.plane = m->n_e * m->stride;
+  P.gamma = ph->gamma;
+  P.GM = ph->GM;
+  P.omega = ph->omega;
+  P.alpha = ph->glm_alpha;
+  P.c_h = ph->c_h;
+  P.powell = ph->powell;
+  P.gravity = ph->gravity;
+  P.coriolis = ph->coriolis;
+  for (int v = 0; v < 9; ++v) P.farfield[v] = ph->farfield[v];
+  if (prec == SD_FP64) {
+    P.Sfam = m->Sfam64;
+    P.invJ = m->invJ64;
+    P.X = m->X64;
+  } else {
+    P.Sfam = m->Sfam32;
+    P.invJ = m->invJ32;
+    P.X = m->X32;
+  }
+  P.nbr = m->nbr;
+  P.meta = m->meta;
+  return P;
+}
+
+void* trace_buf(sd_mesh* m, int prec, int b) { return prec == SD_FP64 ? (void*)m->tr64[b] : (void*)m->tr32[b]; }
+
+sd_status check_common(const sd_mesh* m, const sd_phys* ph, int prec, const sd_background* bg) {
+  if (!m) return fail(SD_ERR_INVALID_ARGUMENT, "mesh is NULL");
+  if (!ph) return fail(SD_ERR_INVALID_ARGUMENT, "phys is NULL");
+  if (prec != SD_FP64 && prec != SD_FP32_MIXED) return fail(SD_ERR_INVALID_ARGUMENT, "unknown precision");
+  if (!(ph->gamma > 1.0)) return fail(SD_ERR_INVALID_ARGUMENT, "gamma must exceed 1");
+  if (prec == SD_FP32_MIXED) {
+    if (!bg) return fail(SD_ERR_INVALID_ARGUMENT, "the FP32-mixed path needs a background (sd_background_create)");
+    if (bg->mesh != m) return fail(SD_ERR_INVALID_ARGUMENT, "background belongs to another mesh");
+    if (bg->gamma != ph->gamma) return fail(SD_ERR_INVALID_ARGUMENT, "background was built with another gamma");
+  }
+  return SD_OK;
+}
+
+// polytrope pressure at radius r (Sec. Initial Conditions), for the dipole scaling
+double polytrope_p(double r, double Nr, double rb, double rt, double rhob, double Rg, double g, double GM) {
+  const double Cp = g * Rg / (g - 1.0);
+  const double Tb = (GM / rb - GM / rt) / (Cp * (1.0 - exp(-(g - 1.0) * Nr)));
+  const double zeta = 1.0 - (GM / rb - GM / r) / (Cp * Tb);
+  return rhob * Rg * Tb * pow(zeta, g / (g - 1.0));
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sd_last_error(void) { return g_err.c_str(); }
+
+sd_status sd_mesh_create(const sd_mesh_desc* desc, void* stream, sd_mesh** out) {
+  if (!out) return fail(SD_ERR_INVALID_ARGUMENT, "out is NULL");
+  *out = nullptr;
+  if (!desc) return fail(SD_ERR_INVALID_ARGUMENT, "desc is NULL");
+  const int N = desc->order;
+  if (N < 2 || N > sd::kMaxN) return fail(SD_ERR_UNSUPPORTED, "order N must be in [2, 8]");
+  if (desc->n_elements < 0 || desc->n_vertices < 0) return fail(SD_ERR_INVALID_ARGUMENT, "negative size");
+  if (desc->n_elements > 0 && (!desc->hex || !desc->vertices))
+    return fail(SD_ERR_INVALID_ARGUMENT, "vertices or hex is NULL");
+  if (desc->geom != 0 && desc->geom != 1) return fail(SD_ERR_INVALID_ARGUMENT, "geom must be 0 or 1");
+  if (desc->n_elements > (int64_t)1 << 30) return fail(SD_ERR_INVALID_ARGUMENT, "too many elements");
+  const int bcs[2] = {desc->bc_inner, desc->bc_outer};
+  for (int b : bcs)
+    if (b < SD_BC_PERIODIC || b > SD_BC_FARFIELD) return fail(SD_ERR_INVALID_ARGUMENT, "unknown boundary condition");
+  const int64_t n_e = desc->n_elements, n_v = desc->n_vertices;
+  const int64_t* hex = desc->hex;
+  for (int64_t i = 0; i < 8 * n_e; ++i)
+    if (hex[i] < 0 || hex[i] >= n_v) return fail(SD_ERR_INVALID_ARGUMENT, "vertex index out of range");
+  double per[3] = {0.0, 0.0, 0.0};
+  if (desc->periodic_lengths)
+    for (int d = 0; d < 3; ++d) per[d] = desc->periodic_lengths[d] > 0.0 ? desc->periodic_lengths[d] : 0.0;
+
+  // ---- corners, unwrapped across periodic directions relative to corner 0
+  std::vector<double> corners((size_t)n_e * 24);
+  for (int64_t e = 0; e < n_e; ++e) {
+    const double* v0 = desc->vertices + 3 * hex[8 * e];
+    for (int c = 0; c < 8; ++c) {
+      const double* v = desc->vertices + 3 * hex[8 * e + c];
+      for (int d = 0; d < 3; ++d) {
+        double x = v[d];
+        if (per[d] > 0.0) x += per[d] * std::nearbyint((v0[d] - v[d]) / per[d]);
+        corners[e * 24 + 3 * c + d] = x;
+      }
+    }
+    for (int c = 0; c < 8; ++c)
+      for (int c2 = c + 1; c2 < 8; ++c2)
+        if (hex[8 * e + c] == hex[8 * e + c2]) return fail(SD_ERR_MESH_TOPOLOGY, "element with repeated corners");
+  }
+
+  // ---- face matching: sort the 6 n_e faces by their sorted corner ids
+  struct FaceKey {
+    std::array<int64_t, 4> k;
+    int64_t e;
+    int F;
+  };
+  std::vector<FaceKey> faces((size_t)n_e * 6);
+  for (int64_t e = 0; e < n_e; ++e)
+    for (int F = 0; F < 6; ++F) {
+      FaceKey& fk = faces[e * 6 + F];
+      for (int s = 0; s < 2; ++s)
+        for (int t = 0; t < 2; ++t) fk.k[2 * s + t] = hex[8 * e + face_corner(F, s, t)];
+      std::sort(fk.k.begin(), fk.k.end());
+      fk.e = e;
+      fk.F = F;
+    }
+  std::sort(faces.begin(), faces.end(), [](const FaceKey& a, const FaceKey& b) {
+    if (a.k != b.k) return a.k < b.k;
+    if (a.e != b.e) return a.e < b.e;
+    return a.F < b.F;
+  });
+  std::vector<int> nbr((size_t)n_e * 6, -1), meta((size_t)n_e * 6, 0);
+  int64_t n_bf = 0, n_if = 0;
+  for (size_t i = 0; i < faces.size();) {
+    size_t j = i + 1;
+    while (j < faces.size() && faces[j].k == faces[i].k) ++j;
+    if (j - i > 2) return fail(SD_ERR_MESH_TOPOLOGY, "a face is shared by more than two elements");
+    if (j - i == 2) {
+      const FaceKey& A = faces[i];
+      const FaceKey& B = faces[i + 1];
+      const int cab = orientation(hex, A.e, A.F, B.e, B.F), cba = orientation(hex, B.e, B.F, A.e, A.F);
+      if (cab < 0 || cba < 0) return fail(SD_ERR_MESH_TOPOLOGY, "matched faces with inconsistent corners");
+      nbr[A.e * 6 + A.F] = (int)B.e;
+      nbr[B.e * 6 + B.F] = (int)A.e;
+      meta[A.e * 6 + A.F] = B.F | (cab << 3) | (1 << 9);
+      meta[B.e * 6 + B.F] = A.F | (cba << 3);
+      ++n_if;
+    } else {
+      const FaceKey& A = faces[i];
+      int bc = desc->bc_inner;
+      if (desc->geom == 1) {
+        double c[3] = {0, 0, 0};
+        for (int s = 0; s < 2; ++s)
+          for (int t = 0; t < 2; ++t) {
+            const int cc = face_corner(A.F, s, t);
+            for (int d = 0; d < 3; ++d) c[d] += 0.25 * corners[A.e * 24 + 3 * cc + d];
+          }
+        const double rc = sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+        bc = rc < 0.5 * (desc->r_inner + desc->r_outer) ? desc->bc_inner : desc->bc_outer;
+      }
+      if (bc == SD_BC_PERIODIC) return fail(SD_ERR_MESH_TOPOLOGY, "unmatched face under a periodic boundary");
+      meta[A.e * 6 + A.F] = bc << 6;
+      ++n_bf;
+    }
+    i = j;
+  }
+
+  // ---- smallest edge chord
+  static const int edges[12][2] = {{0, 1}, {2, 3}, {4, 5}, {6, 7}, {0, 2}, {1, 3},
+                                   {4, 6}, {5, 7}, {0, 4}, {1, 5}, {2, 6}, {3, 7}};
+  double hmin = INFINITY;
+  for (int64_t e = 0; e < n_e; ++e)
+    for (int k = 0; k < 12; ++k) {
+      const double* a = &corners[e * 24 + 3 * edges[k][0]];
+      const double* b = &corners[e * 24 + 3 * edges[k][1]];
+      const double l = sqrt((a[0] - b[0]) * (a[0] - b[0]) + (a[1] - b[1]) * (a[1] - b[1]) + (a[2] - b[2]) * (a[2] - b[2]));
+      hmin = std::min(hmin, l);
+    }
+
+  // ---- device objects
+  sd_mesh* m = new sd_mesh;
+  memset(m, 0, sizeof(sd_mesh));
+  if (cudaGetDevice(&m->device) != cudaSuccess) {
+    delete m;
+    return fail(SD_ERR_CUDA, "no CUDA device");
+  }
+  m->N = N;
+  m->p = N / 2;
+  m->n_e = n_e;
+  m->stride = round_stride(N);
+  m->n_bf = n_bf;
+  m->n_if = n_if;
+  m->h_min = hmin;
+  m->geom = desc->geom;
+  build_ops(N, m->ops64);
+  ops_to_f32(m->ops64, m->ops32);
+  const int64_t N2 = (int64_t)N * N, N3 = N2 * N, NF = N + 1;
+  const size_t ne = (size_t)std::max<int64_t>(n_e, 1);
+  int64_t bytes = 0;
+  cudaError_t err = cudaSuccess;
+#define ALLOC(ptr, cnt)                                   \
+  if (err == cudaSuccess) err = dalloc(&(ptr), (cnt), &bytes);
+  ALLOC(m->Sfam64, ne * 9 * N2 * NF);
+  ALLOC(m->invJ64, ne * N3);
+  ALLOC(m->X64, ne * 3 * N3);
+  ALLOC(m->Sfam32, ne * 9 * N2 * NF);
+  ALLOC(m->invJ32, ne * N3);
+  ALLOC(m->X32, ne * 3 * N3);
+  ALLOC(m->nbr, ne * 6);
+  ALLOC(m->meta, ne * 6);
+  ALLOC(m->tr64[0], ne * 6 * 9 * N2);
+  ALLOC(m->tr64[1], ne * 6 * 9 * N2);
+  ALLOC(m->tr32[0], ne * 6 * 9 * N2);
+  ALLOC(m->tr32[1], ne * 6 * 9 * N2);
+  ALLOC(m->dyn, 4);
+  ALLOC(m->diag_part, ne * 12);
+  ALLOC(m->diag_out, 12);
+  ALLOC(m->divb, ne * N3);
+#undef ALLOC
+  if (err == cudaSuccess) err = cudaMallocHost((void**)&m->host_diag, 12 * sizeof(double));
+  m->device_bytes = bytes;
+  if (err != cudaSuccess) {
+    free_mesh(m);
+    cudaGetLastError();
+    return fail(err == cudaErrorMemoryAllocation ? SD_ERR_OUT_OF_MEMORY : SD_ERR_CUDA,
+                std::string("allocation failed: ") + cudaGetErrorString(err));
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  double* d_corners = nullptr;
+  int* d_flag = nullptr;
+  int h_flag = 0;
+  auto cleanup = [&]() {
+    if (d_corners) cudaFree(d_corners);
+    if (d_flag) cudaFree(d_flag);
+  };
+  err = cudaMalloc((void**)&d_corners, ne * 24 * sizeof(double));
+  if (err == cudaSuccess) err = cudaMalloc((void**)&d_flag, sizeof(int));
+  if (err == cudaSuccess && n_e > 0)
+    err = cudaMemcpyAsync(d_corners, corners.data(), n_e * 24 * sizeof(double), cudaMemcpyHostToDevice, s);
+  if (err == cudaSuccess && n_e > 0)
+    err = cudaMemcpyAsync(m->nbr, nbr.data(), n_e * 6 * sizeof(int), cudaMemcpyHostToDevice, s);
+  if (err == cudaSuccess && n_e > 0)
+    err = cudaMemcpyAsync(m->meta, meta.data(), n_e * 6 * sizeof(int), cudaMemcpyHostToDevice, s);
+  if (err == cudaSuccess) err = cudaMemsetAsync(d_flag, 0, sizeof(int), s);
+  if (err == cudaSuccess) err = sd::launch_geometry(m, d_corners, d_flag, s);
+  if (err == cudaSuccess) err = sd::launch_canonical_faces(m, s);
+  if (err == cudaSuccess) err = cudaMemcpyAsync(&h_flag, d_flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+  cleanup();
+  if (err != cudaSuccess) {
+    free_mesh(m);
+    return cuda_fail(err, "mesh geometry");
+  }
+  if (h_flag) {
+    free_mesh(m);
+    return fail(SD_ERR_MESH_GEOMETRY, "non-positive Jacobian in the element map (left-handed or degenerate element)");
+  }
+  *out = m;
+  return SD_OK;
+}
+
+sd_status sd_mesh_destroy(sd_mesh* m) {
+  if (!m) return SD_OK;
+  DeviceGuard g(m->device);
+  free_mesh(m);
+  return SD_OK;
+}
+
+sd_status sd_mesh_query(const sd_mesh* m, sd_mesh_info* out) {
+  if (!m || !out) return fail(SD_ERR_INVALID_ARGUMENT, "null argument");
+  out->order = m->N;
+  out->p_map = m->p;
+  out->n_elements = m->n_e;
+  out->n_points = m->n_e * m->N * m->N * m->N;
+  out->elem_stride = m->stride;
+  out->state_bytes = 9 * m->n_e * m->stride * (int64_t)sizeof(double);
+  out->n_boundary_faces = m->n_bf;
+  out->n_interior_faces = m->n_if;
+  out->h_min = m->h_min;
+  out->device_bytes = m->device_bytes;
+  return SD_OK;
+}
+
+sd_status sd_state_init(const sd_mesh* m, const sd_phys* ph, const sd_init* in, double* q, double* qbg, void* stream) {
+  if (!m || !ph || !in) return fail(SD_ERR_INVALID_ARGUMENT, "null argument");
+  sd_status st = check_state_ptr(q, "q");
+  if (st != SD_OK) return st;
+  if (qbg && (((uintptr_t)qbg & 15) != 0)) return fail(SD_ERR_INVALID_ARGUMENT, "q_background is not 16-byte aligned");
+  if (in->kind < SD_INIT_UNIFORM || in->kind > SD_INIT_DIVB_PULSE) return fail(SD_ERR_INVALID_ARGUMENT, "unknown init kind");
+  if (!(ph->gamma > 1.0)) return fail(SD_ERR_INVALID_ARGUMENT, "gamma must exceed 1");
+  DeviceGuard g(m->device);
+  double B0 = 0.0;
+  if (in->kind == SD_INIT_SHELL_POLYTROPE) {
+    const double* P = in->params;
+    const double Nr = P[0], rb = P[1], rt = P[2], rhob = P[3], Rg = P[4], ratio = P[6];
+    if (!(rt > rb && rb > 0.0 && rhob > 0.0 && Rg > 0.0 && ph->GM > 0.0))
+      return fail(SD_ERR_INVALID_ARGUMENT, "polytrope needs 0 < r_b < r_t, rho_b > 0, R_gas > 0, GM > 0");
+    // magnetic energy of the unit dipole over the ideal shell: 8 pi (r_b^-3 - r_t^-3) / 3 (times 1/2 below);
+    // internal energy: 4 pi / (gamma - 1) int p0 r^2 dr by 64-point Gauss-Legendre
+    std::vector<double> x, w;
+    gauss_legendre(64, x, w);
+    double Ip = 0.0;
+    for (int k = 0; k < 64; ++k) {
+      const double r = 0.5 * (rb + rt) + 0.5 * (rt - rb) * x[k];
+      Ip += 0.5 * (rt - rb) * w[k] * polytrope_p(r, Nr, rb, rt, rhob, Rg, ph->gamma, ph->GM) * r * r;
+    }
+    Ip *= 4.0 * M_PI / (ph->gamma - 1.0);
+    const double IB = 8.0 * M_PI * (1.0 / (rb * rb * rb) - 1.0 / (rt * rt * rt)) / 3.0;
+    B0 = sqrt(2.0 * ratio * Ip / IB);
+  }
+  cudaError_t err = sd::launch_state_init(m, ph, in, B0, q, qbg, (cudaStream_t)stream);
+  if (err != cudaSuccess) return cuda_fail(err, "state init kernel");
+  return SD_OK;
+}
+
+sd_status sd_background_create(const sd_mesh* m, const sd_phys* ph, const double* q_bg, void* stream,
+                               sd_background** out) {
+  if (!out) return fail(SD_ERR_INVALID_ARGUMENT, "out is NULL");
+  *out = nullptr;
+  sd_status st = check_common(m, ph, SD_FP64, nullptr);
+  if (st != SD_OK) return st;
+  st = check_state_ptr(q_bg, "q_background");
+  if (st != SD_OK) return st;
+  DeviceGuard g(m->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t N2 = (int64_t)m->N * m->N, N3 = N2 * m->N;
+  const size_t ne = (size_t)std::max<int64_t>(m->n_e, 1);
+  sd_background* bg = new sd_background;
+  bg->mesh = m;
+  bg->gamma = ph->gamma;
+  bg->rec = nullptr;
+  bg->jump = nullptr;
+  double *q0 = nullptr, *R0 = nullptr;
+  const size_t state = 9 * ne * m->stride;
+  cudaError_t err = cudaMalloc((void**)&bg->rec, 5 * ne * N3 * sizeof(float));
+  if (err == cudaSuccess) err = cudaMalloc((void**)&bg->jump, ne * 6 * 2 * N2 * sizeof(float));
+  if (err == cudaSuccess) err = cudaMalloc((void**)&q0, state * sizeof(double));
+  if (err == cudaSuccess) err = cudaMalloc((void**)&R0, state * sizeof(double));
+  if (err == cudaSuccess) err = sd::launch_bg_prepare(m, ph->gamma, q_bg, q0, bg->rec, s);
+  sd_mesh* mm = const_cast<sd_mesh*>(m);
+  if (err == cudaSuccess) {
+    sd::StageParams P = base_params(m, ph, SD_FP64);
+    P.q_in = q0;
+    P.tr_out = mm->tr64[0];
+    err = sd::launch_traces(m, SD_FP64, P, s);
+    if (err == cudaSuccess) {
+      // background residual: pressure-gradient flux with central face average, plus rho0 g
+      P.tr_out = nullptr;
+      P.tr_in = mm->tr64[0];
+      P.mode = sd::MODE_RESIDUAL;
+      P.central = 1;
+      P.c_h = 0.0;
+      P.powell = 0;
+      P.coriolis = 0;
+      P.alpha = 0.0;
+      P.out = R0;
+      err = sd::launch_stage(m, SD_FP64, P, s);
+    }
+  }
+  if (err == cudaSuccess) err = sd::launch_bg_finish(m, ph->gamma, R0, bg->rec, bg->jump, mm->tr64[0], s);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+  mm->tr_tag[0] = mm->tr_tag[1] = nullptr;
+  if (q0) cudaFree(q0);
+  if (R0) cudaFree(R0);
+  if (err != cudaSuccess) {
+    if (bg->rec) cudaFree(bg->rec);
+    if (bg->jump) cudaFree(bg->jump);
+    delete bg;
+    cudaGetLastError();
+    return err == cudaErrorMemoryAllocation ? fail(SD_ERR_OUT_OF_MEMORY, "background allocation failed")
+                                            : cuda_fail(err, "background preparation");
+  }
+  *out = bg;
+  return SD_OK;
+}
+
+sd_status sd_background_destroy(sd_background* bg) {
+  if (!bg) return SD_OK;
+  DeviceGuard g(bg->mesh->device);
+  cudaFree(bg->rec);
+  cudaFree(bg->jump);
+  delete bg;
+  return SD_OK;
+}
+
+sd_status sd_residual(const sd_mesh* m, const sd_phys* ph, sd_precision prec, const double* q, const sd_background* bg,
+                      double* dqdt, void* stream) {
+  sd_status st = check_common(m, ph, prec, bg);
+  if (st != SD_OK) return st;
+  if ((st = check_state_ptr(q, "q")) != SD_OK) return st;
+  if ((st = check_state_ptr(dqdt, "dqdt")) != SD_OK) return st;
+  if (q == dqdt) return fail(SD_ERR_INVALID_ARGUMENT, "dqdt must not alias q");
+  DeviceGuard g(m->device);
+  sd_mesh* mm = const_cast<sd_mesh*>(m);
+  cudaStream_t s = (cudaStream_t)stream;
+  sd::StageParams P = base_params(m, ph, prec);
+  if (bg) {
+    P.bg = bg->rec;
+    P.bg_jump = bg->jump;
+  }
+  P.q_in = q;
+  P.tr_out = trace_buf(mm, prec, 0);
+  cudaError_t err = sd::launch_traces(m, prec, P, s);
+  if (err != cudaSuccess) return cuda_fail(err, "trace kernel");
+  mm->tr_tag[0] = mm->tr_tag[1] = nullptr;
+  P.tr_in = P.tr_out;
+  P.tr_out = nullptr;
+  P.mode = sd::MODE_RESIDUAL;
+  P.out = dqdt;
+  err = sd::launch_stage(m, prec, P, s);
+  if (err != cudaSuccess) return cuda_fail(err, "residual kernel");
+  return SD_OK;
+}
+
+static sd_status rk_stage_impl(sd_mesh* m, const sd_phys* ph, int prec, int stage, double dt, const double* dyn,
+                               const double* q_n, const double* q_in, double* q_out, const sd_background* bg,
+                               bool want_traces, cudaStream_t s) {
+  static const double A[3] = {0.0, 0.75, 1.0 / 3.0};
+  static const double B[3] = {1.0, 0.25, 2.0 / 3.0};
+  sd::StageParams P = base_params(m, ph, prec);
+  if (bg) {
+    P.bg = bg->rec;
+    P.bg_jump = bg->jump;
+  }
+  // traces of q_in: reuse those written by the previous stage when it produced q_in
+  int bin = -1;
+  if (stage > 0)
+    for (int b = 0; b < 2; ++b)
+      if (m->tr_tag[b] == q_in && m->tr_prec[b] == prec) bin = b;
+  if (bin < 0) {
+    bin = 0;
+    P.q_in = q_in;
+    P.tr_out = trace_buf(m, prec, bin);
+    cudaError_t err = sd::launch_traces(m, prec, P, s);
+    if (err != cudaSuccess) return cuda_fail(err, "trace kernel");
+  }
+  const int bout = 1 - bin;
+  P.q_in = q_in;
+  P.q_n = q_n;
+  P.out = q_out;
+  P.mode = sd::MODE_RK;
+  P.rk_a = A[stage];
+  P.rk_b = B[stage];
+  P.dt = dt;
+  P.dyn = dyn;
+  P.tr_in = trace_buf(m, prec, bin);
+  P.tr_out = want_traces ? trace_buf(m, prec, bout) : nullptr;
+  cudaError_t err = sd::launch_stage(m, prec, P, s);
+  if (err != cudaSuccess) return cuda_fail(err, "stage kernel");
+  m->tr_tag[bin] = nullptr;
+  m->tr_tag[bout] = want_traces ? q_out : nullptr;
+  m->tr_prec[bout] = prec;
+  return SD_OK;
+}
+
+sd_status sd_rk_stage(const sd_mesh* m, const sd_phys* ph, sd_precision prec, int32_t stage, double dt,
+                      const double* q_n, const double* q_in, double* q_out, const sd_background* bg, void* stream) {
+  sd_status st = check_common(m, ph, prec, bg);
+  if (st != SD_OK) return st;
+  if (stage < 0 || stage > 2) return fail(SD_ERR_INVALID_ARGUMENT, "stage must be 0, 1 or 2");
+  if ((st = check_state_ptr(q_in, "q_in")) != SD_OK) return st;
+  if ((st = check_state_ptr(q_out, "q_out")) != SD_OK) return st;
+  if (stage > 0 && (st = check_state_ptr(q_n, "q_n")) != SD_OK) return st;
+  if (!isfinite(dt)) return fail(SD_ERR_INVALID_ARGUMENT, "dt is not finite");
+  DeviceGuard g(m->device);
+  return rk_stage_impl(const_cast<sd_mesh*>(m), ph, prec, stage, dt, nullptr, stage > 0 ? q_n : q_in, q_in, q_out, bg,
+                       stage < 2, (cudaStream_t)stream);
+}
+
+sd_status sd_step(const sd_mesh* m, const sd_phys* ph, sd_precision prec, double cfl, double* q, double* work,
+                  const sd_background* bg, double* dt_out, void* stream) {
+  sd_status st = check_common(m, ph, prec, bg);
+  if (st != SD_OK) return st;
+  if ((st = check_state_ptr(q, "q")) != SD_OK) return st;
+  if ((st = check_state_ptr(work, "work")) != SD_OK) return st;
+  if (q == work) return fail(SD_ERR_INVALID_ARGUMENT, "work must not alias q");
+  if (!(cfl > 0.0)) return fail(SD_ERR_INVALID_ARGUMENT, "cfl must be positive");
+  DeviceGuard g(m->device);
+  sd_mesh* mm = const_cast<sd_mesh*>(m);
+  cudaStream_t s = (cudaStream_t)stream;
+  // lambda_max of q fused with the traces of q
+  sd::StageParams P = base_params(m, ph, prec);
+  if (bg) {
+    P.bg = bg->rec;
+    P.bg_jump = bg->jump;
+  }
+  SD_CUDA(cudaMemsetAsync(mm->dyn + 2, 0, sizeof(double), s));
+  P.q_in = q;
+  P.tr_out = trace_buf(mm, prec, 0);
+  P.lam_max = reinterpret_cast<unsigned long long*>(mm->dyn + 2);
+  SD_CUDA(sd::launch_traces(m, prec, P, s));
+  SD_CUDA(sd::launch_step_control(m, cfl, ph->c_h, dt_out, s));
+  mm->tr_tag[0] = q;
+  mm->tr_prec[0] = prec;
+  mm->tr_tag[1] = nullptr;
+  // stage 0 finds the traces of q in buffer 0 (tagged above) only if stage > 0; run it explicitly
+  {
+    sd::StageParams S = base_params(m, ph, prec);
+    if (bg) {
+      S.bg = bg->rec;
+      S.bg_jump = bg->jump;
+    }
+    S.q_in = q;
+    S.q_n = q;
+    S.out = work;
+    S.mode = sd::MODE_RK;
+    S.rk_a = 0.0;
+    S.rk_b = 1.0;
+    S.dyn = mm->dyn;
+    S.tr_in = trace_buf(mm, prec, 0);
+    S.tr_out = trace_buf(mm, prec, 1);
+    SD_CUDA(sd::launch_stage(m, prec, S, s));
+    mm->tr_tag[0] = nullptr;
+    mm->tr_tag[1] = work;
+    mm->tr_prec[1] = prec;
+  }
+  st = rk_stage_impl(mm, ph, prec, 1, 0.0, mm->dyn, q, work, work, bg, true, s);
+  if (st != SD_OK) return st;
+  st = rk_stage_impl(mm, ph, prec, 2, 0.0, mm->dyn, q, work, q, bg, false, s);
+  return st;
+}
+
+sd_status sd_diagnostics(const sd_mesh* m, const sd_phys* ph, const double* q, sd_diag* out, void* stream) {
+  sd_status st = check_common(m, ph, SD_FP64, nullptr);
+  if (st != SD_OK) return st;
+  if ((st = check_state_ptr(q, "q")) != SD_OK) return st;
+  if (!out) return fail(SD_ERR_INVALID_ARGUMENT, "out is NULL");
+  DeviceGuard g(m->device);
+  sd_mesh* mm = const_cast<sd_mesh*>(m);
+  cudaStream_t s = (cudaStream_t)stream;
+  sd::StageParams P = base_params(m, ph, SD_FP64);
+  P.q_in = q;
+  P.tr_out = mm->tr64[0];
+  SD_CUDA(sd::launch_traces(m, SD_FP64, P, s));
+  mm->tr_tag[0] = mm->tr_tag[1] = nullptr;
+  P.tr_in = mm->tr64[0];
+  P.tr_out = nullptr;
+  P.mode = sd::MODE_DIVB;
+  P.divb = mm->divb;
+  SD_CUDA(sd::launch_stage(m, SD_FP64, P, s));
+  SD_CUDA(sd::launch_diag(m, ph, q, s));
+  SD_CUDA(cudaMemcpyAsync(mm->host_diag, mm->diag_out, 10 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  SD_CUDA(cudaStreamSynchronize(s));
+  const double* h = mm->host_diag;
+  const double vol = h[4];
+  out->ke = h[0] / vol;
+  out->eb = h[1] / vol;
+  out->mass = h[2];
+  out->energy = h[3];
+  out->volume = vol;
+  out->max_divb = h[5];
+  out->lambda_max = h[6];
+  out->min_rho = h[7];
+  out->min_p = h[8];
+  if (h[9] > 0.0 || h[5] != h[5] || h[6] != h[6])
+    return fail(SD_ERR_NONPHYSICAL, "non-physical state: rho <= 0, p <= 0 or NaN at " +
+                                        std::to_string((long long)h[9]) + " solution points");
+  return SD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,529 @@
+// sd_aux.cu -- geometry, initial state, diagnostics, background and step-control
+// kernels of the SD MHD+GLM library.
+#include <math.h>
+
+#include "sd_internal.h"
+
+namespace sd {
+
+cudaError_t launch_stage_fp64(const sd_mesh* m, const StageParams& P, bool traces_only, cudaStream_t s);
+cudaError_t launch_stage_mixed(const sd_mesh* m, const StageParams& P, bool traces_only, cudaStream_t s);
+
+cudaError_t launch_stage(const sd_mesh* m, int prec, const StageParams& P, cudaStream_t s) {
+  return prec == SD_FP64 ? launch_stage_fp64(m, P, false, s) : launch_stage_mixed(m, P, false, s);
+}
+cudaError_t launch_traces(const sd_mesh* m, int prec, const StageParams& P, cudaStream_t s) {
+  return prec == SD_FP64 ? launch_stage_fp64(m, P, true, s) : launch_stage_mixed(m, P, true, s);
+}
+
+// ---------------------------------------------------------------------------
+// Geometry (Sec. SD Method): transfinite map from the 12 element edges
+// (constant-radius edges are great-circle arcs in the shell), sampled at
+// (p+1)^3 Chebyshev-Lobatto nodes; the tensor Lagrange interpolant of those
+// samples is the element map.  S^xi = x_eta x x_zeta, S^eta = x_zeta x x_xi,
+// S^zeta = x_xi x x_eta at the flux points of each family; |J| and x at the
+// solution points.
+// ---------------------------------------------------------------------------
+
+__device__ void edge_point_d(const double* A, const double* B, double t, int geom, double* out) {
+  if (geom == 0) {
+    for (int d = 0; d < 3; ++d) out[d] = A[d] + t * (B[d] - A[d]);
+    return;
+  }
+  const double ra = sqrt(A[0] * A[0] + A[1] * A[1] + A[2] * A[2]);
+  const double rb = sqrt(B[0] * B[0] + B[1] * B[1] + B[2] * B[2]);
+  double ua[3], ub[3];
+  for (int d = 0; d < 3; ++d) {
+    ua[d] = A[d] / ra;
+    ub[d] = B[d] / rb;
+  }
+  const double cx = ua[1] * ub[2] - ua[2] * ub[1], cy = ua[2] * ub[0] - ua[0] * ub[2], cz = ua[0] * ub[1] - ua[1] * ub[0];
+  const double ang = atan2(sqrt(cx * cx + cy * cy + cz * cz), ua[0] * ub[0] + ua[1] * ub[1] + ua[2] * ub[2]);
+  const double r = ra + t * (rb - ra);
+  double dir[3];
+  if (ang < 1e-12) {
+    double nn = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      dir[d] = (1.0 - t) * ua[d] + t * ub[d];
+      nn += dir[d] * dir[d];
+    }
+    nn = sqrt(nn);
+    for (int d = 0; d < 3; ++d) dir[d] /= nn;
+  } else {
+    const double s = sin(ang);
+    const double wa = sin((1.0 - t) * ang) / s, wb = sin(t * ang) / s;
+    for (int d = 0; d < 3; ++d) dir[d] = wa * ua[d] + wb * ub[d];
+  }
+  for (int d = 0; d < 3; ++d) out[d] = r * dir[d];
+}
+
+// edge-based blend: bilinear projectors of the 12 edges minus twice the trilinear corner projector
+__device__ void tfi_d(const double* V, int geom, double u, double v, double w, double* X) {
+  const double bu[2] = {1.0 - u, u}, bv[2] = {1.0 - v, v}, bw[2] = {1.0 - w, w};
+  double P[3];
+  X[0] = X[1] = X[2] = 0.0;
+  for (int j = 0; j < 2; ++j)
+    for (int k = 0; k < 2; ++k) {
+      edge_point_d(V + 3 * (2 * j + 4 * k), V + 3 * (1 + 2 * j + 4 * k), u, geom, P);
+      for (int d = 0; d < 3; ++d) X[d] += bv[j] * bw[k] * P[d];
+    }
+  for (int i = 0; i < 2; ++i)
+    for (int k = 0; k < 2; ++k) {
+      edge_point_d(V + 3 * (i + 4 * k), V + 3 * (i + 2 + 4 * k), v, geom, P);
+      for (int d = 0; d < 3; ++d) X[d] += bu[i] * bw[k] * P[d];
+    }
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j) {
+      edge_point_d(V + 3 * (i + 2 * j), V + 3 * (i + 2 * j + 4), w, geom, P);
+      for (int d = 0; d < 3; ++d) X[d] += bu[i] * bv[j] * P[d];
+    }
+  for (int c = 0; c < 8; ++c) {
+    const double wc = bu[c & 1] * bv[(c >> 1) & 1] * bw[(c >> 2) & 1];
+    for (int d = 0; d < 3; ++d) X[d] -= 2.0 * wc * V[3 * c + d];
+  }
+}
+
+// Lagrange basis values and derivatives over the p1 nodes y at t
+__device__ void lagrange_1d(const double* y, int p1, double t, double* L, double* dL) {
+  for (int a = 0; a < p1; ++a) {
+    double v = 1.0, dv = 0.0;
+    for (int m = 0; m < p1; ++m) {
+      if (m == a) continue;
+      double prod = 1.0 / (y[a] - y[m]);
+      for (int s = 0; s < p1; ++s)
+        if (s != a && s != m) prod *= (t - y[s]) / (y[a] - y[s]);
+      dv += prod;
+      v *= (t - y[m]) / (y[a] - y[m]);
+    }
+    L[a] = v;
+    dL[a] = dv;
+  }
+}
+
+// dX/dxi, dX/deta, dX/dzeta and X at computational point (u, v, w)
+__device__ void map_jac(const double* Xp, const double* y, int p1, double u, double v, double w, double* J9, double* X) {
+  double Lu[5], dLu[5], Lv[5], dLv[5], Lw[5], dLw[5];
+  lagrange_1d(y, p1, u, Lu, dLu);
+  lagrange_1d(y, p1, v, Lv, dLv);
+  lagrange_1d(y, p1, w, Lw, dLw);
+  for (int i = 0; i < 9; ++i) J9[i] = 0.0;
+  if (X) X[0] = X[1] = X[2] = 0.0;
+  for (int c = 0; c < p1; ++c)
+    for (int b = 0; b < p1; ++b)
+      for (int a = 0; a < p1; ++a) {
+        const double* x = Xp + 3 * (a + p1 * (b + p1 * c));
+        const double w0 = dLu[a] * Lv[b] * Lw[c], w1 = Lu[a] * dLv[b] * Lw[c], w2 = Lu[a] * Lv[b] * dLw[c];
+        for (int d = 0; d < 3; ++d) {
+          J9[0 + d] += w0 * x[d];  // x_xi
+          J9[3 + d] += w1 * x[d];  // x_eta
+          J9[6 + d] += w2 * x[d];  // x_zeta
+        }
+        if (X) {
+          const double wv = Lu[a] * Lv[b] * Lw[c];
+          for (int d = 0; d < 3; ++d) X[d] += wv * x[d];
+        }
+      }
+}
+
+__global__ void geometry_kernel(int N, int p, int geom, const double* __restrict__ corners, const Ops<double> ops,
+                                double* Sfam64, double* invJ64, double* X64, float* Sfam32, float* invJ32, float* X32,
+                                int* flag) {
+  __shared__ double sV[24];
+  __shared__ double sXp[125 * 3];
+  __shared__ double y[5];
+  const int64_t e = blockIdx.x;
+  const int p1 = p + 1, N2 = N * N, N3 = N2 * N, NF = N + 1;
+  for (int i = threadIdx.x; i < 24; i += blockDim.x) sV[i] = corners[e * 24 + i];
+  if (threadIdx.x < p1) y[threadIdx.x] = 0.5 * (1.0 - cos(M_PI * threadIdx.x / p));
+  __syncthreads();
+  for (int t = threadIdx.x; t < p1 * p1 * p1; t += blockDim.x) {
+    const int a = t % p1, b = (t / p1) % p1, c = t / (p1 * p1);
+    tfi_d(sV, geom, y[a], y[b], y[c], sXp + 3 * t);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < 3 * NF * N2; t += blockDim.x) {
+    const int d = t / (NF * N2), r = t % (NF * N2), line = r / NF, f = r % NF, a = line % N, b = line / N;
+    double pt[3];
+    pt[d] = ops.xf[f];
+    pt[d == 0 ? 1 : 0] = ops.xs[a];
+    pt[d == 2 ? 1 : 2] = ops.xs[b];
+    double J9[9];
+    map_jac(sXp, y, p1, pt[0], pt[1], pt[2], J9, nullptr);
+    const double* t1 = J9 + 3 * ((d + 1) % 3);
+    const double* t2 = J9 + 3 * ((d + 2) % 3);
+    const double S[3] = {t1[1] * t2[2] - t1[2] * t2[1], t1[2] * t2[0] - t1[0] * t2[2], t1[0] * t2[1] - t1[1] * t2[0]};
+    for (int c = 0; c < 3; ++c) {
+      const int64_t idx = (((e * 3 + d) * 3 + c) * N2 + line) * NF + f;
+      Sfam64[idx] = S[c];
+      Sfam32[idx] = (float)S[c];
+    }
+  }
+  for (int n = threadIdx.x; n < N3; n += blockDim.x) {
+    const int i = n % N, j = (n / N) % N, k = n / N2;
+    double J9[9], X[3];
+    map_jac(sXp, y, p1, ops.xs[i], ops.xs[j], ops.xs[k], J9, X);
+    const double* xa = J9;
+    const double* xb = J9 + 3;
+    const double* xc = J9 + 6;
+    const double det = xa[0] * (xb[1] * xc[2] - xb[2] * xc[1]) + xa[1] * (xb[2] * xc[0] - xb[0] * xc[2]) +
+                       xa[2] * (xb[0] * xc[1] - xb[1] * xc[0]);
+    if (!(det > 0.0)) atomicExch(flag, 1);
+    invJ64[e * N3 + n] = 1.0 / det;
+    invJ32[e * N3 + n] = (float)(1.0 / det);
+    for (int c = 0; c < 3; ++c) {
+      X64[(e * 3 + c) * N3 + n] = X[c];
+      X32[(e * 3 + c) * N3 + n] = (float)X[c];
+    }
+  }
+}
+
+// The side of an interior face that does not own it takes the owner's metric at
+// the coincident point, negated to its own orientation, so the two sides use
+// exactly opposite normals and equal areas.
+__global__ void canonical_faces_kernel(int N, int64_t n_e, const int* __restrict__ nbr, const int* __restrict__ meta,
+                                       double* Sfam64, float* Sfam32) {
+  const int N2 = N * N, NF = N + 1;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_e * 6 * N2) return;
+  const int64_t e = t / (6 * N2);
+  const int F = (int)((t / N2) % 6), pt = (int)(t % N2), a = pt % N, b = pt / N;
+  const int mt = meta[e * 6 + F];
+  const int nb = nbr[e * 6 + F];
+  if (nb < 0 || meta_owner(mt)) return;
+  const int code = meta_code(mt), nbF = meta_nbF(mt);
+  const int u = (code & 4) ? b : a, w = (code & 4) ? a : b;
+  const int a2 = (code & 2) ? N - 1 - u : u, b2 = (code & 1) ? N - 1 - w : w;
+  const int d = F >> 1, f = (F & 1) ? N : 0, d2 = nbF >> 1, f2 = (nbF & 1) ? N : 0;
+  const double sgn = ((F & 1) ? 1.0 : -1.0) * ((nbF & 1) ? 1.0 : -1.0);
+  for (int c = 0; c < 3; ++c) {
+    const double Sn = Sfam64[((((int64_t)nb * 3 + d2) * 3 + c) * N2 + a2 + N * b2) * NF + f2];
+    const int64_t idx = (((e * 3 + d) * 3 + c) * N2 + pt) * NF + f;
+    Sfam64[idx] = -sgn * Sn;
+    Sfam32[idx] = (float)(-sgn * Sn);
+  }
+}
+
+cudaError_t launch_geometry(sd_mesh* m, const double* d_corners, int* d_flag, cudaStream_t s) {
+  if (m->n_e == 0) return cudaSuccess;
+  geometry_kernel<<<(unsigned)m->n_e, 128, 0, s>>>(m->N, m->p, m->geom, d_corners, m->ops64, m->Sfam64, m->invJ64,
+                                                   m->X64, m->Sfam32, m->invJ32, m->X32, d_flag);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_canonical_faces(sd_mesh* m, cudaStream_t s) {
+  const int64_t tot = m->n_e * 6 * m->N * m->N;
+  if (tot == 0) return cudaSuccess;
+  canonical_faces_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(m->N, m->n_e, m->nbr, m->meta, m->Sfam64,
+                                                                       m->Sfam32);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Initial states (Sec. Initial Conditions)
+// ---------------------------------------------------------------------------
+
+// SplitMix64 (Steele, Lea and Flood; Vigna's reference generator): the
+// (index+1)-th output of the generator whose state starts at seed.
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long seed, unsigned long long index) {
+  unsigned long long z = seed + (index + 1ULL) * 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+__device__ void cons_from_prim(double rho, const double* u, double p, const double* B, double psi, double gamma,
+                               double* Q) {
+  Q[0] = rho;
+  for (int d = 0; d < 3; ++d) Q[1 + d] = rho * u[d];
+  Q[4] = p / (gamma - 1.0) + 0.5 * rho * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]) +
+         0.5 * (B[0] * B[0] + B[1] * B[1] + B[2] * B[2]) + 0.5 * psi * psi;
+  for (int d = 0; d < 3; ++d) Q[5 + d] = B[d];
+  Q[8] = psi;
+}
+
+struct InitArgs {
+  int kind;
+  int N;
+  int64_t n_e, stride, plane;
+  double P[16];
+  unsigned long long seed;
+  double gamma, GM, B0dip;
+};
+
+__global__ void state_init_kernel(const InitArgs A, const double* __restrict__ X64, double* q, double* qbg) {
+  const int N3 = A.N * A.N * A.N;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= A.n_e * A.stride) return;
+  const int64_t e = t / A.stride;
+  const int n = (int)(t % A.stride);
+  double Q[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, Qb[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  if (n < N3) {
+    const double x[3] = {X64[(e * 3 + 0) * N3 + n], X64[(e * 3 + 1) * N3 + n], X64[(e * 3 + 2) * N3 + n]};
+    const double zero[3] = {0.0, 0.0, 0.0};
+    const double* P = A.P;
+    if (A.kind == SD_INIT_UNIFORM) {
+      const double u[3] = {P[1], P[2], P[3]}, B[3] = {P[5], P[6], P[7]};
+      cons_from_prim(P[0], u, P[4], B, P[8], A.gamma, Q);
+    } else if (A.kind == SD_INIT_ALFVEN) {
+      const double rho = P[0], p = P[1], B0 = P[2], amp = P[3], tt = P[7];
+      const double k[3] = {P[4], P[5], P[6]};
+      const double kn = sqrt(k[0] * k[0] + k[1] * k[1] + k[2] * k[2]);
+      const double kh[3] = {k[0] / kn, k[1] / kn, k[2] / kn};
+      // e1 = unit(khat x z) (or unit(x x khat) when k is along z); e2 = khat x e1
+      double e1[3] = {kh[1], -kh[0], 0.0};
+      double n1 = sqrt(e1[0] * e1[0] + e1[1] * e1[1]);
+      if (n1 < 1e-8) {
+        e1[0] = 0.0;
+        e1[1] = -kh[2];
+        e1[2] = kh[1];
+        n1 = sqrt(e1[1] * e1[1] + e1[2] * e1[2]);
+      }
+      for (int d = 0; d < 3; ++d) e1[d] /= n1;
+      const double e2[3] = {kh[1] * e1[2] - kh[2] * e1[1], kh[2] * e1[0] - kh[0] * e1[2], kh[0] * e1[1] - kh[1] * e1[0]};
+      const double om = kn * B0 / sqrt(rho);
+      const double ph = k[0] * x[0] + k[1] * x[1] + k[2] * x[2] - om * tt;
+      const double cp = cos(ph), sp = sin(ph);
+      double B[3], u[3];
+      for (int d = 0; d < 3; ++d) {
+        const double dB = amp * (cp * e1[d] + sp * e2[d]);
+        B[d] = B0 * kh[d] + dB;
+        u[d] = -dB / sqrt(rho);
+      }
+      cons_from_prim(rho, u, p, B, 0.0, A.gamma, Q);
+    } else if (A.kind == SD_INIT_SHELL_POLYTROPE) {
+      // Eq. (polytrop eqns) with T_b from N_rho; R_gas = P[4], C_p = gamma R/(gamma-1)
+      const double Nr = P[0], rb = P[1], rt = P[2], rhob = P[3], Rg = P[4], amp = P[5];
+      const double g = A.gamma;
+      const double Cp = g * Rg / (g - 1.0);
+      const double r = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+      const double Tb = (-A.GM / rt + A.GM / rb) / (Cp * (1.0 - exp(-(g - 1.0) * Nr)));
+      const double pb = rhob * Rg * Tb;
+      const double zeta = 1.0 - (-A.GM / r + A.GM / rb) / (Cp * Tb);
+      const double rho0 = rhob * pow(zeta, 1.0 / (g - 1.0));
+      const double p0 = pb * pow(zeta, g / (g - 1.0));
+      const unsigned long long z = splitmix64(A.seed, (unsigned long long)(e * N3 + n));
+      const double xi = 2.0 * ((double)(z >> 11) * 0x1.0p-53) - 1.0;
+      const double rho = rho0 * (1.0 - amp * xi * sin(M_PI * (r - rb) / (rt - rb)));
+      const double rh[3] = {x[0] / r, x[1] / r, x[2] / r};
+      const double r3 = r * r * r;
+      const double B[3] = {A.B0dip * (3.0 * rh[2] * rh[0]) / r3, A.B0dip * (3.0 * rh[2] * rh[1]) / r3,
+                           A.B0dip * (3.0 * rh[2] * rh[2] - 1.0) / r3};
+      cons_from_prim(rho, zero, p0, B, 0.0, g, Q);
+      cons_from_prim(rho0, zero, p0, zero, 0.0, g, Qb);
+    } else if (A.kind == SD_INIT_DIVB_PULSE) {
+      const double dx = x[0] - P[3], dy = x[1] - P[4], dz = x[2] - P[5];
+      const double B[3] = {P[2] * exp(-(dx * dx + dy * dy + dz * dz) / (2.0 * P[6] * P[6])), 0.0, 0.0};
+      cons_from_prim(P[0], zero, P[1], B, 0.0, A.gamma, Q);
+    }
+  }
+  for (int v = 0; v < 9; ++v) {
+    q[v * A.plane + e * A.stride + n] = Q[v];
+    if (qbg) qbg[v * A.plane + e * A.stride + n] = Qb[v];
+  }
+}
+
+cudaError_t launch_state_init(const sd_mesh* m, const sd_phys* ph, const sd_init* in, double B0dip, double* q,
+                              double* qbg, cudaStream_t s) {
+  InitArgs A;
+  A.kind = in->kind;
+  A.N = m->N;
+  A.n_e = m->n_e;
+  A.stride = m->stride;
+  A.plane = m->n_e * m->stride;
+  for (int i = 0; i < 16; ++i) A.P[i] = in->params[i];
+  A.seed = in->seed;
+  A.gamma = ph->gamma;
+  A.GM = ph->GM;
+  A.B0dip = B0dip;
+  const int64_t tot = m->n_e * m->stride;
+  if (tot == 0) return cudaSuccess;
+  state_init_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(A, m->X64, q, qbg);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Diagnostics (Sec. Results): per-element partial sums, then one block sums
+// the partials in element order -- a fixed order, so results are reproducible.
+// slot: 0 ke, 1 eb, 2 mass, 3 energy, 4 volume, 5 max|divB|, 6 lambda_max,
+//       7 min rho, 8 min p, 9 nonphysical count
+// ---------------------------------------------------------------------------
+
+constexpr int kDiag = 12;
+constexpr int kDiagThreads = 256;
+
+__device__ __forceinline__ double dmax_nan(double a, double b) { return (b > a || b != b) ? b : a; }
+__device__ __forceinline__ double dmin_nan(double a, double b) { return (b < a || b != b) ? b : a; }
+
+__device__ void block_reduce_diag(double* vals, double (*sm)[kDiagThreads]) {
+  const int t = threadIdx.x;
+  for (int k = 0; k < 10; ++k) sm[k][t] = vals[k];
+  __syncthreads();
+  for (int off = kDiagThreads / 2; off > 0; off >>= 1) {
+    if (t < off) {
+      for (int k = 0; k < 5; ++k) sm[k][t] += sm[k][t + off];
+      sm[5][t] = dmax_nan(sm[5][t], sm[5][t + off]);
+      sm[6][t] = dmax_nan(sm[6][t], sm[6][t + off]);
+      sm[7][t] = dmin_nan(sm[7][t], sm[7][t + off]);
+      sm[8][t] = dmin_nan(sm[8][t], sm[8][t + off]);
+      sm[9][t] += sm[9][t + off];
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kDiagThreads) diag_partial_kernel(int N, int64_t stride, int64_t plane, double gamma,
+                                                                    const Ops<double> ops, const double* __restrict__ q,
+                                                                    const double* __restrict__ invJ,
+                                                                    const double* __restrict__ divb, double* part) {
+  __shared__ double sm[10][kDiagThreads];
+  const int64_t e = blockIdx.x;
+  const int N3 = N * N * N;
+  double v[10] = {0, 0, 0, 0, 0, 0, 0, INFINITY, INFINITY, 0};
+  for (int n = threadIdx.x; n < N3; n += kDiagThreads) {
+    const int i = n % N, j = (n / N) % N, k = n / (N * N);
+    double Q[9];
+    for (int c = 0; c < 9; ++c) Q[c] = q[c * plane + e * stride + n];
+    const double wq = ops.w[i] * ops.w[j] * ops.w[k] / invJ[e * N3 + n];
+    const double rho = Q[0];
+    const double m2 = Q[1] * Q[1] + Q[2] * Q[2] + Q[3] * Q[3];
+    const double B2 = Q[5] * Q[5] + Q[6] * Q[6] + Q[7] * Q[7];
+    const double p = (gamma - 1.0) * (Q[4] - 0.5 * (m2 / rho + B2 + Q[8] * Q[8]));
+    v[0] += wq * 0.5 * m2 / rho;
+    v[1] += wq * 0.5 * B2;
+    v[2] += wq * rho;
+    v[3] += wq * Q[4];
+    v[4] += wq;
+    v[5] = dmax_nan(v[5], fabs(divb[e * N3 + n]));
+    v[6] = dmax_nan(v[6], sqrt(m2) / rho + sqrt(gamma * p / rho + B2 / rho));
+    v[7] = dmin_nan(v[7], rho);
+    v[8] = dmin_nan(v[8], p);
+    if (!(rho > 0.0) || !(p > 0.0)) v[9] += 1.0;
+  }
+  block_reduce_diag(v, sm);
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 10; ++k) part[e * kDiag + k] = sm[k][0];
+}
+
+__global__ void __launch_bounds__(kDiagThreads) diag_final_kernel(int64_t n_e, const double* __restrict__ part,
+                                                                  double* out) {
+  __shared__ double sm[10][kDiagThreads];
+  double v[10] = {0, 0, 0, 0, 0, 0, 0, INFINITY, INFINITY, 0};
+  for (int64_t e = threadIdx.x; e < n_e; e += kDiagThreads) {
+    const double* p = part + e * kDiag;
+    for (int k = 0; k < 5; ++k) v[k] += p[k];
+    v[5] = dmax_nan(v[5], p[5]);
+    v[6] = dmax_nan(v[6], p[6]);
+    v[7] = dmin_nan(v[7], p[7]);
+    v[8] = dmin_nan(v[8], p[8]);
+    v[9] += p[9];
+  }
+  block_reduce_diag(v, sm);
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 10; ++k) out[k] = sm[k][0];
+}
+
+cudaError_t launch_diag(const sd_mesh* m, const sd_phys* ph, const double* q, cudaStream_t s) {
+  if (m->n_e == 0) return cudaSuccess;
+  diag_partial_kernel<<<(unsigned)m->n_e, kDiagThreads, 0, s>>>(m->N, m->stride, m->n_e * m->stride, ph->gamma,
+                                                                 m->ops64, q, m->invJ64, m->divb, m->diag_part);
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  diag_final_kernel<<<1, kDiagThreads, 0, s>>>(m->n_e, m->diag_part, m->diag_out);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// FP32-mixed background: rho0 and p0 rounded to FP32 define the background Q0
+// exactly; its FP64 residual R0 and its FP64 face jumps are stored in FP32.
+// ---------------------------------------------------------------------------
+
+__global__ void bg_prepare_kernel(int N, int64_t n_e, int64_t stride, double gamma, const double* __restrict__ qbg,
+                                  double* q0, float* rec) {
+  const int N3 = N * N * N;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_e * stride) return;
+  const int64_t e = t / stride;
+  const int n = (int)(t % stride);
+  const int64_t plane = n_e * stride;
+  double Q[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  if (n < N3) {
+    const float r0 = (float)qbg[e * stride + n];
+    const float p0 = (float)((gamma - 1.0) * qbg[4 * plane + e * stride + n]);
+    rec[e * N3 + n] = r0;
+    rec[n_e * N3 + e * N3 + n] = p0;
+    Q[0] = (double)r0;
+    Q[4] = (double)p0 / (gamma - 1.0);
+  }
+  for (int v = 0; v < 9; ++v) q0[v * plane + e * stride + n] = Q[v];
+}
+
+__global__ void bg_finish_kernel(int N, int64_t n_e, int64_t stride, double gamma, const double* __restrict__ R0,
+                                 const double* __restrict__ tr, const int* __restrict__ nbr,
+                                 const int* __restrict__ meta, float* rec, float* jump) {
+  const int N2 = N * N, N3 = N2 * N;
+  const int64_t plane = n_e * stride;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n_e * N3) {
+    const int64_t e = t / N3;
+    const int n = (int)(t % N3);
+    for (int c = 0; c < 3; ++c) rec[(2 + c) * n_e * N3 + t] = (float)R0[(1 + c) * plane + e * stride + n];
+  }
+  if (t < n_e * 6 * N2) {
+    const int64_t e = t / (6 * N2);
+    const int F = (int)((t / N2) % 6), pt = (int)(t % N2), a = pt % N, b = pt / N;
+    const int nb = nbr[e * 6 + F], mt = meta[e * 6 + F];
+    float jr = 0.0f, jp = 0.0f;
+    if (nb >= 0) {
+      const int code = meta_code(mt);
+      const int u = (code & 4) ? b : a, w = (code & 4) ? a : b;
+      const int a2 = (code & 2) ? N - 1 - u : u, b2 = (code & 1) ? N - 1 - w : w;
+      const double* To = tr + (e * 6 + F) * 9 * N2 + pt;
+      const double* Tn = tr + ((int64_t)nb * 6 + meta_nbF(mt)) * 9 * N2 + a2 + N * b2;
+      jr = (float)(Tn[0] - To[0]);
+      jp = (float)((gamma - 1.0) * (Tn[4 * N2] - To[4 * N2]));
+    }
+    jump[((e * 6 + F) * 2 + 0) * N2 + pt] = jr;
+    jump[((e * 6 + F) * 2 + 1) * N2 + pt] = jp;
+  }
+}
+
+cudaError_t launch_bg_prepare(const sd_mesh* m, double gamma, const double* q_bg, double* q0, float* rec,
+                              cudaStream_t s) {
+  const int64_t tot = m->n_e * m->stride;
+  if (tot == 0) return cudaSuccess;
+  bg_prepare_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(m->N, m->n_e, m->stride, gamma, q_bg, q0, rec);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bg_finish(const sd_mesh* m, double gamma, const double* R0, float* rec, float* jump,
+                             const double* tr, cudaStream_t s) {
+  const int64_t N2 = (int64_t)m->N * m->N;
+  const int64_t tot = m->n_e * (6 * N2 > N2 * m->N ? 6 * N2 : N2 * m->N);
+  if (tot == 0) return cudaSuccess;
+  bg_finish_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(m->N, m->n_e, m->stride, gamma, R0, tr, m->nbr,
+                                                                 m->meta, rec, jump);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Step control: dt = cfl h_min / (N lambda_max), c_h = lambda_max unless fixed.
+// ---------------------------------------------------------------------------
+
+__global__ void step_control_kernel(double* dyn, double cfl, double hmin, int N, double ch_fixed, double* dt_out) {
+  const double lam = __longlong_as_double((long long)(*reinterpret_cast<const unsigned long long*>(dyn + 2)));
+  const double dt = cfl * hmin / (N * lam);
+  const double ch = ch_fixed > 0.0 ? ch_fixed : lam;
+  dyn[0] = dt;
+  dyn[1] = ch;
+  if (dt_out) {
+    dt_out[0] = dt;
+    dt_out[1] = ch;
+  }
+}
+
+cudaError_t launch_step_control(const sd_mesh* m, double cfl, double c_h_fixed, double* dt_out, cudaStream_t s) {
+  step_control_kernel<<<1, 1, 0, s>>>(m->dyn, cfl, m->h_min, m->N, c_h_fixed, dt_out);
+  return cudaGetLastError();
+}
+
+}  // namespace sd

@@ -1,0 +1,122 @@
+// sd_internal.h -- structures shared by the host API and the CUDA kernels of the
+// SD MHD+GLM library.  Not part of the public ABI (include/sdmhd.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/sdmhd.h"
+
+namespace sd {
+
+constexpr int kMaxN = 8;
+constexpr int kNV = 9;  // conserved variables
+
+// 1D operators of one order N (Sec. SD Method): solution points xs, flux points
+// xf, extrapolation E[f][i] = h_i(xf_f), derivative D[i][f] = l_f'(xs_i),
+// quadrature weights w_i = int_0^1 h_i.  Passed to kernels by value.
+template <typename R>
+struct Ops {
+  R E[(kMaxN + 1) * kMaxN];
+  R D[kMaxN * (kMaxN + 1)];
+  R w[kMaxN];
+  R xs[kMaxN];
+  R xf[kMaxN + 1];
+};
+
+// Face metadata word: neighbour face (3 bits) | orientation code << 3 |
+// boundary condition << 6 | owner << 9.  Orientation code: bit 2 swaps the
+// two face-local indices, bits 1 and 0 flip the first and second.
+__host__ __device__ inline int meta_nbF(int m) { return m & 7; }
+__host__ __device__ inline int meta_code(int m) { return (m >> 3) & 7; }
+__host__ __device__ inline int meta_bc(int m) { return (m >> 6) & 7; }
+__host__ __device__ inline int meta_owner(int m) { return (m >> 9) & 1; }
+
+enum StageMode { MODE_RESIDUAL = 0, MODE_RK = 1, MODE_DIVB = 2 };
+
+// Arguments of the fused element kernels.  Geometry pointers are float or
+// double according to the precision policy of the kernel.
+struct StageParams {
+  int64_t n_e;
+  int64_t stride;  // element stride of state arrays
+  int64_t plane;   // n_e * stride
+  const double* q_in;
+  const double* q_n;
+  double* out;     // dqdt (residual) or q_out (RK)
+  int mode;
+  int central;     // 1: face flux is the central average (no Rusanov dissipation)
+  double rk_a, rk_b;
+  double dt, c_h;
+  const double* dyn;  // device (dt, c_h) or nullptr
+  double gamma, GM, omega, alpha;
+  int powell, gravity, coriolis, pad_;
+  double farfield[9];
+  const void* Sfam;   // [e][d][c][line][f]
+  const void* invJ;   // [e][n]
+  const void* X;      // [e][c][n]
+  const int* nbr;     // [e][6] neighbour element or -1
+  const int* meta;    // [e][6]
+  const void* tr_in;  // [e][F][v][N^2] traces of q_in
+  void* tr_out;       // traces of the output state (RK) or nullptr
+  const float* bg;       // [5][n_e * N^3] rho0, p0, R0x, R0y, R0z (FP32 mixed)
+  const float* bg_jump;  // [e][F][2][N^2] background jumps (rho0, p0), neighbour minus own
+  double* divb;          // [n_e * N^3] (MODE_DIVB)
+  unsigned long long* lam_max;  // trace kernel: running max of lambda (bits of a positive double)
+};
+
+}  // namespace sd
+
+struct sd_mesh {
+  int device;
+  int N, p;
+  int64_t n_e;
+  int64_t stride;
+  int64_t n_bf, n_if;
+  double h_min;
+  int geom;
+  // device geometry
+  double* Sfam64;
+  double* invJ64;
+  double* X64;
+  float* Sfam32;
+  float* invJ32;
+  float* X32;
+  int* nbr;
+  int* meta;
+  // scratch: face traces (ping-pong), small device scalars
+  double* tr64[2];
+  float* tr32[2];
+  const double* tr_tag[2];  // state whose traces buffer b holds (stage chaining)
+  int tr_prec[2];
+  double* dyn;              // [4]: dt, c_h, lambda bits, spare
+  double* diag_part;        // [n_e][12]
+  double* diag_out;         // [12]
+  double* divb;             // [n_e * N^3]
+  double* host_diag;        // pinned [12]
+  int64_t device_bytes;
+  sd::Ops<double> ops64;
+  sd::Ops<float> ops32;
+};
+
+struct sd_background {
+  const sd_mesh* mesh;
+  float* rec;    // [5][n_e * N^3]
+  float* jump;   // [n_e][6][2][N^2]
+  double gamma;
+};
+
+namespace sd {
+// kernels launched from the API (defined in the .cu files)
+cudaError_t launch_stage(const sd_mesh* m, int prec, const StageParams& P, cudaStream_t s);
+cudaError_t launch_traces(const sd_mesh* m, int prec, const StageParams& P, cudaStream_t s);
+cudaError_t launch_geometry(sd_mesh* m, const double* d_corners, int* d_flag, cudaStream_t s);
+cudaError_t launch_canonical_faces(sd_mesh* m, cudaStream_t s);
+cudaError_t launch_state_init(const sd_mesh* m, const sd_phys* ph, const sd_init* in, double B0dip, double* q,
+                              double* qbg, cudaStream_t s);
+cudaError_t launch_diag(const sd_mesh* m, const sd_phys* ph, const double* q, cudaStream_t s);
+cudaError_t launch_bg_prepare(const sd_mesh* m, double gamma, const double* q_bg, double* q0, float* rec,
+                              cudaStream_t s);
+cudaError_t launch_bg_finish(const sd_mesh* m, double gamma, const double* R0, float* rec, float* jump,
+                             const double* tr, cudaStream_t s);
+cudaError_t launch_step_control(const sd_mesh* m, double cfl, double c_h_fixed, double* dt_out, cudaStream_t s);
+}  // namespace sd

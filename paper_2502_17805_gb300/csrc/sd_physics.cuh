@@ -1,0 +1,198 @@
+// sd_physics.cuh -- pointwise physics of ideal MHD with GLM cleaning on the
+// device (arXiv 2502.17805, Sec. MHD Governing Equations):
+//   Q = (rho, m = rho U, E, B, psi),  E = p/(gamma-1) + rho|U|^2/2 + |B|^2/2 + psi^2/2  (Eq. 2-3)
+//   inviscid flux through a surface of normal n (Eq. invF):
+//     rho: rho U.n
+//     m  : m U.n + (p + |B|^2/2) n - B (B.n)
+//     E  : U.n (e + p + |B|^2/2) - (B.n)(U.B) + c_h psi (B.n),   e = E - psi^2/2
+//     B  : (U.n) B - (B.n) U + c_h psi n
+//     psi: c_h (B.n)
+// Two precision policies share the SD kernels:
+//   PolFP64  -- every value is the full state in FP64.
+//   PolMixed -- the state is carried as the FP32 perturbation q' about a
+//               hydrostatic background (rho0, p0; U = B = psi = 0), whose
+//               pressure-gradient flux lives in an FP64 background residual.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+
+namespace sd {
+
+struct PolFP64 {
+  using R = double;
+  static constexpr int NV = 9;  // values carried per point
+  static constexpr bool mixed = false;
+};
+
+struct PolMixed {
+  using R = float;
+  static constexpr int NV = 11;  // q'(9), rho0, p0
+  static constexpr bool mixed = true;
+};
+
+template <typename R>
+__device__ __forceinline__ R rcp_(R x) {
+  return R(1) / x;
+}
+
+// Full-state flux through the (not necessarily unit) normal n.
+template <typename R>
+__device__ __forceinline__ void flux_full(const R* q, R nx, R ny, R nz, R gm1, R ch, R* F) {
+  const R ir = rcp_(q[0]);
+  const R ux = q[1] * ir, uy = q[2] * ir, uz = q[3] * ir;
+  const R Bx = q[5], By = q[6], Bz = q[7], psi = q[8];
+  const R B2 = Bx * Bx + By * By + Bz * Bz;
+  const R mu = q[1] * ux + q[2] * uy + q[3] * uz;
+  const R p = gm1 * (q[4] - R(0.5) * (mu + B2 + psi * psi));
+  const R e = q[4] - R(0.5) * psi * psi;
+  const R un = ux * nx + uy * ny + uz * nz;
+  const R Bn = Bx * nx + By * ny + Bz * nz;
+  const R uB = ux * Bx + uy * By + uz * Bz;
+  const R pt = p + R(0.5) * B2;
+  const R chpsi = ch * psi;
+  F[0] = q[0] * un;
+  F[1] = q[1] * un + pt * nx - Bx * Bn;
+  F[2] = q[2] * un + pt * ny - By * Bn;
+  F[3] = q[3] * un + pt * nz - Bz * Bn;
+  F[4] = un * (e + pt) - Bn * uB + chpsi * Bn;
+  F[5] = un * Bx - Bn * ux + chpsi * nx;
+  F[6] = un * By - Bn * uy + chpsi * ny;
+  F[7] = un * Bz - Bn * uz + chpsi * nz;
+  F[8] = ch * Bn;
+}
+
+// Perturbation flux F(Q0 + q') - F(Q0) with Q0 = (rho0, 0, p0/(gamma-1), 0, 0):
+// the background carries only the pressure flux p0 n, which is left out here.
+// q holds q'(9), rho0, p0.  gg1 = gamma/(gamma-1).
+__device__ __forceinline__ void flux_pert(const float* q, float nx, float ny, float nz, float gm1, float gg1, float ch,
+                                          float* F) {
+  const float rho = q[9] + q[0];
+  const float ir = 1.0f / rho;
+  const float ux = q[1] * ir, uy = q[2] * ir, uz = q[3] * ir;
+  const float Bx = q[5], By = q[6], Bz = q[7], psi = q[8];
+  const float B2 = Bx * Bx + By * By + Bz * Bz;
+  const float mu = q[1] * ux + q[2] * uy + q[3] * uz;
+  const float pp = gm1 * (q[4] - 0.5f * (mu + B2 + psi * psi));  // p' = p - p0
+  const float un = ux * nx + uy * ny + uz * nz;
+  const float Bn = Bx * nx + By * ny + Bz * nz;
+  const float uB = ux * Bx + uy * By + uz * Bz;
+  const float ptp = pp + 0.5f * B2;
+  const float chpsi = ch * psi;
+  F[0] = q[1] * nx + q[2] * ny + q[3] * nz;
+  F[1] = q[1] * un + ptp * nx - Bx * Bn;
+  F[2] = q[2] * un + ptp * ny - By * Bn;
+  F[3] = q[3] * un + ptp * nz - Bz * Bn;
+  F[4] = un * (gg1 * q[10] + q[4] + ptp - 0.5f * psi * psi) - Bn * uB + chpsi * Bn;
+  F[5] = un * Bx - Bn * ux + chpsi * nx;
+  F[6] = un * By - Bn * uy + chpsi * ny;
+  F[7] = un * Bz - Bn * uz + chpsi * nz;
+  F[8] = ch * Bn;
+}
+
+// |U.n| + fast magnetosonic speed along the unit normal n.
+template <typename R>
+__device__ __forceinline__ R wave_speed(R rho, R mx, R my, R mz, R p, R Bx, R By, R Bz, R nx, R ny, R nz, R gamma) {
+  const R ir = rcp_(rho);
+  const R a2 = gamma * p * ir;
+  const R b2 = (Bx * Bx + By * By + Bz * Bz) * ir;
+  const R Bn = Bx * nx + By * ny + Bz * nz;
+  const R bn2 = Bn * Bn * ir;
+  const R s = a2 + b2;
+  R disc = s * s - R(4) * a2 * bn2;
+  disc = disc > R(0) ? disc : R(0);
+  const R cf = sqrt(R(0.5) * (s + sqrt(disc)));
+  const R un = (mx * nx + my * ny + mz * nz) * ir;
+  return fabs(un) + cf;
+}
+
+template <typename R>
+__device__ __forceinline__ R pressure_full(const R* q, R gm1) {
+  const R ir = rcp_(q[0]);
+  return gm1 * (q[4] - R(0.5) * ((q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) * ir + q[5] * q[5] + q[6] * q[6] +
+                                  q[7] * q[7] + q[8] * q[8]));
+}
+
+// Wall ghost state: rho, p, psi and E copied, U reflected; conducting walls
+// reflect B, radial walls reverse its tangential part.  For the mixed policy the
+// same rule applies to the perturbation (the background is symmetric).
+template <typename R>
+__device__ __forceinline__ void wall_ghost(const R* q, R nx, R ny, R nz, int bc, R* g) {
+  const R mn = q[1] * nx + q[2] * ny + q[3] * nz;
+  const R Bn = q[5] * nx + q[6] * ny + q[7] * nz;
+  g[0] = q[0];
+  g[1] = q[1] - R(2) * mn * nx;
+  g[2] = q[2] - R(2) * mn * ny;
+  g[3] = q[3] - R(2) * mn * nz;
+  g[4] = q[4];
+  if (bc == SD_BC_WALL_CONDUCTING) {
+    g[5] = q[5] - R(2) * Bn * nx;
+    g[6] = q[6] - R(2) * Bn * ny;
+    g[7] = q[7] - R(2) * Bn * nz;
+  } else {
+    g[5] = R(2) * Bn * nx - q[5];
+    g[6] = R(2) * Bn * ny - q[6];
+    g[7] = R(2) * Bn * nz - q[7];
+  }
+  g[8] = q[8];
+}
+
+// Rusanov common flux along the unit outward normal n of this side:
+//   F* = (F(qo) + F(qn))/2 - lambda/2 (qn - qo),  lambda = max(|u_n|+c_f both sides, c_h).
+// The same instruction sequence runs on both sides of a face with n negated and
+// the states swapped, which makes the two results exact negatives.
+__device__ __forceinline__ void riemann_fp64(const double* qo, const double* qn, double nx, double ny, double nz,
+                                             double gamma, double ch, int central, double* Fs) {
+  const double gm1 = gamma - 1.0;
+  double FL[9], FR[9];
+  flux_full<double>(qo, nx, ny, nz, gm1, ch, FL);
+  flux_full<double>(qn, nx, ny, nz, gm1, ch, FR);
+  if (central) {
+#pragma unroll
+    for (int v = 0; v < 9; ++v) Fs[v] = 0.5 * (FL[v] + FR[v]);
+    return;
+  }
+  const double lo = wave_speed<double>(qo[0], qo[1], qo[2], qo[3], pressure_full<double>(qo, gm1), qo[5], qo[6],
+                                       qo[7], nx, ny, nz, gamma);
+  const double ln = wave_speed<double>(qn[0], qn[1], qn[2], qn[3], pressure_full<double>(qn, gm1), qn[5], qn[6],
+                                       qn[7], nx, ny, nz, gamma);
+  double lam = fmax(lo, ln);
+  lam = fmax(lam, ch);
+  const double hl = 0.5 * lam;
+#pragma unroll
+  for (int v = 0; v < 9; ++v) Fs[v] = 0.5 * (FL[v] + FR[v]) - hl * (qn[v] - qo[v]);
+}
+
+// Mixed-policy Rusanov flux of the perturbation.  qo: own q'(9), rho0, p0;
+// qn: neighbour q'(9) (the background at the face is taken from this side);
+// jr, jp: FP64-accurate background jumps (neighbour minus own) of rho0 and p0.
+__device__ __forceinline__ void riemann_mixed(const float* qo, const float* qn, float nx, float ny, float nz,
+                                              float gamma, float ch, float jr, float jp, float* Fs) {
+  const float gm1 = gamma - 1.0f, gg1 = gamma / (gamma - 1.0f);
+  float qn11[11];
+#pragma unroll
+  for (int v = 0; v < 9; ++v) qn11[v] = qn[v];
+  qn11[9] = qo[9];
+  qn11[10] = qo[10];
+  float FL[9], FR[9];
+  flux_pert(qo, nx, ny, nz, gm1, gg1, ch, FL);
+  flux_pert(qn11, nx, ny, nz, gm1, gg1, ch, FR);
+  const float ro = qo[9] + qo[0], rn = qo[9] + qn[0];
+  const float ppo = gm1 * (qo[4] - 0.5f * ((qo[1] * qo[1] + qo[2] * qo[2] + qo[3] * qo[3]) / ro + qo[5] * qo[5] +
+                                            qo[6] * qo[6] + qo[7] * qo[7] + qo[8] * qo[8]));
+  const float ppn = gm1 * (qn[4] - 0.5f * ((qn[1] * qn[1] + qn[2] * qn[2] + qn[3] * qn[3]) / rn + qn[5] * qn[5] +
+                                            qn[6] * qn[6] + qn[7] * qn[7] + qn[8] * qn[8]));
+  const float lo = wave_speed<float>(ro, qo[1], qo[2], qo[3], qo[10] + ppo, qo[5], qo[6], qo[7], nx, ny, nz, gamma);
+  const float ln = wave_speed<float>(rn, qn[1], qn[2], qn[3], qo[10] + ppn, qn[5], qn[6], qn[7], nx, ny, nz, gamma);
+  float lam = fmaxf(fmaxf(lo, ln), ch);
+  const float hl = 0.5f * lam;
+#pragma unroll
+  for (int v = 0; v < 9; ++v) {
+    float dq = qn[v] - qo[v];
+    if (v == 0) dq += jr;
+    if (v == 4) dq += jp / gm1;
+    Fs[v] = 0.5f * (FL[v] + FR[v]) - hl * dq;
+  }
+}
+
+}  // namespace sd

@@ -1,0 +1,431 @@
+// sd_stage.cuh -- fused SD residual + SSP-RK stage kernel (one element per CTA).
+//
+// Per element (arXiv 2502.17805, Sec. Spectral Difference Method):
+//   load      Q at the N^3 solution points into shared memory
+//   faces     extrapolate Q to the 6 N^2 face points, read the neighbour's face
+//             trace (written by the previous stage), Rusanov common flux and
+//             BR1 normal field along the canonical face normal
+//   for each direction d:
+//     interior  extrapolate Q along the d-lines to the N-1 interior flux points,
+//               contravariant flux S^d . F(Q) and S^d . B
+//     derive    accumulate sum_f D[i][f] Ftilde^d_f at every solution point
+//   epilogue  R = -div/|J| + M(Q, div B), SSP-RK combination in FP64, and the
+//             face traces of the new state for the next stage.
+// Thread layout: BLK >= max(6 N^2, N^3) threads; thread n owns solution point n
+// in the derivative phase and epilogue (its accumulators stay in registers).
+#pragma once
+
+#include "sd_internal.h"
+#include "sd_physics.cuh"
+
+namespace sd {
+
+template <int N>
+struct Dims {
+  static constexpr int N2 = N * N, N3 = N2 * N, NF = N + 1;
+  static constexpr int NFACE = 6 * N2;
+  static constexpr int MAXW = NFACE > N3 ? NFACE : N3;
+  static constexpr int BLK = ((MAXW + 31) / 32) * 32;
+};
+
+template <int N, class Pol>
+struct Smem {
+  using R = typename Pol::R;
+  static constexpr int N2 = N * N, N3 = N2 * N, NF = N + 1, NV = Pol::NV;
+  static constexpr int oQ = 0;
+  static constexpr int oF = oQ + NV * N3;     // [10][NF][N2]
+  static constexpr int oFace = oF + 10 * NF * N2;  // [6][10][N2]
+  static constexpr int oE = oFace + 60 * N2;  // [NF][N]
+  static constexpr int oD = oE + NF * N;      // [N][NF]
+  static constexpr int nR = oD + N * NF;
+  static constexpr size_t bytesR = ((nR * sizeof(R)) + 15) / 16 * 16;
+  static constexpr size_t bytes = bytesR + (Pol::mixed ? 9 * N3 * sizeof(double) : 0);
+};
+
+// index of solution point (i along d; a, b the other two directions in increasing order)
+template <int N>
+__device__ __forceinline__ int sol_index(int d, int i, int a, int b) {
+  return d == 0 ? i + N * (a + N * b) : (d == 1 ? a + N * (i + N * b) : a + N * (b + N * i));
+}
+
+// Load one element's state into shared memory.  Mixed policy: q' = q - Q0 in
+// FP64, rounded to FP32, plus rho0 and p0; the FP64 state also goes to sQd.
+template <int N, class Pol>
+__device__ __forceinline__ void load_element(const StageParams& P, const double* q, int64_t e,
+                                             typename Pol::R* sQ, double* sQd, double* lam_out) {
+  constexpr int N3 = N * N * N, BLK = Dims<N>::BLK;
+  double lam = 0.0;
+  for (int n = threadIdx.x; n < N3; n += BLK) {
+    const int64_t g = e * P.stride + n;
+    double qv[9];
+#pragma unroll
+    for (int v = 0; v < 9; ++v) qv[v] = __ldg(q + v * P.plane + g);
+    if (lam_out) {
+      const double ir = 1.0 / qv[0];
+      const double m2 = qv[1] * qv[1] + qv[2] * qv[2] + qv[3] * qv[3];
+      const double B2 = qv[5] * qv[5] + qv[6] * qv[6] + qv[7] * qv[7];
+      const double p = (P.gamma - 1.0) * (qv[4] - 0.5 * (m2 * ir + B2 + qv[8] * qv[8]));
+      const double l = sqrt(m2) * ir + sqrt(P.gamma * p * ir + B2 * ir);
+      lam = (l > lam || l != l) ? l : lam;
+    }
+    if constexpr (!Pol::mixed) {
+#pragma unroll
+      for (int v = 0; v < 9; ++v) sQ[v * N3 + n] = qv[v];
+    } else {
+      const int64_t gb = e * N3 + n;
+      const float r0 = __ldg(P.bg + gb), p0 = __ldg(P.bg + P.n_e * N3 + gb);
+      if (sQd) {
+#pragma unroll
+        for (int v = 0; v < 9; ++v) sQd[v * N3 + n] = qv[v];
+      }
+#pragma unroll
+      for (int v = 0; v < 9; ++v) sQ[v * N3 + n] = (float)qv[v];
+      sQ[0 * N3 + n] = (float)(qv[0] - (double)r0);
+      sQ[4 * N3 + n] = (float)(qv[4] - (double)p0 / (P.gamma - 1.0));
+      sQ[9 * N3 + n] = r0;
+      sQ[10 * N3 + n] = p0;
+    }
+  }
+  if (lam_out) *lam_out = lam;
+}
+
+// Extrapolate the element state in shared memory to its 6 N^2 face points and
+// write the trace block [F][v][N^2] of element e.
+template <int N, class Pol>
+__device__ __forceinline__ void write_traces(const typename Pol::R* sQ, const typename Pol::R* sE,
+                                             typename Pol::R* tr, int64_t e) {
+  using R = typename Pol::R;
+  constexpr int N2 = N * N, N3 = N2 * N, BLK = Dims<N>::BLK;
+  for (int t = threadIdx.x; t < 6 * N2; t += BLK) {
+    const int F = t / N2, pt = t - F * N2, a = pt % N, b = pt / N;
+    const int d = F >> 1, f = (F & 1) ? N : 0;
+    R* T = tr + (e * 6 + F) * 9 * N2 + pt;
+#pragma unroll
+    for (int v = 0; v < 9; ++v) {
+      R s = R(0);
+#pragma unroll
+      for (int i = 0; i < N; ++i) s += sE[f * N + i] * sQ[v * N3 + sol_index<N>(d, i, a, b)];
+      T[v * N2] = s;
+    }
+  }
+}
+
+template <int N, class Pol>
+__global__ void __launch_bounds__(Dims<N>::BLK) trace_kernel(const StageParams P, const Ops<typename Pol::R> ops) {
+  using R = typename Pol::R;
+  constexpr int NF = N + 1, BLK = Dims<N>::BLK;
+  extern __shared__ __align__(16) unsigned char smem[];
+  using S = Smem<N, Pol>;
+  R* sQ = reinterpret_cast<R*>(smem) + S::oQ;
+  R* sE = reinterpret_cast<R*>(smem) + S::oE;
+  for (int i = threadIdx.x; i < NF * N; i += BLK) sE[i] = ops.E[i];
+  const int64_t e = blockIdx.x;
+  double lam = 0.0;
+  load_element<N, Pol>(P, P.q_in, e, sQ, nullptr, P.lam_max ? &lam : nullptr);
+  if (P.lam_max) {
+    // max over the block, then one atomic; positive doubles order like their bit patterns
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double other = __shfl_xor_sync(0xffffffffu, lam, o);
+      lam = (other > lam || other != other) ? other : lam;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMax(P.lam_max, (unsigned long long)__double_as_longlong(lam));
+  }
+  __syncthreads();
+  write_traces<N, Pol>(sQ, sE, reinterpret_cast<R*>(P.tr_out), e);
+}
+
+// Sources M (Sec. MHD Governing Equations) for the full FP64 state.
+__device__ __forceinline__ void sources_fp64(const StageParams& P, const double* q, double divB, double x0, double x1,
+                                             double x2, double* M) {
+  const double ir = 1.0 / q[0];
+  const double ux = q[1] * ir, uy = q[2] * ir, uz = q[3] * ir;
+#pragma unroll
+  for (int v = 0; v < 9; ++v) M[v] = 0.0;
+  if (P.gravity) {
+    const double r2 = x0 * x0 + x1 * x1 + x2 * x2;
+    const double ir3 = 1.0 / (r2 * sqrt(r2));
+    const double gx = -P.GM * x0 * ir3, gy = -P.GM * x1 * ir3, gz = -P.GM * x2 * ir3;
+    M[1] += q[0] * gx;
+    M[2] += q[0] * gy;
+    M[3] += q[0] * gz;
+    M[4] += q[1] * gx + q[2] * gy + q[3] * gz;
+  }
+  if (P.coriolis) {
+    M[1] += 2.0 * P.omega * q[2];
+    M[2] -= 2.0 * P.omega * q[1];
+  }
+  if (P.powell) {
+    const double uB = ux * q[5] + uy * q[6] + uz * q[7];
+    M[1] -= divB * q[5];
+    M[2] -= divB * q[6];
+    M[3] -= divB * q[7];
+    M[4] -= divB * uB;
+    M[5] -= divB * ux;
+    M[6] -= divB * uy;
+    M[7] -= divB * uz;
+  }
+  M[8] -= P.alpha * q[8];
+}
+
+// Sources of the perturbation (rho0 g lives in the FP64 background residual).
+__device__ __forceinline__ void sources_mixed(const StageParams& P, const float* q, float divB, float x0, float x1,
+                                              float x2, float* M) {
+  const float rho = q[9] + q[0];
+  const float ir = 1.0f / rho;
+  const float ux = q[1] * ir, uy = q[2] * ir, uz = q[3] * ir;
+#pragma unroll
+  for (int v = 0; v < 9; ++v) M[v] = 0.0f;
+  if (P.gravity) {
+    const float r2 = x0 * x0 + x1 * x1 + x2 * x2;
+    const float rr = rsqrtf(r2);
+    const float ir3 = rr * rr * rr;
+    const float GM = (float)P.GM;
+    const float gx = -GM * x0 * ir3, gy = -GM * x1 * ir3, gz = -GM * x2 * ir3;
+    M[1] += q[0] * gx;
+    M[2] += q[0] * gy;
+    M[3] += q[0] * gz;
+    M[4] += q[1] * gx + q[2] * gy + q[3] * gz;
+  }
+  if (P.coriolis) {
+    const float om2 = 2.0f * (float)P.omega;
+    M[1] += om2 * q[2];
+    M[2] -= om2 * q[1];
+  }
+  if (P.powell) {
+    const float uB = ux * q[5] + uy * q[6] + uz * q[7];
+    M[1] -= divB * q[5];
+    M[2] -= divB * q[6];
+    M[3] -= divB * q[7];
+    M[4] -= divB * uB;
+    M[5] -= divB * ux;
+    M[6] -= divB * uy;
+    M[7] -= divB * uz;
+  }
+  M[8] -= (float)P.alpha * q[8];
+}
+
+template <int N, class Pol>
+__global__ void __launch_bounds__(Dims<N>::BLK) stage_kernel(const StageParams P, const Ops<typename Pol::R> ops) {
+  using R = typename Pol::R;
+  using S = Smem<N, Pol>;
+  constexpr int N2 = N * N, N3 = N2 * N, NF = N + 1, BLK = Dims<N>::BLK, NV = Pol::NV;
+  extern __shared__ __align__(16) unsigned char smem[];
+  R* sQ = reinterpret_cast<R*>(smem) + S::oQ;
+  R* sF = reinterpret_cast<R*>(smem) + S::oF;
+  R* sFace = reinterpret_cast<R*>(smem) + S::oFace;
+  R* sE = reinterpret_cast<R*>(smem) + S::oE;
+  R* sD = reinterpret_cast<R*>(smem) + S::oD;
+  double* sQd = Pol::mixed ? reinterpret_cast<double*>(smem + S::bytesR) : nullptr;
+
+  const int tid = threadIdx.x;
+  for (int i = tid; i < NF * N; i += BLK) {
+    sE[i] = ops.E[i];
+    sD[i] = ops.D[i];
+  }
+  const int64_t e = blockIdx.x;
+  const R* Sfam = reinterpret_cast<const R*>(P.Sfam) + e * (9 * N2 * NF);
+  const R gamma = R(P.gamma);
+  const R gm1 = gamma - R(1);
+  double dt = P.dt, chd = P.c_h;
+  if (P.dyn) {
+    dt = P.dyn[0];
+    chd = P.dyn[1];
+  }
+  const R ch = R(chd);
+
+  load_element<N, Pol>(P, P.q_in, e, sQ, sQd, nullptr);
+  __syncthreads();
+
+  // ---- element faces: common flux and BR1 normal field
+  for (int t = tid; t < 6 * N2; t += BLK) {
+    const int F = t / N2, pt = t - F * N2, a = pt % N, b = pt / N;
+    const int d = F >> 1, side = F & 1, f = side ? N : 0;
+    R qo[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      R s = R(0);
+#pragma unroll
+      for (int i = 0; i < N; ++i) s += sE[f * N + i] * sQ[v * N3 + sol_index<N>(d, i, a, b)];
+      qo[v] = s;
+    }
+    const R* Sp = Sfam + (d * 3 * N2 + pt) * NF + f;
+    const R Sx = Sp[0], Sy = Sp[N2 * NF], Sz = Sp[2 * N2 * NF];
+    const R mag = sqrt(Sx * Sx + Sy * Sy + Sz * Sz);
+    const R im = R(1) / mag;
+    const R sg = side ? R(1) : R(-1);
+    const R nx = sg * Sx * im, ny = sg * Sy * im, nz = sg * Sz * im;
+    const int64_t gidx = e * 6 + F;
+    const int nb = P.nbr[gidx];
+    const int mt = P.meta[gidx];
+    R qn[9];
+    float jr = 0.0f, jp = 0.0f;
+    if (nb >= 0) {
+      const int code = meta_code(mt);
+      const int u = (code & 4) ? b : a, w = (code & 4) ? a : b;
+      const int a2 = (code & 2) ? N - 1 - u : u, b2 = (code & 1) ? N - 1 - w : w;
+      const R* T = reinterpret_cast<const R*>(P.tr_in) + ((int64_t)nb * 6 + meta_nbF(mt)) * 9 * N2 + a2 + N * b2;
+#pragma unroll
+      for (int v = 0; v < 9; ++v) qn[v] = T[v * N2];
+      if constexpr (Pol::mixed) {
+        jr = __ldg(P.bg_jump + (gidx * 2 + 0) * N2 + pt);
+        jp = __ldg(P.bg_jump + (gidx * 2 + 1) * N2 + pt);
+      }
+    } else {
+      const int bc = meta_bc(mt);
+      if (bc == SD_BC_FARFIELD) {
+#pragma unroll
+        for (int v = 0; v < 9; ++v) qn[v] = R(P.farfield[v]);
+        if constexpr (Pol::mixed) {
+          qn[0] -= qo[9];
+          qn[4] -= qo[10] / gm1;
+        }
+      } else {
+        wall_ghost<R>(qo, nx, ny, nz, bc, qn);
+      }
+    }
+    R Fs[9];
+    if constexpr (!Pol::mixed) {
+      riemann_fp64(qo, qn, nx, ny, nz, gamma, ch, P.central, Fs);
+    } else {
+      riemann_mixed(qo, qn, nx, ny, nz, gamma, ch, jr, jp, Fs);
+    }
+    const R Bn = R(0.5) * ((qo[5] + qn[5]) * nx + (qo[6] + qn[6]) * ny + (qo[7] + qn[7]) * nz);
+    const R sm = sg * mag;
+#pragma unroll
+    for (int v = 0; v < 9; ++v) sFace[(F * 10 + v) * N2 + pt] = sm * Fs[v];
+    sFace[(F * 10 + 9) * N2 + pt] = sm * Bn;
+  }
+
+  // ---- three directions: interior contravariant fluxes, then derivative
+  R acc[10];
+#pragma unroll
+  for (int v = 0; v < 10; ++v) acc[v] = R(0);
+  const int n = tid;
+  const int i0 = n % N, j0 = (n / N) % N, k0 = n / N2;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    __syncthreads();
+    for (int t = tid; t < (N - 1) * N2; t += BLK) {
+      const int fm = t % (N - 1), line = t / (N - 1), f = fm + 1, a = line % N, b = line / N;
+      R qf[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        R s = R(0);
+#pragma unroll
+        for (int i = 0; i < N; ++i) s += sE[f * N + i] * sQ[v * N3 + sol_index<N>(d, i, a, b)];
+        qf[v] = s;
+      }
+      const R* Sp = Sfam + (d * 3 * N2 + line) * NF + f;
+      const R Sx = Sp[0], Sy = Sp[N2 * NF], Sz = Sp[2 * N2 * NF];
+      R Fv[9];
+      if constexpr (!Pol::mixed) {
+        flux_full<R>(qf, Sx, Sy, Sz, gm1, ch, Fv);
+      } else {
+        flux_pert(qf, Sx, Sy, Sz, gm1, gamma / gm1, ch, Fv);
+      }
+#pragma unroll
+      for (int v = 0; v < 9; ++v) sF[(v * NF + f) * N2 + line] = Fv[v];
+      sF[(9 * NF + f) * N2 + line] = Sx * qf[5] + Sy * qf[6] + Sz * qf[7];
+    }
+    __syncthreads();
+    if (n < N3) {
+      const int id = d == 0 ? i0 : (d == 1 ? j0 : k0);
+      const int line = d == 0 ? j0 + N * k0 : (d == 1 ? i0 + N * k0 : i0 + N * j0);
+      const R* Dr = sD + id * NF;
+#pragma unroll
+      for (int v = 0; v < 10; ++v) {
+        R s = Dr[0] * sFace[((2 * d) * 10 + v) * N2 + line];
+#pragma unroll
+        for (int f = 1; f < N; ++f) s += Dr[f] * sF[(v * NF + f) * N2 + line];
+        s += Dr[N] * sFace[((2 * d + 1) * 10 + v) * N2 + line];
+        acc[v] += s;
+      }
+    }
+  }
+
+  // ---- epilogue: residual, sources, RK combination
+  double qout[9];
+  if (n < N3) {
+    const R iJ = reinterpret_cast<const R*>(P.invJ)[e * N3 + n];
+    const R* Xe = reinterpret_cast<const R*>(P.X) + e * 3 * N3;
+    const R divB = acc[9] * iJ;
+    double Rv[9];
+    double qin[9];
+    if constexpr (!Pol::mixed) {
+      double q[9], M[9];
+#pragma unroll
+      for (int v = 0; v < 9; ++v) q[v] = sQ[v * N3 + n];
+      sources_fp64(P, q, divB, Xe[n], Xe[N3 + n], Xe[2 * N3 + n], M);
+#pragma unroll
+      for (int v = 0; v < 9; ++v) {
+        Rv[v] = -acc[v] * iJ + M[v];
+        qin[v] = q[v];
+      }
+    } else {
+      float q[11], M[9];
+#pragma unroll
+      for (int v = 0; v < 11; ++v) q[v] = sQ[v * N3 + n];
+      sources_mixed(P, q, divB, Xe[n], Xe[N3 + n], Xe[2 * N3 + n], M);
+#pragma unroll
+      for (int v = 0; v < 9; ++v) {
+        Rv[v] = (double)(-acc[v] * iJ + M[v]);
+        qin[v] = sQd[v * N3 + n];
+      }
+      const int64_t gb = e * N3 + n, bp = P.n_e * N3;
+      Rv[1] += (double)__ldg(P.bg + 2 * bp + gb);
+      Rv[2] += (double)__ldg(P.bg + 3 * bp + gb);
+      Rv[3] += (double)__ldg(P.bg + 4 * bp + gb);
+    }
+    const int64_t g = e * P.stride + n;
+    if (P.mode == MODE_RESIDUAL) {
+#pragma unroll
+      for (int v = 0; v < 9; ++v) P.out[v * P.plane + g] = Rv[v];
+    } else if (P.mode == MODE_DIVB) {
+      P.divb[e * N3 + n] = (double)divB;
+    } else {
+      if (P.rk_a != 0.0) {
+#pragma unroll
+        for (int v = 0; v < 9; ++v)
+          qout[v] = P.rk_a * __ldg(P.q_n + v * P.plane + g) + P.rk_b * (qin[v] + dt * Rv[v]);
+      } else {
+#pragma unroll
+        for (int v = 0; v < 9; ++v) qout[v] = P.rk_b * (qin[v] + dt * Rv[v]);
+      }
+#pragma unroll
+      for (int v = 0; v < 9; ++v) P.out[v * P.plane + g] = qout[v];
+    }
+  }
+  if (P.mode == MODE_RK && P.tr_out) {
+    __syncthreads();
+    if (n < N3) {
+      if constexpr (!Pol::mixed) {
+#pragma unroll
+        for (int v = 0; v < 9; ++v) sQ[v * N3 + n] = qout[v];
+      } else {
+#pragma unroll
+        for (int v = 0; v < 9; ++v) sQ[v * N3 + n] = (float)qout[v];
+        sQ[0 * N3 + n] = (float)(qout[0] - (double)sQ[9 * N3 + n]);
+        sQ[4 * N3 + n] = (float)(qout[4] - (double)sQ[10 * N3 + n] / (P.gamma - 1.0));
+      }
+    }
+    __syncthreads();
+    write_traces<N, Pol>(sQ, sE, reinterpret_cast<R*>(P.tr_out), e);
+  }
+}
+
+template <int N, class Pol>
+cudaError_t launch_stage_t(const StageParams& P, const Ops<typename Pol::R>& ops, bool traces_only, cudaStream_t s) {
+  using Sm = Smem<N, Pol>;
+  const size_t bytes = Sm::bytes;
+  auto kern = traces_only ? trace_kernel<N, Pol> : stage_kernel<N, Pol>;
+  if (bytes > 48 * 1024) {
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (err != cudaSuccess) return err;
+  }
+  if (P.n_e == 0) return cudaSuccess;
+  kern<<<(unsigned)P.n_e, Dims<N>::BLK, bytes, s>>>(P, ops);
+  return cudaGetLastError();
+}
+
+}  // namespace sd

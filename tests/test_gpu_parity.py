@@ -1,0 +1,237 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Inputs come from the oracle or the seeded input generators only.  Tolerances:
+  FP64 residual:  |g - o| <= 1e-12 (|o| + s_v) per entry, s_v the oracle's
+                  un-cancelled magnitude of variable v (sum |D F| / |J| + |M|);
+  FP64 states:    1e-12 of the variable's magnitude after one stage or step;
+  FP32-mixed:     max |g - o| / max |o| <= 1e-5 per variable.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import sdref  # noqa: E402
+from paper_2502_17805_gb300 import inputs, sdmhd  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+ALFVEN = [1.0, 0.1, 1.0, 0.1, 2 * math.pi, 2 * math.pi, 2 * math.pi, 0.0]
+TOL64 = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _device():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2502_17805_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+
+
+def _pair(N, v, h, **kw):
+    return sdmhd.Mesh(N, v, h, **kw), sdref.Mesh(N, v, h, **kw)
+
+
+def _phys(**kw):
+    return sdmhd.Phys(**kw), sdref.Phys(**kw)
+
+
+def _rel_c19(g, o, s):
+    return float((np.abs(g - o) / (np.abs(o) + s[:, None, None])).max())
+
+
+def _residual_parity(gm, om, gph, oph, q0):
+    R = gm.to_host(gm.residual(gph, gm.to_device(q0)))
+    torch.cuda.synchronize()
+    Ro, s = om.residual(oph, q0)
+    return _rel_c19(R, Ro, s)
+
+
+@pytest.mark.parametrize("N", [2, 3, 4, 5, 6, 7, 8])
+def test_residual_box_alfven_all_orders(N):
+    v, h, per = inputs.box_mesh(3, jitter=0.1, seed=N)
+    gm, om = _pair(N, v, inputs.reorient(h, seed=N), periodic=per, geom=0)
+    gph, oph = _phys(powell=1, c_h=0.8, glm_alpha=0.3)
+    q0 = om.state_init(oph, sdref.INIT_ALFVEN, ALFVEN)
+    assert _residual_parity(gm, om, gph, oph, q0) < TOL64
+
+
+def test_residual_random_state_box():
+    N = 5
+    v, h, per = inputs.box_mesh(4, jitter=0.15, seed=3)
+    gm, om = _pair(N, v, inputs.reorient(h, seed=4), periodic=per, geom=0)
+    gph, oph = _phys(powell=1, c_h=0.6, glm_alpha=0.4)
+    q0 = inputs.random_state(gm.n_e, N, seed=11)
+    assert _residual_parity(gm, om, gph, oph, q0) < TOL64
+
+
+@pytest.mark.parametrize("N", [4, 6])
+def test_residual_shell_walls_all_sources(N):
+    v, h = inputs.shell_mesh(3, 2)
+    h = inputs.reorient(h, seed=5)
+    gm, om = _pair(N, v, h, geom=1, r_in=0.7, r_out=0.98, bc_in=sdref.BC_WALL_CONDUCTING,
+                   bc_out=sdref.BC_WALL_RADIAL)
+    gph, oph = _phys(powell=1, c_h=0.9, glm_alpha=0.5, gravity=1, GM=1.0, coriolis=1, omega=1.3)
+    q0 = inputs.random_state(gm.n_e, N, seed=6)
+    assert _residual_parity(gm, om, gph, oph, q0) < TOL64
+    q1 = om.state_init(oph, sdref.INIT_SHELL_POLYTROPE, [2.0, 0.7, 0.98, 1.0, 1.0, 1e-4, 1e-3], seed=3)
+    assert _residual_parity(gm, om, gph, oph, q1) < TOL64
+
+
+def test_free_stream_on_shell():
+    N = 6
+    v, h = inputs.shell_mesh(2, 2)
+    h = inputs.reorient(h, seed=8)
+    gm, om = _pair(N, v, h, geom=1, r_in=0.7, r_out=0.98, bc_in=sdref.BC_FARFIELD, bc_out=sdref.BC_FARFIELD)
+    gph, oph = _phys(powell=1, c_h=0.9)
+    q0 = om.state_init(oph, sdref.INIT_UNIFORM, [1.0, 0.3, -0.2, 0.1, 0.5, 0.4, 0.2, -0.3, 0.0])
+    gph.farfield = oph.farfield = list(q0[:, 0, 0])
+    R = gm.to_host(gm.residual(gph, gm.to_device(q0)))
+    _, s = om.residual(oph, q0)
+    for var in range(9):
+        assert np.abs(R[var]).max() <= 1e-13 * s[var]
+
+
+def test_conservation_is_exact_on_periodic_box():
+    N = 5
+    v, h, per = inputs.box_mesh(3, jitter=0.15, seed=2)
+    gm, om = _pair(N, v, inputs.reorient(h, seed=9), periodic=per, geom=0)
+    gph, oph = _phys(powell=0, c_h=0.6)
+    q0 = inputs.random_state(gm.n_e, N, seed=5)
+    R = gm.to_host(gm.residual(gph, gm.to_device(q0)))
+    w = sdref.nodes(N)[4]
+    W = np.einsum("i,j,k->kji", w, w, w).ravel()
+    J = np.stack([om.geometry(e)[1] for e in range(om.n_e)])
+    tot = (R * W * J).sum(axis=(1, 2))
+    mag = (np.abs(R) * W * J).sum(axis=(1, 2))
+    assert np.all(np.abs(tot) <= 1e-13 * mag), tot / mag
+
+
+def test_rk_stages_individually():
+    N = 4
+    v, h, per = inputs.box_mesh(3, jitter=0.1, seed=7)
+    gm, om = _pair(N, v, inputs.reorient(h, seed=7), periodic=per, geom=0)
+    gph, oph = _phys(powell=1, c_h=0.7, glm_alpha=0.2)
+    qn = inputs.random_state(gm.n_e, N, seed=1)
+    qi = inputs.random_state(gm.n_e, N, seed=2)
+    dt = 2e-3
+    for stage in range(3):
+        g_out = gm.empty_state()
+        gm.rk_stage(gph, stage, dt, gm.to_device(qn), gm.to_device(qi), g_out)
+        o_out = om.rk_stage(oph, stage, dt, qn, qi)
+        err = np.abs(gm.to_host(g_out) - o_out).max(axis=(1, 2)) / np.abs(o_out).max(axis=(1, 2))
+        assert err.max() < TOL64, (stage, err)
+
+
+def test_alfven_box_twenty_steps_fp64():
+    """The periodic Alfven-wave box at N = 6: 20 SSP-RK3 steps at CFL 0.2, dt and c_h from lambda_max."""
+    N, cfl = 6, 0.2
+    v, h, per = inputs.box_mesh(4)
+    gm, om = _pair(N, v, h, periodic=per, geom=0)
+    gph, oph = _phys(powell=1, c_h=0.0, glm_alpha=0.0)
+    q0 = om.state_init(oph, sdref.INIT_ALFVEN, ALFVEN)
+    q, work = gm.to_device(q0), gm.empty_state()
+    dts = torch.zeros(2, dtype=torch.float64, device="cuda")
+    hmin = om.info()["h_min"]
+    qo = q0
+    for _ in range(20):
+        gm.step(gph, cfl, q, work, dt_out=dts)
+        lam = om.diagnostics(oph, qo)["lambda_max"]
+        oph.c_h = lam
+        qo = om.rk_step(oph, cfl * hmin / (N * lam), qo)
+        g_dt = dts.cpu().numpy()
+        assert abs(g_dt[0] / (cfl * hmin / (N * lam)) - 1.0) < 1e-12
+    err = np.abs(gm.to_host(q) - qo).max(axis=(1, 2)) / np.abs(qo).max(axis=(1, 2))
+    assert err.max() < 1e-11, err
+
+
+def test_state_init_parity():
+    N = 5
+    v, h = inputs.shell_mesh(3, 2)
+    gm, om = _pair(N, v, h, geom=1, r_in=0.7, r_out=0.98)
+    gph, oph = _phys(gravity=1, GM=1.0)
+    prm = [3.0, 0.7, 0.98, 1.0, 1.0, 1e-4, 1e-6]
+    bg = gm.empty_state()
+    q = gm.state_init(gph, sdmhd.INIT_SHELL_POLYTROPE, prm, seed=7, background=bg)
+    qo, qbo = om.state_init(oph, sdref.INIT_SHELL_POLYTROPE, prm, seed=7, background=True)
+    for g, o in ((gm.to_host(q), qo), (gm.to_host(bg), qbo)):
+        scale = np.maximum(np.abs(o).max(axis=(1, 2)), 1e-300)
+        assert (np.abs(g - o).max(axis=(1, 2)) / scale).max() < TOL64
+    v2, h2, per = inputs.box_mesh(3, jitter=0.1, seed=1)
+    gm2, om2 = _pair(N, v2, h2, periodic=per, geom=0)
+    qa = gm2.to_host(gm2.state_init(gph, sdmhd.INIT_ALFVEN, ALFVEN))
+    qao = om2.state_init(oph, sdref.INIT_ALFVEN, ALFVEN)
+    assert np.abs(qa - qao).max() < 1e-13
+
+
+def test_diagnostics_parity():
+    N = 5
+    v, h = inputs.shell_mesh(3, 2)
+    gm, om = _pair(N, v, inputs.reorient(h, seed=2), geom=1, r_in=0.7, r_out=0.98)
+    gph, oph = _phys(gravity=1, GM=1.0, powell=1)
+    q0 = inputs.random_state(gm.n_e, N, seed=3)
+    g = gm.diagnostics(gph, gm.to_device(q0))
+    o = om.diagnostics(oph, q0)
+    for k in ("ke", "eb", "max_divb", "mass", "energy", "lambda_max", "min_rho", "min_p", "volume"):
+        assert abs(g[k] - o[k]) <= 1e-12 * abs(o[k]), (k, g[k], o[k])
+
+
+def test_diagnostics_flags_nonphysical_state():
+    N = 3
+    v, h, per = inputs.box_mesh(3)
+    gm = sdmhd.Mesh(N, v, h, periodic=per, geom=0)
+    q0 = inputs.random_state(gm.n_e, N, seed=3)
+    q0[0, 4, 5] = -1.0  # negative density planted on the host
+    d = gm.diagnostics(sdmhd.Phys(), gm.to_device(q0), check=False)
+    assert d["status"] == 7 and d["min_rho"] == -1.0
+
+
+def _mixed_case(nz, nr, N, Nrho, seed=0):
+    v, h = inputs.shell_mesh(nz, nr)
+    gm, om = _pair(N, v, h, geom=1, r_in=0.7, r_out=0.98, bc_in=sdref.BC_WALL_CONDUCTING,
+                   bc_out=sdref.BC_WALL_RADIAL)
+    gph, oph = _phys(powell=1, c_h=1.0, glm_alpha=0.5, gravity=1, GM=1.0, coriolis=1, omega=1.0)
+    prm = [Nrho, 0.7, 0.98, 1.0, 1.0, 1e-4, 1e-6]
+    q0, qb = om.state_init(oph, sdref.INIT_SHELL_POLYTROPE, prm, seed=seed, background=True)
+    return gm, om, gph, oph, q0, qb
+
+
+def test_mixed_residual_stratified_shell():
+    gm, om, gph, oph, q0, qb = _mixed_case(4, 2, 6, 3.0)
+    bg = gm.background(gph, gm.to_device(qb))
+    R = gm.to_host(gm.residual(gph, gm.to_device(q0), prec=sdmhd.SD_FP32_MIXED, bg=bg))
+    Ro, _ = om.residual(oph, q0)
+    err = np.abs(R - Ro).max(axis=(1, 2)) / np.abs(Ro).max(axis=(1, 2))
+    assert err.max() <= 1e-5, err
+
+
+def test_mixed_stage_stratified_shell():
+    gm, om, gph, oph, q0, qb = _mixed_case(3, 2, 5, 2.0, seed=4)
+    bg = gm.background(gph, gm.to_device(qb))
+    dt = 1e-3
+    q, work = gm.to_device(q0), gm.empty_state()
+    gm.rk_step(gph, dt, q, work, prec=sdmhd.SD_FP32_MIXED, bg=bg)
+    qo = om.rk_step(oph, dt, q0)
+    # compare the change over the step, per variable
+    dg, do = gm.to_host(q) - q0, qo - q0
+    err = np.abs(dg - do).max(axis=(1, 2)) / np.maximum(np.abs(do).max(axis=(1, 2)), 1e-300)
+    assert err.max() <= 1e-5, err
+
+
+def test_step_equals_three_stages():
+    N = 4
+    v, h = inputs.shell_mesh(2, 2)
+    gm = sdmhd.Mesh(N, v, h, geom=1, r_in=0.7, r_out=0.98)
+    gph = sdmhd.Phys(powell=1, c_h=0.0, glm_alpha=0.5, gravity=1, GM=1.0, coriolis=1, omega=1.0)
+    q0 = inputs.random_state(gm.n_e, N, seed=12)
+    qa, wa = gm.to_device(q0), gm.empty_state()
+    dts = torch.zeros(2, dtype=torch.float64, device="cuda")
+    gm.step(gph, 0.3, qa, wa, dt_out=dts)
+    dt, ch = dts.cpu().numpy()
+    gph.c_h = float(ch)
+    qb, wb = gm.to_device(q0), gm.empty_state()
+    gm.rk_step(gph, float(dt), qb, wb)
+    assert torch.equal(qa, qb)
