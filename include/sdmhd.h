@@ -136,6 +136,15 @@ typedef struct {
   int64_t device_bytes;    /* bytes the library holds on the device for this mesh */
 } sd_mesh_info;
 
+typedef struct {
+  int64_t stage_launches; /* fused element kernels (residual / RK stages) */
+  double stage_ms;        /* their summed device time */
+  int64_t trace_launches; /* face-trace kernels (with lambda_max in sd_step) */
+  double trace_ms;
+  int64_t other_launches; /* step control, geometry-free helpers, diagnostics */
+  double other_ms;
+} sd_profile_stats;
+
 typedef struct sd_mesh sd_mesh;
 typedef struct sd_background sd_background;
 
@@ -206,6 +215,15 @@ sd_status sd_step(const sd_mesh* mesh, const sd_phys* phys, sd_precision prec, d
  * order (deterministic).  Synchronises `stream`; returns SD_ERR_NONPHYSICAL
  * (with *out filled) when rho <= 0, p <= 0 or a NaN is found. */
 sd_status sd_diagnostics(const sd_mesh* mesh, const sd_phys* phys, const double* q, sd_diag* out, void* stream);
+
+/* Kernel timing (tracing): with enable = 1 every kernel the library launches
+ * for this mesh is bracketed by CUDA events on its launching stream; the
+ * counters restart.  At most 65536 launches are recorded.  enable = 0 stops
+ * recording. */
+sd_status sd_profile_enable(sd_mesh* mesh, int32_t enable);
+/* Waits for the recorded events, sums the device time per kernel class into
+ * *out and clears the record. */
+sd_status sd_profile_read(sd_mesh* mesh, sd_profile_stats* out);
 
 #ifdef __cplusplus
 }

@@ -594,7 +594,10 @@ double sdref_fast_speed(const double* q, const double* n, double gam) {
   return sqrt(0.5 * (s + sqrt(disc)));
 }
 
-void sdref_rusanov(const double* qL, const double* qR, const double* n, double gam, double ch, double* F) {
+/* Rusanov flux F; Fmag (may be NULL) receives the magnitude of its terms before they cancel,
+ * (|F_L| + |F_R|)/2 + lambda (|q_L| + |q_R|)/2, used only for the comparison tolerance */
+static void rusanov_mag(const double* qL, const double* qR, const double* n, double gam, double ch, double* F,
+                        double* Fmag) {
   double FL[9], FR[9];
   sdref_flux(qL, n, gam, ch, FL);
   sdref_flux(qR, n, gam, ch, FR);
@@ -605,6 +608,12 @@ void sdref_rusanov(const double* qL, const double* qR, const double* n, double g
   if (lR > lam) lam = lR;
   if (ch > lam) lam = ch;
   for (int v = 0; v < 9; ++v) F[v] = 0.5 * (FL[v] + FR[v]) - 0.5 * lam * (qR[v] - qL[v]);
+  if (Fmag)
+    for (int v = 0; v < 9; ++v) Fmag[v] = 0.5 * (fabs(FL[v]) + fabs(FR[v])) + 0.5 * lam * (fabs(qR[v]) + fabs(qL[v]));
+}
+
+void sdref_rusanov(const double* qL, const double* qR, const double* n, double gam, double ch, double* F) {
+  rusanov_mag(qL, qR, n, gam, ch, F, NULL);
 }
 
 /* wall / far-field ghost state (reading R9) */
@@ -650,20 +659,21 @@ static void face_value(const sdref_mesh* m, const double* q, int64_t e, int F, i
 }
 
 /* common contravariant flux at point (a,b) of face F of element e, given this side's value Qown.
- * Ft[9] receives S^d . F* (the family-d contravariant flux), Bt the BR1 value S^d . B*. */
+ * Ft[9] receives S^d . F* (the family-d contravariant flux), Bt the BR1 value S^d . B*, and
+ * Ftm[9] the magnitude of the terms of Ft before cancellation (tolerance only). */
 static void common_flux(const sdref_mesh* m, const sdref_phys* ph, const double* q, int64_t e, int F, int a,
-                        int b, const double* Qown, double* Ft, double* Bt) {
+                        int b, const double* Qown, double* Ft, double* Bt, double* Ftm) {
   int N = m->N, d = F / 2, side = F & 1, f = side ? N : 0;
   double sgn = side ? 1.0 : -1.0; /* S^d points along increasing d: outward on the d=1 face */
   int64_t k = 6 * e + F;
-  double Fs[9], Bn, mag;
+  double Fs[9], Fm[9], Bn, mag;
   if (m->nb_e[k] < 0) {
     const double* S = geo_S(m, e, d, f, a, b);
     mag = sqrt(S[0] * S[0] + S[1] * S[1] + S[2] * S[2]);
     double n[3] = {sgn * S[0] / mag, sgn * S[1] / mag, sgn * S[2] / mag};
     double g[9];
     ghost_state(Qown, n, m->bc[k], ph, g);
-    sdref_rusanov(Qown, g, n, ph->gamma, ph->c_h, Fs);
+    rusanov_mag(Qown, g, n, ph->gamma, ph->c_h, Fs, Fm);
     Bn = 0.5 * ((Qown[5] + g[5]) * n[0] + (Qown[6] + g[6]) * n[1] + (Qown[7] + g[7]) * n[2]);
   } else {
     int64_t e2 = m->nb_e[k];
@@ -675,7 +685,7 @@ static void common_flux(const sdref_mesh* m, const sdref_phys* ph, const double*
       const double* S = geo_S(m, e, d, f, a, b);
       mag = sqrt(S[0] * S[0] + S[1] * S[1] + S[2] * S[2]);
       double n[3] = {sgn * S[0] / mag, sgn * S[1] / mag, sgn * S[2] / mag};
-      sdref_rusanov(Qown, Q2, n, ph->gamma, ph->c_h, Fs);
+      rusanov_mag(Qown, Q2, n, ph->gamma, ph->c_h, Fs, Fm);
       Bn = 0.5 * ((Qown[5] + Q2[5]) * n[0] + (Qown[6] + Q2[6]) * n[1] + (Qown[7] + Q2[7]) * n[2]);
     } else {
       /* the owner (neighbour) side defines the normal: F* computed with the owner as left state */
@@ -684,13 +694,16 @@ static void common_flux(const sdref_mesh* m, const sdref_phys* ph, const double*
       const double* S = geo_S(m, e2, d2, f2, a2, b2);
       mag = sqrt(S[0] * S[0] + S[1] * S[1] + S[2] * S[2]);
       double n[3] = {sgn2 * S[0] / mag, sgn2 * S[1] / mag, sgn2 * S[2] / mag};
-      sdref_rusanov(Q2, Qown, n, ph->gamma, ph->c_h, Fs);
+      rusanov_mag(Q2, Qown, n, ph->gamma, ph->c_h, Fs, Fm);
       Bn = 0.5 * ((Q2[5] + Qown[5]) * n[0] + (Q2[6] + Qown[6]) * n[1] + (Q2[7] + Qown[7]) * n[2]);
       for (int v = 0; v < 9; ++v) Fs[v] = -Fs[v]; /* this side's outward normal is -n */
       Bn = -Bn;
     }
   }
-  for (int v = 0; v < 9; ++v) Ft[v] = sgn * mag * Fs[v];
+  for (int v = 0; v < 9; ++v) {
+    Ft[v] = sgn * mag * Fs[v];
+    Ftm[v] = mag * Fm[v];
+  }
   *Bt = sgn * mag * Bn;
 }
 
@@ -739,7 +752,7 @@ static void residual_element(const sdref_mesh* m, const sdref_phys* ph, const do
   for (int d = 0; d < 3; ++d)
     for (int b = 0; b < N; ++b)
       for (int a = 0; a < N; ++a) {
-        double Qf[MAXN + 1][9], Ft[MAXN + 1][9], Bt[MAXN + 1];
+        double Qf[MAXN + 1][9], Ft[MAXN + 1][9], Ftm[MAXN + 1][9], Bt[MAXN + 1];
         /* extrapolate the solution along the line to the family-d flux points */
         for (int f = 0; f <= N; ++f)
           for (int v = 0; v < 9; ++v) {
@@ -751,20 +764,20 @@ static void residual_element(const sdref_mesh* m, const sdref_phys* ph, const do
         for (int f = 1; f < N; ++f) {
           const double* S = geo_S(m, e, d, f, a, b);
           sdref_flux(Qf[f], S, ph->gamma, ph->c_h, Ft[f]);
+          for (int v = 0; v < 9; ++v) Ftm[f][v] = fabs(Ft[f][v]);
           Bt[f] = S[0] * Qf[f][5] + S[1] * Qf[f][6] + S[2] * Qf[f][7];
         }
         /* element-boundary flux points: common (Rusanov / BR1) values */
-        common_flux(m, ph, q, e, 2 * d + 0, a, b, Qf[0], Ft[0], &Bt[0]);
-        common_flux(m, ph, q, e, 2 * d + 1, a, b, Qf[N], Ft[N], &Bt[N]);
+        common_flux(m, ph, q, e, 2 * d + 0, a, b, Qf[0], Ft[0], &Bt[0], Ftm[0]);
+        common_flux(m, ph, q, e, 2 * d + 1, a, b, Qf[N], Ft[N], &Bt[N], Ftm[N]);
         /* derivative of the flux polynomial at the solution points */
         for (int i = 0; i < N; ++i) {
           int n = sol_index(N, d, i, a, b);
           for (int v = 0; v < 9; ++v) {
             double s = 0.0, sa = 0.0;
             for (int f = 0; f <= N; ++f) {
-              double t = m->D[i * (N + 1) + f] * Ft[f][v];
-              s += t;
-              sa += fabs(t);
+              s += m->D[i * (N + 1) + f] * Ft[f][v];
+              sa += fabs(m->D[i * (N + 1) + f]) * Ftm[f][v];
             }
             div[v][n] += s;
             mag[v][n] += sa;

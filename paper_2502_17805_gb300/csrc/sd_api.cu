@@ -198,6 +198,7 @@ cudaError_t dalloc(T** p, size_t count, int64_t* bytes) {
 
 void free_mesh(sd_mesh* m) {
   if (!m) return;
+  for (cudaEvent_t ev : m->prof_ev) cudaEventDestroy(ev);
   void* ptrs[] = {m->Sfam64, m->invJ64, m->X64, m->Sfam32, m->invJ32, m->X32, m->nbr, m->meta,
                   m->tr64[0], m->tr64[1], m->tr32[0], m->tr32[1], m->dyn, m->diag_part, m->diag_out, m->divb};
   for (void* p : ptrs)
@@ -242,6 +243,32 @@ sd::StageParams base_params(const sd_mesh* m, const sd_phys* ph, int prec) {
 }
 
 void* trace_buf(sd_mesh* m, int prec, int b) { return prec == SD_FP64 ? (void*)m->tr64[b] : (void*)m->tr32[b]; }
+
+// Kernel timing: CUDA events on the launching stream around one launch.
+enum { PROF_STAGE = 0, PROF_TRACE = 1, PROF_OTHER = 2 };
+constexpr size_t kMaxProf = 65536;
+
+struct ProfScope {
+  sd_mesh* m;
+  cudaStream_t s;
+  bool on;
+  ProfScope(const sd_mesh* mc, int cls, cudaStream_t st) : m(const_cast<sd_mesh*>(mc)), s(st), on(false) {
+    if (!m->prof_on || m->prof_used >= kMaxProf) return;
+    const size_t i = m->prof_used;
+    while (m->prof_ev.size() < 2 * (i + 1)) {
+      cudaEvent_t ev;
+      if (cudaEventCreate(&ev) != cudaSuccess) return;
+      m->prof_ev.push_back(ev);
+    }
+    if (m->prof_cls.size() < i + 1) m->prof_cls.resize(i + 1);
+    m->prof_cls[i] = cls;
+    on = cudaEventRecord(m->prof_ev[2 * i], s) == cudaSuccess;
+  }
+  ~ProfScope() {
+    if (!on) return;
+    if (cudaEventRecord(m->prof_ev[2 * m->prof_used + 1], s) == cudaSuccess) m->prof_used++;
+  }
+};
 
 sd_status check_common(const sd_mesh* m, const sd_phys* ph, int prec, const sd_background* bg) {
   if (!m) return fail(SD_ERR_INVALID_ARGUMENT, "mesh is NULL");
@@ -379,8 +406,7 @@ sd_status sd_mesh_create(const sd_mesh_desc* desc, void* stream, sd_mesh** out) 
     }
 
   // ---- device objects
-  sd_mesh* m = new sd_mesh;
-  memset(m, 0, sizeof(sd_mesh));
+  sd_mesh* m = new sd_mesh();
   if (cudaGetDevice(&m->device) != cudaSuccess) {
     delete m;
     return fail(SD_ERR_CUDA, "no CUDA device");
@@ -601,14 +627,21 @@ sd_status sd_residual(const sd_mesh* m, const sd_phys* ph, sd_precision prec, co
   }
   P.q_in = q;
   P.tr_out = trace_buf(mm, prec, 0);
-  cudaError_t err = sd::launch_traces(m, prec, P, s);
+  cudaError_t err;
+  {
+    ProfScope ps(m, PROF_TRACE, s);
+    err = sd::launch_traces(m, prec, P, s);
+  }
   if (err != cudaSuccess) return cuda_fail(err, "trace kernel");
   mm->tr_tag[0] = mm->tr_tag[1] = nullptr;
   P.tr_in = P.tr_out;
   P.tr_out = nullptr;
   P.mode = sd::MODE_RESIDUAL;
   P.out = dqdt;
-  err = sd::launch_stage(m, prec, P, s);
+  {
+    ProfScope ps(m, PROF_STAGE, s);
+    err = sd::launch_stage(m, prec, P, s);
+  }
   if (err != cudaSuccess) return cuda_fail(err, "residual kernel");
   return SD_OK;
 }
@@ -632,7 +665,11 @@ static sd_status rk_stage_impl(sd_mesh* m, const sd_phys* ph, int prec, int stag
     bin = 0;
     P.q_in = q_in;
     P.tr_out = trace_buf(m, prec, bin);
-    cudaError_t err = sd::launch_traces(m, prec, P, s);
+    cudaError_t err;
+    {
+      ProfScope ps(m, PROF_TRACE, s);
+      err = sd::launch_traces(m, prec, P, s);
+    }
     if (err != cudaSuccess) return cuda_fail(err, "trace kernel");
   }
   const int bout = 1 - bin;
@@ -646,7 +683,11 @@ static sd_status rk_stage_impl(sd_mesh* m, const sd_phys* ph, int prec, int stag
   P.dyn = dyn;
   P.tr_in = trace_buf(m, prec, bin);
   P.tr_out = want_traces ? trace_buf(m, prec, bout) : nullptr;
-  cudaError_t err = sd::launch_stage(m, prec, P, s);
+  cudaError_t err;
+  {
+    ProfScope ps(m, PROF_STAGE, s);
+    err = sd::launch_stage(m, prec, P, s);
+  }
   if (err != cudaSuccess) return cuda_fail(err, "stage kernel");
   m->tr_tag[bin] = nullptr;
   m->tr_tag[bout] = want_traces ? q_out : nullptr;
@@ -689,8 +730,14 @@ sd_status sd_step(const sd_mesh* m, const sd_phys* ph, sd_precision prec, double
   P.q_in = q;
   P.tr_out = trace_buf(mm, prec, 0);
   P.lam_max = reinterpret_cast<unsigned long long*>(mm->dyn + 2);
-  SD_CUDA(sd::launch_traces(m, prec, P, s));
-  SD_CUDA(sd::launch_step_control(m, cfl, ph->c_h, dt_out, s));
+  {
+    ProfScope ps(m, PROF_TRACE, s);
+    SD_CUDA(sd::launch_traces(m, prec, P, s));
+  }
+  {
+    ProfScope ps(m, PROF_OTHER, s);
+    SD_CUDA(sd::launch_step_control(m, cfl, ph->c_h, dt_out, s));
+  }
   mm->tr_tag[0] = q;
   mm->tr_prec[0] = prec;
   mm->tr_tag[1] = nullptr;
@@ -710,7 +757,10 @@ sd_status sd_step(const sd_mesh* m, const sd_phys* ph, sd_precision prec, double
     S.dyn = mm->dyn;
     S.tr_in = trace_buf(mm, prec, 0);
     S.tr_out = trace_buf(mm, prec, 1);
-    SD_CUDA(sd::launch_stage(m, prec, S, s));
+    {
+      ProfScope ps(m, PROF_STAGE, s);
+      SD_CUDA(sd::launch_stage(m, prec, S, s));
+    }
     mm->tr_tag[0] = nullptr;
     mm->tr_tag[1] = work;
     mm->tr_prec[1] = prec;
@@ -732,14 +782,20 @@ sd_status sd_diagnostics(const sd_mesh* m, const sd_phys* ph, const double* q, s
   sd::StageParams P = base_params(m, ph, SD_FP64);
   P.q_in = q;
   P.tr_out = mm->tr64[0];
-  SD_CUDA(sd::launch_traces(m, SD_FP64, P, s));
+  {
+    ProfScope ps(m, PROF_OTHER, s);
+    SD_CUDA(sd::launch_traces(m, SD_FP64, P, s));
+  }
   mm->tr_tag[0] = mm->tr_tag[1] = nullptr;
   P.tr_in = mm->tr64[0];
   P.tr_out = nullptr;
   P.mode = sd::MODE_DIVB;
   P.divb = mm->divb;
-  SD_CUDA(sd::launch_stage(m, SD_FP64, P, s));
-  SD_CUDA(sd::launch_diag(m, ph, q, s));
+  {
+    ProfScope ps(m, PROF_OTHER, s);
+    SD_CUDA(sd::launch_stage(m, SD_FP64, P, s));
+    SD_CUDA(sd::launch_diag(m, ph, q, s));
+  }
   SD_CUDA(cudaMemcpyAsync(mm->host_diag, mm->diag_out, 10 * sizeof(double), cudaMemcpyDeviceToHost, s));
   SD_CUDA(cudaStreamSynchronize(s));
   const double* h = mm->host_diag;
@@ -756,6 +812,36 @@ sd_status sd_diagnostics(const sd_mesh* m, const sd_phys* ph, const double* q, s
   if (h[9] > 0.0 || h[5] != h[5] || h[6] != h[6])
     return fail(SD_ERR_NONPHYSICAL, "non-physical state: rho <= 0, p <= 0 or NaN at " +
                                         std::to_string((long long)h[9]) + " solution points");
+  return SD_OK;
+}
+
+sd_status sd_profile_enable(sd_mesh* m, int32_t enable) {
+  if (!m) return fail(SD_ERR_INVALID_ARGUMENT, "mesh is NULL");
+  m->prof_on = enable ? 1 : 0;
+  m->prof_used = 0;
+  return SD_OK;
+}
+
+sd_status sd_profile_read(sd_mesh* m, sd_profile_stats* out) {
+  if (!m || !out) return fail(SD_ERR_INVALID_ARGUMENT, "null argument");
+  DeviceGuard g(m->device);
+  memset(out, 0, sizeof(*out));
+  for (size_t i = 0; i < m->prof_used; ++i) {
+    SD_CUDA(cudaEventSynchronize(m->prof_ev[2 * i + 1]));
+    float ms = 0.0f;
+    SD_CUDA(cudaEventElapsedTime(&ms, m->prof_ev[2 * i], m->prof_ev[2 * i + 1]));
+    if (m->prof_cls[i] == PROF_STAGE) {
+      out->stage_launches++;
+      out->stage_ms += ms;
+    } else if (m->prof_cls[i] == PROF_TRACE) {
+      out->trace_launches++;
+      out->trace_ms += ms;
+    } else {
+      out->other_launches++;
+      out->other_ms += ms;
+    }
+  }
+  m->prof_used = 0;
   return SD_OK;
 }
 

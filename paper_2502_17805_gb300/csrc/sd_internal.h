@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/sdmhd.h"
 
 namespace sd {
@@ -96,6 +98,11 @@ struct sd_mesh {
   int64_t device_bytes;
   sd::Ops<double> ops64;
   sd::Ops<float> ops32;
+  // kernel timing: event pairs (start, stop) with a kernel class
+  int prof_on;
+  std::vector<cudaEvent_t> prof_ev;
+  std::vector<int> prof_cls;
+  size_t prof_used;
 };
 
 struct sd_background {

@@ -28,7 +28,7 @@ STATUS = {0: "SD_OK", 1: "SD_ERR_INVALID_ARGUMENT", 2: "SD_ERR_UNSUPPORTED", 3: 
 # every symbol include/sdmhd.h declares
 EXPORTS = ["sd_last_error", "sd_mesh_create", "sd_mesh_destroy", "sd_mesh_query", "sd_state_init",
            "sd_background_create", "sd_background_destroy", "sd_residual", "sd_rk_stage", "sd_step",
-           "sd_diagnostics"]
+           "sd_diagnostics", "sd_profile_enable", "sd_profile_read"]
 
 
 class SDError(RuntimeError):
@@ -57,6 +57,11 @@ class InitC(C.Structure):
 class DiagC(C.Structure):
     _fields_ = [(k, C.c_double) for k in
                 ("ke", "eb", "max_divb", "mass", "energy", "lambda_max", "min_rho", "min_p", "volume")]
+
+
+class ProfileC(C.Structure):
+    _fields_ = [("stage_launches", C.c_int64), ("stage_ms", C.c_double), ("trace_launches", C.c_int64),
+                ("trace_ms", C.c_double), ("other_launches", C.c_int64), ("other_ms", C.c_double)]
 
 
 class MeshInfoC(C.Structure):
@@ -109,6 +114,8 @@ def lib():
         L.sd_rk_stage.argtypes = [vp, C.POINTER(PhysC), C.c_int, C.c_int32, C.c_double, vp, vp, vp, vp, vp]
         L.sd_step.argtypes = [vp, C.POINTER(PhysC), C.c_int, C.c_double, vp, vp, vp, vp, vp]
         L.sd_diagnostics.argtypes = [vp, C.POINTER(PhysC), vp, C.POINTER(DiagC), vp]
+        L.sd_profile_enable.argtypes = [vp, C.c_int32]
+        L.sd_profile_read.argtypes = [vp, C.POINTER(ProfileC)]
         for name in EXPORTS:
             getattr(L, name).restype = C.c_int if name != "sd_last_error" else C.c_char_p
         _lib = L
@@ -235,6 +242,15 @@ class Mesh:
         _check(lib().sd_step(self._h, C.byref(ph), int(prec), float(cfl), _ptr(q), _ptr(work),
                              bg._h if bg else None, _ptr(dt_out), _stream(stream)))
         return q
+
+    def profile(self, enable: bool = True):
+        """Start (or stop) CUDA-event timing of every kernel the library launches for this mesh."""
+        _check(lib().sd_profile_enable(self._h, 1 if enable else 0))
+
+    def profile_read(self) -> dict:
+        p = ProfileC()
+        _check(lib().sd_profile_read(self._h, C.byref(p)))
+        return {k: getattr(p, k) for k, _ in ProfileC._fields_}
 
     def diagnostics(self, phys: Phys, q, stream=None, check: bool = True) -> dict:
         d = DiagC()
