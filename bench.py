@@ -1,0 +1,398 @@
+#!/usr/bin/env python
+"""Benchmark of the SD-MHD hot path on one GB300 (or N independent replicas).
+
+Workload (default): the 6th-order cubed-sphere shell of 6 x 24^2 x 12 =
+41,472 hexahedra (8,957,952 solution points per variable), polytrope with
+N_rho = 3, GM = 1, Omega = 1, density noise 1e-4 (seed 0) and a dipole of
+1e-6 of the internal energy.  A step is one full SSP-RK3 step through
+sd_step: lambda_max -> dt, c_h on the device, then the three fused stages.
+
+Headline `value`: DOF-updates/s of the FP32-mixed path (whole job);
+`fp64` holds the same metric for the plain FP64 path.  Inputs are resident
+in HBM and larger than L2.  `e2e` repeats the mixed step through the C ABI
+with the state copied host->device before and device->host after every step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+import argparse
+import glob
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SD-MHD DOF-updates/s at 6th order (FP64 vs FP32-mixed); serve p50/p99 latency"
+UNIT = "DOF-updates/s"
+
+WORKLOADS = {
+    "shell41k": dict(nz=24, nr=12, N=6, Nrho=3.0,
+                     desc="cubed-sphere shell 6 x 24^2 x 12 = 41,472 hexahedra, N=6 (8,957,952 DOF), "
+                          "r in [0.70, 0.98], polytrope n=1.5 N_rho=3, GM=1, Omega=1, noise 1e-4 seed 0, "
+                          "dipole 1e-6 of internal energy"),
+    "shell221k": dict(nz=48, nr=16, N=6, Nrho=3.0,
+                      desc="cubed-sphere shell 6 x 48^2 x 16 = 221,184 hexahedra, N=6 (47,775,744 DOF), "
+                           "polytrope N_rho=3, same recipe"),
+    "shell12k": dict(nz=16, nr=8, N=6, Nrho=3.0,
+                     desc="cubed-sphere shell 6 x 16^2 x 8 = 12,288 hexahedra, N=6 (2,654,208 DOF), "
+                          "polytrope N_rho=3, same recipe (profiling size: state 191 MB > L2)"),
+    "shell1536": dict(nz=8, nr=4, N=6, Nrho=1.0,
+                      desc="cubed-sphere shell 6 x 8^2 x 4 = 1,536 hexahedra, N=6 (331,776 DOF), N_rho=1"),
+}
+CFL = 0.2
+GLM_ALPHA = 1.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="shell41k", choices=sorted(WORKLOADS))
+    ap.add_argument("--fp64-steps", type=int, default=4)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- helpers
+
+def dist_info():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(
+        os.environ.get("LOCAL_RANK", "0"))
+
+
+def algorithmic_bytes_per_dof_step(mixed: bool) -> int:
+    """State streams of one SSP-RK3 step: stage 0 reads q^n and writes q^1; stages 1 and 2 read q^n and
+    q^(s) and write q^(s+1): 8 passes of 9 FP64 values.  The mixed path also reads its FP32 background
+    record (rho0, p0, R0x, R0y, R0z) in each of the 3 stages."""
+    b = 8 * 9 * 8
+    if mixed:
+        b += 3 * 5 * 4
+    return b
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def source_hash() -> str:
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2502_17805_gb300", "csrc", "*"))):
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic(kernel_key: str):
+    """DRAM bytes per launch of a kernel from a committed ncu summary, if it was taken on these sources."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    cur = source_hash()
+    with open(path) as f:
+        for line in f:
+            parts = line.split()
+            if len(parts) >= 3 and parts[0] == kernel_key and parts[2] == cur:
+                return float(parts[1])
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.file = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.file:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.file.name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- our arm
+
+def make_case(wl, device_stream=None):
+    from paper_2502_17805_gb300 import inputs, sdmhd
+    v, h = inputs.shell_mesh(wl["nz"], wl["nr"])
+    mesh = sdmhd.Mesh(wl["N"], v, h, geom=1, r_in=0.70, r_out=0.98, bc_in=sdmhd.BC_WALL_CONDUCTING,
+                      bc_out=sdmhd.BC_WALL_RADIAL)
+    phys = sdmhd.Phys(gamma=5.0 / 3.0, GM=1.0, omega=1.0, glm_alpha=GLM_ALPHA, c_h=0.0, powell=1, gravity=1,
+                      coriolis=1)
+    params = [wl["Nrho"], 0.70, 0.98, 1.0, 1.0, 1e-4, 1e-6]
+    bgs = mesh.empty_state()
+    q0 = mesh.state_init(phys, sdmhd.INIT_SHELL_POLYTROPE, params, seed=0, background=bgs)
+    bg = mesh.background(phys, bgs)
+    del bgs
+    return mesh, phys, q0, bg, params
+
+
+def time_steps(mesh, phys, q, work, prec, bg, steps, warmup, sampler=None, barrier=None):
+    import torch
+    for _ in range(warmup):
+        mesh.step(phys, CFL, q, work, prec=prec, bg=bg)
+    torch.cuda.synchronize()
+    if barrier:
+        barrier()
+    mesh.profile(True)
+    if sampler:
+        sampler.start()
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(s)
+    for _ in range(steps):
+        mesh.step(phys, CFL, q, work, prec=prec, bg=bg)
+    e1.record(s)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    clocks = sampler.stop() if sampler else None
+    prof = mesh.profile_read()
+    mesh.profile(False)
+    if barrier:
+        barrier()
+    return ms, prof, clocks
+
+
+def time_e2e(mesh, phys, q_dev, work, bg, steps, warmup):
+    """Through the C ABI with host buffers: every step copies the state from pinned host memory to the
+    device, runs sd_step, and copies the new state (and dt, c_h) back."""
+    import torch
+
+    from paper_2502_17805_gb300 import sdmhd
+    host = torch.empty(q_dev.shape, dtype=torch.float64, pin_memory=True)
+    host.copy_(q_dev)
+    dts = torch.zeros(2, dtype=torch.float64, device="cuda")
+    dts_h = torch.zeros(2, dtype=torch.float64, pin_memory=True)
+    s = torch.cuda.current_stream()
+
+    def one():
+        q_dev.copy_(host, non_blocking=True)
+        mesh.step(phys, CFL, q_dev, work, prec=sdmhd.SD_FP32_MIXED, bg=bg, dt_out=dts)
+        host.copy_(q_dev, non_blocking=True)
+        dts_h.copy_(dts, non_blocking=True)
+
+    for _ in range(warmup):
+        one()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(steps):
+        one()
+    e1.record(s)
+    torch.cuda.synchronize()
+    nbytes = q_dev.numel() * 8
+    return e0.elapsed_time(e1), nbytes, nbytes + 16
+
+
+class OracleSample:
+    """The CPU oracle, as it stands, on a bounded sample of the workload: one step is the work of one
+    SSP-RK3 step (three residual evaluations) on `n_elems` random elements of the same shell, from the
+    workload's initial state.  Set-up (mesh, geometry, state) is not timed."""
+
+    def __init__(self, wl, n_elems: int, seed: int = 1):
+        import numpy as np
+
+        from oracle import sdref
+        from paper_2502_17805_gb300 import inputs
+        v, h = inputs.shell_mesh(wl["nz"], wl["nr"])
+        self.om = sdref.Mesh(wl["N"], v, h, geom=1, r_in=0.70, r_out=0.98, bc_in=sdref.BC_WALL_CONDUCTING,
+                             bc_out=sdref.BC_WALL_RADIAL)
+        self.ph = sdref.Phys(gamma=5.0 / 3.0, GM=1.0, omega=1.0, glm_alpha=GLM_ALPHA, c_h=1.0, powell=1,
+                             gravity=1, coriolis=1)
+        rng = np.random.default_rng(seed)
+        self.elems = np.sort(rng.choice(self.om.n_e, size=min(n_elems, self.om.n_e), replace=False))
+        self.q = self.om.state_init(self.ph, sdref.INIT_SHELL_POLYTROPE,
+                                    [wl["Nrho"], 0.70, 0.98, 1.0, 1.0, 1e-4, 1e-6], seed=0)
+        self.dof_per_step = self.elems.size * wl["N"] ** 3
+        self.threads = sdref.get_threads()
+
+    def run(self, steps: int):
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            for _stage in range(3):
+                self.om.residual_elements(self.ph, self.q, self.elems)
+        secs = time.perf_counter() - t0
+        return self.dof_per_step * steps / secs if steps else 0.0, secs
+
+
+def run_ours(args):
+    import torch
+
+    from paper_2502_17805_gb300 import build, sdmhd
+    rank, world, local = dist_info()
+    barrier = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        barrier = dist.barrier
+    else:
+        torch.cuda.set_device(0)
+    if rank == 0 or world == 1:
+        build.build()
+    if barrier:
+        barrier()
+    sdmhd.lib()
+    wl = WORKLOADS[args.workload]
+    mesh, phys, q0, bg, params = make_case(wl)
+    n_pts = mesh.info["n_points"]
+    q = q0.clone()
+    work = mesh.empty_state()
+    sampler = ClockSampler(local)
+
+    # headline: FP32-mixed path
+    ms, prof, clocks = time_steps(mesh, phys, q, work, sdmhd.SD_FP32_MIXED, bg, args.steps, args.warmup, sampler,
+                                  barrier)
+    # FP64 path, same workload and initial state
+    q64 = q0.clone()
+    k64 = max(1, min(args.steps, args.fp64_steps))
+    ms64, prof64, _ = time_steps(mesh, phys, q64, work, sdmhd.SD_FP64, None, k64, min(args.warmup, 3), None, barrier)
+
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms, ms64], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, ms64 = float(t[0]), float(t[1])
+
+    value = n_pts * args.steps * world / (ms / 1e3)
+    value64 = n_pts * k64 * world / (ms64 / 1e3)
+    peak, peak_kind = measured_peaks()
+    # dominant kernel: the fused element kernel (three launches per step)
+    stage_avg_ms = prof["stage_ms"] / max(prof["stage_launches"], 1)
+    bytes_per_launch = (algorithmic_bytes_per_dof_step(True) / 3.0) * n_pts
+    achieved = bytes_per_launch / (stage_avg_ms / 1e3) / 1e9
+    step_achieved = algorithmic_bytes_per_dof_step(True) * n_pts * args.steps / (ms / 1e3) / 1e9
+    stage64_ms = prof64["stage_ms"] / max(prof64["stage_launches"], 1)
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 (SD operators) + f64 (background, RK state, reductions)",
+        "data": "synthetic",
+        "config": {"workload": wl["desc"], "precision": "FP32-mixed", "cfl": CFL, "rk": "SSP-RK3 (Shu-Osher)",
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "l2": "inputs larger than L2 (one FP64 state is %.0f MB)" % (mesh.info["state_bytes"] / 1e6)},
+        "roofline": {"kernel": "stage_kernel<6, PolMixed>", "bound": "hbm", "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
+                     "traffic": committed_traffic("stage_mixed_N6"),
+                     "algorithmic_bytes_per_launch": bytes_per_launch,
+                     "avg_launch_ms": stage_avg_ms,
+                     "step_frac": step_achieved / peak},
+        "fp64": {"value": value64, "unit": UNIT, "steps": k64, "ms_per_step": ms64 / k64, "dtype": "f64",
+                 "stage_avg_ms": stage64_ms},
+        "gpu_launches": int(prof["stage_launches"] + prof["trace_launches"] + prof["other_launches"]),
+        "kernel_ms_per_step": {"stage": prof["stage_ms"] / args.steps, "trace_lambda": prof["trace_ms"] / args.steps,
+                               "control": prof["other_ms"] / args.steps},
+    }
+    if clocks:
+        out["clocks"] = clocks
+    if not args.no_e2e:
+        q2 = q0.clone()
+        ems, h2d, d2h = time_e2e(mesh, phys, q2, work, bg, max(1, min(args.steps, 10)), 1)
+        ke = max(1, min(args.steps, 10))
+        out["e2e"] = {"value": n_pts * ke * world / (ems / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                      "d2h_bytes_per_step": d2h, "ms_per_step": ems / ke}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        ors = OracleSample(wl, 2048)
+        ors.run(1)
+        rate, secs = ors.run(3)
+        out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": ors.threads, "kind": "oracle",
+                               "sample": "3 steps, each 3 residual evaluations on %d random elements of the same "
+                                         "shell (%.1f s)" % (ors.elems.size, secs)}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    """The CPU oracle as it stands, on the host cores: each step is the work of one SSP-RK3 step (three
+    residual evaluations) on a bounded random sample of the workload's elements."""
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return
+    from oracle import build as obuild
+    obuild.build()
+    wl = WORKLOADS[args.workload]
+    ors = OracleSample(wl, 512, seed=3)
+    ors.run(args.warmup)
+    rate, secs = ors.run(args.steps)
+    cores, nel = ors.threads, ors.elems.size
+    out = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": secs * 1e3 / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": wl["desc"], "precision": "FP64 oracle"},
+           "cpu_baseline": {"value": rate, "unit": UNIT, "kind": "oracle", "cores": cores,
+                            "sample": "per step: 3 residual evaluations on %d random elements of the shell" % nel},
+           "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

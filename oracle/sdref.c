@@ -860,10 +860,23 @@ int sdref_residual_elements(sdref_mesh* m, const sdref_phys* ph, const double* q
   free(need);
   if (rc) return rc;
   int64_t N3 = (int64_t)m->N * m->N * m->N;
-  double smax[9] = {0};
-  for (int64_t l = 0; l < n_list; ++l) residual_element(m, ph, q, elems[l], out + l * 9 * N3, NULL, smax);
+  int nth = sdref_get_threads();
+  double* sc = (double*)calloc(9 * (size_t)(nth > 0 ? nth : 1), sizeof(double));
+#pragma omp parallel for schedule(dynamic, 4) num_threads(nth)
+  for (int64_t l = 0; l < n_list; ++l) {
+    int tid = 0;
+#ifdef _OPENMP
+    tid = omp_get_thread_num();
+#endif
+    residual_element(m, ph, q, elems[l], out + l * 9 * N3, NULL, sc + 9 * tid);
+  }
   if (scale)
-    for (int v = 0; v < 9; ++v) scale[v] = smax[v];
+    for (int v = 0; v < 9; ++v) {
+      scale[v] = 0.0;
+      for (int t = 0; t < nth; ++t)
+        if (sc[9 * t + v] > scale[v]) scale[v] = sc[9 * t + v];
+    }
+  free(sc);
   return 0;
 }
 
