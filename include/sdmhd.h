@@ -203,7 +203,8 @@ sd_status sd_rk_stage(const sd_mesh* mesh, const sd_phys* phys, sd_precision pre
                       const double* q_n, const double* q_in, double* q_out, const sd_background* bg, void* stream);
 
 /* One full SSP-RK3 step with device-side step control: lambda_max of q (max of
- * |U| + fast speed over the solution points), dt = cfl * h_min / (N lambda_max),
+ * |U| + fast speed over the solution points), dt = cfl * dx_min / lambda_max with
+ * dx_min = h_min (X_s,2 - X_s,1) the smallest solution-point spacing,
  * c_h = lambda_max when phys->c_h <= 0 (else phys->c_h), then the three fused
  * stages.  q (in/out) and work: device states; dt_out: device double[2] or NULL,
  * receives (dt, c_h).  No host synchronisation.  Asynchronous. */

@@ -223,6 +223,7 @@ sd::StageParams base_params(const sd_mesh* m, const sd_phys* ph, int prec) {
   P.GM = ph->GM;
   P.omega = ph->omega;
   P.alpha = ph->glm_alpha;
+  P.inv_gm1 = 1.0 / (ph->gamma - 1.0);
   P.c_h = ph->c_h;
   P.powell = ph->powell;
   P.gravity = ph->gravity;
@@ -563,7 +564,7 @@ sd_status sd_background_create(const sd_mesh* m, const sd_phys* ph, const double
   if (err == cudaSuccess) err = cudaMalloc((void**)&bg->jump, ne * 6 * 2 * N2 * sizeof(float));
   if (err == cudaSuccess) err = cudaMalloc((void**)&q0, state * sizeof(double));
   if (err == cudaSuccess) err = cudaMalloc((void**)&R0, state * sizeof(double));
-  if (err == cudaSuccess) err = sd::launch_bg_prepare(m, ph->gamma, q_bg, q0, bg->rec, s);
+  if (err == cudaSuccess) err = sd::launch_bg_prepare(m, ph->gamma, 1.0 / (ph->gamma - 1.0), q_bg, q0, bg->rec, s);
   sd_mesh* mm = const_cast<sd_mesh*>(m);
   if (err == cudaSuccess) {
     sd::StageParams P = base_params(m, ph, SD_FP64);

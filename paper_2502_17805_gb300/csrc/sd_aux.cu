@@ -437,8 +437,8 @@ cudaError_t launch_diag(const sd_mesh* m, const sd_phys* ph, const double* q, cu
 // exactly; its FP64 residual R0 and its FP64 face jumps are stored in FP32.
 // ---------------------------------------------------------------------------
 
-__global__ void bg_prepare_kernel(int N, int64_t n_e, int64_t stride, double gamma, const double* __restrict__ qbg,
-                                  double* q0, float* rec) {
+__global__ void bg_prepare_kernel(int N, int64_t n_e, int64_t stride, double gamma, double inv_gm1,
+                                  const double* __restrict__ qbg, double* q0, float* rec) {
   const int N3 = N * N * N;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n_e * stride) return;
@@ -452,7 +452,7 @@ __global__ void bg_prepare_kernel(int N, int64_t n_e, int64_t stride, double gam
     rec[e * N3 + n] = r0;
     rec[n_e * N3 + e * N3 + n] = p0;
     Q[0] = (double)r0;
-    Q[4] = (double)p0 / (gamma - 1.0);
+    Q[4] = (double)p0 * inv_gm1;  // the definition of E0 every mixed kernel uses
   }
   for (int v = 0; v < 9; ++v) q0[v * plane + e * stride + n] = Q[v];
 }
@@ -487,11 +487,12 @@ __global__ void bg_finish_kernel(int N, int64_t n_e, int64_t stride, double gamm
   }
 }
 
-cudaError_t launch_bg_prepare(const sd_mesh* m, double gamma, const double* q_bg, double* q0, float* rec,
-                              cudaStream_t s) {
+cudaError_t launch_bg_prepare(const sd_mesh* m, double gamma, double inv_gm1, const double* q_bg, double* q0,
+                              float* rec, cudaStream_t s) {
   const int64_t tot = m->n_e * m->stride;
   if (tot == 0) return cudaSuccess;
-  bg_prepare_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(m->N, m->n_e, m->stride, gamma, q_bg, q0, rec);
+  bg_prepare_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(m->N, m->n_e, m->stride, gamma, inv_gm1, q_bg, q0,
+                                                                  rec);
   return cudaGetLastError();
 }
 
@@ -506,12 +507,14 @@ cudaError_t launch_bg_finish(const sd_mesh* m, double gamma, const double* R0, f
 }
 
 // ---------------------------------------------------------------------------
-// Step control: dt = cfl h_min / (N lambda_max), c_h = lambda_max unless fixed.
+// Step control: dt = cfl * (smallest solution-point spacing) / lambda_max, the
+// spacing being h_min times the first gap of the Chebyshev-Gauss points;
+// c_h = lambda_max unless fixed.
 // ---------------------------------------------------------------------------
 
-__global__ void step_control_kernel(double* dyn, double cfl, double hmin, int N, double ch_fixed, double* dt_out) {
+__global__ void step_control_kernel(double* dyn, double cfl, double dx_min, double ch_fixed, double* dt_out) {
   const double lam = __longlong_as_double((long long)(*reinterpret_cast<const unsigned long long*>(dyn + 2)));
-  const double dt = cfl * hmin / (N * lam);
+  const double dt = cfl * dx_min / lam;
   const double ch = ch_fixed > 0.0 ? ch_fixed : lam;
   dyn[0] = dt;
   dyn[1] = ch;
@@ -522,7 +525,8 @@ __global__ void step_control_kernel(double* dyn, double cfl, double hmin, int N,
 }
 
 cudaError_t launch_step_control(const sd_mesh* m, double cfl, double c_h_fixed, double* dt_out, cudaStream_t s) {
-  step_control_kernel<<<1, 1, 0, s>>>(m->dyn, cfl, m->h_min, m->N, c_h_fixed, dt_out);
+  const double dx_min = m->h_min * (m->ops64.xs[1] - m->ops64.xs[0]);
+  step_control_kernel<<<1, 1, 0, s>>>(m->dyn, cfl, dx_min, c_h_fixed, dt_out);
   return cudaGetLastError();
 }
 

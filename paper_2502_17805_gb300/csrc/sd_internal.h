@@ -51,6 +51,7 @@ struct StageParams {
   double dt, c_h;
   const double* dyn;  // device (dt, c_h) or nullptr
   double gamma, GM, omega, alpha;
+  double inv_gm1;  // 1/(gamma-1); the mixed background energy is E0 = p0 * inv_gm1
   int powell, gravity, coriolis, pad_;
   double farfield[9];
   const void* Sfam;   // [e][d][c][line][f]
@@ -121,8 +122,8 @@ cudaError_t launch_canonical_faces(sd_mesh* m, cudaStream_t s);
 cudaError_t launch_state_init(const sd_mesh* m, const sd_phys* ph, const sd_init* in, double B0dip, double* q,
                               double* qbg, cudaStream_t s);
 cudaError_t launch_diag(const sd_mesh* m, const sd_phys* ph, const double* q, cudaStream_t s);
-cudaError_t launch_bg_prepare(const sd_mesh* m, double gamma, const double* q_bg, double* q0, float* rec,
-                              cudaStream_t s);
+cudaError_t launch_bg_prepare(const sd_mesh* m, double gamma, double inv_gm1, const double* q_bg, double* q0,
+                              float* rec, cudaStream_t s);
 cudaError_t launch_bg_finish(const sd_mesh* m, double gamma, const double* R0, float* rec, float* jump,
                              const double* tr, cudaStream_t s);
 cudaError_t launch_step_control(const sd_mesh* m, double cfl, double c_h_fixed, double* dt_out, cudaStream_t s);

@@ -39,7 +39,7 @@ struct Smem {
   static constexpr int oD = oE + NF * N;      // [N][NF]
   static constexpr int nR = oD + N * NF;
   static constexpr size_t bytesR = ((nR * sizeof(R)) + 15) / 16 * 16;
-  static constexpr size_t bytes = bytesR + (Pol::mixed ? 9 * N3 * sizeof(double) : 0);
+  static constexpr size_t bytes = bytesR;
 };
 
 // index of solution point (i along d; a, b the other two directions in increasing order)
@@ -48,11 +48,14 @@ __device__ __forceinline__ int sol_index(int d, int i, int a, int b) {
   return d == 0 ? i + N * (a + N * b) : (d == 1 ? a + N * (i + N * b) : a + N * (b + N * i));
 }
 
-// Load one element's state into shared memory.  Mixed policy: q' = q - Q0 in
-// FP64, rounded to FP32, plus rho0 and p0; the FP64 state also goes to sQd.
+// Load one element's state into shared memory.  Mixed policy: q' = q - Q0 with
+// the subtraction in FP64 (rho0 and E0 = p0 / (gamma - 1) from the FP32
+// background record), rounded to FP32, plus rho0 and p0.  lam_out receives the
+// largest |U| + sqrt(gamma p / rho + |B|^2 / rho) of the points this thread loaded
+// (FP64 policy in FP64, mixed policy in FP32).
 template <int N, class Pol>
 __device__ __forceinline__ void load_element(const StageParams& P, const double* q, int64_t e,
-                                             typename Pol::R* sQ, double* sQd, double* lam_out) {
+                                             typename Pol::R* sQ, double* lam_out) {
   constexpr int N3 = N * N * N, BLK = Dims<N>::BLK;
   double lam = 0.0;
   for (int n = threadIdx.x; n < N3; n += BLK) {
@@ -60,28 +63,37 @@ __device__ __forceinline__ void load_element(const StageParams& P, const double*
     double qv[9];
 #pragma unroll
     for (int v = 0; v < 9; ++v) qv[v] = __ldg(q + v * P.plane + g);
-    if (lam_out) {
-      const double ir = 1.0 / qv[0];
-      const double m2 = qv[1] * qv[1] + qv[2] * qv[2] + qv[3] * qv[3];
-      const double B2 = qv[5] * qv[5] + qv[6] * qv[6] + qv[7] * qv[7];
-      const double p = (P.gamma - 1.0) * (qv[4] - 0.5 * (m2 * ir + B2 + qv[8] * qv[8]));
-      const double l = sqrt(m2) * ir + sqrt(P.gamma * p * ir + B2 * ir);
-      lam = (l > lam || l != l) ? l : lam;
-    }
     if constexpr (!Pol::mixed) {
+      if (lam_out) {
+        const double ir = 1.0 / qv[0];
+        const double m2 = qv[1] * qv[1] + qv[2] * qv[2] + qv[3] * qv[3];
+        const double B2 = qv[5] * qv[5] + qv[6] * qv[6] + qv[7] * qv[7];
+        const double p = (P.gamma - 1.0) * (qv[4] - 0.5 * (m2 * ir + B2 + qv[8] * qv[8]));
+        const double l = sqrt(m2) * ir + sqrt(P.gamma * p * ir + B2 * ir);
+        lam = (l > lam || l != l) ? l : lam;
+      }
 #pragma unroll
       for (int v = 0; v < 9; ++v) sQ[v * N3 + n] = qv[v];
     } else {
       const int64_t gb = e * N3 + n;
       const float r0 = __ldg(P.bg + gb), p0 = __ldg(P.bg + P.n_e * N3 + gb);
-      if (sQd) {
+      float qf[9];
 #pragma unroll
-        for (int v = 0; v < 9; ++v) sQd[v * N3 + n] = qv[v];
+      for (int v = 0; v < 9; ++v) qf[v] = f64_to_f32(qv[v]);
+      if (lam_out) {
+        const float ir = 1.0f / qf[0];
+        const float m2 = qf[1] * qf[1] + qf[2] * qf[2] + qf[3] * qf[3];
+        const float B2 = qf[5] * qf[5] + qf[6] * qf[6] + qf[7] * qf[7];
+        const float g = (float)P.gamma;
+        const float p = (g - 1.0f) * (qf[4] - 0.5f * (m2 * ir + B2 + qf[8] * qf[8]));
+        const float l = sqrtf(m2) * ir + sqrtf(g * p * ir + B2 * ir);
+        const double ld = (double)l;
+        lam = (ld > lam || l != l) ? ld : lam;
       }
 #pragma unroll
-      for (int v = 0; v < 9; ++v) sQ[v * N3 + n] = (float)qv[v];
-      sQ[0 * N3 + n] = (float)(qv[0] - (double)r0);
-      sQ[4 * N3 + n] = (float)(qv[4] - (double)p0 / (P.gamma - 1.0));
+      for (int v = 0; v < 9; ++v) sQ[v * N3 + n] = qf[v];
+      sQ[0 * N3 + n] = f64_to_f32(qv[0] - f32_to_f64(r0));
+      sQ[4 * N3 + n] = f64_to_f32(fma(-f32_to_f64(p0), P.inv_gm1, qv[4]));
       sQ[9 * N3 + n] = r0;
       sQ[10 * N3 + n] = p0;
     }
@@ -121,7 +133,7 @@ __global__ void __launch_bounds__(Dims<N>::BLK) trace_kernel(const StageParams P
   for (int i = threadIdx.x; i < NF * N; i += BLK) sE[i] = ops.E[i];
   const int64_t e = blockIdx.x;
   double lam = 0.0;
-  load_element<N, Pol>(P, P.q_in, e, sQ, nullptr, P.lam_max ? &lam : nullptr);
+  load_element<N, Pol>(P, P.q_in, e, sQ, P.lam_max ? &lam : nullptr);
   if (P.lam_max) {
     // max over the block, then one atomic; positive doubles order like their bit patterns
 #pragma unroll
@@ -216,7 +228,6 @@ __global__ void __launch_bounds__(Dims<N>::BLK) stage_kernel(const StageParams P
   R* sFace = reinterpret_cast<R*>(smem) + S::oFace;
   R* sE = reinterpret_cast<R*>(smem) + S::oE;
   R* sD = reinterpret_cast<R*>(smem) + S::oD;
-  double* sQd = Pol::mixed ? reinterpret_cast<double*>(smem + S::bytesR) : nullptr;
 
   const int tid = threadIdx.x;
   for (int i = tid; i < NF * N; i += BLK) {
@@ -234,7 +245,7 @@ __global__ void __launch_bounds__(Dims<N>::BLK) stage_kernel(const StageParams P
   }
   const R ch = R(chd);
 
-  load_element<N, Pol>(P, P.q_in, e, sQ, sQd, nullptr);
+  load_element<N, Pol>(P, P.q_in, e, sQ, nullptr);
   __syncthreads();
 
   // ---- element faces: common flux and BR1 normal field
@@ -345,69 +356,81 @@ __global__ void __launch_bounds__(Dims<N>::BLK) stage_kernel(const StageParams P
   }
 
   // ---- epilogue: residual, sources, RK combination
-  double qout[9];
+  // FP64 policy: q_out = a q_n + b (q_in + dt R) in FP64.
+  // Mixed policy: the same combination written as an increment of q_in,
+  //   q_out = q_in + t,  t = a (q_n - q_in) + b dt R  (a + b = 1 for every stage),
+  // with q_n - q_in formed in FP64, t in FP32 and the sum in FP64: the RK state
+  // accumulates in FP64 while the FP64 pipe sees two additions per value.
+  // The next stage's FP32 traces come from q' + t.
   if (n < N3) {
     const R iJ = reinterpret_cast<const R*>(P.invJ)[e * N3 + n];
     const R* Xe = reinterpret_cast<const R*>(P.X) + e * 3 * N3;
     const R divB = acc[9] * iJ;
-    double Rv[9];
-    double qin[9];
+    const int64_t g = e * P.stride + n;
     if constexpr (!Pol::mixed) {
-      double q[9], M[9];
+      double q[9], M[9], Rv[9];
 #pragma unroll
       for (int v = 0; v < 9; ++v) q[v] = sQ[v * N3 + n];
       sources_fp64(P, q, divB, Xe[n], Xe[N3 + n], Xe[2 * N3 + n], M);
 #pragma unroll
-      for (int v = 0; v < 9; ++v) {
-        Rv[v] = -acc[v] * iJ + M[v];
-        qin[v] = q[v];
+      for (int v = 0; v < 9; ++v) Rv[v] = -acc[v] * iJ + M[v];
+      if (P.mode == MODE_RESIDUAL) {
+#pragma unroll
+        for (int v = 0; v < 9; ++v) P.out[v * P.plane + g] = Rv[v];
+      } else if (P.mode == MODE_DIVB) {
+        P.divb[e * N3 + n] = divB;
+      } else {
+        double qout[9];
+        if (P.rk_a != 0.0) {
+#pragma unroll
+          for (int v = 0; v < 9; ++v)
+            qout[v] = P.rk_a * __ldg(P.q_n + v * P.plane + g) + P.rk_b * (q[v] + dt * Rv[v]);
+        } else {
+#pragma unroll
+          for (int v = 0; v < 9; ++v) qout[v] = P.rk_b * (q[v] + dt * Rv[v]);
+        }
+#pragma unroll
+        for (int v = 0; v < 9; ++v) P.out[v * P.plane + g] = qout[v];
+        if (P.tr_out) {
+#pragma unroll
+          for (int v = 0; v < 9; ++v) acc[v] = qout[v];  // kept for the traces below
+        }
       }
     } else {
-      float q[11], M[9];
+      float q[11], M[9], Rv[9];
 #pragma unroll
       for (int v = 0; v < 11; ++v) q[v] = sQ[v * N3 + n];
       sources_mixed(P, q, divB, Xe[n], Xe[N3 + n], Xe[2 * N3 + n], M);
 #pragma unroll
-      for (int v = 0; v < 9; ++v) {
-        Rv[v] = (double)(-acc[v] * iJ + M[v]);
-        qin[v] = sQd[v * N3 + n];
-      }
+      for (int v = 0; v < 9; ++v) Rv[v] = -acc[v] * iJ + M[v];
       const int64_t gb = e * N3 + n, bp = P.n_e * N3;
-      Rv[1] += (double)__ldg(P.bg + 2 * bp + gb);
-      Rv[2] += (double)__ldg(P.bg + 3 * bp + gb);
-      Rv[3] += (double)__ldg(P.bg + 4 * bp + gb);
-    }
-    const int64_t g = e * P.stride + n;
-    if (P.mode == MODE_RESIDUAL) {
+      Rv[1] += __ldg(P.bg + 2 * bp + gb);
+      Rv[2] += __ldg(P.bg + 3 * bp + gb);
+      Rv[3] += __ldg(P.bg + 4 * bp + gb);
+      if (P.mode == MODE_RESIDUAL) {
 #pragma unroll
-      for (int v = 0; v < 9; ++v) P.out[v * P.plane + g] = Rv[v];
-    } else if (P.mode == MODE_DIVB) {
-      P.divb[e * N3 + n] = (double)divB;
-    } else {
-      if (P.rk_a != 0.0) {
-#pragma unroll
-        for (int v = 0; v < 9; ++v)
-          qout[v] = P.rk_a * __ldg(P.q_n + v * P.plane + g) + P.rk_b * (qin[v] + dt * Rv[v]);
+        for (int v = 0; v < 9; ++v) P.out[v * P.plane + g] = f32_to_f64(Rv[v]);
+      } else if (P.mode == MODE_DIVB) {
+        P.divb[e * N3 + n] = f32_to_f64(divB);
       } else {
+        const float bdt = (float)(P.rk_b * dt);
+        const float a = (float)P.rk_a;
 #pragma unroll
-        for (int v = 0; v < 9; ++v) qout[v] = P.rk_b * (qin[v] + dt * Rv[v]);
+        for (int v = 0; v < 9; ++v) {
+          const double qin = __ldg(P.q_in + v * P.plane + g);
+          float t = bdt * Rv[v];
+          if (P.rk_a != 0.0) t = fmaf(a, f64_to_f32(__ldg(P.q_n + v * P.plane + g) - qin), t);
+          P.out[v * P.plane + g] = qin + f32_to_f64(t);
+          acc[v] = q[v] + t;  // q' of the new state, for the traces below
+        }
       }
-#pragma unroll
-      for (int v = 0; v < 9; ++v) P.out[v * P.plane + g] = qout[v];
     }
   }
   if (P.mode == MODE_RK && P.tr_out) {
     __syncthreads();
     if (n < N3) {
-      if constexpr (!Pol::mixed) {
 #pragma unroll
-        for (int v = 0; v < 9; ++v) sQ[v * N3 + n] = qout[v];
-      } else {
-#pragma unroll
-        for (int v = 0; v < 9; ++v) sQ[v * N3 + n] = (float)qout[v];
-        sQ[0 * N3 + n] = (float)(qout[0] - (double)sQ[9 * N3 + n]);
-        sQ[4 * N3 + n] = (float)(qout[4] - (double)sQ[10 * N3 + n] / (P.gamma - 1.0));
-      }
+      for (int v = 0; v < 9; ++v) sQ[v * N3 + n] = acc[v];
     }
     __syncthreads();
     write_traces<N, Pol>(sQ, sE, reinterpret_cast<R*>(P.tr_out), e);

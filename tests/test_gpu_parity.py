@@ -135,19 +135,22 @@ def test_alfven_box_twenty_steps_fp64():
     q0 = om.state_init(oph, sdref.INIT_ALFVEN, ALFVEN)
     q, work = gm.to_device(q0), gm.empty_state()
     dts = torch.zeros(2, dtype=torch.float64, device="cuda")
-    hmin = om.info()["h_min"]
+    xs = sdref.nodes(N)[0]
+    dx_min = om.info()["h_min"] * (xs[1] - xs[0])
     qo = q0
     dt_err = 0.0
     for _ in range(20):
         gm.step(gph, cfl, q, work, dt_out=dts)
         lam = om.diagnostics(oph, qo)["lambda_max"]
         oph.c_h = lam
-        qo = om.rk_step(oph, cfl * hmin / (N * lam), qo)
-        dt_err = max(dt_err, abs(dts.cpu().numpy()[0] / (cfl * hmin / (N * lam)) - 1.0))
-    err = np.abs(gm.to_host(q) - qo).max(axis=(1, 2)) / np.abs(qo).max(axis=(1, 2))
-    # rounding differences grow over the trajectory (and feed back through dt and c_h)
+        qo = om.rk_step(oph, cfl * dx_min / lam, qo)
+        dt_err = max(dt_err, abs(dts.cpu().numpy()[0] / (cfl * dx_min / lam) - 1.0))
+    # psi stays at the rounding-driven level of the discrete div B (~1e-6): measure it against |B|
+    scale = np.abs(qo).max(axis=(1, 2))
+    scale[8] = np.abs(qo[5:8]).max()
+    err = np.abs(gm.to_host(q) - qo).max(axis=(1, 2)) / scale
     print("dt rel err %.2e, state rel err %s" % (dt_err, err))
-    assert dt_err < 1e-10 and err.max() < 1e-10, (dt_err, err)
+    assert dt_err < 1e-12 and err.max() < 1e-11, (dt_err, err)
 
 
 def test_state_init_parity():
