@@ -217,6 +217,24 @@ sd_status sd_step(const sd_mesh* mesh, const sd_phys* phys, sd_precision prec, d
  * (with *out filled) when rho <= 0, p <= 0 or a NaN is found. */
 sd_status sd_diagnostics(const sd_mesh* mesh, const sd_phys* phys, const double* q, sd_diag* out, void* stream);
 
+/* sd_residual_noalloc -- the FP64 residual of sd_residual (same result within
+ * FP64 round-off; the same kernels run) without any memory allocation.  The
+ * paper has no counterpart: this call exists for callers that cannot call
+ * cudaMalloc when they need a residual, for example an application whose memory
+ * pool already holds all the device memory it may use, or a latency-bound loop
+ * that must not risk the device-wide synchronisation an allocation can cause.
+ * Its scratch (the face traces of q) is a fixed 8 MiB device array inside the
+ * library, held on every GPU that loads the library until the process exits;
+ * meshes whose traces need more (n_elements * 6 * 9 * N^2 * 8 bytes > 8 MiB, e.g.
+ * more than 539 elements at N = 6) are rejected with SD_ERR_INVALID_ARGUMENT and
+ * a message.  The first call on each device looks up the array's device address
+ * with that device current; make that first call before any stream capture.
+ * All calls share the one array, which keeps the last call's contents (every
+ * entry a call reads is written earlier in the same call), so calls whose work
+ * overlaps on the GPU (other streams, other threads) race.  q and dqdt: device
+ * states; the mesh must belong to the current device.  Asynchronous. */
+sd_status sd_residual_noalloc(const sd_mesh* mesh, const sd_phys* phys, const double* q, double* dqdt, void* stream);
+
 /* Kernel timing (tracing): with enable = 1 every kernel the library launches
  * for this mesh is bracketed by CUDA events on its launching stream; the
  * counters restart.  At most 65536 launches are recorded.  enable = 0 stops

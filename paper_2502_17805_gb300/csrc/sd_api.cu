@@ -294,6 +294,11 @@ double polytrope_p(double r, double Nr, double rb, double rt, double rhob, doubl
 
 }  // namespace
 
+namespace sd {
+// message for sd_last_error() from entry points defined in other translation units
+void set_last_error(const std::string& msg) { g_err = msg; }
+}  // namespace sd
+
 extern "C" {
 
 const char* sd_last_error(void) { return g_err.c_str(); }

@@ -28,7 +28,7 @@ STATUS = {0: "SD_OK", 1: "SD_ERR_INVALID_ARGUMENT", 2: "SD_ERR_UNSUPPORTED", 3: 
 # every symbol include/sdmhd.h declares
 EXPORTS = ["sd_last_error", "sd_mesh_create", "sd_mesh_destroy", "sd_mesh_query", "sd_state_init",
            "sd_background_create", "sd_background_destroy", "sd_residual", "sd_rk_stage", "sd_step",
-           "sd_diagnostics", "sd_profile_enable", "sd_profile_read"]
+           "sd_diagnostics", "sd_profile_enable", "sd_profile_read", "sd_residual_noalloc"]
 
 
 class SDError(RuntimeError):
@@ -116,6 +116,7 @@ def lib():
         L.sd_diagnostics.argtypes = [vp, C.POINTER(PhysC), vp, C.POINTER(DiagC), vp]
         L.sd_profile_enable.argtypes = [vp, C.c_int32]
         L.sd_profile_read.argtypes = [vp, C.POINTER(ProfileC)]
+        L.sd_residual_noalloc.argtypes = [vp, C.POINTER(PhysC), vp, vp, vp]
         for name in EXPORTS:
             getattr(L, name).restype = C.c_int if name != "sd_last_error" else C.c_char_p
         _lib = L
@@ -219,6 +220,12 @@ class Mesh:
         ph = phys.c()
         _check(lib().sd_residual(self._h, C.byref(ph), int(prec), _ptr(q), bg._h if bg else None, _ptr(dqdt),
                                  _stream(stream)))
+        return dqdt
+
+    def residual_noalloc(self, phys: Phys, q, dqdt, stream=None):
+        """FP64 residual through sd_residual_noalloc: no allocation; scratch in the library's fixed array."""
+        ph = phys.c()
+        _check(lib().sd_residual_noalloc(self._h, C.byref(ph), _ptr(q), _ptr(dqdt), _stream(stream)))
         return dqdt
 
     def rk_stage(self, phys: Phys, stage: int, dt: float, q_n, q_in, q_out, prec: int = SD_FP64,
