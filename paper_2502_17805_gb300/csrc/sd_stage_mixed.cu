@@ -1,17 +1,25 @@
-// Instantiations of the fused element kernels for the FP32-mixed policy, N = 2..8.
+// Instantiations of the fused element kernels for the FP32-mixed policy, N = 2..8:
+// the line-blocked stage kernel (sd_stage_v2.cuh) and the trace kernel.
 #include "sd_stage.cuh"
+#include "sd_stage_v2.cuh"
 
 namespace sd {
 
+template <int N>
+static cudaError_t launch_mixed_n(const sd_mesh* m, const StageParams& P, bool traces_only, cudaStream_t s) {
+  if (traces_only) return launch_stage_t<N, PolMixed>(P, m->ops32, true, s);
+  return launch_stage_v2_t<N>(P, m->ops32, s);
+}
+
 cudaError_t launch_stage_mixed(const sd_mesh* m, const StageParams& P, bool traces_only, cudaStream_t s) {
   switch (m->N) {
-    case 2: return launch_stage_t<2, PolMixed>(P, m->ops32, traces_only, s);
-    case 3: return launch_stage_t<3, PolMixed>(P, m->ops32, traces_only, s);
-    case 4: return launch_stage_t<4, PolMixed>(P, m->ops32, traces_only, s);
-    case 5: return launch_stage_t<5, PolMixed>(P, m->ops32, traces_only, s);
-    case 6: return launch_stage_t<6, PolMixed>(P, m->ops32, traces_only, s);
-    case 7: return launch_stage_t<7, PolMixed>(P, m->ops32, traces_only, s);
-    case 8: return launch_stage_t<8, PolMixed>(P, m->ops32, traces_only, s);
+    case 2: return launch_mixed_n<2>(m, P, traces_only, s);
+    case 3: return launch_mixed_n<3>(m, P, traces_only, s);
+    case 4: return launch_mixed_n<4>(m, P, traces_only, s);
+    case 5: return launch_mixed_n<5>(m, P, traces_only, s);
+    case 6: return launch_mixed_n<6>(m, P, traces_only, s);
+    case 7: return launch_mixed_n<7>(m, P, traces_only, s);
+    case 8: return launch_mixed_n<8>(m, P, traces_only, s);
     default: return cudaErrorInvalidValue;
   }
 }

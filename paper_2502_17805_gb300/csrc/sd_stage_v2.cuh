@@ -1,0 +1,294 @@
+// sd_stage_v2.cuh -- FP32-mixed fused SD residual + SSP-RK stage, line-blocked.
+//
+// Same arithmetic as stage_kernel<N, PolMixed> (sd_stage.cuh), organised so that
+// the 1D operators run from registers.  Per element (one CTA):
+//   A  load     q' (FP32 perturbation), rho0, p0 at the N^3 points -> sQ
+//   B  lines    one thread per line of each direction (3 N^2 threads) keeps the
+//               line's 11 values in registers and writes their extrapolation to
+//               all N+1 flux points of its family -> sX
+//   C  points   interior flux points: contravariant flux; face points: Rusanov
+//               and BR1 against the neighbour trace; results overwrite sX in place
+//   D  lines    each line thread loads its 10 x (N+1) fluxes, then writes the N
+//               derivative values of its line -> sDiv (aliases sX)
+//   E  points   R = -sum_d div_d / |J| + M + R0, FP64 RK sum, q' of the new state -> sQ
+//   F  lines    face traces of the new state (the two ends of every line).
+// Thread count T = max(128, 3 N^2 rounded to a warp).
+#pragma once
+
+#include "sd_internal.h"
+#include "sd_physics.cuh"
+
+namespace sd {
+
+template <int N>
+struct DimsV2 {
+  static constexpr int N2 = N * N, N3 = N2 * N, NF = N + 1, NV = 11;
+  static constexpr int NLINE = 3 * N2;
+  static constexpr int T0 = ((NLINE + 31) / 32) * 32;
+  static constexpr int T = T0 < 128 ? 128 : T0;
+  // shared memory in floats
+  static constexpr int oQ = 0;                       // [11][N3]
+  static constexpr int oX = oQ + NV * N3;            // [3][NF][11][N2]; later sDiv [3][10][N3]
+  static constexpr int nX = 3 * NF * NV * N2;
+  static constexpr int oE = oX + nX;                 // [NF][N]
+  static constexpr int oD = oE + NF * N;             // [N][NF]
+  static constexpr int nF = oD + N * NF;
+  static constexpr size_t bytes = ((nF * 4) + 15) / 16 * 16;
+  static_assert(30 * N3 <= nX, "derivative buffer must fit in the extrapolation buffer");
+};
+
+// solution-point index of position i along the line (d, L): base + i * stride
+template <int N>
+__device__ __forceinline__ void line_geom(int d, int L, int& base, int& stride) {
+  const int a = L % N, b = L / N;
+  if (d == 0) {
+    base = N * L;
+    stride = 1;
+  } else if (d == 1) {
+    base = a + N * N * b;
+    stride = N;
+  } else {
+    base = L;
+    stride = N * N;
+  }
+}
+
+template <int N>
+__global__ void __launch_bounds__(DimsV2<N>::T) stage_kernel_v2(const StageParams P, const Ops<float> ops) {
+  using DV = DimsV2<N>;
+  constexpr int N2 = DV::N2, N3 = DV::N3, NF = DV::NF, T = DV::T, NL = DV::NLINE;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* smem = reinterpret_cast<float*>(smem_raw);
+  float* sQ = smem + DV::oQ;
+  float* sX = smem + DV::oX;
+  float* sDiv = sX;
+  float* sE = smem + DV::oE;
+  float* sD = smem + DV::oD;
+
+  const int tid = threadIdx.x;
+  for (int i = tid; i < NF * N; i += T) {
+    sE[i] = ops.E[i];
+    sD[i] = ops.D[i];
+  }
+  const int64_t e = blockIdx.x;
+  const float* Sfam = reinterpret_cast<const float*>(P.Sfam) + e * (9 * N2 * NF);
+  const float gamma = (float)P.gamma;
+  const float gm1 = gamma - 1.0f;
+  const float gg1 = gamma / gm1;
+  double dt = P.dt, chd = P.c_h;
+  if (P.dyn) {
+    dt = P.dyn[0];
+    chd = P.dyn[1];
+  }
+  const float ch = (float)chd;
+
+  // line role of this thread (B, D, F)
+  const bool is_line = tid < NL;
+  const int ld = is_line ? tid / N2 : 0;
+  const int lL = is_line ? tid % N2 : 0;
+  int lbase = 0, lstride = 1;
+  line_geom<N>(ld, lL, lbase, lstride);
+
+  // ---- A: load
+  for (int n = tid; n < N3; n += T) {
+    const int64_t g = e * P.stride + n;
+    const int64_t gb = e * N3 + n;
+    const float r0 = __ldg(P.bg + gb), p0 = __ldg(P.bg + P.n_e * N3 + gb);
+    double qv[9];
+#pragma unroll
+    for (int v = 0; v < 9; ++v) qv[v] = __ldg(P.q_in + v * P.plane + g);
+    sQ[0 * N3 + n] = f64_to_f32(qv[0] - f32_to_f64(r0));
+#pragma unroll
+    for (int v = 1; v < 9; ++v) sQ[v * N3 + n] = f64_to_f32(qv[v]);
+    sQ[4 * N3 + n] = f64_to_f32(fma(-f32_to_f64(p0), P.inv_gm1, qv[4]));
+    sQ[9 * N3 + n] = r0;
+    sQ[10 * N3 + n] = p0;
+  }
+  __syncthreads();
+
+  // ---- B: extrapolate every line to its N+1 flux points
+  if (is_line) {
+    float ql[11][N];
+#pragma unroll
+    for (int v = 0; v < 11; ++v)
+#pragma unroll
+      for (int i = 0; i < N; ++i) ql[v][i] = sQ[v * N3 + lbase + i * lstride];
+    float* X = sX + (ld * NF * 11) * N2 + lL;
+#pragma unroll
+    for (int f = 0; f <= N; ++f) {
+#pragma unroll
+      for (int v = 0; v < 11; ++v) {
+        float s = 0.0f;
+#pragma unroll
+        for (int i = 0; i < N; ++i) s = fmaf(sE[f * N + i], ql[v][i], s);
+        X[(f * 11 + v) * N2] = s;
+      }
+    }
+  }
+  __syncthreads();
+
+  // ---- C: fluxes at the flux points (interior first, then the element faces)
+  constexpr int NINT = 3 * (N - 1) * N2;
+  for (int t = tid; t < NINT + 6 * N2; t += T) {
+    if (t < NINT) {
+      const int d = t / ((N - 1) * N2), r = t - d * ((N - 1) * N2);
+      const int f = 1 + r / N2, L = r - (f - 1) * N2;
+      float* X = sX + ((d * NF + f) * 11) * N2 + L;
+      float qf[11];
+#pragma unroll
+      for (int v = 0; v < 11; ++v) qf[v] = X[v * N2];
+      const float* Sp = Sfam + (d * 3 * N2 + L) * NF + f;
+      const float Sx = __ldg(Sp), Sy = __ldg(Sp + N2 * NF), Sz = __ldg(Sp + 2 * N2 * NF);
+      float Fv[9];
+      flux_pert(qf, Sx, Sy, Sz, gm1, gg1, ch, Fv);
+#pragma unroll
+      for (int v = 0; v < 9; ++v) X[v * N2] = Fv[v];
+      X[9 * N2] = Sx * qf[5] + Sy * qf[6] + Sz * qf[7];
+    } else {
+      const int u = t - NINT;
+      const int F = u / N2, pt = u - F * N2, a = pt % N, b = pt / N;
+      const int d = F >> 1, side = F & 1, f = side ? N : 0;
+      float* X = sX + ((d * NF + f) * 11) * N2 + pt;
+      float qo[11];
+#pragma unroll
+      for (int v = 0; v < 11; ++v) qo[v] = X[v * N2];
+      const float* Sp = Sfam + (d * 3 * N2 + pt) * NF + f;
+      const float Sx = __ldg(Sp), Sy = __ldg(Sp + N2 * NF), Sz = __ldg(Sp + 2 * N2 * NF);
+      const float mag = sqrtf(Sx * Sx + Sy * Sy + Sz * Sz);
+      const float im = 1.0f / mag;
+      const float sg = side ? 1.0f : -1.0f;
+      const float nx = sg * Sx * im, ny = sg * Sy * im, nz = sg * Sz * im;
+      const int64_t gidx = e * 6 + F;
+      const int nb = __ldg(P.nbr + gidx);
+      const int mt = __ldg(P.meta + gidx);
+      float qn[9];
+      float jr = 0.0f, jp = 0.0f;
+      if (nb >= 0) {
+        const int code = meta_code(mt);
+        const int uu = (code & 4) ? b : a, w = (code & 4) ? a : b;
+        const int a2 = (code & 2) ? N - 1 - uu : uu, b2 = (code & 1) ? N - 1 - w : w;
+        const float* Tn = reinterpret_cast<const float*>(P.tr_in) + ((int64_t)nb * 6 + meta_nbF(mt)) * 9 * N2 + a2 + N * b2;
+#pragma unroll
+        for (int v = 0; v < 9; ++v) qn[v] = Tn[v * N2];
+        jr = __ldg(P.bg_jump + (gidx * 2 + 0) * N2 + pt);
+        jp = __ldg(P.bg_jump + (gidx * 2 + 1) * N2 + pt);
+      } else {
+        const int bc = meta_bc(mt);
+        if (bc == SD_BC_FARFIELD) {
+#pragma unroll
+          for (int v = 0; v < 9; ++v) qn[v] = (float)P.farfield[v];
+          qn[0] -= qo[9];
+          qn[4] -= qo[10] / gm1;
+        } else {
+          wall_ghost<float>(qo, nx, ny, nz, bc, qn);
+        }
+      }
+      float Fs[9];
+      riemann_mixed(qo, qn, nx, ny, nz, gamma, ch, jr, jp, Fs);
+      const float Bn = 0.5f * ((qo[5] + qn[5]) * nx + (qo[6] + qn[6]) * ny + (qo[7] + qn[7]) * nz);
+      const float sm = sg * mag;
+#pragma unroll
+      for (int v = 0; v < 9; ++v) X[v * N2] = sm * Fs[v];
+      X[9 * N2] = sm * Bn;
+    }
+  }
+  __syncthreads();
+
+  // ---- D: derivative of the flux polynomial along every line
+  float fl[10][NF];
+  if (is_line) {
+    const float* X = sX + (ld * NF * 11) * N2 + lL;
+#pragma unroll
+    for (int f = 0; f <= N; ++f)
+#pragma unroll
+      for (int v = 0; v < 10; ++v) fl[v][f] = X[(f * 11 + v) * N2];
+  }
+  __syncthreads();
+  if (is_line) {
+    float* Dv = sDiv + (ld * 10) * N3 + lbase;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+#pragma unroll
+      for (int v = 0; v < 10; ++v) {
+        float s = 0.0f;
+#pragma unroll
+        for (int f = 0; f <= N; ++f) s = fmaf(sD[i * NF + f], fl[v][f], s);
+        Dv[v * N3 + i * lstride] = s;
+      }
+    }
+  }
+  __syncthreads();
+
+  // ---- E: residual, sources, RK sum (see stage_kernel<N, PolMixed> for the increment form)
+  for (int n = tid; n < N3; n += T) {
+    float acc[10];
+#pragma unroll
+    for (int v = 0; v < 10; ++v) acc[v] = sDiv[v * N3 + n] + sDiv[(10 + v) * N3 + n] + sDiv[(20 + v) * N3 + n];
+    const float iJ = __ldg(reinterpret_cast<const float*>(P.invJ) + e * N3 + n);
+    const float* Xe = reinterpret_cast<const float*>(P.X) + e * 3 * N3;
+    const float divB = acc[9] * iJ;
+    float q[11], M[9], Rv[9];
+#pragma unroll
+    for (int v = 0; v < 11; ++v) q[v] = sQ[v * N3 + n];
+    sources_mixed(P, q, divB, __ldg(Xe + n), __ldg(Xe + N3 + n), __ldg(Xe + 2 * N3 + n), M);
+#pragma unroll
+    for (int v = 0; v < 9; ++v) Rv[v] = -acc[v] * iJ + M[v];
+    const int64_t gb = e * N3 + n, bp = P.n_e * N3;
+    Rv[1] += __ldg(P.bg + 2 * bp + gb);
+    Rv[2] += __ldg(P.bg + 3 * bp + gb);
+    Rv[3] += __ldg(P.bg + 4 * bp + gb);
+    const int64_t g = e * P.stride + n;
+    if (P.mode == MODE_RESIDUAL) {
+#pragma unroll
+      for (int v = 0; v < 9; ++v) P.out[v * P.plane + g] = f32_to_f64(Rv[v]);
+    } else if (P.mode == MODE_DIVB) {
+      P.divb[e * N3 + n] = f32_to_f64(divB);
+    } else {
+      const float bdt = (float)(P.rk_b * dt);
+      const float a = (float)P.rk_a;
+#pragma unroll
+      for (int v = 0; v < 9; ++v) {
+        const double qin = __ldg(P.q_in + v * P.plane + g);
+        float t = bdt * Rv[v];
+        if (P.rk_a != 0.0) t = fmaf(a, f64_to_f32(__ldg(P.q_n + v * P.plane + g) - qin), t);
+        P.out[v * P.plane + g] = qin + f32_to_f64(t);
+        sQ[v * N3 + n] = q[v] + t;  // q' of the new state (this thread's own point)
+      }
+    }
+  }
+
+  // ---- F: face traces of the new state
+  if (P.mode == MODE_RK && P.tr_out) {
+    __syncthreads();
+    if (is_line) {
+      float* Tr = reinterpret_cast<float*>(P.tr_out) + (e * 6 + 2 * ld) * 9 * N2 + lL;
+#pragma unroll
+      for (int v = 0; v < 9; ++v) {
+        float s0 = 0.0f, s1 = 0.0f;
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+          const float x = sQ[v * N3 + lbase + i * lstride];
+          s0 = fmaf(sE[i], x, s0);
+          s1 = fmaf(sE[N * N + i], x, s1);
+        }
+        Tr[v * N2] = s0;
+        Tr[9 * N2 + v * N2] = s1;
+      }
+    }
+  }
+}
+
+template <int N>
+cudaError_t launch_stage_v2_t(const StageParams& P, const Ops<float>& ops, cudaStream_t s) {
+  using DV = DimsV2<N>;
+  if (DV::bytes > 48 * 1024) {
+    cudaError_t err = cudaFuncSetAttribute(stage_kernel_v2<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)DV::bytes);
+    if (err != cudaSuccess) return err;
+  }
+  if (P.n_e == 0) return cudaSuccess;
+  stage_kernel_v2<N><<<(unsigned)P.n_e, DV::T, DV::bytes, s>>>(P, ops);
+  return cudaGetLastError();
+}
+
+}  // namespace sd
