@@ -3,13 +3,13 @@
 // Same arithmetic as stage_kernel<N, PolMixed> (sd_stage.cuh), organised so that
 // the 1D operators run from registers.  Per element (one CTA):
 //   A  load     q' (FP32 perturbation), rho0, p0 at the N^3 points -> sQ
-//   B  lines    one thread per line of each direction (3 N^2 threads) keeps the
-//               line's 11 values in registers and writes their extrapolation to
-//               all N+1 flux points of its family -> sX
+//   B  lines    one thread per line of each direction (3 N^2 threads) takes the
+//               line's values of one variable at a time into registers and writes
+//               their extrapolation to all N+1 flux points of its family -> sX
 //   C  points   interior flux points: contravariant flux; face points: Rusanov
 //               and BR1 against the neighbour trace; results overwrite sX in place
-//   D  lines    each line thread loads its 10 x (N+1) fluxes, then writes the N
-//               derivative values of its line -> sDiv (aliases sX)
+//   D  lines    each line thread differentiates its 10 x (N+1) fluxes and writes
+//               the N derivative values over its own flux slots in sX
 //   E  points   R = -sum_d div_d / |J| + M + R0, FP64 RK sum, q' of the new state -> sQ
 //   F  lines    face traces of the new state (the two ends of every line).
 // Thread count T = max(128, 3 N^2 rounded to a warp).
@@ -28,13 +28,12 @@ struct DimsV2 {
   static constexpr int T = T0 < 128 ? 128 : T0;
   // shared memory in floats
   static constexpr int oQ = 0;                       // [11][N3]
-  static constexpr int oX = oQ + NV * N3;            // [3][NF][11][N2]; later sDiv [3][10][N3]
+  static constexpr int oX = oQ + NV * N3;            // [3][NF][11][N2]
   static constexpr int nX = 3 * NF * NV * N2;
   static constexpr int oE = oX + nX;                 // [NF][N]
   static constexpr int oD = oE + NF * N;             // [N][NF]
   static constexpr int nF = oD + N * NF;
   static constexpr size_t bytes = ((nF * 4) + 15) / 16 * 16;
-  static_assert(30 * N3 <= nX, "derivative buffer must fit in the extrapolation buffer");
 };
 
 // solution-point index of position i along the line (d, L): base + i * stride
@@ -54,14 +53,13 @@ __device__ __forceinline__ void line_geom(int d, int L, int& base, int& stride) 
 }
 
 template <int N>
-__global__ void __launch_bounds__(DimsV2<N>::T) stage_kernel_v2(const StageParams P, const Ops<float> ops) {
+__global__ void __launch_bounds__(DimsV2<N>::T, 5) stage_kernel_v2(const StageParams P, const Ops<float> ops) {
   using DV = DimsV2<N>;
   constexpr int N2 = DV::N2, N3 = DV::N3, NF = DV::NF, T = DV::T, NL = DV::NLINE;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* smem = reinterpret_cast<float*>(smem_raw);
   float* sQ = smem + DV::oQ;
   float* sX = smem + DV::oX;
-  float* sDiv = sX;
   float* sE = smem + DV::oE;
   float* sD = smem + DV::oD;
 
@@ -106,21 +104,20 @@ __global__ void __launch_bounds__(DimsV2<N>::T) stage_kernel_v2(const StageParam
   }
   __syncthreads();
 
-  // ---- B: extrapolate every line to its N+1 flux points
+  // ---- B: extrapolate every line to its N+1 flux points (one variable at a time:
+  //      N values in registers, N+1 outputs)
   if (is_line) {
-    float ql[11][N];
-#pragma unroll
-    for (int v = 0; v < 11; ++v)
-#pragma unroll
-      for (int i = 0; i < N; ++i) ql[v][i] = sQ[v * N3 + lbase + i * lstride];
     float* X = sX + (ld * NF * 11) * N2 + lL;
+#pragma unroll 1
+    for (int v = 0; v < 11; ++v) {
+      float ql[N];
 #pragma unroll
-    for (int f = 0; f <= N; ++f) {
+      for (int i = 0; i < N; ++i) ql[i] = sQ[v * N3 + lbase + i * lstride];
 #pragma unroll
-      for (int v = 0; v < 11; ++v) {
+      for (int f = 0; f <= N; ++f) {
         float s = 0.0f;
 #pragma unroll
-        for (int i = 0; i < N; ++i) s = fmaf(sE[f * N + i], ql[v][i], s);
+        for (int i = 0; i < N; ++i) s = fmaf(sE[f * N + i], ql[i], s);
         X[(f * 11 + v) * N2] = s;
       }
     }
@@ -194,26 +191,22 @@ __global__ void __launch_bounds__(DimsV2<N>::T) stage_kernel_v2(const StageParam
   }
   __syncthreads();
 
-  // ---- D: derivative of the flux polynomial along every line
-  float fl[10][NF];
+  // ---- D: derivative of the flux polynomial along every line, written over the
+  //      line's own flux slots (value i of variable v goes to slot (f = i, v)):
+  //      each thread reads and writes only its own line, one variable at a time.
   if (is_line) {
-    const float* X = sX + (ld * NF * 11) * N2 + lL;
+    float* X = sX + (ld * NF * 11) * N2 + lL;
+#pragma unroll 1
+    for (int v = 0; v < 10; ++v) {
+      float fv[NF];
 #pragma unroll
-    for (int f = 0; f <= N; ++f)
+      for (int f = 0; f <= N; ++f) fv[f] = X[(f * 11 + v) * N2];
 #pragma unroll
-      for (int v = 0; v < 10; ++v) fl[v][f] = X[(f * 11 + v) * N2];
-  }
-  __syncthreads();
-  if (is_line) {
-    float* Dv = sDiv + (ld * 10) * N3 + lbase;
-#pragma unroll
-    for (int i = 0; i < N; ++i) {
-#pragma unroll
-      for (int v = 0; v < 10; ++v) {
+      for (int i = 0; i < N; ++i) {
         float s = 0.0f;
 #pragma unroll
-        for (int f = 0; f <= N; ++f) s = fmaf(sD[i * NF + f], fl[v][f], s);
-        Dv[v * N3 + i * lstride] = s;
+        for (int f = 0; f <= N; ++f) s = fmaf(sD[i * NF + f], fv[f], s);
+        X[(i * 11 + v) * N2] = s;
       }
     }
   }
@@ -221,9 +214,13 @@ __global__ void __launch_bounds__(DimsV2<N>::T) stage_kernel_v2(const StageParam
 
   // ---- E: residual, sources, RK sum (see stage_kernel<N, PolMixed> for the increment form)
   for (int n = tid; n < N3; n += T) {
+    const int i0 = n % N, j0 = (n / N) % N, k0 = n / N2;
+    const float* D0 = sX + ((0 * NF + i0) * 11) * N2 + (j0 + N * k0);
+    const float* D1 = sX + ((1 * NF + j0) * 11) * N2 + (i0 + N * k0);
+    const float* D2 = sX + ((2 * NF + k0) * 11) * N2 + (i0 + N * j0);
     float acc[10];
 #pragma unroll
-    for (int v = 0; v < 10; ++v) acc[v] = sDiv[v * N3 + n] + sDiv[(10 + v) * N3 + n] + sDiv[(20 + v) * N3 + n];
+    for (int v = 0; v < 10; ++v) acc[v] = D0[v * N2] + D1[v * N2] + D2[v * N2];
     const float iJ = __ldg(reinterpret_cast<const float*>(P.invJ) + e * N3 + n);
     const float* Xe = reinterpret_cast<const float*>(P.X) + e * 3 * N3;
     const float divB = acc[9] * iJ;
@@ -281,9 +278,11 @@ __global__ void __launch_bounds__(DimsV2<N>::T) stage_kernel_v2(const StageParam
 template <int N>
 cudaError_t launch_stage_v2_t(const StageParams& P, const Ops<float>& ops, cudaStream_t s) {
   using DV = DimsV2<N>;
+  cudaError_t err = cudaFuncSetAttribute(stage_kernel_v2<N>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         (int)cudaSharedmemCarveoutMaxShared);
+  if (err != cudaSuccess) return err;
   if (DV::bytes > 48 * 1024) {
-    cudaError_t err = cudaFuncSetAttribute(stage_kernel_v2<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)DV::bytes);
+    err = cudaFuncSetAttribute(stage_kernel_v2<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DV::bytes);
     if (err != cudaSuccess) return err;
   }
   if (P.n_e == 0) return cudaSuccess;
