@@ -60,6 +60,9 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=64)
+    ap.add_argument("--serve-budget-gb", type=float, default=24.0)
     return ap.parse_args()
 
 
@@ -238,6 +241,54 @@ def time_e2e(mesh, phys, q_dev, work, bg, steps, warmup):
     return e0.elapsed_time(e1), nbytes, nbytes + 16
 
 
+def run_serving(n_requests: int, budget_gb: float):
+    """Serving workload: n requests arriving Poisson (mean gap 20 ms), 6 Nz^2 Nr in {384, 1536, 6144, 24576}
+    elements, N in {4, 5, 6}, N_rho ~ U[1, 3], Omega ~ U[0.5, 2], seeds 0..n-1, 50 FP32-mixed steps each,
+    admitted by HBM footprint under `budget_gb`.  Latency = completion - arrival.  The sequential
+    comparisons run one request at a time through sd_step (FP32-mixed and FP64) on a bounded sample: one
+    request of each size, 5 steps each."""
+    import torch
+
+    from paper_2502_17805_gb300 import sdmhd, serve
+    reqs = serve.poisson_requests(n_requests, 0.020, steps=50)
+    srv = serve.Server(int(budget_gb * 1e9), max_running=max(n_requests, 1))
+    srv.warm(reqs)
+    torch.cuda.synchronize()
+    out = srv.run(reqs)
+    sample = []
+    for shape in ((4, 4), (8, 4), (16, 4), (32, 4)):
+        cand = [r for r in reqs if (r.nz, r.nr) == shape]
+        if cand:
+            sample.append(cand[0])
+    seq = {}
+    for name, prec in (("sequential_mixed", sdmhd.SD_FP32_MIXED), ("sequential_fp64", sdmhd.SD_FP64)):
+        dof = 0
+        ms = 0.0
+        for r in sample:
+            run = serve._Running(serve.Request(r.rid, r.nz, r.nr, r.N, r.n_rho, r.omega, r.seed, 5, 0.0),
+                                 srv.mesh(r.nz, r.nr, r.N))
+            bg = run.bg if prec == sdmhd.SD_FP32_MIXED else None
+            run.mesh.step(run.phys, r.cfl, run.q, run.work, prec=prec, bg=bg)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(5):
+                run.mesh.step(run.phys, r.cfl, run.q, run.work, prec=prec, bg=bg)
+            e1.record()
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+            dof += r.dof * 5
+        seq[name] = dof / (ms / 1e3)
+    return {"requests": out["requests"], "p50_ms": out["p50_ms"], "p99_ms": out["p99_ms"],
+            "mean_ms": out["mean_ms"], "aggregate": out["aggregate"], "unit": UNIT, "wall_s": out["wall_s"],
+            "ticks": out["ticks"], "budget_gb": budget_gb, "peak_gb": out["peak_bytes"] / 1e9,
+            "sequential_mixed": seq["sequential_mixed"], "sequential_fp64": seq["sequential_fp64"],
+            "vs_sequential_fp64": out["aggregate"] / seq["sequential_fp64"],
+            "workload": "%d requests, Poisson arrivals mean 20 ms, 6 Nz^2 x 4 shells with Nz in {4, 8, 16, 32}, "
+                        "N in {4, 5, 6}, N_rho ~ U[1,3], Omega ~ U[0.5,2], seeds 0-%d, 50 FP32-mixed steps each"
+                        % (n_requests, n_requests - 1)}
+
+
 class OracleSample:
     """The CPU oracle, as it stands, on a bounded sample of the workload: one step is the work of one
     SSP-RK3 step (three residual evaluations) on `n_elems` random elements of the same shell, from the
@@ -340,12 +391,18 @@ def run_ours(args):
     }
     if clocks:
         out["clocks"] = clocks
+    q2 = None
     if not args.no_e2e:
         q2 = q0.clone()
         ems, h2d, d2h = time_e2e(mesh, phys, q2, work, bg, max(1, min(args.steps, 10)), 1)
         ke = max(1, min(args.steps, 10))
         out["e2e"] = {"value": n_pts * ke * world / (ems / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                       "d2h_bytes_per_step": d2h, "ms_per_step": ems / ke}
+    if rank == 0 and world == 1 and not args.no_serve:
+        del q, work, q64, q2
+        import torch
+        torch.cuda.empty_cache()
+        out["serve"] = run_serving(args.serve_requests, args.serve_budget_gb)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         ors = OracleSample(wl, WORKLOADS[args.workload]["nz"] ** 2 * 6 * WORKLOADS[args.workload]["nr"])
         ors.run(1)

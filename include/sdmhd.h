@@ -134,6 +134,7 @@ typedef struct {
   int64_t n_interior_faces;
   double h_min;            /* smallest element edge chord, for the time-step rule */
   int64_t device_bytes;    /* bytes the library holds on the device for this mesh */
+  int64_t trace_bytes;     /* scratch one sd_step_req needs for its face traces (FP32, two buffers) */
 } sd_mesh_info;
 
 typedef struct {
@@ -210,6 +211,35 @@ sd_status sd_rk_stage(const sd_mesh* mesh, const sd_phys* phys, sd_precision pre
  * receives (dt, c_h).  No host synchronisation.  Asynchronous. */
 sd_status sd_step(const sd_mesh* mesh, const sd_phys* phys, sd_precision prec, double cfl, double* q, double* work,
                   const sd_background* bg, double* dt_out, void* stream);
+
+/* ---- Packed stepping of many independent solves (serving).
+ * One request is one shell (or box) solve on its own mesh with its own physics,
+ * background and states.  sd_step_packed advances every request by one
+ * SSP-RK3 step of the FP32-mixed path (the same arithmetic as sd_step with
+ * SD_FP32_MIXED): per order N present it launches one lambda_max/trace kernel,
+ * one step-control kernel and three stage kernels over the elements of all
+ * requests of that order, so small solves share launches and fill the GPU.
+ * Each request's result does not depend on the others in the pack. */
+typedef struct {
+  const sd_mesh* mesh;
+  sd_phys phys;             /* c_h <= 0: c_h = lambda_max of the request each step */
+  const sd_background* bg;  /* required */
+  double* q;                /* device state, advanced in place */
+  double* work;             /* device state used inside the step */
+  void* traces;             /* device scratch of sd_mesh_info.trace_bytes bytes, 16-byte aligned */
+  double* dyn;              /* device double[4]: receives (dt, c_h) of the step in [0], [1] */
+  double cfl;               /* dt = cfl * dx_min / lambda_max as in sd_step */
+} sd_step_req;
+
+typedef struct sd_packer sd_packer;
+
+/* A packer holds the device tables of up to max_requests requests per call. */
+sd_status sd_packer_create(int32_t max_requests, sd_packer** out);
+sd_status sd_packer_destroy(sd_packer* packer);
+/* reqs: host array of n requests (n <= max_requests), all meshes on the current
+ * device.  Asynchronous on `stream`; a second call may be issued before the
+ * first finishes (the packer keeps its tables until the GPU has read them). */
+sd_status sd_step_packed(sd_packer* packer, int32_t n, const sd_step_req* reqs, void* stream);
 
 /* Global diagnostics of q in FP64 (Sec. Results: KE, E_B), with the discrete
  * div B of the residual (BR1 face average) for max|div B|.  Sums run in a fixed

@@ -122,16 +122,16 @@ __device__ __forceinline__ void write_traces(const typename Pol::R* sQ, const ty
   }
 }
 
+// Face traces of element e (and, with P.lam_max, its lambda_max contribution).
 template <int N, class Pol>
-__global__ void __launch_bounds__(Dims<N>::BLK) trace_kernel(const StageParams P, const Ops<typename Pol::R> ops) {
+__device__ __forceinline__ void trace_body(const StageParams& P, const Ops<typename Pol::R>& ops, int64_t e,
+                                           unsigned char* smem) {
   using R = typename Pol::R;
   constexpr int NF = N + 1, BLK = Dims<N>::BLK;
-  extern __shared__ __align__(16) unsigned char smem[];
   using S = Smem<N, Pol>;
   R* sQ = reinterpret_cast<R*>(smem) + S::oQ;
   R* sE = reinterpret_cast<R*>(smem) + S::oE;
   for (int i = threadIdx.x; i < NF * N; i += BLK) sE[i] = ops.E[i];
-  const int64_t e = blockIdx.x;
   double lam = 0.0;
   load_element<N, Pol>(P, P.q_in, e, sQ, P.lam_max ? &lam : nullptr);
   if (P.lam_max) {
@@ -145,6 +145,41 @@ __global__ void __launch_bounds__(Dims<N>::BLK) trace_kernel(const StageParams P
   }
   __syncthreads();
   write_traces<N, Pol>(sQ, sE, reinterpret_cast<R*>(P.tr_out), e);
+}
+
+template <int N, class Pol>
+__global__ void __launch_bounds__(Dims<N>::BLK) trace_kernel(const StageParams P, const Ops<typename Pol::R> ops) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  trace_body<N, Pol>(P, ops, (int64_t)blockIdx.x, smem);
+}
+
+// Packed launches: CTA b works on element b - off[r] of request r, off[r] <= b < off[r+1];
+// the request's parameters are copied to shared memory first.
+__device__ __forceinline__ int packed_request(const int64_t* __restrict__ off, int n_req, int64_t b) {
+  int lo = 0, hi = n_req - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(off + mid) <= b) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ void copy_params(const StageParams* __restrict__ src, StageParams* dst) {
+  const int* s = reinterpret_cast<const int*>(src);
+  int* d = reinterpret_cast<int*>(dst);
+  for (int i = threadIdx.x; i < (int)(sizeof(StageParams) / sizeof(int)); i += blockDim.x) d[i] = __ldg(s + i);
+  __syncthreads();
+}
+
+template <int N>
+__global__ void __launch_bounds__(Dims<N>::BLK) trace_kernel_packed(const StageParams* __restrict__ tab,
+                                                                    const int64_t* __restrict__ off, int n_req,
+                                                                    const Ops<float> ops) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ StageParams sP;
+  const int r = packed_request(off, n_req, (int64_t)blockIdx.x);
+  copy_params(tab + r, &sP);
+  trace_body<N, PolMixed>(sP, ops, (int64_t)blockIdx.x - __ldg(off + r), smem);
 }
 
 // Sources M (Sec. MHD Governing Equations) for the full FP64 state.

@@ -17,6 +17,7 @@
 
 #include "sd_internal.h"
 #include "sd_physics.cuh"
+#include "sd_stage.cuh"
 
 namespace sd {
 
@@ -53,10 +54,10 @@ __device__ __forceinline__ void line_geom(int d, int L, int& base, int& stride) 
 }
 
 template <int N>
-__global__ void __launch_bounds__(DimsV2<N>::T, 5) stage_kernel_v2(const StageParams P, const Ops<float> ops) {
+__device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops<float>& ops, const int64_t e,
+                                              unsigned char* smem_raw) {
   using DV = DimsV2<N>;
   constexpr int N2 = DV::N2, N3 = DV::N3, NF = DV::NF, T = DV::T, NL = DV::NLINE;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   float* smem = reinterpret_cast<float*>(smem_raw);
   float* sQ = smem + DV::oQ;
   float* sX = smem + DV::oX;
@@ -68,7 +69,6 @@ __global__ void __launch_bounds__(DimsV2<N>::T, 5) stage_kernel_v2(const StagePa
     sE[i] = ops.E[i];
     sD[i] = ops.D[i];
   }
-  const int64_t e = blockIdx.x;
   const float* Sfam = reinterpret_cast<const float*>(P.Sfam) + e * (9 * N2 * NF);
   const float gamma = (float)P.gamma;
   const float gm1 = gamma - 1.0f;
@@ -276,6 +276,24 @@ __global__ void __launch_bounds__(DimsV2<N>::T, 5) stage_kernel_v2(const StagePa
 }
 
 template <int N>
+__global__ void __launch_bounds__(DimsV2<N>::T, 5) stage_kernel_v2(const StageParams P, const Ops<float> ops) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  stage_body_v2<N>(P, ops, (int64_t)blockIdx.x, smem_raw);
+}
+
+// Packed launch over several requests (see packed_request in sd_stage.cuh).
+template <int N>
+__global__ void __launch_bounds__(DimsV2<N>::T, 5) stage_kernel_v2_packed(const StageParams* __restrict__ tab,
+                                                                         const int64_t* __restrict__ off, int n_req,
+                                                                         const Ops<float> ops) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ StageParams sP;
+  const int r = packed_request(off, n_req, (int64_t)blockIdx.x);
+  copy_params(tab + r, &sP);
+  stage_body_v2<N>(sP, ops, (int64_t)blockIdx.x - __ldg(off + r), smem_raw);
+}
+
+template <int N>
 cudaError_t launch_stage_v2_t(const StageParams& P, const Ops<float>& ops, cudaStream_t s) {
   using DV = DimsV2<N>;
   cudaError_t err = cudaFuncSetAttribute(stage_kernel_v2<N>, cudaFuncAttributePreferredSharedMemoryCarveout,
@@ -287,6 +305,36 @@ cudaError_t launch_stage_v2_t(const StageParams& P, const Ops<float>& ops, cudaS
   }
   if (P.n_e == 0) return cudaSuccess;
   stage_kernel_v2<N><<<(unsigned)P.n_e, DV::T, DV::bytes, s>>>(P, ops);
+  return cudaGetLastError();
+}
+
+// Packed launches of one order N: trace (+lambda) kernel or stage kernel over
+// `blocks` elements of n_req requests.
+template <int N>
+cudaError_t launch_packed_t(bool traces, const StageParams* tab, const int64_t* off, int n_req, int64_t blocks,
+                            const Ops<float>& ops, cudaStream_t s) {
+  if (blocks == 0) return cudaSuccess;
+  if (traces) {
+    const size_t bytes = Smem<N, PolMixed>::bytes;
+    if (bytes > 40 * 1024) {
+      cudaError_t err = cudaFuncSetAttribute(trace_kernel_packed<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)bytes);
+      if (err != cudaSuccess) return err;
+    }
+    trace_kernel_packed<N><<<(unsigned)blocks, Dims<N>::BLK, bytes, s>>>(tab, off, n_req, ops);
+  } else {
+    using DV = DimsV2<N>;
+    cudaError_t err = cudaFuncSetAttribute(stage_kernel_v2_packed<N>,
+                                           cudaFuncAttributePreferredSharedMemoryCarveout,
+                                           (int)cudaSharedmemCarveoutMaxShared);
+    if (err != cudaSuccess) return err;
+    if (DV::bytes > 40 * 1024) {
+      err = cudaFuncSetAttribute(stage_kernel_v2_packed<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)DV::bytes);
+      if (err != cudaSuccess) return err;
+    }
+    stage_kernel_v2_packed<N><<<(unsigned)blocks, DV::T, DV::bytes, s>>>(tab, off, n_req, ops);
+  }
   return cudaGetLastError();
 }
 

@@ -28,7 +28,8 @@ STATUS = {0: "SD_OK", 1: "SD_ERR_INVALID_ARGUMENT", 2: "SD_ERR_UNSUPPORTED", 3: 
 # every symbol include/sdmhd.h declares
 EXPORTS = ["sd_last_error", "sd_mesh_create", "sd_mesh_destroy", "sd_mesh_query", "sd_state_init",
            "sd_background_create", "sd_background_destroy", "sd_residual", "sd_rk_stage", "sd_step",
-           "sd_diagnostics", "sd_profile_enable", "sd_profile_read", "sd_residual_noalloc"]
+           "sd_diagnostics", "sd_profile_enable", "sd_profile_read", "sd_residual_noalloc",
+           "sd_packer_create", "sd_packer_destroy", "sd_step_packed"]
 
 
 class SDError(RuntimeError):
@@ -67,7 +68,13 @@ class ProfileC(C.Structure):
 class MeshInfoC(C.Structure):
     _fields_ = [("order", C.c_int32), ("p_map", C.c_int32), ("n_elements", C.c_int64), ("n_points", C.c_int64),
                 ("elem_stride", C.c_int64), ("state_bytes", C.c_int64), ("n_boundary_faces", C.c_int64),
-                ("n_interior_faces", C.c_int64), ("h_min", C.c_double), ("device_bytes", C.c_int64)]
+                ("n_interior_faces", C.c_int64), ("h_min", C.c_double), ("device_bytes", C.c_int64),
+                ("trace_bytes", C.c_int64)]
+
+
+class StepReqC(C.Structure):
+    _fields_ = [("mesh", C.c_void_p), ("phys", PhysC), ("bg", C.c_void_p), ("q", C.c_void_p), ("work", C.c_void_p),
+                ("traces", C.c_void_p), ("dyn", C.c_void_p), ("cfl", C.c_double)]
 
 
 @dataclass
@@ -117,6 +124,9 @@ def lib():
         L.sd_profile_enable.argtypes = [vp, C.c_int32]
         L.sd_profile_read.argtypes = [vp, C.POINTER(ProfileC)]
         L.sd_residual_noalloc.argtypes = [vp, C.POINTER(PhysC), vp, vp, vp]
+        L.sd_packer_create.argtypes = [C.c_int32, C.POINTER(vp)]
+        L.sd_packer_destroy.argtypes = [vp]
+        L.sd_step_packed.argtypes = [vp, C.c_int32, C.POINTER(StepReqC), vp]
         for name in EXPORTS:
             getattr(L, name).restype = C.c_int if name != "sd_last_error" else C.c_char_p
         _lib = L
@@ -268,3 +278,29 @@ class Mesh:
             _check(rc)
         out["status"] = rc
         return out
+
+
+class Packer:
+    """Packed SSP-RK3 steps of many independent solves (sd_step_packed, FP32-mixed path)."""
+
+    def __init__(self, max_requests: int):
+        out = C.c_void_p()
+        self._h = None
+        _check(lib().sd_packer_create(int(max_requests), C.byref(out)))
+        self._h = out
+        self.cap = int(max_requests)
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            lib().sd_packer_destroy(self._h)
+            self._h = None
+
+    def step(self, reqs, stream=None):
+        """reqs: sequence of (mesh, phys, background, q, work, traces, dyn, cfl)."""
+        arr = (StepReqC * max(len(reqs), 1))()
+        for i, (mesh, phys, bg, q, work, traces, dyn, cfl) in enumerate(reqs):
+            r = arr[i]
+            r.mesh, r.phys, r.bg = mesh._h, phys.c(), bg._h
+            r.q, r.work, r.traces, r.dyn = _ptr(q), _ptr(work), _ptr(traces), _ptr(dyn)
+            r.cfl = float(cfl)
+        _check(lib().sd_step_packed(self._h, len(reqs), arr, _stream(stream)))

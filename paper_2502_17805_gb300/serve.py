@@ -1,0 +1,206 @@
+"""Continuous-batching server of independent SD-MHD shell solves.
+
+Each request is a shell solve (its own mesh shape, order N, density scale
+height N_rho, rotation Omega and seed) that must advance K SSP-RK3 steps of
+the FP32-mixed path.  The server
+
+* admits arrived requests first-in first-out while their device footprint
+  (two FP64 states, FP32 face traces, background tables and the transient of
+  building the background) fits in the HBM budget next to the running ones;
+* keeps every admitted state resident on the device;
+* advances all running requests together: each tick is one sd_step_packed
+  call, i.e. per order N one launch of each kernel over the elements of every
+  running request of that order; requests that arrive meanwhile join at the
+  next tick, so their work overlaps with the others' on the device;
+* retires a request after K steps, records its latency (completion minus
+  arrival) and frees its memory, which may admit waiting requests.
+
+Meshes (geometry) are cached per (Nz, Nr, N) and shared between requests;
+everything a step writes (states, traces, dt) belongs to the request.
+"""
+from __future__ import annotations
+
+import math
+import time
+from dataclasses import dataclass, field
+from typing import Dict, List, Optional, Sequence, Tuple
+
+import numpy as np
+
+from . import inputs, sdmhd
+
+R_IN, R_OUT = 0.70, 0.98
+
+
+@dataclass
+class Request:
+    rid: int
+    nz: int
+    nr: int
+    N: int
+    n_rho: float
+    omega: float
+    seed: int
+    steps: int
+    arrival: float  # seconds after the start of the run
+    cfl: float = 0.2
+    noise: float = 1e-4
+    dipole: float = 1e-6
+    # filled in by the server
+    admitted: float = float("nan")
+    done: float = float("nan")
+
+    @property
+    def n_elements(self) -> int:
+        return 6 * self.nz * self.nz * self.nr
+
+    @property
+    def dof(self) -> int:
+        return self.n_elements * self.N ** 3
+
+    @property
+    def latency(self) -> float:
+        return self.done - self.arrival
+
+
+def poisson_requests(n: int, mean_gap_s: float, seed: int = 1234, steps: int = 50,
+                     shapes: Sequence[Tuple[int, int]] = ((4, 4), (8, 4), (16, 4), (32, 4)),
+                     orders: Sequence[int] = (4, 5, 6)) -> List[Request]:
+    """The serving workload: Poisson arrivals, element counts 6 Nz^2 Nr from `shapes`,
+    orders from `orders`, N_rho ~ U[1, 3], Omega ~ U[0.5, 2]; request i uses seed i for
+    both its parameter draws and its initial noise."""
+    gaps = np.random.default_rng(seed).exponential(mean_gap_s, size=n)
+    t = np.cumsum(gaps) - gaps[0]
+    out = []
+    for i in range(n):
+        r = np.random.default_rng(i)
+        nz, nr = shapes[int(r.integers(len(shapes)))]
+        out.append(Request(rid=i, nz=nz, nr=nr, N=int(orders[int(r.integers(len(orders)))]),
+                           n_rho=float(r.uniform(1.0, 3.0)), omega=float(r.uniform(0.5, 2.0)), seed=i,
+                           steps=steps, arrival=float(t[i])))
+    return out
+
+
+class _Running:
+    def __init__(self, req: Request, mesh: sdmhd.Mesh):
+        import torch
+        self.req = req
+        self.mesh = mesh
+        self.phys = sdmhd.Phys(gamma=5.0 / 3.0, GM=1.0, omega=req.omega, glm_alpha=1.0, c_h=0.0, powell=1,
+                               gravity=1, coriolis=1)
+        params = [req.n_rho, R_IN, R_OUT, 1.0, 1.0, req.noise, req.dipole]
+        bgs = mesh.empty_state()
+        self.q = mesh.state_init(self.phys, sdmhd.INIT_SHELL_POLYTROPE, params, seed=req.seed, background=bgs)
+        self.bg = mesh.background(self.phys, bgs)
+        del bgs
+        self.work = mesh.empty_state()
+        self.traces = torch.empty(mesh.info["trace_bytes"] // 4, dtype=torch.float32, device="cuda")
+        self.dyn = torch.zeros(4, dtype=torch.float64, device="cuda")
+        self.steps_done = 0
+
+    def as_packed(self):
+        return (self.mesh, self.phys, self.bg, self.q, self.work, self.traces, self.dyn, self.req.cfl)
+
+
+def footprint_bytes(info: dict, n_pts: int) -> int:
+    """Device bytes a running request holds, counting the transient of building its background
+    (one more state and an FP64 residual)."""
+    state = info["state_bytes"]
+    bg = 5 * n_pts * 4 + info["n_elements"] * 6 * 2 * info["order"] ** 2 * 4
+    return 4 * state + info["trace_bytes"] + bg + 64
+
+
+class Server:
+    def __init__(self, hbm_budget_bytes: int, max_running: int = 256):
+        self.budget = int(hbm_budget_bytes)
+        self.packer = sdmhd.Packer(max_running)
+        self.max_running = max_running
+        self.meshes: Dict[Tuple[int, int, int], sdmhd.Mesh] = {}
+        self.peak_bytes = 0
+        self.ticks = 0
+
+    def mesh(self, nz: int, nr: int, N: int) -> sdmhd.Mesh:
+        key = (nz, nr, N)
+        if key not in self.meshes:
+            v, h = inputs.shell_mesh(nz, nr, R_IN, R_OUT)
+            self.meshes[key] = sdmhd.Mesh(N, v, h, geom=1, r_in=R_IN, r_out=R_OUT, bc_in=sdmhd.BC_WALL_CONDUCTING,
+                                          bc_out=sdmhd.BC_WALL_RADIAL)
+        return self.meshes[key]
+
+    def warm(self, requests: Sequence[Request]):
+        """Build the meshes of every shape the workload uses (a running service keeps them)."""
+        for r in requests:
+            self.mesh(r.nz, r.nr, r.N)
+
+    def run(self, requests: Sequence[Request], stream=None) -> dict:
+        import torch
+        pending = sorted(requests, key=lambda r: r.arrival)
+        queue: List[Request] = []
+        running: List[Tuple[_Running, int]] = []
+        used = 0
+        finished: List[Request] = []
+        t0 = time.perf_counter()
+        i = 0
+        while i < len(pending) or queue or running:
+            now = time.perf_counter() - t0
+            while i < len(pending) and pending[i].arrival <= now:
+                queue.append(pending[i])
+                i += 1
+            # admission: FIFO while the footprint fits (a lone request is always admitted)
+            while queue and len(running) < self.max_running:
+                r = queue[0]
+                m = self.mesh(r.nz, r.nr, r.N)
+                fp = footprint_bytes(m.info, m.info["n_points"])
+                if running and used + fp > self.budget:
+                    break
+                queue.pop(0)
+                r.admitted = time.perf_counter() - t0
+                running.append((_Running(r, m), fp))
+                used += fp
+                self.peak_bytes = max(self.peak_bytes, used)
+            if not running:
+                if i < len(pending):
+                    time.sleep(max(0.0, pending[i].arrival - (time.perf_counter() - t0)))
+                continue
+            # one tick: every running request advances one step
+            self.packer.step([run.as_packed() for run, _ in running], stream=stream)
+            torch.cuda.current_stream().synchronize()
+            self.ticks += 1
+            t_done = time.perf_counter() - t0
+            keep = []
+            for run, fp in running:
+                run.steps_done += 1
+                if run.steps_done >= run.req.steps:
+                    run.req.done = t_done
+                    finished.append(run.req)
+                    used -= fp
+                else:
+                    keep.append((run, fp))
+            running = keep
+        wall = time.perf_counter() - t0
+        lat = np.array([r.latency for r in finished])
+        dof_updates = sum(r.dof * r.steps for r in finished)
+        return {"requests": len(finished), "wall_s": wall, "dof_updates": dof_updates,
+                "aggregate": dof_updates / wall, "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                "p99_ms": float(np.percentile(lat, 99) * 1e3), "mean_ms": float(lat.mean() * 1e3),
+                "peak_bytes": self.peak_bytes, "budget_bytes": self.budget, "ticks": self.ticks}
+
+    def final_state(self, req: Request):
+        """Run one request alone to completion (for checks); returns its final state on the device."""
+        m = self.mesh(req.nz, req.nr, req.N)
+        run = _Running(req, m)
+        for _ in range(req.steps):
+            self.packer.step([run.as_packed()])
+        return run.q
+
+
+def run_mix(server: Server, reqs: Sequence[Request]):
+    """Advance a fixed set of requests together (all admitted at once), one packed step per tick;
+    returns their final states (for the alone-versus-mix check)."""
+    runs = [_Running(r, server.mesh(r.nz, r.nr, r.N)) for r in reqs]
+    for _ in range(max(r.steps for r in reqs)):
+        active = [run for run in runs if run.steps_done < run.req.steps]
+        server.packer.step([run.as_packed() for run in active])
+        for run in active:
+            run.steps_done += 1
+    return [run.q for run in runs]

@@ -1,0 +1,116 @@
+"""Serving: packed steps of independent solves (sd_step_packed) and the
+continuous-batching server.  A request's result must not depend on which other
+requests share its launches."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2502_17805_gb300 import serve
+
+
+def test_poisson_workload_recipe():
+    reqs = serve.poisson_requests(64, 0.020, steps=50)
+    assert len(reqs) == 64
+    assert [r.seed for r in reqs] == list(range(64))
+    assert {r.n_elements for r in reqs} <= {384, 1536, 6144, 24576}
+    assert {r.N for r in reqs} <= {4, 5, 6}
+    assert all(1.0 <= r.n_rho <= 3.0 and 0.5 <= r.omega <= 2.0 for r in reqs)
+    arr = np.array([r.arrival for r in reqs])
+    assert np.all(np.diff(arr) >= 0) and arr[0] == 0.0
+    assert 0.5 * 0.020 < np.diff(arr).mean() < 2.0 * 0.020
+    # request i draws its parameters from seed i: the same request in another workload is identical
+    again = serve.poisson_requests(8, 0.5, seed=99, steps=50)
+    assert (again[3].nz, again[3].N, again[3].n_rho) == (reqs[3].nz, reqs[3].N, reqs[3].n_rho)
+
+
+def test_footprint_grows_with_the_mesh():
+    info_small = {"state_bytes": 9 * 384 * 64 * 8, "trace_bytes": 2 * 384 * 6 * 9 * 16 * 4, "n_elements": 384,
+                  "order": 4}
+    info_big = {"state_bytes": 9 * 1536 * 64 * 8, "trace_bytes": 2 * 1536 * 6 * 9 * 16 * 4, "n_elements": 1536,
+                "order": 4}
+    assert serve.footprint_bytes(info_big, 1536 * 64) > 3 * serve.footprint_bytes(info_small, 384 * 64)
+
+
+gpu = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_dev():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2502_17805_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+    return torch
+
+
+@gpu
+def test_packed_step_equals_sd_step(torch_dev):
+    torch = torch_dev
+    from paper_2502_17805_gb300 import sdmhd
+    srv = serve.Server(hbm_budget_bytes=1 << 34, max_running=8)
+    req = serve.Request(rid=0, nz=3, nr=2, N=5, n_rho=2.0, omega=1.3, seed=5, steps=3, arrival=0.0)
+    q_packed = srv.final_state(req)
+    run = serve._Running(req, srv.mesh(req.nz, req.nr, req.N))
+    for _ in range(req.steps):
+        run.mesh.step(run.phys, req.cfl, run.q, run.work, prec=sdmhd.SD_FP32_MIXED, bg=run.bg)
+    torch.cuda.synchronize()
+    assert torch.equal(q_packed, run.q)
+
+
+@gpu
+def test_each_result_is_the_same_alone_and_in_the_mix(torch_dev):
+    torch = torch_dev
+    srv = serve.Server(hbm_budget_bytes=1 << 34, max_running=8)
+    reqs = [serve.Request(rid=0, nz=2, nr=2, N=4, n_rho=1.5, omega=0.7, seed=1, steps=4, arrival=0.0),
+            serve.Request(rid=1, nz=3, nr=2, N=6, n_rho=2.5, omega=1.9, seed=2, steps=3, arrival=0.0),
+            serve.Request(rid=2, nz=4, nr=1, N=5, n_rho=1.1, omega=1.0, seed=3, steps=5, arrival=0.0),
+            serve.Request(rid=3, nz=2, nr=1, N=4, n_rho=2.9, omega=0.6, seed=4, steps=2, arrival=0.0)]
+    alone = [srv.final_state(r).clone() for r in reqs]
+    mixed = serve.run_mix(srv, reqs)
+    torch.cuda.synchronize()
+    for a, m in zip(alone, mixed):
+        assert torch.equal(a, m)
+
+
+@gpu
+def test_admission_respects_the_hbm_budget(torch_dev):
+    reqs = serve.poisson_requests(10, 0.002, steps=3, shapes=((2, 2), (4, 2)), orders=(4, 5))
+    srv = serve.Server(hbm_budget_bytes=1 << 20, max_running=16)  # smaller than any two requests
+    srv.warm(reqs)
+    out = srv.run(reqs)
+    assert out["requests"] == 10
+    biggest = max(serve.footprint_bytes(m.info, m.info["n_points"]) for m in srv.meshes.values())
+    assert out["peak_bytes"] <= max(srv.budget, biggest)
+    roomy = serve.Server(hbm_budget_bytes=1 << 34, max_running=16)
+    roomy.warm(reqs)
+    out2 = roomy.run(reqs)
+    assert out2["requests"] == 10 and out2["ticks"] < out["ticks"]  # overlapping requests share ticks
+
+
+@gpu
+def test_packed_step_matches_the_oracle(torch_dev):
+    """One packed step of a stratified shell against the FP64 oracle, given the packed dt and c_h."""
+    torch = torch_dev
+    from oracle import sdref
+    from paper_2502_17805_gb300 import inputs
+    srv = serve.Server(hbm_budget_bytes=1 << 34, max_running=4)
+    req = serve.Request(rid=0, nz=3, nr=2, N=5, n_rho=2.0, omega=1.3, seed=5, steps=1, arrival=0.0)
+    run = serve._Running(req, srv.mesh(req.nz, req.nr, req.N))
+    q_before = run.mesh.to_host(run.q)
+    srv.packer.step([run.as_packed()])
+    dt, ch = run.dyn.cpu().numpy()[:2]
+    v, h = inputs.shell_mesh(req.nz, req.nr)
+    om = sdref.Mesh(req.N, v, h, geom=1, r_in=0.70, r_out=0.98, bc_in=sdref.BC_WALL_CONDUCTING,
+                    bc_out=sdref.BC_WALL_RADIAL)
+    oph = sdref.Phys(gamma=5.0 / 3.0, GM=1.0, omega=req.omega, glm_alpha=1.0, c_h=float(ch), powell=1, gravity=1,
+                     coriolis=1)
+    qo = om.rk_step(oph, float(dt), q_before)
+    dg, do = run.mesh.to_host(run.q) - q_before, qo - q_before
+    err = np.abs(dg - do).max(axis=(1, 2)) / np.maximum(np.abs(do).max(axis=(1, 2)), 1e-300)
+    assert err.max() <= 1e-5, err
+    lam = om.diagnostics(oph, q_before)["lambda_max"]
+    xs = sdref.nodes(req.N)[0]
+    assert abs(dt / (req.cfl * om.info()["h_min"] * (xs[1] - xs[0]) / lam) - 1.0) < 1e-6
