@@ -200,7 +200,8 @@ void free_mesh(sd_mesh* m) {
   if (!m) return;
   for (cudaEvent_t ev : m->prof_ev) cudaEventDestroy(ev);
   void* ptrs[] = {m->Sfam64, m->invJ64, m->X64, m->Sfam32, m->invJ32, m->X32, m->nbr, m->meta,
-                  m->tr64[0], m->tr64[1], m->tr32[0], m->tr32[1], m->dyn, m->diag_part, m->diag_out, m->divb};
+                  m->tr64[0], m->tr64[1], m->tr32[0], m->tr32[1], m->dyn, m->diag_part, m->diag_out, m->divb,
+                  m->err};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (m->host_diag) cudaFreeHost(m->host_diag);
@@ -240,6 +241,7 @@ sd::StageParams base_params(const sd_mesh* m, const sd_phys* ph, int prec) {
   }
   P.nbr = m->nbr;
   P.meta = m->meta;
+  P.err = m->err;
   return P;
 }
 
@@ -449,6 +451,7 @@ sd_status sd_mesh_create(const sd_mesh_desc* desc, void* stream, sd_mesh** out) 
   ALLOC(m->diag_part, ne * 12);
   ALLOC(m->diag_out, 12);
   ALLOC(m->divb, ne * N3);
+  ALLOC(m->err, 4);
 #undef ALLOC
   if (err == cudaSuccess) err = cudaMallocHost((void**)&m->host_diag, 12 * sizeof(double));
   m->device_bytes = bytes;
@@ -475,6 +478,7 @@ sd_status sd_mesh_create(const sd_mesh_desc* desc, void* stream, sd_mesh** out) 
   if (err == cudaSuccess && n_e > 0)
     err = cudaMemcpyAsync(m->meta, meta.data(), n_e * 6 * sizeof(int), cudaMemcpyHostToDevice, s);
   if (err == cudaSuccess) err = cudaMemsetAsync(d_flag, 0, sizeof(int), s);
+  if (err == cudaSuccess) err = cudaMemsetAsync(m->err, 0, sizeof(int), s);
   if (err == cudaSuccess) err = sd::launch_geometry(m, d_corners, d_flag, s);
   if (err == cudaSuccess) err = sd::launch_canonical_faces(m, s);
   if (err == cudaSuccess) err = cudaMemcpyAsync(&h_flag, d_flag, sizeof(int), cudaMemcpyDeviceToHost, s);
@@ -564,10 +568,13 @@ sd_status sd_background_create(const sd_mesh* m, const sd_phys* ph, const double
   bg->gamma = ph->gamma;
   bg->rec = nullptr;
   bg->jump = nullptr;
+  bg->dreg = nullptr;
+  bg->dstride = (N3 + 3) / 4 * 4;
   double *q0 = nullptr, *R0 = nullptr;
   const size_t state = 9 * ne * m->stride;
   cudaError_t err = cudaMalloc((void**)&bg->rec, 5 * ne * N3 * sizeof(float));
   if (err == cudaSuccess) err = cudaMalloc((void**)&bg->jump, ne * 6 * 2 * N2 * sizeof(float));
+  if (err == cudaSuccess) err = cudaMalloc((void**)&bg->dreg, 9 * ne * bg->dstride * sizeof(float));
   if (err == cudaSuccess) err = cudaMalloc((void**)&q0, state * sizeof(double));
   if (err == cudaSuccess) err = cudaMalloc((void**)&R0, state * sizeof(double));
   if (err == cudaSuccess) err = sd::launch_bg_prepare(m, ph->gamma, 1.0 / (ph->gamma - 1.0), q_bg, q0, bg->rec, s);
@@ -599,6 +606,7 @@ sd_status sd_background_create(const sd_mesh* m, const sd_phys* ph, const double
   if (err != cudaSuccess) {
     if (bg->rec) cudaFree(bg->rec);
     if (bg->jump) cudaFree(bg->jump);
+    if (bg->dreg) cudaFree(bg->dreg);
     delete bg;
     cudaGetLastError();
     return err == cudaErrorMemoryAllocation ? fail(SD_ERR_OUT_OF_MEMORY, "background allocation failed")
@@ -613,6 +621,7 @@ sd_status sd_background_destroy(sd_background* bg) {
   DeviceGuard g(bg->mesh->device);
   cudaFree(bg->rec);
   cudaFree(bg->jump);
+  cudaFree(bg->dreg);
   delete bg;
   return SD_OK;
 }
@@ -655,7 +664,7 @@ sd_status sd_residual(const sd_mesh* m, const sd_phys* ph, sd_precision prec, co
 
 static sd_status rk_stage_impl(sd_mesh* m, const sd_phys* ph, int prec, int stage, double dt, const double* dyn,
                                const double* q_n, const double* q_in, double* q_out, const sd_background* bg,
-                               bool want_traces, cudaStream_t s) {
+                               bool want_traces, cudaStream_t s, int lsr_read = 0, int lsr_write = 0) {
   static const double A[3] = {0.0, 0.75, 1.0 / 3.0};
   static const double B[3] = {1.0, 0.25, 2.0 / 3.0};
   sd::StageParams P = base_params(m, ph, prec);
@@ -690,6 +699,12 @@ static sd_status rk_stage_impl(sd_mesh* m, const sd_phys* ph, int prec, int stag
   P.dyn = dyn;
   P.tr_in = trace_buf(m, prec, bin);
   P.tr_out = want_traces ? trace_buf(m, prec, bout) : nullptr;
+  if (bg && (lsr_read || lsr_write)) {
+    P.dreg = bg->dreg;
+    P.dstride = bg->dstride;
+    P.lsr_read = lsr_read;
+    P.lsr_write = lsr_write;
+  }
   cudaError_t err;
   {
     ProfScope ps(m, PROF_STAGE, s);
@@ -764,6 +779,11 @@ sd_status sd_step(const sd_mesh* m, const sd_phys* ph, sd_precision prec, double
     S.dyn = mm->dyn;
     S.tr_in = trace_buf(mm, prec, 0);
     S.tr_out = trace_buf(mm, prec, 1);
+    if (prec == SD_FP32_MIXED) {  // low-storage form: stage 0 stores D = q^1 - q^n
+      S.dreg = bg->dreg;
+      S.dstride = bg->dstride;
+      S.lsr_write = 1;
+    }
     {
       ProfScope ps(m, PROF_STAGE, s);
       SD_CUDA(sd::launch_stage(m, prec, S, s));
@@ -772,9 +792,10 @@ sd_status sd_step(const sd_mesh* m, const sd_phys* ph, sd_precision prec, double
     mm->tr_tag[1] = work;
     mm->tr_prec[1] = prec;
   }
-  st = rk_stage_impl(mm, ph, prec, 1, 0.0, mm->dyn, q, work, work, bg, true, s);
+  const int lsr = prec == SD_FP32_MIXED ? 1 : 0;
+  st = rk_stage_impl(mm, ph, prec, 1, 0.0, mm->dyn, q, work, work, bg, true, s, lsr, lsr ? 2 : 0);
   if (st != SD_OK) return st;
-  st = rk_stage_impl(mm, ph, prec, 2, 0.0, mm->dyn, q, work, q, bg, false, s);
+  st = rk_stage_impl(mm, ph, prec, 2, 0.0, mm->dyn, q, work, q, bg, false, s, lsr, 0);
   return st;
 }
 
@@ -804,7 +825,10 @@ sd_status sd_diagnostics(const sd_mesh* m, const sd_phys* ph, const double* q, s
     SD_CUDA(sd::launch_diag(m, ph, q, s));
   }
   SD_CUDA(cudaMemcpyAsync(mm->host_diag, mm->diag_out, 10 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  SD_CUDA(cudaMemcpyAsync(mm->host_diag + 10, mm->err, sizeof(int), cudaMemcpyDeviceToHost, s));
   SD_CUDA(cudaStreamSynchronize(s));
+  if (*reinterpret_cast<const int*>(mm->host_diag + 10) != 0)
+    return fail(SD_ERR_TIMEOUT, "a bounded device-side wait of a stage kernel ran out since the mesh was created");
   const double* h = mm->host_diag;
   const double vol = h[4];
   out->ke = h[0] / vol;

@@ -65,6 +65,12 @@ struct StageParams {
   const float* bg_jump;  // [e][F][2][N^2] background jumps (rho0, p0), neighbour minus own
   double* divb;          // [n_e * N^3] (MODE_DIVB)
   unsigned long long* lam_max;  // trace kernel: running max of lambda (bits of a positive double)
+  // low-storage form of the mixed RK stages (sd_step): D = q^(s) - q^n in FP32,
+  // [9][n_e * dstride]; lsr_read: use D instead of q_n; lsr_write: 1 store D = t, 2 store D += t
+  float* dreg;
+  int64_t dstride;
+  int lsr_read, lsr_write;
+  int* err;  // device error word (bounded waits that ran out)
 };
 
 }  // namespace sd
@@ -96,6 +102,7 @@ struct sd_mesh {
   double* diag_out;         // [12]
   double* divb;             // [n_e * N^3]
   double* host_diag;        // pinned [12]
+  int* err;                 // device error word of the stage kernels
   int64_t device_bytes;
   sd::Ops<double> ops64;
   sd::Ops<float> ops32;
@@ -110,6 +117,8 @@ struct sd_background {
   const sd_mesh* mesh;
   float* rec;    // [5][n_e * N^3]
   float* jump;   // [n_e][6][2][N^2]
+  float* dreg;   // [9][n_e * dstride]: FP32 difference register of the mixed sd_step
+  int64_t dstride;
   double gamma;
 };
 

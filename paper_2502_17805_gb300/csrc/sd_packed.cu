@@ -200,6 +200,7 @@ sd_status sd_step_packed(sd_packer* pk, int32_t n, const sd_step_req* reqs, void
     P.bg = r.bg->rec;
     P.bg_jump = r.bg->jump;
     P.dyn = r.dyn;
+    P.err = m->err;
     // trace (+lambda) of q into tr0
     sd::StageParams Pt = P;
     Pt.q_in = r.q;
@@ -222,6 +223,11 @@ sd_status sd_step_packed(sd_packer* pk, int32_t n, const sd_step_req* reqs, void
       Ps.out = qout[s];
       Ps.tr_in = tin[s];
       Ps.tr_out = tout[s];
+      // low-storage form (as sd_step): D = q^(s) - q^n in the background's FP32 register
+      Ps.dreg = r.bg->dreg;
+      Ps.dstride = r.bg->dstride;
+      Ps.lsr_read = s > 0 ? 1 : 0;
+      Ps.lsr_write = s == 0 ? 1 : (s == 1 ? 2 : 0);
       T[(1 + s) * n + k] = Ps;
     }
     CTL[k] = {r.dyn, r.cfl, m->h_min * (m->ops64.xs[1] - m->ops64.xs[0]), r.phys.c_h};

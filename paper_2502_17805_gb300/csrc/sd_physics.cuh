@@ -227,3 +227,49 @@ __device__ __forceinline__ void riemann_mixed(const float* qo, const float* qn, 
 }
 
 }  // namespace sd
+
+namespace sd {
+
+// ---- TMA bulk copies (cp.async.bulk) into shared memory, completed on an
+// mbarrier.  Sources, destinations and sizes must be multiples of 16 bytes.
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned phase) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(phase)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on phase `phase` of the barrier.  On time-out the kernel's error
+// word is set, and the wait continues (again bounded) so that no copy is still
+// writing this CTA's shared memory when it exits.  Returns false on time-out.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned phase, int* err) {
+  for (int it = 0; it < (1 << 20); ++it)
+    if (mbar_try_wait(bar, phase)) return true;
+  if (err) atomicExch(err, 1);
+  for (int it = 0; it < (1 << 22); ++it)
+    if (mbar_try_wait(bar, phase)) break;
+  return false;
+}
+
+}  // namespace sd

@@ -33,7 +33,9 @@ struct DimsV2 {
   static constexpr int nX = 3 * NF * NV * N2;
   static constexpr int oE = oX + nX;                 // [NF][N]
   static constexpr int oD = oE + NF * N;             // [N][NF]
-  static constexpr int nF = oD + N * NF;
+  static constexpr int DSTRIDE = (N3 + 3) / 4 * 4;   // element stride of the FP32 difference register
+  static constexpr int oDs = (oD + N * NF + 3) / 4 * 4;  // [9][DSTRIDE]: D staged by a TMA bulk copy
+  static constexpr int nF = oDs + 9 * DSTRIDE;
   static constexpr size_t bytes = ((nF * 4) + 15) / 16 * 16;
 };
 
@@ -79,6 +81,23 @@ __device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops<fl
     chd = P.dyn[1];
   }
   const float ch = (float)chd;
+
+  // low-storage RK: the difference register D of this element is copied to
+  // shared memory by TMA while phases A-D run; the epilogue waits for it.
+  __shared__ __align__(8) unsigned long long dbar;
+  float* sDs = smem + DV::oDs;
+  const bool lsr = P.lsr_read != 0;
+  if (lsr) {
+    if (tid == 0) {
+      mbar_init(&dbar, 1);
+      constexpr unsigned plane_bytes = DV::DSTRIDE * 4;
+      mbar_expect_tx(&dbar, 9 * plane_bytes);
+      const float* src = P.dreg + e * DV::DSTRIDE;
+      const int64_t dplane = P.n_e * DV::DSTRIDE;
+#pragma unroll 1
+      for (int v = 0; v < 9; ++v) tma_load_1d(sDs + v * DV::DSTRIDE, src + v * dplane, plane_bytes, &dbar);
+    }
+  }
 
   // line role of this thread (B, D, F)
   const bool is_line = tid < NL;
@@ -213,6 +232,7 @@ __device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops<fl
   __syncthreads();
 
   // ---- E: residual, sources, RK sum (see stage_kernel<N, PolMixed> for the increment form)
+  if (lsr) mbar_wait_bounded(&dbar, 0u, P.err);
   for (int n = tid; n < N3; n += T) {
     const int i0 = n % N, j0 = (n / N) % N, k0 = n / N2;
     const float* D0 = sX + ((0 * NF + i0) * 11) * N2 + (j0 + N * k0);
@@ -240,6 +260,20 @@ __device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops<fl
       for (int v = 0; v < 9; ++v) P.out[v * P.plane + g] = f32_to_f64(Rv[v]);
     } else if (P.mode == MODE_DIVB) {
       P.divb[e * N3 + n] = f32_to_f64(divB);
+    } else if (P.lsr_read || P.lsr_write) {
+      // low-storage form: t = -a D + b dt R, q_out = q_in + t, D <- D + t, with D = q_in - q_n
+      const float bdt = (float)(P.rk_b * dt);
+      const float a = (float)P.rk_a;
+      const int64_t gd = e * DV::DSTRIDE + n, dplane = P.n_e * DV::DSTRIDE;
+#pragma unroll
+      for (int v = 0; v < 9; ++v) {
+        const double qin = __ldg(P.q_in + v * P.plane + g);
+        const float Dv = P.lsr_read ? sDs[v * DV::DSTRIDE + n] : 0.0f;
+        const float t = fmaf(-a, Dv, bdt * Rv[v]);
+        P.out[v * P.plane + g] = qin + f32_to_f64(t);
+        if (P.lsr_write) P.dreg[v * dplane + gd] = (P.lsr_write == 1) ? t : Dv + t;
+        sQ[v * N3 + n] = q[v] + t;  // q' of the new state (this thread's own point)
+      }
     } else {
       const float bdt = (float)(P.rk_b * dt);
       const float a = (float)P.rk_a;

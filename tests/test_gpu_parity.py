@@ -240,3 +240,22 @@ def test_step_equals_three_stages():
     qb, wb = gm.to_device(q0), gm.empty_state()
     gm.rk_step(gph, float(dt), qb, wb)
     assert torch.equal(qa, qb)
+
+
+def test_mixed_sd_step_low_storage_matches_oracle():
+    """sd_step on the FP32-mixed path (FP32 difference register instead of q^n) follows the FP64
+    oracle over three steps, given each step's dt and c_h."""
+    gm, om, gph, oph, q0, qb = _mixed_case(3, 2, 6, 2.5, seed=9)
+    bg = gm.background(gph, gm.to_device(qb))
+    gph.c_h = 0.0  # c_h = lambda_max each step
+    q, work = gm.to_device(q0), gm.empty_state()
+    dts = torch.zeros(2, dtype=torch.float64, device="cuda")
+    qo = q0
+    for _ in range(3):
+        gm.step(gph, 0.2, q, work, prec=sdmhd.SD_FP32_MIXED, bg=bg, dt_out=dts)
+        dt, ch = dts.cpu().numpy()
+        oph.c_h = float(ch)
+        qo = om.rk_step(oph, float(dt), qo)
+    dg, do = gm.to_host(q) - q0, qo - q0
+    err = np.abs(dg - do).max(axis=(1, 2)) / np.maximum(np.abs(do).max(axis=(1, 2)), 1e-300)
+    assert err.max() <= 1e-5, err
