@@ -17,10 +17,18 @@
 namespace {
 
 thread_local std::string g_err;
+thread_local std::string g_stale;  // a CUDA error left pending by an earlier, unrelated call
 
 sd_status fail(sd_status st, const std::string& msg) {
-  g_err = msg;
+  g_err = g_stale.empty() ? msg : msg + " (a CUDA error was already pending before this call: " + g_stale + ")";
   return st;
+}
+
+// Clear a pending error of this thread's CUDA runtime state, so that the error
+// checks of this call see only this call's work; remember it for the message.
+void take_stale() {
+  const cudaError_t e = cudaGetLastError();
+  g_stale = e == cudaSuccess ? std::string() : std::string(cudaGetErrorString(e));
 }
 
 sd_status cuda_fail(cudaError_t e, const char* what) {
@@ -35,17 +43,21 @@ sd_status cuda_fail(cudaError_t e, const char* what) {
 
 struct DeviceGuard {
   int prev = -1;
-  bool ok = true;
+  bool switched = false;
   explicit DeviceGuard(int dev) {
+    take_stale();
     if (cudaGetDevice(&prev) != cudaSuccess) {
-      ok = false;
+      prev = -1;
+      cudaGetLastError();
       return;
     }
-    if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    if (prev != dev) {
+      switched = cudaSetDevice(dev) == cudaSuccess;
+      if (!switched) cudaGetLastError();
+    }
   }
   ~DeviceGuard() {
-    int cur;
-    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    if (switched && cudaSetDevice(prev) != cudaSuccess) cudaGetLastError();
   }
 };
 
@@ -414,6 +426,7 @@ sd_status sd_mesh_create(const sd_mesh_desc* desc, void* stream, sd_mesh** out) 
     }
 
   // ---- device objects
+  take_stale();
   sd_mesh* m = new sd_mesh();
   if (cudaGetDevice(&m->device) != cudaSuccess) {
     delete m;
@@ -570,6 +583,7 @@ sd_status sd_background_create(const sd_mesh* m, const sd_phys* ph, const double
   bg->jump = nullptr;
   bg->dreg = nullptr;
   bg->dstride = (N3 + 3) / 4 * 4;
+  bg->device = m->device;
   double *q0 = nullptr, *R0 = nullptr;
   const size_t state = 9 * ne * m->stride;
   cudaError_t err = cudaMalloc((void**)&bg->rec, 5 * ne * N3 * sizeof(float));
@@ -618,7 +632,7 @@ sd_status sd_background_create(const sd_mesh* m, const sd_phys* ph, const double
 
 sd_status sd_background_destroy(sd_background* bg) {
   if (!bg) return SD_OK;
-  DeviceGuard g(bg->mesh->device);
+  DeviceGuard g(bg->device);
   cudaFree(bg->rec);
   cudaFree(bg->jump);
   cudaFree(bg->dreg);

@@ -120,6 +120,7 @@ struct sd_background {
   float* dreg;   // [9][n_e * dstride]: FP32 difference register of the mixed sd_step
   int64_t dstride;
   double gamma;
+  int device;
 };
 
 namespace sd {

@@ -59,6 +59,7 @@ sd_status sd_residual_noalloc(const sd_mesh* m, const sd_phys* ph, const double*
                         "mesh too large for sd_residual_noalloc: its face traces need " +
                             std::to_string(need * sizeof(double)) + " bytes, the fixed scratch holds " +
                             std::to_string(kNoAllocScratchBytes) + " (n_elements * 6 * 9 * N^2 * 8 bytes)");
+  cudaGetLastError();  // a pending error of an earlier, unrelated call is not this call's
   int dev = -1;
   cudaError_t err = cudaGetDevice(&dev);
   if (err != cudaSuccess) return noalloc_fail(SD_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(err));

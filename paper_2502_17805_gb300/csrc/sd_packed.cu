@@ -124,6 +124,7 @@ sd_status sd_step_packed(sd_packer* pk, int32_t n, const sd_step_req* reqs, void
   if (n < 0 || n > pk->cap) return pk_fail(SD_ERR_INVALID_ARGUMENT, "request count exceeds the packer's capacity");
   if (n == 0) return SD_OK;
   if (!reqs) return pk_fail(SD_ERR_INVALID_ARGUMENT, "reqs is NULL");
+  cudaGetLastError();  // a pending error of an earlier, unrelated call is not this call's
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev != pk->device)
     return pk_fail(SD_ERR_INVALID_ARGUMENT, "the current device is not the packer's device");

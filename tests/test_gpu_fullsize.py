@@ -75,10 +75,13 @@ def test_shell41k_mixed_residual_sampled():
     q0, qb = om.state_init(oph, sdref.INIT_SHELL_POLYTROPE, prm, seed=0, background=True)
     bg = gm.background(gph, gm.to_device(qb))
     elems = _sample(gm.n_e, seed=1)
-    Ro, _ = om.residual_elements(oph, q0, elems)
+    Ro, s = om.residual_elements(oph, q0, elems)
     R = _gather(gm, gm.residual(gph, gm.to_device(q0), prec=sdmhd.SD_FP32_MIXED, bg=bg), elems)
-    err = np.abs(R - Ro).max(axis=(0, 2)) / np.abs(Ro).max(axis=(0, 2))
-    assert err.max() <= 1e-5, err
+    # per-variable bound of the mixed path: 1e-5 relative, or FP32 round-off of the un-cancelled terms
+    # for a component that cancels below it (the energy of the fluid at rest)
+    err = np.abs(R - Ro).max(axis=(0, 2))
+    bound = 1e-5 * np.abs(Ro).max(axis=(0, 2)) + 4 * 2.0 ** -24 * s
+    assert np.all(err <= bound), (err, bound)
 
 
 def test_shell221k_fp64_residual_sampled():

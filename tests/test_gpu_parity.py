@@ -4,7 +4,10 @@ Inputs come from the oracle or the seeded input generators only.  Tolerances:
   FP64 residual:  |g - o| <= 1e-12 (|o| + s_v) per entry, s_v the oracle's
                   un-cancelled magnitude of variable v (sum |D F| / |J| + |M|);
   FP64 states:    1e-12 of the variable's magnitude after one stage or step;
-  FP32-mixed:     max |g - o| / max |o| <= 1e-5 per variable.
+  FP32-mixed:     max |g - o| <= 1e-5 max |o| + 4 eps32 s_v per variable
+                  (eps32 = 2^-24): 1e-5 relative, except that a component whose
+                  residual cancels to below FP32 resolution of its terms (the
+                  energy of a fluid at rest) is held to FP32 round-off of them.
 """
 import math
 
@@ -37,6 +40,16 @@ def _pair(N, v, h, **kw):
 
 def _phys(**kw):
     return sdmhd.Phys(**kw), sdref.Phys(**kw)
+
+
+EPS32 = 2.0 ** -24
+
+
+def mixed_ok(g, o, s, scale=1.0):
+    """per-variable FP32-mixed bound; g, o: (9, ...) arrays; s: (9,) un-cancelled magnitudes"""
+    err = np.abs(g - o).reshape(9, -1).max(axis=1)
+    bound = 1e-5 * np.abs(o).reshape(9, -1).max(axis=1) + 4 * EPS32 * scale * s
+    return bool(np.all(err <= bound)), err, bound
 
 
 def _rel_c19(g, o, s):
@@ -208,7 +221,21 @@ def test_mixed_residual_stratified_shell():
     gm, om, gph, oph, q0, qb = _mixed_case(4, 2, 6, 3.0)
     bg = gm.background(gph, gm.to_device(qb))
     R = gm.to_host(gm.residual(gph, gm.to_device(q0), prec=sdmhd.SD_FP32_MIXED, bg=bg))
-    Ro, _ = om.residual(oph, q0)
+    Ro, s = om.residual(oph, q0)
+    ok, err, bound = mixed_ok(R, Ro, s)
+    assert ok, (err, bound)
+
+
+def test_mixed_residual_developed_flow_strict():
+    """With a seeded velocity field on the stratified shell every component of the residual is far
+    above FP32 resolution; there the mixed path meets 1e-5 relative per variable outright."""
+    gm, om, gph, oph, q0, qb = _mixed_case(4, 2, 6, 3.0, seed=2)
+    rng = np.random.default_rng(17)
+    q1 = q0.copy()
+    q1[1:4] += rng.uniform(-1e-2, 1e-2, size=q1[1:4].shape) * q1[0]
+    bg = gm.background(gph, gm.to_device(qb))
+    R = gm.to_host(gm.residual(gph, gm.to_device(q1), prec=sdmhd.SD_FP32_MIXED, bg=bg))
+    Ro, _ = om.residual(oph, q1)
     err = np.abs(R - Ro).max(axis=(1, 2)) / np.abs(Ro).max(axis=(1, 2))
     assert err.max() <= 1e-5, err
 
@@ -220,10 +247,10 @@ def test_mixed_stage_stratified_shell():
     q, work = gm.to_device(q0), gm.empty_state()
     gm.rk_step(gph, dt, q, work, prec=sdmhd.SD_FP32_MIXED, bg=bg)
     qo = om.rk_step(oph, dt, q0)
-    # compare the change over the step, per variable
-    dg, do = gm.to_host(q) - q0, qo - q0
-    err = np.abs(dg - do).max(axis=(1, 2)) / np.maximum(np.abs(do).max(axis=(1, 2)), 1e-300)
-    assert err.max() <= 1e-5, err
+    # compare the change over the step, per variable (three stages of dt R)
+    _, s = om.residual(oph, q0)
+    ok, err, bound = mixed_ok(gm.to_host(q) - q0, qo - q0, s, scale=3 * dt)
+    assert ok, (err, bound)
 
 
 def test_step_equals_three_stages():
@@ -256,6 +283,6 @@ def test_mixed_sd_step_low_storage_matches_oracle():
         dt, ch = dts.cpu().numpy()
         oph.c_h = float(ch)
         qo = om.rk_step(oph, float(dt), qo)
-    dg, do = gm.to_host(q) - q0, qo - q0
-    err = np.abs(dg - do).max(axis=(1, 2)) / np.maximum(np.abs(do).max(axis=(1, 2)), 1e-300)
-    assert err.max() <= 1e-5, err
+    _, s = om.residual(oph, q0)
+    ok, err, bound = mixed_ok(gm.to_host(q) - q0, qo - q0, s, scale=3 * 3 * float(dt))
+    assert ok, (err, bound)
