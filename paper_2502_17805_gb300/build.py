@@ -15,6 +15,10 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsdmhd.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 GENCODE = "arch=compute_103a,code=sm_103a"
+# The FP32-mixed kernels (tolerance 1e-5) use approximate FP32 division and square
+# root and flush FP32 subnormals; FP64 arithmetic is unaffected by these flags.
+FAST_FP32 = ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"]
+FAST_FP32_SOURCES = {"sd_stage_mixed.cu"}
 
 
 def _nvcc() -> str:
@@ -54,8 +58,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-        if force or _stale(obj, [src] + hdrs):
-            cmd = [nvcc] + flags + ["-c", src, "-o", obj]
+        if force or _stale(obj, [src] + hdrs + [os.path.abspath(__file__)]):
+            extra = FAST_FP32 if os.path.basename(src) in FAST_FP32_SOURCES else []
+            cmd = [nvcc] + flags + extra + ["-c", src, "-o", obj]
             r = subprocess.run(cmd, capture_output=True, text=True)
             if r.returncode != 0:
                 raise RuntimeError("nvcc failed for %s:\n%s" % (src, r.stderr))

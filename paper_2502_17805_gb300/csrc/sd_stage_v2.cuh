@@ -31,10 +31,8 @@ struct DimsV2 {
   static constexpr int oQ = 0;                       // [11][N3]
   static constexpr int oX = oQ + NV * N3;            // [3][NF][11][N2]
   static constexpr int nX = 3 * NF * NV * N2;
-  static constexpr int oE = oX + nX;                 // [NF][N]
-  static constexpr int oD = oE + NF * N;             // [N][NF]
   static constexpr int DSTRIDE = (N3 + 3) / 4 * 4;   // element stride of the FP32 difference register
-  static constexpr int oDs = (oD + N * NF + 3) / 4 * 4;  // [9][DSTRIDE]: D staged by a TMA bulk copy
+  static constexpr int oDs = (oX + nX + 3) / 4 * 4;  // [9][DSTRIDE]: D staged by a TMA bulk copy
   static constexpr int nF = oDs + 9 * DSTRIDE;
   static constexpr size_t bytes = ((nF * 4) + 15) / 16 * 16;
 };
@@ -63,14 +61,7 @@ __device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops<fl
   float* smem = reinterpret_cast<float*>(smem_raw);
   float* sQ = smem + DV::oQ;
   float* sX = smem + DV::oX;
-  float* sE = smem + DV::oE;
-  float* sD = smem + DV::oD;
-
   const int tid = threadIdx.x;
-  for (int i = tid; i < NF * N; i += T) {
-    sE[i] = ops.E[i];
-    sD[i] = ops.D[i];
-  }
   const float* Sfam = reinterpret_cast<const float*>(P.Sfam) + e * (9 * N2 * NF);
   const float gamma = (float)P.gamma;
   const float gm1 = gamma - 1.0f;
@@ -136,7 +127,7 @@ __device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops<fl
       for (int f = 0; f <= N; ++f) {
         float s = 0.0f;
 #pragma unroll
-        for (int i = 0; i < N; ++i) s = fmaf(sE[f * N + i], ql[i], s);
+        for (int i = 0; i < N; ++i) s = fmaf(ops.E[f * N + i], ql[i], s);  // operator from the parameter bank
         X[(f * 11 + v) * N2] = s;
       }
     }
@@ -224,7 +215,7 @@ __device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops<fl
       for (int i = 0; i < N; ++i) {
         float s = 0.0f;
 #pragma unroll
-        for (int f = 0; f <= N; ++f) s = fmaf(sD[i * NF + f], fv[f], s);
+        for (int f = 0; f <= N; ++f) s = fmaf(ops.D[i * NF + f], fv[f], s);
         X[(i * 11 + v) * N2] = s;
       }
     }
@@ -299,8 +290,8 @@ __device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops<fl
 #pragma unroll
         for (int i = 0; i < N; ++i) {
           const float x = sQ[v * N3 + lbase + i * lstride];
-          s0 = fmaf(sE[i], x, s0);
-          s1 = fmaf(sE[N * N + i], x, s1);
+          s0 = fmaf(ops.E[i], x, s0);
+          s1 = fmaf(ops.E[N * N + i], x, s1);
         }
         Tr[v * N2] = s0;
         Tr[9 * N2 + v * N2] = s1;
