@@ -40,6 +40,9 @@ struct Smem {
   static constexpr int nR = oD + N * NF;
   static constexpr size_t bytesR = ((nR * sizeof(R)) + 15) / 16 * 16;
   static constexpr size_t bytes = bytesR;
+  // the trace kernel needs only the state and the extrapolation table
+  static constexpr int oTE = NV * N3;
+  static constexpr size_t trace_bytes = ((oTE + NF * N) * sizeof(R) + 15) / 16 * 16;
 };
 
 // index of solution point (i along d; a, b the other two directions in increasing order)
@@ -130,7 +133,7 @@ __device__ __forceinline__ void trace_body(const StageParams& P, const Ops<typen
   constexpr int NF = N + 1, BLK = Dims<N>::BLK;
   using S = Smem<N, Pol>;
   R* sQ = reinterpret_cast<R*>(smem) + S::oQ;
-  R* sE = reinterpret_cast<R*>(smem) + S::oE;
+  R* sE = reinterpret_cast<R*>(smem) + S::oTE;
   for (int i = threadIdx.x; i < NF * N; i += BLK) sE[i] = ops.E[i];
   double lam = 0.0;
   load_element<N, Pol>(P, P.q_in, e, sQ, P.lam_max ? &lam : nullptr);
@@ -215,31 +218,39 @@ __device__ __forceinline__ void sources_fp64(const StageParams& P, const double*
   M[8] -= P.alpha * q[8];
 }
 
+// Uniform FP32 constants of the mixed sources, converted once per thread.
+struct MixedConsts {
+  float GM, om2, alpha;
+  int gravity, coriolis, powell;
+};
+
+__device__ __forceinline__ MixedConsts mixed_consts(const StageParams& P) {
+  return MixedConsts{(float)P.GM, 2.0f * (float)P.omega, (float)P.alpha, P.gravity, P.coriolis, P.powell};
+}
+
 // Sources of the perturbation (rho0 g lives in the FP64 background residual).
-__device__ __forceinline__ void sources_mixed(const StageParams& P, const float* q, float divB, float x0, float x1,
+__device__ __forceinline__ void sources_mixed(const MixedConsts& C, const float* q, float divB, float x0, float x1,
                                               float x2, float* M) {
   const float rho = q[9] + q[0];
   const float ir = 1.0f / rho;
   const float ux = q[1] * ir, uy = q[2] * ir, uz = q[3] * ir;
 #pragma unroll
   for (int v = 0; v < 9; ++v) M[v] = 0.0f;
-  if (P.gravity) {
+  if (C.gravity) {
     const float r2 = x0 * x0 + x1 * x1 + x2 * x2;
     const float rr = rsqrtf(r2);
     const float ir3 = rr * rr * rr;
-    const float GM = (float)P.GM;
-    const float gx = -GM * x0 * ir3, gy = -GM * x1 * ir3, gz = -GM * x2 * ir3;
+    const float gx = -C.GM * x0 * ir3, gy = -C.GM * x1 * ir3, gz = -C.GM * x2 * ir3;
     M[1] += q[0] * gx;
     M[2] += q[0] * gy;
     M[3] += q[0] * gz;
     M[4] += q[1] * gx + q[2] * gy + q[3] * gz;
   }
-  if (P.coriolis) {
-    const float om2 = 2.0f * (float)P.omega;
-    M[1] += om2 * q[2];
-    M[2] -= om2 * q[1];
+  if (C.coriolis) {
+    M[1] += C.om2 * q[2];
+    M[2] -= C.om2 * q[1];
   }
-  if (P.powell) {
+  if (C.powell) {
     const float uB = ux * q[5] + uy * q[6] + uz * q[7];
     M[1] -= divB * q[5];
     M[2] -= divB * q[6];
@@ -249,7 +260,7 @@ __device__ __forceinline__ void sources_mixed(const StageParams& P, const float*
     M[6] -= divB * uy;
     M[7] -= divB * uz;
   }
-  M[8] -= (float)P.alpha * q[8];
+  M[8] -= C.alpha * q[8];
 }
 
 template <int N, class Pol>
@@ -435,7 +446,7 @@ __global__ void __launch_bounds__(Dims<N>::BLK) stage_kernel(const StageParams P
       float q[11], M[9], Rv[9];
 #pragma unroll
       for (int v = 0; v < 11; ++v) q[v] = sQ[v * N3 + n];
-      sources_mixed(P, q, divB, Xe[n], Xe[N3 + n], Xe[2 * N3 + n], M);
+      sources_mixed(mixed_consts(P), q, divB, Xe[n], Xe[N3 + n], Xe[2 * N3 + n], M);
 #pragma unroll
       for (int v = 0; v < 9; ++v) Rv[v] = -acc[v] * iJ + M[v];
       const int64_t gb = e * N3 + n, bp = P.n_e * N3;
@@ -475,7 +486,7 @@ __global__ void __launch_bounds__(Dims<N>::BLK) stage_kernel(const StageParams P
 template <int N, class Pol>
 cudaError_t launch_stage_t(const StageParams& P, const Ops<typename Pol::R>& ops, bool traces_only, cudaStream_t s) {
   using Sm = Smem<N, Pol>;
-  const size_t bytes = Sm::bytes;
+  const size_t bytes = traces_only ? Sm::trace_bytes : Sm::bytes;
   auto kern = traces_only ? trace_kernel<N, Pol> : stage_kernel<N, Pol>;
   if (bytes > 48 * 1024) {
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);

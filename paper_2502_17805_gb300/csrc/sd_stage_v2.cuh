@@ -72,6 +72,13 @@ __device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops<fl
     chd = P.dyn[1];
   }
   const float ch = (float)chd;
+  // uniform values of the epilogue, converted once
+  const MixedConsts MC = mixed_consts(P);
+  const float bdt = (float)(P.rk_b * dt);
+  const float rka = (float)P.rk_a;
+  const int mode = P.mode, lsr_read = P.lsr_read, lsr_write = P.lsr_write;
+  const bool classic_qn = P.rk_a != 0.0;
+  const int64_t n_e = P.n_e, stride = P.stride, plane = P.plane;
 
   // low-storage RK: the difference register D of this element is copied to
   // shared memory by TMA while phases A-D run; the epilogue waits for it.
@@ -98,17 +105,18 @@ __device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops<fl
   line_geom<N>(ld, lL, lbase, lstride);
 
   // ---- A: load
+  const double inv_gm1 = P.inv_gm1;
   for (int n = tid; n < N3; n += T) {
-    const int64_t g = e * P.stride + n;
+    const int64_t g = e * stride + n;
     const int64_t gb = e * N3 + n;
-    const float r0 = __ldg(P.bg + gb), p0 = __ldg(P.bg + P.n_e * N3 + gb);
+    const float r0 = __ldg(P.bg + gb), p0 = __ldg(P.bg + n_e * N3 + gb);
     double qv[9];
 #pragma unroll
-    for (int v = 0; v < 9; ++v) qv[v] = __ldg(P.q_in + v * P.plane + g);
+    for (int v = 0; v < 9; ++v) qv[v] = __ldg(P.q_in + v * plane + g);
     sQ[0 * N3 + n] = f64_to_f32(qv[0] - f32_to_f64(r0));
 #pragma unroll
     for (int v = 1; v < 9; ++v) sQ[v * N3 + n] = f64_to_f32(qv[v]);
-    sQ[4 * N3 + n] = f64_to_f32(fma(-f32_to_f64(p0), P.inv_gm1, qv[4]));
+    sQ[4 * N3 + n] = f64_to_f32(fma(-f32_to_f64(p0), inv_gm1, qv[4]));
     sQ[9 * N3 + n] = r0;
     sQ[10 * N3 + n] = p0;
   }
@@ -238,49 +246,45 @@ __device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops<fl
     float q[11], M[9], Rv[9];
 #pragma unroll
     for (int v = 0; v < 11; ++v) q[v] = sQ[v * N3 + n];
-    sources_mixed(P, q, divB, __ldg(Xe + n), __ldg(Xe + N3 + n), __ldg(Xe + 2 * N3 + n), M);
+    sources_mixed(MC, q, divB, __ldg(Xe + n), __ldg(Xe + N3 + n), __ldg(Xe + 2 * N3 + n), M);
 #pragma unroll
     for (int v = 0; v < 9; ++v) Rv[v] = -acc[v] * iJ + M[v];
-    const int64_t gb = e * N3 + n, bp = P.n_e * N3;
+    const int64_t gb = e * N3 + n, bp = n_e * N3;
     Rv[1] += __ldg(P.bg + 2 * bp + gb);
     Rv[2] += __ldg(P.bg + 3 * bp + gb);
     Rv[3] += __ldg(P.bg + 4 * bp + gb);
-    const int64_t g = e * P.stride + n;
-    if (P.mode == MODE_RESIDUAL) {
+    const int64_t g = e * stride + n;
+    if (mode == MODE_RESIDUAL) {
 #pragma unroll
-      for (int v = 0; v < 9; ++v) P.out[v * P.plane + g] = f32_to_f64(Rv[v]);
-    } else if (P.mode == MODE_DIVB) {
+      for (int v = 0; v < 9; ++v) P.out[v * plane + g] = f32_to_f64(Rv[v]);
+    } else if (mode == MODE_DIVB) {
       P.divb[e * N3 + n] = f32_to_f64(divB);
-    } else if (P.lsr_read || P.lsr_write) {
+    } else if (lsr_read || lsr_write) {
       // low-storage form: t = -a D + b dt R, q_out = q_in + t, D <- D + t, with D = q_in - q_n
-      const float bdt = (float)(P.rk_b * dt);
-      const float a = (float)P.rk_a;
-      const int64_t gd = e * DV::DSTRIDE + n, dplane = P.n_e * DV::DSTRIDE;
+      const int64_t gd = e * DV::DSTRIDE + n, dplane = n_e * DV::DSTRIDE;
 #pragma unroll
       for (int v = 0; v < 9; ++v) {
-        const double qin = __ldg(P.q_in + v * P.plane + g);
-        const float Dv = P.lsr_read ? sDs[v * DV::DSTRIDE + n] : 0.0f;
-        const float t = fmaf(-a, Dv, bdt * Rv[v]);
-        P.out[v * P.plane + g] = qin + f32_to_f64(t);
-        if (P.lsr_write) P.dreg[v * dplane + gd] = (P.lsr_write == 1) ? t : Dv + t;
+        const double qin = __ldg(P.q_in + v * plane + g);
+        const float Dv = lsr_read ? sDs[v * DV::DSTRIDE + n] : 0.0f;
+        const float t = fmaf(-rka, Dv, bdt * Rv[v]);
+        P.out[v * plane + g] = qin + f32_to_f64(t);
+        if (lsr_write) P.dreg[v * dplane + gd] = (lsr_write == 1) ? t : Dv + t;
         sQ[v * N3 + n] = q[v] + t;  // q' of the new state (this thread's own point)
       }
     } else {
-      const float bdt = (float)(P.rk_b * dt);
-      const float a = (float)P.rk_a;
 #pragma unroll
       for (int v = 0; v < 9; ++v) {
-        const double qin = __ldg(P.q_in + v * P.plane + g);
+        const double qin = __ldg(P.q_in + v * plane + g);
         float t = bdt * Rv[v];
-        if (P.rk_a != 0.0) t = fmaf(a, f64_to_f32(__ldg(P.q_n + v * P.plane + g) - qin), t);
-        P.out[v * P.plane + g] = qin + f32_to_f64(t);
+        if (classic_qn) t = fmaf(rka, f64_to_f32(__ldg(P.q_n + v * plane + g) - qin), t);
+        P.out[v * plane + g] = qin + f32_to_f64(t);
         sQ[v * N3 + n] = q[v] + t;  // q' of the new state (this thread's own point)
       }
     }
   }
 
   // ---- F: face traces of the new state
-  if (P.mode == MODE_RK && P.tr_out) {
+  if (mode == MODE_RK && P.tr_out) {
     __syncthreads();
     if (is_line) {
       float* Tr = reinterpret_cast<float*>(P.tr_out) + (e * 6 + 2 * ld) * 9 * N2 + lL;
@@ -340,7 +344,7 @@ cudaError_t launch_packed_t(bool traces, const StageParams* tab, const int64_t* 
                             const Ops<float>& ops, cudaStream_t s) {
   if (blocks == 0) return cudaSuccess;
   if (traces) {
-    const size_t bytes = Smem<N, PolMixed>::bytes;
+    const size_t bytes = Smem<N, PolMixed>::trace_bytes;
     if (bytes > 40 * 1024) {
       cudaError_t err = cudaFuncSetAttribute(trace_kernel_packed<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)bytes);
