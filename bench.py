@@ -61,6 +61,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=64)
     ap.add_argument("--serve-budget-gb", type=float, default=24.0)
     return ap.parse_args()
@@ -289,6 +290,51 @@ def run_serving(n_requests: int, budget_gb: float):
                         % (n_requests, n_requests - 1)}
 
 
+def accuracy_report(steps: int = 20):
+    """Error of the FP32-mixed path against the FP64 oracle over `steps` SSP-RK3 steps of the
+    1,536-element shell (N = 6, N_rho = 1 recipe), both advanced with the dt and c_h sequence of the
+    mixed run; per variable max |mixed - oracle| / max |oracle change|.  Also the relative drift of
+    the total energy and the final max|div B| for both GPU paths."""
+    import numpy as np
+    import torch
+
+    from oracle import sdref
+    from paper_2502_17805_gb300 import sdmhd
+    wl = WORKLOADS["shell1536"]
+    mesh, phys, q0, bg, params = make_case(wl)
+    from paper_2502_17805_gb300 import inputs
+    v, h = inputs.shell_mesh(wl["nz"], wl["nr"])
+    om = sdref.Mesh(wl["N"], v, h, geom=1, r_in=0.70, r_out=0.98, bc_in=sdref.BC_WALL_CONDUCTING,
+                    bc_out=sdref.BC_WALL_RADIAL)
+    oph = sdref.Phys(gamma=phys.gamma, GM=phys.GM, omega=phys.omega, glm_alpha=phys.glm_alpha, c_h=0.0,
+                     powell=1, gravity=1, coriolis=1)
+    qo = om.state_init(oph, sdref.INIT_SHELL_POLYTROPE, params, seed=0)
+    q, work = mesh.to_device(qo), mesh.empty_state()
+    q64 = q.clone()
+    dts = torch.zeros(2, dtype=torch.float64, device="cuda")
+    d0 = mesh.diagnostics(phys, q)
+    for _ in range(steps):
+        mesh.step(phys, CFL, q, work, prec=sdmhd.SD_FP32_MIXED, bg=bg, dt_out=dts)
+        dt, ch = (float(x) for x in dts.cpu().numpy())
+        oph.c_h = ch
+        qo = om.rk_step(oph, dt, qo)
+        ph64 = sdmhd.Phys(**{k: getattr(phys, k) for k in ("gamma", "GM", "omega", "glm_alpha", "powell",
+                                                          "gravity", "coriolis")})
+        ph64.c_h = ch
+        mesh.rk_step(ph64, dt, q64, work)
+    qm = mesh.to_host(q)
+    q_init = om.state_init(oph, sdref.INIT_SHELL_POLYTROPE, params, seed=0)
+    err = np.abs(qm - qo).max(axis=(1, 2)) / np.maximum(np.abs(qo - q_init).max(axis=(1, 2)), 1e-300)
+    dm, d64 = mesh.diagnostics(phys, q), mesh.diagnostics(phys, q64)
+    names = ["rho", "mx", "my", "mz", "E", "Bx", "By", "Bz", "psi"]
+    return {"workload": wl["desc"], "steps": steps,
+            "mixed_vs_oracle_rel_err_of_change": {k: float(x) for k, x in zip(names, err)},
+            "energy_drift_mixed": dm["energy"] / d0["energy"] - 1.0,
+            "energy_drift_fp64": d64["energy"] / d0["energy"] - 1.0,
+            "ke_mixed": dm["ke"], "ke_fp64": d64["ke"], "eb_mixed": dm["eb"], "eb_fp64": d64["eb"],
+            "max_divb_mixed": dm["max_divb"], "max_divb_fp64": d64["max_divb"]}
+
+
 class OracleSample:
     """The CPU oracle, as it stands, on a bounded sample of the workload: one step is the work of one
     SSP-RK3 step (three residual evaluations) on `n_elems` random elements of the same shell, from the
@@ -398,6 +444,8 @@ def run_ours(args):
         ke = max(1, min(args.steps, 10))
         out["e2e"] = {"value": n_pts * ke * world / (ems / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                       "d2h_bytes_per_step": d2h, "ms_per_step": ems / ke}
+    if rank == 0 and world == 1 and not args.no_accuracy:
+        out["accuracy"] = accuracy_report()
     if rank == 0 and world == 1 and not args.no_serve:
         del q, work, q64, q2
         import torch

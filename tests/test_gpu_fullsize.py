@@ -95,3 +95,28 @@ def test_shell221k_fp64_residual_sampled():
     R = _gather(gm, gm.residual(gph, q), elems)
     err = (np.abs(R - Ro) / (np.abs(Ro) + s[None, :, None])).max()
     assert err < TOL64, err
+
+
+def test_shell1536_hundred_fp64_steps():
+    """The 1,536-element N=6 shell (N_rho = 1, GM = 1, Omega = 1, noise 1e-4 seed 0, dipole 1e-6):
+    100 SSP-RK3 steps through sd_step (device dt and c_h) against the oracle stepping with its own
+    lambda_max each step."""
+    gm, om = _shell(8, 4)
+    gph, oph = _phys(ch=0.0)
+    prm = [1.0, 0.70, 0.98, 1.0, 1.0, 1e-4, 1e-6]
+    q0 = om.state_init(oph, sdref.INIT_SHELL_POLYTROPE, prm, seed=0)
+    q, work = gm.to_device(q0), gm.empty_state()
+    xs = sdref.nodes(6)[0]
+    dx = om.info()["h_min"] * (xs[1] - xs[0])
+    dts = torch.zeros(2, dtype=torch.float64, device="cuda")
+    qo, dt_err = q0, 0.0
+    for _ in range(100):
+        gm.step(gph, 0.2, q, work, dt_out=dts)
+        lam = om.diagnostics(oph, qo)["lambda_max"]
+        oph.c_h = lam
+        qo = om.rk_step(oph, 0.2 * dx / lam, qo)
+        dt_err = max(dt_err, abs(float(dts[0]) / (0.2 * dx / lam) - 1.0))
+    change = np.abs(qo - q0).max(axis=(1, 2))
+    err = np.abs(gm.to_host(q) - qo).max(axis=(1, 2))
+    # relative to the change over the run; psi and the momentum start at zero
+    assert dt_err < 1e-12 and np.all(err <= 1e-9 * np.maximum(change, 1e-300)), (dt_err, err / change)
