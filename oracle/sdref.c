@@ -23,8 +23,10 @@
  *  R7 the divergence of B in the Powell terms is the discrete SD divergence
  *     with the BR1 face average of the normal field.
  *  R8 no GLM terms beyond those printed (no advection of psi).
- *  R9 inviscid wall ghost: rho, p, psi, E copied; u -> u - 2(u.n)n;
- *     conducting: B -> B - 2(B.n)n; radial: B -> 2(B.n)n - B.
+ *  R9 inviscid wall ghost: rho, p, E copied; u -> u - 2(u.n)n;
+ *     conducting: B -> B - 2(B.n)n, psi copied (B_n = 0);
+ *     radial: B -> 2(B.n)n - B, psi -> -psi (B_t = 0, B_n free, so the
+ *     GLM pair (B_n, psi) takes its one wall condition on psi = 0).
  *  R10 transfinite map: edge-based Gordon-Hall blend (three bilinear edge
  *     projectors minus twice the trilinear corner projector); constant-radius
  *     edges are great-circle arcs, radial edges straight; the geometry is the
@@ -630,6 +632,7 @@ static void ghost_state(const double* q, const double* n, int bc, const sdref_ph
     for (int d = 0; d < 3; ++d) g[5 + d] = q[5 + d] - 2.0 * Bn * n[d];
   } else {
     for (int d = 0; d < 3; ++d) g[5 + d] = 2.0 * Bn * n[d] - q[5 + d];
+    g[8] = -q[8];
   }
 }
 

@@ -144,9 +144,11 @@ __device__ __forceinline__ R pressure_full(const R* q, R gm1) {
                                   q[7] * q[7] + q[8] * q[8]));
 }
 
-// Wall ghost state: rho, p, psi and E copied, U reflected; conducting walls
-// reflect B, radial walls reverse its tangential part.  For the mixed policy the
-// same rule applies to the perturbation (the background is symmetric).
+// Wall ghost state: rho, p and E copied, U reflected.  Conducting walls reflect
+// B (B_n = 0) and copy psi; radial walls reverse the tangential part of B and
+// leave B_n free, so the GLM pair (B_n, psi) takes its one wall condition on
+// psi = 0 (psi reversed).  For the mixed policy the same rule applies to the
+// perturbation (the background is symmetric and has no psi).
 template <typename R>
 __device__ __forceinline__ void wall_ghost(const R* q, R nx, R ny, R nz, int bc, R* g) {
   const R mn = q[1] * nx + q[2] * ny + q[3] * nz;
@@ -160,12 +162,13 @@ __device__ __forceinline__ void wall_ghost(const R* q, R nx, R ny, R nz, int bc,
     g[5] = q[5] - R(2) * Bn * nx;
     g[6] = q[6] - R(2) * Bn * ny;
     g[7] = q[7] - R(2) * Bn * nz;
+    g[8] = q[8];
   } else {
     g[5] = R(2) * Bn * nx - q[5];
     g[6] = R(2) * Bn * ny - q[6];
     g[7] = R(2) * Bn * nz - q[7];
+    g[8] = -q[8];
   }
-  g[8] = q[8];
 }
 
 // Rusanov common flux along the unit outward normal n of this side:

@@ -546,6 +546,60 @@ def test_glm_cleaning_reduces_divergence(oracle):
     assert wrong[-1] > 1.2 * clean[0]
 
 
+def _uniform_psi_residual(oracle, bc, nz=4, nr=2, N=4, ch=0.7, psi0=0.3):
+    v, h = inputs.shell_mesh(nz, nr)
+    m = oracle.Mesh(N, v, inputs.reorient(h, seed=3), geom=1, r_in=0.7, r_out=0.98, bc_in=bc, bc_out=bc)
+    ph = oracle.Phys(powell=0, glm_alpha=0.0, c_h=ch, gravity=0, coriolis=0)
+    q = np.zeros((9, m.n_e, N ** 3))
+    q[0], q[8] = 1.0, psi0
+    q[4] = 1.0 + 0.5 * psi0 ** 2
+    R, s = m.residual(ph, q)
+    xs, xf, E, D, w = oracle.nodes(N)
+    W = np.einsum("i,j,k->kji", w, w, w).ravel()
+    radial = 0.0
+    for e in range(m.n_e):
+        _, J, X, _ = m.geometry(e)
+        rhat = (X / np.sqrt((X ** 2).sum(axis=1))[:, None]).T
+        radial += ((R[5:8, e] * rhat).sum(axis=0) * W * J).sum()
+    return R, s, radial
+
+
+def test_wall_conditions_on_the_glm_pair(oracle):
+    """Each wall imposes one condition on the GLM pair (B_n, psi), whose waves run at +-c_h.
+    A conducting wall fixes B_n = 0 and leaves psi free: a uniform psi at rest with B = 0 is then
+    steady.  A radial wall (B_theta = B_phi = 0, B_r free) takes the condition on psi = 0: the
+    uniform psi0 falls to zero at both walls, and the B residual is the discrete -c_h grad psi of
+    that profile, whose radial part integrates to c_h psi0 * int div(r^) dV = 4 pi c_h psi0 (r_o^2 - r_i^2)
+    (divergence theorem, div r^ = 2/r); a radial wall that left psi free would give zero."""
+    R, s, radial = _uniform_psi_residual(oracle, oracle.BC_WALL_CONDUCTING)
+    assert np.abs(R).max() <= 1e-12 * s.max()
+    _, _, radial = _uniform_psi_residual(oracle, oracle.BC_WALL_RADIAL)
+    exact = 4 * math.pi * 0.7 * 0.3 * (0.98 ** 2 - 0.7 ** 2)
+    assert abs(radial / exact - 1.0) < 2e-3, (radial, exact)
+
+
+def test_radial_walls_keep_a_dipole_bounded(oracle):
+    """100 SSP-RK3 steps of the dipole shell between radial walls (c_h = lambda_max, CFL 0.2):
+    the field settles instead of growing.  With psi left free at the radial walls the GLM pair
+    has no wall condition and this run grows by 10^2 within 75 steps and overflows before 100."""
+    N = 4
+    v, h = inputs.shell_mesh(4, 2)
+    m = oracle.Mesh(N, v, h, geom=1, r_in=0.70, r_out=0.98, bc_in=oracle.BC_WALL_RADIAL,
+                    bc_out=oracle.BC_WALL_RADIAL)
+    ph = oracle.Phys(gamma=GAMMA, GM=1.0, omega=1.0, glm_alpha=1.0, c_h=0.0, powell=1, gravity=1, coriolis=1)
+    q0 = m.state_init(ph, oracle.INIT_SHELL_POLYTROPE, [1.0, 0.70, 0.98, 1.0, 1.0, 0.0, 1e-6], seed=0)
+    xs = oracle.nodes(N)[0]
+    dx = m.info()["h_min"] * (xs[1] - xs[0])
+    q, change = q0, []
+    for it in range(100):
+        lam = m.diagnostics(ph, q)["lambda_max"]
+        ph.c_h = lam
+        q = m.rk_step(ph, 0.2 * dx / lam, q)
+        if it % 25 == 24:
+            change.append(np.abs(q[5:8] - q0[5:8]).max())
+    assert np.all(np.isfinite(change)) and max(change) < 1.5 * change[0] and change[0] < 2e-3, change
+
+
 def test_diagnostics_closed_forms(oracle):
     v, h, per = inputs.box_mesh(3, jitter=0.1, seed=3)
     m = oracle.Mesh(4, v, h, periodic=per, geom=0)
