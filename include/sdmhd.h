@@ -212,6 +212,15 @@ sd_status sd_rk_stage(const sd_mesh* mesh, const sd_phys* phys, sd_precision pre
 sd_status sd_step(const sd_mesh* mesh, const sd_phys* phys, sd_precision prec, double cfl, double* q, double* work,
                   const sd_background* bg, double* dt_out, void* stream);
 
+/* n_steps >= 0 consecutive sd_step calls in one call, with the same results bit
+ * for bit.  The last stage of every step but the final one also returns the
+ * face traces and lambda_max of the state it writes, which the next step uses in
+ * place of its own trace pass (one read of the state per step fewer).  dt_out:
+ * device double[2 * n_steps] or NULL, receives (dt, c_h) of each step in order.
+ * Same arguments and errors as sd_step otherwise.  Asynchronous. */
+sd_status sd_advance(const sd_mesh* mesh, const sd_phys* phys, sd_precision prec, double cfl, int32_t n_steps,
+                     double* q, double* work, const sd_background* bg, double* dt_out, void* stream);
+
 /* ---- Packed stepping of many independent solves (serving).
  * One request is one shell (or box) solve on its own mesh with its own physics,
  * background and states.  sd_step_packed advances every request by one

@@ -745,72 +745,123 @@ sd_status sd_rk_stage(const sd_mesh* m, const sd_phys* ph, sd_precision prec, in
                        stage < 2, (cudaStream_t)stream);
 }
 
-sd_status sd_step(const sd_mesh* m, const sd_phys* ph, sd_precision prec, double cfl, double* q, double* work,
-                  const sd_background* bg, double* dt_out, void* stream) {
+// n_steps SSP-RK3 steps with device-side step control.  Trace buffer `a` holds
+// the traces of q at the start of a step: from the trace pass (first step) or
+// from the last stage of the previous step, which also leaves lambda_max of q in
+// dyn[2].  Stages: q -> work (a -> b), work -> work (b -> a), work -> q (a -> b
+// when another step follows); the buffers then swap roles.
+static sd_status advance_impl(sd_mesh* mm, const sd_phys* ph, sd_precision prec, double cfl, int32_t n_steps,
+                              double* q, double* work, const sd_background* bg, double* dt_out, cudaStream_t s) {
+  const bool mixed = prec == SD_FP32_MIXED;
+  auto stage_params = [&]() {
+    sd::StageParams S = base_params(mm, ph, prec);
+    if (bg) {
+      S.bg = bg->rec;
+      S.bg_jump = bg->jump;
+    }
+    S.mode = sd::MODE_RK;
+    S.dyn = mm->dyn;
+    return S;
+  };
+  int a = 0, b = 1;
+  for (int32_t k = 0; k < n_steps; ++k) {
+    const bool last = k == n_steps - 1;
+    if (k == 0) {  // lambda_max of q fused with the traces of q
+      sd::StageParams P = stage_params();
+      SD_CUDA(cudaMemsetAsync(mm->dyn + 2, 0, sizeof(double), s));
+      P.mode = sd::MODE_RESIDUAL;
+      P.dyn = nullptr;
+      P.q_in = q;
+      P.tr_out = trace_buf(mm, prec, a);
+      P.lam_max = reinterpret_cast<unsigned long long*>(mm->dyn + 2);
+      ProfScope ps(mm, PROF_TRACE, s);
+      SD_CUDA(sd::launch_traces(mm, prec, P, s));
+    }
+    {
+      ProfScope ps(mm, PROF_OTHER, s);
+      SD_CUDA(sd::launch_step_control(mm, cfl, ph->c_h, dt_out ? dt_out + 2 * (int64_t)k : nullptr, s));
+    }
+    // stage 0: work = q + dt R(q); the mixed path starts its difference register D = work - q
+    sd::StageParams S = stage_params();
+    S.q_in = S.q_n = q;
+    S.out = work;
+    S.rk_a = 0.0;
+    S.rk_b = 1.0;
+    S.tr_in = trace_buf(mm, prec, a);
+    S.tr_out = trace_buf(mm, prec, b);
+    if (mixed) {
+      S.dreg = bg->dreg;
+      S.dstride = bg->dstride;
+      S.lsr_write = 1;
+    }
+    {
+      ProfScope ps(mm, PROF_STAGE, s);
+      SD_CUDA(sd::launch_stage(mm, prec, S, s));
+    }
+    // stage 1: work = 3/4 q + 1/4 (work + dt R(work)), in place
+    S.q_in = S.out = work;
+    S.q_n = q;
+    S.rk_a = 0.75;
+    S.rk_b = 0.25;
+    S.tr_in = trace_buf(mm, prec, b);
+    S.tr_out = trace_buf(mm, prec, a);
+    if (mixed) {
+      S.lsr_read = 1;
+      S.lsr_write = 2;
+    }
+    {
+      ProfScope ps(mm, PROF_STAGE, s);
+      SD_CUDA(sd::launch_stage(mm, prec, S, s));
+    }
+    // stage 2: q = 1/3 q + 2/3 (work + dt R(work)); with another step to come it
+    // also writes the traces and lambda_max of the new q
+    S.q_in = work;
+    S.q_n = S.out = q;
+    S.rk_a = 1.0 / 3.0;
+    S.rk_b = 2.0 / 3.0;
+    S.tr_in = trace_buf(mm, prec, a);
+    S.tr_out = last ? nullptr : trace_buf(mm, prec, b);
+    S.lam_max = last ? nullptr : reinterpret_cast<unsigned long long*>(mm->dyn + 2);
+    if (mixed) {
+      S.lsr_read = 1;
+      S.lsr_write = 0;
+    }
+    {
+      ProfScope ps(mm, PROF_STAGE, s);
+      SD_CUDA(sd::launch_stage(mm, prec, S, s));
+    }
+    std::swap(a, b);
+  }
+  mm->tr_tag[0] = mm->tr_tag[1] = nullptr;
+  return SD_OK;
+}
+
+static sd_status check_step(const sd_mesh* m, const sd_phys* ph, sd_precision prec, double cfl, double* q,
+                            double* work, const sd_background* bg) {
   sd_status st = check_common(m, ph, prec, bg);
   if (st != SD_OK) return st;
   if ((st = check_state_ptr(q, "q")) != SD_OK) return st;
   if ((st = check_state_ptr(work, "work")) != SD_OK) return st;
   if (q == work) return fail(SD_ERR_INVALID_ARGUMENT, "work must not alias q");
   if (!(cfl > 0.0)) return fail(SD_ERR_INVALID_ARGUMENT, "cfl must be positive");
-  DeviceGuard g(m->device);
-  sd_mesh* mm = const_cast<sd_mesh*>(m);
-  cudaStream_t s = (cudaStream_t)stream;
-  // lambda_max of q fused with the traces of q
-  sd::StageParams P = base_params(m, ph, prec);
-  if (bg) {
-    P.bg = bg->rec;
-    P.bg_jump = bg->jump;
-  }
-  SD_CUDA(cudaMemsetAsync(mm->dyn + 2, 0, sizeof(double), s));
-  P.q_in = q;
-  P.tr_out = trace_buf(mm, prec, 0);
-  P.lam_max = reinterpret_cast<unsigned long long*>(mm->dyn + 2);
-  {
-    ProfScope ps(m, PROF_TRACE, s);
-    SD_CUDA(sd::launch_traces(m, prec, P, s));
-  }
-  {
-    ProfScope ps(m, PROF_OTHER, s);
-    SD_CUDA(sd::launch_step_control(m, cfl, ph->c_h, dt_out, s));
-  }
-  mm->tr_tag[0] = q;
-  mm->tr_prec[0] = prec;
-  mm->tr_tag[1] = nullptr;
-  // stage 0 finds the traces of q in buffer 0 (tagged above) only if stage > 0; run it explicitly
-  {
-    sd::StageParams S = base_params(m, ph, prec);
-    if (bg) {
-      S.bg = bg->rec;
-      S.bg_jump = bg->jump;
-    }
-    S.q_in = q;
-    S.q_n = q;
-    S.out = work;
-    S.mode = sd::MODE_RK;
-    S.rk_a = 0.0;
-    S.rk_b = 1.0;
-    S.dyn = mm->dyn;
-    S.tr_in = trace_buf(mm, prec, 0);
-    S.tr_out = trace_buf(mm, prec, 1);
-    if (prec == SD_FP32_MIXED) {  // low-storage form: stage 0 stores D = q^1 - q^n
-      S.dreg = bg->dreg;
-      S.dstride = bg->dstride;
-      S.lsr_write = 1;
-    }
-    {
-      ProfScope ps(m, PROF_STAGE, s);
-      SD_CUDA(sd::launch_stage(m, prec, S, s));
-    }
-    mm->tr_tag[0] = nullptr;
-    mm->tr_tag[1] = work;
-    mm->tr_prec[1] = prec;
-  }
-  const int lsr = prec == SD_FP32_MIXED ? 1 : 0;
-  st = rk_stage_impl(mm, ph, prec, 1, 0.0, mm->dyn, q, work, work, bg, true, s, lsr, lsr ? 2 : 0);
+  return SD_OK;
+}
+
+sd_status sd_step(const sd_mesh* m, const sd_phys* ph, sd_precision prec, double cfl, double* q, double* work,
+                  const sd_background* bg, double* dt_out, void* stream) {
+  sd_status st = check_step(m, ph, prec, cfl, q, work, bg);
   if (st != SD_OK) return st;
-  st = rk_stage_impl(mm, ph, prec, 2, 0.0, mm->dyn, q, work, q, bg, false, s, lsr, 0);
-  return st;
+  DeviceGuard g(m->device);
+  return advance_impl(const_cast<sd_mesh*>(m), ph, prec, cfl, 1, q, work, bg, dt_out, (cudaStream_t)stream);
+}
+
+sd_status sd_advance(const sd_mesh* m, const sd_phys* ph, sd_precision prec, double cfl, int32_t n_steps, double* q,
+                     double* work, const sd_background* bg, double* dt_out, void* stream) {
+  sd_status st = check_step(m, ph, prec, cfl, q, work, bg);
+  if (st != SD_OK) return st;
+  if (n_steps < 0) return fail(SD_ERR_INVALID_ARGUMENT, "n_steps must not be negative");
+  DeviceGuard g(m->device);
+  return advance_impl(const_cast<sd_mesh*>(m), ph, prec, cfl, n_steps, q, work, bg, dt_out, (cudaStream_t)stream);
 }
 
 sd_status sd_diagnostics(const sd_mesh* m, const sd_phys* ph, const double* q, sd_diag* out, void* stream) {

@@ -518,6 +518,7 @@ __global__ void step_control_kernel(double* dyn, double cfl, double dx_min, doub
   const double ch = ch_fixed > 0.0 ? ch_fixed : lam;
   dyn[0] = dt;
   dyn[1] = ch;
+  dyn[2] = 0.0;  // ready for the next lambda_max reduction
   if (dt_out) {
     dt_out[0] = dt;
     dt_out[1] = ch;

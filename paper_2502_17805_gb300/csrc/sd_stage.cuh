@@ -51,6 +51,38 @@ __device__ __forceinline__ int sol_index(int d, int i, int a, int b) {
   return d == 0 ? i + N * (a + N * b) : (d == 1 ? a + N * (i + N * b) : a + N * (b + N * i));
 }
 
+// Upper bound of the wave speeds at one point, |U| + sqrt(gamma p / rho + |B|^2 / rho)
+// (>= |u_n| + c_f along every direction), from the full conserved state.  The
+// trace kernel and the stage kernels that also return lambda_max of their output
+// use these same functions, so both give the same bits for the same state.
+__device__ __forceinline__ double point_speed_fp64(const double* qv, double gamma) {
+  const double ir = 1.0 / qv[0];
+  const double m2 = qv[1] * qv[1] + qv[2] * qv[2] + qv[3] * qv[3];
+  const double B2 = qv[5] * qv[5] + qv[6] * qv[6] + qv[7] * qv[7];
+  const double p = (gamma - 1.0) * (qv[4] - 0.5 * (m2 * ir + B2 + qv[8] * qv[8]));
+  return sqrt(m2) * ir + sqrt(gamma * p * ir + B2 * ir);
+}
+
+// The same bound in FP32 from the FP32 rounding of the full state (mixed policy).
+__device__ __forceinline__ float point_speed_mixed(const float* qf, float g) {
+  const float ir = 1.0f / qf[0];
+  const float m2 = qf[1] * qf[1] + qf[2] * qf[2] + qf[3] * qf[3];
+  const float B2 = qf[5] * qf[5] + qf[6] * qf[6] + qf[7] * qf[7];
+  const float p = (g - 1.0f) * (qf[4] - 0.5f * (m2 * ir + B2 + qf[8] * qf[8]));
+  return sqrtf(m2) * ir + sqrtf(g * p * ir + B2 * ir);
+}
+
+// Running maximum that keeps a NaN (a non-physical state must not pass unseen).
+__device__ __forceinline__ double speed_max(double lam, double l) { return (l > lam || l != l) ? l : lam; }
+
+// Maximum over the warp, then one atomic per warp; positive doubles order like
+// their bit patterns, and a NaN (all exponent bits set) is above every finite value.
+__device__ __forceinline__ void speed_reduce(double lam, unsigned long long* dst) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) lam = speed_max(lam, __shfl_xor_sync(0xffffffffu, lam, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(dst, (unsigned long long)__double_as_longlong(lam));
+}
+
 // Load one element's state into shared memory.  Mixed policy: q' = q - Q0 with
 // the subtraction in FP64 (rho0 and E0 = p0 / (gamma - 1) from the FP32
 // background record), rounded to FP32, plus rho0 and p0.  lam_out receives the
@@ -67,14 +99,7 @@ __device__ __forceinline__ void load_element(const StageParams& P, const double*
 #pragma unroll
     for (int v = 0; v < 9; ++v) qv[v] = __ldg(q + v * P.plane + g);
     if constexpr (!Pol::mixed) {
-      if (lam_out) {
-        const double ir = 1.0 / qv[0];
-        const double m2 = qv[1] * qv[1] + qv[2] * qv[2] + qv[3] * qv[3];
-        const double B2 = qv[5] * qv[5] + qv[6] * qv[6] + qv[7] * qv[7];
-        const double p = (P.gamma - 1.0) * (qv[4] - 0.5 * (m2 * ir + B2 + qv[8] * qv[8]));
-        const double l = sqrt(m2) * ir + sqrt(P.gamma * p * ir + B2 * ir);
-        lam = (l > lam || l != l) ? l : lam;
-      }
+      if (lam_out) lam = speed_max(lam, point_speed_fp64(qv, P.gamma));
 #pragma unroll
       for (int v = 0; v < 9; ++v) sQ[v * N3 + n] = qv[v];
     } else {
@@ -83,16 +108,7 @@ __device__ __forceinline__ void load_element(const StageParams& P, const double*
       float qf[9];
 #pragma unroll
       for (int v = 0; v < 9; ++v) qf[v] = f64_to_f32(qv[v]);
-      if (lam_out) {
-        const float ir = 1.0f / qf[0];
-        const float m2 = qf[1] * qf[1] + qf[2] * qf[2] + qf[3] * qf[3];
-        const float B2 = qf[5] * qf[5] + qf[6] * qf[6] + qf[7] * qf[7];
-        const float g = (float)P.gamma;
-        const float p = (g - 1.0f) * (qf[4] - 0.5f * (m2 * ir + B2 + qf[8] * qf[8]));
-        const float l = sqrtf(m2) * ir + sqrtf(g * p * ir + B2 * ir);
-        const double ld = (double)l;
-        lam = (ld > lam || l != l) ? ld : lam;
-      }
+      if (lam_out) lam = speed_max(lam, (double)point_speed_mixed(qf, (float)P.gamma));
 #pragma unroll
       for (int v = 0; v < 9; ++v) sQ[v * N3 + n] = qf[v];
       sQ[0 * N3 + n] = f64_to_f32(qv[0] - f32_to_f64(r0));
@@ -137,15 +153,7 @@ __device__ __forceinline__ void trace_body(const StageParams& P, const Ops<typen
   for (int i = threadIdx.x; i < NF * N; i += BLK) sE[i] = ops.E[i];
   double lam = 0.0;
   load_element<N, Pol>(P, P.q_in, e, sQ, P.lam_max ? &lam : nullptr);
-  if (P.lam_max) {
-    // max over the block, then one atomic; positive doubles order like their bit patterns
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const double other = __shfl_xor_sync(0xffffffffu, lam, o);
-      lam = (other > lam || other != other) ? other : lam;
-    }
-    if ((threadIdx.x & 31) == 0) atomicMax(P.lam_max, (unsigned long long)__double_as_longlong(lam));
-  }
+  if (P.lam_max) speed_reduce(lam, P.lam_max);
   __syncthreads();
   write_traces<N, Pol>(sQ, sE, reinterpret_cast<R*>(P.tr_out), e);
 }
@@ -408,6 +416,7 @@ __global__ void __launch_bounds__(Dims<N>::BLK) stage_kernel(const StageParams P
   // with q_n - q_in formed in FP64, t in FP32 and the sum in FP64: the RK state
   // accumulates in FP64 while the FP64 pipe sees two additions per value.
   // The next stage's FP32 traces come from q' + t.
+  double lam = 0.0;  // lambda_max of the new state (FP64 policy, MODE_RK with P.lam_max)
   if (n < N3) {
     const R iJ = reinterpret_cast<const R*>(P.invJ)[e * N3 + n];
     const R* Xe = reinterpret_cast<const R*>(P.X) + e * 3 * N3;
@@ -437,6 +446,7 @@ __global__ void __launch_bounds__(Dims<N>::BLK) stage_kernel(const StageParams P
         }
 #pragma unroll
         for (int v = 0; v < 9; ++v) P.out[v * P.plane + g] = qout[v];
+        if (P.lam_max) lam = point_speed_fp64(qout, P.gamma);
         if (P.tr_out) {
 #pragma unroll
           for (int v = 0; v < 9; ++v) acc[v] = qout[v];  // kept for the traces below
@@ -471,6 +481,10 @@ __global__ void __launch_bounds__(Dims<N>::BLK) stage_kernel(const StageParams P
         }
       }
     }
+  }
+  // (the mixed policy runs its RK stages in stage_kernel_v2, which returns lambda_max itself)
+  if constexpr (!Pol::mixed) {
+    if (P.mode == MODE_RK && P.lam_max) speed_reduce(lam, P.lam_max);
   }
   if (P.mode == MODE_RK && P.tr_out) {
     __syncthreads();

@@ -37,6 +37,14 @@ struct DimsV2 {
   static constexpr size_t bytes = ((nF * 4) + 15) / 16 * 16;
 };
 
+// q' of variable v at a point of the new state qo (FP64), rounded as load_element
+// rounds a stored state: rho and E lose their background in FP64 first.
+__device__ __forceinline__ float new_qprime(int v, double qo, float qo32, float r0, float p0, double inv_gm1) {
+  if (v == 0) return f64_to_f32(qo - f32_to_f64(r0));
+  if (v == 4) return f64_to_f32(fma(-f32_to_f64(p0), inv_gm1, qo));
+  return qo32;
+}
+
 // solution-point index of position i along the line (d, L): base + i * stride
 template <int N>
 __device__ __forceinline__ void line_geom(int d, int L, int& base, int& stride) {
@@ -231,6 +239,12 @@ __device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops<fl
   __syncthreads();
 
   // ---- E: residual, sources, RK sum (see stage_kernel<N, PolMixed> for the increment form)
+  // With P.lam_max (MODE_RK) the stage also returns lambda_max of its output, and
+  // the q' it leaves for the traces is rounded from the stored FP64 state exactly
+  // as a fresh load would round it: the traces and lambda_max equal those of a
+  // separate trace pass over the output, bit for bit.
+  const bool exact = mode == MODE_RK && P.lam_max != nullptr;
+  double lam = 0.0;
   if (lsr) mbar_wait_bounded(&dbar, 0u, P.err);
   for (int n = tid; n < N3; n += T) {
     const int i0 = n % N, j0 = (n / N) % N, k0 = n / N2;
@@ -262,26 +276,35 @@ __device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops<fl
     } else if (lsr_read || lsr_write) {
       // low-storage form: t = -a D + b dt R, q_out = q_in + t, D <- D + t, with D = q_in - q_n
       const int64_t gd = e * DV::DSTRIDE + n, dplane = n_e * DV::DSTRIDE;
+      float qe[9];
 #pragma unroll
       for (int v = 0; v < 9; ++v) {
         const double qin = __ldg(P.q_in + v * plane + g);
         const float Dv = lsr_read ? sDs[v * DV::DSTRIDE + n] : 0.0f;
         const float t = fmaf(-rka, Dv, bdt * Rv[v]);
-        P.out[v * plane + g] = qin + f32_to_f64(t);
+        const double qo = qin + f32_to_f64(t);
+        P.out[v * plane + g] = qo;
         if (lsr_write) P.dreg[v * dplane + gd] = (lsr_write == 1) ? t : Dv + t;
-        sQ[v * N3 + n] = q[v] + t;  // q' of the new state (this thread's own point)
+        if (exact) qe[v] = f64_to_f32(qo);
+        sQ[v * N3 + n] = exact ? new_qprime(v, qo, qe[v], q[9], q[10], inv_gm1) : q[v] + t;
       }
+      if (exact) lam = speed_max(lam, (double)point_speed_mixed(qe, gamma));
     } else {
+      float qe[9];
 #pragma unroll
       for (int v = 0; v < 9; ++v) {
         const double qin = __ldg(P.q_in + v * plane + g);
         float t = bdt * Rv[v];
         if (classic_qn) t = fmaf(rka, f64_to_f32(__ldg(P.q_n + v * plane + g) - qin), t);
-        P.out[v * plane + g] = qin + f32_to_f64(t);
-        sQ[v * N3 + n] = q[v] + t;  // q' of the new state (this thread's own point)
+        const double qo = qin + f32_to_f64(t);
+        P.out[v * plane + g] = qo;
+        if (exact) qe[v] = f64_to_f32(qo);
+        sQ[v * N3 + n] = exact ? new_qprime(v, qo, qe[v], q[9], q[10], inv_gm1) : q[v] + t;
       }
+      if (exact) lam = speed_max(lam, (double)point_speed_mixed(qe, gamma));
     }
   }
+  if (exact) speed_reduce(lam, P.lam_max);
 
   // ---- F: face traces of the new state
   if (mode == MODE_RK && P.tr_out) {

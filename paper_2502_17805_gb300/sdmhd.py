@@ -27,7 +27,7 @@ STATUS = {0: "SD_OK", 1: "SD_ERR_INVALID_ARGUMENT", 2: "SD_ERR_UNSUPPORTED", 3: 
 
 # every symbol include/sdmhd.h declares
 EXPORTS = ["sd_last_error", "sd_mesh_create", "sd_mesh_destroy", "sd_mesh_query", "sd_state_init",
-           "sd_background_create", "sd_background_destroy", "sd_residual", "sd_rk_stage", "sd_step",
+           "sd_background_create", "sd_background_destroy", "sd_residual", "sd_rk_stage", "sd_step", "sd_advance",
            "sd_diagnostics", "sd_profile_enable", "sd_profile_read", "sd_residual_noalloc",
            "sd_packer_create", "sd_packer_destroy", "sd_step_packed"]
 
@@ -120,6 +120,7 @@ def lib():
         L.sd_residual.argtypes = [vp, C.POINTER(PhysC), C.c_int, vp, vp, vp, vp]
         L.sd_rk_stage.argtypes = [vp, C.POINTER(PhysC), C.c_int, C.c_int32, C.c_double, vp, vp, vp, vp, vp]
         L.sd_step.argtypes = [vp, C.POINTER(PhysC), C.c_int, C.c_double, vp, vp, vp, vp, vp]
+        L.sd_advance.argtypes = [vp, C.POINTER(PhysC), C.c_int, C.c_double, C.c_int32, vp, vp, vp, vp, vp]
         L.sd_diagnostics.argtypes = [vp, C.POINTER(PhysC), vp, C.POINTER(DiagC), vp]
         L.sd_profile_enable.argtypes = [vp, C.c_int32]
         L.sd_profile_read.argtypes = [vp, C.POINTER(ProfileC)]
@@ -258,6 +259,14 @@ class Mesh:
         ph = phys.c()
         _check(lib().sd_step(self._h, C.byref(ph), int(prec), float(cfl), _ptr(q), _ptr(work),
                              bg._h if bg else None, _ptr(dt_out), _stream(stream)))
+        return q
+
+    def advance(self, phys: Phys, cfl: float, n_steps: int, q, work, prec: int = SD_FP64,
+                bg: Optional[Background] = None, dt_out=None, stream=None):
+        """n_steps calls of step() in one (same results); dt_out: device float64[2 * n_steps] or None."""
+        ph = phys.c()
+        _check(lib().sd_advance(self._h, C.byref(ph), int(prec), float(cfl), int(n_steps), _ptr(q), _ptr(work),
+                                bg._h if bg else None, _ptr(dt_out), _stream(stream)))
         return q
 
     def profile(self, enable: bool = True):

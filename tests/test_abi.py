@@ -91,4 +91,5 @@ def test_calls_reject_null_mesh(lib):
     assert lib.sd_rk_stage(None, C.byref(ph), 0, 0, 0.1, None, None, None, None, None) == 1
     assert lib.sd_diagnostics(None, C.byref(ph), None, None, None) == 1
     assert lib.sd_step(None, C.byref(ph), 0, 0.2, None, None, None, None, None) == 1
+    assert lib.sd_advance(None, C.byref(ph), 0, 0.2, 3, None, None, None, None, None) == 1
     assert lib.sd_mesh_destroy(None) == 0

@@ -109,14 +109,19 @@ def test_shell1536_hundred_fp64_steps():
     xs = sdref.nodes(6)[0]
     dx = om.info()["h_min"] * (xs[1] - xs[0])
     dts = torch.zeros(2, dtype=torch.float64, device="cuda")
-    qo, dt_err = q0, 0.0
+    qo, dt_err, t_run = q0, 0.0, 0.0
     for _ in range(100):
         gm.step(gph, 0.2, q, work, dt_out=dts)
         lam = om.diagnostics(oph, qo)["lambda_max"]
         oph.c_h = lam
         qo = om.rk_step(oph, 0.2 * dx / lam, qo)
         dt_err = max(dt_err, abs(float(dts[0]) / (0.2 * dx / lam) - 1.0))
+        t_run += 0.2 * dx / lam
     change = np.abs(qo - q0).max(axis=(1, 2))
     err = np.abs(gm.to_host(q) - qo).max(axis=(1, 2))
-    # relative to the change over the run; psi and the momentum start at zero
-    assert dt_err < 1e-11 and np.all(err <= 1e-9 * np.maximum(change, 1e-300)), (dt_err, err / change)
+    # The momentum is a small difference of pressure and gravity terms: the two FP64 runs part at
+    # the round-off of those un-cancelled magnitudes (s_v per unit time) accumulated over the run,
+    # on top of 1e-9 of the change.
+    _, s = om.residual(oph, q0)
+    bound = 1e-9 * change + 1e-12 * t_run * s
+    assert dt_err < 1e-11 and np.all(err <= bound), (dt_err, err, bound)

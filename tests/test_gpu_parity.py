@@ -286,3 +286,28 @@ def test_mixed_sd_step_low_storage_matches_oracle():
     _, s = om.residual(oph, q0)
     ok, err, bound = mixed_ok(gm.to_host(q) - q0, qo - q0, s, scale=3 * 3 * float(dt))
     assert ok, (err, bound)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_advance_equals_repeated_steps(prec):
+    """sd_advance takes the traces and lambda_max of each step's start state from the last stage of
+    the step before instead of a trace pass; the states and (dt, c_h) are the same bits as sd_step
+    called once per step."""
+    gm, om, gph, oph, q0, qb = _mixed_case(3, 2, 5, 2.0, seed=6)
+    gph.c_h = 0.0
+    kw = dict(prec=sdmhd.SD_FP32_MIXED, bg=gm.background(gph, gm.to_device(qb))) if prec == "mixed" else {}
+    K = 4
+    qa, wa = gm.to_device(q0), gm.empty_state()
+    da = torch.zeros(2 * K, dtype=torch.float64, device="cuda")
+    for k in range(K):
+        gm.step(gph, 0.2, qa, wa, dt_out=da[2 * k: 2 * k + 2], **kw)
+    qb_, wb = gm.to_device(q0), gm.empty_state()
+    db = torch.zeros(2 * K, dtype=torch.float64, device="cuda")
+    gm.advance(gph, 0.2, K, qb_, wb, dt_out=db, **kw)
+    torch.cuda.synchronize()
+    assert torch.equal(da, db) and torch.equal(qa, qb_)
+    assert not torch.equal(qa, gm.to_device(q0))
+    # zero steps leave the state alone
+    qc = qb_.clone()
+    gm.advance(gph, 0.2, 0, qc, wb, **kw)
+    assert torch.equal(qc, qb_)
