@@ -236,7 +236,7 @@ typedef struct {
   double* q;                /* device state, advanced in place */
   double* work;             /* device state used inside the step */
   void* traces;             /* device scratch of sd_mesh_info.trace_bytes bytes, 16-byte aligned */
-  double* dyn;              /* device double[4]: receives (dt, c_h) of the step in [0], [1] */
+  double* dyn;              /* device double[4]: receives (dt, c_h, lambda_max) of the step in [0..2] */
   double cfl;               /* dt = cfl * dx_min / lambda_max as in sd_step */
 } sd_step_req;
 

@@ -460,7 +460,7 @@ sd_status sd_mesh_create(const sd_mesh_desc* desc, void* stream, sd_mesh** out) 
   ALLOC(m->tr64[1], ne * 6 * 9 * N2);
   ALLOC(m->tr32[0], ne * 6 * 9 * N2);
   ALLOC(m->tr32[1], ne * 6 * 9 * N2);
-  ALLOC(m->dyn, 4);
+  ALLOC(m->dyn, 4 + sd::LAM_SLOTS);
   ALLOC(m->diag_part, ne * 12);
   ALLOC(m->diag_out, 12);
   ALLOC(m->divb, ne * N3);
@@ -748,7 +748,8 @@ sd_status sd_rk_stage(const sd_mesh* m, const sd_phys* ph, sd_precision prec, in
 // n_steps SSP-RK3 steps with device-side step control.  Trace buffer `a` holds
 // the traces of q at the start of a step: from the trace pass (first step) or
 // from the last stage of the previous step, which also leaves lambda_max of q in
-// dyn[2].  Stages: q -> work (a -> b), work -> work (b -> a), work -> q (a -> b
+// the partial maxima dyn[4 ...] (cleared by the step-control kernel that reads
+// them).  Stages: q -> work (a -> b), work -> work (b -> a), work -> q (a -> b
 // when another step follows); the buffers then swap roles.
 static sd_status advance_impl(sd_mesh* mm, const sd_phys* ph, sd_precision prec, double cfl, int32_t n_steps,
                               double* q, double* work, const sd_background* bg, double* dt_out, cudaStream_t s) {
@@ -768,12 +769,13 @@ static sd_status advance_impl(sd_mesh* mm, const sd_phys* ph, sd_precision prec,
     const bool last = k == n_steps - 1;
     if (k == 0) {  // lambda_max of q fused with the traces of q
       sd::StageParams P = stage_params();
-      SD_CUDA(cudaMemsetAsync(mm->dyn + 2, 0, sizeof(double), s));
+      SD_CUDA(cudaMemsetAsync(mm->dyn + 4, 0, sd::LAM_SLOTS * sizeof(double), s));
       P.mode = sd::MODE_RESIDUAL;
       P.dyn = nullptr;
       P.q_in = q;
       P.tr_out = trace_buf(mm, prec, a);
-      P.lam_max = reinterpret_cast<unsigned long long*>(mm->dyn + 2);
+      P.lam_max = reinterpret_cast<unsigned long long*>(mm->dyn + 4);
+      P.lam_nslot = sd::LAM_SLOTS;
       ProfScope ps(mm, PROF_TRACE, s);
       SD_CUDA(sd::launch_traces(mm, prec, P, s));
     }
@@ -821,7 +823,8 @@ static sd_status advance_impl(sd_mesh* mm, const sd_phys* ph, sd_precision prec,
     S.rk_b = 2.0 / 3.0;
     S.tr_in = trace_buf(mm, prec, a);
     S.tr_out = last ? nullptr : trace_buf(mm, prec, b);
-    S.lam_max = last ? nullptr : reinterpret_cast<unsigned long long*>(mm->dyn + 2);
+    S.lam_max = last ? nullptr : reinterpret_cast<unsigned long long*>(mm->dyn + 4);
+    S.lam_nslot = sd::LAM_SLOTS;
     if (mixed) {
       S.lsr_read = 1;
       S.lsr_write = 0;

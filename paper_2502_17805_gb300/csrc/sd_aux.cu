@@ -512,13 +512,30 @@ cudaError_t launch_bg_finish(const sd_mesh* m, double gamma, const double* R0, f
 // c_h = lambda_max unless fixed.
 // ---------------------------------------------------------------------------
 
-__global__ void step_control_kernel(double* dyn, double cfl, double dx_min, double ch_fixed, double* dt_out) {
-  const double lam = __longlong_as_double((long long)(*reinterpret_cast<const unsigned long long*>(dyn + 2)));
+// One block of LAM_SLOTS threads: lambda_max = largest of the partial maxima
+// (compared as bit patterns, as the atomics wrote them), which are cleared for
+// the next reduction; then dt and c_h.
+__global__ void __launch_bounds__(LAM_SLOTS) step_control_kernel(double* dyn, double cfl, double dx_min,
+                                                                 double ch_fixed, double* dt_out) {
+  __shared__ unsigned long long part[LAM_SLOTS / 32];
+  unsigned long long* slots = reinterpret_cast<unsigned long long*>(dyn + 4);
+  unsigned long long b = slots[threadIdx.x];
+  slots[threadIdx.x] = 0ull;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long other = __shfl_xor_sync(0xffffffffu, b, o);
+    b = other > b ? other : b;
+  }
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = b;
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  for (int w = 1; w < LAM_SLOTS / 32; ++w) b = part[w] > b ? part[w] : b;
+  const double lam = __longlong_as_double((long long)b);
   const double dt = cfl * dx_min / lam;
   const double ch = ch_fixed > 0.0 ? ch_fixed : lam;
   dyn[0] = dt;
   dyn[1] = ch;
-  dyn[2] = 0.0;  // ready for the next lambda_max reduction
+  dyn[2] = lam;
   if (dt_out) {
     dt_out[0] = dt;
     dt_out[1] = ch;
@@ -527,7 +544,7 @@ __global__ void step_control_kernel(double* dyn, double cfl, double dx_min, doub
 
 cudaError_t launch_step_control(const sd_mesh* m, double cfl, double c_h_fixed, double* dt_out, cudaStream_t s) {
   const double dx_min = m->h_min * (m->ops64.xs[1] - m->ops64.xs[0]);
-  step_control_kernel<<<1, 1, 0, s>>>(m->dyn, cfl, dx_min, c_h_fixed, dt_out);
+  step_control_kernel<<<1, LAM_SLOTS, 0, s>>>(m->dyn, cfl, dx_min, c_h_fixed, dt_out);
   return cudaGetLastError();
 }
 

@@ -64,7 +64,8 @@ struct StageParams {
   const float* bg;       // [5][n_e * N^3] rho0, p0, R0x, R0y, R0z (FP32 mixed)
   const float* bg_jump;  // [e][F][2][N^2] background jumps (rho0, p0), neighbour minus own
   double* divb;          // [n_e * N^3] (MODE_DIVB)
-  unsigned long long* lam_max;  // trace kernel: running max of lambda (bits of a positive double)
+  unsigned long long* lam_max;  // partial maxima of lambda (bits of positive doubles), or nullptr
+  int lam_nslot;                // number of partial maxima at lam_max (a power of two; 0 or 1: one)
   // low-storage form of the mixed RK stages (sd_step): D = q^(s) - q^n in FP32,
   // [9][n_e * dstride]; lsr_read: use D instead of q_n; lsr_write: 1 store D = t, 2 store D += t
   float* dreg;
@@ -97,7 +98,7 @@ struct sd_mesh {
   float* tr32[2];
   const double* tr_tag[2];  // state whose traces buffer b holds (stage chaining)
   int tr_prec[2];
-  double* dyn;              // [4]: dt, c_h, lambda bits, spare
+  double* dyn;              // [4 + LAM_SLOTS]: dt, c_h, lambda_max, spare, then the partial maxima of lambda
   double* diag_part;        // [n_e][12]
   double* diag_out;         // [12]
   double* divb;             // [n_e * N^3]
@@ -124,6 +125,8 @@ struct sd_background {
 };
 
 namespace sd {
+// partial maxima of lambda per mesh: the warps of a launch spread their atomics over these
+constexpr int LAM_SLOTS = 256;
 // kernels launched from the API (defined in the .cu files)
 cudaError_t launch_stage(const sd_mesh* m, int prec, const StageParams& P, cudaStream_t s);
 cudaError_t launch_traces(const sd_mesh* m, int prec, const StageParams& P, cudaStream_t s);

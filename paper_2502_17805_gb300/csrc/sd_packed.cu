@@ -22,23 +22,30 @@ cudaError_t launch_packed_mixed(int N, bool traces, const StageParams* tab, cons
                                 int64_t blocks, const Ops<float>& ops, cudaStream_t s);
 void set_last_error(const std::string& msg);
 
+// partial maxima of lambda per request (the packer's own scratch)
+constexpr int PK_SLOTS = 16;
+
 struct StepCtl {
   double* dyn;
+  unsigned long long* slots;  // [PK_SLOTS]
   double cfl, dx_min, ch_fixed;
 };
 
 __global__ void packed_reset_kernel(const StepCtl* __restrict__ ctl, int n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) ctl[i].dyn[2] = 0.0;
+  if (i < n * PK_SLOTS) ctl[i / PK_SLOTS].slots[i % PK_SLOTS] = 0ull;
 }
 
 __global__ void packed_control_kernel(const StepCtl* __restrict__ ctl, int n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double* dyn = ctl[i].dyn;
-  const double lam = __longlong_as_double((long long)(*reinterpret_cast<const unsigned long long*>(dyn + 2)));
+  unsigned long long b = 0ull;
+  for (int k = 0; k < PK_SLOTS; ++k) b = ctl[i].slots[k] > b ? ctl[i].slots[k] : b;
+  const double lam = __longlong_as_double((long long)b);
   dyn[0] = ctl[i].cfl * ctl[i].dx_min / lam;
   dyn[1] = ctl[i].ch_fixed > 0.0 ? ctl[i].ch_fixed : lam;
+  dyn[2] = lam;
 }
 }  // namespace sd
 
@@ -53,6 +60,7 @@ struct sd_packer {
   int64_t* d_off[2];
   sd::StepCtl* h_ctl[2];
   sd::StepCtl* d_ctl[2];
+  unsigned long long* d_slots;  // [cap][PK_SLOTS]
   cudaEvent_t copied[2];
   bool used[2];
   int device;
@@ -75,6 +83,7 @@ void free_packer(sd_packer* p) {
     if (p->d_ctl[b]) cudaFree(p->d_ctl[b]);
     if (p->copied[b]) cudaEventDestroy(p->copied[b]);
   }
+  if (p->d_slots) cudaFree(p->d_slots);
   delete p;
 }
 
@@ -101,6 +110,8 @@ sd_status sd_packer_create(int32_t max_requests, sd_packer** out) {
     if (err == cudaSuccess) err = cudaMalloc((void**)&p->d_ctl[b], max_requests * sizeof(sd::StepCtl));
     if (err == cudaSuccess) err = cudaEventCreateWithFlags(&p->copied[b], cudaEventDisableTiming);
   }
+  if (err == cudaSuccess)
+    err = cudaMalloc((void**)&p->d_slots, (size_t)max_requests * sd::PK_SLOTS * sizeof(unsigned long long));
   if (err != cudaSuccess) {
     free_packer(p);
     cudaGetLastError();
@@ -206,7 +217,8 @@ sd_status sd_step_packed(sd_packer* pk, int32_t n, const sd_step_req* reqs, void
     sd::StageParams Pt = P;
     Pt.q_in = r.q;
     Pt.tr_out = tr0;
-    Pt.lam_max = reinterpret_cast<unsigned long long*>(r.dyn + 2);
+    Pt.lam_max = pk->d_slots + (size_t)k * sd::PK_SLOTS;
+    Pt.lam_nslot = sd::PK_SLOTS;
     T[0 * n + k] = Pt;
     // stage 0: q -> work, traces tr0 -> tr1; stage 1: (q, work) -> work, tr1 -> tr0;
     // stage 2: (q, work) -> q, reads tr0
@@ -231,7 +243,8 @@ sd_status sd_step_packed(sd_packer* pk, int32_t n, const sd_step_req* reqs, void
       Ps.lsr_write = s == 0 ? 1 : (s == 1 ? 2 : 0);
       T[(1 + s) * n + k] = Ps;
     }
-    CTL[k] = {r.dyn, r.cfl, m->h_min * (m->ops64.xs[1] - m->ops64.xs[0]), r.phys.c_h};
+    CTL[k] = {r.dyn, pk->d_slots + (size_t)k * sd::PK_SLOTS, r.cfl, m->h_min * (m->ops64.xs[1] - m->ops64.xs[0]),
+              r.phys.c_h};
   }
   off_pos += (groups.back().k1 - groups.back().k0) + 1;
 
@@ -245,7 +258,7 @@ sd_status sd_step_packed(sd_packer* pk, int32_t n, const sd_step_req* reqs, void
   pk->parity ^= 1;
 
   const unsigned cblocks = (unsigned)((n + 127) / 128);
-  sd::packed_reset_kernel<<<cblocks, 128, 0, s>>>(pk->d_ctl[b], n);
+  sd::packed_reset_kernel<<<(unsigned)(((int64_t)n * sd::PK_SLOTS + 127) / 128), 128, 0, s>>>(pk->d_ctl[b], n);
   err = cudaGetLastError();
   for (size_t gi = 0; gi < groups.size() && err == cudaSuccess; ++gi) {
     const Group& g = groups[gi];

@@ -75,12 +75,19 @@ __device__ __forceinline__ float point_speed_mixed(const float* qf, float g) {
 // Running maximum that keeps a NaN (a non-physical state must not pass unseen).
 __device__ __forceinline__ double speed_max(double lam, double l) { return (l > lam || l != l) ? l : lam; }
 
-// Maximum over the warp, then one atomic per warp; positive doubles order like
-// their bit patterns, and a NaN (all exponent bits set) is above every finite value.
-__device__ __forceinline__ void speed_reduce(double lam, unsigned long long* dst) {
+// Maximum over the warp, then one atomic per warp into one of nslot (a power of
+// two) partial maxima, so that the atomics of a launch spread over several
+// addresses instead of queueing on one; the step-control kernel reduces the
+// slots.  Positive doubles order like their bit patterns, and a NaN (all
+// exponent bits set) is above every finite value.
+__device__ __forceinline__ void speed_reduce(double lam, unsigned long long* dst, int nslot) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) lam = speed_max(lam, __shfl_xor_sync(0xffffffffu, lam, o));
-  if ((threadIdx.x & 31) == 0) atomicMax(dst, (unsigned long long)__double_as_longlong(lam));
+  if ((threadIdx.x & 31) == 0) {
+    const unsigned warp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const unsigned slot = nslot > 1 ? warp & (unsigned)(nslot - 1) : 0u;
+    atomicMax(dst + slot, (unsigned long long)__double_as_longlong(lam));
+  }
 }
 
 // Load one element's state into shared memory.  Mixed policy: q' = q - Q0 with
@@ -153,7 +160,7 @@ __device__ __forceinline__ void trace_body(const StageParams& P, const Ops<typen
   for (int i = threadIdx.x; i < NF * N; i += BLK) sE[i] = ops.E[i];
   double lam = 0.0;
   load_element<N, Pol>(P, P.q_in, e, sQ, P.lam_max ? &lam : nullptr);
-  if (P.lam_max) speed_reduce(lam, P.lam_max);
+  if (P.lam_max) speed_reduce(lam, P.lam_max, P.lam_nslot);
   __syncthreads();
   write_traces<N, Pol>(sQ, sE, reinterpret_cast<R*>(P.tr_out), e);
 }
@@ -484,7 +491,7 @@ __global__ void __launch_bounds__(Dims<N>::BLK) stage_kernel(const StageParams P
   }
   // (the mixed policy runs its RK stages in stage_kernel_v2, which returns lambda_max itself)
   if constexpr (!Pol::mixed) {
-    if (P.mode == MODE_RK && P.lam_max) speed_reduce(lam, P.lam_max);
+    if (P.mode == MODE_RK && P.lam_max) speed_reduce(lam, P.lam_max, P.lam_nslot);
   }
   if (P.mode == MODE_RK && P.tr_out) {
     __syncthreads();

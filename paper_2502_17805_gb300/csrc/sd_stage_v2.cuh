@@ -33,8 +33,17 @@ struct DimsV2 {
   static constexpr int nX = 3 * NF * NV * N2;
   static constexpr int DSTRIDE = (N3 + 3) / 4 * 4;   // element stride of the FP32 difference register
   static constexpr int oDs = (oX + nX + 3) / 4 * 4;  // [9][DSTRIDE]: D staged by a TMA bulk copy
-  static constexpr int nF = oDs + 9 * DSTRIDE;
+  // With N^3 a multiple of 4 every per-element block of the FP32 geometry and
+  // background planes starts on a 16-byte boundary: 1/|J|, x, y, z and the three
+  // components of R0 are then staged by TMA too, [7][N3].
+  static constexpr bool STAGE_G = N3 % 4 == 0;
+  static constexpr int oG = oDs + 9 * DSTRIDE;
+  static constexpr int nF = oG + (STAGE_G ? 7 * N3 : 0);
   static constexpr size_t bytes = ((nF * 4) + 15) / 16 * 16;
+  // CTAs per SM that the shared memory admits (228 KB per SM, 1 KB reserved per
+  // CTA), capped at 5: the register budget of __launch_bounds__ follows from it.
+  static constexpr int SMEM_CTAS = (int)(233472 / (bytes + 1024 + 64));
+  static constexpr int MINB = SMEM_CTAS < 1 ? 1 : (SMEM_CTAS > 5 ? 5 : SMEM_CTAS);
 };
 
 // q' of variable v at a point of the new state qo (FP64), rounded as load_element
@@ -88,20 +97,29 @@ __device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops<fl
   const bool classic_qn = P.rk_a != 0.0;
   const int64_t n_e = P.n_e, stride = P.stride, plane = P.plane;
 
-  // low-storage RK: the difference register D of this element is copied to
-  // shared memory by TMA while phases A-D run; the epilogue waits for it.
+  // The epilogue's per-element inputs are copied to shared memory by TMA while
+  // phases A-D run: the difference register D of the low-storage RK form, and
+  // (STAGE_G) 1/|J|, x and R0.  The epilogue waits for them on one mbarrier.
   __shared__ __align__(8) unsigned long long dbar;
   float* sDs = smem + DV::oDs;
+  float* sG = smem + DV::oG;
   const bool lsr = P.lsr_read != 0;
-  if (lsr) {
-    if (tid == 0) {
-      mbar_init(&dbar, 1);
-      constexpr unsigned plane_bytes = DV::DSTRIDE * 4;
-      mbar_expect_tx(&dbar, 9 * plane_bytes);
+  const bool staged = lsr || DV::STAGE_G;
+  if (staged && tid == 0) {
+    mbar_init(&dbar, 1);
+    constexpr unsigned plane_bytes = DV::DSTRIDE * 4, blk = N3 * 4;
+    mbar_expect_tx(&dbar, (lsr ? 9 * plane_bytes : 0u) + (DV::STAGE_G ? 7 * blk : 0u));
+    if (lsr) {
       const float* src = P.dreg + e * DV::DSTRIDE;
       const int64_t dplane = P.n_e * DV::DSTRIDE;
 #pragma unroll 1
       for (int v = 0; v < 9; ++v) tma_load_1d(sDs + v * DV::DSTRIDE, src + v * dplane, plane_bytes, &dbar);
+    }
+    if constexpr (DV::STAGE_G) {
+      tma_load_1d(sG, reinterpret_cast<const float*>(P.invJ) + e * N3, blk, &dbar);
+      tma_load_1d(sG + N3, reinterpret_cast<const float*>(P.X) + e * 3 * N3, 3 * blk, &dbar);
+#pragma unroll 1
+      for (int c = 0; c < 3; ++c) tma_load_1d(sG + (4 + c) * N3, P.bg + (2 + c) * P.n_e * N3 + e * N3, blk, &dbar);
     }
   }
 
@@ -112,21 +130,35 @@ __device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops<fl
   int lbase = 0, lstride = 1;
   line_geom<N>(ld, lL, lbase, lstride);
 
-  // ---- A: load
+  // ---- A: load (every round's loads issued before the first conversion)
   const double inv_gm1 = P.inv_gm1;
-  for (int n = tid; n < N3; n += T) {
-    const int64_t g = e * stride + n;
-    const int64_t gb = e * N3 + n;
-    const float r0 = __ldg(P.bg + gb), p0 = __ldg(P.bg + n_e * N3 + gb);
-    double qv[9];
+  {
+    constexpr int NRA = (N3 + T - 1) / T;
+    double qv[NRA][9];
+    float r0[NRA], p0[NRA];
 #pragma unroll
-    for (int v = 0; v < 9; ++v) qv[v] = __ldg(P.q_in + v * plane + g);
-    sQ[0 * N3 + n] = f64_to_f32(qv[0] - f32_to_f64(r0));
+    for (int r = 0; r < NRA; ++r) {
+      const int n = tid + r * T;
+      if (n < N3) {
+        const int64_t g = e * stride + n, gb = e * N3 + n;
+        r0[r] = __ldg(P.bg + gb);
+        p0[r] = __ldg(P.bg + n_e * N3 + gb);
 #pragma unroll
-    for (int v = 1; v < 9; ++v) sQ[v * N3 + n] = f64_to_f32(qv[v]);
-    sQ[4 * N3 + n] = f64_to_f32(fma(-f32_to_f64(p0), inv_gm1, qv[4]));
-    sQ[9 * N3 + n] = r0;
-    sQ[10 * N3 + n] = p0;
+        for (int v = 0; v < 9; ++v) qv[r][v] = __ldg(P.q_in + v * plane + g);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < NRA; ++r) {
+      const int n = tid + r * T;
+      if (n < N3) {
+        sQ[0 * N3 + n] = f64_to_f32(qv[r][0] - f32_to_f64(r0[r]));
+#pragma unroll
+        for (int v = 1; v < 9; ++v) sQ[v * N3 + n] = f64_to_f32(qv[r][v]);
+        sQ[4 * N3 + n] = f64_to_f32(fma(-f32_to_f64(p0[r]), inv_gm1, qv[r][4]));
+        sQ[9 * N3 + n] = r0[r];
+        sQ[10 * N3 + n] = p0[r];
+      }
+    }
   }
   __syncthreads();
 
@@ -245,7 +277,7 @@ __device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops<fl
   // separate trace pass over the output, bit for bit.
   const bool exact = mode == MODE_RK && P.lam_max != nullptr;
   double lam = 0.0;
-  if (lsr) mbar_wait_bounded(&dbar, 0u, P.err);
+  if (staged) mbar_wait_bounded(&dbar, 0u, P.err);
   for (int n = tid; n < N3; n += T) {
     const int i0 = n % N, j0 = (n / N) % N, k0 = n / N2;
     const float* D0 = sX + ((0 * NF + i0) * 11) * N2 + (j0 + N * k0);
@@ -254,19 +286,30 @@ __device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops<fl
     float acc[10];
 #pragma unroll
     for (int v = 0; v < 10; ++v) acc[v] = D0[v * N2] + D1[v * N2] + D2[v * N2];
-    const float iJ = __ldg(reinterpret_cast<const float*>(P.invJ) + e * N3 + n);
-    const float* Xe = reinterpret_cast<const float*>(P.X) + e * 3 * N3;
+    float G[7];  // 1/|J|, x, y, z, R0 (momentum components)
+    if constexpr (DV::STAGE_G) {
+#pragma unroll
+      for (int c = 0; c < 7; ++c) G[c] = sG[c * N3 + n];
+    } else {
+      const int64_t gb = e * N3 + n, bp = n_e * N3;
+      const float* Xe = reinterpret_cast<const float*>(P.X) + e * 3 * N3;
+      G[0] = __ldg(reinterpret_cast<const float*>(P.invJ) + gb);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) G[1 + c] = __ldg(Xe + c * N3 + n);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) G[4 + c] = __ldg(P.bg + (2 + c) * bp + gb);
+    }
+    const float iJ = G[0];
     const float divB = acc[9] * iJ;
     float q[11], M[9], Rv[9];
 #pragma unroll
     for (int v = 0; v < 11; ++v) q[v] = sQ[v * N3 + n];
-    sources_mixed(MC, q, divB, __ldg(Xe + n), __ldg(Xe + N3 + n), __ldg(Xe + 2 * N3 + n), M);
+    sources_mixed(MC, q, divB, G[1], G[2], G[3], M);
 #pragma unroll
     for (int v = 0; v < 9; ++v) Rv[v] = -acc[v] * iJ + M[v];
-    const int64_t gb = e * N3 + n, bp = n_e * N3;
-    Rv[1] += __ldg(P.bg + 2 * bp + gb);
-    Rv[2] += __ldg(P.bg + 3 * bp + gb);
-    Rv[3] += __ldg(P.bg + 4 * bp + gb);
+    Rv[1] += G[4];
+    Rv[2] += G[5];
+    Rv[3] += G[6];
     const int64_t g = e * stride + n;
     if (mode == MODE_RESIDUAL) {
 #pragma unroll
@@ -304,7 +347,7 @@ __device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops<fl
       if (exact) lam = speed_max(lam, (double)point_speed_mixed(qe, gamma));
     }
   }
-  if (exact) speed_reduce(lam, P.lam_max);
+  if (exact) speed_reduce(lam, P.lam_max, P.lam_nslot);
 
   // ---- F: face traces of the new state
   if (mode == MODE_RK && P.tr_out) {
@@ -328,14 +371,14 @@ __device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops<fl
 }
 
 template <int N>
-__global__ void __launch_bounds__(DimsV2<N>::T, 5) stage_kernel_v2(const StageParams P, const Ops<float> ops) {
+__global__ void __launch_bounds__(DimsV2<N>::T, DimsV2<N>::MINB) stage_kernel_v2(const StageParams P, const Ops<float> ops) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   stage_body_v2<N>(P, ops, (int64_t)blockIdx.x, smem_raw);
 }
 
 // Packed launch over several requests (see packed_request in sd_stage.cuh).
 template <int N>
-__global__ void __launch_bounds__(DimsV2<N>::T, 5) stage_kernel_v2_packed(const StageParams* __restrict__ tab,
+__global__ void __launch_bounds__(DimsV2<N>::T, DimsV2<N>::MINB) stage_kernel_v2_packed(const StageParams* __restrict__ tab,
                                                                          const int64_t* __restrict__ off, int n_req,
                                                                          const Ops<float> ops) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
