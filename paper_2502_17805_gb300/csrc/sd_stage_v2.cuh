@@ -70,7 +70,7 @@ __device__ __forceinline__ void line_geom(int d, int L, int& base, int& stride) 
   }
 }
 
-template <int N>
+template <int N, bool EXACT>
 __device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops<float>& ops, const int64_t e,
                                               unsigned char* smem_raw) {
   using DV = DimsV2<N>;
@@ -275,7 +275,7 @@ __device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops<fl
   // the q' it leaves for the traces is rounded from the stored FP64 state exactly
   // as a fresh load would round it: the traces and lambda_max equal those of a
   // separate trace pass over the output, bit for bit.
-  const bool exact = mode == MODE_RK && P.lam_max != nullptr;
+  constexpr bool exact = EXACT;
   double lam = 0.0;
   if (staged) mbar_wait_bounded(&dbar, 0u, P.err);
   for (int n = tid; n < N3; n += T) {
@@ -370,10 +370,10 @@ __device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops<fl
   }
 }
 
-template <int N>
+template <int N, bool EXACT>
 __global__ void __launch_bounds__(DimsV2<N>::T, DimsV2<N>::MINB) stage_kernel_v2(const StageParams P, const Ops<float> ops) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  stage_body_v2<N>(P, ops, (int64_t)blockIdx.x, smem_raw);
+  stage_body_v2<N, EXACT>(P, ops, (int64_t)blockIdx.x, smem_raw);
 }
 
 // Packed launch over several requests (see packed_request in sd_stage.cuh).
@@ -385,22 +385,30 @@ __global__ void __launch_bounds__(DimsV2<N>::T, DimsV2<N>::MINB) stage_kernel_v2
   __shared__ StageParams sP;
   const int r = packed_request(off, n_req, (int64_t)blockIdx.x);
   copy_params(tab + r, &sP);
-  stage_body_v2<N>(sP, ops, (int64_t)blockIdx.x - __ldg(off + r), smem_raw);
+  stage_body_v2<N, false>(sP, ops, (int64_t)blockIdx.x - __ldg(off + r), smem_raw);
 }
 
-template <int N>
-cudaError_t launch_stage_v2_t(const StageParams& P, const Ops<float>& ops, cudaStream_t s) {
+template <int N, bool EXACT>
+cudaError_t launch_stage_v2_e(const StageParams& P, const Ops<float>& ops, cudaStream_t s) {
   using DV = DimsV2<N>;
-  cudaError_t err = cudaFuncSetAttribute(stage_kernel_v2<N>, cudaFuncAttributePreferredSharedMemoryCarveout,
+  cudaError_t err = cudaFuncSetAttribute(stage_kernel_v2<N, EXACT>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                          (int)cudaSharedmemCarveoutMaxShared);
   if (err != cudaSuccess) return err;
   if (DV::bytes > 48 * 1024) {
-    err = cudaFuncSetAttribute(stage_kernel_v2<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DV::bytes);
+    err = cudaFuncSetAttribute(stage_kernel_v2<N, EXACT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DV::bytes);
     if (err != cudaSuccess) return err;
   }
   if (P.n_e == 0) return cudaSuccess;
-  stage_kernel_v2<N><<<(unsigned)P.n_e, DV::T, DV::bytes, s>>>(P, ops);
+  stage_kernel_v2<N, EXACT><<<(unsigned)P.n_e, DV::T, DV::bytes, s>>>(P, ops);
   return cudaGetLastError();
+}
+
+// The exact form (traces and lambda_max of the output as a fresh load of it
+// gives them) is a separate instantiation, so the other stages carry none of it.
+template <int N>
+cudaError_t launch_stage_v2_t(const StageParams& P, const Ops<float>& ops, cudaStream_t s) {
+  if (P.mode == MODE_RK && P.lam_max) return launch_stage_v2_e<N, true>(P, ops, s);
+  return launch_stage_v2_e<N, false>(P, ops, s);
 }
 
 // Packed launches of one order N: trace (+lambda) kernel or stage kernel over

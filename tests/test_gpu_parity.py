@@ -288,12 +288,13 @@ def test_mixed_sd_step_low_storage_matches_oracle():
     assert ok, (err, bound)
 
 
+@pytest.mark.parametrize("N", [5, 6])
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_advance_equals_repeated_steps(prec):
+def test_advance_equals_repeated_steps(prec, N):
     """sd_advance takes the traces and lambda_max of each step's start state from the last stage of
     the step before instead of a trace pass; the states and (dt, c_h) are the same bits as sd_step
     called once per step."""
-    gm, om, gph, oph, q0, qb = _mixed_case(3, 2, 5, 2.0, seed=6)
+    gm, om, gph, oph, q0, qb = _mixed_case(3, 2, N, 2.0, seed=6)
     gph.c_h = 0.0
     kw = dict(prec=sdmhd.SD_FP32_MIXED, bg=gm.background(gph, gm.to_device(qb))) if prec == "mixed" else {}
     K = 4

@@ -47,11 +47,14 @@ def torch_dev():
 
 
 @gpu
-def test_packed_step_equals_sd_step(torch_dev):
+@pytest.mark.parametrize("N", [4, 5, 6])
+def test_packed_step_equals_sd_step(torch_dev, N):
+    """The packed launches (parameters from a device table, one launch over all requests) and sd_step
+    do the same arithmetic in the same order: the same bits, for each order."""
     torch = torch_dev
     from paper_2502_17805_gb300 import sdmhd
     srv = serve.Server(hbm_budget_bytes=1 << 34, max_running=8)
-    req = serve.Request(rid=0, nz=3, nr=2, N=5, n_rho=2.0, omega=1.3, seed=5, steps=3, arrival=0.0)
+    req = serve.Request(rid=0, nz=3, nr=2, N=N, n_rho=2.0, omega=1.3, seed=5, steps=3, arrival=0.0)
     q_packed = srv.final_state(req)
     run = serve._Running(req, srv.mesh(req.nz, req.nr, req.N))
     for _ in range(req.steps):
