@@ -208,7 +208,10 @@ sd_status sd_rk_stage(const sd_mesh* mesh, const sd_phys* phys, sd_precision pre
  * dx_min = h_min (X_s,2 - X_s,1) the smallest solution-point spacing,
  * c_h = lambda_max when phys->c_h <= 0 (else phys->c_h), then the three fused
  * stages.  q (in/out) and work: device states; dt_out: device double[2] or NULL,
- * receives (dt, c_h).  No host synchronisation.  Asynchronous. */
+ * receives (dt, c_h).  SD_FP32_MIXED keeps no FP64 intermediate state: every
+ * stage reads q and the background's FP32 register D = q^(s) - q^n, and only
+ * the last stage writes q (work is then not written).  No host synchronisation.
+ * Asynchronous. */
 sd_status sd_step(const sd_mesh* mesh, const sd_phys* phys, sd_precision prec, double cfl, double* q, double* work,
                   const sd_background* bg, double* dt_out, void* stream);
 

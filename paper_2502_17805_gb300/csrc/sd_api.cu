@@ -783,7 +783,9 @@ static sd_status advance_impl(sd_mesh* mm, const sd_phys* ph, sd_precision prec,
       ProfScope ps(mm, PROF_OTHER, s);
       SD_CUDA(sd::launch_step_control(mm, cfl, ph->c_h, dt_out ? dt_out + 2 * (int64_t)k : nullptr, s));
     }
-    // stage 0: work = q + dt R(q); the mixed path starts its difference register D = work - q
+    // stage 0: work = q + dt R(q).  The mixed path runs the increment form: it keeps
+    // no FP64 intermediate state, only D = q^(s) - q^n in FP32 (D = dt R(q) here),
+    // and every stage reads q^n.
     sd::StageParams S = stage_params();
     S.q_in = S.q_n = q;
     S.out = work;
@@ -795,13 +797,15 @@ static sd_status advance_impl(sd_mesh* mm, const sd_phys* ph, sd_precision prec,
       S.dreg = bg->dreg;
       S.dstride = bg->dstride;
       S.lsr_write = 1;
+      S.incr = 1;
     }
     {
       ProfScope ps(mm, PROF_STAGE, s);
       SD_CUDA(sd::launch_stage(mm, prec, S, s));
     }
-    // stage 1: work = 3/4 q + 1/4 (work + dt R(work)), in place
-    S.q_in = S.out = work;
+    // stage 1: work = 3/4 q + 1/4 (work + dt R(work)), in place (mixed: D advances)
+    S.q_in = mixed ? q : work;
+    S.out = work;
     S.q_n = q;
     S.rk_a = 0.75;
     S.rk_b = 0.25;
@@ -816,8 +820,8 @@ static sd_status advance_impl(sd_mesh* mm, const sd_phys* ph, sd_precision prec,
       SD_CUDA(sd::launch_stage(mm, prec, S, s));
     }
     // stage 2: q = 1/3 q + 2/3 (work + dt R(work)); with another step to come it
-    // also writes the traces and lambda_max of the new q
-    S.q_in = work;
+    // also writes the traces and lambda_max of the new q (mixed: q = q + D + t)
+    S.q_in = mixed ? q : work;
     S.q_n = S.out = q;
     S.rk_a = 1.0 / 3.0;
     S.rk_b = 2.0 / 3.0;

@@ -71,6 +71,9 @@ struct StageParams {
   float* dreg;
   int64_t dstride;
   int lsr_read, lsr_write;
+  // increment form (FP32-mixed sd_step): q_in is q^n in every stage and the stage's
+  // state is q^n + D; stages with lsr_write only advance D, the last writes q^n + D + t
+  int incr;
   int* err;  // device error word (bounded waits that ran out)
 };
 

@@ -220,9 +220,10 @@ sd_status sd_step_packed(sd_packer* pk, int32_t n, const sd_step_req* reqs, void
     Pt.lam_max = pk->d_slots + (size_t)k * sd::PK_SLOTS;
     Pt.lam_nslot = sd::PK_SLOTS;
     T[0 * n + k] = Pt;
-    // stage 0: q -> work, traces tr0 -> tr1; stage 1: (q, work) -> work, tr1 -> tr0;
-    // stage 2: (q, work) -> q, reads tr0
-    const double* qin[3] = {r.q, r.work, r.work};
+    // increment form (as sd_step): every stage reads q^n and the FP32 register D
+    // carries the stage states.  Stage 0: D = t, traces tr0 -> tr1; stage 1: D += t,
+    // tr1 -> tr0; stage 2: q = q + D + t, reads tr0 (work is not written)
+    const double* qin[3] = {r.q, r.q, r.q};
     double* qout[3] = {r.work, r.work, r.q};
     void* tin[3] = {tr0, tr1, tr0};
     void* tout[3] = {tr1, tr0, nullptr};
@@ -241,6 +242,7 @@ sd_status sd_step_packed(sd_packer* pk, int32_t n, const sd_step_req* reqs, void
       Ps.dstride = r.bg->dstride;
       Ps.lsr_read = s > 0 ? 1 : 0;
       Ps.lsr_write = s == 0 ? 1 : (s == 1 ? 2 : 0);
+      Ps.incr = 1;
       T[(1 + s) * n + k] = Ps;
     }
     CTL[k] = {r.dyn, pk->d_slots + (size_t)k * sd::PK_SLOTS, r.cfl, m->h_min * (m->ops64.xs[1] - m->ops64.xs[0]),

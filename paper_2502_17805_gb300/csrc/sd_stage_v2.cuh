@@ -70,7 +70,7 @@ __device__ __forceinline__ void line_geom(int d, int L, int& base, int& stride) 
   }
 }
 
-template <int N, bool EXACT>
+template <int N, bool EXACT, bool INCR>
 __device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops<float>& ops, const int64_t e,
                                               unsigned char* smem_raw) {
   using DV = DimsV2<N>;
@@ -94,34 +94,40 @@ __device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops<fl
   const float bdt = (float)(P.rk_b * dt);
   const float rka = (float)P.rk_a;
   const int mode = P.mode, lsr_read = P.lsr_read, lsr_write = P.lsr_write;
+  constexpr bool incr = INCR;
   const bool classic_qn = P.rk_a != 0.0;
   const int64_t n_e = P.n_e, stride = P.stride, plane = P.plane;
 
-  // The epilogue's per-element inputs are copied to shared memory by TMA while
-  // phases A-D run: the difference register D of the low-storage RK form, and
-  // (STAGE_G) 1/|J|, x and R0.  The epilogue waits for them on one mbarrier.
-  __shared__ __align__(8) unsigned long long dbar;
+  // Per-element inputs copied to shared memory by TMA at kernel start: the
+  // difference register D of the low-storage RK form (mbarrier dbar; read by the
+  // epilogue, and by phase A in the increment form) and, with STAGE_G, 1/|J|, x
+  // and R0 for the epilogue (mbarrier gbar).
+  __shared__ __align__(8) unsigned long long dbar, gbar;
   float* sDs = smem + DV::oDs;
   float* sG = smem + DV::oG;
   const bool lsr = P.lsr_read != 0;
-  const bool staged = lsr || DV::STAGE_G;
-  if (staged && tid == 0) {
-    mbar_init(&dbar, 1);
+  if (tid == 0) {
     constexpr unsigned plane_bytes = DV::DSTRIDE * 4, blk = N3 * 4;
-    mbar_expect_tx(&dbar, (lsr ? 9 * plane_bytes : 0u) + (DV::STAGE_G ? 7 * blk : 0u));
     if (lsr) {
+      mbar_init(&dbar, 1);
+      mbar_expect_tx(&dbar, 9 * plane_bytes);
       const float* src = P.dreg + e * DV::DSTRIDE;
       const int64_t dplane = P.n_e * DV::DSTRIDE;
 #pragma unroll 1
       for (int v = 0; v < 9; ++v) tma_load_1d(sDs + v * DV::DSTRIDE, src + v * dplane, plane_bytes, &dbar);
     }
     if constexpr (DV::STAGE_G) {
-      tma_load_1d(sG, reinterpret_cast<const float*>(P.invJ) + e * N3, blk, &dbar);
-      tma_load_1d(sG + N3, reinterpret_cast<const float*>(P.X) + e * 3 * N3, 3 * blk, &dbar);
+      mbar_init(&gbar, 1);
+      mbar_expect_tx(&gbar, 7 * blk);
+      tma_load_1d(sG, reinterpret_cast<const float*>(P.invJ) + e * N3, blk, &gbar);
+      tma_load_1d(sG + N3, reinterpret_cast<const float*>(P.X) + e * 3 * N3, 3 * blk, &gbar);
 #pragma unroll 1
-      for (int c = 0; c < 3; ++c) tma_load_1d(sG + (4 + c) * N3, P.bg + (2 + c) * P.n_e * N3 + e * N3, blk, &dbar);
+      for (int c = 0; c < 3; ++c) tma_load_1d(sG + (4 + c) * N3, P.bg + (2 + c) * P.n_e * N3 + e * N3, blk, &gbar);
     }
   }
+  // increment form: the stage's state is q_in + D, so phase A needs D (waited for
+  // after the state loads are issued)
+  if (incr && lsr) __syncthreads();  // dbar initialised before anyone polls it
 
   // line role of this thread (B, D, F)
   const bool is_line = tid < NL;
@@ -147,14 +153,22 @@ __device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops<fl
         for (int v = 0; v < 9; ++v) qv[r][v] = __ldg(P.q_in + v * plane + g);
       }
     }
+    if (incr && lsr) mbar_wait_bounded(&dbar, 0u, P.err);
 #pragma unroll
     for (int r = 0; r < NRA; ++r) {
       const int n = tid + r * T;
       if (n < N3) {
-        sQ[0 * N3 + n] = f64_to_f32(qv[r][0] - f32_to_f64(r0[r]));
+        float qp[9];
+        qp[0] = f64_to_f32(qv[r][0] - f32_to_f64(r0[r]));
 #pragma unroll
-        for (int v = 1; v < 9; ++v) sQ[v * N3 + n] = f64_to_f32(qv[r][v]);
-        sQ[4 * N3 + n] = f64_to_f32(fma(-f32_to_f64(p0[r]), inv_gm1, qv[r][4]));
+        for (int v = 1; v < 9; ++v) qp[v] = f64_to_f32(qv[r][v]);
+        qp[4] = f64_to_f32(fma(-f32_to_f64(p0[r]), inv_gm1, qv[r][4]));
+        if (incr && lsr) {
+#pragma unroll
+          for (int v = 0; v < 9; ++v) qp[v] += sDs[v * DV::DSTRIDE + n];
+        }
+#pragma unroll
+        for (int v = 0; v < 9; ++v) sQ[v * N3 + n] = qp[v];
         sQ[9 * N3 + n] = r0[r];
         sQ[10 * N3 + n] = p0[r];
       }
@@ -277,7 +291,8 @@ __device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops<fl
   // separate trace pass over the output, bit for bit.
   constexpr bool exact = EXACT;
   double lam = 0.0;
-  if (staged) mbar_wait_bounded(&dbar, 0u, P.err);
+  if (lsr && !incr) mbar_wait_bounded(&dbar, 0u, P.err);
+  if (DV::STAGE_G) mbar_wait_bounded(&gbar, 0u, P.err);
   for (int n = tid; n < N3; n += T) {
     const int i0 = n % N, j0 = (n / N) % N, k0 = n / N2;
     const float* D0 = sX + ((0 * NF + i0) * 11) * N2 + (j0 + N * k0);
@@ -316,6 +331,27 @@ __device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops<fl
       for (int v = 0; v < 9; ++v) P.out[v * plane + g] = f32_to_f64(Rv[v]);
     } else if (mode == MODE_DIVB) {
       P.divb[e * N3 + n] = f32_to_f64(divB);
+    } else if (incr) {
+      // increment form: the stage's state is q^n + D (q_in = q^n, D = 0 at stage 0);
+      // t = -a D + b dt R; intermediate stages only advance D <- D + t (FP32),
+      // the last writes q^n + (D + t) in FP64
+      const int64_t gd = e * DV::DSTRIDE + n, dplane = n_e * DV::DSTRIDE;
+      float qe[9];
+#pragma unroll
+      for (int v = 0; v < 9; ++v) {
+        const float Dv = lsr_read ? sDs[v * DV::DSTRIDE + n] : 0.0f;
+        const float t = fmaf(-rka, Dv, bdt * Rv[v]);
+        if (lsr_write) {
+          P.dreg[v * dplane + gd] = Dv + t;
+          sQ[v * N3 + n] = q[v] + t;
+        } else {
+          const double qo = __ldg(P.q_in + v * plane + g) + f32_to_f64(Dv + t);
+          P.out[v * plane + g] = qo;
+          if (exact) qe[v] = f64_to_f32(qo);
+          sQ[v * N3 + n] = exact ? new_qprime(v, qo, qe[v], q[9], q[10], inv_gm1) : q[v] + t;
+        }
+      }
+      if (exact) lam = speed_max(lam, (double)point_speed_mixed(qe, gamma));
     } else if (lsr_read || lsr_write) {
       // low-storage form: t = -a D + b dt R, q_out = q_in + t, D <- D + t, with D = q_in - q_n
       const int64_t gd = e * DV::DSTRIDE + n, dplane = n_e * DV::DSTRIDE;
@@ -370,13 +406,14 @@ __device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops<fl
   }
 }
 
-template <int N, bool EXACT>
+template <int N, bool EXACT, bool INCR>
 __global__ void __launch_bounds__(DimsV2<N>::T, DimsV2<N>::MINB) stage_kernel_v2(const StageParams P, const Ops<float> ops) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  stage_body_v2<N, EXACT>(P, ops, (int64_t)blockIdx.x, smem_raw);
+  stage_body_v2<N, EXACT, INCR>(P, ops, (int64_t)blockIdx.x, smem_raw);
 }
 
-// Packed launch over several requests (see packed_request in sd_stage.cuh).
+// Packed launch over several requests (see packed_request in sd_stage.cuh); the
+// packed stages always run the increment form.
 template <int N>
 __global__ void __launch_bounds__(DimsV2<N>::T, DimsV2<N>::MINB) stage_kernel_v2_packed(const StageParams* __restrict__ tab,
                                                                          const int64_t* __restrict__ off, int n_req,
@@ -385,30 +422,33 @@ __global__ void __launch_bounds__(DimsV2<N>::T, DimsV2<N>::MINB) stage_kernel_v2
   __shared__ StageParams sP;
   const int r = packed_request(off, n_req, (int64_t)blockIdx.x);
   copy_params(tab + r, &sP);
-  stage_body_v2<N, false>(sP, ops, (int64_t)blockIdx.x - __ldg(off + r), smem_raw);
+  stage_body_v2<N, false, true>(sP, ops, (int64_t)blockIdx.x - __ldg(off + r), smem_raw);
 }
 
-template <int N, bool EXACT>
+template <int N, bool EXACT, bool INCR>
 cudaError_t launch_stage_v2_e(const StageParams& P, const Ops<float>& ops, cudaStream_t s) {
   using DV = DimsV2<N>;
-  cudaError_t err = cudaFuncSetAttribute(stage_kernel_v2<N, EXACT>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                         (int)cudaSharedmemCarveoutMaxShared);
+  auto kern = stage_kernel_v2<N, EXACT, INCR>;
+  cudaError_t err =
+      cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
   if (err != cudaSuccess) return err;
   if (DV::bytes > 48 * 1024) {
-    err = cudaFuncSetAttribute(stage_kernel_v2<N, EXACT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DV::bytes);
+    err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DV::bytes);
     if (err != cudaSuccess) return err;
   }
   if (P.n_e == 0) return cudaSuccess;
-  stage_kernel_v2<N, EXACT><<<(unsigned)P.n_e, DV::T, DV::bytes, s>>>(P, ops);
+  kern<<<(unsigned)P.n_e, DV::T, DV::bytes, s>>>(P, ops);
   return cudaGetLastError();
 }
 
 // The exact form (traces and lambda_max of the output as a fresh load of it
-// gives them) is a separate instantiation, so the other stages carry none of it.
+// gives them) and the increment form are separate instantiations, so each
+// stage carries only the code it runs.
 template <int N>
 cudaError_t launch_stage_v2_t(const StageParams& P, const Ops<float>& ops, cudaStream_t s) {
-  if (P.mode == MODE_RK && P.lam_max) return launch_stage_v2_e<N, true>(P, ops, s);
-  return launch_stage_v2_e<N, false>(P, ops, s);
+  const bool exact = P.mode == MODE_RK && P.lam_max;
+  if (P.incr) return exact ? launch_stage_v2_e<N, true, true>(P, ops, s) : launch_stage_v2_e<N, false, true>(P, ops, s);
+  return exact ? launch_stage_v2_e<N, true, false>(P, ops, s) : launch_stage_v2_e<N, false, false>(P, ops, s);
 }
 
 // Packed launches of one order N: trace (+lambda) kernel or stage kernel over
