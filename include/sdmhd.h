@@ -177,9 +177,15 @@ sd_status sd_state_init(const sd_mesh* mesh, const sd_phys* phys, const sd_init*
  * rounds rho0 and p0 to FP32, computes in FP64 the background residual R0
  * (pressure gradient with central face average, plus rho0 g) and the FP64 jumps
  * of the background across faces.  The handle stays valid while the mesh
- * lives.  Synchronises `stream`. */
+ * lives.  Asynchronous: its device memory comes from the stream-ordered
+ * allocator on `stream`, and the tables are complete once the work issued to
+ * `stream` so far is (use the handle on `stream`, or after synchronising it).
+ * q_background may be released once that work is complete. */
 sd_status sd_background_create(const sd_mesh* mesh, const sd_phys* phys, const double* q_background, void* stream,
                                sd_background** out);
+/* Releases the background's device memory in stream order on the legacy default
+ * stream (after all work issued so far to it and to blocking streams); work on
+ * a non-blocking stream that uses the background must be complete first. */
 sd_status sd_background_destroy(sd_background* bg);
 
 /* dqdt = -div F / |J| + M at every solution point (Sec. SD Method: extrapolate to

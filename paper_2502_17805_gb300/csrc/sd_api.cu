@@ -586,11 +586,12 @@ sd_status sd_background_create(const sd_mesh* m, const sd_phys* ph, const double
   bg->device = m->device;
   double *q0 = nullptr, *R0 = nullptr;
   const size_t state = 9 * ne * m->stride;
-  cudaError_t err = cudaMalloc((void**)&bg->rec, 5 * ne * N3 * sizeof(float));
-  if (err == cudaSuccess) err = cudaMalloc((void**)&bg->jump, ne * 6 * 2 * N2 * sizeof(float));
-  if (err == cudaSuccess) err = cudaMalloc((void**)&bg->dreg, 9 * ne * bg->dstride * sizeof(float));
-  if (err == cudaSuccess) err = cudaMalloc((void**)&q0, state * sizeof(double));
-  if (err == cudaSuccess) err = cudaMalloc((void**)&R0, state * sizeof(double));
+  // stream-ordered allocations: building a background never waits for the device
+  cudaError_t err = cudaMallocAsync((void**)&bg->rec, 5 * ne * N3 * sizeof(float), s);
+  if (err == cudaSuccess) err = cudaMallocAsync((void**)&bg->jump, ne * 6 * 2 * N2 * sizeof(float), s);
+  if (err == cudaSuccess) err = cudaMallocAsync((void**)&bg->dreg, 9 * ne * bg->dstride * sizeof(float), s);
+  if (err == cudaSuccess) err = cudaMallocAsync((void**)&q0, state * sizeof(double), s);
+  if (err == cudaSuccess) err = cudaMallocAsync((void**)&R0, state * sizeof(double), s);
   if (err == cudaSuccess) err = sd::launch_bg_prepare(m, ph->gamma, 1.0 / (ph->gamma - 1.0), q_bg, q0, bg->rec, s);
   sd_mesh* mm = const_cast<sd_mesh*>(m);
   if (err == cudaSuccess) {
@@ -613,14 +614,13 @@ sd_status sd_background_create(const sd_mesh* m, const sd_phys* ph, const double
     }
   }
   if (err == cudaSuccess) err = sd::launch_bg_finish(m, ph->gamma, R0, bg->rec, bg->jump, mm->tr64[0], s);
-  if (err == cudaSuccess) err = cudaStreamSynchronize(s);
   mm->tr_tag[0] = mm->tr_tag[1] = nullptr;
-  if (q0) cudaFree(q0);
-  if (R0) cudaFree(R0);
+  if (q0) cudaFreeAsync(q0, s);
+  if (R0) cudaFreeAsync(R0, s);
   if (err != cudaSuccess) {
-    if (bg->rec) cudaFree(bg->rec);
-    if (bg->jump) cudaFree(bg->jump);
-    if (bg->dreg) cudaFree(bg->dreg);
+    if (bg->rec) cudaFreeAsync(bg->rec, s);
+    if (bg->jump) cudaFreeAsync(bg->jump, s);
+    if (bg->dreg) cudaFreeAsync(bg->dreg, s);
     delete bg;
     cudaGetLastError();
     return err == cudaErrorMemoryAllocation ? fail(SD_ERR_OUT_OF_MEMORY, "background allocation failed")
@@ -633,9 +633,11 @@ sd_status sd_background_create(const sd_mesh* m, const sd_phys* ph, const double
 sd_status sd_background_destroy(sd_background* bg) {
   if (!bg) return SD_OK;
   DeviceGuard g(bg->device);
-  cudaFree(bg->rec);
-  cudaFree(bg->jump);
-  cudaFree(bg->dreg);
+  // stream-ordered on the legacy default stream: after all work already issued
+  // to it and to the blocking streams
+  cudaFreeAsync(bg->rec, 0);
+  cudaFreeAsync(bg->jump, 0);
+  cudaFreeAsync(bg->dreg, 0);
   delete bg;
   return SD_OK;
 }

@@ -13,7 +13,11 @@ the FP32-mixed path.  The server
   running request of that order; requests that arrive meanwhile join at the
   next tick, so their work overlaps with the others' on the device;
 * retires a request after K steps, records its latency (completion minus
-  arrival) and frees its memory, which may admit waiting requests.
+  arrival, the completion taken from a CUDA event after its last tick) and
+  frees its memory, which may admit waiting requests;
+* never waits for the device between ticks: admission only enqueues work, up
+  to two ticks are in flight, and the host blocks only on the oldest tick's
+  event.
 
 Meshes (geometry) are cached per (Nz, Nr, N) and shared between requests;
 everything a step writes (states, traces, dt) belongs to the request.
@@ -132,16 +136,37 @@ class Server:
         for r in requests:
             self.mesh(r.nz, r.nr, r.N)
 
-    def run(self, requests: Sequence[Request], stream=None) -> dict:
+    def run(self, requests: Sequence[Request], depth: int = 2) -> dict:
+        """Serve `requests` (arrival times relative to the call) to completion.
+
+        Ticks are issued without waiting for the device: up to `depth` ticks are in
+        flight, and admitting a request (initial state, background tables) only
+        enqueues work, so the host prepares the next tick while the device runs the
+        current one.  A request's completion time is the device time of the event
+        recorded after its last tick."""
         import torch
         pending = sorted(requests, key=lambda r: r.arrival)
         queue: List[Request] = []
         running: List[Tuple[_Running, int]] = []
+        inflight: list = []  # (event, requests completing at that tick, their _Running objects)
         used = 0
         finished: List[Request] = []
+        stream = torch.cuda.current_stream()
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
         t0 = time.perf_counter()
+
+        def retire_oldest():
+            ev, reqs, _runs = inflight.pop(0)
+            ev.synchronize()
+            t_done = ev0.elapsed_time(ev) / 1e3
+            for r in reqs:
+                r.done = t_done
+                finished.append(r)
+
         i = 0
-        while i < len(pending) or queue or running:
+        while i < len(pending) or queue or running or inflight:
             now = time.perf_counter() - t0
             while i < len(pending) and pending[i].arrival <= now:
                 queue.append(pending[i])
@@ -159,25 +184,30 @@ class Server:
                 used += fp
                 self.peak_bytes = max(self.peak_bytes, used)
             if not running:
-                if i < len(pending):
+                if inflight:
+                    retire_oldest()
+                elif i < len(pending):
                     time.sleep(max(0.0, pending[i].arrival - (time.perf_counter() - t0)))
                 continue
             # one tick: every running request advances one step
-            self.packer.step([run.as_packed() for run, _ in running], stream=stream)
-            torch.cuda.current_stream().synchronize()
+            self.packer.step([run.as_packed() for run, _ in running])
+            ev = torch.cuda.Event(enable_timing=True)
+            ev.record(stream)
             self.ticks += 1
-            t_done = time.perf_counter() - t0
-            keep = []
+            keep, done_reqs, done_runs = [], [], []
             for run, fp in running:
                 run.steps_done += 1
                 if run.steps_done >= run.req.steps:
-                    run.req.done = t_done
-                    finished.append(run.req)
+                    done_reqs.append(run.req)
+                    done_runs.append(run)  # released (stream-ordered) once retired
                     used -= fp
                 else:
                     keep.append((run, fp))
             running = keep
-        wall = time.perf_counter() - t0
+            inflight.append((ev, done_reqs, done_runs))
+            if len(inflight) >= depth:
+                retire_oldest()
+        wall = max(r.done for r in finished) if finished else time.perf_counter() - t0
         lat = np.array([r.latency for r in finished])
         dof_updates = sum(r.dof * r.steps for r in finished)
         return {"requests": len(finished), "wall_s": wall, "dof_updates": dof_updates,
