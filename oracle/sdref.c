@@ -35,6 +35,24 @@
  *  R11 time stepping: Shu-Osher SSP-RK3 (the SSPRK(5,3) table the paper
  *     cites is not given in the paper).
  *  R12 shell initial noise and dipole (see sdref_state_init).
+ *  Viscous, resistive and thermal fluxes (phys.viscous; Sec. MHD Governing Equations and the BR1
+ *  paragraph of Sec. SD Method):
+ *  V1 the gradients F_vis needs are those of the primitive variables w = (U, T, S, B), with
+ *     T = p / (rho R) and S = C_p ln(p^(1/gamma) / rho).
+ *  V2 w is evaluated from the conserved state extrapolated to the flux points of each family (as
+ *     for the inviscid flux); at an element face the common value is the BR1 average of the two
+ *     sides (the far side being the neighbour, or the wall / far-field ghost state); the
+ *     gradient at the solution points is |J| dw/dx_j = sum_d D_d (S^d_j w).
+ *  V3 the gradients are extrapolated to the flux points like the solution; there
+ *     F_vis . n = (0, tau n, (U . tau - q + eta B x J) . n, eta J x n, 0) with
+ *     tau = mu (grad U + grad U^T) - 2/3 mu (div U) I, q = -kappa rho T grad S - kappa_r rho C_p grad T,
+ *     J = curl B; the printed induction row "eta curl B" is read as the antisymmetric flux whose
+ *     divergence is curl(eta J), i.e. eta J x n along n.
+ *  V4 at an element face the common viscous flux is the average of the two sides' F_vis . n
+ *     (each side's state and extrapolated gradients), along the owner's normal.
+ *  V5 at wall and far-field faces the viscous flux is this side's own (the paper's stress-free,
+ *     heat-flux and magnetic boundary conditions are not part of the inviscid wall ghost).
+ *  V6 the coefficients mu, eta, kappa, kappa_r and R are constants.
  */
 #include "sdref.h"
 
@@ -661,11 +679,169 @@ static void face_value(const sdref_mesh* m, const double* q, int64_t e, int F, i
   }
 }
 
+/* ------------------------------------------------------------------ */
+/* Viscous, resistive and thermal fluxes (Sec. MHD Governing Equations: */
+/* F = F_inv - F_vis, shear stress, heat flux, entropy; Sec. SD Method:  */
+/* BR1 common solution and viscous flux; readings V1-V6)                */
+/* ------------------------------------------------------------------ */
+
+#define NW 8 /* primitive variables whose gradients F_vis needs: u, v, w, T, S, Bx, By, Bz */
+
+/* primitive variables of a conserved state (reading V1): velocity, temperature T = p / (rho R),
+ * specific entropy S = C_p ln(p^(1/gamma) / rho) with C_p = gamma R / (gamma - 1), magnetic field */
+static void prim_w(const double* Q, const sdref_phys* ph, double* w) {
+  double rho = Q[0];
+  double p = pressure(Q, ph->gamma);
+  double cp = ph->gamma * ph->R_gas / (ph->gamma - 1.0);
+  w[0] = Q[1] / rho;
+  w[1] = Q[2] / rho;
+  w[2] = Q[3] / rho;
+  w[3] = p / (rho * ph->R_gas);
+  w[4] = cp * log(pow(p, 1.0 / ph->gamma) / rho);
+  w[5] = Q[5];
+  w[6] = Q[6];
+  w[7] = Q[7];
+}
+
+/* F_vis contracted with the vector n (reading V3), from the state Q and the gradients
+ * g[3c + j] = d w_c / d x_j:
+ *   momentum  tau n,  tau = mu (grad U + grad U^T) - 2/3 mu (div U) I
+ *   energy    (U . tau - q + eta B x J) . n,  q = -kappa rho T grad S - kappa_r rho C_p grad T
+ *   induction eta J x n,  J = curl B   (the antisymmetric flux whose divergence is curl(eta J))
+ * fm[] receives the sum of the magnitudes of the terms (comparison tolerance only). */
+static void visc_flux(const double* Q, const double* g, const double* n, const sdref_phys* ph, double* F,
+                      double* fm) {
+  double w[NW];
+  prim_w(Q, ph, w);
+  const double* u = w;
+  const double* B = w + 5;
+  double rho = Q[0], T = w[3];
+  double cp = ph->gamma * ph->R_gas / (ph->gamma - 1.0);
+  double mu = ph->mu, lam = -2.0 / 3.0 * ph->mu, eta = ph->eta;
+  double divu = g[0 * 3 + 0] + g[1 * 3 + 1] + g[2 * 3 + 2];
+  double tau[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) tau[i][j] = mu * (g[i * 3 + j] + g[j * 3 + i]) + (i == j ? lam * divu : 0.0);
+  double J[3] = {g[7 * 3 + 1] - g[6 * 3 + 2], g[5 * 3 + 2] - g[7 * 3 + 0], g[6 * 3 + 0] - g[5 * 3 + 1]};
+  double qh[3], BxJ[3], Jxn[3], uT[3];
+  for (int j = 0; j < 3; ++j) qh[j] = -ph->kappa * rho * T * g[4 * 3 + j] - ph->kappa_r * rho * cp * g[3 * 3 + j];
+  cross3(B, J, BxJ);
+  cross3(J, n, Jxn);
+  for (int j = 0; j < 3; ++j) uT[j] = u[0] * tau[0][j] + u[1] * tau[1][j] + u[2] * tau[2][j];
+  for (int v = 0; v < 9; ++v) { F[v] = 0.0; fm[v] = 0.0; }
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      F[1 + i] += tau[i][j] * n[j];
+      fm[1 + i] += fabs(tau[i][j] * n[j]);
+    }
+  for (int j = 0; j < 3; ++j) {
+    F[4] += (uT[j] - qh[j] + eta * BxJ[j]) * n[j];
+    fm[4] += (fabs(uT[j]) + fabs(qh[j]) + fabs(eta * BxJ[j])) * fabs(n[j]);
+  }
+  for (int i = 0; i < 3; ++i) {
+    F[5 + i] = eta * Jxn[i];
+    fm[5 + i] = eta * (fabs(J[(i + 1) % 3] * n[(i + 2) % 3]) + fabs(J[(i + 2) % 3] * n[(i + 1) % 3]));
+  }
+}
+
+/* this side's face state at point (a,b) of face F and the state across it: the neighbour's
+ * extrapolated solution, or the ghost state of a wall / far-field face (unit normal n of this side) */
+static void face_partner(const sdref_mesh* m, const sdref_phys* ph, const double* q, int64_t e, int F, int a, int b,
+                         const double* Qown, double* Q2) {
+  int64_t k = 6 * e + F;
+  if (m->nb_e[k] >= 0) {
+    int a2, b2;
+    map_point(m->code[k], m->N, a, b, &a2, &b2);
+    face_value(m, q, m->nb_e[k], m->nb_f[k], a2, b2, Q2);
+  } else {
+    int N = m->N, d = F / 2, f = (F & 1) ? N : 0;
+    double sgn = (F & 1) ? 1.0 : -1.0;
+    const double* S = geo_S(m, e, d, f, a, b);
+    double mag = sqrt(S[0] * S[0] + S[1] * S[1] + S[2] * S[2]);
+    double n[3] = {sgn * S[0] / mag, sgn * S[1] / mag, sgn * S[2] / mag};
+    ghost_state(Qown, n, m->bc[k], ph, Q2);
+  }
+}
+
+/* gradients of the primitive variables of element e at its solution points, g[(3c + j) N^3 + n]
+ * (reading V2): w at the flux points of each family from the extrapolated conserved state (as for
+ * the inviscid flux), the BR1 common value w^ = (w_this + w_across) / 2 at the element faces, then
+ * |J| dw/dx_j = sum_d D_d (S^d_j w) at the solution points (the conservative metric form) */
+static void element_gradient(const sdref_mesh* m, const sdref_phys* ph, const double* q, int64_t e, double* g) {
+  int N = m->N, N3 = N * N * N;
+  for (int i = 0; i < NW * 3 * N3; ++i) g[i] = 0.0;
+  for (int d = 0; d < 3; ++d)
+    for (int b = 0; b < N; ++b)
+      for (int a = 0; a < N; ++a) {
+        double Qf[MAXN + 1][9], wf[MAXN + 1][NW];
+        for (int f = 0; f <= N; ++f) {
+          for (int v = 0; v < 9; ++v) {
+            double s = 0.0;
+            for (int i = 0; i < N; ++i) s += m->E[f * N + i] * qat(m, q, v, e, sol_index(N, d, i, a, b));
+            Qf[f][v] = s;
+          }
+          prim_w(Qf[f], ph, wf[f]);
+        }
+        for (int side = 0; side < 2; ++side) {
+          int f = side ? N : 0;
+          double Q2[9], w2[NW];
+          face_partner(m, ph, q, e, 2 * d + side, a, b, Qf[f], Q2);
+          prim_w(Q2, ph, w2);
+          for (int c = 0; c < NW; ++c) wf[f][c] = 0.5 * (wf[f][c] + w2[c]);
+        }
+        for (int i = 0; i < N; ++i) {
+          int n = sol_index(N, d, i, a, b);
+          for (int c = 0; c < NW; ++c)
+            for (int j = 0; j < 3; ++j) {
+              double s = 0.0;
+              for (int f = 0; f <= N; ++f) s += m->D[i * (N + 1) + f] * geo_S(m, e, d, f, a, b)[j] * wf[f][c];
+              g[(3 * c + j) * N3 + n] += s;
+            }
+        }
+      }
+  for (int n = 0; n < N3; ++n) {
+    double J = geo_J(m, e, n);
+    for (int k = 0; k < NW * 3; ++k) g[k * N3 + n] /= J;
+  }
+}
+
+/* gradients of element e (block ge = G + e NW 3 N^3) extrapolated to point (a,b) of its face F */
+static void grad_face_value(const sdref_mesh* m, const double* G, int64_t e, int F, int a, int b, double* out) {
+  int N = m->N, N3 = N * N * N, d = F / 2, f = (F & 1) ? N : 0;
+  const double* ge = G + (int64_t)e * NW * 3 * N3;
+  for (int k = 0; k < NW * 3; ++k) {
+    double s = 0.0;
+    for (int i = 0; i < N; ++i) s += m->E[f * N + i] * ge[k * N3 + sol_index(N, d, i, a, b)];
+    out[k] = s;
+  }
+}
+
+/* common viscous flux through face F of element e at (a,b) along the unit normal n (reading V4):
+ * the average of both sides' F_vis . n; at a wall or far-field face this side's alone (reading V5) */
+static void common_visc(const sdref_mesh* m, const sdref_phys* ph, const double* q, const double* G, int64_t e, int F,
+                        int a, int b, const double* Qown, const double* gown, const double* n, double* Fv,
+                        double* Fvm) {
+  int64_t k = 6 * e + F;
+  visc_flux(Qown, gown, n, ph, Fv, Fvm);
+  if (m->nb_e[k] < 0) return;
+  int a2, b2;
+  map_point(m->code[k], m->N, a, b, &a2, &b2);
+  double Q2[9], g2[NW * 3], F2[9], F2m[9];
+  face_value(m, q, m->nb_e[k], m->nb_f[k], a2, b2, Q2);
+  grad_face_value(m, G, m->nb_e[k], m->nb_f[k], a2, b2, g2);
+  visc_flux(Q2, g2, n, ph, F2, F2m);
+  for (int v = 0; v < 9; ++v) {
+    Fv[v] = 0.5 * (Fv[v] + F2[v]);
+    Fvm[v] = 0.5 * (Fvm[v] + F2m[v]);
+  }
+}
+
 /* common contravariant flux at point (a,b) of face F of element e, given this side's value Qown.
  * Ft[9] receives S^d . F* (the family-d contravariant flux), Bt the BR1 value S^d . B*, and
  * Ftm[9] the magnitude of the terms of Ft before cancellation (tolerance only). */
-static void common_flux(const sdref_mesh* m, const sdref_phys* ph, const double* q, int64_t e, int F, int a,
-                        int b, const double* Qown, double* Ft, double* Bt, double* Ftm) {
+static void common_flux(const sdref_mesh* m, const sdref_phys* ph, const double* q, const double* G, int64_t e,
+                        int F, int a, int b, const double* Qown, const double* gown, double* Ft, double* Bt,
+                        double* Ftm) {
   int N = m->N, d = F / 2, side = F & 1, f = side ? N : 0;
   double sgn = side ? 1.0 : -1.0; /* S^d points along increasing d: outward on the d=1 face */
   int64_t k = 6 * e + F;
@@ -678,6 +854,11 @@ static void common_flux(const sdref_mesh* m, const sdref_phys* ph, const double*
     ghost_state(Qown, n, m->bc[k], ph, g);
     rusanov_mag(Qown, g, n, ph->gamma, ph->c_h, Fs, Fm);
     Bn = 0.5 * ((Qown[5] + g[5]) * n[0] + (Qown[6] + g[6]) * n[1] + (Qown[7] + g[7]) * n[2]);
+    if (G) {
+      double Fv[9], Fvm[9];
+      common_visc(m, ph, q, G, e, F, a, b, Qown, gown, n, Fv, Fvm);
+      for (int v = 0; v < 9; ++v) { Fs[v] -= Fv[v]; Fm[v] += Fvm[v]; }
+    }
   } else {
     int64_t e2 = m->nb_e[k];
     int F2 = m->nb_f[k], a2, b2;
@@ -690,6 +871,11 @@ static void common_flux(const sdref_mesh* m, const sdref_phys* ph, const double*
       double n[3] = {sgn * S[0] / mag, sgn * S[1] / mag, sgn * S[2] / mag};
       rusanov_mag(Qown, Q2, n, ph->gamma, ph->c_h, Fs, Fm);
       Bn = 0.5 * ((Qown[5] + Q2[5]) * n[0] + (Qown[6] + Q2[6]) * n[1] + (Qown[7] + Q2[7]) * n[2]);
+      if (G) {
+        double Fv[9], Fvm[9];
+        common_visc(m, ph, q, G, e, F, a, b, Qown, gown, n, Fv, Fvm);
+        for (int v = 0; v < 9; ++v) { Fs[v] -= Fv[v]; Fm[v] += Fvm[v]; }
+      }
     } else {
       /* the owner (neighbour) side defines the normal: F* computed with the owner as left state */
       int d2 = F2 / 2, f2 = (F2 & 1) ? N : 0;
@@ -699,6 +885,11 @@ static void common_flux(const sdref_mesh* m, const sdref_phys* ph, const double*
       double n[3] = {sgn2 * S[0] / mag, sgn2 * S[1] / mag, sgn2 * S[2] / mag};
       rusanov_mag(Q2, Qown, n, ph->gamma, ph->c_h, Fs, Fm);
       Bn = 0.5 * ((Q2[5] + Qown[5]) * n[0] + (Q2[6] + Qown[6]) * n[1] + (Q2[7] + Qown[7]) * n[2]);
+      if (G) { /* the average of both sides' F_vis . n is symmetric in the two sides */
+        double Fv[9], Fvm[9];
+        common_visc(m, ph, q, G, e, F, a, b, Qown, gown, n, Fv, Fvm);
+        for (int v = 0; v < 9; ++v) { Fs[v] -= Fv[v]; Fm[v] += Fvm[v]; }
+      }
       for (int v = 0; v < 9; ++v) Fs[v] = -Fs[v]; /* this side's outward normal is -n */
       Bn = -Bn;
     }
@@ -742,9 +933,11 @@ static void sources(const sdref_phys* ph, const double* Q, double divB, const do
   mag[8] += fabs(ph->glm_alpha * Q[8]);
 }
 
-/* residual of one element: out[9][N^3]; divb[N^3] (may be NULL); smax[9] running max of scale */
-static void residual_element(const sdref_mesh* m, const sdref_phys* ph, const double* q, int64_t e, double* out,
-                             double* divb, double* smax) {
+/* residual of one element: out[9][N^3]; divb[N^3] (may be NULL); smax[9] running max of scale;
+ * G: gradients of every element the residual reads ([n_e][3 NW][N^3], element_gradient), or NULL
+ * without the viscous fluxes */
+static void residual_element(const sdref_mesh* m, const sdref_phys* ph, const double* q, const double* G, int64_t e,
+                             double* out, double* divb, double* smax) {
   int N = m->N, N3 = N * N * N;
   double Qe[9][MAXN * MAXN * MAXN];
   double div[9][MAXN * MAXN * MAXN], mag[9][MAXN * MAXN * MAXN], dB[MAXN * MAXN * MAXN];
@@ -756,6 +949,7 @@ static void residual_element(const sdref_mesh* m, const sdref_phys* ph, const do
     for (int b = 0; b < N; ++b)
       for (int a = 0; a < N; ++a) {
         double Qf[MAXN + 1][9], Ft[MAXN + 1][9], Ftm[MAXN + 1][9], Bt[MAXN + 1];
+        double gf[MAXN + 1][NW * 3];
         /* extrapolate the solution along the line to the family-d flux points */
         for (int f = 0; f <= N; ++f)
           for (int v = 0; v < 9; ++v) {
@@ -763,16 +957,31 @@ static void residual_element(const sdref_mesh* m, const sdref_phys* ph, const do
             for (int i = 0; i < N; ++i) s += m->E[f * N + i] * Qe[v][sol_index(N, d, i, a, b)];
             Qf[f][v] = s;
           }
-        /* interior flux points: contravariant flux S^d . F(Q) */
+        /* and the solution gradients (viscous fluxes, reading V3), with grad_face_value's sums */
+        if (G) {
+          const double* ge = G + (int64_t)e * NW * 3 * N3;
+          for (int f = 0; f <= N; ++f)
+            for (int k = 0; k < NW * 3; ++k) {
+              double s = 0.0;
+              for (int i = 0; i < N; ++i) s += m->E[f * N + i] * ge[k * N3 + sol_index(N, d, i, a, b)];
+              gf[f][k] = s;
+            }
+        }
+        /* interior flux points: contravariant flux S^d . (F_inv(Q) - F_vis(Q, grad w)) */
         for (int f = 1; f < N; ++f) {
           const double* S = geo_S(m, e, d, f, a, b);
           sdref_flux(Qf[f], S, ph->gamma, ph->c_h, Ft[f]);
           for (int v = 0; v < 9; ++v) Ftm[f][v] = fabs(Ft[f][v]);
+          if (G) {
+            double Fv[9], Fvm[9];
+            visc_flux(Qf[f], gf[f], S, ph, Fv, Fvm);
+            for (int v = 0; v < 9; ++v) { Ft[f][v] -= Fv[v]; Ftm[f][v] += Fvm[v]; }
+          }
           Bt[f] = S[0] * Qf[f][5] + S[1] * Qf[f][6] + S[2] * Qf[f][7];
         }
         /* element-boundary flux points: common (Rusanov / BR1) values */
-        common_flux(m, ph, q, e, 2 * d + 0, a, b, Qf[0], Ft[0], &Bt[0], Ftm[0]);
-        common_flux(m, ph, q, e, 2 * d + 1, a, b, Qf[N], Ft[N], &Bt[N], Ftm[N]);
+        common_flux(m, ph, q, G, e, 2 * d + 0, a, b, Qf[0], gf[0], Ft[0], &Bt[0], Ftm[0]);
+        common_flux(m, ph, q, G, e, 2 * d + 1, a, b, Qf[N], gf[N], Ft[N], &Bt[N], Ftm[N]);
         /* derivative of the flux polynomial at the solution points */
         for (int i = 0; i < N; ++i) {
           int n = sol_index(N, d, i, a, b);
@@ -817,6 +1026,12 @@ int sdref_residual(sdref_mesh* m, const sdref_phys* ph, const double* q, double*
   int N = m->N;
   int64_t N3 = (int64_t)N * N * N;
   int nth = sdref_get_threads();
+  double* G = NULL;
+  if (ph->viscous) {
+    G = (double*)malloc(sizeof(double) * NW * 3 * N3 * m->n_e);
+#pragma omp parallel for schedule(dynamic, 8) num_threads(nth)
+    for (int64_t e = 0; e < m->n_e; ++e) element_gradient(m, ph, q, e, G + e * NW * 3 * N3);
+  }
   double* sc = (double*)calloc(9 * (size_t)(nth > 0 ? nth : 1), sizeof(double));
 #pragma omp parallel num_threads(nth)
   {
@@ -828,7 +1043,7 @@ int sdref_residual(sdref_mesh* m, const sdref_phys* ph, const double* q, double*
     double* db = (double*)malloc(sizeof(double) * N3);
 #pragma omp for schedule(dynamic, 8)
     for (int64_t e = 0; e < m->n_e; ++e) {
-      residual_element(m, ph, q, e, buf, db, sc + 9 * tid);
+      residual_element(m, ph, q, G, e, buf, db, sc + 9 * tid);
       for (int v = 0; v < 9; ++v)
         for (int64_t n = 0; n < N3; ++n) dqdt[((int64_t)v * m->n_e + e) * N3 + n] = buf[v * N3 + n];
       if (divb)
@@ -845,6 +1060,7 @@ int sdref_residual(sdref_mesh* m, const sdref_phys* ph, const double* q, double*
     }
   }
   free(sc);
+  free(G);
   return 0;
 }
 
@@ -859,11 +1075,20 @@ int sdref_residual_elements(sdref_mesh* m, const sdref_phys* ph, const double* q
     for (int F = 0; F < 6; ++F)
       if (m->nb_e[6 * e + F] >= 0) need[m->nb_e[6 * e + F]] = 1;
   }
-  int rc = ensure_geometry(m, need);
-  free(need);
-  if (rc) return rc;
   int64_t N3 = (int64_t)m->N * m->N * m->N;
   int nth = sdref_get_threads();
+  double* G = NULL;
+  int rc = ensure_geometry(m, need);
+  if (rc) { free(need); return rc; }
+  if (ph->viscous) {
+    /* gradients of the listed elements and of their neighbours (an element's gradients read only
+       its own geometry and its neighbours' states) */
+    G = (double*)calloc((size_t)NW * 3 * N3 * m->n_e, sizeof(double));
+#pragma omp parallel for schedule(dynamic, 4) num_threads(nth)
+    for (int64_t e = 0; e < m->n_e; ++e)
+      if (need[e]) element_gradient(m, ph, q, e, G + e * NW * 3 * N3);
+  }
+  free(need);
   double* sc = (double*)calloc(9 * (size_t)(nth > 0 ? nth : 1), sizeof(double));
 #pragma omp parallel for schedule(dynamic, 4) num_threads(nth)
   for (int64_t l = 0; l < n_list; ++l) {
@@ -871,8 +1096,9 @@ int sdref_residual_elements(sdref_mesh* m, const sdref_phys* ph, const double* q
 #ifdef _OPENMP
     tid = omp_get_thread_num();
 #endif
-    residual_element(m, ph, q, elems[l], out + l * 9 * N3, NULL, sc + 9 * tid);
+    residual_element(m, ph, q, G, elems[l], out + l * 9 * N3, NULL, sc + 9 * tid);
   }
+  free(G);
   if (scale)
     for (int v = 0; v < 9; ++v) {
       scale[v] = 0.0;
@@ -880,6 +1106,18 @@ int sdref_residual_elements(sdref_mesh* m, const sdref_phys* ph, const double* q
         if (sc[9 * t + v] > scale[v]) scale[v] = sc[9 * t + v];
     }
   free(sc);
+  return 0;
+}
+
+/* gradients of the primitive variables (u, v, w, T, S, Bx, By, Bz) at every solution point,
+ * grad[e][3 c + j][N^3] = d w_c / d x_j (reading V2) */
+int sdref_gradients(sdref_mesh* m, const sdref_phys* ph, const double* q, double* grad) {
+  if (check_inputs(m, ph, q) || !grad) return 1;
+  if (ensure_geometry(m, NULL)) return 2;
+  int64_t N3 = (int64_t)m->N * m->N * m->N;
+  int nth = sdref_get_threads();
+#pragma omp parallel for schedule(dynamic, 8) num_threads(nth)
+  for (int64_t e = 0; e < m->n_e; ++e) element_gradient(m, ph, q, e, grad + e * NW * 3 * N3);
   return 0;
 }
 

@@ -42,6 +42,12 @@ typedef struct {
   double gamma, GM, omega, glm_alpha, c_h;
   int32_t powell, gravity, coriolis, pad_;
   double farfield[9]; /* conserved ghost state for SDREF_BC_FARFIELD faces */
+  /* viscous, resistive and thermal fluxes F_vis (Sec. MHD Governing Equations), used when viscous != 0:
+   * dynamic viscosity mu (lambda = -2/3 mu), magnetic diffusivity eta, thermal diffusivity kappa of the
+   * entropy term, radiative diffusivity kappa_r, specific gas constant R_gas (T = p / (rho R_gas),
+   * C_p = gamma R_gas / (gamma - 1)), all constant */
+  double mu, eta, kappa, kappa_r, R_gas;
+  int32_t viscous, pad2_;
 } sdref_phys;
 
 typedef struct {
@@ -76,6 +82,9 @@ int sdref_geometry(sdref_mesh* m, int64_t e, double* S, double* J, double* X, do
  * may be NULL. */
 int sdref_residual(sdref_mesh* m, const sdref_phys* ph, const double* q, double* dqdt, double* divb, double* scale);
 /* Residual on a list of elements only; out[list][9][N^3]. */
+/* gradients of the primitive variables (u, v, w, T, S, Bx, By, Bz) at the solution points with the
+ * BR1 common solution at element faces: grad[e][3 c + j][N^3] = d w_c / d x_j (viscous fluxes) */
+int sdref_gradients(sdref_mesh* m, const sdref_phys* ph, const double* q, double* grad);
 int sdref_residual_elements(sdref_mesh* m, const sdref_phys* ph, const double* q, int64_t n_list,
                             const int64_t* elems, double* out, double* scale);
 /* One Shu-Osher SSP-RK3 stage: q_out = a_s q_n + b_s (q_in + dt R(q_in)). */

@@ -24,7 +24,8 @@ class _Phys(C.Structure):
     _fields_ = [("gamma", C.c_double), ("GM", C.c_double), ("omega", C.c_double),
                 ("glm_alpha", C.c_double), ("c_h", C.c_double), ("powell", C.c_int32),
                 ("gravity", C.c_int32), ("coriolis", C.c_int32), ("pad_", C.c_int32),
-                ("farfield", C.c_double * 9)]
+                ("farfield", C.c_double * 9), ("mu", C.c_double), ("eta", C.c_double), ("kappa", C.c_double),
+                ("kappa_r", C.c_double), ("R_gas", C.c_double), ("viscous", C.c_int32), ("pad2_", C.c_int32)]
 
 
 class _Diag(C.Structure):
@@ -43,6 +44,13 @@ class Phys:
     gravity: int = 0
     coriolis: int = 0
     farfield: Sequence[float] = field(default_factory=lambda: [0.0] * 9)
+    # viscous, resistive and thermal fluxes (off unless viscous=1)
+    mu: float = 0.0
+    eta: float = 0.0
+    kappa: float = 0.0
+    kappa_r: float = 0.0
+    R_gas: float = 1.0
+    viscous: int = 0
 
     def _c(self) -> _Phys:
         p = _Phys()
@@ -50,6 +58,8 @@ class Phys:
         p.powell, p.gravity, p.coriolis = int(self.powell), int(self.gravity), int(self.coriolis)
         for i in range(9):
             p.farfield[i] = float(self.farfield[i])
+        p.mu, p.eta, p.kappa, p.kappa_r, p.R_gas = self.mu, self.eta, self.kappa, self.kappa_r, self.R_gas
+        p.viscous = int(self.viscous)
         return p
 
 
@@ -71,6 +81,7 @@ def lib():
         L.sdref_geometry.argtypes = [C.c_void_p, C.c_int64, dp, dp, dp, dp]
         L.sdref_residual.argtypes = [C.c_void_p, C.POINTER(_Phys), dp, dp, dp, dp]
         L.sdref_residual_elements.argtypes = [C.c_void_p, C.POINTER(_Phys), dp, C.c_int64, ip, dp, dp]
+        L.sdref_gradients.argtypes = [C.c_void_p, C.POINTER(_Phys), dp, dp]
         L.sdref_rk_stage.argtypes = [C.c_void_p, C.POINTER(_Phys), C.c_int, C.c_double, dp, dp, dp]
         L.sdref_diagnostics.argtypes = [C.c_void_p, C.POINTER(_Phys), dp, C.POINTER(_Diag)]
         L.sdref_state_init.argtypes = [C.c_void_p, C.POINTER(_Phys), C.c_int, dp, C.c_uint64, dp, dp]
@@ -224,6 +235,14 @@ class Mesh:
         _check(lib().sdref_residual_elements(self._h_ptr, C.byref(ph), _dp(q), el.size,
                                              el.ctypes.data_as(C.POINTER(C.c_int64)), _dp(out), _dp(scale)))
         return out, scale
+
+    def gradients(self, phys: Phys, q):
+        """gradients of (u, v, w, T, S, Bx, By, Bz) at the solution points: [n_e, 8, 3, N^3]"""
+        q = self._q(q)
+        out = np.zeros((self.n_e, 8, 3, self.N3))
+        ph = phys._c()
+        _check(lib().sdref_gradients(self._h_ptr, C.byref(ph), _dp(q), _dp(out)))
+        return out
 
     def rk_stage(self, phys: Phys, stage: int, dt: float, q_n, q_in):
         q_in = self._q(q_in)
