@@ -103,6 +103,15 @@ typedef struct {
   int32_t coriolis; /* 1: Coriolis force in M */
   int32_t pad_;
   double farfield[9]; /* conserved ghost state of SD_BC_FARFIELD faces */
+  /* Viscous, resistive and thermal fluxes F_vis (Sec. MHD Governing Equations; F = F_inv - F_vis),
+   * with gradients of (U, T, S, B) by the BR1 scheme (Sec. SD Method), when viscous != 0 (SD_FP64
+   * only; constant coefficients):  mu dynamic viscosity (lambda = -2/3 mu), eta magnetic
+   * diffusivity, kappa thermal diffusivity of the entropy term, kappa_r radiative diffusivity,
+   * R_gas specific gas constant (T = p / (rho R_gas), C_p = gamma R_gas / (gamma - 1)).  The
+   * time step of sd_step stays the inviscid one: the caller keeps cfl within the viscous limit. */
+  double mu, eta, kappa, kappa_r, R_gas;
+  int32_t viscous;
+  int32_t pad2_;
 } sd_phys;
 
 typedef struct {
@@ -280,7 +289,9 @@ sd_status sd_diagnostics(const sd_mesh* mesh, const sd_phys* phys, const double*
  * All calls share the one array, which keeps the last call's contents (every
  * entry a call reads is written earlier in the same call), so calls whose work
  * overlaps on the GPU (other streams, other threads) race.  q and dqdt: device
- * states; the mesh must belong to the current device.  Asynchronous. */
+ * states; the mesh must belong to the current device.  Inviscid only: phys with
+ * viscous set is rejected with SD_ERR_UNSUPPORTED (the viscous fluxes need
+ * gradient buffers).  Asynchronous. */
 sd_status sd_residual_noalloc(const sd_mesh* mesh, const sd_phys* phys, const double* q, double* dqdt, void* stream);
 
 /* Kernel timing (tracing): with enable = 1 every kernel the library launches

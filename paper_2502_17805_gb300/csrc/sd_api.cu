@@ -213,7 +213,7 @@ void free_mesh(sd_mesh* m) {
   for (cudaEvent_t ev : m->prof_ev) cudaEventDestroy(ev);
   void* ptrs[] = {m->Sfam64, m->invJ64, m->X64, m->Sfam32, m->invJ32, m->X32, m->nbr, m->meta,
                   m->tr64[0], m->tr64[1], m->tr32[0], m->tr32[1], m->dyn, m->diag_part, m->diag_out, m->divb,
-                  m->err};
+                  m->err, m->grad, m->gtr};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (m->host_diag) cudaFreeHost(m->host_diag);
@@ -254,8 +254,15 @@ sd::StageParams base_params(const sd_mesh* m, const sd_phys* ph, int prec) {
   P.nbr = m->nbr;
   P.meta = m->meta;
   P.err = m->err;
+  P.visc = ph->viscous ? 1 : 0;
+  P.mu = ph->mu;
+  P.eta = ph->eta;
+  P.kappa = ph->kappa;
+  P.kappa_r = ph->kappa_r;
+  P.R_gas = ph->R_gas;
   return P;
 }
+
 
 void* trace_buf(sd_mesh* m, int prec, int b) { return prec == SD_FP64 ? (void*)m->tr64[b] : (void*)m->tr32[b]; }
 
@@ -285,11 +292,47 @@ struct ProfScope {
   }
 };
 
+// Viscous FP64 path: the BR1 gradients of P.q_in (whose face traces are P.tr_in)
+// and their face traces, into the mesh's gradient buffers (allocated on first use);
+// P then points the stage kernel at them.  No-op without viscous fluxes.
+cudaError_t prepare_viscous(sd_mesh* m, sd::StageParams& P, cudaStream_t s) {
+  if (!P.visc) return cudaSuccess;
+  const size_t N2 = (size_t)m->N * m->N, N3 = N2 * m->N, ne = (size_t)std::max<int64_t>(m->n_e, 1);
+  cudaError_t err = cudaSuccess;
+  if (!m->grad) {
+    err = cudaMalloc((void**)&m->grad, ne * sd::NGRAD * N3 * sizeof(double));
+    if (err != cudaSuccess) return err;
+    m->device_bytes += (int64_t)(ne * sd::NGRAD * N3 * sizeof(double));
+  }
+  if (!m->gtr) {
+    err = cudaMalloc((void**)&m->gtr, ne * 6 * sd::NGRAD * N2 * sizeof(double));
+    if (err != cudaSuccess) return err;
+    m->device_bytes += (int64_t)(ne * 6 * sd::NGRAD * N2 * sizeof(double));
+  }
+  sd::StageParams G = P;
+  G.grad_out = m->grad;
+  G.gtr_out = m->gtr;
+  {
+    ProfScope ps(m, PROF_OTHER, s);
+    err = sd::launch_grad(m, G, s);
+  }
+  P.grad = m->grad;
+  P.gtr_in = m->gtr;
+  return err;
+}
+
 sd_status check_common(const sd_mesh* m, const sd_phys* ph, int prec, const sd_background* bg) {
   if (!m) return fail(SD_ERR_INVALID_ARGUMENT, "mesh is NULL");
   if (!ph) return fail(SD_ERR_INVALID_ARGUMENT, "phys is NULL");
   if (prec != SD_FP64 && prec != SD_FP32_MIXED) return fail(SD_ERR_INVALID_ARGUMENT, "unknown precision");
   if (!(ph->gamma > 1.0)) return fail(SD_ERR_INVALID_ARGUMENT, "gamma must exceed 1");
+  if (ph->viscous) {
+    if (prec != SD_FP64) return fail(SD_ERR_UNSUPPORTED, "viscous fluxes run on the SD_FP64 path only");
+    if (!(ph->mu >= 0.0) || !(ph->eta >= 0.0) || !(ph->kappa >= 0.0) || !(ph->kappa_r >= 0.0) ||
+        !isfinite(ph->mu + ph->eta + ph->kappa + ph->kappa_r))
+      return fail(SD_ERR_INVALID_ARGUMENT, "viscous coefficients must be finite and non-negative");
+    if (!(ph->R_gas > 0.0) || !isfinite(ph->R_gas)) return fail(SD_ERR_INVALID_ARGUMENT, "R_gas must be positive");
+  }
   if (prec == SD_FP32_MIXED) {
     if (!bg) return fail(SD_ERR_INVALID_ARGUMENT, "the FP32-mixed path needs a background (sd_background_create)");
     if (bg->mesh != m) return fail(SD_ERR_INVALID_ARGUMENT, "background belongs to another mesh");
@@ -670,6 +713,7 @@ sd_status sd_residual(const sd_mesh* m, const sd_phys* ph, sd_precision prec, co
   P.tr_out = nullptr;
   P.mode = sd::MODE_RESIDUAL;
   P.out = dqdt;
+  if ((err = prepare_viscous(mm, P, s)) != cudaSuccess) return cuda_fail(err, "gradient kernel");
   {
     ProfScope ps(m, PROF_STAGE, s);
     err = sd::launch_stage(m, prec, P, s);
@@ -721,7 +765,8 @@ static sd_status rk_stage_impl(sd_mesh* m, const sd_phys* ph, int prec, int stag
     P.lsr_read = lsr_read;
     P.lsr_write = lsr_write;
   }
-  cudaError_t err;
+  cudaError_t err = prepare_viscous(m, P, s);
+  if (err != cudaSuccess) return cuda_fail(err, "gradient kernel");
   {
     ProfScope ps(m, PROF_STAGE, s);
     err = sd::launch_stage(m, prec, P, s);
@@ -801,6 +846,7 @@ static sd_status advance_impl(sd_mesh* mm, const sd_phys* ph, sd_precision prec,
       S.lsr_write = 1;
       S.incr = 1;
     }
+    SD_CUDA(prepare_viscous(mm, S, s));
     {
       ProfScope ps(mm, PROF_STAGE, s);
       SD_CUDA(sd::launch_stage(mm, prec, S, s));
@@ -817,6 +863,7 @@ static sd_status advance_impl(sd_mesh* mm, const sd_phys* ph, sd_precision prec,
       S.lsr_read = 1;
       S.lsr_write = 2;
     }
+    SD_CUDA(prepare_viscous(mm, S, s));
     {
       ProfScope ps(mm, PROF_STAGE, s);
       SD_CUDA(sd::launch_stage(mm, prec, S, s));
@@ -835,6 +882,7 @@ static sd_status advance_impl(sd_mesh* mm, const sd_phys* ph, sd_precision prec,
       S.lsr_read = 1;
       S.lsr_write = 0;
     }
+    SD_CUDA(prepare_viscous(mm, S, s));
     {
       ProfScope ps(mm, PROF_STAGE, s);
       SD_CUDA(sd::launch_stage(mm, prec, S, s));

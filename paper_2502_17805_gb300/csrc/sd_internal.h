@@ -75,6 +75,15 @@ struct StageParams {
   // state is q^n + D; stages with lsr_write only advance D, the last writes q^n + D + t
   int incr;
   int* err;  // device error word (bounded waits that ran out)
+  // viscous, resistive and thermal fluxes (FP64 policy): coefficients, the gradients of
+  // (U, T, S, B) at the solution points [e][24][N^3] (grad[3c + j] = d w_c / d x_j) and their
+  // face traces [e][F][24][N^2]; the gradient kernel writes grad_out / gtr_out
+  int visc;
+  double mu, eta, kappa, kappa_r, R_gas;
+  const double* grad;
+  const double* gtr_in;
+  double* grad_out;
+  double* gtr_out;
 };
 
 }  // namespace sd
@@ -107,6 +116,8 @@ struct sd_mesh {
   double* divb;             // [n_e * N^3]
   double* host_diag;        // pinned [12]
   int* err;                 // device error word of the stage kernels
+  double* grad;             // viscous path, allocated on first use: gradients [e][24][N^3]
+  double* gtr;              //   and their face traces [e][F][24][N^2]
   int64_t device_bytes;
   sd::Ops<double> ops64;
   sd::Ops<float> ops32;
@@ -130,9 +141,13 @@ struct sd_background {
 namespace sd {
 // partial maxima of lambda per mesh: the warps of a launch spread their atomics over these
 constexpr int LAM_SLOTS = 256;
+// gradients the viscous fluxes need: 8 primitive variables x 3 directions, index 3 c + j
+constexpr int NGRAD = 24;
 // kernels launched from the API (defined in the .cu files)
 cudaError_t launch_stage(const sd_mesh* m, int prec, const StageParams& P, cudaStream_t s);
 cudaError_t launch_traces(const sd_mesh* m, int prec, const StageParams& P, cudaStream_t s);
+// BR1 gradients of the primitive variables and their face traces (viscous FP64 path)
+cudaError_t launch_grad(const sd_mesh* m, const StageParams& P, cudaStream_t s);
 cudaError_t launch_geometry(sd_mesh* m, const double* d_corners, int* d_flag, cudaStream_t s);
 cudaError_t launch_canonical_faces(sd_mesh* m, cudaStream_t s);
 cudaError_t launch_state_init(const sd_mesh* m, const sd_phys* ph, const sd_init* in, double B0dip, double* q,

@@ -52,6 +52,8 @@ sd_status sd_residual_noalloc(const sd_mesh* m, const sd_phys* ph, const double*
     return noalloc_fail(SD_ERR_INVALID_ARGUMENT, "q and dqdt must be 16-byte aligned");
   if (q == dqdt) return noalloc_fail(SD_ERR_INVALID_ARGUMENT, "dqdt must not alias q");
   if (!(ph->gamma > 1.0)) return noalloc_fail(SD_ERR_INVALID_ARGUMENT, "gamma must exceed 1");
+  if (ph->viscous)
+    return noalloc_fail(SD_ERR_UNSUPPORTED, "viscous fluxes need gradient buffers: use sd_residual");
   const size_t N2 = (size_t)m->N * m->N;
   const size_t need = (size_t)m->n_e * 6 * 9 * N2;
   if (need > kNoAllocScratchDoubles)

@@ -21,6 +21,20 @@
 namespace sd {
 
 template <int N>
+struct Dims;
+template <int N, class Pol>
+__device__ __forceinline__ void load_element(const StageParams& P, const double* q, int64_t e,
+                                             typename Pol::R* sQ, double* lam_out);
+template <int N>
+__device__ __forceinline__ int sol_index(int d, int i, int a, int b);
+
+}  // namespace sd
+
+#include "sd_viscous.cuh"
+
+namespace sd {
+
+template <int N>
 struct Dims {
   static constexpr int N2 = N * N, N3 = N2 * N, NF = N + 1;
   static constexpr int NFACE = 6 * N2;
@@ -278,10 +292,11 @@ __device__ __forceinline__ void sources_mixed(const MixedConsts& C, const float*
   M[8] -= C.alpha * q[8];
 }
 
-template <int N, class Pol>
+template <int N, class Pol, bool VISC>
 __global__ void __launch_bounds__(Dims<N>::BLK) stage_kernel(const StageParams P, const Ops<typename Pol::R> ops) {
   using R = typename Pol::R;
   using S = Smem<N, Pol>;
+  static_assert(!VISC || !Pol::mixed, "viscous fluxes run on the FP64 policy");
   constexpr int N2 = N * N, N3 = N2 * N, NF = N + 1, BLK = Dims<N>::BLK, NV = Pol::NV;
   extern __shared__ __align__(16) unsigned char smem[];
   R* sQ = reinterpret_cast<R*>(smem) + S::oQ;
@@ -307,6 +322,14 @@ __global__ void __launch_bounds__(Dims<N>::BLK) stage_kernel(const StageParams P
   const R ch = R(chd);
 
   load_element<N, Pol>(P, P.q_in, e, sQ, nullptr);
+  // viscous fluxes: this element's gradients [24][N3] after the state
+  [[maybe_unused]] double* sG = reinterpret_cast<double*>(smem + S::bytes);
+  [[maybe_unused]] ViscCoef vc;
+  if constexpr (VISC) {
+    vc = visc_coef(P);
+    const double* Ge = P.grad + e * NGRAD * N3;
+    for (int i = tid; i < NGRAD * N3; i += BLK) sG[i] = Ge[i];
+  }
   __syncthreads();
 
   // ---- element faces: common flux and BR1 normal field
@@ -362,6 +385,26 @@ __global__ void __launch_bounds__(Dims<N>::BLK) stage_kernel(const StageParams P
     } else {
       riemann_mixed(qo, qn, nx, ny, nz, gamma, ch, jr, jp, Fs);
     }
+    if constexpr (VISC) {
+      // average of both sides' F_vis . n (this side's alone at a wall or far-field face)
+      double g[NGRAD], Fv[9];
+      grad_face<N>(sG, sE, F, a, b, g);
+      visc_flux(qo, g, nx, ny, nz, vc, Fv);
+      if (nb >= 0) {
+        const int code = meta_code(mt);
+        const int u = (code & 4) ? b : a, w = (code & 4) ? a : b;
+        const int a2 = (code & 2) ? N - 1 - u : u, b2 = (code & 1) ? N - 1 - w : w;
+        const double* Gt = P.gtr_in + ((int64_t)nb * 6 + meta_nbF(mt)) * NGRAD * N2 + a2 + N * b2;
+#pragma unroll
+        for (int k = 0; k < NGRAD; ++k) g[k] = Gt[k * N2];
+        double Fn[9];
+        visc_flux(qn, g, nx, ny, nz, vc, Fn);
+#pragma unroll
+        for (int v = 0; v < 9; ++v) Fv[v] = 0.5 * (Fv[v] + Fn[v]);
+      }
+#pragma unroll
+      for (int v = 0; v < 9; ++v) Fs[v] -= Fv[v];
+    }
     const R Bn = R(0.5) * ((qo[5] + qn[5]) * nx + (qo[6] + qn[6]) * ny + (qo[7] + qn[7]) * nz);
     const R sm = sg * mag;
 #pragma unroll
@@ -395,6 +438,19 @@ __global__ void __launch_bounds__(Dims<N>::BLK) stage_kernel(const StageParams P
         flux_full<R>(qf, Sx, Sy, Sz, gm1, ch, Fv);
       } else {
         flux_pert(qf, Sx, Sy, Sz, gm1, gamma / gm1, ch, Fv);
+      }
+      if constexpr (VISC) {
+        double g[NGRAD], Fvis[9];
+#pragma unroll
+        for (int k = 0; k < NGRAD; ++k) {
+          double s = 0.0;
+#pragma unroll
+          for (int i = 0; i < N; ++i) s += sE[f * N + i] * sG[k * N3 + sol_index<N>(d, i, a, b)];
+          g[k] = s;
+        }
+        visc_flux(qf, g, Sx, Sy, Sz, vc, Fvis);
+#pragma unroll
+        for (int v = 0; v < 9; ++v) Fv[v] -= Fvis[v];
       }
 #pragma unroll
       for (int v = 0; v < 9; ++v) sF[(v * NF + f) * N2 + line] = Fv[v];
@@ -504,11 +560,11 @@ __global__ void __launch_bounds__(Dims<N>::BLK) stage_kernel(const StageParams P
   }
 }
 
-template <int N, class Pol>
+template <int N, class Pol, bool VISC = false>
 cudaError_t launch_stage_t(const StageParams& P, const Ops<typename Pol::R>& ops, bool traces_only, cudaStream_t s) {
   using Sm = Smem<N, Pol>;
-  const size_t bytes = traces_only ? Sm::trace_bytes : Sm::bytes;
-  auto kern = traces_only ? trace_kernel<N, Pol> : stage_kernel<N, Pol>;
+  const size_t bytes = traces_only ? Sm::trace_bytes : Sm::bytes + (VISC ? NGRAD * N * N * N * sizeof(double) : 0);
+  auto kern = traces_only ? trace_kernel<N, Pol> : stage_kernel<N, Pol, VISC>;
   if (bytes > 48 * 1024) {
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (err != cudaSuccess) return err;

@@ -1,17 +1,39 @@
-// Instantiations of the fused element kernels for the FP64 policy, N = 2..8.
+// Instantiations of the fused element kernels for the FP64 policy, N = 2..8,
+// with and without the viscous fluxes, and of the BR1 gradient kernel.
 #include "sd_stage.cuh"
 
 namespace sd {
 
+template <int N>
+static cudaError_t launch_fp64_n(const sd_mesh* m, const StageParams& P, bool traces_only, cudaStream_t s) {
+  // the viscous instantiation once the gradient pass has filled P.grad (not for MODE_DIVB)
+  if (P.visc && P.grad && !traces_only && P.mode != MODE_DIVB)
+    return launch_stage_t<N, PolFP64, true>(P, m->ops64, false, s);
+  return launch_stage_t<N, PolFP64>(P, m->ops64, traces_only, s);
+}
+
 cudaError_t launch_stage_fp64(const sd_mesh* m, const StageParams& P, bool traces_only, cudaStream_t s) {
   switch (m->N) {
-    case 2: return launch_stage_t<2, PolFP64>(P, m->ops64, traces_only, s);
-    case 3: return launch_stage_t<3, PolFP64>(P, m->ops64, traces_only, s);
-    case 4: return launch_stage_t<4, PolFP64>(P, m->ops64, traces_only, s);
-    case 5: return launch_stage_t<5, PolFP64>(P, m->ops64, traces_only, s);
-    case 6: return launch_stage_t<6, PolFP64>(P, m->ops64, traces_only, s);
-    case 7: return launch_stage_t<7, PolFP64>(P, m->ops64, traces_only, s);
-    case 8: return launch_stage_t<8, PolFP64>(P, m->ops64, traces_only, s);
+    case 2: return launch_fp64_n<2>(m, P, traces_only, s);
+    case 3: return launch_fp64_n<3>(m, P, traces_only, s);
+    case 4: return launch_fp64_n<4>(m, P, traces_only, s);
+    case 5: return launch_fp64_n<5>(m, P, traces_only, s);
+    case 6: return launch_fp64_n<6>(m, P, traces_only, s);
+    case 7: return launch_fp64_n<7>(m, P, traces_only, s);
+    case 8: return launch_fp64_n<8>(m, P, traces_only, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_grad(const sd_mesh* m, const StageParams& P, cudaStream_t s) {
+  switch (m->N) {
+    case 2: return launch_grad_t<2>(P, m->ops64, s);
+    case 3: return launch_grad_t<3>(P, m->ops64, s);
+    case 4: return launch_grad_t<4>(P, m->ops64, s);
+    case 5: return launch_grad_t<5>(P, m->ops64, s);
+    case 6: return launch_grad_t<6>(P, m->ops64, s);
+    case 7: return launch_grad_t<7>(P, m->ops64, s);
+    case 8: return launch_grad_t<8>(P, m->ops64, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -48,7 +48,9 @@ class MeshDesc(C.Structure):
 class PhysC(C.Structure):
     _fields_ = [("gamma", C.c_double), ("GM", C.c_double), ("omega", C.c_double), ("glm_alpha", C.c_double),
                 ("c_h", C.c_double), ("powell", C.c_int32), ("gravity", C.c_int32), ("coriolis", C.c_int32),
-                ("pad_", C.c_int32), ("farfield", C.c_double * 9)]
+                ("pad_", C.c_int32), ("farfield", C.c_double * 9), ("mu", C.c_double), ("eta", C.c_double),
+                ("kappa", C.c_double), ("kappa_r", C.c_double), ("R_gas", C.c_double), ("viscous", C.c_int32),
+                ("pad2_", C.c_int32)]
 
 
 class InitC(C.Structure):
@@ -88,6 +90,13 @@ class Phys:
     gravity: int = 0
     coriolis: int = 0
     farfield: Sequence[float] = field(default_factory=lambda: [0.0] * 9)
+    # viscous, resistive and thermal fluxes (FP64 path; off unless viscous=1)
+    mu: float = 0.0
+    eta: float = 0.0
+    kappa: float = 0.0
+    kappa_r: float = 0.0
+    R_gas: float = 1.0
+    viscous: int = 0
 
     def c(self) -> PhysC:
         p = PhysC()
@@ -95,6 +104,8 @@ class Phys:
         p.powell, p.gravity, p.coriolis = int(self.powell), int(self.gravity), int(self.coriolis)
         for i in range(9):
             p.farfield[i] = float(self.farfield[i])
+        p.mu, p.eta, p.kappa, p.kappa_r, p.R_gas = self.mu, self.eta, self.kappa, self.kappa_r, self.R_gas
+        p.viscous = int(self.viscous)
         return p
 
 

@@ -1,0 +1,118 @@
+"""Parity of the viscous, resistive and thermal fluxes (FP64 path, BR1 gradients) of the CUDA path
+with the FP64 oracle; tolerances as in test_gpu_parity (|g - o| <= 1e-12 (|o| + s_v) per residual
+entry, s_v the oracle's un-cancelled magnitude, which includes the viscous terms)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import sdref  # noqa: E402
+from paper_2502_17805_gb300 import inputs, sdmhd  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+VISC = dict(viscous=1, mu=0.03, eta=0.02, kappa=0.01, kappa_r=0.015, R_gas=0.9)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _device():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2502_17805_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+
+
+def _pair(N, v, h, **kw):
+    return sdmhd.Mesh(N, v, h, **kw), sdref.Mesh(N, v, h, **kw)
+
+
+def _phys(**kw):
+    return sdmhd.Phys(**kw), sdref.Phys(**kw)
+
+
+def _c19(g, o, s):
+    return float((np.abs(g - o) / (np.abs(o) + s[:, None, None])).max())
+
+
+@pytest.mark.parametrize("N", [2, 3, 4, 5, 6, 7, 8])
+def test_viscous_residual_jittered_periodic_box(N):
+    v, h, per = inputs.box_mesh(3, jitter=0.15, seed=N)
+    gm, om = _pair(N, v, h, periodic=per, geom=0)
+    gph, oph = _phys(powell=1, c_h=0.7, glm_alpha=0.3, **VISC)
+    q0 = inputs.random_state(gm.n_e, N, seed=20 + N)
+    R = gm.to_host(gm.residual(gph, gm.to_device(q0)))
+    Ro, s = om.residual(oph, q0)
+    # the viscous part is a sizeable share of this residual
+    R0, _ = om.residual(sdref.Phys(powell=1, c_h=0.7, glm_alpha=0.3), q0)
+    assert np.abs(Ro - R0).max() > 1e-2 * np.abs(R0).max()
+    assert _c19(R, Ro, s) < TOL64
+
+
+@pytest.mark.parametrize("N", [4, 6])
+def test_viscous_residual_shell_with_walls_and_sources(N):
+    """Curved shell: BR1 averages against the wall ghost states, a wall's own viscous flux, every
+    source on."""
+    v, h = inputs.shell_mesh(2, 2)
+    h = inputs.reorient(h, seed=4)
+    gm, om = _pair(N, v, h, geom=1, r_in=0.7, r_out=0.98, bc_in=sdref.BC_WALL_CONDUCTING,
+                   bc_out=sdref.BC_WALL_RADIAL)
+    gph, oph = _phys(powell=1, c_h=0.8, glm_alpha=0.5, gravity=1, GM=1.0, coriolis=1, omega=1.0, **VISC)
+    q0 = inputs.random_state(gm.n_e, N, seed=31)
+    R = gm.to_host(gm.residual(gph, gm.to_device(q0)))
+    Ro, s = om.residual(oph, q0)
+    assert _c19(R, Ro, s) < TOL64
+
+
+def test_viscous_steps_follow_the_oracle():
+    """Three SSP-RK3 steps through sd_step (device dt, c_h) against the oracle given them."""
+    N = 4
+    v, h, per = inputs.box_mesh(3, jitter=0.1, seed=6)
+    gm, om = _pair(N, v, h, periodic=per, geom=0)
+    gph, oph = _phys(powell=1, c_h=0.0, glm_alpha=0.3, **VISC)
+    q0 = inputs.random_state(gm.n_e, N, seed=8)
+    q, work = gm.to_device(q0), gm.empty_state()
+    dts = torch.zeros(2, dtype=torch.float64, device="cuda")
+    qo = q0
+    for _ in range(3):
+        gm.step(gph, 0.1, q, work, dt_out=dts)
+        dt, ch = dts.cpu().numpy()
+        oph.c_h = float(ch)
+        qo = om.rk_step(oph, float(dt), qo)
+    change = np.abs(qo - q0).max(axis=(1, 2))
+    err = np.abs(gm.to_host(q) - qo).max(axis=(1, 2))
+    scale = np.abs(q0).max(axis=(1, 2))
+    assert np.all(err <= 1e-12 * scale + 1e-9 * change), (err, change)
+
+
+def test_viscous_advance_equals_repeated_steps():
+    N = 5
+    v, h, per = inputs.box_mesh(3, jitter=0.1, seed=7)
+    gm = sdmhd.Mesh(N, v, h, periodic=per, geom=0)
+    gph = sdmhd.Phys(powell=1, c_h=0.0, glm_alpha=0.3, **VISC)
+    q0 = inputs.random_state(gm.n_e, N, seed=9)
+    qa, wa = gm.to_device(q0), gm.empty_state()
+    for _ in range(3):
+        gm.step(gph, 0.1, qa, wa)
+    qb, wb = gm.to_device(q0), gm.empty_state()
+    gm.advance(gph, 0.1, 3, qb, wb)
+    torch.cuda.synchronize()
+    assert torch.equal(qa, qb)
+
+
+def test_viscous_fluxes_are_rejected_where_unsupported():
+    N = 4
+    v, h = inputs.shell_mesh(2, 1)
+    gm = sdmhd.Mesh(N, v, h, geom=1, r_in=0.7, r_out=0.98)
+    gph = sdmhd.Phys(gravity=1, GM=1.0, **VISC)
+    qb = gm.empty_state()
+    q = gm.state_init(gph, sdmhd.INIT_SHELL_POLYTROPE, [1.5, 0.7, 0.98, 1.0, 1.0, 1e-4, 0.0], seed=0, background=qb)
+    bg = gm.background(gph, qb)
+    with pytest.raises(sdmhd.SDError, match="FP64"):
+        gm.residual(gph, q, prec=sdmhd.SD_FP32_MIXED, bg=bg)
+    with pytest.raises(sdmhd.SDError, match="sd_residual"):
+        gm.residual_noalloc(gph, q, gm.empty_state())
+    bad = sdmhd.Phys(gravity=1, GM=1.0, **dict(VISC, mu=-1.0))
+    with pytest.raises(sdmhd.SDError, match="non-negative"):
+        gm.residual(bad, q)
