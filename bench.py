@@ -47,6 +47,8 @@ WORKLOADS = {
 }
 CFL = 0.2
 GLM_ALPHA = 1.0
+# coefficients of the viscous FP64 leg: small enough that the inviscid CFL 0.2 step is also stable for them
+VISCOUS = dict(viscous=1, mu=1e-4, eta=1e-4, kappa=1e-4, kappa_r=1e-4, R_gas=1.0)
 
 
 def parse():
@@ -61,6 +63,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--no-viscous", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=64)
     ap.add_argument("--serve-budget-gb", type=float, default=24.0)
     return ap.parse_args()
@@ -401,6 +404,20 @@ def run_ours(args):
     q64 = q0.clone()
     k64 = max(1, min(args.steps, args.fp64_steps))
     ms64, prof64, _ = time_steps(mesh, phys, q64, work, sdmhd.SD_FP64, None, k64, min(args.warmup, 3), None, barrier)
+    # FP64 path with the viscous, resistive and thermal fluxes (BR1 gradient pass before every stage)
+    visc = None
+    if not args.no_viscous:
+        phys_v = sdmhd.Phys(**{k: getattr(phys, k) for k in ("gamma", "GM", "omega", "glm_alpha", "c_h", "powell",
+                                                            "gravity", "coriolis")}, **VISCOUS)
+        qv = q0.clone()
+        msv, profv, _ = time_steps(mesh, phys_v, qv, work, sdmhd.SD_FP64, None, k64, min(args.warmup, 3), None,
+                                   barrier)
+        visc = {"value": n_pts * k64 * world / (msv / 1e3), "unit": UNIT, "steps": k64, "ms_per_step": msv / k64,
+                "dtype": "f64", "coefficients": {k: v for k, v in VISCOUS.items() if k != "viscous"},
+                "kernel_ms_per_step": {"stage": profv["stage_ms"] / k64,
+                                       "gradients_and_control": profv["other_ms"] / k64,
+                                       "trace_lambda": profv["trace_ms"] / k64}}
+        del qv
 
     if world > 1:
         import torch.distributed as dist
@@ -434,6 +451,7 @@ def run_ours(args):
                      "step_frac": step_achieved / peak},
         "fp64": {"value": value64, "unit": UNIT, "steps": k64, "ms_per_step": ms64 / k64, "dtype": "f64",
                  "stage_avg_ms": stage64_ms},
+        "viscous_fp64": visc,
         "gpu_launches": int(prof["stage_launches"] + prof["trace_launches"] + prof["other_launches"]),
         "kernel_ms_per_step": {"stage": prof["stage_ms"] / args.steps, "trace_lambda": prof["trace_ms"] / args.steps,
                                "control": prof["other_ms"] / args.steps},
