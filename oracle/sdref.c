@@ -53,6 +53,10 @@
  *  V5 at wall and far-field faces the viscous flux is this side's own (the paper's stress-free,
  *     heat-flux and magnetic boundary conditions are not part of the inviscid wall ghost).
  *  V6 the coefficients mu, eta, kappa, kappa_r and R are constants.
+ *  D1 spherical diagnostics: the "longitudinal average" of a quantity is its volume-weighted mean
+ *     over the solution points in a bin of radius and colatitude (every longitude); the meridional
+ *     speed is formed from the averaged V_r and V_theta; the magnetic energies use B^2 / 2 (R16's
+ *     units, mu_0 = 1) in place of the printed B^2 / 8 pi.
  */
 #include "sdref.h"
 
@@ -1188,6 +1192,58 @@ int sdref_diagnostics(sdref_mesh* m, const sdref_phys* ph, const double* q, sdre
   out->min_rho = minr;
   out->min_p = minp;
   out->volume = vol;
+  return 0;
+}
+
+/* Longitude averages on the spherical shell (Sec. Results: differential rotation, meridional
+ * circulation, poloidal and toroidal magnetic energy; reading D1): bins of equal width in radius
+ * over [r_in, r_out] and in colatitude over [0, pi]; each solution point adds its quadrature weight
+ * w |J| times (1, V_r, V_theta, V_phi, (B_r^2 + B_theta^2)/2, B_phi^2/2, rho, rho |U|^2 / 2) to the
+ * bin holding it.  out: [n_r][n_theta][8], elements in order. */
+int sdref_spherical_averages(sdref_mesh* m, const double* q, int n_r, int n_theta, double* out) {
+  if (!m || !q || !out || n_r < 1 || n_theta < 1) { set_err("bad argument"); return 1; }
+  if (!(m->r_out > m->r_in)) { set_err("the mesh has no radial extent"); return 1; }
+  if (ensure_geometry(m, NULL)) return 2;
+  int N = m->N;
+  for (int64_t i = 0; i < (int64_t)n_r * n_theta * 8; ++i) out[i] = 0.0;
+  for (int64_t e = 0; e < m->n_e; ++e)
+    for (int k = 0; k < N; ++k)
+      for (int j = 0; j < N; ++j)
+        for (int i = 0; i < N; ++i) {
+          int n = i + N * (j + N * k);
+          const double* x = geo_X(m, e, n);
+          double wq = m->w[i] * m->w[j] * m->w[k] * geo_J(m, e, n);
+          double Q[9];
+          for (int v = 0; v < 9; ++v) Q[v] = qat(m, q, v, e, n);
+          double r = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+          double s = sqrt(x[0] * x[0] + x[1] * x[1]); /* distance from the rotation axis */
+          double th = atan2(s, x[2]);                 /* colatitude in [0, pi] */
+          /* unit vectors; on the axis phi is taken as 0 */
+          double cp = s > 0.0 ? x[0] / s : 1.0, sp = s > 0.0 ? x[1] / s : 0.0;
+          double ct = cos(th), st = sin(th);
+          double er[3] = {st * cp, st * sp, ct}, et[3] = {ct * cp, ct * sp, -st}, ep[3] = {-sp, cp, 0.0};
+          double U[3] = {Q[1] / Q[0], Q[2] / Q[0], Q[3] / Q[0]};
+          const double* B = Q + 5;
+          double Vr = U[0] * er[0] + U[1] * er[1] + U[2] * er[2];
+          double Vt = U[0] * et[0] + U[1] * et[1] + U[2] * et[2];
+          double Vp = U[0] * ep[0] + U[1] * ep[1] + U[2] * ep[2];
+          double Br = B[0] * er[0] + B[1] * er[1] + B[2] * er[2];
+          double Bt = B[0] * et[0] + B[1] * et[1] + B[2] * et[2];
+          double Bp = B[0] * ep[0] + B[1] * ep[1] + B[2] * ep[2];
+          int ir = (int)floor((r - m->r_in) / (m->r_out - m->r_in) * n_r);
+          int it = (int)floor(th / M_PI * n_theta);
+          ir = ir < 0 ? 0 : (ir >= n_r ? n_r - 1 : ir);
+          it = it < 0 ? 0 : (it >= n_theta ? n_theta - 1 : it);
+          double* o = out + ((int64_t)ir * n_theta + it) * 8;
+          o[0] += wq;
+          o[1] += wq * Vr;
+          o[2] += wq * Vt;
+          o[3] += wq * Vp;
+          o[4] += wq * 0.5 * (Br * Br + Bt * Bt);
+          o[5] += wq * 0.5 * Bp * Bp;
+          o[6] += wq * Q[0];
+          o[7] += wq * 0.5 * Q[0] * (U[0] * U[0] + U[1] * U[1] + U[2] * U[2]);
+        }
   return 0;
 }
 

@@ -85,6 +85,9 @@ int sdref_residual(sdref_mesh* m, const sdref_phys* ph, const double* q, double*
 /* gradients of the primitive variables (u, v, w, T, S, Bx, By, Bz) at the solution points with the
  * BR1 common solution at element faces: grad[e][3 c + j][N^3] = d w_c / d x_j (viscous fluxes) */
 int sdref_gradients(sdref_mesh* m, const sdref_phys* ph, const double* q, double* grad);
+/* volume sums over bins of radius x colatitude on the shell: out[n_r][n_theta][8] =
+ * (volume, V_r, V_theta, V_phi, (B_r^2 + B_theta^2)/2, B_phi^2/2, rho, rho |U|^2/2), each times w |J| */
+int sdref_spherical_averages(sdref_mesh* m, const double* q, int n_r, int n_theta, double* out);
 int sdref_residual_elements(sdref_mesh* m, const sdref_phys* ph, const double* q, int64_t n_list,
                             const int64_t* elems, double* out, double* scale);
 /* One Shu-Osher SSP-RK3 stage: q_out = a_s q_n + b_s (q_in + dt R(q_in)). */

@@ -82,6 +82,7 @@ def lib():
         L.sdref_residual.argtypes = [C.c_void_p, C.POINTER(_Phys), dp, dp, dp, dp]
         L.sdref_residual_elements.argtypes = [C.c_void_p, C.POINTER(_Phys), dp, C.c_int64, ip, dp, dp]
         L.sdref_gradients.argtypes = [C.c_void_p, C.POINTER(_Phys), dp, dp]
+        L.sdref_spherical_averages.argtypes = [C.c_void_p, dp, C.c_int, C.c_int, dp]
         L.sdref_rk_stage.argtypes = [C.c_void_p, C.POINTER(_Phys), C.c_int, C.c_double, dp, dp, dp]
         L.sdref_diagnostics.argtypes = [C.c_void_p, C.POINTER(_Phys), dp, C.POINTER(_Diag)]
         L.sdref_state_init.argtypes = [C.c_void_p, C.POINTER(_Phys), C.c_int, dp, C.c_uint64, dp, dp]
@@ -235,6 +236,13 @@ class Mesh:
         _check(lib().sdref_residual_elements(self._h_ptr, C.byref(ph), _dp(q), el.size,
                                              el.ctypes.data_as(C.POINTER(C.c_int64)), _dp(out), _dp(scale)))
         return out, scale
+
+    def spherical_sums(self, q, n_r: int, n_theta: int):
+        """[n_r, n_theta, 8] volume sums (volume, V_r, V_theta, V_phi, E_pol, E_tor, rho, KE) per bin"""
+        q = self._q(q)
+        out = np.zeros((n_r, n_theta, 8))
+        _check(lib().sdref_spherical_averages(self._h_ptr, _dp(q), int(n_r), int(n_theta), _dp(out)))
+        return out
 
     def gradients(self, phys: Phys, q):
         """gradients of (u, v, w, T, S, Bx, By, Bz) at the solution points: [n_e, 8, 3, N^3]"""
