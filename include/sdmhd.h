@@ -239,6 +239,21 @@ sd_status sd_step(const sd_mesh* mesh, const sd_phys* phys, sd_precision prec, d
 sd_status sd_advance(const sd_mesh* mesh, const sd_phys* phys, sd_precision prec, double cfl, int32_t n_steps,
                      double* q, double* work, const sd_background* bg, double* dt_out, void* stream);
 
+/* Longitude averages on a spherical shell (Sec. Results: differential rotation
+ * <V_phi>, meridional circulation from <V_r> and <V_theta>, poloidal and
+ * toroidal magnetic energy): the shell r in [r_min, r_max] about the origin is
+ * divided into n_r bins of equal radial width and n_theta bins of equal
+ * colatitude width over [0, pi]; every solution point adds its quadrature weight
+ * w |J| times (1, V_r, V_theta, V_phi, (B_r^2 + B_theta^2)/2, B_phi^2/2, rho,
+ * rho |U|^2/2) to the bin that holds it (points outside [r_min, r_max] go to the
+ * nearest radial bin; on the rotation axis phi is taken as 0).  Dividing by the
+ * first entry gives the bin means.  out: device double[n_r][n_theta][8],
+ * overwritten.  The summation order is not fixed (atomic additions): results
+ * agree with a fixed-order sum to round-off.  The paper's B^2 / 8 pi is B^2 / 2
+ * in the library's units.  Asynchronous. */
+sd_status sd_spherical_sums(const sd_mesh* mesh, const double* q, double r_min, double r_max, int32_t n_r,
+                            int32_t n_theta, double* out, void* stream);
+
 /* ---- Packed stepping of many independent solves (serving).
  * One request is one shell (or box) solve on its own mesh with its own physics,
  * background and states.  sd_step_packed advances every request by one

@@ -921,6 +921,27 @@ sd_status sd_advance(const sd_mesh* m, const sd_phys* ph, sd_precision prec, dou
   return advance_impl(const_cast<sd_mesh*>(m), ph, prec, cfl, n_steps, q, work, bg, dt_out, (cudaStream_t)stream);
 }
 
+sd_status sd_spherical_sums(const sd_mesh* m, const double* q, double r_min, double r_max, int32_t n_r,
+                            int32_t n_theta, double* out, void* stream) {
+  if (!m) return fail(SD_ERR_INVALID_ARGUMENT, "mesh is NULL");
+  sd_status st = check_state_ptr(q, "q");
+  if (st != SD_OK) return st;
+  if (!out) return fail(SD_ERR_INVALID_ARGUMENT, "out is NULL");
+  if (!(r_max > r_min) || !isfinite(r_min) || !isfinite(r_max))
+    return fail(SD_ERR_INVALID_ARGUMENT, "need finite r_min < r_max");
+  if (n_r < 1 || n_theta < 1 || (int64_t)n_r * n_theta > (1 << 24))
+    return fail(SD_ERR_INVALID_ARGUMENT, "n_r and n_theta must be >= 1 with n_r * n_theta <= 2^24");
+  DeviceGuard g(m->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t err;
+  {
+    ProfScope ps(m, PROF_OTHER, s);
+    err = sd::launch_spherical(m, q, r_min, r_max, n_r, n_theta, out, s);
+  }
+  if (err != cudaSuccess) return cuda_fail(err, "spherical sums kernel");
+  return SD_OK;
+}
+
 sd_status sd_diagnostics(const sd_mesh* m, const sd_phys* ph, const double* q, sd_diag* out, void* stream) {
   sd_status st = check_common(m, ph, SD_FP64, nullptr);
   if (st != SD_OK) return st;

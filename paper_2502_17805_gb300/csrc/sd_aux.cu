@@ -1,5 +1,6 @@
 // sd_aux.cu -- geometry, initial state, diagnostics, background and step-control
 // kernels of the SD MHD+GLM library.
+#include <limits.h>
 #include <math.h>
 
 #include "sd_internal.h"
@@ -429,6 +430,108 @@ cudaError_t launch_diag(const sd_mesh* m, const sd_phys* ph, const double* q, cu
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
   diag_final_kernel<<<1, kDiagThreads, 0, s>>>(m->n_e, m->diag_part, m->diag_out);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Longitude averages on the shell (Sec. Results): volume sums over bins of
+// radius x colatitude of (1, V_r, V_theta, V_phi, (B_r^2 + B_theta^2)/2,
+// B_phi^2/2, rho, rho |U|^2 / 2), each weighted by w |J|.  One CTA per element:
+// its points touch a small window of bins, which the CTA sums in shared memory
+// before adding the window to the global table (one atomic per touched entry);
+// a window too large for shared memory adds point by point.  The summation
+// order is not fixed: results agree with a fixed-order sum to round-off.
+// ---------------------------------------------------------------------------
+
+constexpr int kSphThreads = 256;
+constexpr int kSphVals = 8;
+constexpr int kSphWindow = 64;  // bins per element window in shared memory
+
+__device__ __forceinline__ void sph_point(const double* Q, const double* x, double wq, double r_min, double r_max,
+                                          int n_r, int n_t, int& bin, double* val) {
+  const double r = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+  const double s = sqrt(x[0] * x[0] + x[1] * x[1]);
+  const double th = atan2(s, x[2]);
+  const double cp = s > 0.0 ? x[0] / s : 1.0, sp = s > 0.0 ? x[1] / s : 0.0;
+  const double ct = cos(th), st = sin(th);
+  const double ir = 1.0 / Q[0];
+  const double U[3] = {Q[1] * ir, Q[2] * ir, Q[3] * ir};
+  const double Vr = (U[0] * cp + U[1] * sp) * st + U[2] * ct;
+  const double Vt = (U[0] * cp + U[1] * sp) * ct - U[2] * st;
+  const double Vp = -U[0] * sp + U[1] * cp;
+  const double Br = (Q[5] * cp + Q[6] * sp) * st + Q[7] * ct;
+  const double Bt = (Q[5] * cp + Q[6] * sp) * ct - Q[7] * st;
+  const double Bp = -Q[5] * sp + Q[6] * cp;
+  int kr = (int)floor((r - r_min) / (r_max - r_min) * n_r);
+  int kt = (int)floor(th / M_PI * n_t);
+  kr = kr < 0 ? 0 : (kr >= n_r ? n_r - 1 : kr);
+  kt = kt < 0 ? 0 : (kt >= n_t ? n_t - 1 : kt);
+  bin = kr * n_t + kt;
+  val[0] = wq;
+  val[1] = wq * Vr;
+  val[2] = wq * Vt;
+  val[3] = wq * Vp;
+  val[4] = wq * 0.5 * (Br * Br + Bt * Bt);
+  val[5] = wq * 0.5 * Bp * Bp;
+  val[6] = wq * Q[0];
+  val[7] = wq * 0.5 * Q[0] * (U[0] * U[0] + U[1] * U[1] + U[2] * U[2]);
+}
+
+__global__ void __launch_bounds__(kSphThreads) spherical_kernel(int N, int64_t stride, int64_t plane, const Ops<double> ops,
+                                                                const double* __restrict__ q,
+                                                                const double* __restrict__ X,
+                                                                const double* __restrict__ invJ, double r_min,
+                                                                double r_max, int n_r, int n_t, double* out) {
+  __shared__ double win[kSphWindow * kSphVals];
+  __shared__ int lo_hi[2];
+  const int64_t e = blockIdx.x;
+  const int N3 = N * N * N;
+  if (threadIdx.x == 0) {
+    lo_hi[0] = INT_MAX;
+    lo_hi[1] = -1;
+  }
+  for (int i = threadIdx.x; i < kSphWindow * kSphVals; i += kSphThreads) win[i] = 0.0;
+  __syncthreads();
+  // pass 1: the range of bins this element touches
+  for (int n = threadIdx.x; n < N3; n += kSphThreads) {
+    const int i = n % N, j = (n / N) % N, k = n / (N * N);
+    double Q[9], x[3], val[kSphVals];
+    for (int c = 0; c < 9; ++c) Q[c] = q[c * plane + e * stride + n];
+    for (int c = 0; c < 3; ++c) x[c] = X[(e * 3 + c) * N3 + n];
+    int bin;
+    sph_point(Q, x, ops.w[i] * ops.w[j] * ops.w[k] / invJ[e * N3 + n], r_min, r_max, n_r, n_t, bin, val);
+    atomicMin(&lo_hi[0], bin);
+    atomicMax(&lo_hi[1], bin);
+  }
+  __syncthreads();
+  const int lo = lo_hi[0], span = lo_hi[1] - lo_hi[0] + 1;
+  const bool local = span <= kSphWindow;
+  // pass 2: sums (in the window when it fits)
+  for (int n = threadIdx.x; n < N3; n += kSphThreads) {
+    const int i = n % N, j = (n / N) % N, k = n / (N * N);
+    double Q[9], x[3], val[kSphVals];
+    for (int c = 0; c < 9; ++c) Q[c] = q[c * plane + e * stride + n];
+    for (int c = 0; c < 3; ++c) x[c] = X[(e * 3 + c) * N3 + n];
+    int bin;
+    sph_point(Q, x, ops.w[i] * ops.w[j] * ops.w[k] / invJ[e * N3 + n], r_min, r_max, n_r, n_t, bin, val);
+    if (local) {
+      for (int c = 0; c < kSphVals; ++c) atomicAdd(&win[(bin - lo) * kSphVals + c], val[c]);
+    } else {
+      for (int c = 0; c < kSphVals; ++c) atomicAdd(&out[(int64_t)bin * kSphVals + c], val[c]);
+    }
+  }
+  __syncthreads();
+  if (local)
+    for (int t = threadIdx.x; t < span * kSphVals; t += kSphThreads)
+      if (win[t] != 0.0) atomicAdd(&out[(int64_t)lo * kSphVals + t], win[t]);
+}
+
+cudaError_t launch_spherical(const sd_mesh* m, const double* q, double r_min, double r_max, int n_r, int n_t,
+                             double* out, cudaStream_t s) {
+  cudaError_t err = cudaMemsetAsync(out, 0, (size_t)n_r * n_t * kSphVals * sizeof(double), s);
+  if (err != cudaSuccess || m->n_e == 0) return err;
+  spherical_kernel<<<(unsigned)m->n_e, kSphThreads, 0, s>>>(m->N, m->stride, m->n_e * m->stride, m->ops64, q, m->X64,
+                                                            m->invJ64, r_min, r_max, n_r, n_t, out);
   return cudaGetLastError();
 }
 

@@ -146,6 +146,9 @@ constexpr int NGRAD = 24;
 // kernels launched from the API (defined in the .cu files)
 cudaError_t launch_stage(const sd_mesh* m, int prec, const StageParams& P, cudaStream_t s);
 cudaError_t launch_traces(const sd_mesh* m, int prec, const StageParams& P, cudaStream_t s);
+// longitude averages on the shell: volume sums per bin of radius x colatitude into out[n_r][n_t][8]
+cudaError_t launch_spherical(const sd_mesh* m, const double* q, double r_min, double r_max, int n_r, int n_t,
+                             double* out, cudaStream_t s);
 // BR1 gradients of the primitive variables and their face traces (viscous FP64 path)
 cudaError_t launch_grad(const sd_mesh* m, const StageParams& P, cudaStream_t s);
 cudaError_t launch_geometry(sd_mesh* m, const double* d_corners, int* d_flag, cudaStream_t s);

@@ -28,7 +28,7 @@ STATUS = {0: "SD_OK", 1: "SD_ERR_INVALID_ARGUMENT", 2: "SD_ERR_UNSUPPORTED", 3: 
 # every symbol include/sdmhd.h declares
 EXPORTS = ["sd_last_error", "sd_mesh_create", "sd_mesh_destroy", "sd_mesh_query", "sd_state_init",
            "sd_background_create", "sd_background_destroy", "sd_residual", "sd_rk_stage", "sd_step", "sd_advance",
-           "sd_diagnostics", "sd_profile_enable", "sd_profile_read", "sd_residual_noalloc",
+           "sd_diagnostics", "sd_spherical_sums", "sd_profile_enable", "sd_profile_read", "sd_residual_noalloc",
            "sd_packer_create", "sd_packer_destroy", "sd_step_packed"]
 
 
@@ -132,6 +132,7 @@ def lib():
         L.sd_rk_stage.argtypes = [vp, C.POINTER(PhysC), C.c_int, C.c_int32, C.c_double, vp, vp, vp, vp, vp]
         L.sd_step.argtypes = [vp, C.POINTER(PhysC), C.c_int, C.c_double, vp, vp, vp, vp, vp]
         L.sd_advance.argtypes = [vp, C.POINTER(PhysC), C.c_int, C.c_double, C.c_int32, vp, vp, vp, vp, vp]
+        L.sd_spherical_sums.argtypes = [vp, vp, C.c_double, C.c_double, C.c_int32, C.c_int32, vp, vp]
         L.sd_diagnostics.argtypes = [vp, C.POINTER(PhysC), vp, C.POINTER(DiagC), vp]
         L.sd_profile_enable.argtypes = [vp, C.c_int32]
         L.sd_profile_read.argtypes = [vp, C.POINTER(ProfileC)]
@@ -279,6 +280,15 @@ class Mesh:
         _check(lib().sd_advance(self._h, C.byref(ph), int(prec), float(cfl), int(n_steps), _ptr(q), _ptr(work),
                                 bg._h if bg else None, _ptr(dt_out), _stream(stream)))
         return q
+
+    def spherical_sums(self, q, r_min: float, r_max: float, n_r: int, n_theta: int, out=None, stream=None):
+        """device float64 [n_r, n_theta, 8]: w|J|-weighted sums of (1, V_r, V_theta, V_phi, E_pol, E_tor, rho,
+        KE) per bin of radius x colatitude (divide by [..., 0] for the means)"""
+        import torch
+        out = torch.empty((n_r, n_theta, 8), dtype=torch.float64, device="cuda") if out is None else out
+        _check(lib().sd_spherical_sums(self._h, _ptr(q), float(r_min), float(r_max), int(n_r), int(n_theta),
+                                       _ptr(out), _stream(stream)))
+        return out
 
     def profile(self, enable: bool = True):
         """Start (or stop) CUDA-event timing of every kernel the library launches for this mesh."""
