@@ -53,6 +53,12 @@
  *  V5 at wall and far-field faces the viscous flux is this side's own (the paper's stress-free,
  *     heat-flux and magnetic boundary conditions are not part of the inviscid wall ghost).
  *  V6 the coefficients mu, eta, kappa, kappa_r and R are constants.
+ *  F1 flux-balanced initial profile (Sec. Initial Conditions): the printed density equation has
+ *     exp(+gamma S / C_p); hydrostatic balance dp/dr = -rho g with S = C_p ln(p^(1/gamma) / rho)
+ *     requires exp(-gamma S / C_p), which is used (with it the isentropic case is the polytrope).
+ *  F2 the conducted flux is L / (4 pi r^2) (the same luminosity through every radial layer, as the
+ *     text states; the printed r_b fixes only its value at the bottom).
+ *  F3 rho and T in the entropy gradient are the polytrope's (the profile the text starts from).
  *  D1 spherical diagnostics: the "longitudinal average" of a quantity is its volume-weighted mean
  *     over the solution points in a bin of radius and colatitude (every longitude); the meridional
  *     speed is formed from the averaged V_r and V_theta; the magnetic energies use B^2 / 2 (R16's
@@ -1277,6 +1283,82 @@ int sdref_polytrope(double r, double N_rho, double r_b, double r_t, double rho_b
   return 0;
 }
 
+/* Almost flux-balanced initial profile (Sec. Initial Conditions; readings F1, F2).  From the
+ * polytrope rho_p, T_p of the same N_rho the entropy gradient that carries the luminosity L by
+ * conduction, dS/dr = (L / (4 pi r^2) + kappa_r rho_p C_p dT_p/dr) / (kappa rho_p T_p), is integrated
+ * from S_b = S(r_b) of the polytrope, and the density from rho(r_b) = rho_b with the hydrostatic
+ * drho/dr = -(rho / C_p dS/dr + (g / gamma) rho^(2 - gamma) exp(-gamma S / C_p)), g = GM / r^2;
+ * then p = (rho exp(S / C_p))^gamma.  P = (N_rho, r_b, r_t, rho_b, R, noise, dipole, L, kappa, kappa_r).
+ * Classical RK4 on nfb uniform steps over [r_b, r_t]; between the nodes cubic Hermite interpolation
+ * of rho and S with the derivatives the ODE gives at the nodes. */
+typedef struct {
+  int n;
+  double rb, rt, h, Cp, gam, GM, L, kappa, kappa_r, Nr, rhob, R;
+  double *rho, *S, *drho, *dS;
+} fb_table;
+
+static double fb_dS(const fb_table* t, double r) {
+  double rp, Tp;
+  sdref_polytrope(r, t->Nr, t->rb, t->rt, t->rhob, t->R, t->gam, t->GM, &rp, NULL, &Tp);
+  double dTp = -t->GM / (t->Cp * r * r); /* T_p = T_b (1 - (Phi - Phi_b) / (C_p T_b)), Phi = -GM / r */
+  return (t->L / (4.0 * M_PI * r * r) + t->kappa_r * rp * t->Cp * dTp) / (t->kappa * rp * Tp);
+}
+
+static double fb_drho(const fb_table* t, double r, double rho, double S, double dS) {
+  double g = t->GM / (r * r);
+  return -(rho / t->Cp * dS + g / t->gam * pow(rho, 2.0 - t->gam) * exp(-t->gam * S / t->Cp));
+}
+
+static void fb_build(fb_table* t, const double* P, double gam, double GM, int n) {
+  t->Nr = P[0]; t->rb = P[1]; t->rt = P[2]; t->rhob = P[3]; t->R = P[4];
+  t->L = P[7]; t->kappa = P[8]; t->kappa_r = P[9];
+  t->gam = gam; t->GM = GM; t->Cp = gam * t->R / (gam - 1.0);
+  t->n = n; t->h = (t->rt - t->rb) / n;
+  t->rho = (double*)malloc(sizeof(double) * 4 * (n + 1));
+  t->S = t->rho + (n + 1); t->drho = t->S + (n + 1); t->dS = t->drho + (n + 1);
+  double pb, Tb;
+  sdref_polytrope(t->rb, t->Nr, t->rb, t->rt, t->rhob, t->R, gam, GM, NULL, &pb, &Tb);
+  double rho = t->rhob, S = t->Cp * log(pow(pb, 1.0 / gam) / t->rhob);
+  for (int k = 0; k <= n; ++k) {
+    double r = t->rb + k * t->h;
+    t->rho[k] = rho; t->S[k] = S;
+    t->dS[k] = fb_dS(t, r);
+    t->drho[k] = fb_drho(t, r, rho, S, t->dS[k]);
+    if (k == n) break;
+    double h = t->h;
+    double s1 = t->dS[k], q1 = t->drho[k];
+    double s2 = fb_dS(t, r + 0.5 * h), q2 = fb_drho(t, r + 0.5 * h, rho + 0.5 * h * q1, S + 0.5 * h * s1, s2);
+    double s3 = s2, q3 = fb_drho(t, r + 0.5 * h, rho + 0.5 * h * q2, S + 0.5 * h * s2, s3);
+    double s4 = fb_dS(t, r + h), q4 = fb_drho(t, r + h, rho + h * q3, S + h * s3, s4);
+    rho += h / 6.0 * (q1 + 2.0 * q2 + 2.0 * q3 + q4);
+    S += h / 6.0 * (s1 + 2.0 * s2 + 2.0 * s3 + s4);
+  }
+}
+
+static void fb_eval(const fb_table* t, double r, double* rho, double* p) {
+  double u = (r - t->rb) / t->h;
+  int k = (int)floor(u);
+  k = k < 0 ? 0 : (k >= t->n ? t->n - 1 : k);
+  double s = u - k, h = t->h;
+  double h00 = (1 + 2 * s) * (1 - s) * (1 - s), h10 = s * (1 - s) * (1 - s), h01 = s * s * (3 - 2 * s),
+         h11 = s * s * (s - 1);
+  double rr = h00 * t->rho[k] + h10 * h * t->drho[k] + h01 * t->rho[k + 1] + h11 * h * t->drho[k + 1];
+  double SS = h00 * t->S[k] + h10 * h * t->dS[k] + h01 * t->S[k + 1] + h11 * h * t->dS[k + 1];
+  *rho = rr;
+  *p = pow(rr * exp(SS / t->Cp), t->gam);
+}
+
+int sdref_flux_balanced(const double* P, double gam, double GM, int n_nodes, int n_r, const double* r, double* rho,
+                        double* p) {
+  if (!P || !r || !rho || !p || n_nodes < 2) { set_err("bad argument"); return 1; }
+  if (!(P[8] > 0.0)) { set_err("kappa must be positive"); return 1; }
+  fb_table t;
+  fb_build(&t, P, gam, GM, n_nodes);
+  for (int i = 0; i < n_r; ++i) fb_eval(&t, r[i], rho + i, p + i);
+  free(t.rho);
+  return 0;
+}
+
 static void prim_to_cons(double rho, const double* u, double p, const double* B, double psi, double gam, double* Q) {
   Q[0] = rho;
   for (int d = 0; d < 3; ++d) Q[1 + d] = rho * u[d];
@@ -1294,7 +1376,13 @@ int sdref_state_init(sdref_mesh* m, const sdref_phys* ph, int kind, const double
   int64_t N3 = (int64_t)N * N * N;
   double gam = ph->gamma;
   double B0dip = 0.0;
-  if (kind == SDREF_INIT_SHELL_POLYTROPE) {
+  fb_table fbt;
+  fbt.rho = NULL;
+  if (kind == SDREF_INIT_SHELL_FLUX_BALANCED) {
+    if (!(P[8] > 0.0)) { set_err("kappa must be positive"); return 1; }
+    fb_build(&fbt, P, gam, ph->GM, 4096);
+  }
+  if (kind == SDREF_INIT_SHELL_POLYTROPE || kind == SDREF_INIT_SHELL_FLUX_BALANCED) {
     /* dipole amplitude: int 1/2 |B|^2 dV = ratio * int p0/(gamma-1) dV over the ideal shell
      * (reading R12: the kinetic energy is zero at t = 0, so the internal energy is the reference) */
     double Nr = P[0], rb = P[1], rt = P[2], rhob = P[3], Rg = P[4], ratio = P[6];
@@ -1302,8 +1390,11 @@ int sdref_state_init(sdref_mesh* m, const sdref_phys* ph, int kind, const double
     double t[64], wg[64], Ip = 0.0;
     legendre_roots(64, t, wg);
     for (int qd = 0; qd < 64; ++qd) {
-      double r = 0.5 * (rb + rt) + 0.5 * (rt - rb) * t[qd], pr;
-      sdref_polytrope(r, Nr, rb, rt, rhob, Rg, gam, ph->GM, NULL, &pr, NULL);
+      double r = 0.5 * (rb + rt) + 0.5 * (rt - rb) * t[qd], pr, rr;
+      if (kind == SDREF_INIT_SHELL_POLYTROPE)
+        sdref_polytrope(r, Nr, rb, rt, rhob, Rg, gam, ph->GM, NULL, &pr, NULL);
+      else
+        fb_eval(&fbt, r, &rr, &pr);
       Ip += 0.5 * (rt - rb) * wg[qd] * pr * r * r;
     }
     Ip *= 4.0 * M_PI / (gam - 1.0);
@@ -1339,11 +1430,14 @@ int sdref_state_init(sdref_mesh* m, const sdref_phys* ph, int kind, const double
           u[d] = -dB / sqrt(rho);
         }
         prim_to_cons(rho, u, p, B, 0.0, gam, Q);
-      } else if (kind == SDREF_INIT_SHELL_POLYTROPE) {
+      } else if (kind == SDREF_INIT_SHELL_POLYTROPE || kind == SDREF_INIT_SHELL_FLUX_BALANCED) {
         double Nr = P[0], rb = P[1], rt = P[2], rhob = P[3], Rg = P[4], amp = P[5];
         double r = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
         double rho0, p0;
-        sdref_polytrope(r, Nr, rb, rt, rhob, Rg, gam, ph->GM, &rho0, &p0, NULL);
+        if (kind == SDREF_INIT_SHELL_POLYTROPE)
+          sdref_polytrope(r, Nr, rb, rt, rhob, Rg, gam, ph->GM, &rho0, &p0, NULL);
+        else
+          fb_eval(&fbt, r, &rho0, &p0);
         /* entropy noise: density perturbed at fixed pressure, tapered to zero at both walls */
         double xi = sdref_uniform(seed, (uint64_t)(e * N3 + n));
         double rho = rho0 * (1.0 - amp * xi * sin(M_PI * (r - rb) / (rt - rb)));
@@ -1366,5 +1460,6 @@ int sdref_state_init(sdref_mesh* m, const sdref_phys* ph, int kind, const double
         if (qbg) qbg[((int64_t)v * m->n_e + e) * N3 + n] = Qb[v];
       }
     }
+  free(fbt.rho);
   return 0;
 }

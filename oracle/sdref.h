@@ -36,7 +36,7 @@ extern "C" {
 
 enum { SDREF_BC_PERIODIC = 0, SDREF_BC_WALL_CONDUCTING = 1, SDREF_BC_WALL_RADIAL = 2, SDREF_BC_FARFIELD = 3 };
 enum { SDREF_INIT_UNIFORM = 0, SDREF_INIT_ALFVEN = 1, SDREF_INIT_SHELL_POLYTROPE = 2,
-       SDREF_INIT_DIVB_PULSE = 3, SDREF_INIT_SINB = 4 };
+       SDREF_INIT_DIVB_PULSE = 3, SDREF_INIT_SINB = 4, SDREF_INIT_SHELL_FLUX_BALANCED = 5 };
 
 typedef struct {
   double gamma, GM, omega, glm_alpha, c_h;
@@ -88,6 +88,10 @@ int sdref_gradients(sdref_mesh* m, const sdref_phys* ph, const double* q, double
 /* volume sums over bins of radius x colatitude on the shell: out[n_r][n_theta][8] =
  * (volume, V_r, V_theta, V_phi, (B_r^2 + B_theta^2)/2, B_phi^2/2, rho, rho |U|^2/2), each times w |J| */
 int sdref_spherical_averages(sdref_mesh* m, const double* q, int n_r, int n_theta, double* out);
+/* almost flux-balanced profile (Sec. Initial Conditions) at radii r[n_r]: rho, p; P as for
+ * SDREF_INIT_SHELL_FLUX_BALANCED (N_rho, r_b, r_t, rho_b, R, noise, dipole, L, kappa, kappa_r) */
+int sdref_flux_balanced(const double* P, double gam, double GM, int n_nodes, int n_r, const double* r, double* rho,
+                        double* p);
 int sdref_residual_elements(sdref_mesh* m, const sdref_phys* ph, const double* q, int64_t n_list,
                             const int64_t* elems, double* out, double* scale);
 /* One Shu-Osher SSP-RK3 stage: q_out = a_s q_n + b_s (q_in + dt R(q_in)). */

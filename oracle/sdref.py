@@ -17,7 +17,7 @@ from . import build as _build
 _lib = None
 
 BC_PERIODIC, BC_WALL_CONDUCTING, BC_WALL_RADIAL, BC_FARFIELD = 0, 1, 2, 3
-INIT_UNIFORM, INIT_ALFVEN, INIT_SHELL_POLYTROPE, INIT_DIVB_PULSE, INIT_SINB = 0, 1, 2, 3, 4
+INIT_UNIFORM, INIT_ALFVEN, INIT_SHELL_POLYTROPE, INIT_DIVB_PULSE, INIT_SINB, INIT_SHELL_FLUX_BALANCED = 0, 1, 2, 3, 4, 5
 
 
 class _Phys(C.Structure):
@@ -83,6 +83,7 @@ def lib():
         L.sdref_residual_elements.argtypes = [C.c_void_p, C.POINTER(_Phys), dp, C.c_int64, ip, dp, dp]
         L.sdref_gradients.argtypes = [C.c_void_p, C.POINTER(_Phys), dp, dp]
         L.sdref_spherical_averages.argtypes = [C.c_void_p, dp, C.c_int, C.c_int, dp]
+        L.sdref_flux_balanced.argtypes = [dp, C.c_double, C.c_double, C.c_int, C.c_int, dp, dp, dp]
         L.sdref_rk_stage.argtypes = [C.c_void_p, C.POINTER(_Phys), C.c_int, C.c_double, dp, dp, dp]
         L.sdref_diagnostics.argtypes = [C.c_void_p, C.POINTER(_Phys), dp, C.POINTER(_Diag)]
         L.sdref_state_init.argtypes = [C.c_void_p, C.POINTER(_Phys), C.c_int, dp, C.c_uint64, dp, dp]
@@ -120,6 +121,16 @@ def set_threads(n: int):
 
 def get_threads() -> int:
     return int(lib().sdref_get_threads())
+
+
+def flux_balanced(params, r, gamma=5.0 / 3.0, GM=1.0, n_nodes=4096):
+    """almost flux-balanced profile rho(r), p(r) (Sec. Initial Conditions); params as for
+    INIT_SHELL_FLUX_BALANCED: N_rho, r_b, r_t, rho_b, R, noise, dipole, L, kappa, kappa_r"""
+    P = _f64(np.asarray(list(params) + [0.0] * (16 - len(params))))
+    r = _f64(np.atleast_1d(r))
+    rho, p = np.zeros_like(r), np.zeros_like(r)
+    _check(lib().sdref_flux_balanced(_dp(P), float(gamma), float(GM), int(n_nodes), r.size, _dp(r), _dp(rho), _dp(p)))
+    return rho, p
 
 
 def nodes(N: int):
