@@ -77,8 +77,21 @@ typedef enum { SD_BC_PERIODIC = 0, SD_BC_WALL_CONDUCTING = 1, SD_BC_WALL_RADIAL 
  *                          rho0 (1 - A xi sin(pi (r - r_b)/(r_t - r_b))), xi = SplitMix64 draw in
  *                          [-1, 1) keyed by (seed, e*N^3 + n); dipole B0 (3 (z.r)r - z)/r^3 scaled
  *                          so that its magnetic energy is `ratio` times the internal energy
- *  SD_INIT_DIVB_PULSE      rho, p, amplitude, cx, cy, cz, sigma: Bx Gaussian bump, U = 0 */
-typedef enum { SD_INIT_UNIFORM = 0, SD_INIT_ALFVEN = 1, SD_INIT_SHELL_POLYTROPE = 2, SD_INIT_DIVB_PULSE = 3 } sd_init_kind;
+ *  SD_INIT_DIVB_PULSE      rho, p, amplitude, cx, cy, cz, sigma: Bx Gaussian bump, U = 0
+ *  SD_INIT_SHELL_FLUX_BALANCED  as SD_INIT_SHELL_POLYTROPE, then L, kappa, kappa_r: the almost
+ *                          flux-balanced profile (Sec. Initial Conditions): the entropy gradient
+ *                          dS/dr = (L / (4 pi r^2) + kappa_r rho_p C_p dT_p/dr) / (kappa rho_p T_p)
+ *                          of the polytrope rho_p, T_p, integrated from the polytrope's bottom
+ *                          entropy, and the hydrostatic density drho/dr = -(rho S'/C_p +
+ *                          (g/gamma) rho^(2-gamma) exp(-gamma S/C_p)) from rho_b (RK4 on 4,096
+ *                          nodes, cubic Hermite interpolation); p = (rho exp(S/C_p))^gamma */
+typedef enum {
+  SD_INIT_UNIFORM = 0,
+  SD_INIT_ALFVEN = 1,
+  SD_INIT_SHELL_POLYTROPE = 2,
+  SD_INIT_DIVB_PULSE = 3,
+  SD_INIT_SHELL_FLUX_BALANCED = 4
+} sd_init_kind;
 
 typedef struct {
   int32_t order;              /* N: solution points per direction, 2..8 (Sec. SD Method) */
@@ -176,8 +189,9 @@ sd_status sd_mesh_query(const sd_mesh* mesh, sd_mesh_info* out);
 
 /* Write the initial state (Sec. Initial Conditions) at the solution points.
  * q: device state (layout above).  q_background: device state or NULL; for
- * SD_INIT_SHELL_POLYTROPE it receives the noise-free, field-free polytrope
- * (rho0, 0, p0/(gamma-1), 0, 0), otherwise zeros.  Asynchronous. */
+ * SD_INIT_SHELL_POLYTROPE and SD_INIT_SHELL_FLUX_BALANCED it receives the
+ * noise-free, field-free profile (rho0, 0, p0/(gamma-1), 0, 0), otherwise zeros.
+ * Asynchronous. */
 sd_status sd_state_init(const sd_mesh* mesh, const sd_phys* phys, const sd_init* init, double* q,
                         double* q_background, void* stream);
 

@@ -349,6 +349,85 @@ double polytrope_p(double r, double Nr, double rb, double rt, double rhob, doubl
   return rhob * Rg * Tb * pow(zeta, g / (g - 1.0));
 }
 
+// Almost flux-balanced shell profile (Sec. Initial Conditions): S and rho on
+// n + 1 uniform nodes over [r_b, r_t] with their derivatives, integrated by
+// classical RK4 from the polytrope's bottom state.  P = (N_rho, r_b, r_t, rho_b,
+// R, noise, dipole, L, kappa, kappa_r).
+constexpr int kFluxNodes = 4096;
+
+struct FluxProfile {
+  int n = 0;
+  double rb = 0.0, h = 1.0, Cp = 1.0, gamma = 1.0;
+  std::vector<double> tab;  // [4][n + 1]: rho, S, drho/dr, dS/dr
+};
+
+FluxProfile flux_profile(const double* P, double gamma, double GM, int n) {
+  const double Nr = P[0], rb = P[1], rt = P[2], rhob = P[3], Rg = P[4], L = P[7], kap = P[8], kapr = P[9];
+  FluxProfile F;
+  F.n = n;
+  F.rb = rb;
+  F.h = (rt - rb) / n;
+  F.gamma = gamma;
+  F.Cp = gamma * Rg / (gamma - 1.0);
+  const double Cp = F.Cp;
+  const double Tb = (GM / rb - GM / rt) / (Cp * (1.0 - exp(-(gamma - 1.0) * Nr)));
+  // polytrope rho_p, T_p and dT_p/dr at radius r
+  auto poly = [&](double r, double& rp, double& Tp, double& dTp) {
+    const double z = 1.0 - (GM / rb - GM / r) / (Cp * Tb);
+    rp = rhob * pow(z, 1.0 / (gamma - 1.0));
+    Tp = Tb * z;
+    dTp = -GM / (Cp * r * r);
+  };
+  auto dS = [&](double r) {
+    double rp, Tp, dTp;
+    poly(r, rp, Tp, dTp);
+    return (L / (4.0 * M_PI * r * r) + kapr * rp * Cp * dTp) / (kap * rp * Tp);
+  };
+  auto drho = [&](double r, double rho, double S, double Sp) {
+    return -(rho * Sp / Cp + GM / (r * r) / gamma * pow(rho, 2.0 - gamma) * exp(-gamma * S / Cp));
+  };
+  F.tab.assign(4 * (size_t)(n + 1), 0.0);
+  double* T_rho = F.tab.data();
+  double* T_S = T_rho + (n + 1);
+  double* T_drho = T_S + (n + 1);
+  double* T_dS = T_drho + (n + 1);
+  const double pb = rhob * Rg * Tb;
+  double rho = rhob, S = Cp * (log(pb) / gamma - log(rhob));
+  const double h = F.h;
+  for (int k = 0; k <= n; ++k) {
+    const double r = rb + k * h;
+    const double s1 = dS(r), q1 = drho(r, rho, S, s1);
+    T_rho[k] = rho;
+    T_S[k] = S;
+    T_drho[k] = q1;
+    T_dS[k] = s1;
+    if (k == n) break;
+    const double s2 = dS(r + 0.5 * h);
+    const double q2 = drho(r + 0.5 * h, rho + 0.5 * h * q1, S + 0.5 * h * s1, s2);
+    const double q3 = drho(r + 0.5 * h, rho + 0.5 * h * q2, S + 0.5 * h * s2, s2);
+    const double s4 = dS(r + h);
+    const double q4 = drho(r + h, rho + h * q3, S + h * s2, s4);
+    rho += h * (q1 + 2.0 * q2 + 2.0 * q3 + q4) / 6.0;
+    S += h * (s1 + 4.0 * s2 + s4) / 6.0;
+  }
+  return F;
+}
+
+// pressure of the profile at r (the device kernel interpolates the same way)
+double flux_profile_p(const FluxProfile& F, double r) {
+  double u = (r - F.rb) / F.h;
+  int k = (int)floor(u);
+  k = k < 0 ? 0 : (k >= F.n ? F.n - 1 : k);
+  const double t = u - k, h = F.h;
+  const double* T = F.tab.data();
+  const int n1 = F.n + 1;
+  const double a = (1 + 2 * t) * (1 - t) * (1 - t), b = t * (1 - t) * (1 - t), c = t * t * (3 - 2 * t),
+               d = t * t * (t - 1);
+  const double rho = a * T[k] + b * h * T[2 * n1 + k] + c * T[k + 1] + d * h * T[2 * n1 + k + 1];
+  const double S = a * T[n1 + k] + b * h * T[3 * n1 + k] + c * T[n1 + k + 1] + d * h * T[3 * n1 + k + 1];
+  return pow(rho * exp(S / F.Cp), F.gamma);
+}
+
 }  // namespace
 
 namespace sd {
@@ -580,15 +659,23 @@ sd_status sd_state_init(const sd_mesh* m, const sd_phys* ph, const sd_init* in, 
   sd_status st = check_state_ptr(q, "q");
   if (st != SD_OK) return st;
   if (qbg && (((uintptr_t)qbg & 15) != 0)) return fail(SD_ERR_INVALID_ARGUMENT, "q_background is not 16-byte aligned");
-  if (in->kind < SD_INIT_UNIFORM || in->kind > SD_INIT_DIVB_PULSE) return fail(SD_ERR_INVALID_ARGUMENT, "unknown init kind");
+  if (in->kind < SD_INIT_UNIFORM || in->kind > SD_INIT_SHELL_FLUX_BALANCED)
+    return fail(SD_ERR_INVALID_ARGUMENT, "unknown init kind");
   if (!(ph->gamma > 1.0)) return fail(SD_ERR_INVALID_ARGUMENT, "gamma must exceed 1");
   DeviceGuard g(m->device);
   double B0 = 0.0;
-  if (in->kind == SD_INIT_SHELL_POLYTROPE) {
+  const bool fluxbal = in->kind == SD_INIT_SHELL_FLUX_BALANCED;
+  FluxProfile F;
+  if (in->kind == SD_INIT_SHELL_POLYTROPE || fluxbal) {
     const double* P = in->params;
     const double Nr = P[0], rb = P[1], rt = P[2], rhob = P[3], Rg = P[4], ratio = P[6];
     if (!(rt > rb && rb > 0.0 && rhob > 0.0 && Rg > 0.0 && ph->GM > 0.0))
       return fail(SD_ERR_INVALID_ARGUMENT, "polytrope needs 0 < r_b < r_t, rho_b > 0, R_gas > 0, GM > 0");
+    if (fluxbal) {
+      if (!(P[8] > 0.0) || !(P[9] >= 0.0) || !isfinite(P[7]))
+        return fail(SD_ERR_INVALID_ARGUMENT, "flux-balanced profile needs kappa > 0, kappa_r >= 0, finite L");
+      F = flux_profile(P, ph->gamma, ph->GM, kFluxNodes);
+    }
     // magnetic energy of the unit dipole over the ideal shell: 8 pi (r_b^-3 - r_t^-3) / 3 (times 1/2 below);
     // internal energy: 4 pi / (gamma - 1) int p0 r^2 dr by 64-point Gauss-Legendre
     std::vector<double> x, w;
@@ -596,13 +683,25 @@ sd_status sd_state_init(const sd_mesh* m, const sd_phys* ph, const sd_init* in, 
     double Ip = 0.0;
     for (int k = 0; k < 64; ++k) {
       const double r = 0.5 * (rb + rt) + 0.5 * (rt - rb) * x[k];
-      Ip += 0.5 * (rt - rb) * w[k] * polytrope_p(r, Nr, rb, rt, rhob, Rg, ph->gamma, ph->GM) * r * r;
+      const double p0 = fluxbal ? flux_profile_p(F, r) : polytrope_p(r, Nr, rb, rt, rhob, Rg, ph->gamma, ph->GM);
+      Ip += 0.5 * (rt - rb) * w[k] * p0 * r * r;
     }
     Ip *= 4.0 * M_PI / (ph->gamma - 1.0);
     const double IB = 8.0 * M_PI * (1.0 / (rb * rb * rb) - 1.0 / (rt * rt * rt)) / 3.0;
     B0 = sqrt(2.0 * ratio * Ip / IB);
   }
-  cudaError_t err = sd::launch_state_init(m, ph, in, B0, q, qbg, (cudaStream_t)stream);
+  // the flux-balanced profile's table goes to the device for the duration of the kernel
+  double* dtab = nullptr;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (fluxbal) {
+    const size_t bytes = F.tab.size() * sizeof(double);
+    cudaError_t e1 = cudaMallocAsync((void**)&dtab, bytes, s);
+    if (e1 == cudaSuccess) e1 = cudaMemcpyAsync(dtab, F.tab.data(), bytes, cudaMemcpyHostToDevice, s);
+    if (e1 != cudaSuccess) return cuda_fail(e1, "flux-balanced profile table");
+  }
+  const sd::ProfileTable tab{dtab, F.n, F.rb, F.h, F.Cp};
+  cudaError_t err = sd::launch_state_init(m, ph, in, B0, tab, q, qbg, s);
+  if (dtab) cudaFreeAsync(dtab, s);
   if (err != cudaSuccess) return cuda_fail(err, "state init kernel");
   return SD_OK;
 }

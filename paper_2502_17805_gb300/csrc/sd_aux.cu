@@ -249,7 +249,24 @@ struct InitArgs {
   double P[16];
   unsigned long long seed;
   double gamma, GM, B0dip;
+  ProfileTable tab;
 };
+
+// rho and p of the flux-balanced profile at radius r: cubic Hermite interpolation of rho and S
+// between the table's nodes, p = (rho exp(S / C_p))^gamma
+__device__ __forceinline__ void profile_at(const ProfileTable& T, double gamma, double r, double& rho, double& p) {
+  const double u = (r - T.rb) / T.h;
+  int k = (int)floor(u);
+  k = k < 0 ? 0 : (k >= T.n ? T.n - 1 : k);
+  const double t = u - k, h = T.h;
+  const int n1 = T.n + 1;
+  const double* R = T.tab;
+  const double a = (1 + 2 * t) * (1 - t) * (1 - t), b = t * (1 - t) * (1 - t), c = t * t * (3 - 2 * t),
+               d = t * t * (t - 1);
+  rho = a * R[k] + b * h * R[2 * n1 + k] + c * R[k + 1] + d * h * R[2 * n1 + k + 1];
+  const double S = a * R[n1 + k] + b * h * R[3 * n1 + k] + c * R[n1 + k + 1] + d * h * R[3 * n1 + k + 1];
+  p = pow(rho * exp(S / T.Cp), gamma);
+}
 
 __global__ void state_init_kernel(const InitArgs A, const double* __restrict__ X64, double* q, double* qbg) {
   const int N3 = A.N * A.N * A.N;
@@ -291,17 +308,23 @@ __global__ void state_init_kernel(const InitArgs A, const double* __restrict__ X
         u[d] = -dB / sqrt(rho);
       }
       cons_from_prim(rho, u, p, B, 0.0, A.gamma, Q);
-    } else if (A.kind == SD_INIT_SHELL_POLYTROPE) {
-      // Eq. (polytrop eqns) with T_b from N_rho; R_gas = P[4], C_p = gamma R/(gamma-1)
+    } else if (A.kind == SD_INIT_SHELL_POLYTROPE || A.kind == SD_INIT_SHELL_FLUX_BALANCED) {
+      // Eq. (polytrop eqns) with T_b from N_rho; R_gas = P[4], C_p = gamma R/(gamma-1); or the
+      // flux-balanced profile's table
       const double Nr = P[0], rb = P[1], rt = P[2], rhob = P[3], Rg = P[4], amp = P[5];
       const double g = A.gamma;
       const double Cp = g * Rg / (g - 1.0);
       const double r = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
-      const double Tb = (-A.GM / rt + A.GM / rb) / (Cp * (1.0 - exp(-(g - 1.0) * Nr)));
-      const double pb = rhob * Rg * Tb;
-      const double zeta = 1.0 - (-A.GM / r + A.GM / rb) / (Cp * Tb);
-      const double rho0 = rhob * pow(zeta, 1.0 / (g - 1.0));
-      const double p0 = pb * pow(zeta, g / (g - 1.0));
+      double rho0, p0;
+      if (A.kind == SD_INIT_SHELL_POLYTROPE) {
+        const double Tb = (-A.GM / rt + A.GM / rb) / (Cp * (1.0 - exp(-(g - 1.0) * Nr)));
+        const double pb = rhob * Rg * Tb;
+        const double zeta = 1.0 - (-A.GM / r + A.GM / rb) / (Cp * Tb);
+        rho0 = rhob * pow(zeta, 1.0 / (g - 1.0));
+        p0 = pb * pow(zeta, g / (g - 1.0));
+      } else {
+        profile_at(A.tab, g, r, rho0, p0);
+      }
       const unsigned long long z = splitmix64(A.seed, (unsigned long long)(e * N3 + n));
       const double xi = 2.0 * ((double)(z >> 11) * 0x1.0p-53) - 1.0;
       const double rho = rho0 * (1.0 - amp * xi * sin(M_PI * (r - rb) / (rt - rb)));
@@ -323,7 +346,8 @@ __global__ void state_init_kernel(const InitArgs A, const double* __restrict__ X
   }
 }
 
-cudaError_t launch_state_init(const sd_mesh* m, const sd_phys* ph, const sd_init* in, double B0dip, double* q,
+cudaError_t launch_state_init(const sd_mesh* m, const sd_phys* ph, const sd_init* in, double B0dip,
+                              const ProfileTable& tab, double* q,
                               double* qbg, cudaStream_t s) {
   InitArgs A;
   A.kind = in->kind;
@@ -336,6 +360,8 @@ cudaError_t launch_state_init(const sd_mesh* m, const sd_phys* ph, const sd_init
   A.gamma = ph->gamma;
   A.GM = ph->GM;
   A.B0dip = B0dip;
+  A.tab = tab;
+  if (in->kind == SD_INIT_SHELL_FLUX_BALANCED && !tab.tab) return cudaErrorInvalidValue;
   const int64_t tot = m->n_e * m->stride;
   if (tot == 0) return cudaSuccess;
   state_init_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(A, m->X64, q, qbg);

@@ -153,7 +153,15 @@ cudaError_t launch_spherical(const sd_mesh* m, const double* q, double r_min, do
 cudaError_t launch_grad(const sd_mesh* m, const StageParams& P, cudaStream_t s);
 cudaError_t launch_geometry(sd_mesh* m, const double* d_corners, int* d_flag, cudaStream_t s);
 cudaError_t launch_canonical_faces(sd_mesh* m, cudaStream_t s);
-cudaError_t launch_state_init(const sd_mesh* m, const sd_phys* ph, const sd_init* in, double B0dip, double* q,
+// radial profile table of the flux-balanced initial state: [4][n + 1] = rho, S, drho/dr, dS/dr on
+// uniform nodes r_b + k h (tab = nullptr for the other kinds)
+struct ProfileTable {
+  const double* tab;
+  int n;
+  double rb, h, Cp;
+};
+cudaError_t launch_state_init(const sd_mesh* m, const sd_phys* ph, const sd_init* in, double B0dip,
+                              const ProfileTable& tab, double* q,
                               double* qbg, cudaStream_t s);
 cudaError_t launch_diag(const sd_mesh* m, const sd_phys* ph, const double* q, cudaStream_t s);
 cudaError_t launch_bg_prepare(const sd_mesh* m, double gamma, double inv_gm1, const double* q_bg, double* q0,

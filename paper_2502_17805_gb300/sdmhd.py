@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(HERE, "libsdmhd.so")
 
 SD_FP64, SD_FP32_MIXED = 0, 1
 BC_PERIODIC, BC_WALL_CONDUCTING, BC_WALL_RADIAL, BC_FARFIELD = 0, 1, 2, 3
-INIT_UNIFORM, INIT_ALFVEN, INIT_SHELL_POLYTROPE, INIT_DIVB_PULSE = 0, 1, 2, 3
+INIT_UNIFORM, INIT_ALFVEN, INIT_SHELL_POLYTROPE, INIT_DIVB_PULSE, INIT_SHELL_FLUX_BALANCED = 0, 1, 2, 3, 4
 STATUS = {0: "SD_OK", 1: "SD_ERR_INVALID_ARGUMENT", 2: "SD_ERR_UNSUPPORTED", 3: "SD_ERR_MESH_TOPOLOGY",
           4: "SD_ERR_MESH_GEOMETRY", 5: "SD_ERR_OUT_OF_MEMORY", 6: "SD_ERR_CUDA", 7: "SD_ERR_NONPHYSICAL",
           8: "SD_ERR_TIMEOUT"}

@@ -312,3 +312,26 @@ def test_advance_equals_repeated_steps(prec, N):
     qc = qb_.clone()
     gm.advance(gph, 0.2, 0, qc, wb, **kw)
     assert torch.equal(qc, qb_)
+
+
+def test_flux_balanced_state_and_mixed_residual():
+    """The almost flux-balanced initial state (host-integrated radial table, interpolated on the
+    device) against the oracle's, and the FP32-mixed residual around it as background."""
+    N = 5
+    v, h = inputs.shell_mesh(3, 2)
+    gm, om = _pair(N, v, h, geom=1, r_in=0.7, r_out=0.98, bc_in=sdref.BC_WALL_CONDUCTING,
+                   bc_out=sdref.BC_WALL_RADIAL)
+    gph, oph = _phys(powell=1, c_h=1.0, glm_alpha=0.5, gravity=1, GM=1.0, coriolis=1, omega=1.0)
+    prm = [3.0, 0.7, 0.98, 1.0, 1.0, 1e-4, 1e-6, 0.02, 0.05, 0.01]
+    q0, qb = om.state_init(oph, sdref.INIT_SHELL_FLUX_BALANCED, prm, seed=3, background=True)
+    gb = gm.empty_state()
+    gq = gm.state_init(gph, sdmhd.INIT_SHELL_FLUX_BALANCED, prm, seed=3, background=gb)
+    for g, o in ((gm.to_host(gq), q0), (gm.to_host(gb), qb)):
+        scale = np.abs(o).reshape(9, -1).max(axis=1)
+        err = np.abs(g - o).reshape(9, -1).max(axis=1)
+        assert np.all(err <= 1e-12 * np.maximum(scale, 1e-300)), (err, scale)
+    bg = gm.background(gph, gm.to_device(qb))
+    R = gm.to_host(gm.residual(gph, gm.to_device(q0), prec=sdmhd.SD_FP32_MIXED, bg=bg))
+    Ro, s = om.residual(oph, q0)
+    ok, err, bound = mixed_ok(R, Ro, s)
+    assert ok, (err, bound)
