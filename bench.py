@@ -217,9 +217,12 @@ def time_steps(mesh, phys, q, work, prec, bg, steps, warmup, sampler=None, barri
     return ms, prof, clocks
 
 
-def time_e2e(mesh, phys, q_dev, work, bg, steps, warmup):
-    """Through the C ABI with host buffers: every step copies the state from pinned host memory to the
-    device, runs sd_step, and copies the new state (and dt, c_h) back."""
+def time_e2e(mesh, phys, q_dev, work, bg, steps, warmup, chunks=16):
+    """Through the C ABI with host buffers: every step copies the whole state from pinned host memory
+    to the device, runs sd_step, and copies the whole new state (and dt, c_h) back.  The copies run
+    in `chunks` pieces on two copy streams: piece i of a step's input goes up as soon as piece i of
+    the previous step's result has come down, so the two directions overlap; the step waits for all
+    of its input."""
     import torch
 
     from paper_2502_17805_gb300 import sdmhd
@@ -228,12 +231,28 @@ def time_e2e(mesh, phys, q_dev, work, bg, steps, warmup):
     dts = torch.zeros(2, dtype=torch.float64, device="cuda")
     dts_h = torch.zeros(2, dtype=torch.float64, pin_memory=True)
     s = torch.cuda.current_stream()
+    up, down = torch.cuda.Stream(), torch.cuda.Stream()
+    hflat, dflat = host.view(-1), q_dev.view(-1)
+    bounds = [len(hflat) * k // chunks for k in range(chunks + 1)]
+    came_down = [torch.cuda.Event() for _ in range(chunks)]
+    for ev in came_down:
+        ev.record(down)
 
     def one():
-        q_dev.copy_(host, non_blocking=True)
+        # this step's input, piece by piece behind the previous step's result
+        up.wait_stream(s)
+        for k in range(chunks):
+            up.wait_event(came_down[k])
+            with torch.cuda.stream(up):
+                dflat[bounds[k]:bounds[k + 1]].copy_(hflat[bounds[k]:bounds[k + 1]], non_blocking=True)
+        s.wait_stream(up)
         mesh.step(phys, CFL, q_dev, work, prec=sdmhd.SD_FP32_MIXED, bg=bg, dt_out=dts)
-        host.copy_(q_dev, non_blocking=True)
-        dts_h.copy_(dts, non_blocking=True)
+        down.wait_stream(s)
+        with torch.cuda.stream(down):
+            for k in range(chunks):
+                hflat[bounds[k]:bounds[k + 1]].copy_(dflat[bounds[k]:bounds[k + 1]], non_blocking=True)
+                came_down[k].record(down)
+            dts_h.copy_(dts, non_blocking=True)
 
     for _ in range(warmup):
         one()
@@ -242,6 +261,7 @@ def time_e2e(mesh, phys, q_dev, work, bg, steps, warmup):
     e0.record(s)
     for _ in range(steps):
         one()
+    s.wait_stream(down)
     e1.record(s)
     torch.cuda.synchronize()
     nbytes = q_dev.numel() * 8
