@@ -53,6 +53,13 @@
  *  V5 at wall and far-field faces the viscous flux is this side's own (the paper's stress-free,
  *     heat-flux and magnetic boundary conditions are not part of the inviscid wall ghost).
  *  V6 the coefficients mu, eta, kappa, kappa_r and R are constants.
+ *  W1 viscous walls (visc_walls; Sec. Problem Formulation): stress-free and impenetrable, i.e. of
+ *     the viscous stress only n.tau.n acts through a wall, on the face state (the average of the two
+ *     sides, whose normal velocity vanishes), so the wall does no viscous work.
+ *  W2 the heat flux through the inner sphere is the prescribed q_bottom (the paper's L / (4 pi r_b^2));
+ *     the outer sphere holds T = T_top as the common (BR1) value of T in the gradients and conducts
+ *     with this side's gradients.  The paper's magnetic derivative conditions are not modelled: the
+ *     resistive wall terms are this side's.
  *  F1 flux-balanced initial profile (Sec. Initial Conditions): the printed density equation has
  *     exp(+gamma S / C_p); hydrostatic balance dp/dr = -rho g with S = C_p ln(p^(1/gamma) / rho)
  *     requires exp(-gamma S / C_p), which is used (with it the isentropic case is the polytrope).
@@ -195,6 +202,7 @@ struct sdref_mesh {
   int32_t* owner;  /* [n_e*6] 1 if this side computes the common flux */
   int32_t* code;   /* [n_e*6] orientation code */
   int32_t* bc;     /* [n_e*6] boundary condition of a boundary face */
+  int32_t* outer;  /* [n_e*6] 1 for a boundary face on the outer sphere of the shell */
   int64_t n_bf, n_if;
   double h_min;
   double** gcache; /* per element geometry block */
@@ -307,6 +315,7 @@ sdref_mesh* sdref_mesh_create(int N, int64_t n_v, const double* verts, int64_t n
   m->owner = (int32_t*)calloc(6 * n_e, sizeof(int32_t));
   m->code = (int32_t*)calloc(6 * n_e, sizeof(int32_t));
   m->bc = (int32_t*)calloc(6 * n_e, sizeof(int32_t));
+  m->outer = (int32_t*)calloc(6 * n_e, sizeof(int32_t));
   m->gcache = (double**)calloc(n_e, sizeof(double*));
   for (int64_t i = 0; i < 6 * n_e; ++i) m->nb_e[i] = -1;
 
@@ -349,6 +358,7 @@ sdref_mesh* sdref_mesh_create(int N, int64_t n_v, const double* verts, int64_t n
           }
         double rc = sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
         bcv = rc < 0.5 * (r_in + r_out) ? bc_in : bc_out;
+        m->outer[6 * e + F] = rc < 0.5 * (r_in + r_out) ? 0 : 1;
       }
       if (bcv == SDREF_BC_PERIODIC) { set_err("unmatched face with periodic boundary condition"); free(fr); sdref_mesh_destroy(m); return NULL; }
       m->bc[6 * e + F] = bcv;
@@ -379,7 +389,7 @@ void sdref_mesh_destroy(sdref_mesh* m) {
   if (m->gcache)
     for (int64_t e = 0; e < m->n_e; ++e) free(m->gcache[e]);
   free(m->gcache);
-  free(m->verts); free(m->hex); free(m->nb_e); free(m->nb_f); free(m->owner); free(m->code); free(m->bc);
+  free(m->verts); free(m->hex); free(m->nb_e); free(m->nb_f); free(m->owner); free(m->code); free(m->bc); free(m->outer);
   free(m);
 }
 
@@ -797,6 +807,8 @@ static void element_gradient(const sdref_mesh* m, const sdref_phys* ph, const do
           double Q2[9], w2[NW];
           face_partner(m, ph, q, e, 2 * d + side, a, b, Qf[f], Q2);
           prim_w(Q2, ph, w2);
+          int64_t kf = 6 * e + 2 * d + side;
+          if (ph->visc_walls && m->nb_e[kf] < 0 && m->outer[kf]) w2[3] = 2.0 * ph->T_top - wf[f][3]; /* W2 */
           for (int c = 0; c < NW; ++c) wf[f][c] = 0.5 * (wf[f][c] + w2[c]);
         }
         for (int i = 0; i < N; ++i) {
@@ -826,12 +838,57 @@ static void grad_face_value(const sdref_mesh* m, const double* G, int64_t e, int
   }
 }
 
+/* viscous flux through a wall face along its unit outward normal n (readings W1, W2): stress-free
+ * and impenetrable, only the normal viscous stress n.tau.n acts, on the face state (the average of
+ * this side and its wall ghost, whose normal velocity vanishes); the heat flux is q_bottom into the
+ * shell on the inner sphere and the conducted one (this side's gradients) on the outer; the
+ * resistive terms are this side's */
+static void wall_visc(const sdref_mesh* m, const sdref_phys* ph, int64_t e, int F, const double* Qown,
+                      const double* g, const double* n, double* F_, double* fm) {
+  int64_t k = 6 * e + F;
+  double gh[9], Qf[9], w[NW];
+  ghost_state(Qown, n, m->bc[k], ph, gh);
+  for (int v = 0; v < 9; ++v) Qf[v] = 0.5 * (Qown[v] + gh[v]);
+  prim_w(Qf, ph, w);
+  double rho = Qf[0], T = w[3], cp = ph->gamma * ph->R_gas / (ph->gamma - 1.0);
+  double divu = g[0 * 3 + 0] + g[1 * 3 + 1] + g[2 * 3 + 2], tnn = 0.0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      tnn += n[i] * (ph->mu * (g[i * 3 + j] + g[j * 3 + i]) + (i == j ? -2.0 / 3.0 * ph->mu * divu : 0.0)) * n[j];
+  double J[3] = {g[7 * 3 + 1] - g[6 * 3 + 2], g[5 * 3 + 2] - g[7 * 3 + 0], g[6 * 3 + 0] - g[5 * 3 + 1]};
+  double BxJ[3], Jxn[3];
+  cross3(w + 5, J, BxJ);
+  cross3(J, n, Jxn);
+  double qn = 0.0, qm = 0.0;
+  if (m->outer[k]) {
+    for (int j = 0; j < 3; ++j) {
+      double qj = -ph->kappa * rho * T * g[4 * 3 + j] - ph->kappa_r * rho * cp * g[3 * 3 + j];
+      qn += qj * n[j];
+      qm += fabs(qj * n[j]);
+    }
+  } else {
+    qn = -ph->q_bottom; /* q = q_bottom r^ and n = -r^ on the inner sphere */
+    qm = fabs(qn);
+  }
+  double un = w[0] * n[0] + w[1] * n[1] + w[2] * n[2];
+  double bj = ph->eta * (BxJ[0] * n[0] + BxJ[1] * n[1] + BxJ[2] * n[2]);
+  for (int v = 0; v < 9; ++v) { F_[v] = 0.0; fm[v] = 0.0; }
+  for (int i = 0; i < 3; ++i) { F_[1 + i] = tnn * n[i]; fm[1 + i] = fabs(tnn * n[i]); }
+  F_[4] = un * tnn - qn + bj;
+  fm[4] = fabs(un * tnn) + qm + fabs(bj);
+  for (int i = 0; i < 3; ++i) { F_[5 + i] = ph->eta * Jxn[i]; fm[5 + i] = fabs(ph->eta * Jxn[i]); }
+}
+
 /* common viscous flux through face F of element e at (a,b) along the unit normal n (reading V4):
  * the average of both sides' F_vis . n; at a wall or far-field face this side's alone (reading V5) */
 static void common_visc(const sdref_mesh* m, const sdref_phys* ph, const double* q, const double* G, int64_t e, int F,
                         int a, int b, const double* Qown, const double* gown, const double* n, double* Fv,
                         double* Fvm) {
   int64_t k = 6 * e + F;
+  if (m->nb_e[k] < 0 && ph->visc_walls) {
+    wall_visc(m, ph, e, F, Qown, gown, n, Fv, Fvm);
+    return;
+  }
   visc_flux(Qown, gown, n, ph, Fv, Fvm);
   if (m->nb_e[k] < 0) return;
   int a2, b2;

@@ -48,6 +48,11 @@ typedef struct {
    * C_p = gamma R_gas / (gamma - 1)), all constant */
   double mu, eta, kappa, kappa_r, R_gas;
   int32_t viscous, pad2_;
+  /* walls of the viscous path (Sec. Problem Formulation; readings W1, W2), when visc_walls != 0:
+   * stress-free and impenetrable walls, the heat flux q_bottom (per area, into the shell) through the
+   * inner sphere, the temperature T_top on the outer sphere; otherwise a wall takes its own F_vis */
+  double q_bottom, T_top;
+  int32_t visc_walls, pad3_;
 } sdref_phys;
 
 typedef struct {
