@@ -125,6 +125,14 @@ typedef struct {
   double mu, eta, kappa, kappa_r, R_gas;
   int32_t viscous;
   int32_t pad2_;
+  /* Walls of the viscous path (Sec. Problem Formulation) when visc_walls != 0: stress-free and
+   * impenetrable (only the normal viscous stress acts, on the face state whose normal velocity
+   * vanishes), the heat flux q_bottom (per area, into the shell) through the inner sphere and the
+   * temperature T_top held on the outer sphere (the common value of T in the BR1 gradients).  The
+   * paper's magnetic derivative conditions are not modelled.  Otherwise a wall passes its own F_vis. */
+  double q_bottom, T_top;
+  int32_t visc_walls;
+  int32_t pad3_;
 } sd_phys;
 
 typedef struct {

@@ -260,6 +260,9 @@ sd::StageParams base_params(const sd_mesh* m, const sd_phys* ph, int prec) {
   P.kappa = ph->kappa;
   P.kappa_r = ph->kappa_r;
   P.R_gas = ph->R_gas;
+  P.visc_walls = ph->visc_walls ? 1 : 0;
+  P.q_bottom = ph->q_bottom;
+  P.T_top = ph->T_top;
   return P;
 }
 
@@ -332,6 +335,8 @@ sd_status check_common(const sd_mesh* m, const sd_phys* ph, int prec, const sd_b
         !isfinite(ph->mu + ph->eta + ph->kappa + ph->kappa_r))
       return fail(SD_ERR_INVALID_ARGUMENT, "viscous coefficients must be finite and non-negative");
     if (!(ph->R_gas > 0.0) || !isfinite(ph->R_gas)) return fail(SD_ERR_INVALID_ARGUMENT, "R_gas must be positive");
+    if (ph->visc_walls && (!(ph->T_top > 0.0) || !isfinite(ph->T_top) || !isfinite(ph->q_bottom)))
+      return fail(SD_ERR_INVALID_ARGUMENT, "viscous walls need T_top > 0 and a finite q_bottom");
   }
   if (prec == SD_FP32_MIXED) {
     if (!bg) return fail(SD_ERR_INVALID_ARGUMENT, "the FP32-mixed path needs a background (sd_background_create)");
@@ -517,7 +522,7 @@ sd_status sd_mesh_create(const sd_mesh_desc* desc, void* stream, sd_mesh** out) 
       ++n_if;
     } else {
       const FaceKey& A = faces[i];
-      int bc = desc->bc_inner;
+      int bc = desc->bc_inner, outer = 0;
       if (desc->geom == 1) {
         double c[3] = {0, 0, 0};
         for (int s = 0; s < 2; ++s)
@@ -527,9 +532,10 @@ sd_status sd_mesh_create(const sd_mesh_desc* desc, void* stream, sd_mesh** out) 
           }
         const double rc = sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
         bc = rc < 0.5 * (desc->r_inner + desc->r_outer) ? desc->bc_inner : desc->bc_outer;
+        outer = rc < 0.5 * (desc->r_inner + desc->r_outer) ? 0 : 1;
       }
       if (bc == SD_BC_PERIODIC) return fail(SD_ERR_MESH_TOPOLOGY, "unmatched face under a periodic boundary");
-      meta[A.e * 6 + A.F] = bc << 6;
+      meta[A.e * 6 + A.F] = (bc << 6) | (outer << 10);
       ++n_bf;
     }
     i = j;

@@ -32,6 +32,8 @@ struct Ops {
 __host__ __device__ inline int meta_nbF(int m) { return m & 7; }
 __host__ __device__ inline int meta_code(int m) { return (m >> 3) & 7; }
 __host__ __device__ inline int meta_bc(int m) { return (m >> 6) & 7; }
+// boundary face on the outer sphere of a shell (bit 10)
+__host__ __device__ inline int meta_outer(int m) { return (m >> 10) & 1; }
 __host__ __device__ inline int meta_owner(int m) { return (m >> 9) & 1; }
 
 enum StageMode { MODE_RESIDUAL = 0, MODE_RK = 1, MODE_DIVB = 2 };
@@ -78,8 +80,9 @@ struct StageParams {
   // viscous, resistive and thermal fluxes (FP64 policy): coefficients, the gradients of
   // (U, T, S, B) at the solution points [e][24][N^3] (grad[3c + j] = d w_c / d x_j) and their
   // face traces [e][F][24][N^2]; the gradient kernel writes grad_out / gtr_out
-  int visc;
+  int visc, visc_walls;
   double mu, eta, kappa, kappa_r, R_gas;
+  double q_bottom, T_top;  // wall conditions of the viscous path (visc_walls)
   const double* grad;
   const double* gtr_in;
   double* grad_out;

@@ -386,10 +386,14 @@ __global__ void __launch_bounds__(Dims<N>::BLK) stage_kernel(const StageParams P
       riemann_mixed(qo, qn, nx, ny, nz, gamma, ch, jr, jp, Fs);
     }
     if constexpr (VISC) {
-      // average of both sides' F_vis . n (this side's alone at a wall or far-field face)
+      // average of both sides' F_vis . n (this side's alone at a wall or far-field face,
+      // or the wall conditions of visc_walls)
       double g[NGRAD], Fv[9];
       grad_face<N>(sG, sE, F, a, b, g);
-      visc_flux(qo, g, nx, ny, nz, vc, Fv);
+      if (nb < 0 && P.visc_walls)
+        wall_visc_flux(qo, qn, g, nx, ny, nz, meta_outer(mt) != 0, P.q_bottom, vc, Fv);
+      else
+        visc_flux(qo, g, nx, ny, nz, vc, Fv);
       if (nb >= 0) {
         const int code = meta_code(mt);
         const int u = (code & 4) ? b : a, w = (code & 4) ? a : b;

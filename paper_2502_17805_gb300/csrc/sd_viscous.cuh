@@ -99,6 +99,50 @@ __device__ __forceinline__ void visc_flux(const double* Q, const double* g, doub
   F[8] = 0.0;
 }
 
+// Viscous flux through a wall face along its unit outward normal n (visc_walls):
+// stress-free and impenetrable, only the normal stress n.tau.n acts, on the face
+// state qf = (own + ghost) / 2 (whose normal velocity vanishes); the heat flux is
+// q_bottom into the shell on the inner sphere (q = q_bottom r^, n = -r^) and the
+// conducted one on the outer; the resistive terms are this side's.
+__device__ __forceinline__ void wall_visc_flux(const double* qo, const double* qn, const double* g, double nx,
+                                               double ny, double nz, bool outer, double q_bottom,
+                                               const ViscCoef& c, double* F) {
+  double qf[9], w[8];
+#pragma unroll
+  for (int v = 0; v < 9; ++v) qf[v] = 0.5 * (qo[v] + qn[v]);
+  prim_w(qf, c, w);
+  const double n[3] = {nx, ny, nz};
+  const double divu = g[0] + g[4] + g[8];
+  double tnn = 0.0;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      tnn += n[i] * (c.mu * (g[3 * i + j] + g[3 * j + i]) + (i == j ? c.lam * divu : 0.0)) * n[j];
+  const double Jx = g[3 * 7 + 1] - g[3 * 6 + 2], Jy = g[3 * 5 + 2] - g[3 * 7 + 0], Jz = g[3 * 6 + 0] - g[3 * 5 + 1];
+  const double Bx = w[5], By = w[6], Bz = w[7];
+  const double bj = c.eta * ((By * Jz - Bz * Jy) * nx + (Bz * Jx - Bx * Jz) * ny + (Bx * Jy - By * Jx) * nz);
+  double qdn;
+  if (outer) {
+    const double rT = qf[0] * w[3];
+    qdn = 0.0;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) qdn += (-c.kappa * rT * g[3 * 4 + j] - c.kappa_r * qf[0] * c.cp * g[3 * 3 + j]) * n[j];
+  } else {
+    qdn = -q_bottom;
+  }
+  const double un = w[0] * nx + w[1] * ny + w[2] * nz;
+  F[0] = 0.0;
+  F[1] = tnn * nx;
+  F[2] = tnn * ny;
+  F[3] = tnn * nz;
+  F[4] = un * tnn - qdn + bj;
+  F[5] = c.eta * (Jy * nz - Jz * ny);
+  F[6] = c.eta * (Jz * nx - Jx * nz);
+  F[7] = c.eta * (Jx * ny - Jy * nx);
+  F[8] = 0.0;
+}
+
 // gradients of element e's solution extrapolated to point (a, b) of its face F
 // (sG: [24][N^3] in shared memory); the stage kernel and the face traces below
 // use this same sum, so both sides of a face see the same bits
@@ -193,6 +237,7 @@ __global__ void __launch_bounds__(Dims<N>::BLK) grad_kernel(const StageParams P,
           }
         }
         prim_w(Q2, c, w2);
+        if (nb < 0 && P.visc_walls && meta_outer(mt)) w2[3] = 2.0 * P.T_top - w[3];  // T held on the outer wall
 #pragma unroll
         for (int k = 0; k < 8; ++k) w[k] = 0.5 * (w[k] + w2[k]);
       }

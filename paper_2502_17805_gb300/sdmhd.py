@@ -50,7 +50,8 @@ class PhysC(C.Structure):
                 ("c_h", C.c_double), ("powell", C.c_int32), ("gravity", C.c_int32), ("coriolis", C.c_int32),
                 ("pad_", C.c_int32), ("farfield", C.c_double * 9), ("mu", C.c_double), ("eta", C.c_double),
                 ("kappa", C.c_double), ("kappa_r", C.c_double), ("R_gas", C.c_double), ("viscous", C.c_int32),
-                ("pad2_", C.c_int32)]
+                ("pad2_", C.c_int32), ("q_bottom", C.c_double), ("T_top", C.c_double), ("visc_walls", C.c_int32),
+                ("pad3_", C.c_int32)]
 
 
 class InitC(C.Structure):
@@ -97,6 +98,10 @@ class Phys:
     kappa_r: float = 0.0
     R_gas: float = 1.0
     viscous: int = 0
+    # walls of the viscous path: stress-free, heat flux through the inner sphere, temperature on the outer
+    q_bottom: float = 0.0
+    T_top: float = 1.0
+    visc_walls: int = 0
 
     def c(self) -> PhysC:
         p = PhysC()
@@ -106,6 +111,7 @@ class Phys:
             p.farfield[i] = float(self.farfield[i])
         p.mu, p.eta, p.kappa, p.kappa_r, p.R_gas = self.mu, self.eta, self.kappa, self.kappa_r, self.R_gas
         p.viscous = int(self.viscous)
+        p.q_bottom, p.T_top, p.visc_walls = self.q_bottom, self.T_top, int(self.visc_walls)
         return p
 
 

@@ -116,3 +116,21 @@ def test_viscous_fluxes_are_rejected_where_unsupported():
     bad = sdmhd.Phys(gravity=1, GM=1.0, **dict(VISC, mu=-1.0))
     with pytest.raises(sdmhd.SDError, match="non-negative"):
         gm.residual(bad, q)
+
+
+@pytest.mark.parametrize("N", [4, 5])
+def test_viscous_walls_residual(N):
+    """Stress-free walls, heat flux through the inner sphere, temperature held on the outer sphere."""
+    v, h = inputs.shell_mesh(2, 2)
+    h = inputs.reorient(h, seed=6)
+    gm, om = _pair(N, v, h, geom=1, r_in=0.7, r_out=0.98, bc_in=sdref.BC_WALL_CONDUCTING,
+                   bc_out=sdref.BC_WALL_RADIAL)
+    walls = dict(VISC, visc_walls=1, q_bottom=0.05, T_top=0.6)
+    gph, oph = _phys(powell=1, c_h=0.8, glm_alpha=0.5, gravity=1, GM=1.0, coriolis=1, omega=1.0, **walls)
+    q0 = inputs.random_state(gm.n_e, N, seed=41)
+    R = gm.to_host(gm.residual(gph, gm.to_device(q0)))
+    Ro, s = om.residual(oph, q0)
+    assert _c19(R, Ro, s) < TOL64
+    # and the walls change the residual of the wall elements
+    R_own, _ = om.residual(sdref.Phys(**dict(vars(oph), visc_walls=0)), q0)
+    assert np.abs(Ro - R_own).max() > 1e-3 * np.abs(Ro).max()
