@@ -88,19 +88,21 @@ __device__ __forceinline__ float point_speed_mixed(const float* qf, float g) {
 
 // Running maximum that keeps a NaN (a non-physical state must not pass unseen).
 __device__ __forceinline__ double speed_max(double lam, double l) { return (l > lam || l != l) ? l : lam; }
+__device__ __forceinline__ float speed_max(float lam, float l) { return (l > lam || l != l) ? l : lam; }
 
 // Maximum over the warp, then one atomic per warp into one of nslot (a power of
 // two) partial maxima, so that the atomics of a launch spread over several
 // addresses instead of queueing on one; the step-control kernel reduces the
 // slots.  Positive doubles order like their bit patterns, and a NaN (all
 // exponent bits set) is above every finite value.
-__device__ __forceinline__ void speed_reduce(double lam, unsigned long long* dst, int nslot) {
+template <typename R>
+__device__ __forceinline__ void speed_reduce(R lam, unsigned long long* dst, int nslot) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) lam = speed_max(lam, __shfl_xor_sync(0xffffffffu, lam, o));
   if ((threadIdx.x & 31) == 0) {
     const unsigned warp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const unsigned slot = nslot > 1 ? warp & (unsigned)(nslot - 1) : 0u;
-    atomicMax(dst + slot, (unsigned long long)__double_as_longlong(lam));
+    atomicMax(dst + slot, (unsigned long long)__double_as_longlong((double)lam));
   }
 }
 
@@ -114,6 +116,7 @@ __device__ __forceinline__ void load_element(const StageParams& P, const double*
                                              typename Pol::R* sQ, double* lam_out) {
   constexpr int N3 = N * N * N, BLK = Dims<N>::BLK;
   double lam = 0.0;
+  float lamf = 0.0f;  // mixed policy: the maximum of FP32 speeds, taken in FP32 (the same value)
   for (int n = threadIdx.x; n < N3; n += BLK) {
     const int64_t g = e * P.stride + n;
     double qv[9];
@@ -129,7 +132,7 @@ __device__ __forceinline__ void load_element(const StageParams& P, const double*
       float qf[9];
 #pragma unroll
       for (int v = 0; v < 9; ++v) qf[v] = f64_to_f32(qv[v]);
-      if (lam_out) lam = speed_max(lam, (double)point_speed_mixed(qf, (float)P.gamma));
+      if (lam_out) lamf = speed_max(lamf, point_speed_mixed(qf, (float)P.gamma));
 #pragma unroll
       for (int v = 0; v < 9; ++v) sQ[v * N3 + n] = qf[v];
       sQ[0 * N3 + n] = f64_to_f32(qv[0] - f32_to_f64(r0));
@@ -138,7 +141,7 @@ __device__ __forceinline__ void load_element(const StageParams& P, const double*
       sQ[10 * N3 + n] = p0;
     }
   }
-  if (lam_out) *lam_out = lam;
+  if (lam_out) *lam_out = Pol::mixed ? (double)lamf : lam;
 }
 
 // Extrapolate the element state in shared memory to its 6 N^2 face points and
@@ -174,7 +177,12 @@ __device__ __forceinline__ void trace_body(const StageParams& P, const Ops<typen
   for (int i = threadIdx.x; i < NF * N; i += BLK) sE[i] = ops.E[i];
   double lam = 0.0;
   load_element<N, Pol>(P, P.q_in, e, sQ, P.lam_max ? &lam : nullptr);
-  if (P.lam_max) speed_reduce(lam, P.lam_max, P.lam_nslot);
+  if (P.lam_max) {
+    if constexpr (Pol::mixed)
+      speed_reduce((float)lam, P.lam_max, P.lam_nslot);  // exact: lam holds an FP32 value
+    else
+      speed_reduce(lam, P.lam_max, P.lam_nslot);
+  }
   __syncthreads();
   write_traces<N, Pol>(sQ, sE, reinterpret_cast<R*>(P.tr_out), e);
 }

@@ -290,7 +290,7 @@ __device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops<fl
   // as a fresh load would round it: the traces and lambda_max equal those of a
   // separate trace pass over the output, bit for bit.
   constexpr bool exact = EXACT;
-  double lam = 0.0;
+  float lam = 0.0f;  // maximum of FP32 speeds (taken in FP32, converted once when reduced)
   if (lsr && !incr) mbar_wait_bounded(&dbar, 0u, P.err);
   if (DV::STAGE_G) mbar_wait_bounded(&gbar, 0u, P.err);
   for (int n = tid; n < N3; n += T) {
@@ -351,7 +351,7 @@ __device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops<fl
           sQ[v * N3 + n] = exact ? new_qprime(v, qo, qe[v], q[9], q[10], inv_gm1) : q[v] + t;
         }
       }
-      if (exact) lam = speed_max(lam, (double)point_speed_mixed(qe, gamma));
+      if (exact) lam = speed_max(lam, point_speed_mixed(qe, gamma));
     } else if (lsr_read || lsr_write) {
       // low-storage form: t = -a D + b dt R, q_out = q_in + t, D <- D + t, with D = q_in - q_n
       const int64_t gd = e * DV::DSTRIDE + n, dplane = n_e * DV::DSTRIDE;
@@ -367,7 +367,7 @@ __device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops<fl
         if (exact) qe[v] = f64_to_f32(qo);
         sQ[v * N3 + n] = exact ? new_qprime(v, qo, qe[v], q[9], q[10], inv_gm1) : q[v] + t;
       }
-      if (exact) lam = speed_max(lam, (double)point_speed_mixed(qe, gamma));
+      if (exact) lam = speed_max(lam, point_speed_mixed(qe, gamma));
     } else {
       float qe[9];
 #pragma unroll
@@ -380,7 +380,7 @@ __device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops<fl
         if (exact) qe[v] = f64_to_f32(qo);
         sQ[v * N3 + n] = exact ? new_qprime(v, qo, qe[v], q[9], q[10], inv_gm1) : q[v] + t;
       }
-      if (exact) lam = speed_max(lam, (double)point_speed_mixed(qe, gamma));
+      if (exact) lam = speed_max(lam, point_speed_mixed(qe, gamma));
     }
   }
   if (exact) speed_reduce(lam, P.lam_max, P.lam_nslot);
