@@ -197,28 +197,51 @@ __device__ __forceinline__ void riemann_fp64(const double* qo, const double* qn,
   for (int v = 0; v < 9; ++v) Fs[v] = 0.5 * (FL[v] + FR[v]) - hl * (qn[v] - qo[v]);
 }
 
+// One side of the mixed-policy Rusanov flux: the perturbation flux of q (q'(9);
+// background rho0 = r0, p0 = p0) along the unit normal n, and |U.n| + c_f.  The
+// velocity, 1/rho, |B|^2, B.n and p' serve both.
+__device__ __forceinline__ float side_mixed(const float* q, float r0, float p0, float nx, float ny, float nz,
+                                            float gamma, float gm1, float gg1, float ch, float* F) {
+  const float rho = r0 + q[0];
+  const float ir = 1.0f / rho;
+  const float ux = q[1] * ir, uy = q[2] * ir, uz = q[3] * ir;
+  const float Bx = q[5], By = q[6], Bz = q[7], psi = q[8];
+  const float B2 = Bx * Bx + By * By + Bz * Bz;
+  const float mu = q[1] * ux + q[2] * uy + q[3] * uz;
+  const float pp = gm1 * (q[4] - 0.5f * (mu + B2 + psi * psi));  // p' = p - p0
+  const float un = ux * nx + uy * ny + uz * nz;
+  const float Bn = Bx * nx + By * ny + Bz * nz;
+  const float uB = ux * Bx + uy * By + uz * Bz;
+  const float ptp = pp + 0.5f * B2;
+  const float chpsi = ch * psi;
+  F[0] = q[1] * nx + q[2] * ny + q[3] * nz;
+  F[1] = q[1] * un + ptp * nx - Bx * Bn;
+  F[2] = q[2] * un + ptp * ny - By * Bn;
+  F[3] = q[3] * un + ptp * nz - Bz * Bn;
+  F[4] = un * (gg1 * p0 + q[4] + ptp - 0.5f * psi * psi) - Bn * uB + chpsi * Bn;
+  F[5] = un * Bx - Bn * ux + chpsi * nx;
+  F[6] = un * By - Bn * uy + chpsi * ny;
+  F[7] = un * Bz - Bn * uz + chpsi * nz;
+  F[8] = ch * Bn;
+  // fast magnetosonic speed along n
+  const float a2 = gamma * (p0 + pp) * ir;
+  const float b2 = B2 * ir;
+  const float s = a2 + b2;
+  float disc = s * s - 4.0f * a2 * (Bn * Bn * ir);
+  disc = disc > 0.0f ? disc : 0.0f;
+  return fabsf(un) + sqrtf(0.5f * (s + sqrtf(disc)));
+}
+
 // Mixed-policy Rusanov flux of the perturbation.  qo: own q'(9), rho0, p0;
 // qn: neighbour q'(9) (the background at the face is taken from this side);
 // jr, jp: FP64-accurate background jumps (neighbour minus own) of rho0 and p0.
 __device__ __forceinline__ void riemann_mixed(const float* qo, const float* qn, float nx, float ny, float nz,
                                               float gamma, float ch, float jr, float jp, float* Fs) {
   const float gm1 = gamma - 1.0f, gg1 = gamma / (gamma - 1.0f);
-  float qn11[11];
-#pragma unroll
-  for (int v = 0; v < 9; ++v) qn11[v] = qn[v];
-  qn11[9] = qo[9];
-  qn11[10] = qo[10];
   float FL[9], FR[9];
-  flux_pert(qo, nx, ny, nz, gm1, gg1, ch, FL);
-  flux_pert(qn11, nx, ny, nz, gm1, gg1, ch, FR);
-  const float ro = qo[9] + qo[0], rn = qo[9] + qn[0];
-  const float ppo = gm1 * (qo[4] - 0.5f * ((qo[1] * qo[1] + qo[2] * qo[2] + qo[3] * qo[3]) / ro + qo[5] * qo[5] +
-                                            qo[6] * qo[6] + qo[7] * qo[7] + qo[8] * qo[8]));
-  const float ppn = gm1 * (qn[4] - 0.5f * ((qn[1] * qn[1] + qn[2] * qn[2] + qn[3] * qn[3]) / rn + qn[5] * qn[5] +
-                                            qn[6] * qn[6] + qn[7] * qn[7] + qn[8] * qn[8]));
-  const float lo = wave_speed<float>(ro, qo[1], qo[2], qo[3], qo[10] + ppo, qo[5], qo[6], qo[7], nx, ny, nz, gamma);
-  const float ln = wave_speed<float>(rn, qn[1], qn[2], qn[3], qo[10] + ppn, qn[5], qn[6], qn[7], nx, ny, nz, gamma);
-  float lam = fmaxf(fmaxf(lo, ln), ch);
+  const float lo = side_mixed(qo, qo[9], qo[10], nx, ny, nz, gamma, gm1, gg1, ch, FL);
+  const float ln = side_mixed(qn, qo[9], qo[10], nx, ny, nz, gamma, gm1, gg1, ch, FR);
+  const float lam = fmaxf(fmaxf(lo, ln), ch);
   const float hl = 0.5f * lam;
 #pragma unroll
   for (int v = 0; v < 9; ++v) {

@@ -3,16 +3,16 @@
 // Same arithmetic as stage_kernel<N, PolMixed> (sd_stage.cuh), organised so that
 // the 1D operators run from registers.  Per element (one CTA):
 //   A  load     q' (FP32 perturbation), rho0, p0 at the N^3 points -> sQ
-//   B  lines    one thread per line of each direction (3 N^2 threads) takes the
-//               line's values of one variable at a time into registers and writes
+//   B  lines    G threads per line of each direction (3 N^2 lines) take the
+//               line's values of one variable at a time into registers and write
 //               their extrapolation to all N+1 flux points of its family -> sX
 //   C  points   interior flux points: contravariant flux; face points: Rusanov
 //               and BR1 against the neighbour trace; results overwrite sX in place
-//   D  lines    each line thread differentiates its 10 x (N+1) fluxes and writes
+//   D  lines    the line threads differentiate the 10 x (N+1) fluxes and write
 //               the N derivative values over its own flux slots in sX
 //   E  points   R = -sum_d div_d / |J| + M + R0, FP64 RK sum, q' of the new state -> sQ
 //   F  lines    face traces of the new state (the two ends of every line).
-// Thread count T = max(128, 3 N^2 rounded to a warp).
+// Thread count T = 256; G = T / (3 N^2) threads share a line in B, D and F.
 #pragma once
 
 #include "sd_internal.h"
@@ -25,8 +25,11 @@ template <int N>
 struct DimsV2 {
   static constexpr int N2 = N * N, N3 = N2 * N, NF = N + 1, NV = 11;
   static constexpr int NLINE = 3 * N2;
-  static constexpr int T0 = ((NLINE + 31) / 32) * 32;
-  static constexpr int T = T0 < 128 ? 128 : T0;
+  // 256 threads: up to G = T / (3 N^2) threads share a line in the line phases,
+  // each taking every G-th variable
+  static constexpr int T = 256;
+  static_assert(NLINE <= T, "one thread per line at least");
+  static constexpr int G = T / NLINE;
   // shared memory in floats
   static constexpr int oQ = 0;                       // [11][N3]
   static constexpr int oX = oQ + NV * N3;            // [3][NF][11][N2]
@@ -43,7 +46,10 @@ struct DimsV2 {
   // CTAs per SM that the shared memory admits (228 KB per SM, 1 KB reserved per
   // CTA), capped at 5: the register budget of __launch_bounds__ follows from it.
   static constexpr int SMEM_CTAS = (int)(233472 / (bytes + 1024 + 64));
-  static constexpr int MINB = SMEM_CTAS < 1 ? 1 : (SMEM_CTAS > 5 ? 5 : SMEM_CTAS);
+  // CTAs per SM that 64 registers per thread admit
+  static constexpr int REG_CTAS = 65536 / (T * 64);
+  static constexpr int MIN_CTAS = SMEM_CTAS < REG_CTAS ? SMEM_CTAS : REG_CTAS;
+  static constexpr int MINB = MIN_CTAS < 1 ? 1 : MIN_CTAS;
 };
 
 // q' of variable v at a point of the new state qo (FP64), rounded as load_element
@@ -129,10 +135,14 @@ __device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops<fl
   // after the state loads are issued)
   if (incr && lsr) __syncthreads();  // dbar initialised before anyone polls it
 
-  // line role of this thread (B, D, F)
-  const bool is_line = tid < NL;
-  const int ld = is_line ? tid / N2 : 0;
-  const int lL = is_line ? tid % N2 : 0;
+  // line role of this thread (B, D, F): G threads per line, thread g of a line
+  // takes the variables g, g + G, ...
+  constexpr int G = DV::G;
+  const bool is_line = tid < G * NL;
+  const int lg = is_line ? tid / NL : 0;
+  const int lline = tid - lg * NL;
+  const int ld = is_line ? lline / N2 : 0;
+  const int lL = is_line ? lline % N2 : 0;
   int lbase = 0, lstride = 1;
   line_geom<N>(ld, lL, lbase, lstride);
 
@@ -181,7 +191,7 @@ __device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops<fl
   if (is_line) {
     float* X = sX + (ld * NF * 11) * N2 + lL;
 #pragma unroll 1
-    for (int v = 0; v < 11; ++v) {
+    for (int v = lg; v < 11; v += G) {
       float ql[N];
 #pragma unroll
       for (int i = 0; i < N; ++i) ql[i] = sQ[v * N3 + lbase + i * lstride];
@@ -197,9 +207,12 @@ __device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops<fl
   __syncthreads();
 
   // ---- C: fluxes at the flux points (interior first, then the element faces)
-  constexpr int NINT = 3 * (N - 1) * N2;
-  for (int t = tid; t < NINT + 6 * N2; t += T) {
-    if (t < NINT) {
+  // interior points first, their count padded to whole warps so that no warp
+  // mixes the two kinds of point
+  constexpr int NINT = 3 * (N - 1) * N2, NINT_W = (NINT + 31) / 32 * 32;
+  for (int t = tid; t < NINT_W + 6 * N2; t += T) {
+    if (t < NINT_W) {
+      if (t >= NINT) continue;
       const int d = t / ((N - 1) * N2), r = t - d * ((N - 1) * N2);
       const int f = 1 + r / N2, L = r - (f - 1) * N2;
       float* X = sX + ((d * NF + f) * 11) * N2 + L;
@@ -214,7 +227,7 @@ __device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops<fl
       for (int v = 0; v < 9; ++v) X[v * N2] = Fv[v];
       X[9 * N2] = Sx * qf[5] + Sy * qf[6] + Sz * qf[7];
     } else {
-      const int u = t - NINT;
+      const int u = t - NINT_W;
       const int F = u / N2, pt = u - F * N2, a = pt % N, b = pt / N;
       const int d = F >> 1, side = F & 1, f = side ? N : 0;
       float* X = sX + ((d * NF + f) * 11) * N2 + pt;
@@ -269,7 +282,7 @@ __device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops<fl
   if (is_line) {
     float* X = sX + (ld * NF * 11) * N2 + lL;
 #pragma unroll 1
-    for (int v = 0; v < 10; ++v) {
+    for (int v = lg; v < 10; v += G) {
       float fv[NF];
 #pragma unroll
       for (int f = 0; f <= N; ++f) fv[f] = X[(f * 11 + v) * N2];
@@ -390,8 +403,8 @@ __device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops<fl
     __syncthreads();
     if (is_line) {
       float* Tr = reinterpret_cast<float*>(P.tr_out) + (e * 6 + 2 * ld) * 9 * N2 + lL;
-#pragma unroll
-      for (int v = 0; v < 9; ++v) {
+#pragma unroll 1
+      for (int v = lg; v < 9; v += G) {
         float s0 = 0.0f, s1 = 0.0f;
 #pragma unroll
         for (int i = 0; i < N; ++i) {
