@@ -207,8 +207,11 @@ sd_status sd_state_init(const sd_mesh* mesh, const sd_phys* phys, const sd_init*
  * (device state, only rho and E are read; U = B = psi = 0 is assumed):
  * rounds rho0 and p0 to FP32, computes in FP64 the background residual R0
  * (pressure gradient with central face average, plus rho0 g) and the FP64 jumps
- * of the background across faces.  The handle stays valid while the mesh
- * lives.  Asynchronous: its device memory comes from the stream-ordered
+ * of the background across faces.  The handle also holds the FP32 scratch of
+ * the mixed sd_step (the register D and the FP32 perturbation q' of the step's
+ * starting state, 72 bytes per solution point), so one background serves one
+ * sd_step / sd_advance / packed request at a time.  The handle stays valid
+ * while the mesh lives.  Asynchronous: its device memory comes from the stream-ordered
  * allocator on `stream`, and the tables are complete once the work issued to
  * `stream` so far is (use the handle on `stream`, or after synchronising it).
  * q_background may be released once that work is complete. */
@@ -245,9 +248,11 @@ sd_status sd_rk_stage(const sd_mesh* mesh, const sd_phys* phys, sd_precision pre
  * dx_min = h_min (X_s,2 - X_s,1) the smallest solution-point spacing,
  * c_h = lambda_max when phys->c_h <= 0 (else phys->c_h), then the three fused
  * stages.  q (in/out) and work: device states; dt_out: device double[2] or NULL,
- * receives (dt, c_h).  SD_FP32_MIXED keeps no FP64 intermediate state: every
- * stage reads q and the background's FP32 register D = q^(s) - q^n, and only
- * the last stage writes q (work is then not written).  No host synchronisation.
+ * receives (dt, c_h).  SD_FP32_MIXED keeps no FP64 intermediate state: the
+ * lambda_max pass also stores q' = q^n - Q0 in FP32 in the background, every
+ * stage reads q' and the background's FP32 register D = q^(s) - q^n, and only
+ * the last stage reads and writes q (work is then not written).  No host
+ * synchronisation.
  * Asynchronous. */
 sd_status sd_step(const sd_mesh* mesh, const sd_phys* phys, sd_precision prec, double cfl, double* q, double* work,
                   const sd_background* bg, double* dt_out, void* stream);
@@ -287,7 +292,7 @@ sd_status sd_spherical_sums(const sd_mesh* mesh, const double* q, double r_min, 
 typedef struct {
   const sd_mesh* mesh;
   sd_phys phys;             /* c_h <= 0: c_h = lambda_max of the request each step */
-  const sd_background* bg;  /* required */
+  const sd_background* bg;  /* required, and not shared with another request of the call */
   double* q;                /* device state, advanced in place */
   double* work;             /* device state used inside the step */
   void* traces;             /* device scratch of sd_mesh_info.trace_bytes bytes, 16-byte aligned */

@@ -730,6 +730,7 @@ sd_status sd_background_create(const sd_mesh* m, const sd_phys* ph, const double
   bg->rec = nullptr;
   bg->jump = nullptr;
   bg->dreg = nullptr;
+  bg->qp = nullptr;
   bg->dstride = (N3 + 3) / 4 * 4;
   bg->device = m->device;
   double *q0 = nullptr, *R0 = nullptr;
@@ -737,7 +738,9 @@ sd_status sd_background_create(const sd_mesh* m, const sd_phys* ph, const double
   // stream-ordered allocations: building a background never waits for the device
   cudaError_t err = cudaMallocAsync((void**)&bg->rec, 5 * ne * N3 * sizeof(float), s);
   if (err == cudaSuccess) err = cudaMallocAsync((void**)&bg->jump, ne * 6 * 2 * N2 * sizeof(float), s);
-  if (err == cudaSuccess) err = cudaMallocAsync((void**)&bg->dreg, 9 * ne * bg->dstride * sizeof(float), s);
+  // D and q' of the mixed step: 18 planes of n_e * dstride floats
+  if (err == cudaSuccess) err = cudaMallocAsync((void**)&bg->dreg, 18 * ne * bg->dstride * sizeof(float), s);
+  if (err == cudaSuccess) bg->qp = bg->dreg + 9 * ne * bg->dstride;
   if (err == cudaSuccess) err = cudaMallocAsync((void**)&q0, state * sizeof(double), s);
   if (err == cudaSuccess) err = cudaMallocAsync((void**)&R0, state * sizeof(double), s);
   if (err == cudaSuccess) err = sd::launch_bg_prepare(m, ph->gamma, 1.0 / (ph->gamma - 1.0), q_bg, q0, bg->rec, s);
@@ -928,6 +931,10 @@ static sd_status advance_impl(sd_mesh* mm, const sd_phys* ph, sd_precision prec,
       P.tr_out = trace_buf(mm, prec, a);
       P.lam_max = reinterpret_cast<unsigned long long*>(mm->dyn + 4);
       P.lam_nslot = sd::LAM_SLOTS;
+      if (mixed) {  // and q' of q for the increment-form stages
+        P.qp_out = bg->qp;
+        P.dstride = bg->dstride;
+      }
       ProfScope ps(mm, PROF_TRACE, s);
       SD_CUDA(sd::launch_traces(mm, prec, P, s));
     }
@@ -950,6 +957,7 @@ static sd_status advance_impl(sd_mesh* mm, const sd_phys* ph, sd_precision prec,
       S.dstride = bg->dstride;
       S.lsr_write = 1;
       S.incr = 1;
+      S.qp_in = bg->qp;
     }
     SD_CUDA(prepare_viscous(mm, S, s));
     {
@@ -986,6 +994,7 @@ static sd_status advance_impl(sd_mesh* mm, const sd_phys* ph, sd_precision prec,
     if (mixed) {
       S.lsr_read = 1;
       S.lsr_write = 0;
+      S.qp_out = last ? nullptr : bg->qp;  // q' of the new q, for the next step
     }
     SD_CUDA(prepare_viscous(mm, S, s));
     {

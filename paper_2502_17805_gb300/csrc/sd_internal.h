@@ -76,6 +76,11 @@ struct StageParams {
   // increment form (FP32-mixed sd_step): q_in is q^n in every stage and the stage's
   // state is q^n + D; stages with lsr_write only advance D, the last writes q^n + D + t
   int incr;
+  // FP32 q' of q^n, [9][n_e * dstride], rounded from q^n as a load of it rounds
+  // it: read by the increment-form stages (qp_in) in place of q^n; written by a
+  // mixed trace pass and by an exact last stage (qp_out, for the new state)
+  const float* qp_in;
+  float* qp_out;
   int* err;  // device error word (bounded waits that ran out)
   // viscous, resistive and thermal fluxes (FP64 policy): coefficients, the gradients of
   // (U, T, S, B) at the solution points [e][24][N^3] (grad[3c + j] = d w_c / d x_j) and their
@@ -136,6 +141,7 @@ struct sd_background {
   float* rec;    // [5][n_e * N^3]
   float* jump;   // [n_e][6][2][N^2]
   float* dreg;   // [9][n_e * dstride]: FP32 difference register of the mixed sd_step
+  float* qp;     // [9][n_e * dstride]: FP32 q' of q^n (same allocation as dreg)
   int64_t dstride;
   double gamma;
   int device;

@@ -152,6 +152,13 @@ sd_status sd_step_packed(sd_packer* pk, int32_t n, const sd_step_req* reqs, void
     if (!(r.cfl > 0.0)) return pk_fail(SD_ERR_INVALID_ARGUMENT, where + "cfl must be positive");
     if (r.phys.viscous) return pk_fail(SD_ERR_UNSUPPORTED, where + "viscous fluxes run on the SD_FP64 path only");
   }
+  {  // the background holds the step's FP32 scratch: one request per background
+    std::vector<const sd_background*> bgs(n);
+    for (int i = 0; i < n; ++i) bgs[i] = reqs[i].bg;
+    std::sort(bgs.begin(), bgs.end());
+    if (std::adjacent_find(bgs.begin(), bgs.end()) != bgs.end())
+      return pk_fail(SD_ERR_INVALID_ARGUMENT, "two requests share a background");
+  }
   // group by order
   std::vector<int> order(n);
   for (int i = 0; i < n; ++i) order[i] = i;
@@ -220,6 +227,8 @@ sd_status sd_step_packed(sd_packer* pk, int32_t n, const sd_step_req* reqs, void
     Pt.tr_out = tr0;
     Pt.lam_max = pk->d_slots + (size_t)k * sd::PK_SLOTS;
     Pt.lam_nslot = sd::PK_SLOTS;
+    Pt.qp_out = r.bg->qp;  // q' of q for the stages
+    Pt.dstride = r.bg->dstride;
     T[0 * n + k] = Pt;
     // increment form (as sd_step): every stage reads q^n and the FP32 register D
     // carries the stage states.  Stage 0: D = t, traces tr0 -> tr1; stage 1: D += t,
@@ -244,6 +253,7 @@ sd_status sd_step_packed(sd_packer* pk, int32_t n, const sd_step_req* reqs, void
       Ps.lsr_read = s > 0 ? 1 : 0;
       Ps.lsr_write = s == 0 ? 1 : (s == 1 ? 2 : 0);
       Ps.incr = 1;
+      Ps.qp_in = r.bg->qp;
       T[(1 + s) * n + k] = Ps;
     }
     CTL[k] = {r.dyn, pk->d_slots + (size_t)k * sd::PK_SLOTS, r.cfl, m->h_min * (m->ops64.xs[1] - m->ops64.xs[0]),

@@ -133,10 +133,15 @@ __device__ __forceinline__ void load_element(const StageParams& P, const double*
 #pragma unroll
       for (int v = 0; v < 9; ++v) qf[v] = f64_to_f32(qv[v]);
       if (lam_out) lamf = speed_max(lamf, point_speed_mixed(qf, (float)P.gamma));
+      qf[0] = f64_to_f32(qv[0] - f32_to_f64(r0));
+      qf[4] = f64_to_f32(fma(-f32_to_f64(p0), P.inv_gm1, qv[4]));
 #pragma unroll
       for (int v = 0; v < 9; ++v) sQ[v * N3 + n] = qf[v];
-      sQ[0 * N3 + n] = f64_to_f32(qv[0] - f32_to_f64(r0));
-      sQ[4 * N3 + n] = f64_to_f32(fma(-f32_to_f64(p0), P.inv_gm1, qv[4]));
+      if (P.qp_out) {
+        const int64_t qplane = P.n_e * P.dstride;
+#pragma unroll
+        for (int v = 0; v < 9; ++v) P.qp_out[v * qplane + e * P.dstride + n] = qf[v];
+      }
       sQ[9 * N3 + n] = r0;
       sQ[10 * N3 + n] = p0;
     }

@@ -108,12 +108,25 @@ __device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops<fl
   // difference register D of the low-storage RK form (mbarrier dbar; read by the
   // epilogue, and by phase A in the increment form) and, with STAGE_G, 1/|J|, x
   // and R0 for the epilogue (mbarrier gbar).
-  __shared__ __align__(8) unsigned long long dbar, gbar;
+  // In the increment form the stage state q^n + D starts from the stored FP32 q'
+  // of q^n (P.qp_in): with STAGE_G it is copied, with rho0 and p0, straight into
+  // sQ by TMA as well (mbarrier qbar).
+  __shared__ __align__(8) unsigned long long dbar, gbar, qbar;
   float* sDs = smem + DV::oDs;
   float* sG = smem + DV::oG;
   const bool lsr = P.lsr_read != 0;
+  constexpr bool qtma = INCR && DV::STAGE_G;
   if (tid == 0) {
     constexpr unsigned plane_bytes = DV::DSTRIDE * 4, blk = N3 * 4;
+    if constexpr (qtma) {
+      mbar_init(&qbar, 1);
+      mbar_expect_tx(&qbar, 11 * blk);
+      const int64_t qplane = P.n_e * DV::DSTRIDE;
+#pragma unroll 1
+      for (int v = 0; v < 9; ++v) tma_load_1d(sQ + v * N3, P.qp_in + v * qplane + e * DV::DSTRIDE, blk, &qbar);
+      tma_load_1d(sQ + 9 * N3, P.bg + e * N3, blk, &qbar);
+      tma_load_1d(sQ + 10 * N3, P.bg + P.n_e * N3 + e * N3, blk, &qbar);
+    }
     if (lsr) {
       mbar_init(&dbar, 1);
       mbar_expect_tx(&dbar, 9 * plane_bytes);
@@ -131,9 +144,9 @@ __device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops<fl
       for (int c = 0; c < 3; ++c) tma_load_1d(sG + (4 + c) * N3, P.bg + (2 + c) * P.n_e * N3 + e * N3, blk, &gbar);
     }
   }
-  // increment form: the stage's state is q_in + D, so phase A needs D (waited for
-  // after the state loads are issued)
-  if (incr && lsr) __syncthreads();  // dbar initialised before anyone polls it
+  // increment form: the stage's state is q' + D, so phase A needs D (and, with
+  // qtma, the copied q')
+  if (incr && (lsr || qtma)) __syncthreads();  // barriers initialised before anyone polls them
 
   // line role of this thread (B, D, F): G threads per line, thread g of a line
   // takes the variables g, g + G, ...
@@ -148,7 +161,46 @@ __device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops<fl
 
   // ---- A: load (every round's loads issued before the first conversion)
   const double inv_gm1 = P.inv_gm1;
-  {
+  if constexpr (qtma) {
+    // q', rho0, p0 are in sQ once qbar completes; add D
+    mbar_wait_bounded(&qbar, 0u, P.err);
+    if (lsr) {
+      mbar_wait_bounded(&dbar, 0u, P.err);
+      for (int n = tid; n < N3; n += T) {
+#pragma unroll
+        for (int v = 0; v < 9; ++v) sQ[v * N3 + n] += sDs[v * DV::DSTRIDE + n];
+      }
+    }
+  } else if constexpr (INCR) {
+    // stored q' (element blocks not 16-byte aligned: plain loads)
+    constexpr int NRA = (N3 + T - 1) / T;
+    float qv[NRA][11];
+    const int64_t qplane = n_e * DV::DSTRIDE;
+#pragma unroll
+    for (int r = 0; r < NRA; ++r) {
+      const int n = tid + r * T;
+      if (n < N3) {
+        const int64_t gb = e * N3 + n;
+#pragma unroll
+        for (int v = 0; v < 9; ++v) qv[r][v] = __ldg(P.qp_in + v * qplane + e * DV::DSTRIDE + n);
+        qv[r][9] = __ldg(P.bg + gb);
+        qv[r][10] = __ldg(P.bg + n_e * N3 + gb);
+      }
+    }
+    if (lsr) mbar_wait_bounded(&dbar, 0u, P.err);
+#pragma unroll
+    for (int r = 0; r < NRA; ++r) {
+      const int n = tid + r * T;
+      if (n < N3) {
+        if (lsr) {
+#pragma unroll
+          for (int v = 0; v < 9; ++v) qv[r][v] += sDs[v * DV::DSTRIDE + n];
+        }
+#pragma unroll
+        for (int v = 0; v < 11; ++v) sQ[v * N3 + n] = qv[r][v];
+      }
+    }
+  } else {
     constexpr int NRA = (N3 + T - 1) / T;
     double qv[NRA][9];
     float r0[NRA], p0[NRA];
@@ -163,7 +215,6 @@ __device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops<fl
         for (int v = 0; v < 9; ++v) qv[r][v] = __ldg(P.q_in + v * plane + g);
       }
     }
-    if (incr && lsr) mbar_wait_bounded(&dbar, 0u, P.err);
 #pragma unroll
     for (int r = 0; r < NRA; ++r) {
       const int n = tid + r * T;
@@ -173,10 +224,6 @@ __device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops<fl
 #pragma unroll
         for (int v = 1; v < 9; ++v) qp[v] = f64_to_f32(qv[r][v]);
         qp[4] = f64_to_f32(fma(-f32_to_f64(p0[r]), inv_gm1, qv[r][4]));
-        if (incr && lsr) {
-#pragma unroll
-          for (int v = 0; v < 9; ++v) qp[v] += sDs[v * DV::DSTRIDE + n];
-        }
 #pragma unroll
         for (int v = 0; v < 9; ++v) sQ[v * N3 + n] = qp[v];
         sQ[9 * N3 + n] = r0[r];
@@ -360,8 +407,14 @@ __device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops<fl
         } else {
           const double qo = __ldg(P.q_in + v * plane + g) + f32_to_f64(Dv + t);
           P.out[v * plane + g] = qo;
-          if (exact) qe[v] = f64_to_f32(qo);
-          sQ[v * N3 + n] = exact ? new_qprime(v, qo, qe[v], q[9], q[10], inv_gm1) : q[v] + t;
+          if (exact) {
+            qe[v] = f64_to_f32(qo);
+            const float qpn = new_qprime(v, qo, qe[v], q[9], q[10], inv_gm1);
+            sQ[v * N3 + n] = qpn;
+            if (P.qp_out) P.qp_out[v * dplane + gd] = qpn;  // q' of the new state for the next step
+          } else {
+            sQ[v * N3 + n] = q[v] + t;
+          }
         }
       }
       if (exact) lam = speed_max(lam, point_speed_mixed(qe, gamma));

@@ -108,9 +108,10 @@ class _Running:
 
 def footprint_bytes(info: dict, n_pts: int) -> int:
     """Device bytes a running request holds, counting the transient of building its background
-    (one more state and an FP64 residual)."""
+    (one more state and an FP64 residual).  The background holds rho0, p0, R0 (5 FP32 values per
+    point), the face jumps and the step's FP32 scratch D and q' (18 values per point)."""
     state = info["state_bytes"]
-    bg = 5 * n_pts * 4 + info["n_elements"] * 6 * 2 * info["order"] ** 2 * 4
+    bg = (5 + 18) * n_pts * 4 + info["n_elements"] * 6 * 2 * info["order"] ** 2 * 4
     return 4 * state + info["trace_bytes"] + bg + 64
 
 

@@ -119,3 +119,18 @@ def test_packed_step_matches_the_oracle(torch_dev):
     lam = om.diagnostics(oph, q_before)["lambda_max"]
     xs = sdref.nodes(req.N)[0]
     assert abs(dt / (req.cfl * om.info()["h_min"] * (xs[1] - xs[0]) / lam) - 1.0) < 1e-6
+
+
+@gpu
+def test_requests_may_not_share_a_background(torch_dev):
+    """The background holds the step's FP32 scratch (D and q'), so a pack with two requests on one
+    background is refused before any launch."""
+    from paper_2502_17805_gb300 import sdmhd
+    srv = serve.Server(hbm_budget_bytes=1 << 34, max_running=4)
+    req = serve.Request(rid=0, nz=2, nr=1, N=4, n_rho=2.0, omega=1.0, seed=5, steps=1, arrival=0.0)
+    run = serve._Running(req, srv.mesh(req.nz, req.nr, req.N))
+    other = serve._Running(req, srv.mesh(req.nz, req.nr, req.N))
+    a, b = run.as_packed(), list(other.as_packed())
+    b[2] = a[2]  # other's states, run's background
+    with pytest.raises(sdmhd.SDError, match="share a background"):
+        srv.packer.step([a, tuple(b)])
