@@ -139,6 +139,19 @@ void build_ops(int N, sd::Ops<double>& o) {
     for (int i = 0; i < N; ++i) o.E[f * N + i] = lagr(o.xs, N, i, o.xf[f]);
   for (int i = 0; i < N; ++i)
     for (int f = 0; f <= N; ++f) o.D[i * (N + 1) + f] = lagr_d(o.xf, N + 1, f, o.xs[i]);
+  // even-odd split: solution indices i <= N-1-i, flux indices f <= N-f
+  for (int f = 0; 2 * f <= N; ++f)
+    for (int i = 0; 2 * i <= N - 1; ++i) {
+      const double a = o.E[f * N + i], b = o.E[f * N + N - 1 - i];
+      o.Es[f * N + i] = (2 * i == N - 1) ? a : 0.5 * (a + b);
+      o.Ed[f * N + i] = (2 * i == N - 1) ? 0.0 : 0.5 * (a - b);
+    }
+  for (int i = 0; 2 * i <= N - 1; ++i)
+    for (int f = 0; 2 * f <= N; ++f) {
+      const double a = o.D[i * (N + 1) + f], b = o.D[i * (N + 1) + N - f];
+      o.Ds[i * (N + 1) + f] = (2 * f == N) ? a : 0.5 * (a + b);
+      o.Dd[i * (N + 1) + f] = (2 * f == N) ? 0.0 : 0.5 * (a - b);
+    }
   std::vector<double> g, gw;
   gauss_legendre(N + 3, g, gw);
   for (int i = 0; i < N; ++i) {
@@ -152,6 +165,10 @@ void ops_to_f32(const sd::Ops<double>& a, sd::Ops<float>& b) {
   for (int i = 0; i < (sd::kMaxN + 1) * sd::kMaxN; ++i) {
     b.E[i] = (float)a.E[i];
     b.D[i] = (float)a.D[i];
+    b.Es[i] = (float)a.Es[i];
+    b.Ed[i] = (float)a.Ed[i];
+    b.Ds[i] = (float)a.Ds[i];
+    b.Dd[i] = (float)a.Dd[i];
   }
   for (int i = 0; i < sd::kMaxN; ++i) {
     b.w[i] = (float)a.w[i];

@@ -21,6 +21,15 @@ template <typename R>
 struct Ops {
   R E[(kMaxN + 1) * kMaxN];
   R D[kMaxN * (kMaxN + 1)];
+  // Even-odd split of E and D.  Solution and flux points are symmetric about
+  // 1/2, so E[N-f][N-1-i] = E[f][i] and D[N-1-i][f] = -D[i][N-f].  For f <= N/2,
+  // i <= (N-1)/2: Es[f N + i] = (E[f][i] + E[f][N-1-i]) / 2, Ed = the half
+  // difference (the middle solution point: Es = E, Ed = 0); Ds[i (N+1) + f] and
+  // Dd alike over the flux-point pairs (f, N-f) (the middle flux point: Ds = D).
+  R Es[(kMaxN + 1) * kMaxN];
+  R Ed[(kMaxN + 1) * kMaxN];
+  R Ds[kMaxN * (kMaxN + 1)];
+  R Dd[kMaxN * (kMaxN + 1)];
   R w[kMaxN];
   R xs[kMaxN];
   R xf[kMaxN + 1];

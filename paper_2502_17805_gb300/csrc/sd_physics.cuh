@@ -276,6 +276,16 @@ __device__ __forceinline__ void tma_load_1d(void* dst, const void* src, unsigned
                : "memory");
 }
 
+// Hint to fetch global memory [p, p + bytes) into L2 (cp.async.bulk.prefetch).
+// The range is first shrunk to the 16-byte boundaries inside it, so nothing
+// outside it is touched.
+__device__ __forceinline__ void l2_prefetch(const void* p, size_t bytes) {
+  const unsigned long long a = reinterpret_cast<unsigned long long>(p);
+  const unsigned long long lo = (a + 15ull) & ~15ull, hi = (a + bytes) & ~15ull;
+  if (hi > lo)
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(lo), "r"((unsigned)(hi - lo)) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned phase) {
   unsigned ok;
   asm volatile(

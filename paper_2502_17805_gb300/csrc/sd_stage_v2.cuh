@@ -86,22 +86,29 @@ __device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops<fl
   float* sX = smem + DV::oX;
   const int tid = threadIdx.x;
   const float* Sfam = reinterpret_cast<const float*>(P.Sfam) + e * (9 * N2 * NF);
-  const float gamma = (float)P.gamma;
-  const float gm1 = gamma - 1.0f;
-  const float gg1 = gamma / gm1;
-  double dt = P.dt, chd = P.c_h;
-  if (P.dyn) {
-    dt = P.dyn[0];
-    chd = P.dyn[1];
+  // FP32 copies of the uniform FP64 parameters, converted once per CTA by thread 0
+  // (the FP64 pipe of an SM is narrow: per-thread conversions cost more than the
+  // point work of some phases) and read after the first barrier
+  __shared__ float sConst[9];
+  if (tid == 0) {
+    double dt = P.dt, chd = P.c_h;
+    if (P.dyn) {
+      dt = P.dyn[0];
+      chd = P.dyn[1];
+    }
+    const float g = (float)P.gamma;
+    sConst[0] = g;
+    sConst[1] = g - 1.0f;
+    sConst[2] = g / (g - 1.0f);
+    sConst[3] = (float)chd;
+    sConst[4] = (float)(P.rk_b * dt);
+    sConst[5] = (float)P.rk_a;
+    sConst[6] = (float)P.GM;
+    sConst[7] = 2.0f * (float)P.omega;
+    sConst[8] = (float)P.alpha;
   }
-  const float ch = (float)chd;
-  // uniform values of the epilogue, converted once
-  const MixedConsts MC = mixed_consts(P);
-  const float bdt = (float)(P.rk_b * dt);
-  const float rka = (float)P.rk_a;
   const int mode = P.mode, lsr_read = P.lsr_read, lsr_write = P.lsr_write;
   constexpr bool incr = INCR;
-  const bool classic_qn = P.rk_a != 0.0;
   const int64_t n_e = P.n_e, stride = P.stride, plane = P.plane;
 
   // Per-element inputs copied to shared memory by TMA at kernel start: the
@@ -144,6 +151,28 @@ __device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops<fl
       for (int c = 0; c < 3; ++c) tma_load_1d(sG + (4 + c) * N3, P.bg + (2 + c) * P.n_e * N3 + e * N3, blk, &gbar);
     }
   }
+  // L2 prefetch, at kernel start, of what the element reads from global memory
+  // later: the neighbours' face traces, S^d and the background jumps (phase C)
+  // and, in the last stage of the increment form, q^n (epilogue).  One thread of
+  // the second warp per block, so that the TMA issue above is not delayed.
+  if (tid >= 32 && tid < 32 + 17) {
+    const int k = tid - 32;
+    if (k < 6) {
+      const int nb = __ldg(P.nbr + e * 6 + k);
+      if (nb >= 0 && P.tr_in) {
+        const int mt = __ldg(P.meta + e * 6 + k);
+        l2_prefetch(reinterpret_cast<const float*>(P.tr_in) + ((int64_t)nb * 6 + meta_nbF(mt)) * 9 * N2,
+                    9 * N2 * sizeof(float));
+      }
+    } else if (k == 6) {
+      l2_prefetch(Sfam, 9 * N2 * NF * sizeof(float));
+    } else if (k == 7) {
+      if (P.bg_jump) l2_prefetch(P.bg_jump + e * 6 * 2 * N2, 6 * 2 * N2 * sizeof(float));
+    } else if (INCR && mode == MODE_RK && lsr_write == 0) {
+      l2_prefetch(P.q_in + (k - 8) * plane + e * stride, N3 * sizeof(double));
+    }
+  }
+
   // increment form: the stage's state is q' + D, so phase A needs D (and, with
   // qtma, the copied q')
   if (incr && (lsr || qtma)) __syncthreads();  // barriers initialised before anyone polls them
@@ -232,6 +261,10 @@ __device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops<fl
     }
   }
   __syncthreads();
+  const float gamma = sConst[0], gm1 = sConst[1], gg1 = sConst[2], ch = sConst[3];
+  const float bdt = sConst[4], rka = sConst[5];
+  const bool classic_qn = rka != 0.0f;
+  const MixedConsts MC{sConst[6], sConst[7], sConst[8], P.gravity, P.coriolis, P.powell};
 
   // ---- B: extrapolate every line to its N+1 flux points (one variable at a time:
   //      N values in registers, N+1 outputs)
@@ -242,12 +275,30 @@ __device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops<fl
       float ql[N];
 #pragma unroll
       for (int i = 0; i < N; ++i) ql[i] = sQ[v * N3 + lbase + i * lstride];
+      // even-odd form: the pair (f, N-f) of outputs from the sums and differences
+      // of the pairs (i, N-1-i) of inputs (operators from the parameter bank)
+      constexpr int HP = N / 2;
+      float sv[HP], dv[HP];
 #pragma unroll
-      for (int f = 0; f <= N; ++f) {
-        float s = 0.0f;
+      for (int i = 0; i < HP; ++i) {
+        sv[i] = ql[i] + ql[N - 1 - i];
+        dv[i] = ql[i] - ql[N - 1 - i];
+      }
 #pragma unroll
-        for (int i = 0; i < N; ++i) s = fmaf(ops.E[f * N + i], ql[i], s);  // operator from the parameter bank
-        X[(f * 11 + v) * N2] = s;
+      for (int f = 0; 2 * f <= N; ++f) {
+        float a = (N & 1) ? ops.Es[f * N + HP] * ql[HP] : 0.0f;
+        float b = 0.0f;
+#pragma unroll
+        for (int i = 0; i < HP; ++i) {
+          a = fmaf(ops.Es[f * N + i], sv[i], a);
+          b = fmaf(ops.Ed[f * N + i], dv[i], b);
+        }
+        if (2 * f == N) {
+          X[(f * 11 + v) * N2] = a;
+        } else {
+          X[(f * 11 + v) * N2] = a + b;
+          X[((N - f) * 11 + v) * N2] = a - b;
+        }
       }
     }
   }
@@ -333,12 +384,30 @@ __device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops<fl
       float fv[NF];
 #pragma unroll
       for (int f = 0; f <= N; ++f) fv[f] = X[(f * 11 + v) * N2];
+      // even-odd form: D[N-1-i][f] = -D[i][N-f] gives the pair (i, N-1-i) from the
+      // sums and differences of the flux pairs (f, N-f)
+      constexpr int HF = NF / 2;
+      float sf[HF], df[HF];
 #pragma unroll
-      for (int i = 0; i < N; ++i) {
-        float s = 0.0f;
+      for (int f = 0; f < HF; ++f) {
+        sf[f] = fv[f] + fv[N - f];
+        df[f] = fv[f] - fv[N - f];
+      }
 #pragma unroll
-        for (int f = 0; f <= N; ++f) s = fmaf(ops.D[i * NF + f], fv[f], s);
-        X[(i * 11 + v) * N2] = s;
+      for (int i = 0; 2 * i <= N - 1; ++i) {
+        float p = (NF & 1) ? ops.Ds[i * NF + HF] * fv[HF] : 0.0f;
+        float r = 0.0f;
+#pragma unroll
+        for (int f = 0; f < HF; ++f) {
+          p = fmaf(ops.Ds[i * NF + f], sf[f], p);
+          r = fmaf(ops.Dd[i * NF + f], df[f], r);
+        }
+        if (2 * i == N - 1) {
+          X[(i * 11 + v) * N2] = r;
+        } else {
+          X[(i * 11 + v) * N2] = p + r;
+          X[((N - 1 - i) * 11 + v) * N2] = r - p;
+        }
       }
     }
   }
