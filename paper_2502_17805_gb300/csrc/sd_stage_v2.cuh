@@ -155,12 +155,15 @@ __device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops<fl
   // later: the neighbours' face traces, S^d and the background jumps (phase C)
   // and, in the last stage of the increment form, q^n (epilogue).  One thread of
   // the second warp per block, so that the TMA issue above is not delayed.
+  __shared__ int sNb[6], sMt[6];
   if (tid >= 32 && tid < 32 + 17) {
     const int k = tid - 32;
     if (k < 6) {
       const int nb = __ldg(P.nbr + e * 6 + k);
+      const int mt = __ldg(P.meta + e * 6 + k);
+      sNb[k] = nb;
+      sMt[k] = mt;
       if (nb >= 0 && P.tr_in) {
-        const int mt = __ldg(P.meta + e * 6 + k);
         l2_prefetch(reinterpret_cast<const float*>(P.tr_in) + ((int64_t)nb * 6 + meta_nbF(mt)) * 9 * N2,
                     9 * N2 * sizeof(float));
       }
@@ -339,8 +342,8 @@ __device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops<fl
       const float sg = side ? 1.0f : -1.0f;
       const float nx = sg * Sx * im, ny = sg * Sy * im, nz = sg * Sz * im;
       const int64_t gidx = e * 6 + F;
-      const int nb = __ldg(P.nbr + gidx);
-      const int mt = __ldg(P.meta + gidx);
+      const int nb = sNb[F];
+      const int mt = sMt[F];
       float qn[9];
       float jr = 0.0f, jp = 0.0f;
       if (nb >= 0) {
