@@ -58,8 +58,13 @@
  *     sides, whose normal velocity vanishes), so the wall does no viscous work.
  *  W2 the heat flux through the inner sphere is the prescribed q_bottom (the paper's L / (4 pi r_b^2));
  *     the outer sphere holds T = T_top as the common (BR1) value of T in the gradients and conducts
- *     with this side's gradients.  The paper's magnetic derivative conditions are not modelled: the
- *     resistive wall terms are this side's.
+ *     with this side's gradients.
+ *  W3 magnetic wall conditions (same section): a perfectly conducting wall has J = J_r r^, so the
+ *     resistive wall terms take only the normal part (J.n) n of this side's current, and both
+ *     eta J x n and eta (B x J).n vanish there.  The derivative conditions the paper derives from it,
+ *     B_r = d(r B_theta)/dr = d(r B_phi)/dr = 0, are what J = J_r r^ means for the field.  A radial-
+ *     field wall holds B_theta = B_phi = 0 through the common (ghost-averaged) face state; its
+ *     d(r^2 B_r)/dr = 0 constrains only dB_r/dr, which does not enter the curl J, so it changes no flux.
  *  F1 flux-balanced initial profile (Sec. Initial Conditions): the printed density equation has
  *     exp(+gamma S / C_p); hydrostatic balance dp/dr = -rho g with S = C_p ln(p^(1/gamma) / rho)
  *     requires exp(-gamma S / C_p), which is used (with it the isentropic case is the polytrope).
@@ -838,11 +843,12 @@ static void grad_face_value(const sdref_mesh* m, const double* G, int64_t e, int
   }
 }
 
-/* viscous flux through a wall face along its unit outward normal n (readings W1, W2): stress-free
+/* viscous flux through a wall face along its unit outward normal n (readings W1-W3): stress-free
  * and impenetrable, only the normal viscous stress n.tau.n acts, on the face state (the average of
  * this side and its wall ghost, whose normal velocity vanishes); the heat flux is q_bottom into the
  * shell on the inner sphere and the conducted one (this side's gradients) on the outer; the
- * resistive terms are this side's */
+ * resistive terms take this side's current, of which a perfectly conducting wall keeps only the
+ * normal part */
 static void wall_visc(const sdref_mesh* m, const sdref_phys* ph, int64_t e, int F, const double* Qown,
                       const double* g, const double* n, double* F_, double* fm) {
   int64_t k = 6 * e + F;
@@ -856,6 +862,10 @@ static void wall_visc(const sdref_mesh* m, const sdref_phys* ph, int64_t e, int 
     for (int j = 0; j < 3; ++j)
       tnn += n[i] * (ph->mu * (g[i * 3 + j] + g[j * 3 + i]) + (i == j ? -2.0 / 3.0 * ph->mu * divu : 0.0)) * n[j];
   double J[3] = {g[7 * 3 + 1] - g[6 * 3 + 2], g[5 * 3 + 2] - g[7 * 3 + 0], g[6 * 3 + 0] - g[5 * 3 + 1]};
+  if (m->bc[k] == SDREF_BC_WALL_CONDUCTING) { /* W3: J = (J.n) n */
+    double jn = J[0] * n[0] + J[1] * n[1] + J[2] * n[2];
+    for (int i = 0; i < 3; ++i) J[i] = jn * n[i];
+  }
   double BxJ[3], Jxn[3];
   cross3(w + 5, J, BxJ);
   cross3(J, n, Jxn);

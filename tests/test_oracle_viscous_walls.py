@@ -109,3 +109,47 @@ def test_stress_free_walls_exert_no_torque(oracle):
         d = _dR(oracle, m, q, mu=mu, visc_walls=walls, T_top=1.0)
         torque = (W * (x * d[2] - y * d[1])).sum()
         assert abs(torque - want) < 2e-3 * exact, (walls, torque, want)
+
+
+def _mhd_state(X):
+    """rho = 1, U = 0, p = 1 and a smooth field with tangential components and current at both walls"""
+    x, y, z = X[..., 0], X[..., 1], X[..., 2]
+    B = [0.2 * z - 0.3 * y, 0.3 * x + 0.1 * z * z, 0.2 * x * y]
+    q = np.zeros((9,) + x.shape)
+    q[0] = 1.0
+    for d in range(3):
+        q[5 + d] = B[d]
+    q[4] = 1.0 / (GAMMA - 1.0) + 0.5 * (B[0] ** 2 + B[1] ** 2 + B[2] ** 2)
+    return q
+
+
+def _resistive_integrals(oracle, bc_in, bc_out, walls):
+    v, h = inputs.shell_mesh(6, 4)
+    m = oracle.Mesh(5, v, h, geom=1, r_in=RB, r_out=RT, bc_in=bc_in, bc_out=bc_out)
+    X = _points(m)
+    q = _mhd_state(X)
+    W = _weights(oracle, m)
+    d = _dR(oracle, m, q, eta=0.02, visc_walls=walls, q_bottom=0.0, T_top=1.0)
+    return np.array([(W * d[v]).sum() for v in (4, 5, 6, 7)])
+
+
+def test_conducting_walls_pass_no_resistive_flux(oracle):
+    """A perfectly conducting wall has J = J_r r^ (Sec. Problem Formulation): neither the resistive
+    induction flux eta J x n nor the resistive energy flux eta (B x J).n passes it, so with both walls
+    conducting the shell integrals of the resistive residual of E and B vanish (the interior fluxes
+    cancel between elements).  A wall that passes its own tangential current lets them through."""
+    cond = oracle.BC_WALL_CONDUCTING
+    own = _resistive_integrals(oracle, cond, cond, 0)
+    scale = np.abs(own).max()
+    assert scale > 1e-4, own
+    held = _resistive_integrals(oracle, cond, cond, 1)
+    assert np.abs(held).max() < 1e-12 * scale, (held, own)
+
+
+def test_radial_field_walls_carry_surface_current(oracle):
+    """A radial-field wall holds B_theta = B_phi = 0 on its face: it passes no resistive energy
+    (B x J is tangential to the wall) but a surface current, i.e. resistive induction flux."""
+    rad = oracle.BC_WALL_RADIAL
+    held = _resistive_integrals(oracle, rad, rad, 1)
+    assert abs(held[0]) < 1e-12 * np.abs(held[1:]).max(), held
+    assert np.abs(held[1:]).max() > 1e-4, held
