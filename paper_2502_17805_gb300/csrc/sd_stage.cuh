@@ -404,7 +404,8 @@ __global__ void __launch_bounds__(Dims<N>::BLK) stage_kernel(const StageParams P
       double g[NGRAD], Fv[9];
       grad_face<N>(sG, sE, F, a, b, g);
       if (nb < 0 && P.visc_walls)
-        wall_visc_flux(qo, qn, g, nx, ny, nz, meta_outer(mt) != 0, P.q_bottom, vc, Fv);
+        wall_visc_flux(qo, qn, g, nx, ny, nz, meta_outer(mt) != 0, meta_bc(mt) == SD_BC_WALL_CONDUCTING, P.q_bottom,
+                       vc, Fv);
       else
         visc_flux(qo, g, nx, ny, nz, vc, Fv);
       if (nb >= 0) {

@@ -103,9 +103,10 @@ __device__ __forceinline__ void visc_flux(const double* Q, const double* g, doub
 // stress-free and impenetrable, only the normal stress n.tau.n acts, on the face
 // state qf = (own + ghost) / 2 (whose normal velocity vanishes); the heat flux is
 // q_bottom into the shell on the inner sphere (q = q_bottom r^, n = -r^) and the
-// conducted one on the outer; the resistive terms are this side's.
+// conducted one on the outer; the resistive terms take this side's current, of
+// which a perfectly conducting wall keeps only the normal part (J = J_r r^).
 __device__ __forceinline__ void wall_visc_flux(const double* qo, const double* qn, const double* g, double nx,
-                                               double ny, double nz, bool outer, double q_bottom,
+                                               double ny, double nz, bool outer, bool conducting, double q_bottom,
                                                const ViscCoef& c, double* F) {
   double qf[9], w[8];
 #pragma unroll
@@ -119,7 +120,13 @@ __device__ __forceinline__ void wall_visc_flux(const double* qo, const double* q
 #pragma unroll
     for (int j = 0; j < 3; ++j)
       tnn += n[i] * (c.mu * (g[3 * i + j] + g[3 * j + i]) + (i == j ? c.lam * divu : 0.0)) * n[j];
-  const double Jx = g[3 * 7 + 1] - g[3 * 6 + 2], Jy = g[3 * 5 + 2] - g[3 * 7 + 0], Jz = g[3 * 6 + 0] - g[3 * 5 + 1];
+  double Jx = g[3 * 7 + 1] - g[3 * 6 + 2], Jy = g[3 * 5 + 2] - g[3 * 7 + 0], Jz = g[3 * 6 + 0] - g[3 * 5 + 1];
+  if (conducting) {  // a perfectly conducting wall: J = J_r r^, the normal part only
+    const double jn = Jx * nx + Jy * ny + Jz * nz;
+    Jx = jn * nx;
+    Jy = jn * ny;
+    Jz = jn * nz;
+  }
   const double Bx = w[5], By = w[6], Bz = w[7];
   const double bj = c.eta * ((By * Jz - Bz * Jy) * nx + (Bz * Jx - Bx * Jz) * ny + (Bx * Jy - By * Jx) * nz);
   double qdn;
