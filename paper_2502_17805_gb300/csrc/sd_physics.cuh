@@ -121,29 +121,6 @@ __device__ __forceinline__ void flux_pert(const float* q, float nx, float ny, fl
   F[8] = ch * Bn;
 }
 
-// |U.n| + fast magnetosonic speed along the unit normal n.
-template <typename R>
-__device__ __forceinline__ R wave_speed(R rho, R mx, R my, R mz, R p, R Bx, R By, R Bz, R nx, R ny, R nz, R gamma) {
-  const R ir = rcp_(rho);
-  const R a2 = gamma * p * ir;
-  const R b2 = (Bx * Bx + By * By + Bz * Bz) * ir;
-  const R Bn = Bx * nx + By * ny + Bz * nz;
-  const R bn2 = Bn * Bn * ir;
-  const R s = a2 + b2;
-  R disc = s * s - R(4) * a2 * bn2;
-  disc = disc > R(0) ? disc : R(0);
-  const R cf = sqrt(R(0.5) * (s + sqrt(disc)));
-  const R un = (mx * nx + my * ny + mz * nz) * ir;
-  return fabs(un) + cf;
-}
-
-template <typename R>
-__device__ __forceinline__ R pressure_full(const R* q, R gm1) {
-  const R ir = rcp_(q[0]);
-  return gm1 * (q[4] - R(0.5) * ((q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) * ir + q[5] * q[5] + q[6] * q[6] +
-                                  q[7] * q[7] + q[8] * q[8]));
-}
-
 // Wall ghost state: rho, p and E copied, U reflected.  Conducting walls reflect
 // B (B_n = 0) and copy psi; radial walls reverse the tangential part of B and
 // leave B_n free, so the GLM pair (B_n, psi) takes its one wall condition on
@@ -171,6 +148,41 @@ __device__ __forceinline__ void wall_ghost(const R* q, R nx, R ny, R nz, int bc,
   }
 }
 
+// One side of the FP64 Rusanov flux: the flux of q along the unit normal n and,
+// with `speed`, |U.n| + c_f (else 0); 1/rho, the velocity, |B|^2, B.n and p
+// serve both.
+__device__ __forceinline__ double side_fp64(const double* q, double nx, double ny, double nz, double gamma,
+                                            double gm1, double ch, bool speed, double* F) {
+  const double ir = 1.0 / q[0];
+  const double ux = q[1] * ir, uy = q[2] * ir, uz = q[3] * ir;
+  const double Bx = q[5], By = q[6], Bz = q[7], psi = q[8];
+  const double B2 = Bx * Bx + By * By + Bz * Bz;
+  const double mu = q[1] * ux + q[2] * uy + q[3] * uz;
+  const double p = gm1 * (q[4] - 0.5 * (mu + B2 + psi * psi));
+  const double e = q[4] - 0.5 * psi * psi;
+  const double un = ux * nx + uy * ny + uz * nz;
+  const double Bn = Bx * nx + By * ny + Bz * nz;
+  const double uB = ux * Bx + uy * By + uz * Bz;
+  const double pt = p + 0.5 * B2;
+  const double chpsi = ch * psi;
+  F[0] = q[0] * un;
+  F[1] = q[1] * un + pt * nx - Bx * Bn;
+  F[2] = q[2] * un + pt * ny - By * Bn;
+  F[3] = q[3] * un + pt * nz - Bz * Bn;
+  F[4] = un * (e + pt) - Bn * uB + chpsi * Bn;
+  F[5] = un * Bx - Bn * ux + chpsi * nx;
+  F[6] = un * By - Bn * uy + chpsi * ny;
+  F[7] = un * Bz - Bn * uz + chpsi * nz;
+  F[8] = ch * Bn;
+  if (!speed) return 0.0;
+  const double a2 = gamma * p * ir;
+  const double b2 = B2 * ir;
+  const double s = a2 + b2;
+  double disc = s * s - 4.0 * a2 * (Bn * Bn * ir);
+  disc = disc > 0.0 ? disc : 0.0;
+  return fabs(un) + sqrt(0.5 * (s + sqrt(disc)));
+}
+
 // Rusanov common flux along the unit outward normal n of this side:
 //   F* = (F(qo) + F(qn))/2 - lambda/2 (qn - qo),  lambda = max(|u_n|+c_f both sides, c_h).
 // The same instruction sequence runs on both sides of a face with n negated and
@@ -179,17 +191,13 @@ __device__ __forceinline__ void riemann_fp64(const double* qo, const double* qn,
                                              double gamma, double ch, int central, double* Fs) {
   const double gm1 = gamma - 1.0;
   double FL[9], FR[9];
-  flux_full<double>(qo, nx, ny, nz, gm1, ch, FL);
-  flux_full<double>(qn, nx, ny, nz, gm1, ch, FR);
+  const double lo = side_fp64(qo, nx, ny, nz, gamma, gm1, ch, !central, FL);
+  const double ln = side_fp64(qn, nx, ny, nz, gamma, gm1, ch, !central, FR);
   if (central) {
 #pragma unroll
     for (int v = 0; v < 9; ++v) Fs[v] = 0.5 * (FL[v] + FR[v]);
     return;
   }
-  const double lo = wave_speed<double>(qo[0], qo[1], qo[2], qo[3], pressure_full<double>(qo, gm1), qo[5], qo[6],
-                                       qo[7], nx, ny, nz, gamma);
-  const double ln = wave_speed<double>(qn[0], qn[1], qn[2], qn[3], pressure_full<double>(qn, gm1), qn[5], qn[6],
-                                       qn[7], nx, ny, nz, gamma);
   double lam = fmax(lo, ln);
   lam = fmax(lam, ch);
   const double hl = 0.5 * lam;
@@ -233,14 +241,18 @@ __device__ __forceinline__ float side_mixed(const float* q, float r0, float p0, 
 }
 
 // Mixed-policy Rusanov flux of the perturbation.  qo: own q'(9), rho0, p0;
-// qn: neighbour q'(9) (the background at the face is taken from this side);
-// jr, jp: FP64-accurate background jumps (neighbour minus own) of rho0 and p0.
+// qn: neighbour q'(9); jr, jp: FP64-accurate background jumps (neighbour minus
+// own) of rho0 and p0 at the face point.  Each side's perturbation flux and
+// wave speed are taken about its own background (the neighbour's is this side's
+// plus the jumps), so that with the background's central face flux (in R0) the
+// average is that of the full-state fluxes: F(Q0 + q') - F(Q0) depends on Q0,
+// and the extrapolated background of the two sides differs at a face.
 __device__ __forceinline__ void riemann_mixed(const float* qo, const float* qn, float nx, float ny, float nz,
                                               float gamma, float ch, float jr, float jp, float* Fs) {
   const float gm1 = gamma - 1.0f, gg1 = gamma / (gamma - 1.0f);
   float FL[9], FR[9];
   const float lo = side_mixed(qo, qo[9], qo[10], nx, ny, nz, gamma, gm1, gg1, ch, FL);
-  const float ln = side_mixed(qn, qo[9], qo[10], nx, ny, nz, gamma, gm1, gg1, ch, FR);
+  const float ln = side_mixed(qn, qo[9] + jr, qo[10] + jp, nx, ny, nz, gamma, gm1, gg1, ch, FR);
   const float lam = fmaxf(fmaxf(lo, ln), ch);
   const float hl = 0.5f * lam;
 #pragma unroll

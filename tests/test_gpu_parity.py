@@ -269,10 +269,12 @@ def test_step_equals_three_stages():
     assert torch.equal(qa, qb)
 
 
-def test_mixed_sd_step_low_storage_matches_oracle():
-    """sd_step on the FP32-mixed path (FP32 difference register instead of q^n) follows the FP64
-    oracle over three steps, given each step's dt and c_h."""
-    gm, om, gph, oph, q0, qb = _mixed_case(3, 2, 6, 2.5, seed=9)
+@pytest.mark.parametrize("N", [2, 3, 4, 5, 6, 7, 8])
+def test_mixed_sd_step_low_storage_matches_oracle(N):
+    """sd_step on the FP32-mixed path (the stored FP32 q' of q^n and the FP32 difference register
+    instead of q^n: bulk-copied for even N, loaded for odd N) follows the FP64 oracle over three
+    steps, given each step's dt and c_h."""
+    gm, om, gph, oph, q0, qb = _mixed_case(3, 2, N, 2.5, seed=9)
     bg = gm.background(gph, gm.to_device(qb))
     gph.c_h = 0.0  # c_h = lambda_max each step
     q, work = gm.to_device(q0), gm.empty_state()
@@ -288,8 +290,7 @@ def test_mixed_sd_step_low_storage_matches_oracle():
     assert ok, (err, bound)
 
 
-@pytest.mark.parametrize("N", [5, 6])
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec,N", [("fp64", 5), ("fp64", 6)] + [("mixed", n) for n in range(2, 9)])
 def test_advance_equals_repeated_steps(prec, N):
     """sd_advance takes the traces and lambda_max of each step's start state from the last stage of
     the step before instead of a trace pass; the states and (dt, c_h) are the same bits as sd_step
