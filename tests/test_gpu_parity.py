@@ -81,7 +81,7 @@ def test_residual_random_state_box():
     assert _residual_parity(gm, om, gph, oph, q0) < TOL64
 
 
-@pytest.mark.parametrize("N", [4, 6])
+@pytest.mark.parametrize("N", [2, 3, 4, 5, 6, 7, 8])
 def test_residual_shell_walls_all_sources(N):
     v, h = inputs.shell_mesh(3, 2)
     h = inputs.reorient(h, seed=5)
@@ -217,8 +217,9 @@ def _mixed_case(nz, nr, N, Nrho, seed=0):
     return gm, om, gph, oph, q0, qb
 
 
-def test_mixed_residual_stratified_shell():
-    gm, om, gph, oph, q0, qb = _mixed_case(4, 2, 6, 3.0)
+@pytest.mark.parametrize("N", [2, 3, 4, 5, 6, 7, 8])
+def test_mixed_residual_stratified_shell(N):
+    gm, om, gph, oph, q0, qb = _mixed_case(4 if N <= 6 else 3, 2, N, 3.0)
     bg = gm.background(gph, gm.to_device(qb))
     R = gm.to_host(gm.residual(gph, gm.to_device(q0), prec=sdmhd.SD_FP32_MIXED, bg=bg))
     Ro, s = om.residual(oph, q0)
@@ -226,10 +227,11 @@ def test_mixed_residual_stratified_shell():
     assert ok, (err, bound)
 
 
-def test_mixed_residual_developed_flow_strict():
+@pytest.mark.parametrize("N", [3, 6, 8])
+def test_mixed_residual_developed_flow_strict(N):
     """With a seeded velocity field on the stratified shell every component of the residual is far
     above FP32 resolution; there the mixed path meets 1e-5 relative per variable outright."""
-    gm, om, gph, oph, q0, qb = _mixed_case(4, 2, 6, 3.0, seed=2)
+    gm, om, gph, oph, q0, qb = _mixed_case(4 if N <= 6 else 3, 2, N, 3.0, seed=2)
     rng = np.random.default_rng(17)
     q1 = q0.copy()
     q1[1:4] += rng.uniform(-1e-2, 1e-2, size=q1[1:4].shape) * q1[0]
@@ -240,8 +242,11 @@ def test_mixed_residual_developed_flow_strict():
     assert err.max() <= 1e-5, err
 
 
-def test_mixed_stage_stratified_shell():
-    gm, om, gph, oph, q0, qb = _mixed_case(3, 2, 5, 2.0, seed=4)
+@pytest.mark.parametrize("N", [2, 3, 4, 5, 6, 7, 8])
+def test_mixed_stage_stratified_shell(N):
+    """sd_rk_stage on the FP32-mixed path (the q^n form with FP64 stage states, the FP64 state
+    loaded and converted in the kernel) against the oracle's RK step."""
+    gm, om, gph, oph, q0, qb = _mixed_case(3, 2, N, 2.0, seed=4)
     bg = gm.background(gph, gm.to_device(qb))
     dt = 1e-3
     q, work = gm.to_device(q0), gm.empty_state()

@@ -47,7 +47,7 @@ def torch_dev():
 
 
 @gpu
-@pytest.mark.parametrize("N", [4, 5, 6])
+@pytest.mark.parametrize("N", [2, 3, 4, 5, 6, 7, 8])
 def test_packed_step_equals_sd_step(torch_dev, N):
     """The packed launches (parameters from a device table, one launch over all requests) and sd_step
     do the same arithmetic in the same order: the same bits, for each order."""
