@@ -12,8 +12,8 @@
 //               the N derivative values over its own flux slots in sX
 //   E  points   R = -sum_d div_d / |J| + M + R0, FP64 RK sum, q' of the new state -> sQ
 //   F  lines    face traces of the new state (the two ends of every line).
-// Thread count T = 256 (N >= 6) or 128; G = T / (3 N^2) threads share a line in
-// B, D and F.
+// Thread count T = 256 (N >= 6), 96 (N = 4) or 128; G = T / (3 N^2) threads
+// share a line in B, D and F.
 #pragma once
 
 #include "sd_internal.h"
@@ -26,10 +26,12 @@ template <int N>
 struct DimsV2 {
   static constexpr int N2 = N * N, N3 = N2 * N, NF = N + 1, NV = 11;
   static constexpr int NLINE = 3 * N2;
-  // 256 threads from N = 6 up, 128 below (N^3 <= 125 points per element): up to
-  // G = T / (3 N^2) threads share a line in the line phases, each taking every
-  // G-th variable
-  static constexpr int T = N >= 6 ? 256 : 128;
+  // 256 threads from N = 6 up; below, where an element has at most 125 points,
+  // 96 at N = 4 (two per line) and 128 otherwise (measured on 24,576-element
+  // shells: N = 4 128 -> 96 threads 0.53 -> 0.48 ms per step, N = 5 160 threads
+  // no faster than 128).  Up to G = T / (3 N^2) threads share a line in the line
+  // phases, each taking every G-th variable.
+  static constexpr int T = N >= 6 ? 256 : (N == 4 ? 96 : 128);
   static_assert(NLINE <= T, "one thread per line at least");
   static constexpr int G = T / NLINE;
   // shared memory in floats
