@@ -260,15 +260,11 @@ __device__ __forceinline__ void sources_fp64(const StageParams& P, const double*
   M[8] -= P.alpha * q[8];
 }
 
-// Uniform FP32 constants of the mixed sources, converted once per thread.
+// Uniform FP32 constants of the mixed sources (GM, 2 Omega, the GLM damping).
 struct MixedConsts {
   float GM, om2, alpha;
   int gravity, coriolis, powell;
 };
-
-__device__ __forceinline__ MixedConsts mixed_consts(const StageParams& P) {
-  return MixedConsts{(float)P.GM, 2.0f * (float)P.omega, (float)P.alpha, P.gravity, P.coriolis, P.powell};
-}
 
 // Sources of the perturbation (rho0 g lives in the FP64 background residual).
 __device__ __forceinline__ void sources_mixed(const MixedConsts& C, const float* q, float divB, float x0, float x1,
@@ -309,7 +305,7 @@ template <int N, class Pol, bool VISC>
 __global__ void __launch_bounds__(Dims<N>::BLK) stage_kernel(const StageParams P, const Ops<typename Pol::R> ops) {
   using R = typename Pol::R;
   using S = Smem<N, Pol>;
-  static_assert(!VISC || !Pol::mixed, "viscous fluxes run on the FP64 policy");
+  static_assert(!Pol::mixed, "the FP32-mixed stages run stage_kernel_v2");
   constexpr int N2 = N * N, N3 = N2 * N, NF = N + 1, BLK = Dims<N>::BLK, NV = Pol::NV;
   extern __shared__ __align__(16) unsigned char smem[];
   R* sQ = reinterpret_cast<R*>(smem) + S::oQ;
@@ -367,7 +363,6 @@ __global__ void __launch_bounds__(Dims<N>::BLK) stage_kernel(const StageParams P
     const int nb = P.nbr[gidx];
     const int mt = P.meta[gidx];
     R qn[9];
-    float jr = 0.0f, jp = 0.0f;
     if (nb >= 0) {
       const int code = meta_code(mt);
       const int u = (code & 4) ? b : a, w = (code & 4) ? a : b;
@@ -375,29 +370,17 @@ __global__ void __launch_bounds__(Dims<N>::BLK) stage_kernel(const StageParams P
       const R* T = reinterpret_cast<const R*>(P.tr_in) + ((int64_t)nb * 6 + meta_nbF(mt)) * 9 * N2 + a2 + N * b2;
 #pragma unroll
       for (int v = 0; v < 9; ++v) qn[v] = T[v * N2];
-      if constexpr (Pol::mixed) {
-        jr = __ldg(P.bg_jump + (gidx * 2 + 0) * N2 + pt);
-        jp = __ldg(P.bg_jump + (gidx * 2 + 1) * N2 + pt);
-      }
     } else {
       const int bc = meta_bc(mt);
       if (bc == SD_BC_FARFIELD) {
 #pragma unroll
         for (int v = 0; v < 9; ++v) qn[v] = R(P.farfield[v]);
-        if constexpr (Pol::mixed) {
-          qn[0] -= qo[9];
-          qn[4] -= qo[10] / gm1;
-        }
       } else {
         wall_ghost<R>(qo, nx, ny, nz, bc, qn);
       }
     }
     R Fs[9];
-    if constexpr (!Pol::mixed) {
-      riemann_fp64(qo, qn, nx, ny, nz, gamma, ch, P.central, Fs);
-    } else {
-      riemann_mixed(qo, qn, nx, ny, nz, gamma, ch, jr, jp, Fs);
-    }
+    riemann_fp64(qo, qn, nx, ny, nz, gamma, ch, P.central, Fs);
     if constexpr (VISC) {
       // average of both sides' F_vis . n (this side's alone at a wall or far-field face,
       // or the wall conditions of visc_walls)
@@ -452,11 +435,7 @@ __global__ void __launch_bounds__(Dims<N>::BLK) stage_kernel(const StageParams P
       const R* Sp = Sfam + (d * 3 * N2 + line) * NF + f;
       const R Sx = Sp[0], Sy = Sp[N2 * NF], Sz = Sp[2 * N2 * NF];
       R Fv[9];
-      if constexpr (!Pol::mixed) {
-        flux_full<R>(qf, Sx, Sy, Sz, gm1, ch, Fv);
-      } else {
-        flux_pert(qf, Sx, Sy, Sz, gm1, gamma / gm1, ch, Fv);
-      }
+      flux_full<R>(qf, Sx, Sy, Sz, gm1, ch, Fv);
       if constexpr (VISC) {
         double g[NGRAD], Fvis[9];
 #pragma unroll
@@ -490,83 +469,44 @@ __global__ void __launch_bounds__(Dims<N>::BLK) stage_kernel(const StageParams P
     }
   }
 
-  // ---- epilogue: residual, sources, RK combination
-  // FP64 policy: q_out = a q_n + b (q_in + dt R) in FP64.
-  // Mixed policy: the same combination written as an increment of q_in,
-  //   q_out = q_in + t,  t = a (q_n - q_in) + b dt R  (a + b = 1 for every stage),
-  // with q_n - q_in formed in FP64, t in FP32 and the sum in FP64: the RK state
-  // accumulates in FP64 while the FP64 pipe sees two additions per value.
-  // The next stage's FP32 traces come from q' + t.
-  double lam = 0.0;  // lambda_max of the new state (FP64 policy, MODE_RK with P.lam_max)
+  // ---- epilogue: residual, sources, RK combination q_out = a q_n + b (q_in + dt R)
+  double lam = 0.0;  // lambda_max of the new state (MODE_RK with P.lam_max)
   if (n < N3) {
     const R iJ = reinterpret_cast<const R*>(P.invJ)[e * N3 + n];
     const R* Xe = reinterpret_cast<const R*>(P.X) + e * 3 * N3;
     const R divB = acc[9] * iJ;
     const int64_t g = e * P.stride + n;
-    if constexpr (!Pol::mixed) {
-      double q[9], M[9], Rv[9];
+    double q[9], M[9], Rv[9];
 #pragma unroll
-      for (int v = 0; v < 9; ++v) q[v] = sQ[v * N3 + n];
-      sources_fp64(P, q, divB, Xe[n], Xe[N3 + n], Xe[2 * N3 + n], M);
+    for (int v = 0; v < 9; ++v) q[v] = sQ[v * N3 + n];
+    sources_fp64(P, q, divB, Xe[n], Xe[N3 + n], Xe[2 * N3 + n], M);
 #pragma unroll
-      for (int v = 0; v < 9; ++v) Rv[v] = -acc[v] * iJ + M[v];
-      if (P.mode == MODE_RESIDUAL) {
+    for (int v = 0; v < 9; ++v) Rv[v] = -acc[v] * iJ + M[v];
+    if (P.mode == MODE_RESIDUAL) {
 #pragma unroll
-        for (int v = 0; v < 9; ++v) P.out[v * P.plane + g] = Rv[v];
-      } else if (P.mode == MODE_DIVB) {
-        P.divb[e * N3 + n] = divB;
-      } else {
-        double qout[9];
-        if (P.rk_a != 0.0) {
-#pragma unroll
-          for (int v = 0; v < 9; ++v)
-            qout[v] = P.rk_a * __ldg(P.q_n + v * P.plane + g) + P.rk_b * (q[v] + dt * Rv[v]);
-        } else {
-#pragma unroll
-          for (int v = 0; v < 9; ++v) qout[v] = P.rk_b * (q[v] + dt * Rv[v]);
-        }
-#pragma unroll
-        for (int v = 0; v < 9; ++v) P.out[v * P.plane + g] = qout[v];
-        if (P.lam_max) lam = point_speed_fp64(qout, P.gamma);
-        if (P.tr_out) {
-#pragma unroll
-          for (int v = 0; v < 9; ++v) acc[v] = qout[v];  // kept for the traces below
-        }
-      }
+      for (int v = 0; v < 9; ++v) P.out[v * P.plane + g] = Rv[v];
+    } else if (P.mode == MODE_DIVB) {
+      P.divb[e * N3 + n] = divB;
     } else {
-      float q[11], M[9], Rv[9];
+      double qout[9];
+      if (P.rk_a != 0.0) {
 #pragma unroll
-      for (int v = 0; v < 11; ++v) q[v] = sQ[v * N3 + n];
-      sources_mixed(mixed_consts(P), q, divB, Xe[n], Xe[N3 + n], Xe[2 * N3 + n], M);
-#pragma unroll
-      for (int v = 0; v < 9; ++v) Rv[v] = -acc[v] * iJ + M[v];
-      const int64_t gb = e * N3 + n, bp = P.n_e * N3;
-      Rv[1] += __ldg(P.bg + 2 * bp + gb);
-      Rv[2] += __ldg(P.bg + 3 * bp + gb);
-      Rv[3] += __ldg(P.bg + 4 * bp + gb);
-      if (P.mode == MODE_RESIDUAL) {
-#pragma unroll
-        for (int v = 0; v < 9; ++v) P.out[v * P.plane + g] = f32_to_f64(Rv[v]);
-      } else if (P.mode == MODE_DIVB) {
-        P.divb[e * N3 + n] = f32_to_f64(divB);
+        for (int v = 0; v < 9; ++v)
+          qout[v] = P.rk_a * __ldg(P.q_n + v * P.plane + g) + P.rk_b * (q[v] + dt * Rv[v]);
       } else {
-        const float bdt = (float)(P.rk_b * dt);
-        const float a = (float)P.rk_a;
 #pragma unroll
-        for (int v = 0; v < 9; ++v) {
-          const double qin = __ldg(P.q_in + v * P.plane + g);
-          float t = bdt * Rv[v];
-          if (P.rk_a != 0.0) t = fmaf(a, f64_to_f32(__ldg(P.q_n + v * P.plane + g) - qin), t);
-          P.out[v * P.plane + g] = qin + f32_to_f64(t);
-          acc[v] = q[v] + t;  // q' of the new state, for the traces below
-        }
+        for (int v = 0; v < 9; ++v) qout[v] = P.rk_b * (q[v] + dt * Rv[v]);
+      }
+#pragma unroll
+      for (int v = 0; v < 9; ++v) P.out[v * P.plane + g] = qout[v];
+      if (P.lam_max) lam = point_speed_fp64(qout, P.gamma);
+      if (P.tr_out) {
+#pragma unroll
+        for (int v = 0; v < 9; ++v) acc[v] = qout[v];  // kept for the traces below
       }
     }
   }
-  // (the mixed policy runs its RK stages in stage_kernel_v2, which returns lambda_max itself)
-  if constexpr (!Pol::mixed) {
-    if (P.mode == MODE_RK && P.lam_max) speed_reduce(lam, P.lam_max, P.lam_nslot);
-  }
+  if (P.mode == MODE_RK && P.lam_max) speed_reduce(lam, P.lam_max, P.lam_nslot);
   if (P.mode == MODE_RK && P.tr_out) {
     __syncthreads();
     if (n < N3) {
@@ -578,11 +518,27 @@ __global__ void __launch_bounds__(Dims<N>::BLK) stage_kernel(const StageParams P
   }
 }
 
+// The trace (+lambda_max) kernel of either policy.
+template <int N, class Pol>
+cudaError_t launch_traces_t(const StageParams& P, const Ops<typename Pol::R>& ops, cudaStream_t s) {
+  const size_t bytes = Smem<N, Pol>::trace_bytes;
+  if (bytes > 48 * 1024) {
+    cudaError_t err = cudaFuncSetAttribute(trace_kernel<N, Pol>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (err != cudaSuccess) return err;
+  }
+  if (P.n_e == 0) return cudaSuccess;
+  trace_kernel<N, Pol><<<(unsigned)P.n_e, Dims<N>::BLK, bytes, s>>>(P, ops);
+  return cudaGetLastError();
+}
+
+// The FP64 stage kernel, or its trace kernel.
 template <int N, class Pol, bool VISC = false>
 cudaError_t launch_stage_t(const StageParams& P, const Ops<typename Pol::R>& ops, bool traces_only, cudaStream_t s) {
+  static_assert(!Pol::mixed, "the FP32-mixed stages run stage_kernel_v2");
+  if (traces_only) return launch_traces_t<N, Pol>(P, ops, s);
   using Sm = Smem<N, Pol>;
-  const size_t bytes = traces_only ? Sm::trace_bytes : Sm::bytes + (VISC ? NGRAD * N * N * N * sizeof(double) : 0);
-  auto kern = traces_only ? trace_kernel<N, Pol> : stage_kernel<N, Pol, VISC>;
+  const size_t bytes = Sm::bytes + (VISC ? NGRAD * N * N * N * sizeof(double) : 0);
+  auto kern = stage_kernel<N, Pol, VISC>;
   if (bytes > 48 * 1024) {
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (err != cudaSuccess) return err;

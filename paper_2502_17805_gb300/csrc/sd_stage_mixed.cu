@@ -7,7 +7,7 @@ namespace sd {
 
 template <int N>
 static cudaError_t launch_mixed_n(const sd_mesh* m, const StageParams& P, bool traces_only, cudaStream_t s) {
-  if (traces_only) return launch_stage_t<N, PolMixed>(P, m->ops32, true, s);
+  if (traces_only) return launch_traces_t<N, PolMixed>(P, m->ops32, s);
   return launch_stage_v2_t<N>(P, m->ops32, s);
 }
 

@@ -1,7 +1,9 @@
 // sd_stage_v2.cuh -- FP32-mixed fused SD residual + SSP-RK stage, line-blocked.
 //
-// Same arithmetic as stage_kernel<N, PolMixed> (sd_stage.cuh), organised so that
-// the 1D operators run from registers.  Per element (one CTA):
+// The SD residual of the perturbation q' = q - Q0 in FP32 (arXiv 2502.17805,
+// Sec. Spectral Difference Method; the background Q0 and its FP64 residual R0
+// come from sd_background_create), organised so that the 1D operators run from
+// registers.  Per element (one CTA):
 //   A  load     q' (FP32 perturbation), rho0, p0 at the N^3 points -> sQ
 //   B  lines    G threads per line of each direction (3 N^2 lines) take the
 //               line's values of one variable at a time into registers and write
@@ -48,7 +50,7 @@ struct DimsV2 {
   static constexpr int nF = oG + (STAGE_G ? 7 * N3 : 0);
   static constexpr size_t bytes = ((nF * 4) + 15) / 16 * 16;
   // CTAs per SM that the shared memory admits (228 KB per SM, 1 KB reserved per
-  // CTA), capped at 5: the register budget of __launch_bounds__ follows from it.
+  // CTA); with the register bound below it sets __launch_bounds__.
   static constexpr int SMEM_CTAS = (int)(233472 / (bytes + 1024 + 64));
   // CTAs per SM that 64 registers per thread admit
   static constexpr int REG_CTAS = 65536 / (T * 64);
@@ -420,7 +422,7 @@ __device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops<fl
   }
   __syncthreads();
 
-  // ---- E: residual, sources, RK sum (see stage_kernel<N, PolMixed> for the increment form)
+  // ---- E: residual, sources, RK sum
   // With P.lam_max (MODE_RK) the stage also returns lambda_max of its output, and
   // the q' it leaves for the traces is rounded from the stored FP64 state exactly
   // as a fresh load would round it: the traces and lambda_max equal those of a
