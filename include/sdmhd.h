@@ -164,7 +164,8 @@ typedef struct {
   int64_t n_interior_faces;
   double h_min;            /* smallest element edge chord, for the time-step rule */
   int64_t device_bytes;    /* bytes the library holds on the device for this mesh */
-  int64_t trace_bytes;     /* scratch one sd_step_req needs for its face traces (FP32, two buffers) */
+  int64_t trace_bytes;     /* scratch one sd_step_req needs: three FP32 face-trace buffers and 128
+                              bytes of lambda_max partial maxima */
 } sd_mesh_info;
 
 typedef struct {
@@ -298,7 +299,18 @@ typedef struct {
   void* traces;             /* device scratch of sd_mesh_info.trace_bytes bytes, 16-byte aligned */
   double* dyn;              /* device double[4]: receives (dt, c_h, lambda_max) of the step in [0..2] */
   double cfl;               /* dt = cfl * dx_min / lambda_max as in sd_step */
+  int32_t flags;            /* SD_REQ_* bits below, 0 for a plain step */
+  int32_t pad_;
 } sd_step_req;
+
+/* sd_step_req.flags.  SD_REQ_KEEP_TRACES: the last stage also leaves the face
+ * traces and lambda_max of the new q (and its FP32 perturbation, in the
+ * background) in `traces`, as sd_advance does between its steps.
+ * SD_REQ_TRACES_READY: `traces` holds what the previous call of this request
+ * left with SD_REQ_KEEP_TRACES, and q has not been changed since; the call then
+ * skips the request's lambda_max/trace pass.  The results are the same bits
+ * with or without the flags. */
+enum { SD_REQ_KEEP_TRACES = 1, SD_REQ_TRACES_READY = 2 };
 
 typedef struct sd_packer sd_packer;
 

@@ -673,7 +673,8 @@ sd_status sd_mesh_query(const sd_mesh* m, sd_mesh_info* out) {
   out->n_interior_faces = m->n_if;
   out->h_min = m->h_min;
   out->device_bytes = m->device_bytes;
-  out->trace_bytes = 2 * m->n_e * 6 * 9 * (int64_t)m->N * m->N * (int64_t)sizeof(float);
+  // three FP32 trace buffers (the packed step's stage cycle) and 16 partial maxima of lambda
+  out->trace_bytes = 3 * m->n_e * 6 * 9 * (int64_t)m->N * m->N * (int64_t)sizeof(float) + 16 * 8;
   return SD_OK;
 }
 

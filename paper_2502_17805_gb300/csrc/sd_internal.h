@@ -90,6 +90,8 @@ struct StageParams {
   // mixed trace pass and by an exact last stage (qp_out, for the new state)
   const float* qp_in;
   float* qp_out;
+  // packed trace launch: this request's traces are already current, the CTA returns at once
+  int skip;
   int* err;  // device error word (bounded waits that ran out)
   // viscous, resistive and thermal fluxes (FP64 policy): coefficients, the gradients of
   // (U, T, S, B) at the solution points [e][24][N^3] (grad[3c + j] = d w_c / d x_j) and their

@@ -4,10 +4,16 @@
 // Requests are grouped by order N.  Per call the packer writes, for every
 // request, the parameters of its trace (+lambda) launch and of its three stage
 // launches into pinned host tables, copies them to the device in one transfer,
-// and launches: lambda reset (all requests), one packed trace kernel per N, one
-// step-control kernel (all requests), then for each stage one packed stage
-// kernel per N.  A CTA of a packed kernel finds its request by binary search in
-// the element offsets of its group.
+// and launches: lambda reset, one packed trace kernel per N, one step-control
+// kernel (all requests), then for each stage one packed stage kernel per N (the
+// last one in the exact form).  A CTA of a packed kernel finds its request by
+// binary search in the element offsets of its group.
+//
+// A request's `traces` scratch holds three trace buffers A, B, C and its 16
+// partial maxima of lambda.  The trace pass writes A; stage 0 reads A and writes
+// B, stage 1 reads B and writes C, stage 2 reads C and, with
+// SD_REQ_KEEP_TRACES, writes A and the maxima again for the next call, which
+// with SD_REQ_TRACES_READY then skips its trace pass (its CTAs return at once).
 #include <math.h>
 #include <string.h>
 
@@ -18,30 +24,37 @@
 #include "sd_internal.h"
 
 namespace sd {
-cudaError_t launch_packed_mixed(int N, bool traces, const StageParams* tab, const int64_t* off, int n_req,
+cudaError_t launch_packed_mixed(int N, int kind, const StageParams* tab, const int64_t* off, int n_req,
                                 int64_t blocks, const Ops<float>& ops, cudaStream_t s);
 void set_last_error(const std::string& msg);
 
-// partial maxima of lambda per request (the packer's own scratch)
+// partial maxima of lambda per request (at the end of the request's traces scratch)
 constexpr int PK_SLOTS = 16;
 
 struct StepCtl {
   double* dyn;
   unsigned long long* slots;  // [PK_SLOTS]
   double cfl, dx_min, ch_fixed;
+  int reset;  // the maxima are cleared before the trace pass (not for SD_REQ_TRACES_READY)
+  int pad_;
 };
 
 __global__ void packed_reset_kernel(const StepCtl* __restrict__ ctl, int n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n * PK_SLOTS) ctl[i / PK_SLOTS].slots[i % PK_SLOTS] = 0ull;
+  if (i < n * PK_SLOTS && ctl[i / PK_SLOTS].reset) ctl[i / PK_SLOTS].slots[i % PK_SLOTS] = 0ull;
 }
 
+// dt, c_h and lambda_max from the maxima, which are then cleared for the exact
+// last stage to fill
 __global__ void packed_control_kernel(const StepCtl* __restrict__ ctl, int n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double* dyn = ctl[i].dyn;
   unsigned long long b = 0ull;
-  for (int k = 0; k < PK_SLOTS; ++k) b = ctl[i].slots[k] > b ? ctl[i].slots[k] : b;
+  for (int k = 0; k < PK_SLOTS; ++k) {
+    b = ctl[i].slots[k] > b ? ctl[i].slots[k] : b;
+    ctl[i].slots[k] = 0ull;
+  }
   const double lam = __longlong_as_double((long long)b);
   dyn[0] = ctl[i].cfl * ctl[i].dx_min / lam;
   dyn[1] = ctl[i].ch_fixed > 0.0 ? ctl[i].ch_fixed : lam;
@@ -60,7 +73,6 @@ struct sd_packer {
   int64_t* d_off[2];
   sd::StepCtl* h_ctl[2];
   sd::StepCtl* d_ctl[2];
-  unsigned long long* d_slots;  // [cap][PK_SLOTS]
   cudaEvent_t copied[2];
   bool used[2];
   int device;
@@ -83,7 +95,6 @@ void free_packer(sd_packer* p) {
     if (p->d_ctl[b]) cudaFree(p->d_ctl[b]);
     if (p->copied[b]) cudaEventDestroy(p->copied[b]);
   }
-  if (p->d_slots) cudaFree(p->d_slots);
   delete p;
 }
 
@@ -110,8 +121,6 @@ sd_status sd_packer_create(int32_t max_requests, sd_packer** out) {
     if (err == cudaSuccess) err = cudaMalloc((void**)&p->d_ctl[b], max_requests * sizeof(sd::StepCtl));
     if (err == cudaSuccess) err = cudaEventCreateWithFlags(&p->copied[b], cudaEventDisableTiming);
   }
-  if (err == cudaSuccess)
-    err = cudaMalloc((void**)&p->d_slots, (size_t)max_requests * sd::PK_SLOTS * sizeof(unsigned long long));
   if (err != cudaSuccess) {
     free_packer(p);
     cudaGetLastError();
@@ -151,6 +160,8 @@ sd_status sd_step_packed(sd_packer* pk, int32_t n, const sd_step_req* reqs, void
       return pk_fail(SD_ERR_INVALID_ARGUMENT, where + "q, work, traces must be distinct 16-byte aligned buffers, dyn non-NULL");
     if (!(r.cfl > 0.0)) return pk_fail(SD_ERR_INVALID_ARGUMENT, where + "cfl must be positive");
     if (r.phys.viscous) return pk_fail(SD_ERR_UNSUPPORTED, where + "viscous fluxes run on the SD_FP64 path only");
+    if (r.flags & ~(SD_REQ_KEEP_TRACES | SD_REQ_TRACES_READY))
+      return pk_fail(SD_ERR_INVALID_ARGUMENT, where + "unknown flags");
   }
   {  // the background holds the step's FP32 scratch: one request per background
     std::vector<const sd_background*> bgs(n);
@@ -195,8 +206,11 @@ sd_status sd_step_packed(sd_packer* pk, int32_t n, const sd_step_req* reqs, void
     Group& g = groups.back();
     OFF[g.off0 + (k - g.k0) + 1] = OFF[g.off0 + (k - g.k0)] + m->n_e;
     const int64_t trace_elems = m->n_e * 6 * 9 * (int64_t)m->N * m->N;
-    float* tr0 = static_cast<float*>(r.traces);
-    float* tr1 = tr0 + trace_elems;
+    float* trA = static_cast<float*>(r.traces);
+    float* trB = trA + trace_elems;
+    float* trC = trB + trace_elems;
+    unsigned long long* slots = reinterpret_cast<unsigned long long*>(trC + trace_elems);
+    const bool ready = (r.flags & SD_REQ_TRACES_READY) != 0, keep = (r.flags & SD_REQ_KEEP_TRACES) != 0;
     sd::StageParams P;
     memset(&P, 0, sizeof(P));
     P.n_e = m->n_e;
@@ -221,22 +235,24 @@ sd_status sd_step_packed(sd_packer* pk, int32_t n, const sd_step_req* reqs, void
     P.bg_jump = r.bg->jump;
     P.dyn = r.dyn;
     P.err = m->err;
-    // trace (+lambda) of q into tr0
+    // trace (+lambda) of q into A (skipped when the previous call left them there)
     sd::StageParams Pt = P;
     Pt.q_in = r.q;
-    Pt.tr_out = tr0;
-    Pt.lam_max = pk->d_slots + (size_t)k * sd::PK_SLOTS;
+    Pt.tr_out = trA;
+    Pt.lam_max = slots;
     Pt.lam_nslot = sd::PK_SLOTS;
     Pt.qp_out = r.bg->qp;  // q' of q for the stages
     Pt.dstride = r.bg->dstride;
+    Pt.skip = ready ? 1 : 0;
     T[0 * n + k] = Pt;
     // increment form (as sd_step): every stage reads q^n and the FP32 register D
-    // carries the stage states.  Stage 0: D = t, traces tr0 -> tr1; stage 1: D += t,
-    // tr1 -> tr0; stage 2: q = q + D + t, reads tr0 (work is not written)
+    // carries the stage states.  Stage 0: D = t, traces A -> B; stage 1: D += t,
+    // B -> C; stage 2: q = q + D + t, reads C (work is not written) and, to keep
+    // them, writes the traces of the new q into A
     const double* qin[3] = {r.q, r.q, r.q};
     double* qout[3] = {r.work, r.work, r.q};
-    void* tin[3] = {tr0, tr1, tr0};
-    void* tout[3] = {tr1, tr0, nullptr};
+    void* tin[3] = {trA, trB, trC};
+    void* tout[3] = {trB, trC, keep ? trA : nullptr};
     for (int s = 0; s < 3; ++s) {
       sd::StageParams Ps = P;
       Ps.mode = sd::MODE_RK;
@@ -254,10 +270,14 @@ sd_status sd_step_packed(sd_packer* pk, int32_t n, const sd_step_req* reqs, void
       Ps.lsr_write = s == 0 ? 1 : (s == 1 ? 2 : 0);
       Ps.incr = 1;
       Ps.qp_in = r.bg->qp;
+      if (s == 2 && keep) {  // lambda_max and q' of the new q for the next call
+        Ps.lam_max = slots;
+        Ps.lam_nslot = sd::PK_SLOTS;
+        Ps.qp_out = r.bg->qp;
+      }
       T[(1 + s) * n + k] = Ps;
     }
-    CTL[k] = {r.dyn, pk->d_slots + (size_t)k * sd::PK_SLOTS, r.cfl, m->h_min * (m->ops64.xs[1] - m->ops64.xs[0]),
-              r.phys.c_h};
+    CTL[k] = {r.dyn, slots, r.cfl, m->h_min * (m->ops64.xs[1] - m->ops64.xs[0]), r.phys.c_h, ready ? 0 : 1, 0};
   }
   off_pos += (groups.back().k1 - groups.back().k0) + 1;
 
@@ -277,7 +297,7 @@ sd_status sd_step_packed(sd_packer* pk, int32_t n, const sd_step_req* reqs, void
     const Group& g = groups[gi];
     const int ng = g.k1 - g.k0;
     const int64_t blocks = OFF[g.off0 + ng];
-    err = sd::launch_packed_mixed(g.N, true, pk->d_tab[b] + 0 * n + g.k0, pk->d_off[b] + g.off0, ng, blocks,
+    err = sd::launch_packed_mixed(g.N, 0, pk->d_tab[b] + 0 * n + g.k0, pk->d_off[b] + g.off0, ng, blocks,
                                   reqs[order[g.k0]].mesh->ops32, s);
   }
   if (err == cudaSuccess) {
@@ -289,7 +309,7 @@ sd_status sd_step_packed(sd_packer* pk, int32_t n, const sd_step_req* reqs, void
       const Group& g = groups[gi];
       const int ng = g.k1 - g.k0;
       const int64_t blocks = OFF[g.off0 + ng];
-      err = sd::launch_packed_mixed(g.N, false, pk->d_tab[b] + (1 + st) * n + g.k0, pk->d_off[b] + g.off0, ng,
+      err = sd::launch_packed_mixed(g.N, st == 2 ? 2 : 1, pk->d_tab[b] + (1 + st) * n + g.k0, pk->d_off[b] + g.off0, ng,
                                     blocks, reqs[order[g.k0]].mesh->ops32, s);
     }
   if (err != cudaSuccess) return pk_fail(SD_ERR_CUDA, std::string("packed launch: ") + cudaGetErrorString(err));

@@ -224,6 +224,7 @@ __global__ void __launch_bounds__(Dims<N>::BLK) trace_kernel_packed(const StageP
   __shared__ StageParams sP;
   const int r = packed_request(off, n_req, (int64_t)blockIdx.x);
   copy_params(tab + r, &sP);
+  if (sP.skip) return;  // uniform over the CTA
   trace_body<N, PolMixed>(sP, ops, (int64_t)blockIdx.x - __ldg(off + r), smem);
 }
 

@@ -24,16 +24,16 @@ cudaError_t launch_stage_mixed(const sd_mesh* m, const StageParams& P, bool trac
   }
 }
 
-cudaError_t launch_packed_mixed(int N, bool traces, const StageParams* tab, const int64_t* off, int n_req,
+cudaError_t launch_packed_mixed(int N, int kind, const StageParams* tab, const int64_t* off, int n_req,
                                 int64_t blocks, const Ops<float>& ops, cudaStream_t s) {
   switch (N) {
-    case 2: return launch_packed_t<2>(traces, tab, off, n_req, blocks, ops, s);
-    case 3: return launch_packed_t<3>(traces, tab, off, n_req, blocks, ops, s);
-    case 4: return launch_packed_t<4>(traces, tab, off, n_req, blocks, ops, s);
-    case 5: return launch_packed_t<5>(traces, tab, off, n_req, blocks, ops, s);
-    case 6: return launch_packed_t<6>(traces, tab, off, n_req, blocks, ops, s);
-    case 7: return launch_packed_t<7>(traces, tab, off, n_req, blocks, ops, s);
-    case 8: return launch_packed_t<8>(traces, tab, off, n_req, blocks, ops, s);
+    case 2: return launch_packed_t<2>(kind, tab, off, n_req, blocks, ops, s);
+    case 3: return launch_packed_t<3>(kind, tab, off, n_req, blocks, ops, s);
+    case 4: return launch_packed_t<4>(kind, tab, off, n_req, blocks, ops, s);
+    case 5: return launch_packed_t<5>(kind, tab, off, n_req, blocks, ops, s);
+    case 6: return launch_packed_t<6>(kind, tab, off, n_req, blocks, ops, s);
+    case 7: return launch_packed_t<7>(kind, tab, off, n_req, blocks, ops, s);
+    case 8: return launch_packed_t<8>(kind, tab, off, n_req, blocks, ops, s);
     default: return cudaErrorInvalidValue;
   }
 }

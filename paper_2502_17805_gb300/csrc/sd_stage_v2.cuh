@@ -527,7 +527,7 @@ __device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops<fl
       if (exact) lam = speed_max(lam, point_speed_mixed(qe, gamma));
     }
   }
-  if (exact) speed_reduce(lam, P.lam_max, P.lam_nslot);
+  if (exact && P.lam_max) speed_reduce(lam, P.lam_max, P.lam_nslot);
 
   // ---- F: face traces of the new state
   if (mode == MODE_RK && P.tr_out) {
@@ -557,8 +557,11 @@ __global__ void __launch_bounds__(DimsV2<N>::T, DimsV2<N>::MINB) stage_kernel_v2
 }
 
 // Packed launch over several requests (see packed_request in sd_stage.cuh); the
-// packed stages always run the increment form.
-template <int N>
+// packed stages always run the increment form.  The last stage runs the exact
+// form (EXACT): a request whose row has tr_out, lam_max and qp_out set leaves
+// the traces, lambda_max and q' of its new state for its next step; with them
+// unset it gets what the plain last stage gives (the state is the same bits).
+template <int N, bool EXACT>
 __global__ void __launch_bounds__(DimsV2<N>::T, DimsV2<N>::MINB) stage_kernel_v2_packed(const StageParams* __restrict__ tab,
                                                                          const int64_t* __restrict__ off, int n_req,
                                                                          const Ops<float> ops) {
@@ -566,7 +569,7 @@ __global__ void __launch_bounds__(DimsV2<N>::T, DimsV2<N>::MINB) stage_kernel_v2
   __shared__ StageParams sP;
   const int r = packed_request(off, n_req, (int64_t)blockIdx.x);
   copy_params(tab + r, &sP);
-  stage_body_v2<N, false, true>(sP, ops, (int64_t)blockIdx.x - __ldg(off + r), smem_raw);
+  stage_body_v2<N, EXACT, true>(sP, ops, (int64_t)blockIdx.x - __ldg(off + r), smem_raw);
 }
 
 template <int N, bool EXACT, bool INCR>
@@ -595,13 +598,30 @@ cudaError_t launch_stage_v2_t(const StageParams& P, const Ops<float>& ops, cudaS
   return exact ? launch_stage_v2_e<N, true, false>(P, ops, s) : launch_stage_v2_e<N, false, false>(P, ops, s);
 }
 
-// Packed launches of one order N: trace (+lambda) kernel or stage kernel over
-// `blocks` elements of n_req requests.
+// Packed launches of one order N over `blocks` elements of n_req requests: the
+// trace (+lambda) kernel (kind 0), a stage (kind 1) or the last stage in the
+// exact form (kind 2).
+template <int N, bool EXACT>
+cudaError_t launch_packed_stage(const StageParams* tab, const int64_t* off, int n_req, int64_t blocks,
+                                const Ops<float>& ops, cudaStream_t s) {
+  using DV = DimsV2<N>;
+  auto kern = stage_kernel_v2_packed<N, EXACT>;
+  cudaError_t err =
+      cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+  if (err != cudaSuccess) return err;
+  if (DV::bytes > 40 * 1024) {
+    err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DV::bytes);
+    if (err != cudaSuccess) return err;
+  }
+  kern<<<(unsigned)blocks, DV::T, DV::bytes, s>>>(tab, off, n_req, ops);
+  return cudaGetLastError();
+}
+
 template <int N>
-cudaError_t launch_packed_t(bool traces, const StageParams* tab, const int64_t* off, int n_req, int64_t blocks,
+cudaError_t launch_packed_t(int kind, const StageParams* tab, const int64_t* off, int n_req, int64_t blocks,
                             const Ops<float>& ops, cudaStream_t s) {
   if (blocks == 0) return cudaSuccess;
-  if (traces) {
+  if (kind == 0) {
     const size_t bytes = Smem<N, PolMixed>::trace_bytes;
     if (bytes > 40 * 1024) {
       cudaError_t err = cudaFuncSetAttribute(trace_kernel_packed<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -609,20 +629,10 @@ cudaError_t launch_packed_t(bool traces, const StageParams* tab, const int64_t* 
       if (err != cudaSuccess) return err;
     }
     trace_kernel_packed<N><<<(unsigned)blocks, Dims<N>::BLK, bytes, s>>>(tab, off, n_req, ops);
-  } else {
-    using DV = DimsV2<N>;
-    cudaError_t err = cudaFuncSetAttribute(stage_kernel_v2_packed<N>,
-                                           cudaFuncAttributePreferredSharedMemoryCarveout,
-                                           (int)cudaSharedmemCarveoutMaxShared);
-    if (err != cudaSuccess) return err;
-    if (DV::bytes > 40 * 1024) {
-      err = cudaFuncSetAttribute(stage_kernel_v2_packed<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)DV::bytes);
-      if (err != cudaSuccess) return err;
-    }
-    stage_kernel_v2_packed<N><<<(unsigned)blocks, DV::T, DV::bytes, s>>>(tab, off, n_req, ops);
+    return cudaGetLastError();
   }
-  return cudaGetLastError();
+  return kind == 2 ? launch_packed_stage<N, true>(tab, off, n_req, blocks, ops, s)
+                   : launch_packed_stage<N, false>(tab, off, n_req, blocks, ops, s);
 }
 
 }  // namespace sd

@@ -77,7 +77,13 @@ class MeshInfoC(C.Structure):
 
 class StepReqC(C.Structure):
     _fields_ = [("mesh", C.c_void_p), ("phys", PhysC), ("bg", C.c_void_p), ("q", C.c_void_p), ("work", C.c_void_p),
-                ("traces", C.c_void_p), ("dyn", C.c_void_p), ("cfl", C.c_double)]
+                ("traces", C.c_void_p), ("dyn", C.c_void_p), ("cfl", C.c_double), ("flags", C.c_int32),
+                ("pad_", C.c_int32)]
+
+
+# sd_step_req.flags
+REQ_KEEP_TRACES = 1
+REQ_TRACES_READY = 2
 
 
 @dataclass
@@ -332,11 +338,13 @@ class Packer:
             self._h = None
 
     def step(self, reqs, stream=None):
-        """reqs: sequence of (mesh, phys, background, q, work, traces, dyn, cfl)."""
+        """reqs: sequence of (mesh, phys, background, q, work, traces, dyn, cfl[, flags])."""
         arr = (StepReqC * max(len(reqs), 1))()
-        for i, (mesh, phys, bg, q, work, traces, dyn, cfl) in enumerate(reqs):
+        for i, req in enumerate(reqs):
+            mesh, phys, bg, q, work, traces, dyn, cfl = req[:8]
             r = arr[i]
             r.mesh, r.phys, r.bg = mesh._h, phys.c(), bg._h
             r.q, r.work, r.traces, r.dyn = _ptr(q), _ptr(work), _ptr(traces), _ptr(dyn)
             r.cfl = float(cfl)
+            r.flags = int(req[8]) if len(req) > 8 else 0
         _check(lib().sd_step_packed(self._h, len(reqs), arr, _stream(stream)))

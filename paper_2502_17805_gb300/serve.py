@@ -101,9 +101,20 @@ class _Running:
         self.traces = torch.empty(mesh.info["trace_bytes"] // 4, dtype=torch.float32, device="cuda")
         self.dyn = torch.zeros(4, dtype=torch.float64, device="cuda")
         self.steps_done = 0
+        self.ready = False  # the previous step left the traces and lambda_max of q
+
+    def keep(self) -> bool:
+        """another step of this request follows the one about to be issued"""
+        return self.steps_done + 1 < self.req.steps
 
     def as_packed(self):
-        return (self.mesh, self.phys, self.bg, self.q, self.work, self.traces, self.dyn, self.req.cfl)
+        flags = (sdmhd.REQ_KEEP_TRACES if self.keep() else 0) | (sdmhd.REQ_TRACES_READY if self.ready else 0)
+        return (self.mesh, self.phys, self.bg, self.q, self.work, self.traces, self.dyn, self.req.cfl, flags)
+
+    def advanced(self):
+        """after the step from as_packed() has been issued"""
+        self.ready = self.keep()
+        self.steps_done += 1
 
 
 def footprint_bytes(info: dict, n_pts: int) -> int:
@@ -197,7 +208,7 @@ class Server:
             self.ticks += 1
             keep, done_reqs, done_runs = [], [], []
             for run, fp in running:
-                run.steps_done += 1
+                run.advanced()
                 if run.steps_done >= run.req.steps:
                     done_reqs.append(run.req)
                     done_runs.append(run)  # released (stream-ordered) once retired
@@ -222,6 +233,7 @@ class Server:
         run = _Running(req, m)
         for _ in range(req.steps):
             self.packer.step([run.as_packed()])
+            run.advanced()
         return run.q
 
 
@@ -233,5 +245,5 @@ def run_mix(server: Server, reqs: Sequence[Request]):
         active = [run for run in runs if run.steps_done < run.req.steps]
         server.packer.step([run.as_packed() for run in active])
         for run in active:
-            run.steps_done += 1
+            run.advanced()
     return [run.q for run in runs]

@@ -134,3 +134,40 @@ def test_requests_may_not_share_a_background(torch_dev):
     b[2] = a[2]  # other's states, run's background
     with pytest.raises(sdmhd.SDError, match="share a background"):
         srv.packer.step([a, tuple(b)])
+
+
+@gpu
+@pytest.mark.parametrize("N", [4, 6])
+def test_kept_traces_give_the_same_bits(torch_dev, N):
+    """With SD_REQ_KEEP_TRACES / SD_REQ_TRACES_READY the last stage of one call leaves the traces and
+    lambda_max of the new state and the next call skips its trace pass; the states and (dt, c_h, lambda)
+    are the same bits as plain calls (each with its own trace pass)."""
+    torch = torch_dev
+    from paper_2502_17805_gb300 import sdmhd
+    srv = serve.Server(hbm_budget_bytes=1 << 34, max_running=4)
+    req = serve.Request(rid=0, nz=3, nr=2, N=N, n_rho=2.0, omega=1.3, seed=5, steps=4, arrival=0.0)
+    fused = serve._Running(req, srv.mesh(req.nz, req.nr, req.N))
+    plain = serve._Running(req, srv.mesh(req.nz, req.nr, req.N))
+    assert fused.mesh.info["trace_bytes"] == 3 * fused.mesh.n_e * 6 * 9 * N * N * 4 + 128
+    flags_seen = []
+    for _ in range(req.steps):
+        pf = fused.as_packed()
+        flags_seen.append(pf[8])
+        srv.packer.step([pf])
+        fused.advanced()
+        srv.packer.step([plain.as_packed()[:8]])  # flags 0
+        plain.advanced()
+        torch.cuda.synchronize()
+        assert torch.equal(fused.q, plain.q) and torch.equal(fused.dyn[:3], plain.dyn[:3])
+    K, R = sdmhd.REQ_KEEP_TRACES, sdmhd.REQ_TRACES_READY
+    assert flags_seen == [K, K | R, K | R, R]
+
+
+@gpu
+def test_unknown_request_flags_are_refused(torch_dev):
+    from paper_2502_17805_gb300 import sdmhd
+    srv = serve.Server(hbm_budget_bytes=1 << 34, max_running=4)
+    req = serve.Request(rid=0, nz=2, nr=1, N=4, n_rho=2.0, omega=1.0, seed=5, steps=1, arrival=0.0)
+    run = serve._Running(req, srv.mesh(req.nz, req.nr, req.N))
+    with pytest.raises(sdmhd.SDError, match="unknown flags"):
+        srv.packer.step([run.as_packed()[:8] + (4,)])
