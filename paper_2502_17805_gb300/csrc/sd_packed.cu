@@ -296,6 +296,9 @@ sd_status sd_step_packed(sd_packer* pk, int32_t n, const sd_step_req* reqs, void
   for (size_t gi = 0; gi < groups.size() && err == cudaSuccess; ++gi) {
     const Group& g = groups[gi];
     const int ng = g.k1 - g.k0;
+    bool any = false;  // a request of the group needs its trace pass
+    for (int k = g.k0; k < g.k1 && !any; ++k) any = !(reqs[order[k]].flags & SD_REQ_TRACES_READY);
+    if (!any) continue;
     const int64_t blocks = OFF[g.off0 + ng];
     err = sd::launch_packed_mixed(g.N, 0, pk->d_tab[b] + 0 * n + g.k0, pk->d_off[b] + g.off0, ng, blocks,
                                   reqs[order[g.k0]].mesh->ops32, s);
