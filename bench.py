@@ -124,8 +124,15 @@ def source_hash() -> str:
     return h.hexdigest()[:16]
 
 
+def fp64_peak_tflops(n_sm: int, sm_mhz: float) -> float:
+    """FP64 peak from unit counts and clocks: 2 FP64 FMA per SM and clock on GB300 (its nominal
+    1.25 TFLOP/s over 152 SMs at about 2 GHz), 2 flop per FMA."""
+    return n_sm * 2 * 2 * sm_mhz * 1e6 / 1e12
+
+
 def committed_traffic(kernel_key: str):
-    """DRAM bytes per launch of a kernel from a committed ncu summary, if it was taken on these sources."""
+    """A per-launch counter of a kernel (DRAM bytes, FP64 flops) from a committed ncu summary, if it
+    was taken on these sources."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
@@ -409,6 +416,21 @@ class OracleSample:
         return self.dof_per_step * steps / secs if steps else 0.0, secs
 
 
+def fp64_roofline(stage_ms: float, clocks):
+    """The FP64 stage kernel against the FP64 pipe: its FP64 flops per launch (committed ncu count of
+    DFMA, DADD, DMUL on these sources, scaled to the bench shell) over its live average launch time."""
+    import torch
+    n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = clocks["sm_max_mhz"] if clocks else 2070.0
+    peak = fp64_peak_tflops(n_sm, mhz)
+    flops = committed_traffic("stage_fp64_N6_flops")
+    achieved = flops / (stage_ms / 1e3) / 1e12 if flops else None
+    return {"kernel": "stage_kernel<6, PolFP64> (FP64 fused stage)", "bound": "fp64", "achieved": achieved,
+            "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak if achieved else None,
+            "peak_source": "derived: %d SMs x 2 FP64 FMA/clk x 2 flop x %.0f MHz" % (n_sm, mhz),
+            "flops_per_launch": flops}
+
+
 def run_ours(args):
     import torch
 
@@ -483,7 +505,7 @@ def run_ours(args):
                      "avg_launch_ms": stage_avg_ms,
                      "step_frac": step_achieved / peak},
         "fp64": {"value": value64, "unit": UNIT, "steps": k64, "ms_per_step": ms64 / k64, "dtype": "f64",
-                 "stage_avg_ms": stage64_ms},
+                 "stage_avg_ms": stage64_ms, "roofline": fp64_roofline(stage64_ms, clocks)},
         "viscous_fp64": visc,
         "gpu_launches": int(prof["stage_launches"] + prof["trace_launches"] + prof["other_launches"]),
         "kernel_ms_per_step": {"stage": prof["stage_ms"] / args.steps, "trace_lambda": prof["trace_ms"] / args.steps,
