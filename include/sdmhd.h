@@ -207,8 +207,9 @@ sd_status sd_state_init(const sd_mesh* mesh, const sd_phys* phys, const sd_init*
 /* Prepare the FP32-mixed precision path around a hydrostatic background Q0
  * (device state, only rho and E are read; U = B = psi = 0 is assumed):
  * rounds rho0 and p0 to FP32, computes in FP64 the background residual R0
- * (pressure gradient with central face average, plus rho0 g) and the FP64 jumps
- * of the background across faces.  The handle also holds the FP32 scratch of
+ * (pressure gradient with central face average, plus rho0 g; at a far-field
+ * face the background is its own ghost, the far field entering the mixed
+ * stages as a perturbation) and the FP64 jumps of the background across faces.  The handle also holds the FP32 scratch of
  * the mixed sd_step (the register D and the FP32 perturbation q' of the step's
  * starting state, 72 bytes per solution point), so one background serves one
  * sd_step / sd_advance / packed request at a time.  The handle stays valid

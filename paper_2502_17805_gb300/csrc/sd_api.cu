@@ -769,11 +769,15 @@ sd_status sd_background_create(const sd_mesh* m, const sd_phys* ph, const double
     P.tr_out = mm->tr64[0];
     err = sd::launch_traces(m, SD_FP64, P, s);
     if (err == cudaSuccess) {
-      // background residual: pressure-gradient flux with central face average, plus rho0 g
+      // background residual: pressure-gradient flux with central face average, plus rho0 g.  A
+      // far-field face takes the element's own background as its ghost: the mixed stages carry the
+      // far field as the perturbation Q_ff - Q0 about that same background, so the two parts add
+      // up to the full flux there.
       P.tr_out = nullptr;
       P.tr_in = mm->tr64[0];
       P.mode = sd::MODE_RESIDUAL;
       P.central = 1;
+      P.ff_own = 1;
       P.c_h = 0.0;
       P.powell = 0;
       P.coriolis = 0;

@@ -58,6 +58,7 @@ struct StageParams {
   double* out;     // dqdt (residual) or q_out (RK)
   int mode;
   int central;     // 1: face flux is the central average (no Rusanov dissipation)
+  int ff_own;      // 1: a far-field face takes this side's own state as its ghost (the background pass)
   double rk_a, rk_b;
   double dt, c_h;
   const double* dyn;  // device (dt, c_h) or nullptr

@@ -375,7 +375,7 @@ __global__ void __launch_bounds__(Dims<N>::BLK) stage_kernel(const StageParams P
       const int bc = meta_bc(mt);
       if (bc == SD_BC_FARFIELD) {
 #pragma unroll
-        for (int v = 0; v < 9; ++v) qn[v] = R(P.farfield[v]);
+        for (int v = 0; v < 9; ++v) qn[v] = P.ff_own ? qo[v] : R(P.farfield[v]);
       } else {
         wall_ghost<R>(qo, nx, ny, nz, bc, qn);
       }

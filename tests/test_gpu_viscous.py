@@ -118,7 +118,7 @@ def test_viscous_fluxes_are_rejected_where_unsupported():
         gm.residual(bad, q)
 
 
-@pytest.mark.parametrize("N", [4, 5])
+@pytest.mark.parametrize("N", [2, 3, 4, 5, 6, 7, 8])
 def test_viscous_walls_residual(N):
     """Stress-free walls, heat flux through the inner sphere, temperature held on the outer sphere."""
     v, h = inputs.shell_mesh(2, 2)
