@@ -249,6 +249,26 @@ def test_mixed_residual_stratified_shell(N):
     assert ok, (err, bound)
 
 
+@pytest.mark.parametrize("N", [2, 3, 4, 5, 6, 7, 8])
+def test_mixed_residual_random_background_periodic_box(N):
+    """FP32-mixed residual about a non-uniform, non-hydrostatic background on a jittered, reoriented
+    periodic box: the background jumps across every interior and periodic face (each side's flux is
+    taken about its own background), there are no walls, and R0 carries the background's residual."""
+    v, h, per = inputs.box_mesh(3, jitter=0.15, seed=N)
+    gm, om = _pair(N, v, inputs.reorient(h, seed=N), periodic=per, geom=0)
+    gph, oph = _phys(powell=1, c_h=0.7, glm_alpha=0.3)
+    q0 = inputs.random_state(gm.n_e, N, seed=40 + N)
+    src = inputs.random_state(gm.n_e, N, seed=80 + N)
+    qb = np.zeros_like(q0)
+    qb[0] = src[0]          # rho0 in [0.8, 1.2]
+    qb[4] = 0.8 * src[4]    # E0 = p0 / (gamma - 1) in [1.2, 2.0]
+    bg = gm.background(gph, gm.to_device(qb))
+    R = gm.to_host(gm.residual(gph, gm.to_device(q0), prec=sdmhd.SD_FP32_MIXED, bg=bg))
+    Ro, s = om.residual(oph, q0)
+    ok, err, bound = mixed_ok(R, Ro, s)
+    assert ok, (err, bound)
+
+
 @pytest.mark.parametrize("N", [3, 6, 8])
 def test_mixed_residual_developed_flow_strict(N):
     """With a seeded velocity field on the stratified shell every component of the residual is far
