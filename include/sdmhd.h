@@ -190,8 +190,10 @@ const char* sd_last_error(void);
  * corner projector, Sec. SD Method) sampled at Chebyshev-Lobatto nodes as a
  * degree-floor(N/2) polynomial map, its contravariant metrics S^d = |J| grad xi_d
  * at the flux points, |J| and x at the solution points.  Synchronises `stream`.
- * Errors: SD_ERR_INVALID_ARGUMENT, SD_ERR_UNSUPPORTED, SD_ERR_MESH_TOPOLOGY,
- * SD_ERR_MESH_GEOMETRY, SD_ERR_OUT_OF_MEMORY, SD_ERR_CUDA.  *out is NULL on error. */
+ * A mesh has at least one element (an empty description is
+ * SD_ERR_INVALID_ARGUMENT).  Errors: SD_ERR_INVALID_ARGUMENT, SD_ERR_UNSUPPORTED,
+ * SD_ERR_MESH_TOPOLOGY, SD_ERR_MESH_GEOMETRY, SD_ERR_OUT_OF_MEMORY, SD_ERR_CUDA.
+ * *out is NULL on error. */
 sd_status sd_mesh_create(const sd_mesh_desc* desc, void* stream, sd_mesh** out);
 sd_status sd_mesh_destroy(sd_mesh* mesh);
 sd_status sd_mesh_query(const sd_mesh* mesh, sd_mesh_info* out);

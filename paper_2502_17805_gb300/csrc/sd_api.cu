@@ -468,8 +468,8 @@ sd_status sd_mesh_create(const sd_mesh_desc* desc, void* stream, sd_mesh** out) 
   const int N = desc->order;
   if (N < 2 || N > sd::kMaxN) return fail(SD_ERR_UNSUPPORTED, "order N must be in [2, 8]");
   if (desc->n_elements < 0 || desc->n_vertices < 0) return fail(SD_ERR_INVALID_ARGUMENT, "negative size");
-  if (desc->n_elements > 0 && (!desc->hex || !desc->vertices))
-    return fail(SD_ERR_INVALID_ARGUMENT, "vertices or hex is NULL");
+  if (desc->n_elements == 0) return fail(SD_ERR_INVALID_ARGUMENT, "a mesh needs at least one element");
+  if (!desc->hex || !desc->vertices) return fail(SD_ERR_INVALID_ARGUMENT, "vertices or hex is NULL");
   if (desc->geom != 0 && desc->geom != 1) return fail(SD_ERR_INVALID_ARGUMENT, "geom must be 0 or 1");
   if (desc->n_elements > (int64_t)1 << 30) return fail(SD_ERR_INVALID_ARGUMENT, "too many elements");
   const int bcs[2] = {desc->bc_inner, desc->bc_outer};

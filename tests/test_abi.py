@@ -68,6 +68,15 @@ def test_mesh_create_rejects_bad_arguments(lib):
     assert not out.value
 
 
+def test_mesh_create_rejects_an_empty_mesh(lib):
+    out = C.c_void_p()
+    v, h, per = inputs.box_mesh(3)
+    d, keep = _desc(4, v, h[:0], None)
+    assert lib.sd_mesh_create(C.byref(d), None, C.byref(out)) == 1
+    assert "at least one element" in lib.sd_last_error().decode()
+    assert not out.value
+
+
 def test_mesh_create_detects_non_conforming_topology(lib):
     out = C.c_void_p()
     v, h, per = inputs.box_mesh(3)

@@ -171,3 +171,9 @@ def test_unknown_request_flags_are_refused(torch_dev):
     run = serve._Running(req, srv.mesh(req.nz, req.nr, req.N))
     with pytest.raises(sdmhd.SDError, match="unknown flags"):
         srv.packer.step([run.as_packed()[:8] + (4,)])
+
+
+@gpu
+def test_an_empty_pack_is_a_no_op(torch_dev):
+    srv = serve.Server(hbm_budget_bytes=1 << 34, max_running=4)
+    srv.packer.step([])
