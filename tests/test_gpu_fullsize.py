@@ -125,3 +125,44 @@ def test_shell1536_hundred_fp64_steps():
     _, s = om.residual(oph, q0)
     bound = 1e-9 * change + 1e-12 * t_run * s
     assert dt_err < 1e-11 and np.all(err <= bound), (dt_err, err, bound)
+
+
+def test_shell41k_mixed_advance_matches_the_oracle():
+    """The benchmark's launch configuration: two FP32-mixed steps of sd_advance on the 41,472-element
+    shell (fused stages, the second step taking its traces and lambda_max from the first step's last
+    stage) against two oracle steps with the same dt and c_h, on every element."""
+    gm, om = _shell(24, 12)
+    gph, oph = _phys(ch=0.0)
+    prm = [3.0, 0.70, 0.98, 1.0, 1.0, 1e-4, 1e-6]
+    q0, qb = om.state_init(oph, sdref.INIT_SHELL_POLYTROPE, prm, seed=0, background=True)
+    bg = gm.background(gph, gm.to_device(qb))
+    del qb
+    q, work = gm.to_device(q0), gm.empty_state()
+    dts = torch.zeros(4, dtype=torch.float64, device="cuda")
+    gm.advance(gph, 0.2, 2, q, work, prec=sdmhd.SD_FP32_MIXED, bg=bg, dt_out=dts)
+    d = dts.cpu().numpy()
+    qo = q0
+    for k in range(2):
+        oph.c_h = float(d[2 * k + 1])
+        qo = om.rk_step(oph, float(d[2 * k]), qo)
+    _, s = om.residual(oph, q0)
+    g = gm.to_host(q)
+    change = np.abs(qo - q0).reshape(9, -1).max(axis=1)
+    err = np.abs(g - qo).reshape(9, -1).max(axis=1)
+    bound = 1e-5 * change + 4 * 2.0 ** -24 * 2 * 3 * float(d[0]) * s
+    assert np.all(err <= bound), (err, bound)
+
+
+def test_shell221k_mixed_residual_sampled():
+    gm, om = _shell(48, 16)
+    gph, oph = _phys()
+    prm = [3.0, 0.70, 0.98, 1.0, 1.0, 1e-4, 1e-6]
+    q0, qb = om.state_init(oph, sdref.INIT_SHELL_POLYTROPE, prm, seed=0, background=True)
+    bg = gm.background(gph, gm.to_device(qb))
+    del qb
+    elems = _sample(gm.n_e, k=32, seed=3)
+    Ro, s = om.residual_elements(oph, q0, elems)
+    R = _gather(gm, gm.residual(gph, gm.to_device(q0), prec=sdmhd.SD_FP32_MIXED, bg=bg), elems)
+    err = np.abs(R - Ro).max(axis=(0, 2))
+    bound = 1e-5 * np.abs(Ro).max(axis=(0, 2)) + 4 * 2.0 ** -24 * s
+    assert np.all(err <= bound), (err, bound)
