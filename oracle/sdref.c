@@ -52,7 +52,11 @@
  *     (each side's state and extrapolated gradients), along the owner's normal.
  *  V5 at wall and far-field faces the viscous flux is this side's own (the paper's stress-free,
  *     heat-flux and magnetic boundary conditions are not part of the inviscid wall ghost).
- *  V6 the coefficients mu, eta, kappa, kappa_r and R are constants.
+ *  V6 the coefficients mu, eta, kappa and R are constants.
+ *  V7 the radiative diffusivity depends on the radius, kappa_r(r) = kappa_r + kappa_r1 r + kappa_r2 r^2
+ *     (Sec. Benchmark Problem Definition gives it as a factor, left undefined, times a quadratic in
+ *     r; the caller's three coefficients take both), evaluated at the point of the heat flux: the
+ *     flux point, the face point or the wall.
  *  W1 viscous walls (visc_walls; Sec. Problem Formulation): stress-free and impenetrable, i.e. of
  *     the viscous stress only n.tau.n acts through a wall, on the face state (the average of the two
  *     sides, whose normal velocity vanishes), so the wall does no viscous work.
@@ -565,6 +569,12 @@ static const double* geo_S(const sdref_mesh* m, int64_t e, int d, int f, int a, 
 }
 static double geo_J(const sdref_mesh* m, int64_t e, int n) { return m->gcache[e][gsz_S(m) + n]; }
 static const double* geo_X(const sdref_mesh* m, int64_t e, int n) { return m->gcache[e] + gsz_S(m) + gsz_J(m) + 3 * n; }
+/* position of point (f, a, b) of flux family d of element e: its polynomial map there */
+static void family_x(const sdref_mesh* m, int64_t e, int d, int f, int a, int b, double* x) {
+  double pt[3];
+  family_point(m, d, f, a, b, pt);
+  map_value(m, m->gcache[e] + gsz_S(m) + 4 * gsz_J(m), pt, x);
+}
 
 int sdref_geometry(sdref_mesh* m, int64_t e, double* S, double* J, double* X, double* Xp) {
   if (e < 0 || e >= m->n_e) { set_err("element out of range"); return 1; }
@@ -734,7 +744,14 @@ static void prim_w(const double* Q, const sdref_phys* ph, double* w) {
  *   energy    (U . tau - q + eta B x J) . n,  q = -kappa rho T grad S - kappa_r rho C_p grad T
  *   induction eta J x n,  J = curl B   (the antisymmetric flux whose divergence is curl(eta J))
  * fm[] receives the sum of the magnitudes of the terms (comparison tolerance only). */
-static void visc_flux(const double* Q, const double* g, const double* n, const sdref_phys* ph, double* F,
+/* radiative diffusivity at position x (reading V7) */
+static double kappa_r_at(const sdref_phys* ph, const double* x) {
+  double r = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+  return ph->kappa_r + ph->kappa_r1 * r + ph->kappa_r2 * r * r;
+}
+
+/* viscous flux F_vis(Q, grad w) . n with the radiative diffusivity kr at the point */
+static void visc_flux(const double* Q, const double* g, const double* n, const sdref_phys* ph, double kr, double* F,
                       double* fm) {
   double w[NW];
   prim_w(Q, ph, w);
@@ -749,7 +766,7 @@ static void visc_flux(const double* Q, const double* g, const double* n, const s
     for (int j = 0; j < 3; ++j) tau[i][j] = mu * (g[i * 3 + j] + g[j * 3 + i]) + (i == j ? lam * divu : 0.0);
   double J[3] = {g[7 * 3 + 1] - g[6 * 3 + 2], g[5 * 3 + 2] - g[7 * 3 + 0], g[6 * 3 + 0] - g[5 * 3 + 1]};
   double qh[3], BxJ[3], Jxn[3], uT[3];
-  for (int j = 0; j < 3; ++j) qh[j] = -ph->kappa * rho * T * g[4 * 3 + j] - ph->kappa_r * rho * cp * g[3 * 3 + j];
+  for (int j = 0; j < 3; ++j) qh[j] = -ph->kappa * rho * T * g[4 * 3 + j] - kr * rho * cp * g[3 * 3 + j];
   cross3(B, J, BxJ);
   cross3(J, n, Jxn);
   for (int j = 0; j < 3; ++j) uT[j] = u[0] * tau[0][j] + u[1] * tau[1][j] + u[2] * tau[2][j];
@@ -850,7 +867,7 @@ static void grad_face_value(const sdref_mesh* m, const double* G, int64_t e, int
  * resistive terms take this side's current, of which a perfectly conducting wall keeps only the
  * normal part */
 static void wall_visc(const sdref_mesh* m, const sdref_phys* ph, int64_t e, int F, const double* Qown,
-                      const double* g, const double* n, double* F_, double* fm) {
+                      const double* g, const double* n, double kr, double* F_, double* fm) {
   int64_t k = 6 * e + F;
   double gh[9], Qf[9], w[NW];
   ghost_state(Qown, n, m->bc[k], ph, gh);
@@ -872,7 +889,7 @@ static void wall_visc(const sdref_mesh* m, const sdref_phys* ph, int64_t e, int 
   double qn = 0.0, qm = 0.0;
   if (m->outer[k]) {
     for (int j = 0; j < 3; ++j) {
-      double qj = -ph->kappa * rho * T * g[4 * 3 + j] - ph->kappa_r * rho * cp * g[3 * 3 + j];
+      double qj = -ph->kappa * rho * T * g[4 * 3 + j] - kr * rho * cp * g[3 * 3 + j];
       qn += qj * n[j];
       qm += fabs(qj * n[j]);
     }
@@ -895,18 +912,21 @@ static void common_visc(const sdref_mesh* m, const sdref_phys* ph, const double*
                         int a, int b, const double* Qown, const double* gown, const double* n, double* Fv,
                         double* Fvm) {
   int64_t k = 6 * e + F;
+  double xf[3];
+  family_x(m, e, F / 2, (F & 1) ? m->N : 0, a, b, xf);
+  const double kr = kappa_r_at(ph, xf); /* both sides at this face point (reading V7) */
   if (m->nb_e[k] < 0 && ph->visc_walls) {
-    wall_visc(m, ph, e, F, Qown, gown, n, Fv, Fvm);
+    wall_visc(m, ph, e, F, Qown, gown, n, kr, Fv, Fvm);
     return;
   }
-  visc_flux(Qown, gown, n, ph, Fv, Fvm);
+  visc_flux(Qown, gown, n, ph, kr, Fv, Fvm);
   if (m->nb_e[k] < 0) return;
   int a2, b2;
   map_point(m->code[k], m->N, a, b, &a2, &b2);
   double Q2[9], g2[NW * 3], F2[9], F2m[9];
   face_value(m, q, m->nb_e[k], m->nb_f[k], a2, b2, Q2);
   grad_face_value(m, G, m->nb_e[k], m->nb_f[k], a2, b2, g2);
-  visc_flux(Q2, g2, n, ph, F2, F2m);
+  visc_flux(Q2, g2, n, ph, kr, F2, F2m);
   for (int v = 0; v < 9; ++v) {
     Fv[v] = 0.5 * (Fv[v] + F2[v]);
     Fvm[v] = 0.5 * (Fvm[v] + F2m[v]);
@@ -1051,7 +1071,9 @@ static void residual_element(const sdref_mesh* m, const sdref_phys* ph, const do
           for (int v = 0; v < 9; ++v) Ftm[f][v] = fabs(Ft[f][v]);
           if (G) {
             double Fv[9], Fvm[9];
-            visc_flux(Qf[f], gf[f], S, ph, Fv, Fvm);
+            double xf[3];
+            family_x(m, e, d, f, a, b, xf);
+            visc_flux(Qf[f], gf[f], S, ph, kappa_r_at(ph, xf), Fv, Fvm);
             for (int v = 0; v < 9; ++v) { Ft[f][v] -= Fv[v]; Ftm[f][v] += Fvm[v]; }
           }
           Bt[f] = S[0] * Qf[f][5] + S[1] * Qf[f][6] + S[2] * Qf[f][7];
@@ -1355,12 +1377,13 @@ int sdref_polytrope(double r, double N_rho, double r_b, double r_t, double rho_b
  * conduction, dS/dr = (L / (4 pi r^2) + kappa_r rho_p C_p dT_p/dr) / (kappa rho_p T_p), is integrated
  * from S_b = S(r_b) of the polytrope, and the density from rho(r_b) = rho_b with the hydrostatic
  * drho/dr = -(rho / C_p dS/dr + (g / gamma) rho^(2 - gamma) exp(-gamma S / C_p)), g = GM / r^2;
- * then p = (rho exp(S / C_p))^gamma.  P = (N_rho, r_b, r_t, rho_b, R, noise, dipole, L, kappa, kappa_r).
+ * then p = (rho exp(S / C_p))^gamma.  P = (N_rho, r_b, r_t, rho_b, R, noise, dipole, L, kappa, kappa_r,
+ * kappa_r1, kappa_r2), kappa_r(r) = kappa_r + kappa_r1 r + kappa_r2 r^2 (reading V7).
  * Classical RK4 on nfb uniform steps over [r_b, r_t]; between the nodes cubic Hermite interpolation
  * of rho and S with the derivatives the ODE gives at the nodes. */
 typedef struct {
   int n;
-  double rb, rt, h, Cp, gam, GM, L, kappa, kappa_r, Nr, rhob, R;
+  double rb, rt, h, Cp, gam, GM, L, kappa, kappa_r, kappa_r1, kappa_r2, Nr, rhob, R;
   double *rho, *S, *drho, *dS;
 } fb_table;
 
@@ -1368,7 +1391,8 @@ static double fb_dS(const fb_table* t, double r) {
   double rp, Tp;
   sdref_polytrope(r, t->Nr, t->rb, t->rt, t->rhob, t->R, t->gam, t->GM, &rp, NULL, &Tp);
   double dTp = -t->GM / (t->Cp * r * r); /* T_p = T_b (1 - (Phi - Phi_b) / (C_p T_b)), Phi = -GM / r */
-  return (t->L / (4.0 * M_PI * r * r) + t->kappa_r * rp * t->Cp * dTp) / (t->kappa * rp * Tp);
+  double kr = t->kappa_r + t->kappa_r1 * r + t->kappa_r2 * r * r; /* reading V7 */
+  return (t->L / (4.0 * M_PI * r * r) + kr * rp * t->Cp * dTp) / (t->kappa * rp * Tp);
 }
 
 static double fb_drho(const fb_table* t, double r, double rho, double S, double dS) {
@@ -1378,7 +1402,7 @@ static double fb_drho(const fb_table* t, double r, double rho, double S, double 
 
 static void fb_build(fb_table* t, const double* P, double gam, double GM, int n) {
   t->Nr = P[0]; t->rb = P[1]; t->rt = P[2]; t->rhob = P[3]; t->R = P[4];
-  t->L = P[7]; t->kappa = P[8]; t->kappa_r = P[9];
+  t->L = P[7]; t->kappa = P[8]; t->kappa_r = P[9]; t->kappa_r1 = P[10]; t->kappa_r2 = P[11];
   t->gam = gam; t->GM = GM; t->Cp = gam * t->R / (gam - 1.0);
   t->n = n; t->h = (t->rt - t->rb) / n;
   t->rho = (double*)malloc(sizeof(double) * 4 * (n + 1));

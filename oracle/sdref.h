@@ -53,6 +53,9 @@ typedef struct {
    * inner sphere, the temperature T_top on the outer sphere; otherwise a wall takes its own F_vis */
   double q_bottom, T_top;
   int32_t visc_walls, pad3_;
+  /* radius-dependent radiative diffusivity (reading V7): kappa_r(r) = kappa_r + kappa_r1 r + kappa_r2 r^2,
+   * r = |x| at the point where the heat flux is evaluated */
+  double kappa_r1, kappa_r2;
 } sdref_phys;
 
 typedef struct {
@@ -94,7 +97,8 @@ int sdref_gradients(sdref_mesh* m, const sdref_phys* ph, const double* q, double
  * (volume, V_r, V_theta, V_phi, (B_r^2 + B_theta^2)/2, B_phi^2/2, rho, rho |U|^2/2), each times w |J| */
 int sdref_spherical_averages(sdref_mesh* m, const double* q, int n_r, int n_theta, double* out);
 /* almost flux-balanced profile (Sec. Initial Conditions) at radii r[n_r]: rho, p; P as for
- * SDREF_INIT_SHELL_FLUX_BALANCED (N_rho, r_b, r_t, rho_b, R, noise, dipole, L, kappa, kappa_r) */
+ * SDREF_INIT_SHELL_FLUX_BALANCED (N_rho, r_b, r_t, rho_b, R, noise, dipole, L, kappa, kappa_r,
+ * kappa_r1, kappa_r2): kappa_r(r) = kappa_r + kappa_r1 r + kappa_r2 r^2 */
 int sdref_flux_balanced(const double* P, double gam, double GM, int n_nodes, int n_r, const double* r, double* rho,
                         double* p);
 int sdref_residual_elements(sdref_mesh* m, const sdref_phys* ph, const double* q, int64_t n_list,

@@ -81,3 +81,30 @@ def test_state_init_uses_the_profile(oracle):
     rho, p = oracle.flux_balanced(P, r, GAMMA, GM)
     assert np.abs(q[0].ravel() / rho - 1.0).max() < 1e-14
     assert np.abs(q[4].ravel() * (GAMMA - 1.0) / p - 1.0).max() < 1e-14
+
+
+def test_entropy_gradient_with_radius_dependent_kappa_r(oracle):
+    """With kappa_r(r) = kappa_r + kappa_r1 r + kappa_r2 r^2 (reading V7) the profile's entropy gradient
+    carries the luminosity with that diffusivity at each radius."""
+    kr0, kr1, kr2 = 0.004, 0.01, -0.003
+    P = _params(L=0.02, kappa=0.05, kappa_r=kr0) + [kr1, kr2]
+    r = np.linspace(RB + 3 * H, RT - 3 * H, 41)
+    L, kappa, R = P[7], P[8], P[4]
+    cp = GAMMA * R / (GAMMA - 1.0)
+
+    def f(rr):
+        rho, p = oracle.flux_balanced(P, rr, GAMMA, GM)
+        return cp * np.log(p ** (1.0 / GAMMA) / rho)
+    dSdr = (f(r - 2 * H) - 8 * f(r - H) + 8 * f(r + H) - f(r + 2 * H)) / (12 * H)
+    want = []
+    for ri in r:
+        rho_poly, _, T_poly = oracle.polytrope(ri, 3.0, RB, RT, 1.0, R, GAMMA, GM)
+        dT = -GM / (cp * ri * ri)
+        kr = kr0 + kr1 * ri + kr2 * ri * ri
+        want.append((L / (4 * math.pi * ri * ri) + kr * rho_poly * cp * dT) / (kappa * rho_poly * T_poly))
+    want = np.array(want)
+    assert np.all(np.abs(dSdr - want) <= 1e-8 * np.abs(want)), np.abs(dSdr / want - 1.0).max()
+    # and it differs from the constant-kappa_r profile
+    rho_c, _ = oracle.flux_balanced(_params(L=0.02, kappa=0.05, kappa_r=kr0), r, GAMMA, GM)
+    rho_v, _ = oracle.flux_balanced(P, r, GAMMA, GM)
+    assert np.abs(rho_v / rho_c - 1.0).max() > 1e-4

@@ -6,6 +6,7 @@ viscous fluxes cancel between elements, so what remains is what the walls let th
 import math
 
 import numpy as np
+import pytest
 
 from paper_2502_17805_gb300 import inputs
 
@@ -153,3 +154,32 @@ def test_radial_field_walls_carry_surface_current(oracle):
     held = _resistive_integrals(oracle, rad, rad, 1)
     assert abs(held[0]) < 1e-12 * np.abs(held[1:]).max(), held
     assert np.abs(held[1:]).max() > 1e-4, held
+
+
+def _conducted_net(oracle, T_of_r, **kw):
+    """shell integral of the conductive energy residual (rho = 1, U = 0) with each wall passing its
+    own conducted flux: minus the net heat flowing out through the two spheres"""
+    m = _shell(oracle)
+    X = _points(m)
+    r = np.sqrt((X ** 2).sum(axis=-1))
+    zero = np.zeros_like(r)
+    R = 0.8
+    q = _state(X, [zero] * 3, T_of_r(r), R)
+    W = _weights(oracle, m)
+    return (W * _dR(oracle, m, q, R_gas=R, visc_walls=0, **kw)[4]).sum()
+
+
+@pytest.mark.parametrize("power", [1, 2])
+def test_radius_dependent_radiative_diffusivity(oracle, power):
+    """kappa_r(r) = k r^power (reading V7): T = A - C / ((power + 1) k r^(power + 1)) makes
+    r^2 kappa_r dT/dr constant, so as much heat leaves through the outer sphere as enters through the
+    inner one and the shell gains nothing; the same profile with a constant kappa_r (its value at mid
+    radius) does not conduct a constant flux and the shell gains or loses heat."""
+    k, A, C = 0.02, 1.0, 0.004
+    T = lambda r: A - C / ((power + 1) * k * r ** (power + 1))  # noqa: E731
+    coef = {1: dict(kappa_r1=k), 2: dict(kappa_r2=k)}[power]
+    steady = _conducted_net(oracle, T, **coef)
+    rm = 0.5 * (RB + RT)
+    flat = _conducted_net(oracle, T, kappa_r=k * rm ** power)
+    assert abs(flat) > 1e-3 * GAMMA * 0.8 / (GAMMA - 1.0) * C, flat
+    assert abs(steady) < 1e-4 * abs(flat), (steady, flat)
