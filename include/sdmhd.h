@@ -78,9 +78,10 @@ typedef enum { SD_BC_PERIODIC = 0, SD_BC_WALL_CONDUCTING = 1, SD_BC_WALL_RADIAL 
  *                          [-1, 1) keyed by (seed, e*N^3 + n); dipole B0 (3 (z.r)r - z)/r^3 scaled
  *                          so that its magnetic energy is `ratio` times the internal energy
  *  SD_INIT_DIVB_PULSE      rho, p, amplitude, cx, cy, cz, sigma: Bx Gaussian bump, U = 0
- *  SD_INIT_SHELL_FLUX_BALANCED  as SD_INIT_SHELL_POLYTROPE, then L, kappa, kappa_r: the almost
- *                          flux-balanced profile (Sec. Initial Conditions): the entropy gradient
- *                          dS/dr = (L / (4 pi r^2) + kappa_r rho_p C_p dT_p/dr) / (kappa rho_p T_p)
+ *  SD_INIT_SHELL_FLUX_BALANCED  as SD_INIT_SHELL_POLYTROPE, then L, kappa, kappa_r, kappa_r1,
+ *                          kappa_r2: the almost flux-balanced profile (Sec. Initial Conditions):
+ *                          the entropy gradient dS/dr = (L / (4 pi r^2) + kappa_r(r) rho_p C_p
+ *                          dT_p/dr) / (kappa rho_p T_p), kappa_r(r) = kappa_r + kappa_r1 r + kappa_r2 r^2,
  *                          of the polytrope rho_p, T_p, integrated from the polytrope's bottom
  *                          entropy, and the hydrostatic density drho/dr = -(rho S'/C_p +
  *                          (g/gamma) rho^(2-gamma) exp(-gamma S/C_p)) from rho_b (RK4 on 4,096
@@ -118,9 +119,10 @@ typedef struct {
   double farfield[9]; /* conserved ghost state of SD_BC_FARFIELD faces */
   /* Viscous, resistive and thermal fluxes F_vis (Sec. MHD Governing Equations; F = F_inv - F_vis),
    * with gradients of (U, T, S, B) by the BR1 scheme (Sec. SD Method), when viscous != 0 (SD_FP64
-   * only; constant coefficients):  mu dynamic viscosity (lambda = -2/3 mu), eta magnetic
-   * diffusivity, kappa thermal diffusivity of the entropy term, kappa_r radiative diffusivity,
-   * R_gas specific gas constant (T = p / (rho R_gas), C_p = gamma R_gas / (gamma - 1)).  The
+   * only):  mu dynamic viscosity (lambda = -2/3 mu), eta magnetic diffusivity, kappa thermal
+   * diffusivity of the entropy term (constants), kappa_r radiative diffusivity (with kappa_r1 and
+   * kappa_r2 below: kappa_r(r) = kappa_r + kappa_r1 r + kappa_r2 r^2, r = |x| at the point of the heat
+   * flux; the caller keeps it non-negative on the mesh), R_gas specific gas constant (T = p / (rho R_gas), C_p = gamma R_gas / (gamma - 1)).  The
    * time step of sd_step stays the inviscid one: the caller keeps cfl within the viscous limit. */
   double mu, eta, kappa, kappa_r, R_gas;
   int32_t viscous;
@@ -128,11 +130,14 @@ typedef struct {
   /* Walls of the viscous path (Sec. Problem Formulation) when visc_walls != 0: stress-free and
    * impenetrable (only the normal viscous stress acts, on the face state whose normal velocity
    * vanishes), the heat flux q_bottom (per area, into the shell) through the inner sphere and the
-   * temperature T_top held on the outer sphere (the common value of T in the BR1 gradients).  The
-   * paper's magnetic derivative conditions are not modelled.  Otherwise a wall passes its own F_vis. */
+   * temperature T_top held on the outer sphere (the common value of T in the BR1 gradients); a
+   * perfectly conducting wall keeps only the normal part of the current in the resistive terms
+   * (J = J_r r^), a radial-field wall holds B_theta = B_phi = 0 through its face state.  Otherwise a
+   * wall passes its own F_vis. */
   double q_bottom, T_top;
   int32_t visc_walls;
   int32_t pad3_;
+  double kappa_r1, kappa_r2; /* radius dependence of kappa_r (Sec. Benchmark Problem Definition) */
 } sd_phys;
 
 typedef struct {

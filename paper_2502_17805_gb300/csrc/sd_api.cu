@@ -276,6 +276,8 @@ sd::StageParams base_params(const sd_mesh* m, const sd_phys* ph, int prec) {
   P.eta = ph->eta;
   P.kappa = ph->kappa;
   P.kappa_r = ph->kappa_r;
+  P.kappa_r1 = ph->kappa_r1;
+  P.kappa_r2 = ph->kappa_r2;
   P.R_gas = ph->R_gas;
   P.visc_walls = ph->visc_walls ? 1 : 0;
   P.q_bottom = ph->q_bottom;
@@ -349,7 +351,7 @@ sd_status check_common(const sd_mesh* m, const sd_phys* ph, int prec, const sd_b
   if (ph->viscous) {
     if (prec != SD_FP64) return fail(SD_ERR_UNSUPPORTED, "viscous fluxes run on the SD_FP64 path only");
     if (!(ph->mu >= 0.0) || !(ph->eta >= 0.0) || !(ph->kappa >= 0.0) || !(ph->kappa_r >= 0.0) ||
-        !isfinite(ph->mu + ph->eta + ph->kappa + ph->kappa_r))
+        !isfinite(ph->mu + ph->eta + ph->kappa + ph->kappa_r) || !isfinite(ph->kappa_r1) || !isfinite(ph->kappa_r2))
       return fail(SD_ERR_INVALID_ARGUMENT, "viscous coefficients must be finite and non-negative");
     if (!(ph->R_gas > 0.0) || !isfinite(ph->R_gas)) return fail(SD_ERR_INVALID_ARGUMENT, "R_gas must be positive");
     if (ph->visc_walls && (!(ph->T_top > 0.0) || !isfinite(ph->T_top) || !isfinite(ph->q_bottom)))
@@ -374,7 +376,8 @@ double polytrope_p(double r, double Nr, double rb, double rt, double rhob, doubl
 // Almost flux-balanced shell profile (Sec. Initial Conditions): S and rho on
 // n + 1 uniform nodes over [r_b, r_t] with their derivatives, integrated by
 // classical RK4 from the polytrope's bottom state.  P = (N_rho, r_b, r_t, rho_b,
-// R, noise, dipole, L, kappa, kappa_r).
+// R, noise, dipole, L, kappa, kappa_r, kappa_r1, kappa_r2), the radiative
+// diffusivity kappa_r(r) = kappa_r + kappa_r1 r + kappa_r2 r^2.
 constexpr int kFluxNodes = 4096;
 
 struct FluxProfile {
@@ -384,7 +387,8 @@ struct FluxProfile {
 };
 
 FluxProfile flux_profile(const double* P, double gamma, double GM, int n) {
-  const double Nr = P[0], rb = P[1], rt = P[2], rhob = P[3], Rg = P[4], L = P[7], kap = P[8], kapr = P[9];
+  const double Nr = P[0], rb = P[1], rt = P[2], rhob = P[3], Rg = P[4], L = P[7], kap = P[8];
+  const double kr0 = P[9], kr1 = P[10], kr2 = P[11];
   FluxProfile F;
   F.n = n;
   F.rb = rb;
@@ -403,6 +407,7 @@ FluxProfile flux_profile(const double* P, double gamma, double GM, int n) {
   auto dS = [&](double r) {
     double rp, Tp, dTp;
     poly(r, rp, Tp, dTp);
+    const double kapr = kr0 + kr1 * r + kr2 * r * r;
     return (L / (4.0 * M_PI * r * r) + kapr * rp * Cp * dTp) / (kap * rp * Tp);
   };
   auto drho = [&](double r, double rho, double S, double Sp) {
@@ -699,6 +704,10 @@ sd_status sd_state_init(const sd_mesh* m, const sd_phys* ph, const sd_init* in, 
       if (!(P[8] > 0.0) || !(P[9] >= 0.0) || !isfinite(P[7]))
         return fail(SD_ERR_INVALID_ARGUMENT, "flux-balanced profile needs kappa > 0, kappa_r >= 0, finite L");
       F = flux_profile(P, ph->gamma, ph->GM, kFluxNodes);
+      for (int k = 0; k <= F.n; ++k)  // rho and S at every node
+        if (!(F.tab[k] > 0.0) || !isfinite(F.tab[k]) || !isfinite(F.tab[F.n + 1 + k]))
+          return fail(SD_ERR_INVALID_ARGUMENT,
+                      "the flux-balanced profile does not stay positive and finite with these parameters");
     }
     // magnetic energy of the unit dipole over the ideal shell: 8 pi (r_b^-3 - r_t^-3) / 3 (times 1/2 below);
     // internal energy: 4 pi / (gamma - 1) int p0 r^2 dr by 64-point Gauss-Legendre

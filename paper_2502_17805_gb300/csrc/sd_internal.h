@@ -99,6 +99,7 @@ struct StageParams {
   // face traces [e][F][24][N^2]; the gradient kernel writes grad_out / gtr_out
   int visc, visc_walls;
   double mu, eta, kappa, kappa_r, R_gas;
+  double kappa_r1, kappa_r2;  // kappa_r(r) = kappa_r + kappa_r1 r + kappa_r2 r^2
   double q_bottom, T_top;  // wall conditions of the viscous path (visc_walls)
   const double* grad;
   const double* gtr_in;

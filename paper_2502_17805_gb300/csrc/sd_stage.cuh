@@ -335,6 +335,21 @@ __global__ void __launch_bounds__(Dims<N>::BLK) stage_kernel(const StageParams P
   // viscous fluxes: this element's gradients [24][N3] after the state
   [[maybe_unused]] double* sG = reinterpret_cast<double*>(smem + S::bytes);
   [[maybe_unused]] ViscCoef vc;
+  // radiative diffusivity at point (f, a, b) of flux family d: the element's map is a polynomial
+  // of degree floor(N/2) < N, so E gives its position there exactly from the solution points
+  [[maybe_unused]] auto kr_at = [&](int d, int f, int a, int b) -> double {
+    if (!vc.kr_varies) return vc.kappa_r;
+    const double* Xe = reinterpret_cast<const double*>(P.X) + e * 3 * N3;
+    double x[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      double s = 0.0;
+#pragma unroll
+      for (int i = 0; i < N; ++i) s += sE[f * N + i] * __ldg(Xe + c * N3 + sol_index<N>(d, i, a, b));
+      x[c] = s;
+    }
+    return kappa_r_at(vc, x[0], x[1], x[2]);
+  };
   if constexpr (VISC) {
     vc = visc_coef(P);
     const double* Ge = P.grad + e * NGRAD * N3;
@@ -387,11 +402,12 @@ __global__ void __launch_bounds__(Dims<N>::BLK) stage_kernel(const StageParams P
       // or the wall conditions of visc_walls)
       double g[NGRAD], Fv[9];
       grad_face<N>(sG, sE, F, a, b, g);
+      const double kr = kr_at(d, f, a, b);  // both sides at this face point
       if (nb < 0 && P.visc_walls)
         wall_visc_flux(qo, qn, g, nx, ny, nz, meta_outer(mt) != 0, meta_bc(mt) == SD_BC_WALL_CONDUCTING, P.q_bottom,
-                       vc, Fv);
+                       vc, kr, Fv);
       else
-        visc_flux(qo, g, nx, ny, nz, vc, Fv);
+        visc_flux(qo, g, nx, ny, nz, vc, kr, Fv);
       if (nb >= 0) {
         const int code = meta_code(mt);
         const int u = (code & 4) ? b : a, w = (code & 4) ? a : b;
@@ -400,7 +416,7 @@ __global__ void __launch_bounds__(Dims<N>::BLK) stage_kernel(const StageParams P
 #pragma unroll
         for (int k = 0; k < NGRAD; ++k) g[k] = Gt[k * N2];
         double Fn[9];
-        visc_flux(qn, g, nx, ny, nz, vc, Fn);
+        visc_flux(qn, g, nx, ny, nz, vc, kr, Fn);
 #pragma unroll
         for (int v = 0; v < 9; ++v) Fv[v] = 0.5 * (Fv[v] + Fn[v]);
       }
@@ -446,7 +462,7 @@ __global__ void __launch_bounds__(Dims<N>::BLK) stage_kernel(const StageParams P
           for (int i = 0; i < N; ++i) s += sE[f * N + i] * sG[k * N3 + sol_index<N>(d, i, a, b)];
           g[k] = s;
         }
-        visc_flux(qf, g, Sx, Sy, Sz, vc, Fvis);
+        visc_flux(qf, g, Sx, Sy, Sz, vc, kr_at(d, f, a, b), Fvis);
 #pragma unroll
         for (int v = 0; v < 9; ++v) Fv[v] -= Fvis[v];
       }

@@ -24,8 +24,15 @@
 namespace sd {
 
 struct ViscCoef {
-  double gamma, mu, lam, eta, kappa, kappa_r, R, cp, inv_gamma;
+  double gamma, mu, lam, eta, kappa, kappa_r, kappa_r1, kappa_r2, R, cp, inv_gamma;
+  bool kr_varies;  // kappa_r depends on the radius
 };
+
+// radiative diffusivity at position (x, y, z): kappa_r + kappa_r1 r + kappa_r2 r^2
+__device__ __forceinline__ double kappa_r_at(const ViscCoef& c, double x, double y, double z) {
+  const double r = sqrt(x * x + y * y + z * z);
+  return c.kappa_r + c.kappa_r1 * r + c.kappa_r2 * r * r;
+}
 
 __host__ __device__ inline ViscCoef visc_coef(const StageParams& P) {
   ViscCoef c;
@@ -35,6 +42,9 @@ __host__ __device__ inline ViscCoef visc_coef(const StageParams& P) {
   c.eta = P.eta;
   c.kappa = P.kappa;
   c.kappa_r = P.kappa_r;
+  c.kappa_r1 = P.kappa_r1;
+  c.kappa_r2 = P.kappa_r2;
+  c.kr_varies = P.kappa_r1 != 0.0 || P.kappa_r2 != 0.0;
   c.R = P.R_gas;
   c.cp = P.gamma * P.R_gas / (P.gamma - 1.0);
   c.inv_gamma = 1.0 / P.gamma;
@@ -59,7 +69,7 @@ __device__ __forceinline__ void prim_w(const double* Q, const ViscCoef& c, doubl
 // F_vis contracted with the vector (nx, ny, nz), from the state Q and the
 // gradients g[3 c + j] = d w_c / d x_j
 __device__ __forceinline__ void visc_flux(const double* Q, const double* g, double nx, double ny, double nz,
-                                          const ViscCoef& c, double* F) {
+                                          const ViscCoef& c, double kr, double* F) {
   double w[8];
   prim_w(Q, c, w);
   const double n[3] = {nx, ny, nz};
@@ -85,7 +95,7 @@ __device__ __forceinline__ void visc_flux(const double* Q, const double* g, doub
   double e = 0.0;
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
-    const double qh = -c.kappa * rT * g[3 * 4 + j] - c.kappa_r * Q[0] * c.cp * g[3 * 3 + j];
+    const double qh = -c.kappa * rT * g[3 * 4 + j] - kr * Q[0] * c.cp * g[3 * 3 + j];
     e += (uT[j] - qh + c.eta * BJ[j]) * n[j];
   }
   F[0] = 0.0;
@@ -107,7 +117,7 @@ __device__ __forceinline__ void visc_flux(const double* Q, const double* g, doub
 // which a perfectly conducting wall keeps only the normal part (J = J_r r^).
 __device__ __forceinline__ void wall_visc_flux(const double* qo, const double* qn, const double* g, double nx,
                                                double ny, double nz, bool outer, bool conducting, double q_bottom,
-                                               const ViscCoef& c, double* F) {
+                                               const ViscCoef& c, double kr, double* F) {
   double qf[9], w[8];
 #pragma unroll
   for (int v = 0; v < 9; ++v) qf[v] = 0.5 * (qo[v] + qn[v]);
@@ -134,7 +144,7 @@ __device__ __forceinline__ void wall_visc_flux(const double* qo, const double* q
     const double rT = qf[0] * w[3];
     qdn = 0.0;
 #pragma unroll
-    for (int j = 0; j < 3; ++j) qdn += (-c.kappa * rT * g[3 * 4 + j] - c.kappa_r * qf[0] * c.cp * g[3 * 3 + j]) * n[j];
+    for (int j = 0; j < 3; ++j) qdn += (-c.kappa * rT * g[3 * 4 + j] - kr * qf[0] * c.cp * g[3 * 3 + j]) * n[j];
   } else {
     qdn = -q_bottom;
   }

@@ -51,7 +51,7 @@ class PhysC(C.Structure):
                 ("pad_", C.c_int32), ("farfield", C.c_double * 9), ("mu", C.c_double), ("eta", C.c_double),
                 ("kappa", C.c_double), ("kappa_r", C.c_double), ("R_gas", C.c_double), ("viscous", C.c_int32),
                 ("pad2_", C.c_int32), ("q_bottom", C.c_double), ("T_top", C.c_double), ("visc_walls", C.c_int32),
-                ("pad3_", C.c_int32)]
+                ("pad3_", C.c_int32), ("kappa_r1", C.c_double), ("kappa_r2", C.c_double)]
 
 
 class InitC(C.Structure):
@@ -108,6 +108,9 @@ class Phys:
     q_bottom: float = 0.0
     T_top: float = 1.0
     visc_walls: int = 0
+    # radiative diffusivity kappa_r(r) = kappa_r + kappa_r1 r + kappa_r2 r^2
+    kappa_r1: float = 0.0
+    kappa_r2: float = 0.0
 
     def c(self) -> PhysC:
         p = PhysC()
@@ -118,6 +121,7 @@ class Phys:
         p.mu, p.eta, p.kappa, p.kappa_r, p.R_gas = self.mu, self.eta, self.kappa, self.kappa_r, self.R_gas
         p.viscous = int(self.viscous)
         p.q_bottom, p.T_top, p.visc_walls = self.q_bottom, self.T_top, int(self.visc_walls)
+        p.kappa_r1, p.kappa_r2 = self.kappa_r1, self.kappa_r2
         return p
 
 

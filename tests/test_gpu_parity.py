@@ -362,15 +362,17 @@ def test_advance_equals_repeated_steps(prec, N):
     assert torch.equal(qc, qb_)
 
 
-def test_flux_balanced_state_and_mixed_residual():
+@pytest.mark.parametrize("kr", [(0.01,), (0.004, 0.01, -0.003)])
+def test_flux_balanced_state_and_mixed_residual(kr):
     """The almost flux-balanced initial state (host-integrated radial table, interpolated on the
-    device) against the oracle's, and the FP32-mixed residual around it as background."""
+    device) against the oracle's, with a constant or a radius-dependent kappa_r, and the FP32-mixed
+    residual around it as background."""
     N = 5
     v, h = inputs.shell_mesh(3, 2)
     gm, om = _pair(N, v, h, geom=1, r_in=0.7, r_out=0.98, bc_in=sdref.BC_WALL_CONDUCTING,
                    bc_out=sdref.BC_WALL_RADIAL)
     gph, oph = _phys(powell=1, c_h=1.0, glm_alpha=0.5, gravity=1, GM=1.0, coriolis=1, omega=1.0)
-    prm = [3.0, 0.7, 0.98, 1.0, 1.0, 1e-4, 1e-6, 0.02, 0.05, 0.01]
+    prm = [3.0, 0.7, 0.98, 1.0, 1.0, 1e-4, 1e-6, 0.02, 0.05] + list(kr)
     q0, qb = om.state_init(oph, sdref.INIT_SHELL_FLUX_BALANCED, prm, seed=3, background=True)
     gb = gm.empty_state()
     gq = gm.state_init(gph, sdmhd.INIT_SHELL_FLUX_BALANCED, prm, seed=3, background=gb)
@@ -383,3 +385,15 @@ def test_flux_balanced_state_and_mixed_residual():
     Ro, s = om.residual(oph, q0)
     ok, err, bound = mixed_ok(R, Ro, s)
     assert ok, (err, bound)
+
+
+def test_flux_balanced_profile_that_turns_negative_is_refused():
+    """A radiative diffusivity large enough that the profile's density integrates through zero is an
+    invalid argument, not a state with NaNs."""
+    N = 4
+    v, h = inputs.shell_mesh(2, 1)
+    gm = sdmhd.Mesh(N, v, h, geom=1, r_in=0.7, r_out=0.98)
+    gph = sdmhd.Phys(gravity=1, GM=1.0)
+    prm = [3.0, 0.7, 0.98, 1.0, 1.0, 1e-4, 1e-6, 0.02, 0.05, 0.01, 0.012, -0.004]
+    with pytest.raises(sdmhd.SDError, match="positive and finite"):
+        gm.state_init(gph, sdmhd.INIT_SHELL_FLUX_BALANCED, prm, seed=0)

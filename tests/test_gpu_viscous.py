@@ -134,3 +134,35 @@ def test_viscous_walls_residual(N):
     # and the walls change the residual of the wall elements
     R_own, _ = om.residual(sdref.Phys(**dict(vars(oph), visc_walls=0)), q0)
     assert np.abs(Ro - R_own).max() > 1e-3 * np.abs(Ro).max()
+
+
+VISC_R = dict(VISC, kappa_r=0.004, kappa_r1=0.012, kappa_r2=0.006)
+
+
+@pytest.mark.parametrize("N", [3, 4, 6])
+def test_radius_dependent_kappa_r_box(N):
+    """kappa_r(r) = kappa_r + kappa_r1 r + kappa_r2 r^2 at every flux, face and wall point (reading V7)."""
+    v, h, per = inputs.box_mesh(3, jitter=0.15, seed=N)
+    gm, om = _pair(N, v, h, periodic=per, geom=0)
+    gph, oph = _phys(powell=1, c_h=0.7, glm_alpha=0.3, **VISC_R)
+    q0 = inputs.random_state(gm.n_e, N, seed=60 + N)
+    R = gm.to_host(gm.residual(gph, gm.to_device(q0)))
+    Ro, s = om.residual(oph, q0)
+    # the radius dependence is a visible part of this residual
+    R1, _ = om.residual(sdref.Phys(**dict(vars(oph), kappa_r1=0.0, kappa_r2=0.0)), q0)
+    assert np.abs(Ro - R1).max() > 1e-4 * np.abs(Ro).max()
+    assert _c19(R, Ro, s) < TOL64
+
+
+@pytest.mark.parametrize("N", [4, 5])
+def test_radius_dependent_kappa_r_shell_walls(N):
+    v, h = inputs.shell_mesh(2, 2)
+    h = inputs.reorient(h, seed=7)
+    gm, om = _pair(N, v, h, geom=1, r_in=0.7, r_out=0.98, bc_in=sdref.BC_WALL_CONDUCTING,
+                   bc_out=sdref.BC_WALL_RADIAL)
+    walls = dict(VISC_R, visc_walls=1, q_bottom=0.05, T_top=0.6)
+    gph, oph = _phys(powell=1, c_h=0.8, glm_alpha=0.5, gravity=1, GM=1.0, coriolis=1, omega=1.0, **walls)
+    q0 = inputs.random_state(gm.n_e, N, seed=71)
+    R = gm.to_host(gm.residual(gph, gm.to_device(q0)))
+    Ro, s = om.residual(oph, q0)
+    assert _c19(R, Ro, s) < TOL64
