@@ -95,3 +95,48 @@ def test_packed_steps_on_a_side_stream(torch_dev):
     side = run(torch.cuda.Stream())
     for a, b in zip(plain, side):
         assert torch.equal(a, b)
+
+
+@gpu
+def test_two_meshes_from_two_threads_on_two_streams(torch_dev):
+    """Distinct mesh objects may be used from distinct host threads: two solves (N = 4 on the FP64
+    path, N = 6 on the FP32-mixed path), each from its own thread on its own stream at the same
+    time, give the same bits as each alone (no scratch, lambda slot or error state is shared)."""
+    torch = torch_dev
+    import threading
+    from paper_2502_17805_gb300 import sdmhd
+    cases = [(_shell_case(4), sdmhd.SD_FP64), (_shell_case(6), sdmhd.SD_FP32_MIXED)]
+
+    def solve(case, prec, stream, out, i):
+        (mesh, phys, q, bg), w = case, out[i][1]
+        mesh.advance(phys, 0.2, 6, out[i][0], w, prec=prec, bg=bg if prec == sdmhd.SD_FP32_MIXED else None,
+                     stream=stream)
+        out[i].append(mesh.diagnostics(phys, out[i][0], stream=stream))
+
+    alone = [[c[0][2].clone(), c[0][0].empty_state()] for c in cases]
+    for i, (case, prec) in enumerate(cases):
+        solve(case, prec, None, alone, i)
+    torch.cuda.synchronize()
+
+    both = [[c[0][2].clone(), c[0][0].empty_state()] for c in cases]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    for s in streams:
+        s.wait_stream(torch.cuda.current_stream())
+    errors = []
+
+    def worker(i):
+        try:
+            solve(cases[i][0], cases[i][1], streams[i], both, i)
+        except Exception as exc:  # reported below, on the test's thread
+            errors.append(exc)
+
+    threads = [threading.Thread(target=worker, args=(i,)) for i in range(2)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    torch.cuda.synchronize()
+    assert not errors, errors
+    for a, b in zip(alone, both):
+        assert torch.equal(a[0], b[0])
+        assert a[2] == b[2]
