@@ -334,7 +334,7 @@ __global__ void __launch_bounds__(Dims<N>::BLK) stage_kernel(const StageParams P
   load_element<N, Pol>(P, P.q_in, e, sQ, nullptr);
   // viscous fluxes: this element's gradients [24][N3] after the state
   [[maybe_unused]] double* sG = reinterpret_cast<double*>(smem + S::bytes);
-  [[maybe_unused]] ViscCoef vc;
+  [[maybe_unused]] ViscCoef vc{};  // set below in the viscous instances, the only ones that read it
   // radiative diffusivity at point (f, a, b) of flux family d: the element's map is a polynomial
   // of degree floor(N/2) < N, so E gives its position there exactly from the solution points
   [[maybe_unused]] auto kr_at = [&](int d, int f, int a, int b) -> double {
