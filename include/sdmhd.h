@@ -333,7 +333,9 @@ sd_status sd_step_packed(sd_packer* packer, int32_t n, const sd_step_req* reqs, 
 /* Global diagnostics of q in FP64 (Sec. Results: KE, E_B), with the discrete
  * div B of the residual (BR1 face average) for max|div B|.  Sums run in a fixed
  * order (deterministic).  Synchronises `stream`; returns SD_ERR_NONPHYSICAL
- * (with *out filled) when rho <= 0, p <= 0 or a NaN is found. */
+ * (with *out filled) when rho <= 0, p <= 0 or a NaN is found, and
+ * SD_ERR_TIMEOUT (*out not filled) when a bounded device-side wait of a stage
+ * kernel on this mesh ran out since the previous sd_diagnostics call. */
 sd_status sd_diagnostics(const sd_mesh* mesh, const sd_phys* phys, const double* q, sd_diag* out, void* stream);
 
 /* sd_residual_noalloc -- the FP64 residual of sd_residual (same result within
@@ -355,6 +357,16 @@ sd_status sd_diagnostics(const sd_mesh* mesh, const sd_phys* phys, const double*
  * viscous set is rejected with SD_ERR_UNSUPPORTED (the viscous fluxes need
  * gradient buffers).  Asynchronous. */
 sd_status sd_residual_noalloc(const sd_mesh* mesh, const sd_phys* phys, const double* q, double* dqdt, void* stream);
+
+/* Failure-detection test hook: the number of polls a stage kernel makes on
+ * each of its bounded device-side waits (the shared-memory bulk copies of the
+ * FP32-mixed stages) before it records a time-out.  spins < 0 restores the
+ * default (65536 polls, about a millisecond).  A wait that runs out still lets
+ * its copies land before the kernel goes on (a second bounded wait), so the
+ * results stay valid; the time-out is recorded in the mesh's error word, which
+ * the next sd_diagnostics call reports as SD_ERR_TIMEOUT and then clears.
+ * With spins = 0 every wait of the next stage launches runs out at once. */
+sd_status sd_mesh_set_wait_limit(sd_mesh* mesh, int32_t spins);
 
 /* Kernel timing (tracing): with enable = 1 every kernel the library launches
  * for this mesh is bracketed by CUDA events on its launching stream; the

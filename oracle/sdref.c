@@ -8,7 +8,7 @@
  * concession is an OpenMP loop over independent elements, which changes no
  * arithmetic).
  *
- * Readings of passages the paper leaves open (each also listed in the design notes):
+ * Readings of passages the paper leaves open:
  *  R1 flux points: the N+1 points {0, roots of the Legendre polynomial P_{N-1}
  *     mapped to [0,1], 1}; the paper's "N-th degree" would give N+2 points,
  *     contradicting the N+1 flux points per line it requires (Sec. SD Method).

@@ -271,6 +271,7 @@ sd::StageParams base_params(const sd_mesh* m, const sd_phys* ph, int prec) {
   P.nbr = m->nbr;
   P.meta = m->meta;
   P.err = m->err;
+  P.wait_spins = m->wait_spins;
   P.visc = ph->viscous ? 1 : 0;
   P.mu = ph->mu;
   P.eta = ph->eta;
@@ -590,6 +591,7 @@ sd_status sd_mesh_create(const sd_mesh_desc* desc, void* stream, sd_mesh** out) 
   m->n_if = n_if;
   m->h_min = hmin;
   m->geom = desc->geom;
+  m->wait_spins = sd::kWaitSpins;
   build_ops(N, m->ops64);
   ops_to_f32(m->ops64, m->ops32);
   const int64_t N2 = (int64_t)N * N, N3 = N2 * N, NF = N + 1;
@@ -1115,8 +1117,12 @@ sd_status sd_diagnostics(const sd_mesh* m, const sd_phys* ph, const double* q, s
   SD_CUDA(cudaMemcpyAsync(mm->host_diag, mm->diag_out, 10 * sizeof(double), cudaMemcpyDeviceToHost, s));
   SD_CUDA(cudaMemcpyAsync(mm->host_diag + 10, mm->err, sizeof(int), cudaMemcpyDeviceToHost, s));
   SD_CUDA(cudaStreamSynchronize(s));
-  if (*reinterpret_cast<const int*>(mm->host_diag + 10) != 0)
-    return fail(SD_ERR_TIMEOUT, "a bounded device-side wait of a stage kernel ran out since the mesh was created");
+  if (*reinterpret_cast<const int*>(mm->host_diag + 10) != 0) {
+    // reported once: the word is cleared for the calls that follow
+    SD_CUDA(cudaMemsetAsync(mm->err, 0, sizeof(int), s));
+    SD_CUDA(cudaStreamSynchronize(s));
+    return fail(SD_ERR_TIMEOUT, "a bounded device-side wait of a stage kernel ran out since the last sd_diagnostics call");
+  }
   const double* h = mm->host_diag;
   const double vol = h[4];
   out->ke = h[0] / vol;
@@ -1131,6 +1137,12 @@ sd_status sd_diagnostics(const sd_mesh* m, const sd_phys* ph, const double* q, s
   if (h[9] > 0.0 || h[5] != h[5] || h[6] != h[6])
     return fail(SD_ERR_NONPHYSICAL, "non-physical state: rho <= 0, p <= 0 or NaN at " +
                                         std::to_string((long long)h[9]) + " solution points");
+  return SD_OK;
+}
+
+sd_status sd_mesh_set_wait_limit(sd_mesh* m, int32_t spins) {
+  if (!m) return fail(SD_ERR_INVALID_ARGUMENT, "mesh is NULL");
+  m->wait_spins = spins < 0 ? sd::kWaitSpins : spins;
   return SD_OK;
 }
 

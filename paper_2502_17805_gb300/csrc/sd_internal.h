@@ -94,6 +94,7 @@ struct StageParams {
   // packed trace launch: this request's traces are already current, the CTA returns at once
   int skip;
   int* err;  // device error word (bounded waits that ran out)
+  int wait_spins;  // polls of a bounded wait before it reports a time-out
   // viscous, resistive and thermal fluxes (FP64 policy): coefficients, the gradients of
   // (U, T, S, B) at the solution points [e][24][N^3] (grad[3c + j] = d w_c / d x_j) and their
   // face traces [e][F][24][N^2]; the gradient kernel writes grad_out / gtr_out
@@ -137,6 +138,7 @@ struct sd_mesh {
   double* divb;             // [n_e * N^3]
   double* host_diag;        // pinned [12]
   int* err;                 // device error word of the stage kernels
+  int wait_spins;           // polls of a stage kernel's bounded wait before a time-out (sd_mesh_set_wait_limit)
   double* grad;             // viscous path, allocated on first use: gradients [e][24][N^3]
   double* gtr;              //   and their face traces [e][F][24][N^2]
   int64_t device_bytes;
@@ -161,6 +163,8 @@ struct sd_background {
 };
 
 namespace sd {
+// polls of a bounded mbarrier wait before it reports a time-out (about a millisecond)
+constexpr int kWaitSpins = 1 << 16;
 // partial maxima of lambda per mesh: the warps of a launch spread their atomics over these
 constexpr int LAM_SLOTS = 256;
 // gradients the viscous fluxes need: 8 primitive variables x 3 directions, index 3 c + j

@@ -102,6 +102,8 @@ sd_status sd_residual_noalloc(const sd_mesh* m, const sd_phys* ph, const double*
   P.X = m->X64;
   P.nbr = m->nbr;
   P.meta = m->meta;
+  P.err = m->err;
+  P.wait_spins = m->wait_spins;
   // every trace entry the second kernel reads is written by the first, so the
   // scratch needs no clearing between calls
   P.q_in = q;

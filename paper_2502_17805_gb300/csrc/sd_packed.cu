@@ -73,7 +73,11 @@ struct sd_packer {
   int64_t* d_off[2];
   sd::StepCtl* h_ctl[2];
   sd::StepCtl* d_ctl[2];
+  // copied[b]: the host tables of buffer b have reached the device (the host may
+  // refill them); read[b]: the kernels of the last call on buffer b have run (the
+  // device tables may be overwritten, on whichever stream the next call uses)
   cudaEvent_t copied[2];
+  cudaEvent_t read[2];
   bool used[2];
   int device;
 };
@@ -94,6 +98,7 @@ void free_packer(sd_packer* p) {
     if (p->d_off[b]) cudaFree(p->d_off[b]);
     if (p->d_ctl[b]) cudaFree(p->d_ctl[b]);
     if (p->copied[b]) cudaEventDestroy(p->copied[b]);
+    if (p->read[b]) cudaEventDestroy(p->read[b]);
   }
   delete p;
 }
@@ -120,6 +125,7 @@ sd_status sd_packer_create(int32_t max_requests, sd_packer** out) {
     if (err == cudaSuccess) err = cudaMalloc((void**)&p->d_off[b], noff * sizeof(int64_t));
     if (err == cudaSuccess) err = cudaMalloc((void**)&p->d_ctl[b], max_requests * sizeof(sd::StepCtl));
     if (err == cudaSuccess) err = cudaEventCreateWithFlags(&p->copied[b], cudaEventDisableTiming);
+    if (err == cudaSuccess) err = cudaEventCreateWithFlags(&p->read[b], cudaEventDisableTiming);
   }
   if (err != cudaSuccess) {
     free_packer(p);
@@ -134,7 +140,10 @@ sd_status sd_packer_create(int32_t max_requests, sd_packer** out) {
 sd_status sd_packer_destroy(sd_packer* p) {
   if (!p) return SD_OK;
   for (int b = 0; b < 2; ++b)
-    if (p->used[b]) cudaEventSynchronize(p->copied[b]);
+    if (p->used[b]) {
+      cudaEventSynchronize(p->copied[b]);
+      cudaEventSynchronize(p->read[b]);
+    }
   free_packer(p);
   return SD_OK;
 }
@@ -235,6 +244,7 @@ sd_status sd_step_packed(sd_packer* pk, int32_t n, const sd_step_req* reqs, void
     P.bg_jump = r.bg->jump;
     P.dyn = r.dyn;
     P.err = m->err;
+    P.wait_spins = m->wait_spins;
     // trace (+lambda) of q into A (skipped when the previous call left them there)
     sd::StageParams Pt = P;
     Pt.q_in = r.q;
@@ -282,7 +292,10 @@ sd_status sd_step_packed(sd_packer* pk, int32_t n, const sd_step_req* reqs, void
   off_pos += (groups.back().k1 - groups.back().k0) + 1;
 
   cudaStream_t s = (cudaStream_t)stream;
-  cudaError_t err = cudaMemcpyAsync(pk->d_tab[b], T, 4 * (size_t)n * sizeof(sd::StageParams), cudaMemcpyHostToDevice, s);
+  // the device tables of buffer b may still be read by the kernels of the call
+  // before last, which may have run on another stream
+  cudaError_t err = pk->used[b] ? cudaStreamWaitEvent(s, pk->read[b], 0) : cudaSuccess;
+  if (err == cudaSuccess) err = cudaMemcpyAsync(pk->d_tab[b], T, 4 * (size_t)n * sizeof(sd::StageParams), cudaMemcpyHostToDevice, s);
   if (err == cudaSuccess) err = cudaMemcpyAsync(pk->d_off[b], OFF, off_pos * sizeof(int64_t), cudaMemcpyHostToDevice, s);
   if (err == cudaSuccess) err = cudaMemcpyAsync(pk->d_ctl[b], CTL, n * sizeof(sd::StepCtl), cudaMemcpyHostToDevice, s);
   if (err == cudaSuccess) err = cudaEventRecord(pk->copied[b], s);
@@ -315,6 +328,7 @@ sd_status sd_step_packed(sd_packer* pk, int32_t n, const sd_step_req* reqs, void
       err = sd::launch_packed_mixed(g.N, st == 2 ? 2 : 1, pk->d_tab[b] + (1 + st) * n + g.k0, pk->d_off[b] + g.off0, ng,
                                     blocks, reqs[order[g.k0]].mesh->ops32, s);
     }
+  if (err == cudaSuccess) err = cudaEventRecord(pk->read[b], s);
   if (err != cudaSuccess) return pk_fail(SD_ERR_CUDA, std::string("packed launch: ") + cudaGetErrorString(err));
   return SD_OK;
 }

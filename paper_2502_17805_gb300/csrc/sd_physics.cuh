@@ -308,12 +308,13 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
   return ok != 0;
 }
 
-// Bounded wait on phase `phase` of the barrier.  On time-out (or once another
-// CTA has reported one in the kernel's error word) the error word is set and
-// the wait continues, again bounded, so that no copy is still writing this
-// CTA's shared memory when it exits.  Returns false on time-out.
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned phase, int* err) {
-  for (int it = 0; it < (1 << 16); ++it) {
+// Bounded wait on phase `phase` of the barrier: at most `spins` polls.  On
+// time-out (or once another CTA has reported one in the kernel's error word)
+// the error word is set and the wait continues, again bounded, so that no copy
+// is still writing this CTA's shared memory when it exits.  Returns false on
+// time-out.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned phase, int* err, int spins) {
+  for (int it = 0; it < spins; ++it) {
     if (mbar_try_wait(bar, phase)) return true;
     if ((it & 255) == 255 && err && *reinterpret_cast<volatile int*>(err)) break;
   }

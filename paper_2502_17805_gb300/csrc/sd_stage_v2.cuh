@@ -201,9 +201,9 @@ __device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops<fl
   const double inv_gm1 = P.inv_gm1;
   if constexpr (qtma) {
     // q', rho0, p0 are in sQ once qbar completes; add D
-    mbar_wait_bounded(&qbar, 0u, P.err);
+    mbar_wait_bounded(&qbar, 0u, P.err, P.wait_spins);
     if (lsr) {
-      mbar_wait_bounded(&dbar, 0u, P.err);
+      mbar_wait_bounded(&dbar, 0u, P.err, P.wait_spins);
       for (int n = tid; n < N3; n += T) {
 #pragma unroll
         for (int v = 0; v < 9; ++v) sQ[v * N3 + n] += sDs[v * DV::DSTRIDE + n];
@@ -225,7 +225,7 @@ __device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops<fl
         qv[r][10] = __ldg(P.bg + n_e * N3 + gb);
       }
     }
-    if (lsr) mbar_wait_bounded(&dbar, 0u, P.err);
+    if (lsr) mbar_wait_bounded(&dbar, 0u, P.err, P.wait_spins);
 #pragma unroll
     for (int r = 0; r < NRA; ++r) {
       const int n = tid + r * T;
@@ -429,8 +429,8 @@ __device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops<fl
   // separate trace pass over the output, bit for bit.
   constexpr bool exact = EXACT;
   float lam = 0.0f;  // maximum of FP32 speeds (taken in FP32, converted once when reduced)
-  if (lsr && !incr) mbar_wait_bounded(&dbar, 0u, P.err);
-  if (DV::STAGE_G) mbar_wait_bounded(&gbar, 0u, P.err);
+  if (lsr && !incr) mbar_wait_bounded(&dbar, 0u, P.err, P.wait_spins);
+  if (DV::STAGE_G) mbar_wait_bounded(&gbar, 0u, P.err, P.wait_spins);
   for (int n = tid; n < N3; n += T) {
     const int i0 = n % N, j0 = (n / N) % N, k0 = n / N2;
     const float* D0 = sX + ((0 * NF + i0) * 11) * N2 + (j0 + N * k0);

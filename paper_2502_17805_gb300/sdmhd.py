@@ -29,7 +29,7 @@ STATUS = {0: "SD_OK", 1: "SD_ERR_INVALID_ARGUMENT", 2: "SD_ERR_UNSUPPORTED", 3: 
 EXPORTS = ["sd_last_error", "sd_mesh_create", "sd_mesh_destroy", "sd_mesh_query", "sd_state_init",
            "sd_background_create", "sd_background_destroy", "sd_residual", "sd_rk_stage", "sd_step", "sd_advance",
            "sd_diagnostics", "sd_spherical_sums", "sd_profile_enable", "sd_profile_read", "sd_residual_noalloc",
-           "sd_packer_create", "sd_packer_destroy", "sd_step_packed"]
+           "sd_packer_create", "sd_packer_destroy", "sd_step_packed", "sd_mesh_set_wait_limit"]
 
 
 class SDError(RuntimeError):
@@ -151,6 +151,7 @@ def lib():
         L.sd_spherical_sums.argtypes = [vp, vp, C.c_double, C.c_double, C.c_int32, C.c_int32, vp, vp]
         L.sd_diagnostics.argtypes = [vp, C.POINTER(PhysC), vp, C.POINTER(DiagC), vp]
         L.sd_profile_enable.argtypes = [vp, C.c_int32]
+        L.sd_mesh_set_wait_limit.argtypes = [vp, C.c_int32]
         L.sd_profile_read.argtypes = [vp, C.POINTER(ProfileC)]
         L.sd_residual_noalloc.argtypes = [vp, C.POINTER(PhysC), vp, vp, vp]
         L.sd_packer_create.argtypes = [C.c_int32, C.POINTER(vp)]
@@ -305,6 +306,11 @@ class Mesh:
         _check(lib().sd_spherical_sums(self._h, _ptr(q), float(r_min), float(r_max), int(n_r), int(n_theta),
                                        _ptr(out), _stream(stream)))
         return out
+
+    def set_wait_limit(self, spins: int = -1):
+        """Polls of a stage kernel's bounded waits before a time-out (failure-detection test
+        hook); -1 restores the default."""
+        _check(lib().sd_mesh_set_wait_limit(self._h, int(spins)))
 
     def profile(self, enable: bool = True):
         """Start (or stop) CUDA-event timing of every kernel the library launches for this mesh."""

@@ -148,20 +148,22 @@ class Server:
         for r in requests:
             self.mesh(r.nz, r.nr, r.N)
 
-    def run(self, requests: Sequence[Request], depth: int = 2) -> dict:
+    def run(self, requests: Sequence[Request], depth: int = 2, states: Optional[dict] = None) -> dict:
         """Serve `requests` (arrival times relative to the call) to completion.
 
         Ticks are issued without waiting for the device: up to `depth` ticks are in
         flight, and admitting a request (initial state, background tables) only
         enqueues work, so the host prepares the next tick while the device runs the
         current one.  A request's completion time is the device time of the event
-        recorded after its last tick."""
+        recorded after its last tick.  With `states` (a dict), each finished
+        request's final device state is stored there under its rid."""
         import torch
         pending = sorted(requests, key=lambda r: r.arrival)
         queue: List[Request] = []
         running: List[Tuple[_Running, int]] = []
-        inflight: list = []  # (event, requests completing at that tick, their _Running objects)
-        used = 0
+        # (event, requests completing at that tick, their _Running objects, their footprint)
+        inflight: list = []
+        used = 0  # footprint of the running requests and of finished ones still held by a tick in flight
         finished: List[Request] = []
         stream = torch.cuda.current_stream()
         torch.cuda.synchronize()
@@ -170,8 +172,13 @@ class Server:
         t0 = time.perf_counter()
 
         def retire_oldest():
-            ev, reqs, _runs = inflight.pop(0)
+            nonlocal used
+            ev, reqs, runs_done, fp_done = inflight.pop(0)
             ev.synchronize()
+            used -= fp_done  # their tensors are dropped with this tick's record
+            if states is not None:
+                for run in runs_done:
+                    states[run.req.rid] = run.q
             t_done = ev0.elapsed_time(ev) / 1e3
             for r in reqs:
                 r.done = t_done
@@ -183,12 +190,14 @@ class Server:
             while i < len(pending) and pending[i].arrival <= now:
                 queue.append(pending[i])
                 i += 1
-            # admission: FIFO while the footprint fits (a lone request is always admitted)
+            # admission: FIFO while the footprint fits next to the running requests and the finished
+            # ones whose memory a tick in flight still holds (a request is always admitted when
+            # nothing else holds memory)
             while queue and len(running) < self.max_running:
                 r = queue[0]
                 m = self.mesh(r.nz, r.nr, r.N)
                 fp = footprint_bytes(m.info, m.info["n_points"])
-                if running and used + fp > self.budget:
+                if used > 0 and used + fp > self.budget:
                     break
                 queue.pop(0)
                 r.admitted = time.perf_counter() - t0
@@ -206,17 +215,17 @@ class Server:
             ev = torch.cuda.Event(enable_timing=True)
             ev.record(stream)
             self.ticks += 1
-            keep, done_reqs, done_runs = [], [], []
+            keep, done_reqs, done_runs, fp_done = [], [], [], 0
             for run, fp in running:
                 run.advanced()
                 if run.steps_done >= run.req.steps:
                     done_reqs.append(run.req)
                     done_runs.append(run)  # released (stream-ordered) once retired
-                    used -= fp
+                    fp_done += fp
                 else:
                     keep.append((run, fp))
             running = keep
-            inflight.append((ev, done_reqs, done_runs))
+            inflight.append((ev, done_reqs, done_runs, fp_done))
             if len(inflight) >= depth:
                 retire_oldest()
         wall = max(r.done for r in finished) if finished else time.perf_counter() - t0

@@ -4,10 +4,11 @@ Inputs come from the oracle or the seeded input generators only.  Tolerances:
   FP64 residual:  |g - o| <= 1e-12 (|o| + s_v) per entry, s_v the oracle's
                   un-cancelled magnitude of variable v (sum |D F| / |J| + |M|);
   FP64 states:    1e-12 of the variable's magnitude after one stage or step;
-  FP32-mixed:     max |g - o| <= 1e-5 max |o| + 4 eps32 s_v per variable
-                  (eps32 = 2^-24): 1e-5 relative, except that a component whose
-                  residual cancels to below FP32 resolution of its terms (the
-                  energy of a fluid at rest) is held to FP32 round-off of them.
+  FP32-mixed:     max |g - o| <= 1e-5 max |o| per variable (1e-5 relative,
+                  normwise per variable).  Only the variables a test names in
+                  `floor` may add 4 eps32 s_v (eps32 = 2^-24): components whose
+                  residual cancels to below FP32 resolution of their own terms,
+                  each named with its reason at the test.
 """
 import math
 
@@ -45,10 +46,28 @@ def _phys(**kw):
 EPS32 = 2.0 ** -24
 
 
-def mixed_ok(g, o, s, scale=1.0):
-    """per-variable FP32-mixed bound; g, o: (9, ...) arrays; s: (9,) un-cancelled magnitudes"""
+VARS = ("rho", "mx", "my", "mz", "E", "Bx", "By", "Bz", "psi")
+# The residual of the energy of a fluid at rest (U = 0): R_E is the Rusanov dissipation of face
+# jumps of E that are themselves at the discretisation error (~1e-12 of E); the FP32 split into a
+# rounded background and an FP32 perturbation resolves it only to a few eps32 of its terms.  Only
+# the residual tests of a state at rest take this floor; every stage, step and advance test holds
+# all nine variables to 1e-5 of their change outright.
+AT_REST_FLOOR = (4,)
+
+
+def mixed_ok(g, o, s, scale=1.0, floor=(), label=""):
+    """Per-variable FP32-mixed bound max|g - o| <= 1e-5 max|o|; the variables in `floor` may add
+    4 eps32 scale s_v.  g, o: (9, ...) arrays; s: (9,) un-cancelled magnitudes.  Prints the plain
+    ratio max|g - o| / (1e-5 max|o|) of every variable."""
     err = np.abs(g - o).reshape(9, -1).max(axis=1)
-    bound = 1e-5 * np.abs(o).reshape(9, -1).max(axis=1) + 4 * EPS32 * scale * s
+    strict = 1e-5 * np.abs(o).reshape(9, -1).max(axis=1)
+    fl = np.zeros(9)
+    idx = list(floor)
+    fl[idx] = 4 * EPS32 * scale * np.asarray(s, dtype=np.float64).reshape(9)[idx]
+    bound = strict + fl
+    ratio = err / np.maximum(strict, 1e-300)
+    print("mixed %s: max|g-o|/(1e-5 max|o|) = %s; floor on %s" % (
+        label, " ".join("%s %.2e" % (n, r) for n, r in zip(VARS, ratio)), [VARS[i] for i in idx]))
     return bool(np.all(err <= bound)), err, bound
 
 
@@ -56,10 +75,19 @@ def _rel_c19(g, o, s):
     return float((np.abs(g - o) / (np.abs(o) + s[:, None, None])).max())
 
 
-def _residual_parity(gm, om, gph, oph, q0):
+def _rel_plain(g, o):
+    """max |g - o| / max |o| per variable, no cancellation scale"""
+    return np.abs(g - o).reshape(9, -1).max(axis=1) / np.maximum(np.abs(o).reshape(9, -1).max(axis=1), 1e-300)
+
+
+def _residual_parity(gm, om, gph, oph, q0, plain_tol=None):
     R = gm.to_host(gm.residual(gph, gm.to_device(q0)))
     torch.cuda.synchronize()
     Ro, s = om.residual(oph, q0)
+    plain = _rel_plain(R, Ro)
+    print("fp64 residual: c19 %.2e, plain per variable %s" % (_rel_c19(R, Ro, s), " ".join("%.1e" % x for x in plain)))
+    if plain_tol is not None:
+        assert plain.max() < plain_tol, plain
     return _rel_c19(R, Ro, s)
 
 
@@ -69,6 +97,8 @@ def test_residual_box_alfven_all_orders(N):
     gm, om = _pair(N, v, inputs.reorient(h, seed=N), periodic=per, geom=0)
     gph, oph = _phys(powell=1, c_h=0.8, glm_alpha=0.3)
     q0 = om.state_init(oph, sdref.INIT_ALFVEN, ALFVEN)
+    # the wave's rho, E and psi residuals vanish up to the discretisation error (k.U = 0, U.B and
+    # |B| uniform): only the c19 measure applies to them, the plain one is printed
     assert _residual_parity(gm, om, gph, oph, q0) < TOL64
 
 
@@ -78,7 +108,7 @@ def test_residual_random_state_box():
     gm, om = _pair(N, v, inputs.reorient(h, seed=4), periodic=per, geom=0)
     gph, oph = _phys(powell=1, c_h=0.6, glm_alpha=0.4)
     q0 = inputs.random_state(gm.n_e, N, seed=11)
-    assert _residual_parity(gm, om, gph, oph, q0) < TOL64
+    assert _residual_parity(gm, om, gph, oph, q0, plain_tol=TOL64) < TOL64
 
 
 @pytest.mark.parametrize("N", [2, 3, 4, 5, 6, 7, 8])
@@ -89,7 +119,7 @@ def test_residual_shell_walls_all_sources(N):
                    bc_out=sdref.BC_WALL_RADIAL)
     gph, oph = _phys(powell=1, c_h=0.9, glm_alpha=0.5, gravity=1, GM=1.0, coriolis=1, omega=1.3)
     q0 = inputs.random_state(gm.n_e, N, seed=6)
-    assert _residual_parity(gm, om, gph, oph, q0) < TOL64
+    assert _residual_parity(gm, om, gph, oph, q0, plain_tol=TOL64) < TOL64
     q1 = om.state_init(oph, sdref.INIT_SHELL_POLYTROPE, [2.0, 0.7, 0.98, 1.0, 1.0, 1e-4, 1e-3], seed=3)
     assert _residual_parity(gm, om, gph, oph, q1) < TOL64
 
@@ -245,7 +275,7 @@ def test_mixed_residual_stratified_shell(N):
     bg = gm.background(gph, gm.to_device(qb))
     R = gm.to_host(gm.residual(gph, gm.to_device(q0), prec=sdmhd.SD_FP32_MIXED, bg=bg))
     Ro, s = om.residual(oph, q0)
-    ok, err, bound = mixed_ok(R, Ro, s)
+    ok, err, bound = mixed_ok(R, Ro, s, floor=AT_REST_FLOOR, label="residual at rest N=%d" % N)
     assert ok, (err, bound)
 
 
@@ -265,7 +295,7 @@ def test_mixed_residual_random_background_periodic_box(N):
     bg = gm.background(gph, gm.to_device(qb))
     R = gm.to_host(gm.residual(gph, gm.to_device(q0), prec=sdmhd.SD_FP32_MIXED, bg=bg))
     Ro, s = om.residual(oph, q0)
-    ok, err, bound = mixed_ok(R, Ro, s)
+    ok, err, bound = mixed_ok(R, Ro, s, label="residual random background N=%d" % N)
     assert ok, (err, bound)
 
 
@@ -296,7 +326,7 @@ def test_mixed_stage_stratified_shell(N):
     qo = om.rk_step(oph, dt, q0)
     # compare the change over the step, per variable (three stages of dt R)
     _, s = om.residual(oph, q0)
-    ok, err, bound = mixed_ok(gm.to_host(q) - q0, qo - q0, s, scale=3 * dt)
+    ok, err, bound = mixed_ok(gm.to_host(q) - q0, qo - q0, s, label="rk_stage step N=%d" % N)
     assert ok, (err, bound)
 
 
@@ -333,7 +363,39 @@ def test_mixed_sd_step_low_storage_matches_oracle(N):
         oph.c_h = float(ch)
         qo = om.rk_step(oph, float(dt), qo)
     _, s = om.residual(oph, q0)
-    ok, err, bound = mixed_ok(gm.to_host(q) - q0, qo - q0, s, scale=3 * 3 * float(dt))
+    ok, err, bound = mixed_ok(gm.to_host(q) - q0, qo - q0, s, label="sd_step x3 N=%d" % N)
+    assert ok, (err, bound)
+
+
+def _developed(q0, seed=17, amp=1e-2):
+    """q0 with a seeded velocity field U ~ amp U[-1, 1] per component (momentum rho U): every residual
+    component, B and psi included (the induction of the seed field), is far above FP32 resolution"""
+    rng = np.random.default_rng(seed)
+    q1 = q0.copy()
+    mom = rng.uniform(-amp, amp, size=q1[1:4].shape) * q1[0]
+    q1[1:4] += mom
+    q1[4] += 0.5 * (mom ** 2).sum(axis=0) / q1[0]  # kinetic energy of the added flow, pressure unchanged
+    return q1
+
+
+@pytest.mark.parametrize("N", [2, 3, 4, 5, 6, 7, 8])
+def test_mixed_sd_step_developed_flow_strict(N):
+    """Three FP32-mixed sd_step steps from the stratified shell with a seeded flow: every variable's
+    change over the steps within 1e-5 of its largest value, no floor."""
+    gm, om, gph, oph, q0, qb = _mixed_case(3, 2, N, 2.5, seed=9)
+    q0 = _developed(q0, seed=N)
+    bg = gm.background(gph, gm.to_device(qb))
+    gph.c_h = 0.0
+    q, work = gm.to_device(q0), gm.empty_state()
+    dts = torch.zeros(2, dtype=torch.float64, device="cuda")
+    qo = q0
+    for _ in range(3):
+        gm.step(gph, 0.2, q, work, prec=sdmhd.SD_FP32_MIXED, bg=bg, dt_out=dts)
+        dt, ch = dts.cpu().numpy()
+        oph.c_h = float(ch)
+        qo = om.rk_step(oph, float(dt), qo)
+    _, s = om.residual(oph, q0)
+    ok, err, bound = mixed_ok(gm.to_host(q) - q0, qo - q0, s, label="sd_step x3 developed N=%d" % N)
     assert ok, (err, bound)
 
 
@@ -383,7 +445,7 @@ def test_flux_balanced_state_and_mixed_residual(kr):
     bg = gm.background(gph, gm.to_device(qb))
     R = gm.to_host(gm.residual(gph, gm.to_device(q0), prec=sdmhd.SD_FP32_MIXED, bg=bg))
     Ro, s = om.residual(oph, q0)
-    ok, err, bound = mixed_ok(R, Ro, s)
+    ok, err, bound = mixed_ok(R, Ro, s, floor=AT_REST_FLOOR, label="residual flux-balanced")
     assert ok, (err, bound)
 
 

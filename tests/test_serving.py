@@ -112,10 +112,11 @@ def test_packed_step_matches_the_oracle(torch_dev):
                      coriolis=1)
     qo = om.rk_step(oph, float(dt), q_before)
     dg, do = run.mesh.to_host(run.q) - q_before, qo - q_before
-    _, s = om.residual(oph, q_before)
+    # every variable within 1e-5 of its largest change over the step
     err = np.abs(dg - do).max(axis=(1, 2))
-    bound = 1e-5 * np.abs(do).max(axis=(1, 2)) + 4 * 2.0 ** -24 * 3 * float(dt) * s
-    assert np.all(err <= bound), (err, bound)
+    strict = 1e-5 * np.abs(do).max(axis=(1, 2))
+    print("packed step vs oracle: max|g-o|/(1e-5 max|change|) = %s" % (err / strict))
+    assert np.all(err <= strict), (err, strict)
     lam = om.diagnostics(oph, q_before)["lambda_max"]
     xs = sdref.nodes(req.N)[0]
     assert abs(dt / (req.cfl * om.info()["h_min"] * (xs[1] - xs[0]) / lam) - 1.0) < 1e-6
@@ -177,3 +178,57 @@ def test_unknown_request_flags_are_refused(torch_dev):
 def test_an_empty_pack_is_a_no_op(torch_dev):
     srv = serve.Server(hbm_budget_bytes=1 << 34, max_running=4)
     srv.packer.step([])
+
+
+@gpu
+def test_staggered_arrivals_give_each_result_alone(torch_dev):
+    """Requests arriving while others run (staggered arrival times through Server.run, so they join
+    at different ticks and share launches with different partners) end with the same bits as each
+    request run alone."""
+    torch = torch_dev
+    srv = serve.Server(hbm_budget_bytes=1 << 34, max_running=8)
+    shapes = [(2, 2, 4), (3, 2, 6), (4, 1, 5), (2, 1, 4), (3, 1, 6), (2, 2, 5)]
+    reqs = [serve.Request(rid=i, nz=nz, nr=nr, N=N, n_rho=1.2 + 0.3 * i, omega=0.6 + 0.2 * i, seed=10 + i,
+                          steps=6 + (i % 3), arrival=0.004 * i)
+            for i, (nz, nr, N) in enumerate(shapes)]
+    srv.warm(reqs)
+    alone = {r.rid: srv.final_state(serve.Request(**{k: getattr(r, k) for k in
+                                                     ("rid", "nz", "nr", "N", "n_rho", "omega", "seed", "steps",
+                                                      "arrival")})).clone() for r in reqs}
+    states = {}
+    out = srv.run(reqs, states=states)
+    torch.cuda.synchronize()
+    assert out["requests"] == len(reqs) and sorted(states) == sorted(alone)
+    for rid, q in states.items():
+        assert torch.equal(q, alone[rid]), rid
+
+
+@gpu
+def test_packed_calls_alternating_streams(torch_dev):
+    """Consecutive sd_step_packed calls on two streams in turn (the packer's double-buffered device
+    tables are then reused by a call on another stream than the one whose kernels read them last) give
+    the bits of the same calls on one stream."""
+    torch = torch_dev
+    srv = serve.Server(hbm_budget_bytes=1 << 34, max_running=4)
+    reqs = [serve.Request(rid=0, nz=3, nr=2, N=6, n_rho=2.0, omega=1.3, seed=5, steps=5, arrival=0.0),
+            serve.Request(rid=1, nz=2, nr=2, N=4, n_rho=1.5, omega=0.8, seed=6, steps=5, arrival=0.0)]
+    one = [serve._Running(r, srv.mesh(r.nz, r.nr, r.N)) for r in reqs]
+    two = [serve._Running(r, srv.mesh(r.nz, r.nr, r.N)) for r in reqs]
+    torch.cuda.synchronize()
+    for _ in range(5):
+        srv.packer.step([run.as_packed() for run in one])
+        for run in one:
+            run.advanced()
+    torch.cuda.synchronize()
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    prev = torch.cuda.current_stream()
+    for k in range(5):
+        s = streams[k % 2]
+        s.wait_stream(prev)  # the step reads the state the previous call wrote
+        srv.packer.step([run.as_packed() for run in two], stream=s)
+        for run in two:
+            run.advanced()
+        prev = s
+    torch.cuda.synchronize()
+    for a, b in zip(one, two):
+        assert torch.equal(a.q, b.q)
