@@ -64,6 +64,9 @@ def parse():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-viscous", action="store_true")
+    ap.add_argument("--no-largest", action="store_true")
+    ap.add_argument("--accuracy-steps", type=int, default=200)
+    ap.add_argument("--largest-steps", type=int, default=50)
     ap.add_argument("--serve-requests", type=int, default=64)
     ap.add_argument("--serve-budget-gb", type=float, default=24.0)
     return ap.parse_args()
@@ -95,12 +98,17 @@ def whole_job_rate(dof_per_rank: int, steps: int, world: int, ms: float) -> floa
 
 def algorithmic_bytes_per_dof_step(mixed: bool) -> int:
     """State streams of one SSP-RK3 step: stage 0 reads q^n and writes q^1; stages 1 and 2 read q^n and
-    q^(s) and write q^(s+1): 8 passes of 9 FP64 values.  The mixed path also reads its FP32 background
-    record (rho0, p0, R0x, R0y, R0z) in each of the 3 stages."""
+    q^(s) and write q^(s+1): 8 passes of 9 FP64 values (576 B).  The mixed path also reads the
+    background residual R0 (3 momentum components, counted as FP64) in each of the 3 stages: 648 B."""
     b = 8 * 9 * 8
     if mixed:
-        b += 3 * 5 * 4
+        b += 3 * 3 * 8
     return b
+
+
+# FP64 flops of one residual evaluation per solution point at N = 6 (extrapolation and derivative
+# 163k, interior fluxes 54k, face fluxes 32k, div B 13k, sources 9k, RK sum 8k per element: 280k / 216)
+ALGORITHMIC_FLOP_PER_DOF_STAGE = 1300
 
 
 def measured_peaks():
@@ -197,6 +205,14 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def bench_config(wl, world: int) -> dict:
+    """The workload description both arms print (the reference arm runs a bounded sample of it)."""
+    return {"workload": wl["desc"], "cfl": CFL, "rk": "SSP-RK3 (Shu-Osher)",
+            "parallelism": "replicas" if world > 1 else "single GPU",
+            "l2": "inputs larger than L2 (one FP64 state is %.0f MB)" % (
+                9 * 8 * 6 * wl["nz"] ** 2 * wl["nr"] * wl["N"] ** 3 / 1e6)}
+
+
 # ----------------------------------------------------------------------------- our arm
 
 def make_case(wl, device_stream=None):
@@ -214,11 +230,14 @@ def make_case(wl, device_stream=None):
     return mesh, phys, q0, bg, params
 
 
-def time_steps(mesh, phys, q, work, prec, bg, steps, warmup, sampler=None, barrier=None):
+def time_steps(mesh, phys, q, work, prec, bg, steps, warmup, sampler=None, barrier=None, reset_to=None):
     """The timed steps run as one sd_advance call: each step's lambda_max and face traces come from
-    the last stage of the step before (one trace pass per call instead of one per step)."""
+    the last stage of the step before (one trace pass per call instead of one per step).  With
+    reset_to, q is set back to that state after the warm-up steps."""
     import torch
     mesh.advance(phys, CFL, warmup, q, work, prec=prec, bg=bg)
+    if reset_to is not None:
+        q.copy_(reset_to)
     torch.cuda.synchronize()
     if barrier:
         barrier()
@@ -292,12 +311,59 @@ def time_e2e(mesh, phys, q_dev, work, bg, steps, warmup, chunks=16):
     return e0.elapsed_time(e1), nbytes, nbytes + 16
 
 
-def run_serving(n_requests: int, budget_gb: float):
+def sequential_fifo(srv, reqs, prec=None):
+    """The same requests served one at a time, first in first out, without batching: each request
+    (initial state, background, then its K steps in one sd_advance call) is issued once it has
+    arrived and the request before it has been issued; at most two are in flight.  Latency =
+    completion (device event after its last step) - arrival."""
+    import numpy as np
+    import torch
+
+    from paper_2502_17805_gb300 import sdmhd, serve
+    prec = sdmhd.SD_FP32_MIXED if prec is None else prec
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    t0 = time.perf_counter()
+    inflight, lat, dof = [], [], 0
+    for r in sorted(reqs, key=lambda x: x.arrival):
+        wait = r.arrival - (time.perf_counter() - t0)
+        if wait > 0:
+            time.sleep(wait)
+        run = serve._Running(r, srv.mesh(r.nz, r.nr, r.N))
+        run.mesh.advance(run.phys, r.cfl, r.steps, run.q, run.work, prec=prec,
+                         bg=run.bg if prec == sdmhd.SD_FP32_MIXED else None)
+        ev = torch.cuda.Event(enable_timing=True)
+        ev.record(stream)
+        inflight.append((ev, r, run))
+        dof += r.dof * r.steps
+        if len(inflight) >= 2:
+            e, rr, _ = inflight.pop(0)
+            e.synchronize()
+            lat.append(ev0.elapsed_time(e) / 1e3 - rr.arrival)
+    done = 0.0
+    for e, rr, _ in inflight:
+        e.synchronize()
+        lat.append(ev0.elapsed_time(e) / 1e3 - rr.arrival)
+        done = ev0.elapsed_time(e) / 1e3
+    lat = np.array(lat)
+    return {"p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+            "mean_ms": float(lat.mean() * 1e3), "aggregate": dof / done, "wall_s": done}
+
+
+def run_serving(n_requests: int, budget_gb: float, tight_budget_gb: float = 4.0):
     """Serving workload: n requests arriving Poisson (mean gap 20 ms), 6 Nz^2 Nr in {384, 1536, 6144, 24576}
     elements, N in {4, 5, 6}, N_rho ~ U[1, 3], Omega ~ U[0.5, 2], seeds 0..n-1, 50 FP32-mixed steps each,
-    admitted by HBM footprint under `budget_gb`.  Latency = completion - arrival.  The sequential
-    comparisons run one request at a time through sd_step (FP32-mixed and FP64) on a bounded sample: one
-    request of each size, 5 steps each."""
+    admitted by HBM footprint under `budget_gb`.  Latency = completion - arrival.
+
+    Beside it: the same requests all arriving at t = 0 (saturating: the aggregate then measures capacity,
+    not the arrival rate), once under `budget_gb` and once under `tight_budget_gb`; and a sequential
+    first-in first-out server without batching (one request at a time through sd_advance) under both
+    arrival traces.  The sequential FP64 rate is measured on a bounded sample (one request of each size,
+    5 steps each)."""
+    import dataclasses
+
     import torch
 
     from paper_2502_17805_gb300 import sdmhd, serve
@@ -305,39 +371,69 @@ def run_serving(n_requests: int, budget_gb: float):
     srv = serve.Server(int(budget_gb * 1e9), max_running=max(n_requests, 1))
     srv.warm(reqs)
     torch.cuda.synchronize()
-    out = srv.run(reqs)
+
+    def fresh(rs, at_zero=False):
+        return [dataclasses.replace(r, arrival=0.0 if at_zero else r.arrival) for r in rs]
+
+    def served(server, rs):
+        server.peak_bytes, server.ticks = 0, 0
+        o = server.run(rs)
+        torch.cuda.synchronize()
+        return {"p50_ms": o["p50_ms"], "p99_ms": o["p99_ms"], "mean_ms": o["mean_ms"], "aggregate": o["aggregate"],
+                "wall_s": o["wall_s"], "ticks": o["ticks"], "budget_gb": o["budget_bytes"] / 1e9,
+                "peak_gb": o["peak_bytes"] / 1e9}
+
+    out = served(srv, fresh(reqs))
+    sat = served(srv, fresh(reqs, at_zero=True))
+    tight_srv = serve.Server(int(tight_budget_gb * 1e9), max_running=max(n_requests, 1))
+    tight_srv.meshes = srv.meshes
+    tight = served(tight_srv, fresh(reqs, at_zero=True))
+    share = serve.Server(int(budget_gb * 1e9), max_running=max(n_requests, 1), policy="all")
+    share.meshes = srv.meshes
+    share_poisson = served(share, fresh(reqs))
+    share_sat = served(share, fresh(reqs, at_zero=True))
+    srpt = serve.Server(int(budget_gb * 1e9), max_running=max(n_requests, 1), policy="srpt")
+    srpt.meshes = srv.meshes
+    srpt_poisson = served(srpt, fresh(reqs))
+    srpt_sat = served(srpt, fresh(reqs, at_zero=True))
+    fifo = sequential_fifo(srv, fresh(reqs))
+    fifo_sat = sequential_fifo(srv, fresh(reqs, at_zero=True))
     sample = []
     for shape in ((4, 4), (8, 4), (16, 4), (32, 4)):
         cand = [r for r in reqs if (r.nz, r.nr) == shape]
         if cand:
             sample.append(cand[0])
-    seq = {}
-    for name, prec in (("sequential_mixed", sdmhd.SD_FP32_MIXED), ("sequential_fp64", sdmhd.SD_FP64)):
-        dof = 0
-        ms = 0.0
-        for r in sample:
-            run = serve._Running(serve.Request(r.rid, r.nz, r.nr, r.N, r.n_rho, r.omega, r.seed, 5, 0.0),
-                                 srv.mesh(r.nz, r.nr, r.N))
-            bg = run.bg if prec == sdmhd.SD_FP32_MIXED else None
-            run.mesh.step(run.phys, r.cfl, run.q, run.work, prec=prec, bg=bg)
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            for _ in range(5):
-                run.mesh.step(run.phys, r.cfl, run.q, run.work, prec=prec, bg=bg)
-            e1.record()
-            torch.cuda.synchronize()
-            ms += e0.elapsed_time(e1)
-            dof += r.dof * 5
-        seq[name] = dof / (ms / 1e3)
-    return {"requests": out["requests"], "p50_ms": out["p50_ms"], "p99_ms": out["p99_ms"],
-            "mean_ms": out["mean_ms"], "aggregate": out["aggregate"], "unit": UNIT, "wall_s": out["wall_s"],
-            "ticks": out["ticks"], "budget_gb": budget_gb, "peak_gb": out["peak_bytes"] / 1e9,
-            "sequential_mixed": seq["sequential_mixed"], "sequential_fp64": seq["sequential_fp64"],
-            "vs_sequential_fp64": out["aggregate"] / seq["sequential_fp64"],
-            "workload": "%d requests, Poisson arrivals mean 20 ms, 6 Nz^2 x 4 shells with Nz in {4, 8, 16, 32}, "
-                        "N in {4, 5, 6}, N_rho ~ U[1,3], Omega ~ U[0.5,2], seeds 0-%d, 50 FP32-mixed steps each"
-                        % (n_requests, n_requests - 1)}
+    dof, ms = 0, 0.0
+    for r in sample:
+        run = serve._Running(dataclasses.replace(r, steps=5, arrival=0.0), srv.mesh(r.nz, r.nr, r.N))
+        run.mesh.step(run.phys, r.cfl, run.q, run.work, prec=sdmhd.SD_FP64)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        run.mesh.advance(run.phys, r.cfl, 5, run.q, run.work, prec=sdmhd.SD_FP64)
+        e1.record()
+        torch.cuda.synchronize()
+        ms += e0.elapsed_time(e1)
+        dof += r.dof * 5
+    seq64 = dof / (ms / 1e3)
+    res = dict(out)
+    res.update({
+        "requests": n_requests, "unit": UNIT,
+        "policy": "oldest request every tick, backfilled with the least remaining work up to max(%d DOF, "
+                  "%.2f x the oldest request's DOF)" % (srv.tick_dof, 1 + srv.backfill_frac),
+        "saturating": sat, "saturating_tight_budget": tight,
+        "every_request_every_tick": {"poisson": share_poisson, "saturating": share_sat},
+        "least_remaining_work_first": {"poisson": srpt_poisson, "saturating": srpt_sat},
+        "sequential_fifo": fifo, "sequential_fifo_saturating": fifo_sat,
+        "sequential_mixed": fifo_sat["aggregate"], "sequential_fp64": seq64,
+        "sequential_fp64_sample": "one request of each of the four sizes, 5 FP64 steps each (sd_advance)",
+        "vs_sequential_fp64": out["aggregate"] / seq64,
+        "saturating_vs_sequential_mixed": sat["aggregate"] / fifo_sat["aggregate"],
+        "p50_vs_sequential_fifo": out["p50_ms"] / fifo["p50_ms"], "p99_vs_sequential_fifo": out["p99_ms"] / fifo["p99_ms"],
+        "workload": "%d requests, Poisson arrivals mean 20 ms, 6 Nz^2 x 4 shells with Nz in {4, 8, 16, 32}, "
+                    "N in {4, 5, 6}, N_rho ~ U[1,3], Omega ~ U[0.5,2], seeds 0-%d, 50 FP32-mixed steps each; "
+                    "saturating: the same requests all at t = 0" % (n_requests, n_requests - 1)})
+    return res
 
 
 def accuracy_report(steps: int = 20):
@@ -385,6 +481,77 @@ def accuracy_report(steps: int = 20):
             "max_divb_mixed": dm["max_divb"], "max_divb_fp64": d64["max_divb"]}
 
 
+def accuracy_fp32_vs_fp64(mesh, phys, q0, bg, steps: int):
+    """FP32-mixed against the FP64 path on the GPU (parity-checked against the oracle to 1e-12 per
+    entry) over `steps` SSP-RK3 steps of the same shell: the mixed run takes dt and c_h from its own
+    lambda_max each step (sd_advance); the FP64 run repeats that dt and c_h sequence through
+    sd_rk_stage.  Per variable max|mixed - FP64| / max|FP64 - initial|; relative drift of the total
+    energy, KE, E_B and max|div B| (GLM cleaning on) of both, at the start and the end."""
+    import torch
+
+    from paper_2502_17805_gb300 import sdmhd
+    qm, q64, work = q0.clone(), q0.clone(), mesh.empty_state()
+    dts = torch.zeros(2 * steps, dtype=torch.float64, device="cuda")
+    d0 = mesh.diagnostics(phys, q0)
+    mesh.advance(phys, CFL, steps, qm, work, prec=sdmhd.SD_FP32_MIXED, bg=bg, dt_out=dts)
+    d = dts.cpu().numpy()
+    ph64 = sdmhd.Phys(**{k: getattr(phys, k) for k in ("gamma", "GM", "omega", "glm_alpha", "powell", "gravity",
+                                                       "coriolis")})
+    for k in range(steps):
+        ph64.c_h = float(d[2 * k + 1])
+        mesh.rk_step(ph64, float(d[2 * k]), q64, work)
+    torch.cuda.synchronize()
+    n3 = mesh.N ** 3
+    change = (q64[:, :, :n3] - q0[:, :, :n3]).abs().amax(dim=(1, 2))
+    err = (qm[:, :, :n3] - q64[:, :, :n3]).abs().amax(dim=(1, 2))
+    rel = (err / change.clamp_min(1e-300)).cpu().tolist()
+    dm, d64 = mesh.diagnostics(phys, qm), mesh.diagnostics(phys, q64)
+    del qm, q64, work
+    names = ["rho", "mx", "my", "mz", "E", "Bx", "By", "Bz", "psi"]
+    return {"steps": steps, "reference": "FP64 GPU path (parity-checked against the FP64 oracle), same dt and c_h",
+            "mixed_vs_fp64_rel_err_of_change": dict(zip(names, rel)),
+            "max_rel_err_of_change": max(rel), "t_end": float(d[0::2].sum()),
+            "energy_drift_mixed": dm["energy"] / d0["energy"] - 1.0,
+            "energy_drift_fp64": d64["energy"] / d0["energy"] - 1.0,
+            "ke_mixed": dm["ke"], "ke_fp64": d64["ke"], "eb_start": d0["eb"], "eb_mixed": dm["eb"], "eb_fp64": d64["eb"],
+            "max_divb_start": d0["max_divb"], "max_divb_mixed": dm["max_divb"], "max_divb_fp64": d64["max_divb"]}
+
+
+def largest_shell_leg(steps: int, fp64_steps: int, peak: float, peak_kind: str):
+    """The largest single-GPU configuration: the 221,184-element shell (N = 6, N_rho = 3), `steps`
+    FP32-mixed steps and `fp64_steps` FP64 steps from the initial state (after untimed warm-up steps
+    on the same state, which is then reset), DOF-updates/s, the mixed stage kernel against the HBM
+    roofline, and max|div B| under GLM cleaning before and after."""
+    import torch
+
+    from paper_2502_17805_gb300 import sdmhd
+    wl = WORKLOADS["shell221k"]
+    mesh, phys, q0, bg, _ = make_case(wl)
+    n_pts = mesh.info["n_points"]
+    d0 = mesh.diagnostics(phys, q0)
+    q, work = q0.clone(), mesh.empty_state()
+    ms, prof, _ = time_steps(mesh, phys, q, work, sdmhd.SD_FP32_MIXED, bg, steps, 3, reset_to=q0)
+    dm = mesh.diagnostics(phys, q)
+    q.copy_(q0)
+    ms64, prof64, _ = time_steps(mesh, phys, q, work, sdmhd.SD_FP64, None, fp64_steps, 1, reset_to=q0)
+    d64 = mesh.diagnostics(phys, q)
+    stage_ms = prof["stage_ms"] / max(prof["stage_launches"], 1)
+    bpl = algorithmic_bytes_per_dof_step(True) / 3.0 * n_pts
+    achieved = bpl / (stage_ms / 1e3) / 1e9
+    del q, work, q0, bg, mesh
+    torch.cuda.empty_cache()
+    return {"workload": wl["desc"], "dof": n_pts,
+            "mixed": {"value": n_pts * steps / (ms / 1e3), "unit": UNIT, "steps": steps, "ms_per_step": ms / steps,
+                      "roofline": {"kernel": "stage_kernel_v2<6>", "bound": "hbm", "achieved": achieved,
+                                   "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
+                                   "avg_launch_ms": stage_ms, "algorithmic_bytes_per_launch": bpl},
+                      "max_divb": dm["max_divb"], "energy_drift": dm["energy"] / d0["energy"] - 1.0},
+            "fp64": {"value": n_pts * fp64_steps / (ms64 / 1e3), "unit": UNIT, "steps": fp64_steps,
+                     "ms_per_step": ms64 / fp64_steps, "max_divb": d64["max_divb"],
+                     "energy_drift": d64["energy"] / d0["energy"] - 1.0},
+            "max_divb_start": d0["max_divb"], "eb_start": d0["eb"]}
+
+
 class OracleSample:
     """The CPU oracle, as it stands, on a bounded sample of the workload: one step is the work of one
     SSP-RK3 step (three residual evaluations) on `n_elems` random elements of the same shell, from the
@@ -416,19 +583,24 @@ class OracleSample:
         return self.dof_per_step * steps / secs if steps else 0.0, secs
 
 
-def fp64_roofline(stage_ms: float, clocks):
-    """The FP64 stage kernel against the FP64 pipe: its FP64 flops per launch (committed ncu count of
-    DFMA, DADD, DMUL on these sources, scaled to the bench shell) over its live average launch time."""
+def fp64_roofline(stage_ms: float, clocks, n_pts: int):
+    """The FP64 stage kernel against the FP64 pipe: the algorithmic FP64 flops of one stage (1,300 per
+    solution point at N = 6) over its live average launch time, against a peak derived from unit
+    counts and clocks (no measured FP64 peak is available).  The committed ncu count of the kernel's
+    DFMA, DADD, DMUL (scaled to the bench shell) is reported beside it when it was taken on these
+    sources."""
     import torch
     n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     mhz = clocks["sm_max_mhz"] if clocks else 2070.0
     peak = fp64_peak_tflops(n_sm, mhz)
-    flops = committed_traffic("stage_fp64_N6_flops")
-    achieved = flops / (stage_ms / 1e3) / 1e12 if flops else None
+    flops = ALGORITHMIC_FLOP_PER_DOF_STAGE * n_pts
+    achieved = flops / (stage_ms / 1e3) / 1e12
+    counted = committed_traffic("stage_fp64_N6_flops")
     return {"kernel": "stage_kernel<6, PolFP64> (FP64 fused stage)", "bound": "fp64", "achieved": achieved,
-            "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak if achieved else None,
+            "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "peak_source": "derived: %d SMs x 2 FP64 FMA/clk x 2 flop x %.0f MHz" % (n_sm, mhz),
-            "flops_per_launch": flops}
+            "algorithmic_flops_per_launch": flops, "counted_flops_per_launch": counted,
+            "counted_tflops": counted / (stage_ms / 1e3) / 1e12 if counted else None}
 
 
 def run_ours(args):
@@ -495,9 +667,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32 (SD operators) + f64 (background, RK state, reductions)",
         "data": "synthetic",
-        "config": {"workload": wl["desc"], "precision": "FP32-mixed", "cfl": CFL, "rk": "SSP-RK3 (Shu-Osher)",
-                   "parallelism": "replicas" if world > 1 else "single GPU",
-                   "l2": "inputs larger than L2 (one FP64 state is %.0f MB)" % (mesh.info["state_bytes"] / 1e6)},
+        "config": bench_config(wl, world), "precision": "FP32-mixed (headline); FP64 under fp64",
         "roofline": {"kernel": "stage_kernel_v2<6> (FP32-mixed fused stage)", "bound": "hbm", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
                      "traffic": committed_traffic("stage_mixed_N6"),
@@ -505,7 +675,7 @@ def run_ours(args):
                      "avg_launch_ms": stage_avg_ms,
                      "step_frac": step_achieved / peak},
         "fp64": {"value": value64, "unit": UNIT, "steps": k64, "ms_per_step": ms64 / k64, "dtype": "f64",
-                 "stage_avg_ms": stage64_ms, "roofline": fp64_roofline(stage64_ms, clocks)},
+                 "stage_avg_ms": stage64_ms, "roofline": fp64_roofline(stage64_ms, clocks, n_pts)},
         "viscous_fp64": visc,
         "gpu_launches": int(prof["stage_launches"] + prof["trace_launches"] + prof["other_launches"]),
         "kernel_ms_per_step": {"stage": prof["stage_ms"] / args.steps, "trace_lambda": prof["trace_ms"] / args.steps,
@@ -521,9 +691,17 @@ def run_ours(args):
         out["e2e"] = {"value": n_pts * ke * world / (ems / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                       "d2h_bytes_per_step": d2h, "ms_per_step": ems / ke}
     if rank == 0 and world == 1 and not args.no_accuracy:
-        out["accuracy"] = accuracy_report()
-    if rank == 0 and world == 1 and not args.no_serve:
+        out["accuracy_vs_oracle"] = accuracy_report()
+        out["accuracy"] = accuracy_fp32_vs_fp64(mesh, phys, q0, bg, args.accuracy_steps)
+        out["accuracy"]["workload"] = wl["desc"]
+    if rank == 0 and world == 1 and not args.no_largest:
         del q, work, q64, q2
+        q = work = q64 = q2 = None
+        import torch
+        torch.cuda.empty_cache()
+        out["largest"] = largest_shell_leg(args.largest_steps, args.largest_steps, peak, peak_kind)
+    if rank == 0 and world == 1 and not args.no_serve:
+        del q, work, q64, q2, mesh, bg, q0
         import torch
         torch.cuda.empty_cache()
         out["serve"] = run_serving(args.serve_requests, args.serve_budget_gb)
@@ -557,12 +735,16 @@ def run_reference(args):
     ors.run(args.warmup)
     rate, secs = ors.run(args.steps)
     cores, nel = ors.threads, ors.elems.size
+    n_pts = 6 * wl["nz"] ** 2 * wl["nr"] * wl["N"] ** 3
+    # value and ms_per_step on the same basis: one SSP-RK3 step of the whole shell at the sample's rate
     out = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": secs * 1e3 / args.steps, "higher_is_better": True,
+           "warmup": args.warmup, "ms_per_step": n_pts / rate * 1e3, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": wl["desc"], "precision": "FP64 oracle"},
+           "precision": "FP64 oracle", "config": bench_config(wl, world),
+           "sample_ms_per_step": secs * 1e3 / args.steps,
            "cpu_baseline": {"value": rate, "unit": UNIT, "kind": "oracle", "cores": cores,
-                            "sample": "per step: 3 residual evaluations on %d random elements of the shell" % nel},
+                            "sample": "per step: 3 residual evaluations on %d random elements of the shell; "
+                                      "ms_per_step scales the sample's time to the whole shell" % nel},
            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 

@@ -344,11 +344,13 @@ sd_status sd_diagnostics(const sd_mesh* mesh, const sd_phys* phys, const double*
  * cudaMalloc when they need a residual, for example an application whose memory
  * pool already holds all the device memory it may use, or a latency-bound loop
  * that must not risk the device-wide synchronisation an allocation can cause.
- * Its scratch (the face traces of q) is a fixed 8 MiB device array inside the
- * library, held on every GPU that loads the library until the process exits;
- * meshes whose traces need more (n_elements * 6 * 9 * N^2 * 8 bytes > 8 MiB, e.g.
- * more than 539 elements at N = 6) are rejected with SD_ERR_INVALID_ARGUMENT and
- * a message.  The first call on each device looks up the array's device address
+ * Its scratch (the face traces of q and the common face fluxes) is a fixed
+ * 8 MiB device array inside the library, held on every GPU that loads the
+ * library until the process exits; meshes that need more ((n_elements * 54 +
+ * n_owned_faces * 10) * N^2 * 8 bytes > 8 MiB, where every interior face counts
+ * once and every boundary face once: about 25 KB per element of a closed mesh
+ * at N = 6, i.e. about 330 elements) are rejected with SD_ERR_INVALID_ARGUMENT
+ * and a message.  The first call on each device looks up the array's device address
  * with that device current; make that first call before any stream capture.
  * All calls share the one array, which keeps the last call's contents (every
  * entry a call reads is written earlier in the same call), so calls whose work

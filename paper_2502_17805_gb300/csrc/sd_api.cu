@@ -228,7 +228,8 @@ cudaError_t dalloc(T** p, size_t count, int64_t* bytes) {
 void free_mesh(sd_mesh* m) {
   if (!m) return;
   for (cudaEvent_t ev : m->prof_ev) cudaEventDestroy(ev);
-  void* ptrs[] = {m->Sfam64, m->invJ64, m->X64, m->Sfam32, m->invJ32, m->X32, m->nbr, m->meta,
+  void* ptrs[] = {m->own_faces, m->face_k, m->gface64, m->Sfam64, m->invJ64, m->X64, m->Sfam32, m->invJ32, m->X32,
+                  m->nbr, m->meta,
                   m->tr64[0], m->tr64[1], m->tr32[0], m->tr32[1], m->dyn, m->diag_part, m->diag_out, m->divb,
                   m->err, m->grad, m->gtr};
   for (void* p : ptrs)
@@ -272,6 +273,10 @@ sd::StageParams base_params(const sd_mesh* m, const sd_phys* ph, int prec) {
   P.meta = m->meta;
   P.err = m->err;
   P.wait_spins = m->wait_spins;
+  P.n_own = m->n_own;
+  P.own_faces = m->own_faces;
+  P.face_k = m->face_k;
+  P.gface = m->gface64;
   P.visc = ph->viscous ? 1 : 0;
   P.mu = ph->mu;
   P.eta = ph->eta;
@@ -597,9 +602,25 @@ sd_status sd_mesh_create(const sd_mesh_desc* desc, void* stream, sd_mesh** out) 
   const int64_t N2 = (int64_t)N * N, N3 = N2 * N, NF = N + 1;
   const size_t ne = (size_t)std::max<int64_t>(n_e, 1);
   int64_t bytes = 0;
+  // faces owned by an element (the first of a matched pair, or a boundary face): the FP64
+  // face-flux kernel computes each of them once, for both sides
+  std::vector<int> own_faces, face_k((size_t)n_e * 6, -1);
+  for (int64_t e = 0; e < n_e; ++e)
+    for (int F = 0; F < 6; ++F)
+      if (nbr[e * 6 + F] < 0 || sd::meta_owner(meta[e * 6 + F])) {
+        face_k[e * 6 + F] = (int)own_faces.size();
+        own_faces.push_back((int)(e * 6 + F));
+      }
+  for (int64_t e = 0; e < n_e; ++e)
+    for (int F = 0; F < 6; ++F)
+      if (face_k[e * 6 + F] < 0) face_k[e * 6 + F] = face_k[(int64_t)nbr[e * 6 + F] * 6 + sd::meta_nbF(meta[e * 6 + F])];
+  m->n_own = (int64_t)own_faces.size();
   cudaError_t err = cudaSuccess;
 #define ALLOC(ptr, cnt)                                   \
   if (err == cudaSuccess) err = dalloc(&(ptr), (cnt), &bytes);
+  ALLOC(m->own_faces, (size_t)m->n_own);
+  ALLOC(m->face_k, ne * 6);
+  ALLOC(m->gface64, (size_t)m->n_own * 10 * N2);
   ALLOC(m->Sfam64, ne * 9 * N2 * NF);
   ALLOC(m->invJ64, ne * N3);
   ALLOC(m->X64, ne * 3 * N3);
@@ -642,6 +663,10 @@ sd_status sd_mesh_create(const sd_mesh_desc* desc, void* stream, sd_mesh** out) 
     err = cudaMemcpyAsync(m->nbr, nbr.data(), n_e * 6 * sizeof(int), cudaMemcpyHostToDevice, s);
   if (err == cudaSuccess && n_e > 0)
     err = cudaMemcpyAsync(m->meta, meta.data(), n_e * 6 * sizeof(int), cudaMemcpyHostToDevice, s);
+  if (err == cudaSuccess && n_e > 0)
+    err = cudaMemcpyAsync(m->face_k, face_k.data(), n_e * 6 * sizeof(int), cudaMemcpyHostToDevice, s);
+  if (err == cudaSuccess && m->n_own > 0)
+    err = cudaMemcpyAsync(m->own_faces, own_faces.data(), m->n_own * sizeof(int), cudaMemcpyHostToDevice, s);
   if (err == cudaSuccess) err = cudaMemsetAsync(d_flag, 0, sizeof(int), s);
   if (err == cudaSuccess) err = cudaMemsetAsync(m->err, 0, sizeof(int), s);
   if (err == cudaSuccess) err = sd::launch_geometry(m, d_corners, d_flag, s);

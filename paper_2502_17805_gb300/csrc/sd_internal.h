@@ -95,6 +95,13 @@ struct StageParams {
   int skip;
   int* err;  // device error word (bounded waits that ran out)
   int wait_spins;  // polls of a bounded wait before it reports a time-out
+  // FP64 face fluxes, computed once per face by its owner: the faces this mesh's
+  // elements own (e * 6 + F, boundary faces included), the index k of the face of
+  // (e, F) in that list (for either side), and the values [k][10][N^2]
+  int64_t n_own;
+  const int* own_faces;
+  const int* face_k;
+  void* gface;
   // viscous, resistive and thermal fluxes (FP64 policy): coefficients, the gradients of
   // (U, T, S, B) at the solution points [e][24][N^3] (grad[3c + j] = d w_c / d x_j) and their
   // face traces [e][F][24][N^2]; the gradient kernel writes grad_out / gtr_out
@@ -137,6 +144,10 @@ struct sd_mesh {
   double* diag_out;         // [12]
   double* divb;             // [n_e * N^3]
   double* host_diag;        // pinned [12]
+  int* own_faces;           // [n_own] e * 6 + F of the faces the elements own (boundary faces included)
+  int* face_k;              // [n_e][6] index in own_faces of the face of (e, F), either side
+  int64_t n_own;
+  double* gface64;          // [n_own][10][N^2] FP64 common face fluxes of the current stage
   int* err;                 // device error word of the stage kernels
   int wait_spins;           // polls of a stage kernel's bounded wait before a time-out (sd_mesh_set_wait_limit)
   double* grad;             // viscous path, allocated on first use: gradients [e][24][N^3]

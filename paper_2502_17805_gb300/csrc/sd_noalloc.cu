@@ -5,9 +5,10 @@
 // whose memory pool has already reserved the device memory it is allowed to
 // use, or a latency-bound loop that must not risk the device-wide
 // synchronisation an allocation can cause.  This entry point performs no
-// allocation of any kind.  Its only scratch is the face-trace buffer below, a
-// file-scope device array of kNoAllocScratchBytes that every GPU loading this
-// library holds until the process exits.
+// allocation of any kind.  Its only scratch is the buffer below (the face
+// traces of q, then the common face fluxes), a file-scope device array of
+// kNoAllocScratchBytes that every GPU loading this library holds until the
+// process exits.
 #include <string.h>
 
 #include <mutex>
@@ -21,7 +22,8 @@ constexpr size_t kNoAllocScratchBytes = 8u << 20;  // 8 MiB per device
 constexpr size_t kNoAllocScratchDoubles = kNoAllocScratchBytes / sizeof(double);
 constexpr int kMaxDevices = 64;
 
-// Face traces of the input state: [element][face][variable][N^2] doubles.
+// Face traces of the input state, [element][face][variable][N^2] doubles, then
+// the common face fluxes [owned face][10][N^2].
 static __device__ __align__(256) double g_noalloc_traces[kNoAllocScratchDoubles];
 
 // Device address of g_noalloc_traces on each device, looked up once per device
@@ -55,12 +57,14 @@ sd_status sd_residual_noalloc(const sd_mesh* m, const sd_phys* ph, const double*
   if (ph->viscous)
     return noalloc_fail(SD_ERR_UNSUPPORTED, "viscous fluxes need gradient buffers: use sd_residual");
   const size_t N2 = (size_t)m->N * m->N;
-  const size_t need = (size_t)m->n_e * 6 * 9 * N2;
+  const size_t n_tr = ((size_t)m->n_e * 6 * 9 * N2 + 31) / 32 * 32;  // traces, then the face fluxes
+  const size_t need = n_tr + (size_t)m->n_own * 10 * N2;
   if (need > kNoAllocScratchDoubles)
     return noalloc_fail(SD_ERR_INVALID_ARGUMENT,
-                        "mesh too large for sd_residual_noalloc: its face traces need " +
+                        "mesh too large for sd_residual_noalloc: its face traces and face fluxes need " +
                             std::to_string(need * sizeof(double)) + " bytes, the fixed scratch holds " +
-                            std::to_string(kNoAllocScratchBytes) + " (n_elements * 6 * 9 * N^2 * 8 bytes)");
+                            std::to_string(kNoAllocScratchBytes) +
+                            " ((n_elements * 54 + n_owned_faces * 10) * N^2 * 8 bytes)");
   cudaGetLastError();  // a pending error of an earlier, unrelated call is not this call's
   int dev = -1;
   cudaError_t err = cudaGetDevice(&dev);
@@ -104,8 +108,12 @@ sd_status sd_residual_noalloc(const sd_mesh* m, const sd_phys* ph, const double*
   P.meta = m->meta;
   P.err = m->err;
   P.wait_spins = m->wait_spins;
-  // every trace entry the second kernel reads is written by the first, so the
-  // scratch needs no clearing between calls
+  P.n_own = m->n_own;
+  P.own_faces = m->own_faces;
+  P.face_k = m->face_k;
+  P.gface = tr + n_tr;
+  // every trace and face-flux entry a kernel reads is written earlier in the
+  // same call, so the scratch needs no clearing between calls
   P.q_in = q;
   P.tr_out = tr;
   err = sd::launch_stage_fp64(m, P, true, s);

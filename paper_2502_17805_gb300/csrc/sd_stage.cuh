@@ -65,6 +65,23 @@ __device__ __forceinline__ int sol_index(int d, int i, int a, int b) {
   return d == 0 ? i + N * (a + N * b) : (d == 1 ? a + N * (i + N * b) : a + N * (b + N * i));
 }
 
+// solution-point index of position i along the line (d, L), L = a + N b over the
+// other two directions in increasing order: base + i * stride
+template <int N>
+__device__ __forceinline__ void line_geom(int d, int L, int& base, int& stride) {
+  const int a = L % N, b = L / N;
+  if (d == 0) {
+    base = N * L;
+    stride = 1;
+  } else if (d == 1) {
+    base = a + N * N * b;
+    stride = N;
+  } else {
+    base = L;
+    stride = N * N;
+  }
+}
+
 // Upper bound of the wave speeds at one point, |U| + sqrt(gamma p / rho + |B|^2 / rho)
 // (>= |u_n| + c_f along every direction), from the full conserved state.  The
 // trace kernel and the stage kernels that also return lambda_max of their output

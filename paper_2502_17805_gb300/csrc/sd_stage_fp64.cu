@@ -1,15 +1,17 @@
-// Instantiations of the fused element kernels for the FP64 policy, N = 2..8,
-// with and without the viscous fluxes, and of the BR1 gradient kernel.
+// Instantiations of the fused element kernels for the FP64 policy, N = 2..8:
+// the face-flux and line-blocked element kernels of the inviscid stages, the
+// viscous stage kernel, the trace kernel, and the BR1 gradient kernel.
 #include "sd_stage.cuh"
+#include "sd_stage_f64.cuh"
 
 namespace sd {
 
 template <int N>
 static cudaError_t launch_fp64_n(const sd_mesh* m, const StageParams& P, bool traces_only, cudaStream_t s) {
+  if (traces_only) return launch_traces_t<N, PolFP64>(P, m->ops64, s);
   // the viscous instantiation once the gradient pass has filled P.grad (not for MODE_DIVB)
-  if (P.visc && P.grad && !traces_only && P.mode != MODE_DIVB)
-    return launch_stage_t<N, PolFP64, true>(P, m->ops64, false, s);
-  return launch_stage_t<N, PolFP64>(P, m->ops64, traces_only, s);
+  if (P.visc && P.grad && P.mode != MODE_DIVB) return launch_stage_t<N, PolFP64, true>(P, m->ops64, false, s);
+  return launch_stage_f64_t<N>(P, m->ops64, s);
 }
 
 cudaError_t launch_stage_fp64(const sd_mesh* m, const StageParams& P, bool traces_only, cudaStream_t s) {

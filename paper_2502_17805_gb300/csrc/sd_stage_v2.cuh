@@ -66,22 +66,6 @@ __device__ __forceinline__ float new_qprime(int v, double qo, float qo32, float 
   return qo32;
 }
 
-// solution-point index of position i along the line (d, L): base + i * stride
-template <int N>
-__device__ __forceinline__ void line_geom(int d, int L, int& base, int& stride) {
-  const int a = L % N, b = L / N;
-  if (d == 0) {
-    base = N * L;
-    stride = 1;
-  } else if (d == 1) {
-    base = a + N * N * b;
-    stride = N;
-  } else {
-    base = L;
-    stride = N * N;
-  }
-}
-
 template <int N, bool EXACT, bool INCR>
 __device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops<float>& ops, const int64_t e,
                                               unsigned char* smem_raw) {

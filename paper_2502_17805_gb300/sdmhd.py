@@ -347,14 +347,21 @@ class Packer:
             lib().sd_packer_destroy(self._h)
             self._h = None
 
+    @staticmethod
+    def request(mesh, phys, bg, q, work, traces, dyn, cfl, flags=0) -> StepReqC:
+        """The C record of one request (the caller keeps the tensors alive while it is used)."""
+        r = StepReqC()
+        r.mesh, r.phys, r.bg = mesh._h, phys.c(), bg._h
+        r.q, r.work, r.traces, r.dyn = _ptr(q), _ptr(work), _ptr(traces), _ptr(dyn)
+        r.cfl = float(cfl)
+        r.flags = int(flags)
+        return r
+
     def step(self, reqs, stream=None):
         """reqs: sequence of (mesh, phys, background, q, work, traces, dyn, cfl[, flags])."""
-        arr = (StepReqC * max(len(reqs), 1))()
-        for i, req in enumerate(reqs):
-            mesh, phys, bg, q, work, traces, dyn, cfl = req[:8]
-            r = arr[i]
-            r.mesh, r.phys, r.bg = mesh._h, phys.c(), bg._h
-            r.q, r.work, r.traces, r.dyn = _ptr(q), _ptr(work), _ptr(traces), _ptr(dyn)
-            r.cfl = float(cfl)
-            r.flags = int(req[8]) if len(req) > 8 else 0
-        _check(lib().sd_step_packed(self._h, len(reqs), arr, _stream(stream)))
+        self.step_records([self.request(*req) for req in reqs], stream)
+
+    def step_records(self, recs, stream=None):
+        """recs: sequence of StepReqC records (see request())."""
+        arr = (StepReqC * max(len(recs), 1))(*recs)
+        _check(lib().sd_step_packed(self._h, len(recs), arr, _stream(stream)))

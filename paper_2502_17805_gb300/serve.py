@@ -8,10 +8,13 @@ the FP32-mixed path.  The server
   (two FP64 states, FP32 face traces, background tables and the transient of
   building the background) fits in the HBM budget next to the running ones;
 * keeps every admitted state resident on the device;
-* advances all running requests together: each tick is one sd_step_packed
-  call, i.e. per order N one launch of each kernel over the elements of every
-  running request of that order; requests that arrive meanwhile join at the
-  next tick, so their work overlaps with the others' on the device;
+* advances running requests together: each tick is one sd_step_packed call,
+  i.e. per order N one launch of each kernel over the elements of every
+  request the tick steps; by default a tick takes the requests with the least
+  remaining work first, up to a solution-point budget that fills the GPU, so
+  small requests are not held back behind large ones and several small ones
+  share launches; requests that arrive meanwhile join at the next tick, so
+  their work overlaps with the others' on the device;
 * retires a request after K steps, records its latency (completion minus
   arrival, the completion taken from a CUDA event after its last tick) and
   frees its memory, which may admit waiting requests;
@@ -102,14 +105,24 @@ class _Running:
         self.dyn = torch.zeros(4, dtype=torch.float64, device="cuda")
         self.steps_done = 0
         self.ready = False  # the previous step left the traces and lambda_max of q
+        self._rec = None
 
     def keep(self) -> bool:
         """another step of this request follows the one about to be issued"""
         return self.steps_done + 1 < self.req.steps
 
+    def flags(self) -> int:
+        return (sdmhd.REQ_KEEP_TRACES if self.keep() else 0) | (sdmhd.REQ_TRACES_READY if self.ready else 0)
+
     def as_packed(self):
-        flags = (sdmhd.REQ_KEEP_TRACES if self.keep() else 0) | (sdmhd.REQ_TRACES_READY if self.ready else 0)
-        return (self.mesh, self.phys, self.bg, self.q, self.work, self.traces, self.dyn, self.req.cfl, flags)
+        return (self.mesh, self.phys, self.bg, self.q, self.work, self.traces, self.dyn, self.req.cfl, self.flags())
+
+    def record(self):
+        """the request's C record for the next step (built once, its flags updated)"""
+        if self._rec is None:
+            self._rec = sdmhd.Packer.request(*self.as_packed())
+        self._rec.flags = self.flags()
+        return self._rec
 
     def advanced(self):
         """after the step from as_packed() has been issued"""
@@ -127,8 +140,24 @@ def footprint_bytes(info: dict, n_pts: int) -> int:
 
 
 class Server:
-    def __init__(self, hbm_budget_bytes: int, max_running: int = 256):
+    def __init__(self, hbm_budget_bytes: int, max_running: int = 256, policy: str = "backfill",
+                 tick_dof: int = 2_000_000, backfill_frac: float = 0.25):
+        """Which running requests a tick steps (the others stay resident and wait):
+        "backfill" (default): the oldest running request every tick, so that no request waits
+            behind later ones, plus the others in order of least remaining work (steps left x
+            DOF) while the tick holds at most max(tick_dof, (1 + backfill_frac) x the oldest
+            request's DOF) solution points: small requests ride along in the capacity a large
+            one leaves, and several small ones fill one tick;
+        "srpt": least remaining work first up to tick_dof solution points (at least one
+            request): the smallest mean latency, but a large request waits while smaller ones
+            keep arriving;
+        "all": every running request every tick (processor sharing)."""
+        if policy not in ("backfill", "srpt", "all"):
+            raise ValueError("policy must be 'backfill', 'srpt' or 'all'")
         self.budget = int(hbm_budget_bytes)
+        self.policy = policy
+        self.tick_dof = int(tick_dof)
+        self.backfill_frac = float(backfill_frac)
         self.packer = sdmhd.Packer(max_running)
         self.max_running = max_running
         self.meshes: Dict[Tuple[int, int, int], sdmhd.Mesh] = {}
@@ -210,14 +239,16 @@ class Server:
                 elif i < len(pending):
                     time.sleep(max(0.0, pending[i].arrival - (time.perf_counter() - t0)))
                 continue
-            # one tick: every running request advances one step
-            self.packer.step([run.as_packed() for run, _ in running])
+            # one tick: the chosen running requests advance one step
+            chosen = self.choose(running)
+            self.packer.step_records([running[k][0].record() for k in chosen])
             ev = torch.cuda.Event(enable_timing=True)
             ev.record(stream)
             self.ticks += 1
+            for k in chosen:
+                running[k][0].advanced()
             keep, done_reqs, done_runs, fp_done = [], [], [], 0
             for run, fp in running:
-                run.advanced()
                 if run.steps_done >= run.req.steps:
                     done_reqs.append(run.req)
                     done_runs.append(run)  # released (stream-ordered) once retired
@@ -235,6 +266,25 @@ class Server:
                 "aggregate": dof_updates / wall, "p50_ms": float(np.percentile(lat, 50) * 1e3),
                 "p99_ms": float(np.percentile(lat, 99) * 1e3), "mean_ms": float(lat.mean() * 1e3),
                 "peak_bytes": self.peak_bytes, "budget_bytes": self.budget, "ticks": self.ticks}
+
+    def choose(self, running) -> List[int]:
+        """Indices into `running` ((_Running, footprint) pairs) of the requests the next tick steps."""
+        if self.policy == "all":
+            return list(range(len(running)))
+        order = sorted(range(len(running)), key=lambda k: (
+            (running[k][0].req.steps - running[k][0].steps_done) * running[k][0].req.dof, running[k][0].req.arrival))
+        chosen, dof, cap = [], 0, self.tick_dof
+        if self.policy == "backfill":
+            head = min(range(len(running)), key=lambda k: (running[k][0].req.arrival, running[k][0].req.rid))
+            chosen, dof = [head], running[head][0].req.dof
+            cap = max(self.tick_dof, (1.0 + self.backfill_frac) * dof)
+            order = [k for k in order if k != head]
+        for k in order:
+            if chosen and dof + running[k][0].req.dof > cap:
+                continue  # a smaller request further on may still fit
+            chosen.append(k)
+            dof += running[k][0].req.dof
+        return sorted(chosen)
 
     def final_state(self, req: Request):
         """Run one request alone to completion (for checks); returns its final state on the device."""

@@ -32,6 +32,39 @@ def test_footprint_grows_with_the_mesh():
     assert serve.footprint_bytes(info_big, 1536 * 64) > 3 * serve.footprint_bytes(info_small, 384 * 64)
 
 
+def test_tick_policy_takes_least_remaining_work_first_up_to_the_budget():
+    from types import SimpleNamespace as NS
+
+    def run(dof, steps_left, arrival=0.0):
+        return (NS(req=NS(dof=dof, steps=steps_left, arrival=arrival), steps_done=0), 0)
+
+    srv = serve.Server.__new__(serve.Server)
+    srv.policy, srv.tick_dof, srv.backfill_frac = "srpt", 1000, 0.25
+    running = [run(900, 10), run(100, 50), run(300, 2), run(50, 1), run(600, 1)]
+    # remaining work: 9000, 5000, 600, 50, 600 -> order 3, 2, 4 (ties keep their order), 1, 0
+    assert srv.choose(running) == [2, 3, 4]  # 50 + 300 + 600 DOF; 100 more would pass the 1000 budget
+    srv.tick_dof = 10
+    assert srv.choose(running) == [3]  # a lone request always runs, even above the budget
+    srv.policy = "all"
+    assert srv.choose(running) == [0, 1, 2, 3, 4]
+
+
+def test_backfill_policy_always_steps_the_oldest_request():
+    from types import SimpleNamespace as NS
+
+    def run(rid, dof, steps_left, arrival):
+        return (NS(req=NS(rid=rid, dof=dof, steps=steps_left, arrival=arrival), steps_done=0), 0)
+
+    srv = serve.Server.__new__(serve.Server)
+    srv.policy, srv.tick_dof, srv.backfill_frac = "backfill", 1000, 0.25
+    # the oldest (index 1) is large: the tick may hold 1.25 x its 4000 DOF, smallest remaining work first
+    running = [run(0, 300, 5, 0.2), run(1, 4000, 40, 0.0), run(2, 800, 1, 0.3), run(3, 200, 2, 0.1)]
+    assert srv.choose(running) == [1, 2, 3]  # 4000 + 200 (rid 3) + 800 (rid 2) = 5000; rid 0 no longer fits
+    # a small oldest request: the tick fills up to tick_dof
+    running[1] = run(1, 100, 3, 0.0)
+    assert srv.choose(running) == [0, 1, 3]  # 100 + 200 + 300 = 600; rid 2 would make 1400
+
+
 gpu = pytest.mark.gpu
 
 

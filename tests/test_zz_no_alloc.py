@@ -55,7 +55,7 @@ def test_noalloc_residual_matches_sd_residual_on_consecutive_calls(case, N):
 
 def test_noalloc_rejects_meshes_beyond_its_scratch():
     N = 6
-    v, h = inputs.shell_mesh(4, 6)  # 576 elements: traces need 8.96 MB > 8 MiB
+    v, h = inputs.shell_mesh(4, 6)  # 576 elements: traces and face fluxes need 14.2 MB > 8 MiB
     gm = sdmhd.Mesh(N, v, h, geom=1, r_in=0.7, r_out=0.98)
     q = gm.empty_state()
     with pytest.raises(sdmhd.SDError) as exc:
