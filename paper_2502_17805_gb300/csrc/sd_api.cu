@@ -177,6 +177,20 @@ void ops_to_f32(const sd::Ops<double>& a, sd::Ops<float>& b) {
   for (int i = 0; i <= sd::kMaxN; ++i) b.xf[i] = (float)a.xf[i];
 }
 
+void ops_to_pairs(int N, const sd::Ops<float>& a, sd::Ops2& b) {
+  memset(&b, 0, sizeof(b));
+  for (int i = 0; i < (sd::kMaxN + 1) * sd::kMaxN; ++i) {
+    b.Es[i] = make_float2(a.Es[i], a.Es[i]);
+    b.Ed[i] = make_float2(a.Ed[i], a.Ed[i]);
+    b.Ds[i] = make_float2(a.Ds[i], a.Ds[i]);
+    b.Dd[i] = make_float2(a.Dd[i], a.Dd[i]);
+  }
+  for (int i = 0; i < N; ++i) {
+    b.E0[i] = make_float2(a.E[i], a.E[i]);
+    b.EN[i] = make_float2(a.E[N * N + i], a.E[N * N + i]);
+  }
+}
+
 // ---------------------------------------------------------------- mesh topology
 
 // corner of face F at face-local corner (s, t); the face-local axes are the two
@@ -599,6 +613,7 @@ sd_status sd_mesh_create(const sd_mesh_desc* desc, void* stream, sd_mesh** out) 
   m->wait_spins = sd::kWaitSpins;
   build_ops(N, m->ops64);
   ops_to_f32(m->ops64, m->ops32);
+  ops_to_pairs(N, m->ops32, m->ops2);
   const int64_t N2 = (int64_t)N * N, N3 = N2 * N, NF = N + 1;
   const size_t ne = (size_t)std::max<int64_t>(n_e, 1);
   int64_t bytes = 0;

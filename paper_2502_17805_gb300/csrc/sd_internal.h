@@ -35,6 +35,19 @@ struct Ops {
   R xf[kMaxN + 1];
 };
 
+// The FP32 line operators for Blackwell's paired FP32 arithmetic: every
+// coefficient of the even-odd split of E and D (Ops::Es, Ed, Ds, Dd) and of the
+// extrapolation to the two ends of a line (E[0][i], E[N][i]) held twice,
+// {c, c}, so that one paired FMA applies it to two variables at once.
+struct Ops2 {
+  float2 Es[(kMaxN + 1) * kMaxN];
+  float2 Ed[(kMaxN + 1) * kMaxN];
+  float2 Ds[kMaxN * (kMaxN + 1)];
+  float2 Dd[kMaxN * (kMaxN + 1)];
+  float2 E0[kMaxN];
+  float2 EN[kMaxN];
+};
+
 // Face metadata word: neighbour face (3 bits) | orientation code << 3 |
 // boundary condition << 6 | owner << 9.  Orientation code: bit 2 swaps the
 // two face-local indices, bits 1 and 0 flip the first and second.
@@ -155,6 +168,7 @@ struct sd_mesh {
   int64_t device_bytes;
   sd::Ops<double> ops64;
   sd::Ops<float> ops32;
+  sd::Ops2 ops2;
   // kernel timing: event pairs (start, stop) with a kernel class
   int prof_on;
   std::vector<cudaEvent_t> prof_ev;

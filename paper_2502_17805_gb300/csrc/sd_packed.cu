@@ -25,7 +25,7 @@
 
 namespace sd {
 cudaError_t launch_packed_mixed(int N, int kind, const StageParams* tab, const int64_t* off, int n_req,
-                                int64_t blocks, const Ops<float>& ops, cudaStream_t s);
+                                int64_t blocks, const Ops<float>& ops, const Ops2& o2, cudaStream_t s);
 void set_last_error(const std::string& msg);
 
 // partial maxima of lambda per request (at the end of the request's traces scratch)
@@ -314,7 +314,7 @@ sd_status sd_step_packed(sd_packer* pk, int32_t n, const sd_step_req* reqs, void
     if (!any) continue;
     const int64_t blocks = OFF[g.off0 + ng];
     err = sd::launch_packed_mixed(g.N, 0, pk->d_tab[b] + 0 * n + g.k0, pk->d_off[b] + g.off0, ng, blocks,
-                                  reqs[order[g.k0]].mesh->ops32, s);
+                                  reqs[order[g.k0]].mesh->ops32, reqs[order[g.k0]].mesh->ops2, s);
   }
   if (err == cudaSuccess) {
     sd::packed_control_kernel<<<cblocks, 128, 0, s>>>(pk->d_ctl[b], n);
@@ -326,7 +326,7 @@ sd_status sd_step_packed(sd_packer* pk, int32_t n, const sd_step_req* reqs, void
       const int ng = g.k1 - g.k0;
       const int64_t blocks = OFF[g.off0 + ng];
       err = sd::launch_packed_mixed(g.N, st == 2 ? 2 : 1, pk->d_tab[b] + (1 + st) * n + g.k0, pk->d_off[b] + g.off0, ng,
-                                    blocks, reqs[order[g.k0]].mesh->ops32, s);
+                                    blocks, reqs[order[g.k0]].mesh->ops32, reqs[order[g.k0]].mesh->ops2, s);
     }
   if (err == cudaSuccess) err = cudaEventRecord(pk->read[b], s);
   if (err != cudaSuccess) return pk_fail(SD_ERR_CUDA, std::string("packed launch: ") + cudaGetErrorString(err));

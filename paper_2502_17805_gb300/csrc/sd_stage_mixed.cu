@@ -8,7 +8,7 @@ namespace sd {
 template <int N>
 static cudaError_t launch_mixed_n(const sd_mesh* m, const StageParams& P, bool traces_only, cudaStream_t s) {
   if (traces_only) return launch_traces_t<N, PolMixed>(P, m->ops32, s);
-  return launch_stage_v2_t<N>(P, m->ops32, s);
+  return launch_stage_v2_t<N>(P, m->ops2, s);
 }
 
 cudaError_t launch_stage_mixed(const sd_mesh* m, const StageParams& P, bool traces_only, cudaStream_t s) {
@@ -25,15 +25,15 @@ cudaError_t launch_stage_mixed(const sd_mesh* m, const StageParams& P, bool trac
 }
 
 cudaError_t launch_packed_mixed(int N, int kind, const StageParams* tab, const int64_t* off, int n_req,
-                                int64_t blocks, const Ops<float>& ops, cudaStream_t s) {
+                                int64_t blocks, const Ops<float>& ops, const Ops2& o2, cudaStream_t s) {
   switch (N) {
-    case 2: return launch_packed_t<2>(kind, tab, off, n_req, blocks, ops, s);
-    case 3: return launch_packed_t<3>(kind, tab, off, n_req, blocks, ops, s);
-    case 4: return launch_packed_t<4>(kind, tab, off, n_req, blocks, ops, s);
-    case 5: return launch_packed_t<5>(kind, tab, off, n_req, blocks, ops, s);
-    case 6: return launch_packed_t<6>(kind, tab, off, n_req, blocks, ops, s);
-    case 7: return launch_packed_t<7>(kind, tab, off, n_req, blocks, ops, s);
-    case 8: return launch_packed_t<8>(kind, tab, off, n_req, blocks, ops, s);
+    case 2: return launch_packed_t<2>(kind, tab, off, n_req, blocks, ops, o2, s);
+    case 3: return launch_packed_t<3>(kind, tab, off, n_req, blocks, ops, o2, s);
+    case 4: return launch_packed_t<4>(kind, tab, off, n_req, blocks, ops, o2, s);
+    case 5: return launch_packed_t<5>(kind, tab, off, n_req, blocks, ops, o2, s);
+    case 6: return launch_packed_t<6>(kind, tab, off, n_req, blocks, ops, o2, s);
+    case 7: return launch_packed_t<7>(kind, tab, off, n_req, blocks, ops, o2, s);
+    case 8: return launch_packed_t<8>(kind, tab, off, n_req, blocks, ops, o2, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -15,11 +15,15 @@
 //   E  points   R = -sum_d div_d / |J| + M + R0, FP64 RK sum, q' of the new state -> sQ
 //   F  lines    face traces of the new state (the two ends of every line).
 // Thread count T = 256 (N >= 6), 96 (N = 4) or 128; G = T / (3 N^2) threads
-// share a line in B, D and F.
+// share a line in B, D and F.  The line phases work on two variables at a time
+// and phase C on two interior flux points at a time, in Blackwell's paired FP32
+// arithmetic (one instruction for both lanes, each lane rounded as the scalar
+// operation rounds it).
 #pragma once
 
 #include "sd_internal.h"
 #include "sd_physics.cuh"
+#include "sd_physics2.cuh"
 #include "sd_stage.cuh"
 
 namespace sd {
@@ -67,7 +71,7 @@ __device__ __forceinline__ float new_qprime(int v, double qo, float qo32, float 
 }
 
 template <int N, bool EXACT, bool INCR>
-__device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops<float>& ops, const int64_t e,
+__device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops2& o2, const int64_t e,
                                               unsigned char* smem_raw) {
   using DV = DimsV2<N>;
   constexpr int N2 = DV::N2, N3 = DV::N3, NF = DV::NF, T = DV::T, NL = DV::NLINE;
@@ -259,66 +263,87 @@ __device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops<fl
   const bool classic_qn = rka != 0.0f;
   const MixedConsts MC{sConst[6], sConst[7], sConst[8], P.gravity, P.coriolis, P.powell};
 
-  // ---- B: extrapolate every line to its N+1 flux points (one variable at a time:
-  //      N values in registers, N+1 outputs)
+  // ---- B: extrapolate every line to its N+1 flux points, two variables at a time
+  //      (variable pairs (0,1) ... (10,10): N values of each in the lanes of a
+  //      register pair, N+1 outputs)
   if (is_line) {
     float* X = sX + (ld * NF * 11) * N2 + lL;
 #pragma unroll 1
-    for (int v = lg; v < 11; v += G) {
-      float ql[N];
+    for (int pr = lg; pr < 6; pr += G) {
+      const int v0 = 2 * pr, v1 = v0 + 1 < 11 ? v0 + 1 : v0;
+      float2 ql[N];
 #pragma unroll
-      for (int i = 0; i < N; ++i) ql[i] = sQ[v * N3 + lbase + i * lstride];
+      for (int i = 0; i < N; ++i)
+        ql[i] = make_float2(sQ[v0 * N3 + lbase + i * lstride], sQ[v1 * N3 + lbase + i * lstride]);
       // even-odd form: the pair (f, N-f) of outputs from the sums and differences
-      // of the pairs (i, N-1-i) of inputs (operators from the parameter bank)
+      // of the pairs (i, N-1-i) of inputs
       constexpr int HP = N / 2;
-      float sv[HP], dv[HP];
+      float2 sv[HP], dv[HP];
 #pragma unroll
       for (int i = 0; i < HP; ++i) {
-        sv[i] = ql[i] + ql[N - 1 - i];
-        dv[i] = ql[i] - ql[N - 1 - i];
+        sv[i] = add2(ql[i], ql[N - 1 - i]);
+        dv[i] = sub2(ql[i], ql[N - 1 - i]);
       }
 #pragma unroll
       for (int f = 0; 2 * f <= N; ++f) {
-        float a = (N & 1) ? ops.Es[f * N + HP] * ql[HP] : 0.0f;
-        float b = 0.0f;
+        float2 a = (N & 1) ? mul2(o2.Es[f * N + HP], ql[HP]) : make_float2(0.0f, 0.0f);
+        float2 b = make_float2(0.0f, 0.0f);
 #pragma unroll
         for (int i = 0; i < HP; ++i) {
-          a = fmaf(ops.Es[f * N + i], sv[i], a);
-          b = fmaf(ops.Ed[f * N + i], dv[i], b);
+          a = fma2(o2.Es[f * N + i], sv[i], a);
+          b = fma2(o2.Ed[f * N + i], dv[i], b);
         }
         if (2 * f == N) {
-          X[(f * 11 + v) * N2] = a;
+          X[(f * 11 + v0) * N2] = a.x;
+          X[(f * 11 + v1) * N2] = a.y;
         } else {
-          X[(f * 11 + v) * N2] = a + b;
-          X[((N - f) * 11 + v) * N2] = a - b;
+          const float2 pa = add2(a, b), ma = sub2(a, b);
+          X[(f * 11 + v0) * N2] = pa.x;
+          X[(f * 11 + v1) * N2] = pa.y;
+          X[((N - f) * 11 + v0) * N2] = ma.x;
+          X[((N - f) * 11 + v1) * N2] = ma.y;
         }
       }
     }
   }
   __syncthreads();
 
-  // ---- C: fluxes at the flux points (interior first, then the element faces)
-  // interior points first, their count padded to whole warps so that no warp
-  // mixes the two kinds of point
-  constexpr int NINT = 3 * (N - 1) * N2, NINT_W = (NINT + 31) / 32 * 32;
-  for (int t = tid; t < NINT_W + 6 * N2; t += T) {
-    if (t < NINT_W) {
-      if (t >= NINT) continue;
-      const int d = t / ((N - 1) * N2), r = t - d * ((N - 1) * N2);
-      const int f = 1 + r / N2, L = r - (f - 1) * N2;
-      float* X = sX + ((d * NF + f) * 11) * N2 + L;
-      float qf[11];
+  // ---- C: fluxes at the flux points: pairs of interior points first (point r and
+  //      point r + NINT/2 in the lanes of one paired evaluation), their count
+  //      padded to whole warps so that no warp mixes the two kinds of work, then
+  //      the element faces one point at a time
+  constexpr int NINT = 3 * (N - 1) * N2, NIP = NINT / 2, NIP_W = (NIP + 31) / 32 * 32;
+  static_assert(NINT % 2 == 0, "interior flux points pair up");
+  const Mixed2 C2{f2(gamma), f2(gm1), f2(gg1), f2(ch), f2(0.5f)};
+  for (int t = tid; t < NIP_W + 6 * N2; t += T) {
+    if (t < NIP_W) {
+      if (t >= NIP) continue;
+      float* Xp[2];
+      float2 qf[11], S[3];
 #pragma unroll
-      for (int v = 0; v < 11; ++v) qf[v] = X[v * N2];
-      const float* Sp = Sfam + (d * 3 * N2 + L) * NF + f;
-      const float Sx = __ldg(Sp), Sy = __ldg(Sp + N2 * NF), Sz = __ldg(Sp + 2 * N2 * NF);
-      float Fv[9];
-      flux_pert(qf, Sx, Sy, Sz, gm1, gg1, ch, Fv);
+      for (int h = 0; h < 2; ++h) {
+        const int r0 = t + h * NIP;
+        const int d = r0 / ((N - 1) * N2), r = r0 - d * ((N - 1) * N2);
+        const int f = 1 + r / N2, L = r - (f - 1) * N2;
+        Xp[h] = sX + ((d * NF + f) * 11) * N2 + L;
+        const float* Sp = Sfam + (d * 3 * N2 + L) * NF + f;
 #pragma unroll
-      for (int v = 0; v < 9; ++v) X[v * N2] = Fv[v];
-      X[9 * N2] = Sx * qf[5] + Sy * qf[6] + Sz * qf[7];
+        for (int c = 0; c < 3; ++c) (h ? S[c].y : S[c].x) = __ldg(Sp + c * N2 * NF);
+#pragma unroll
+        for (int v = 0; v < 11; ++v) (h ? qf[v].y : qf[v].x) = Xp[h][v * N2];
+      }
+      float2 Fv[9];
+      flux_pert2(qf, S[0], S[1], S[2], C2, Fv);
+      const float2 SB = dot3(S[0], S[1], S[2], qf[5], qf[6], qf[7]);
+#pragma unroll
+      for (int v = 0; v < 9; ++v) {
+        Xp[0][v * N2] = Fv[v].x;
+        Xp[1][v * N2] = Fv[v].y;
+      }
+      Xp[0][9 * N2] = SB.x;
+      Xp[1][9 * N2] = SB.y;
     } else {
-      const int u = t - NINT_W;
+      const int u = t - NIP_W;
       const int F = u / N2, pt = u - F * N2, a = pt % N, b = pt / N;
       const int d = F >> 1, side = F & 1, f = side ? N : 0;
       float* X = sX + ((d * NF + f) * 11) * N2 + pt;
@@ -369,37 +394,42 @@ __device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops<fl
 
   // ---- D: derivative of the flux polynomial along every line, written over the
   //      line's own flux slots (value i of variable v goes to slot (f = i, v)):
-  //      each thread reads and writes only its own line, one variable at a time.
+  //      each thread reads and writes only its own line, two variables at a time.
   if (is_line) {
     float* X = sX + (ld * NF * 11) * N2 + lL;
 #pragma unroll 1
-    for (int v = lg; v < 10; v += G) {
-      float fv[NF];
+    for (int pr = lg; pr < 5; pr += G) {
+      const int v0 = 2 * pr, v1 = v0 + 1;
+      float2 fv[NF];
 #pragma unroll
-      for (int f = 0; f <= N; ++f) fv[f] = X[(f * 11 + v) * N2];
+      for (int f = 0; f <= N; ++f) fv[f] = make_float2(X[(f * 11 + v0) * N2], X[(f * 11 + v1) * N2]);
       // even-odd form: D[N-1-i][f] = -D[i][N-f] gives the pair (i, N-1-i) from the
       // sums and differences of the flux pairs (f, N-f)
       constexpr int HF = NF / 2;
-      float sf[HF], df[HF];
+      float2 sf[HF], df[HF];
 #pragma unroll
       for (int f = 0; f < HF; ++f) {
-        sf[f] = fv[f] + fv[N - f];
-        df[f] = fv[f] - fv[N - f];
+        sf[f] = add2(fv[f], fv[N - f]);
+        df[f] = sub2(fv[f], fv[N - f]);
       }
 #pragma unroll
       for (int i = 0; 2 * i <= N - 1; ++i) {
-        float p = (NF & 1) ? ops.Ds[i * NF + HF] * fv[HF] : 0.0f;
-        float r = 0.0f;
+        float2 p = (NF & 1) ? mul2(o2.Ds[i * NF + HF], fv[HF]) : make_float2(0.0f, 0.0f);
+        float2 r = make_float2(0.0f, 0.0f);
 #pragma unroll
         for (int f = 0; f < HF; ++f) {
-          p = fmaf(ops.Ds[i * NF + f], sf[f], p);
-          r = fmaf(ops.Dd[i * NF + f], df[f], r);
+          p = fma2(o2.Ds[i * NF + f], sf[f], p);
+          r = fma2(o2.Dd[i * NF + f], df[f], r);
         }
         if (2 * i == N - 1) {
-          X[(i * 11 + v) * N2] = r;
+          X[(i * 11 + v0) * N2] = r.x;
+          X[(i * 11 + v1) * N2] = r.y;
         } else {
-          X[(i * 11 + v) * N2] = p + r;
-          X[((N - 1 - i) * 11 + v) * N2] = r - p;
+          const float2 pr_ = add2(p, r), mr = sub2(r, p);
+          X[(i * 11 + v0) * N2] = pr_.x;
+          X[(i * 11 + v1) * N2] = pr_.y;
+          X[((N - 1 - i) * 11 + v0) * N2] = mr.x;
+          X[((N - 1 - i) * 11 + v1) * N2] = mr.y;
         }
       }
     }
@@ -524,31 +554,35 @@ __device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops<fl
   }
   if (exact && P.lam_max) speed_reduce(lam, P.lam_max, P.lam_nslot);
 
-  // ---- F: face traces of the new state
+  // ---- F: face traces of the new state, two variables at a time (each lane the
+  //      trace kernel's sum in its order)
   if (mode == MODE_RK && P.tr_out) {
     __syncthreads();
     if (is_line) {
       float* Tr = reinterpret_cast<float*>(P.tr_out) + (e * 6 + 2 * ld) * 9 * N2 + lL;
 #pragma unroll 1
-      for (int v = lg; v < 9; v += G) {
-        float s0 = 0.0f, s1 = 0.0f;
+      for (int pr = lg; pr < 5; pr += G) {
+        const int v0 = 2 * pr, v1 = v0 + 1 < 9 ? v0 + 1 : v0;
+        float2 s0 = make_float2(0.0f, 0.0f), s1 = make_float2(0.0f, 0.0f);
 #pragma unroll
         for (int i = 0; i < N; ++i) {
-          const float x = sQ[v * N3 + lbase + i * lstride];
-          s0 = fmaf(ops.E[i], x, s0);
-          s1 = fmaf(ops.E[N * N + i], x, s1);
+          const float2 x = make_float2(sQ[v0 * N3 + lbase + i * lstride], sQ[v1 * N3 + lbase + i * lstride]);
+          s0 = fma2(o2.E0[i], x, s0);
+          s1 = fma2(o2.EN[i], x, s1);
         }
-        Tr[v * N2] = s0;
-        Tr[9 * N2 + v * N2] = s1;
+        Tr[v0 * N2] = s0.x;
+        Tr[9 * N2 + v0 * N2] = s1.x;
+        Tr[v1 * N2] = s0.y;
+        Tr[9 * N2 + v1 * N2] = s1.y;
       }
     }
   }
 }
 
 template <int N, bool EXACT, bool INCR>
-__global__ void __launch_bounds__(DimsV2<N>::T, DimsV2<N>::MINB) stage_kernel_v2(const StageParams P, const Ops<float> ops) {
+__global__ void __launch_bounds__(DimsV2<N>::T, DimsV2<N>::MINB) stage_kernel_v2(const StageParams P, const Ops2 o2) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  stage_body_v2<N, EXACT, INCR>(P, ops, (int64_t)blockIdx.x, smem_raw);
+  stage_body_v2<N, EXACT, INCR>(P, o2, (int64_t)blockIdx.x, smem_raw);
 }
 
 // Packed launch over several requests (see packed_request in sd_stage.cuh); the
@@ -559,16 +593,16 @@ __global__ void __launch_bounds__(DimsV2<N>::T, DimsV2<N>::MINB) stage_kernel_v2
 template <int N, bool EXACT>
 __global__ void __launch_bounds__(DimsV2<N>::T, DimsV2<N>::MINB) stage_kernel_v2_packed(const StageParams* __restrict__ tab,
                                                                          const int64_t* __restrict__ off, int n_req,
-                                                                         const Ops<float> ops) {
+                                                                         const Ops2 o2) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ StageParams sP;
   const int r = packed_request(off, n_req, (int64_t)blockIdx.x);
   copy_params(tab + r, &sP);
-  stage_body_v2<N, EXACT, true>(sP, ops, (int64_t)blockIdx.x - __ldg(off + r), smem_raw);
+  stage_body_v2<N, EXACT, true>(sP, o2, (int64_t)blockIdx.x - __ldg(off + r), smem_raw);
 }
 
 template <int N, bool EXACT, bool INCR>
-cudaError_t launch_stage_v2_e(const StageParams& P, const Ops<float>& ops, cudaStream_t s) {
+cudaError_t launch_stage_v2_e(const StageParams& P, const Ops2& o2, cudaStream_t s) {
   using DV = DimsV2<N>;
   auto kern = stage_kernel_v2<N, EXACT, INCR>;
   cudaError_t err =
@@ -579,7 +613,7 @@ cudaError_t launch_stage_v2_e(const StageParams& P, const Ops<float>& ops, cudaS
     if (err != cudaSuccess) return err;
   }
   if (P.n_e == 0) return cudaSuccess;
-  kern<<<(unsigned)P.n_e, DV::T, DV::bytes, s>>>(P, ops);
+  kern<<<(unsigned)P.n_e, DV::T, DV::bytes, s>>>(P, o2);
   return cudaGetLastError();
 }
 
@@ -587,10 +621,10 @@ cudaError_t launch_stage_v2_e(const StageParams& P, const Ops<float>& ops, cudaS
 // gives them) and the increment form are separate instantiations, so each
 // stage carries only the code it runs.
 template <int N>
-cudaError_t launch_stage_v2_t(const StageParams& P, const Ops<float>& ops, cudaStream_t s) {
+cudaError_t launch_stage_v2_t(const StageParams& P, const Ops2& o2, cudaStream_t s) {
   const bool exact = P.mode == MODE_RK && P.lam_max;
-  if (P.incr) return exact ? launch_stage_v2_e<N, true, true>(P, ops, s) : launch_stage_v2_e<N, false, true>(P, ops, s);
-  return exact ? launch_stage_v2_e<N, true, false>(P, ops, s) : launch_stage_v2_e<N, false, false>(P, ops, s);
+  if (P.incr) return exact ? launch_stage_v2_e<N, true, true>(P, o2, s) : launch_stage_v2_e<N, false, true>(P, o2, s);
+  return exact ? launch_stage_v2_e<N, true, false>(P, o2, s) : launch_stage_v2_e<N, false, false>(P, o2, s);
 }
 
 // Packed launches of one order N over `blocks` elements of n_req requests: the
@@ -598,7 +632,7 @@ cudaError_t launch_stage_v2_t(const StageParams& P, const Ops<float>& ops, cudaS
 // exact form (kind 2).
 template <int N, bool EXACT>
 cudaError_t launch_packed_stage(const StageParams* tab, const int64_t* off, int n_req, int64_t blocks,
-                                const Ops<float>& ops, cudaStream_t s) {
+                                const Ops2& o2, cudaStream_t s) {
   using DV = DimsV2<N>;
   auto kern = stage_kernel_v2_packed<N, EXACT>;
   cudaError_t err =
@@ -608,13 +642,13 @@ cudaError_t launch_packed_stage(const StageParams* tab, const int64_t* off, int 
     err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DV::bytes);
     if (err != cudaSuccess) return err;
   }
-  kern<<<(unsigned)blocks, DV::T, DV::bytes, s>>>(tab, off, n_req, ops);
+  kern<<<(unsigned)blocks, DV::T, DV::bytes, s>>>(tab, off, n_req, o2);
   return cudaGetLastError();
 }
 
 template <int N>
 cudaError_t launch_packed_t(int kind, const StageParams* tab, const int64_t* off, int n_req, int64_t blocks,
-                            const Ops<float>& ops, cudaStream_t s) {
+                            const Ops<float>& ops, const Ops2& o2, cudaStream_t s) {
   if (blocks == 0) return cudaSuccess;
   if (kind == 0) {
     const size_t bytes = Smem<N, PolMixed>::trace_bytes;
@@ -626,8 +660,8 @@ cudaError_t launch_packed_t(int kind, const StageParams* tab, const int64_t* off
     trace_kernel_packed<N><<<(unsigned)blocks, Dims<N>::BLK, bytes, s>>>(tab, off, n_req, ops);
     return cudaGetLastError();
   }
-  return kind == 2 ? launch_packed_stage<N, true>(tab, off, n_req, blocks, ops, s)
-                   : launch_packed_stage<N, false>(tab, off, n_req, blocks, ops, s);
+  return kind == 2 ? launch_packed_stage<N, true>(tab, off, n_req, blocks, o2, s)
+                   : launch_packed_stage<N, false>(tab, off, n_req, blocks, o2, s);
 }
 
 }  // namespace sd

@@ -158,6 +158,10 @@ class Server:
         self.policy = policy
         self.tick_dof = int(tick_dof)
         self.backfill_frac = float(backfill_frac)
+        # multi-step ticks: a tick of small requests takes several steps (see steps_per_tick)
+        self.tick_seconds = 0.4e-3
+        self.dof_rate = 2.9e9
+        self.step_overhead_s = 30e-6
         self.packer = sdmhd.Packer(max_running)
         self.max_running = max_running
         self.meshes: Dict[Tuple[int, int, int], sdmhd.Mesh] = {}
@@ -187,12 +191,14 @@ class Server:
         recorded after its last tick.  With `states` (a dict), each finished
         request's final device state is stored there under its rid."""
         import torch
+        self.peak_bytes, self.ticks = 0, 0
         pending = sorted(requests, key=lambda r: r.arrival)
         queue: List[Request] = []
         running: List[Tuple[_Running, int]] = []
         # (event, requests completing at that tick, their _Running objects, their footprint)
         inflight: list = []
         used = 0  # footprint of the running requests and of finished ones still held by a tick in flight
+        peak_running = 0
         finished: List[Request] = []
         stream = torch.cuda.current_stream()
         torch.cuda.synchronize()
@@ -233,20 +239,24 @@ class Server:
                 running.append((_Running(r, m), fp))
                 used += fp
                 self.peak_bytes = max(self.peak_bytes, used)
+                peak_running = max(peak_running, len(running))
             if not running:
                 if inflight:
                     retire_oldest()
                 elif i < len(pending):
                     time.sleep(max(0.0, pending[i].arrival - (time.perf_counter() - t0)))
                 continue
-            # one tick: the chosen running requests advance one step
+            # one tick: the chosen running requests advance one step, or several when their step is
+            # short (fewer host round trips per unit of GPU work; none of them finishes early)
             chosen = self.choose(running)
-            self.packer.step_records([running[k][0].record() for k in chosen])
+            n_steps = self.steps_per_tick([running[k][0] for k in chosen])
+            for _ in range(n_steps):
+                self.packer.step_records([running[k][0].record() for k in chosen])
+                for k in chosen:
+                    running[k][0].advanced()
             ev = torch.cuda.Event(enable_timing=True)
             ev.record(stream)
             self.ticks += 1
-            for k in chosen:
-                running[k][0].advanced()
             keep, done_reqs, done_runs, fp_done = [], [], [], 0
             for run, fp in running:
                 if run.steps_done >= run.req.steps:
@@ -265,7 +275,17 @@ class Server:
         return {"requests": len(finished), "wall_s": wall, "dof_updates": dof_updates,
                 "aggregate": dof_updates / wall, "p50_ms": float(np.percentile(lat, 50) * 1e3),
                 "p99_ms": float(np.percentile(lat, 99) * 1e3), "mean_ms": float(lat.mean() * 1e3),
-                "peak_bytes": self.peak_bytes, "budget_bytes": self.budget, "ticks": self.ticks}
+                "peak_bytes": self.peak_bytes, "budget_bytes": self.budget, "ticks": self.ticks,
+                "peak_running": peak_running}
+
+    def steps_per_tick(self, runs) -> int:
+        """Steps a tick takes: enough for about `tick_seconds` of GPU work at `dof_rate` DOF-updates/s
+        (with `step_overhead_s` of launches per step), at most the fewest steps any chosen request
+        has left."""
+        dof = sum(r.req.dof for r in runs)
+        per_step = dof / self.dof_rate + self.step_overhead_s
+        k = max(1, int(self.tick_seconds / per_step))
+        return min(k, min(r.req.steps - r.steps_done for r in runs))
 
     def choose(self, running) -> List[int]:
         """Indices into `running` ((_Running, footprint) pairs) of the requests the next tick steps."""

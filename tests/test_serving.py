@@ -1,6 +1,7 @@
 """Serving: packed steps of independent solves (sd_step_packed) and the
 continuous-batching server.  A request's result must not depend on which other
 requests share its launches."""
+import dataclasses
 import math
 
 import numpy as np
@@ -120,10 +121,15 @@ def test_admission_respects_the_hbm_budget(torch_dev):
     assert out["requests"] == 10
     biggest = max(serve.footprint_bytes(m.info, m.info["n_points"]) for m in srv.meshes.values())
     assert out["peak_bytes"] <= max(srv.budget, biggest)
+    assert out["peak_running"] == 1
+    # all arrived at once: a roomy budget runs them together (they share ticks), the tight one in turn
+    at_once = [dataclasses.replace(r, arrival=0.0) for r in reqs]
     roomy = serve.Server(hbm_budget_bytes=1 << 34, max_running=16)
     roomy.warm(reqs)
-    out2 = roomy.run(reqs)
-    assert out2["requests"] == 10 and out2["ticks"] < out["ticks"]  # overlapping requests share ticks
+    out2 = roomy.run(at_once)
+    out3 = srv.run([dataclasses.replace(r) for r in at_once])
+    assert out2["requests"] == 10 and out2["peak_running"] == 10 and out3["peak_running"] == 1
+    assert out2["ticks"] < out3["ticks"]
 
 
 @gpu
@@ -265,3 +271,14 @@ def test_packed_calls_alternating_streams(torch_dev):
     torch.cuda.synchronize()
     for a, b in zip(one, two):
         assert torch.equal(a.q, b.q)
+
+
+def test_small_ticks_take_several_steps():
+    from types import SimpleNamespace as NS
+    srv = serve.Server.__new__(serve.Server)
+    srv.tick_seconds, srv.dof_rate, srv.step_overhead_s = 0.4e-3, 2.9e9, 30e-6
+    small = [NS(req=NS(dof=24_576, steps=50), steps_done=0), NS(req=NS(dof=48_000, steps=50), steps_done=47)]
+    big = [NS(req=NS(dof=5_308_416, steps=50), steps_done=0)]
+    assert srv.steps_per_tick(small) == 3          # several steps, but no more than a request has left
+    assert srv.steps_per_tick(small[:1]) == 10     # 0.4 ms / (8.5 us + 30 us)
+    assert srv.steps_per_tick(big) == 1            # one step of a large request already fills a tick
