@@ -47,3 +47,16 @@ def test_spherical_sums_reject_bad_arguments():
         gm.spherical_sums(q, 0.70, 0.98, 0, 2, out=out)
     with pytest.raises(sdmhd.SDError, match="out is NULL"):
         gm.spherical_sums(q, 0.70, 0.98, 2, 2, out=torch.zeros(0, dtype=torch.float64, device="cuda"))
+
+
+def test_spherical_sums_repeat_to_round_off():
+    """The bin sums use atomic additions (no fixed order): two calls on the same state agree to
+    round-off of each bin's sum of magnitudes."""
+    N = 5
+    v, h = inputs.shell_mesh(8, 4)
+    gm = sdmhd.Mesh(N, v, h, geom=1, r_in=0.70, r_out=0.98)
+    q = gm.to_device(inputs.random_state(gm.n_e, N, seed=13))
+    a = gm.spherical_sums(q, 0.70, 0.98, 4, 16).cpu().numpy()
+    b = gm.spherical_sums(q, 0.70, 0.98, 4, 16).cpu().numpy()
+    scale = np.abs(a).reshape(-1, 8).max(axis=0)
+    assert np.all(np.abs(a - b).reshape(-1, 8).max(axis=0) <= 1e-13 * scale)
