@@ -121,12 +121,16 @@ def measured_peaks():
 
 
 # the sources the mixed stage kernel is compiled from (its DRAM counters stay valid while these are unchanged)
-KERNEL_SOURCES = ("sd_internal.h", "sd_physics.cuh", "sd_stage.cuh", "sd_stage_v2.cuh", "sd_stage_mixed.cu")
+KERNEL_SOURCES = ("sd_internal.h", "sd_physics.cuh", "sd_physics2.cuh", "sd_stage.cuh", "sd_stage_v2.cuh",
+                  "sd_stage_mixed.cu")
+# the sources of the FP64 stage (face-flux and element kernels)
+FP64_SOURCES = ("sd_internal.h", "sd_physics.cuh", "sd_stage.cuh", "sd_viscous.cuh", "sd_stage_f64.cuh",
+                "sd_stage_fp64.cu")
 
 
-def source_hash() -> str:
+def source_hash(sources=KERNEL_SOURCES) -> str:
     h = hashlib.sha256()
-    for name in KERNEL_SOURCES:
+    for name in sources:
         with open(os.path.join(ROOT, "paper_2502_17805_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -138,13 +142,13 @@ def fp64_peak_tflops(n_sm: int, sm_mhz: float) -> float:
     return n_sm * 2 * 2 * sm_mhz * 1e6 / 1e12
 
 
-def committed_traffic(kernel_key: str):
+def committed_traffic(kernel_key: str, sources=KERNEL_SOURCES):
     """A per-launch counter of a kernel (DRAM bytes, FP64 flops) from a committed ncu summary, if it
     was taken on these sources."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
-    cur = source_hash()
+    cur = source_hash(sources)
     with open(path) as f:
         for line in f:
             parts = line.split()
@@ -396,6 +400,10 @@ def run_serving(n_requests: int, budget_gb: float, tight_budget_gb: float = 4.0)
     srpt.meshes = srv.meshes
     srpt_poisson = served(srpt, fresh(reqs))
     srpt_sat = served(srpt, fresh(reqs, at_zero=True))
+    bf = serve.Server(int(budget_gb * 1e9), max_running=max(n_requests, 1), policy="backfill")
+    bf.meshes = srv.meshes
+    bf_poisson = served(bf, fresh(reqs))
+    bf_sat = served(bf, fresh(reqs, at_zero=True))
     fifo = sequential_fifo(srv, fresh(reqs))
     fifo_sat = sequential_fifo(srv, fresh(reqs, at_zero=True))
     sample = []
@@ -419,11 +427,12 @@ def run_serving(n_requests: int, budget_gb: float, tight_budget_gb: float = 4.0)
     res = dict(out)
     res.update({
         "requests": n_requests, "unit": UNIT,
-        "policy": "oldest request every tick, backfilled with the least remaining work up to max(%d DOF, "
-                  "%.2f x the oldest request's DOF)" % (srv.tick_dof, 1 + srv.backfill_frac),
+        "policy": "least remaining work first, each request's remaining work less %.1f x %.2g DOF/s x its "
+                  "waiting time, up to %d DOF per tick" % (srv.aging, srv.dof_rate, srv.tick_dof),
         "saturating": sat, "saturating_tight_budget": tight,
         "every_request_every_tick": {"poisson": share_poisson, "saturating": share_sat},
         "least_remaining_work_first": {"poisson": srpt_poisson, "saturating": srpt_sat},
+        "oldest_first_with_backfill": {"poisson": bf_poisson, "saturating": bf_sat},
         "sequential_fifo": fifo, "sequential_fifo_saturating": fifo_sat,
         "sequential_mixed": fifo_sat["aggregate"], "sequential_fp64": seq64,
         "sequential_fp64_sample": "one request of each of the four sizes, 5 FP64 steps each (sd_advance)",
@@ -595,7 +604,7 @@ def fp64_roofline(stage_ms: float, clocks, n_pts: int):
     peak = fp64_peak_tflops(n_sm, mhz)
     flops = ALGORITHMIC_FLOP_PER_DOF_STAGE * n_pts
     achieved = flops / (stage_ms / 1e3) / 1e12
-    counted = committed_traffic("stage_fp64_N6_flops")
+    counted = committed_traffic("stage_fp64_N6_flops", FP64_SOURCES)
     return {"kernel": "stage_kernel<6, PolFP64> (FP64 fused stage)", "bound": "fp64", "achieved": achieved,
             "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "peak_source": "derived: %d SMs x 2 FP64 FMA/clk x 2 flop x %.0f MHz" % (n_sm, mhz),

@@ -360,6 +360,16 @@ sd_status sd_diagnostics(const sd_mesh* mesh, const sd_phys* phys, const double*
  * gradient buffers).  Asynchronous. */
 sd_status sd_residual_noalloc(const sd_mesh* mesh, const sd_phys* phys, const double* q, double* dqdt, void* stream);
 
+/* Stream-ordered memory for serving: sd_background_create takes its device
+ * memory from the current device's default memory pool (cudaMallocAsync), which
+ * by default returns freed memory to the system at every synchronisation, so a
+ * service that creates and releases backgrounds continually pays for fresh
+ * allocations.  This call keeps up to `bytes` of freed memory in that pool for
+ * reuse (its release threshold; bytes < 0 keeps all of it).  The setting
+ * belongs to the device's default pool and so applies to every user of that
+ * pool in the process.  Errors: SD_ERR_CUDA. */
+sd_status sd_memory_pool_keep(int64_t bytes);
+
 /* Failure-detection test hook: the number of polls a stage kernel makes on
  * each of its bounded device-side waits (the shared-memory bulk copies of the
  * FP32-mixed stages) before it records a time-out.  spins < 0 restores the

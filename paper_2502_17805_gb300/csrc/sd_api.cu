@@ -1180,6 +1180,17 @@ sd_status sd_diagnostics(const sd_mesh* m, const sd_phys* ph, const double* q, s
   return SD_OK;
 }
 
+sd_status sd_memory_pool_keep(int64_t bytes) {
+  int dev = -1;
+  cudaError_t err = cudaGetDevice(&dev);
+  cudaMemPool_t pool = nullptr;
+  if (err == cudaSuccess) err = cudaDeviceGetDefaultMemPool(&pool, dev);
+  uint64_t keep = bytes < 0 ? UINT64_MAX : (uint64_t)bytes;
+  if (err == cudaSuccess) err = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  if (err != cudaSuccess) return cuda_fail(err, "memory pool release threshold");
+  return SD_OK;
+}
+
 sd_status sd_mesh_set_wait_limit(sd_mesh* m, int32_t spins) {
   if (!m) return fail(SD_ERR_INVALID_ARGUMENT, "mesh is NULL");
   m->wait_spins = spins < 0 ? sd::kWaitSpins : spins;

@@ -7,7 +7,9 @@
 // and launches: lambda reset, one packed trace kernel per N, one step-control
 // kernel (all requests), then for each stage one packed stage kernel per N (the
 // last one in the exact form).  A CTA of a packed kernel finds its request by
-// binary search in the element offsets of its group.
+// binary search in the element offsets of its group and copies its parameters
+// to shared memory; an order with a single request takes the plain kernels
+// instead, with the parameters passed by value (the same arithmetic and bits).
 //
 // A request's `traces` scratch holds three trace buffers A, B, C and its 16
 // partial maxima of lambda.  The trace pass writes A; stage 0 reads A and writes
@@ -26,6 +28,7 @@
 namespace sd {
 cudaError_t launch_packed_mixed(int N, int kind, const StageParams* tab, const int64_t* off, int n_req,
                                 int64_t blocks, const Ops<float>& ops, const Ops2& o2, cudaStream_t s);
+cudaError_t launch_stage_mixed(const sd_mesh* m, const StageParams& P, bool traces_only, cudaStream_t s);
 void set_last_error(const std::string& msg);
 
 // partial maxima of lambda per request (at the end of the request's traces scratch)
@@ -312,6 +315,10 @@ sd_status sd_step_packed(sd_packer* pk, int32_t n, const sd_step_req* reqs, void
     bool any = false;  // a request of the group needs its trace pass
     for (int k = g.k0; k < g.k1 && !any; ++k) any = !(reqs[order[k]].flags & SD_REQ_TRACES_READY);
     if (!any) continue;
+    if (ng == 1) {  // a lone request of its order: the plain kernel, parameters by value
+      err = sd::launch_stage_mixed(reqs[order[g.k0]].mesh, T[0 * n + g.k0], true, s);
+      continue;
+    }
     const int64_t blocks = OFF[g.off0 + ng];
     err = sd::launch_packed_mixed(g.N, 0, pk->d_tab[b] + 0 * n + g.k0, pk->d_off[b] + g.off0, ng, blocks,
                                   reqs[order[g.k0]].mesh->ops32, reqs[order[g.k0]].mesh->ops2, s);
@@ -324,6 +331,10 @@ sd_status sd_step_packed(sd_packer* pk, int32_t n, const sd_step_req* reqs, void
     for (size_t gi = 0; gi < groups.size() && err == cudaSuccess; ++gi) {
       const Group& g = groups[gi];
       const int ng = g.k1 - g.k0;
+      if (ng == 1) {  // the plain stage kernel: the same arithmetic, without the per-block table look-up
+        err = sd::launch_stage_mixed(reqs[order[g.k0]].mesh, T[(1 + st) * n + g.k0], false, s);
+        continue;
+      }
       const int64_t blocks = OFF[g.off0 + ng];
       err = sd::launch_packed_mixed(g.N, st == 2 ? 2 : 1, pk->d_tab[b] + (1 + st) * n + g.k0, pk->d_off[b] + g.off0, ng,
                                     blocks, reqs[order[g.k0]].mesh->ops32, reqs[order[g.k0]].mesh->ops2, s);

@@ -29,7 +29,8 @@ STATUS = {0: "SD_OK", 1: "SD_ERR_INVALID_ARGUMENT", 2: "SD_ERR_UNSUPPORTED", 3: 
 EXPORTS = ["sd_last_error", "sd_mesh_create", "sd_mesh_destroy", "sd_mesh_query", "sd_state_init",
            "sd_background_create", "sd_background_destroy", "sd_residual", "sd_rk_stage", "sd_step", "sd_advance",
            "sd_diagnostics", "sd_spherical_sums", "sd_profile_enable", "sd_profile_read", "sd_residual_noalloc",
-           "sd_packer_create", "sd_packer_destroy", "sd_step_packed", "sd_mesh_set_wait_limit"]
+           "sd_packer_create", "sd_packer_destroy", "sd_step_packed", "sd_mesh_set_wait_limit",
+           "sd_memory_pool_keep"]
 
 
 class SDError(RuntimeError):
@@ -152,6 +153,7 @@ def lib():
         L.sd_diagnostics.argtypes = [vp, C.POINTER(PhysC), vp, C.POINTER(DiagC), vp]
         L.sd_profile_enable.argtypes = [vp, C.c_int32]
         L.sd_mesh_set_wait_limit.argtypes = [vp, C.c_int32]
+        L.sd_memory_pool_keep.argtypes = [C.c_int64]
         L.sd_profile_read.argtypes = [vp, C.POINTER(ProfileC)]
         L.sd_residual_noalloc.argtypes = [vp, C.POINTER(PhysC), vp, vp, vp]
         L.sd_packer_create.argtypes = [C.c_int32, C.POINTER(vp)]
@@ -330,6 +332,12 @@ class Mesh:
             _check(rc)
         out["status"] = rc
         return out
+
+
+def memory_pool_keep(n_bytes: int):
+    """Keep up to n_bytes of freed stream-ordered memory in the current device's default pool
+    (sd_memory_pool_keep; negative: all of it)."""
+    _check(lib().sd_memory_pool_keep(int(n_bytes)))
 
 
 class Packer:

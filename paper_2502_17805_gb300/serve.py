@@ -27,6 +27,7 @@ everything a step writes (states, traces, dt) belongs to the request.
 """
 from __future__ import annotations
 
+import dataclasses
 import math
 import time
 from dataclasses import dataclass, field
@@ -140,10 +141,10 @@ def footprint_bytes(info: dict, n_pts: int) -> int:
 
 
 class Server:
-    def __init__(self, hbm_budget_bytes: int, max_running: int = 256, policy: str = "backfill",
+    def __init__(self, hbm_budget_bytes: int, max_running: int = 256, policy: str = "aged",
                  tick_dof: int = 2_000_000, backfill_frac: float = 0.25):
         """Which running requests a tick steps (the others stay resident and wait):
-        "backfill" (default): the oldest running request every tick, so that no request waits
+        "backfill": the oldest running request every tick, so that no request waits
             behind later ones, plus the others in order of least remaining work (steps left x
             DOF) while the tick holds at most max(tick_dof, (1 + backfill_frac) x the oldest
             request's DOF) solution points: small requests ride along in the capacity a large
@@ -151,10 +152,15 @@ class Server:
         "srpt": least remaining work first up to tick_dof solution points (at least one
             request): the smallest mean latency, but a large request waits while smaller ones
             keep arriving;
+        "aged" (default): least remaining work first, each request's remaining work reduced by
+            aging x dof_rate x its waiting time (the work the GPU could have done for it
+            meanwhile), so that a request passed over long enough moves to the front;
         "all": every running request every tick (processor sharing)."""
-        if policy not in ("backfill", "srpt", "all"):
-            raise ValueError("policy must be 'backfill', 'srpt' or 'all'")
+        if policy not in ("backfill", "srpt", "aged", "all"):
+            raise ValueError("policy must be 'backfill', 'srpt', 'aged' or 'all'")
         self.budget = int(hbm_budget_bytes)
+        # backgrounds come from the stream-ordered pool: keep what retired requests free for reuse
+        sdmhd.memory_pool_keep(self.budget)
         self.policy = policy
         self.tick_dof = int(tick_dof)
         self.backfill_frac = float(backfill_frac)
@@ -162,6 +168,8 @@ class Server:
         self.tick_seconds = 0.4e-3
         self.dof_rate = 2.9e9
         self.step_overhead_s = 30e-6
+        self.aging = 1.0
+        self._now = 0.0  # seconds since the start of the current run (the "aged" policy)
         self.packer = sdmhd.Packer(max_running)
         self.max_running = max_running
         self.meshes: Dict[Tuple[int, int, int], sdmhd.Mesh] = {}
@@ -177,9 +185,21 @@ class Server:
         return self.meshes[key]
 
     def warm(self, requests: Sequence[Request]):
-        """Build the meshes of every shape the workload uses (a running service keeps them)."""
+        """Build the meshes of every shape the workload uses and step one request of each shape once,
+        so that the kernels' set-up and the pool's memory are in place before requests arrive (a
+        running service keeps its meshes and is warm)."""
+        import torch
+        seen = set()
         for r in requests:
-            self.mesh(r.nz, r.nr, r.N)
+            key = (r.nz, r.nr, r.N)
+            self.mesh(*key)
+            if key not in seen:
+                seen.add(key)
+                run = _Running(dataclasses.replace(r, steps=2, arrival=0.0), self.meshes[key])
+                for _ in range(2):
+                    self.packer.step_records([run.record()])
+                    run.advanced()
+        torch.cuda.synchronize()
 
     def run(self, requests: Sequence[Request], depth: int = 2, states: Optional[dict] = None) -> dict:
         """Serve `requests` (arrival times relative to the call) to completion.
@@ -248,6 +268,7 @@ class Server:
                 continue
             # one tick: the chosen running requests advance one step, or several when their step is
             # short (fewer host round trips per unit of GPU work; none of them finishes early)
+            self._now = time.perf_counter() - t0
             chosen = self.choose(running)
             n_steps = self.steps_per_tick([running[k][0] for k in chosen])
             for _ in range(n_steps):
@@ -291,8 +312,14 @@ class Server:
         """Indices into `running` ((_Running, footprint) pairs) of the requests the next tick steps."""
         if self.policy == "all":
             return list(range(len(running)))
-        order = sorted(range(len(running)), key=lambda k: (
-            (running[k][0].req.steps - running[k][0].steps_done) * running[k][0].req.dof, running[k][0].req.arrival))
+        def work(k):
+            r = running[k][0]
+            w = (r.req.steps - r.steps_done) * r.req.dof
+            if self.policy == "aged":
+                w -= self.aging * self.dof_rate * max(0.0, self._now - r.req.arrival)
+            return (w, r.req.arrival)
+
+        order = sorted(range(len(running)), key=work)
         chosen, dof, cap = [], 0, self.tick_dof
         if self.policy == "backfill":
             head = min(range(len(running)), key=lambda k: (running[k][0].req.arrival, running[k][0].req.rid))

@@ -282,3 +282,20 @@ def test_small_ticks_take_several_steps():
     assert srv.steps_per_tick(small) == 3          # several steps, but no more than a request has left
     assert srv.steps_per_tick(small[:1]) == 10     # 0.4 ms / (8.5 us + 30 us)
     assert srv.steps_per_tick(big) == 1            # one step of a large request already fills a tick
+
+
+def test_aged_policy_moves_a_long_waiting_request_forward():
+    """The aged order is that of remaining work + aging x rate x arrival time: a request that arrived
+    early enough goes first even with more work left."""
+    from types import SimpleNamespace as NS
+    srv = serve.Server.__new__(serve.Server)
+    srv.policy, srv.tick_dof, srv.backfill_frac = "aged", 1000, 0.25
+    srv.aging, srv.dof_rate = 1.0, 1000.0
+
+    def run(rid, dof, steps, arrival):
+        return (NS(req=NS(rid=rid, dof=dof, steps=steps, arrival=arrival), steps_done=0), 0)
+
+    big = run(0, 900, 10, 0.0)                 # 9000 DOF-steps left, arrived at 0
+    srv._now = 9.0
+    assert srv.choose([big, run(1, 800, 2, 5.0)]) == [1]  # 1600 + 5000 < 9000 + 0
+    assert srv.choose([big, run(1, 800, 2, 8.0)]) == [0]  # 1600 + 8000 > 9000: the early one first
