@@ -644,21 +644,42 @@ def run_ours(args):
     q64 = q0.clone()
     k64 = max(1, min(args.steps, args.fp64_steps))
     ms64, prof64, _ = time_steps(mesh, phys, q64, work, sdmhd.SD_FP64, None, k64, min(args.warmup, 3), None, barrier)
-    # FP64 path with the viscous, resistive and thermal fluxes (BR1 gradient pass before every stage)
-    visc = None
+    # the viscous, resistive and thermal fluxes: FP64 path (BR1 gradient pass before every stage) and
+    # FP32-mixed path (perturbation gradients and viscous fluxes before every stage, about a background
+    # built with the same coefficients), the same steps from the same state; the mixed path's change of
+    # the state against the FP64 path's, per variable
+    visc = visc_mixed = None
     if not args.no_viscous:
         phys_v = sdmhd.Phys(**{k: getattr(phys, k) for k in ("gamma", "GM", "omega", "glm_alpha", "c_h", "powell",
                                                             "gravity", "coriolis")}, **VISCOUS)
+        coef = {k: v for k, v in VISCOUS.items() if k != "viscous"}
+        wv = min(args.warmup, 3)
         qv = q0.clone()
-        msv, profv, _ = time_steps(mesh, phys_v, qv, work, sdmhd.SD_FP64, None, k64, min(args.warmup, 3), None,
-                                   barrier)
-        msv = max_over_ranks([msv], device="cuda")[0]
+        msv, profv, _ = time_steps(mesh, phys_v, qv, work, sdmhd.SD_FP64, None, k64, wv, None, barrier)
+        bgs = mesh.empty_state()
+        mesh.state_init(phys_v, sdmhd.INIT_SHELL_POLYTROPE, params, seed=0, q=work, background=bgs)
+        bg_v = mesh.background(phys_v, bgs)
+        del bgs
+        qm = q0.clone()
+        msm, profm, _ = time_steps(mesh, phys_v, qm, work, sdmhd.SD_FP32_MIXED, bg_v, k64, wv, None, barrier)
+        dv, dm = qv - q0, qm - q0
+        rel = ((dm - dv).abs().amax(dim=(1, 2)) / dv.abs().amax(dim=(1, 2)).clamp_min(1e-300)).cpu().tolist()
+        msv, msm = max_over_ranks([msv, msm], device="cuda")
         visc = {"value": whole_job_rate(n_pts, k64, world, msv), "unit": UNIT, "steps": k64, "ms_per_step": msv / k64,
-                "dtype": "f64", "coefficients": {k: v for k, v in VISCOUS.items() if k != "viscous"},
+                "dtype": "f64", "coefficients": coef,
                 "kernel_ms_per_step": {"stage": profv["stage_ms"] / k64,
                                        "gradients_and_control": profv["other_ms"] / k64,
                                        "trace_lambda": profv["trace_ms"] / k64}}
-        del qv
+        visc_mixed = {"value": whole_job_rate(n_pts, k64, world, msm), "unit": UNIT, "steps": k64,
+                      "ms_per_step": msm / k64, "dtype": "f32 (perturbation) + f64 (background, RK state)",
+                      "coefficients": coef,
+                      "kernel_ms_per_step": {"stage": profm["stage_ms"] / k64,
+                                             "viscous_gradients_fluxes_and_control": profm["other_ms"] / k64,
+                                             "trace_lambda": profm["trace_ms"] / k64},
+                      "change_vs_fp64": {"steps": wv + k64, "max_rel_per_variable": rel,
+                                         "basis": "max |dq_mixed - dq_fp64| / max |dq_fp64| per variable, "
+                                                  "dq the change of the state over the steps"}}
+        del qv, qm, bg_v
 
     ms, ms64 = max_over_ranks([ms, ms64], device="cuda")
     value = whole_job_rate(n_pts, args.steps, world, ms)
@@ -686,6 +707,7 @@ def run_ours(args):
         "fp64": {"value": value64, "unit": UNIT, "steps": k64, "ms_per_step": ms64 / k64, "dtype": "f64",
                  "stage_avg_ms": stage64_ms, "roofline": fp64_roofline(stage64_ms, clocks, n_pts)},
         "viscous_fp64": visc,
+        "viscous_mixed": visc_mixed,
         "gpu_launches": int(prof["stage_launches"] + prof["trace_launches"] + prof["other_launches"]),
         "kernel_ms_per_step": {"stage": prof["stage_ms"] / args.steps, "trace_lambda": prof["trace_ms"] / args.steps,
                                "control": prof["other_ms"] / args.steps},

@@ -118,12 +118,14 @@ typedef struct {
   int32_t pad_;
   double farfield[9]; /* conserved ghost state of SD_BC_FARFIELD faces */
   /* Viscous, resistive and thermal fluxes F_vis (Sec. MHD Governing Equations; F = F_inv - F_vis),
-   * with gradients of (U, T, S, B) by the BR1 scheme (Sec. SD Method), when viscous != 0 (SD_FP64
-   * only):  mu dynamic viscosity (lambda = -2/3 mu), eta magnetic diffusivity, kappa thermal
-   * diffusivity of the entropy term (constants), kappa_r radiative diffusivity (with kappa_r1 and
-   * kappa_r2 below: kappa_r(r) = kappa_r + kappa_r1 r + kappa_r2 r^2, r = |x| at the point of the heat
-   * flux; the caller keeps it non-negative on the mesh), R_gas specific gas constant (T = p / (rho R_gas), C_p = gamma R_gas / (gamma - 1)).  The
-   * time step of sd_step stays the inviscid one: the caller keeps cfl within the viscous limit. */
+   * with gradients of (U, T, S, B) by the BR1 scheme (Sec. SD Method), when viscous != 0 (both
+   * precisions; SD_FP32_MIXED needs a background built with the same coefficients): mu dynamic
+   * viscosity (lambda = -2/3 mu), eta magnetic diffusivity, kappa thermal diffusivity of the entropy
+   * term (constants), kappa_r radiative diffusivity (with kappa_r1 and kappa_r2 below: kappa_r(r) =
+   * kappa_r + kappa_r1 r + kappa_r2 r^2, r = |x| at the point of the heat flux; the caller keeps it
+   * non-negative on the mesh), R_gas specific gas constant (T = p / (rho R_gas), C_p = gamma R_gas /
+   * (gamma - 1)).  The time step of sd_step stays the inviscid one: the caller keeps cfl within the
+   * viscous limit. */
   double mu, eta, kappa, kappa_r, R_gas;
   int32_t viscous;
   int32_t pad2_;
@@ -133,7 +135,7 @@ typedef struct {
    * temperature T_top held on the outer sphere (the common value of T in the BR1 gradients); a
    * perfectly conducting wall keeps only the normal part of the current in the resistive terms
    * (J = J_r r^), a radial-field wall holds B_theta = B_phi = 0 through its face state.  Otherwise a
-   * wall passes its own F_vis. */
+   * wall passes its own F_vis.  visc_walls runs on SD_FP64 only. */
   double q_bottom, T_top;
   int32_t visc_walls;
   int32_t pad3_;
@@ -223,7 +225,14 @@ sd_status sd_state_init(const sd_mesh* mesh, const sd_phys* phys, const sd_init*
  * while the mesh lives.  Asynchronous: its device memory comes from the stream-ordered
  * allocator on `stream`, and the tables are complete once the work issued to
  * `stream` so far is (use the handle on `stream`, or after synchronising it).
- * q_background may be released once that work is complete. */
+ * q_background may be released once that work is complete.
+ * With phys->viscous set the background also carries, for the viscous fluxes of
+ * the mixed path, its own viscous residual (FP64, rounded to FP32: the heat flux
+ * of Q0, in the energy component) and grad T0, grad S0 with their face traces
+ * (28 more bytes per solution point); the mixed path then takes the viscous
+ * fluxes of the perturbation in FP32 (gradients of (U, T', S', B)) for phys
+ * with the same mu, eta, kappa, kappa_r(r) and R_gas.  Not taken with viscous
+ * set: visc_walls != 0 or far-field faces (SD_ERR_UNSUPPORTED). */
 sd_status sd_background_create(const sd_mesh* mesh, const sd_phys* phys, const double* q_background, void* stream,
                                sd_background** out);
 /* Releases the background's device memory in stream order on the legacy default

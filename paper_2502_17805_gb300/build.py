@@ -18,7 +18,7 @@ GENCODE = "arch=compute_103a,code=sm_103a"
 # The FP32-mixed kernels (tolerance 1e-5) use approximate FP32 division and square
 # root and flush FP32 subnormals; FP64 arithmetic is unaffected by these flags.
 FAST_FP32 = ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"]
-FAST_FP32_SOURCES = {"sd_stage_mixed.cu"}
+FAST_FP32_SOURCES = {"sd_stage_mixed.cu", "sd_mixed_visc.cu"}
 
 
 def _nvcc() -> str:

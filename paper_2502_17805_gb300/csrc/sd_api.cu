@@ -245,7 +245,7 @@ void free_mesh(sd_mesh* m) {
   void* ptrs[] = {m->own_faces, m->face_k, m->gface64, m->Sfam64, m->invJ64, m->X64, m->Sfam32, m->invJ32, m->X32,
                   m->nbr, m->meta,
                   m->tr64[0], m->tr64[1], m->tr32[0], m->tr32[1], m->dyn, m->diag_part, m->diag_out, m->divb,
-                  m->err, m->grad, m->gtr};
+                  m->err, m->grad, m->gtr, m->grad32, m->gtr32, m->rvis32};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (m->host_diag) cudaFreeHost(m->host_diag);
@@ -334,11 +334,47 @@ struct ProfScope {
   }
 };
 
+// Viscous FP32-mixed path: the perturbation gradients of the stage state that P
+// describes (whose face traces are P.tr_in) and their face traces, then the
+// viscous residual of that state (the background's included) into the mesh's
+// buffers (allocated on first use); P then points the stage kernel at it.
+cudaError_t prepare_viscous_mixed(sd_mesh* m, sd::StageParams& P, const sd_background* bg, cudaStream_t s) {
+  const size_t N2 = (size_t)m->N * m->N, N3 = N2 * m->N, ne = (size_t)std::max<int64_t>(m->n_e, 1);
+  cudaError_t err = cudaSuccess;
+  struct Buf {
+    float** p;
+    size_t count;
+  } bufs[3] = {{&m->grad32, ne * sd::NGRAD * N3}, {&m->gtr32, ne * 6 * sd::NGRAD * N2}, {&m->rvis32, 7 * ne * N3}};
+  for (const Buf& b : bufs)
+    if (!*b.p) {
+      err = cudaMalloc((void**)b.p, b.count * sizeof(float));
+      if (err != cudaSuccess) return err;
+      m->device_bytes += (int64_t)(b.count * sizeof(float));
+    }
+  sd::StageParams Pg = P, Pv = P;
+  Pg.mgrad_out = m->grad32;
+  Pg.mgtr_out = m->gtr32;
+  Pv.mgrad = m->grad32;
+  Pv.mgtr_in = m->gtr32;
+  Pv.bg_visc = bg->vrec;
+  Pv.bg_vtr = bg->vtr;
+  Pv.rvis_out = m->rvis32;
+  {
+    ProfScope ps(m, PROF_OTHER, s);
+    err = sd::launch_mixed_visc(m, Pg, Pv, s);
+  }
+  P.rvis = m->rvis32;
+  return err;
+}
+
 // Viscous FP64 path: the BR1 gradients of P.q_in (whose face traces are P.tr_in)
 // and their face traces, into the mesh's gradient buffers (allocated on first use);
-// P then points the stage kernel at them.  No-op without viscous fluxes.
-cudaError_t prepare_viscous(sd_mesh* m, sd::StageParams& P, cudaStream_t s) {
+// P then points the stage kernel at them.  The FP32-mixed path goes through
+// prepare_viscous_mixed.  No-op without viscous fluxes.
+cudaError_t prepare_viscous(sd_mesh* m, sd::StageParams& P, cudaStream_t s, int prec = SD_FP64,
+                            const sd_background* bg = nullptr) {
   if (!P.visc) return cudaSuccess;
+  if (prec == SD_FP32_MIXED) return prepare_viscous_mixed(m, P, bg, s);
   const size_t N2 = (size_t)m->N * m->N, N3 = N2 * m->N, ne = (size_t)std::max<int64_t>(m->n_e, 1);
   cudaError_t err = cudaSuccess;
   if (!m->grad) {
@@ -369,7 +405,18 @@ sd_status check_common(const sd_mesh* m, const sd_phys* ph, int prec, const sd_b
   if (prec != SD_FP64 && prec != SD_FP32_MIXED) return fail(SD_ERR_INVALID_ARGUMENT, "unknown precision");
   if (!(ph->gamma > 1.0)) return fail(SD_ERR_INVALID_ARGUMENT, "gamma must exceed 1");
   if (ph->viscous) {
-    if (prec != SD_FP64) return fail(SD_ERR_UNSUPPORTED, "viscous fluxes run on the SD_FP64 path only");
+    if (prec == SD_FP32_MIXED) {
+      if (!bg || bg->visc_coef[7] != 1.0)
+        return fail(SD_ERR_INVALID_ARGUMENT, "viscous fluxes on the FP32-mixed path need a background built with them");
+      const double want[7] = {ph->mu, ph->eta, ph->kappa, ph->kappa_r, ph->kappa_r1, ph->kappa_r2, ph->R_gas};
+      for (int i = 0; i < 7; ++i)
+        if (bg->visc_coef[i] != want[i])
+          return fail(SD_ERR_INVALID_ARGUMENT, "background was built with other viscous coefficients");
+      if (ph->visc_walls)
+        return fail(SD_ERR_UNSUPPORTED, "the wall conditions of the viscous path (visc_walls) run on SD_FP64 only");
+      if (m->has_farfield)
+        return fail(SD_ERR_UNSUPPORTED, "viscous fluxes on the FP32-mixed path take no far-field faces");
+    }
     if (!(ph->mu >= 0.0) || !(ph->eta >= 0.0) || !(ph->kappa >= 0.0) || !(ph->kappa_r >= 0.0) ||
         !isfinite(ph->mu + ph->eta + ph->kappa + ph->kappa_r) || !isfinite(ph->kappa_r1) || !isfinite(ph->kappa_r2))
       return fail(SD_ERR_INVALID_ARGUMENT, "viscous coefficients must be finite and non-negative");
@@ -548,6 +595,7 @@ sd_status sd_mesh_create(const sd_mesh_desc* desc, void* stream, sd_mesh** out) 
   });
   std::vector<int> nbr((size_t)n_e * 6, -1), meta((size_t)n_e * 6, 0);
   int64_t n_bf = 0, n_if = 0;
+  bool has_ff = false;
   for (size_t i = 0; i < faces.size();) {
     size_t j = i + 1;
     while (j < faces.size() && faces[j].k == faces[i].k) ++j;
@@ -577,6 +625,7 @@ sd_status sd_mesh_create(const sd_mesh_desc* desc, void* stream, sd_mesh** out) 
         outer = rc < 0.5 * (desc->r_inner + desc->r_outer) ? 0 : 1;
       }
       if (bc == SD_BC_PERIODIC) return fail(SD_ERR_MESH_TOPOLOGY, "unmatched face under a periodic boundary");
+      if (bc == SD_BC_FARFIELD) has_ff = true;
       meta[A.e * 6 + A.F] = (bc << 6) | (outer << 10);
       ++n_bf;
     }
@@ -610,6 +659,7 @@ sd_status sd_mesh_create(const sd_mesh_desc* desc, void* stream, sd_mesh** out) 
   m->n_if = n_if;
   m->h_min = hmin;
   m->geom = desc->geom;
+  m->has_farfield = has_ff ? 1 : 0;
   m->wait_spins = sd::kWaitSpins;
   build_ops(N, m->ops64);
   ops_to_f32(m->ops64, m->ops32);
@@ -802,7 +852,19 @@ sd_status sd_background_create(const sd_mesh* m, const sd_phys* ph, const double
   bg->qp = nullptr;
   bg->dstride = (N3 + 3) / 4 * 4;
   bg->device = m->device;
-  double *q0 = nullptr, *R0 = nullptr;
+  bg->vrec = nullptr;
+  bg->vtr = nullptr;
+  for (int i = 0; i < 8; ++i) bg->visc_coef[i] = 0.0;
+  const bool visc = ph->viscous != 0;
+  if (visc && ph->visc_walls) {
+    delete bg;
+    return fail(SD_ERR_UNSUPPORTED, "the wall conditions of the viscous path (visc_walls) run on SD_FP64 only");
+  }
+  if (visc && m->has_farfield) {
+    delete bg;
+    return fail(SD_ERR_UNSUPPORTED, "viscous fluxes on the FP32-mixed path take no far-field faces");
+  }
+  double *q0 = nullptr, *R0 = nullptr, *R0v = nullptr;
   const size_t state = 9 * ne * m->stride;
   // stream-ordered allocations: building a background never waits for the device
   cudaError_t err = cudaMallocAsync((void**)&bg->rec, 5 * ne * N3 * sizeof(float), s);
@@ -837,14 +899,42 @@ sd_status sd_background_create(const sd_mesh* m, const sd_phys* ph, const double
       err = sd::launch_stage(m, SD_FP64, P, s);
     }
   }
+  if (err == cudaSuccess && visc) {
+    // the background's viscous residual (its residual with the viscous fluxes less the one above,
+    // both FP64: only the heat flux of Q0 is left, in the energy component), grad T0 and grad S0
+    err = cudaMallocAsync((void**)&bg->vrec, 7 * ne * N3 * sizeof(float), s);
+    if (err == cudaSuccess) err = cudaMallocAsync((void**)&bg->vtr, ne * 6 * 6 * N2 * sizeof(float), s);
+    if (err == cudaSuccess) err = cudaMallocAsync((void**)&R0v, state * sizeof(double), s);
+    if (err == cudaSuccess) {
+      sd::StageParams P = base_params(m, ph, SD_FP64);
+      P.q_in = q0;
+      P.tr_in = mm->tr64[0];
+      P.mode = sd::MODE_RESIDUAL;
+      P.central = 1;
+      P.ff_own = 1;
+      P.c_h = 0.0;
+      P.powell = 0;
+      P.coriolis = 0;
+      P.alpha = 0.0;
+      P.out = R0v;
+      err = prepare_viscous(mm, P, s);  // FP64 BR1 gradients of Q0 into the mesh's buffers
+      if (err == cudaSuccess) err = sd::launch_stage(m, SD_FP64, P, s);
+      if (err == cudaSuccess) err = sd::launch_bg_visc(m, R0, R0v, mm->grad, mm->gtr, bg->vrec, bg->vtr, s);
+    }
+    const double coef[8] = {ph->mu, ph->eta, ph->kappa, ph->kappa_r, ph->kappa_r1, ph->kappa_r2, ph->R_gas, 1.0};
+    for (int i = 0; i < 8; ++i) bg->visc_coef[i] = coef[i];
+  }
   if (err == cudaSuccess) err = sd::launch_bg_finish(m, ph->gamma, R0, bg->rec, bg->jump, mm->tr64[0], s);
   mm->tr_tag[0] = mm->tr_tag[1] = nullptr;
   if (q0) cudaFreeAsync(q0, s);
   if (R0) cudaFreeAsync(R0, s);
+  if (R0v) cudaFreeAsync(R0v, s);
   if (err != cudaSuccess) {
     if (bg->rec) cudaFreeAsync(bg->rec, s);
     if (bg->jump) cudaFreeAsync(bg->jump, s);
     if (bg->dreg) cudaFreeAsync(bg->dreg, s);
+    if (bg->vrec) cudaFreeAsync(bg->vrec, s);
+    if (bg->vtr) cudaFreeAsync(bg->vtr, s);
     delete bg;
     cudaGetLastError();
     return err == cudaErrorMemoryAllocation ? fail(SD_ERR_OUT_OF_MEMORY, "background allocation failed")
@@ -862,6 +952,8 @@ sd_status sd_background_destroy(sd_background* bg) {
   cudaFreeAsync(bg->rec, 0);
   cudaFreeAsync(bg->jump, 0);
   cudaFreeAsync(bg->dreg, 0);
+  if (bg->vrec) cudaFreeAsync(bg->vrec, 0);
+  if (bg->vtr) cudaFreeAsync(bg->vtr, 0);
   delete bg;
   return SD_OK;
 }
@@ -894,7 +986,7 @@ sd_status sd_residual(const sd_mesh* m, const sd_phys* ph, sd_precision prec, co
   P.tr_out = nullptr;
   P.mode = sd::MODE_RESIDUAL;
   P.out = dqdt;
-  if ((err = prepare_viscous(mm, P, s)) != cudaSuccess) return cuda_fail(err, "gradient kernel");
+  if ((err = prepare_viscous(mm, P, s, prec, bg)) != cudaSuccess) return cuda_fail(err, "gradient kernel");
   {
     ProfScope ps(m, PROF_STAGE, s);
     err = sd::launch_stage(m, prec, P, s);
@@ -946,7 +1038,7 @@ static sd_status rk_stage_impl(sd_mesh* m, const sd_phys* ph, int prec, int stag
     P.lsr_read = lsr_read;
     P.lsr_write = lsr_write;
   }
-  cudaError_t err = prepare_viscous(m, P, s);
+  cudaError_t err = prepare_viscous(m, P, s, prec, bg);
   if (err != cudaSuccess) return cuda_fail(err, "gradient kernel");
   {
     ProfScope ps(m, PROF_STAGE, s);
@@ -1032,7 +1124,7 @@ static sd_status advance_impl(sd_mesh* mm, const sd_phys* ph, sd_precision prec,
       S.incr = 1;
       S.qp_in = bg->qp;
     }
-    SD_CUDA(prepare_viscous(mm, S, s));
+    SD_CUDA(prepare_viscous(mm, S, s, prec, bg));
     {
       ProfScope ps(mm, PROF_STAGE, s);
       SD_CUDA(sd::launch_stage(mm, prec, S, s));
@@ -1049,7 +1141,7 @@ static sd_status advance_impl(sd_mesh* mm, const sd_phys* ph, sd_precision prec,
       S.lsr_read = 1;
       S.lsr_write = 2;
     }
-    SD_CUDA(prepare_viscous(mm, S, s));
+    SD_CUDA(prepare_viscous(mm, S, s, prec, bg));
     {
       ProfScope ps(mm, PROF_STAGE, s);
       SD_CUDA(sd::launch_stage(mm, prec, S, s));
@@ -1069,7 +1161,7 @@ static sd_status advance_impl(sd_mesh* mm, const sd_phys* ph, sd_precision prec,
       S.lsr_write = 0;
       S.qp_out = last ? nullptr : bg->qp;  // q' of the new q, for the next step
     }
-    SD_CUDA(prepare_viscous(mm, S, s));
+    SD_CUDA(prepare_viscous(mm, S, s, prec, bg));
     {
       ProfScope ps(mm, PROF_STAGE, s);
       SD_CUDA(sd::launch_stage(mm, prec, S, s));

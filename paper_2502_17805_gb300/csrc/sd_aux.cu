@@ -552,6 +552,42 @@ __global__ void __launch_bounds__(kSphThreads) spherical_kernel(int N, int64_t s
       if (win[t] != 0.0) atomicAdd(&out[(int64_t)lo * kSphVals + t], win[t]);
 }
 
+// ---------------------------------------------------------------------------
+// Viscous record of the FP32-mixed background: the energy component of the
+// background's viscous residual (its residual with viscous fluxes less the one
+// without, both FP64), grad T0 and grad S0 at the solution points (gradient
+// components 3 c + j, c = 3 for T and 4 for S) and their face traces, in FP32.
+// ---------------------------------------------------------------------------
+
+__global__ void bg_visc_kernel(int N, int64_t n_e, int64_t stride, const double* __restrict__ R0,
+                               const double* __restrict__ R0v, const double* __restrict__ grad,
+                               const double* __restrict__ gtr, float* __restrict__ vrec, float* __restrict__ vtr) {
+  const int N2 = N * N, N3 = N2 * N;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t plane = n_e * stride;
+  if (t < n_e * N3) {
+    const int64_t e = t / N3;
+    const int n = (int)(t - e * N3);
+    const int64_t g = e * stride + n;
+    vrec[t] = (float)(R0v[4 * plane + g] - R0[4 * plane + g]);
+    for (int k = 0; k < 6; ++k) vrec[(1 + k) * n_e * N3 + t] = (float)grad[(e * NGRAD + 9 + k) * N3 + n];
+  }
+  if (t < n_e * 6 * N2) {
+    const int64_t ef = t / N2;
+    const int pt = (int)(t - ef * N2);
+    for (int k = 0; k < 6; ++k) vtr[(ef * 6 + k) * N2 + pt] = (float)gtr[(ef * NGRAD + 9 + k) * N2 + pt];
+  }
+}
+
+cudaError_t launch_bg_visc(const sd_mesh* m, const double* R0, const double* R0v, const double* grad,
+                           const double* gtr, float* vrec, float* vtr, cudaStream_t s) {
+  const int64_t N2 = (int64_t)m->N * m->N, N3 = N2 * m->N;
+  const int64_t tot = m->n_e * (N3 > 6 * N2 ? N3 : 6 * N2);
+  if (tot == 0) return cudaSuccess;
+  bg_visc_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(m->N, m->n_e, m->stride, R0, R0v, grad, gtr, vrec, vtr);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_spherical(const sd_mesh* m, const double* q, double r_min, double r_max, int n_r, int n_t,
                              double* out, cudaStream_t s) {
   cudaError_t err = cudaMemsetAsync(out, 0, (size_t)n_r * n_t * kSphVals * sizeof(double), s);

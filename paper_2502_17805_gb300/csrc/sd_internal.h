@@ -126,6 +126,18 @@ struct StageParams {
   const double* gtr_in;
   double* grad_out;
   double* gtr_out;
+  // viscous fluxes on the FP32-mixed path: perturbation gradients [e][24][N^3] and their face
+  // traces [e][F][24][N^2], the background's viscous record [7][n_e N^3] (its energy residual, grad T0,
+  // grad S0) and its face traces [e][F][6][N^2], and the viscous residual of the stage state
+  // [7][n_e N^3] (components rho U, E, B) that the mixed stage kernel adds
+  const float* mgrad;
+  const float* mgtr_in;
+  float* mgrad_out;
+  float* mgtr_out;
+  const float* bg_visc;
+  const float* bg_vtr;
+  float* rvis_out;
+  const float* rvis;
 };
 
 }  // namespace sd
@@ -165,6 +177,10 @@ struct sd_mesh {
   int wait_spins;           // polls of a stage kernel's bounded wait before a time-out (sd_mesh_set_wait_limit)
   double* grad;             // viscous path, allocated on first use: gradients [e][24][N^3]
   double* gtr;              //   and their face traces [e][F][24][N^2]
+  float* grad32;            // viscous FP32-mixed path, allocated on first use: perturbation gradients,
+  float* gtr32;             //   their face traces
+  float* rvis32;            //   and the viscous residual [7][n_e N^3]
+  int has_farfield;         // the mesh has far-field boundary faces
   int64_t device_bytes;
   sd::Ops<double> ops64;
   sd::Ops<float> ops32;
@@ -185,6 +201,11 @@ struct sd_background {
   int64_t dstride;
   double gamma;
   int device;
+  // built with viscous fluxes: the background's viscous energy residual, grad T0, grad S0
+  // [7][n_e N^3] and the face traces of the gradients [e][F][6][N^2], with the coefficients used
+  float* vrec;
+  float* vtr;
+  double visc_coef[8];  // mu, eta, kappa, kappa_r, kappa_r1, kappa_r2, R_gas, 1 when built with viscous fluxes
 };
 
 namespace sd {
@@ -202,6 +223,12 @@ cudaError_t launch_spherical(const sd_mesh* m, const double* q, double r_min, do
                              double* out, cudaStream_t s);
 // BR1 gradients of the primitive variables and their face traces (viscous FP64 path)
 cudaError_t launch_grad(const sd_mesh* m, const StageParams& P, cudaStream_t s);
+// viscous FP32-mixed path: perturbation gradients (Pg), then the viscous residual (Pv)
+cudaError_t launch_mixed_visc(const sd_mesh* m, const StageParams& Pg, const StageParams& Pv, cudaStream_t s);
+// the background's viscous record from the FP64 residuals with and without viscous fluxes and the
+// FP64 gradients of the background
+cudaError_t launch_bg_visc(const sd_mesh* m, const double* R0, const double* R0v, const double* grad,
+                           const double* gtr, float* vrec, float* vtr, cudaStream_t s);
 cudaError_t launch_geometry(sd_mesh* m, const double* d_corners, int* d_flag, cudaStream_t s);
 cudaError_t launch_canonical_faces(sd_mesh* m, cudaStream_t s);
 // radial profile table of the flux-balanced initial state: [4][n + 1] = rho, S, drho/dr, dS/dr on

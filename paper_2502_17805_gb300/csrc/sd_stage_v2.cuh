@@ -517,6 +517,11 @@ __device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops2& 
     Rv[1] += G[4];
     Rv[2] += G[5];
     Rv[3] += G[6];
+    if (P.rvis) {  // viscous fluxes: the residual the viscous kernels computed for this stage state
+      const float* rv = P.rvis + e * N3 + n;
+#pragma unroll
+      for (int v = 0; v < 7; ++v) Rv[1 + v] += __ldg(rv + v * n_e * N3);
+    }
     const int64_t g = e * stride + n;
     if (mode == MODE_RESIDUAL) {
 #pragma unroll

@@ -108,9 +108,13 @@ def test_viscous_fluxes_are_rejected_where_unsupported():
     gph = sdmhd.Phys(gravity=1, GM=1.0, **VISC)
     qb = gm.empty_state()
     q = gm.state_init(gph, sdmhd.INIT_SHELL_POLYTROPE, [1.5, 0.7, 0.98, 1.0, 1.0, 1e-4, 0.0], seed=0, background=qb)
-    bg = gm.background(gph, qb)
-    with pytest.raises(sdmhd.SDError, match="FP64"):
+    # the mixed path takes viscous fluxes only about a background built with them
+    bg = gm.background(sdmhd.Phys(gravity=1, GM=1.0), qb)
+    with pytest.raises(sdmhd.SDError, match="background built with them"):
         gm.residual(gph, q, prec=sdmhd.SD_FP32_MIXED, bg=bg)
+    walls = sdmhd.Phys(gravity=1, GM=1.0, visc_walls=1, q_bottom=0.05, T_top=0.6, **VISC)
+    with pytest.raises(sdmhd.SDError, match="FP64"):
+        gm.background(walls, qb)
     with pytest.raises(sdmhd.SDError, match="sd_residual"):
         gm.residual_noalloc(gph, q, gm.empty_state())
     bad = sdmhd.Phys(gravity=1, GM=1.0, **dict(VISC, mu=-1.0))
