@@ -156,7 +156,7 @@ __global__ void geometry_kernel(int N, int p, int geom, const double* __restrict
     for (int c = 0; c < 3; ++c) {
       const int64_t idx = (((e * 3 + d) * 3 + c) * N2 + line) * NF + f;
       Sfam64[idx] = S[c];
-      Sfam32[idx] = (float)S[c];
+      Sfam32[e * 9 * N2 * NF + s32_index(N, d, f, c, line)] = (float)S[c];
     }
   }
   for (int n = threadIdx.x; n < N3; n += blockDim.x) {
@@ -200,7 +200,7 @@ __global__ void canonical_faces_kernel(int N, int64_t n_e, const int* __restrict
     const double Sn = Sfam64[((((int64_t)nb * 3 + d2) * 3 + c) * N2 + a2 + N * b2) * NF + f2];
     const int64_t idx = (((e * 3 + d) * 3 + c) * N2 + pt) * NF + f;
     Sfam64[idx] = -sgn * Sn;
-    Sfam32[idx] = (float)(-sgn * Sn);
+    Sfam32[e * 9 * N2 * NF + s32_index(N, d, f, c, pt)] = (float)(-sgn * Sn);
   }
 }
 

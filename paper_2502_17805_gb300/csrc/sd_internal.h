@@ -58,6 +58,14 @@ __host__ __device__ inline int meta_bc(int m) { return (m >> 6) & 7; }
 __host__ __device__ inline int meta_outer(int m) { return (m >> 10) & 1; }
 __host__ __device__ inline int meta_owner(int m) { return (m >> 9) & 1; }
 
+// Offset, within one element's block of the FP32 metrics S^d (9 (N+1) N^2
+// values), of component c of S^d at flux point f of line `line` of family d.
+// The N^2 lines of one (d, f, c) are contiguous, so that the threads of a warp,
+// which take consecutive lines of one flux point, read consecutive words.
+__host__ __device__ constexpr inline int s32_index(int N, int d, int f, int c, int line) {
+  return ((d * (N + 1) + f) * 3 + c) * N * N + line;
+}
+
 enum StageMode { MODE_RESIDUAL = 0, MODE_RK = 1, MODE_DIVB = 2 };
 
 // Arguments of the fused element kernels.  Geometry pointers are float or
@@ -79,7 +87,7 @@ struct StageParams {
   double inv_gm1;  // 1/(gamma-1); the mixed background energy is E0 = p0 * inv_gm1
   int powell, gravity, coriolis, pad_;
   double farfield[9];
-  const void* Sfam;   // [e][d][c][line][f]
+  const void* Sfam;   // FP64: [e][d][c][line][f]; FP32: [e][d][f][c][line] (s32_index)
   const void* invJ;   // [e][n]
   const void* X;      // [e][c][n]
   const int* nbr;     // [e][6] neighbour element or -1

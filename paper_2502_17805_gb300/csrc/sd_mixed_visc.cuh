@@ -217,8 +217,8 @@ __global__ void __launch_bounds__(MVDims<N>::T) mgrad_kernel(const StageParams P
           r2 += __ldg(P.bg_jump + (gidx * 2 + 0) * N2 + pt);
           p2 += __ldg(P.bg_jump + (gidx * 2 + 1) * N2 + pt);
         } else {
-          const float* Sp = Sfam + (d * 3 * N2 + line) * NF + f;
-          const float Sx = Sp[0], Sy = Sp[N2 * NF], Sz = Sp[2 * N2 * NF];
+          const float* Sp = Sfam + s32_index(N, d, f, 0, line);
+          const float Sx = Sp[0], Sy = Sp[N2], Sz = Sp[2 * N2];
           const float im = rsqrtf(Sx * Sx + Sy * Sy + Sz * Sz), sg = side ? 1.0f : -1.0f;
           wall_ghost<float>(Qf, sg * Sx * im, sg * Sy * im, sg * Sz * im, meta_bc(mt), q2);
         }
@@ -236,9 +236,9 @@ __global__ void __launch_bounds__(MVDims<N>::T) mgrad_kernel(const StageParams P
       const int line = d == 0 ? j0 + N * k0 : (d == 1 ? i0 + N * k0 : i0 + N * j0);
 #pragma unroll 1
       for (int f = 0; f <= N; ++f) {
-        const float* Sp = Sfam + (d * 3 * N2 + line) * NF + f;
+        const float* Sp = Sfam + s32_index(N, d, f, 0, line);
         const float Df = ops.D[id * NF + f];
-        const float DS0 = Df * Sp[0], DS1 = Df * Sp[N2 * NF], DS2 = Df * Sp[2 * N2 * NF];
+        const float DS0 = Df * Sp[0], DS1 = Df * Sp[N2], DS2 = Df * Sp[2 * N2];
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
           const float wv = sW[(k * NF + f) * N2 + line];
@@ -319,8 +319,8 @@ __global__ void __launch_bounds__(MVDims<N>::T) mvisc_kernel(const StageParams P
         for (int i = 0; i < N; ++i) s = fmaf(ops.E[f * N + i], sQ[v * N3 + sol_index<N>(d, i, a, b)], s);
         x[v] = s;
       }
-      const float* Sp = Sfam + (d * 3 * N2 + line) * NF + f;
-      const float Sx = Sp[0], Sy = Sp[N2 * NF], Sz = Sp[2 * N2 * NF];
+      const float* Sp = Sfam + s32_index(N, d, f, 0, line);
+      const float Sx = Sp[0], Sy = Sp[N2], Sz = Sp[2 * N2];
       const float kr = mv_kappa_r(c, x[NQ - 3], x[NQ - 2], x[NQ - 1]);
       float Fv[7];
       if (f > 0 && f < N) {

@@ -355,9 +355,9 @@ __device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops2& 
         const int d = r0 / ((N - 1) * N2), r = r0 - d * ((N - 1) * N2);
         const int f = 1 + r / N2, L = r - (f - 1) * N2;
         Xp[h] = sX + f * DV::XF + d * DV::XD + L;
-        const float* Sp = Sfam + (d * 3 * N2 + L) * NF + f;
+        const float* Sp = Sfam + s32_index(N, d, f, 0, L);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) (h ? S[c].y : S[c].x) = __ldg(Sp + c * N2 * NF);
+        for (int c = 0; c < 3; ++c) (h ? S[c].y : S[c].x) = __ldg(Sp + c * N2);
 #pragma unroll
         for (int v = 0; v < 11; ++v) (h ? qf[v].y : qf[v].x) = Xp[h][v * DV::XV];
       }
@@ -379,8 +379,8 @@ __device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops2& 
       float qo[11];
 #pragma unroll
       for (int v = 0; v < 11; ++v) qo[v] = X[v * DV::XV];
-      const float* Sp = Sfam + (d * 3 * N2 + pt) * NF + f;
-      const float Sx = __ldg(Sp), Sy = __ldg(Sp + N2 * NF), Sz = __ldg(Sp + 2 * N2 * NF);
+      const float* Sp = Sfam + s32_index(N, d, f, 0, pt);
+      const float Sx = __ldg(Sp), Sy = __ldg(Sp + N2), Sz = __ldg(Sp + 2 * N2);
       const float mag = sqrtf(Sx * Sx + Sy * Sy + Sz * Sz);
       const float im = 1.0f / mag;
       const float sg = side ? 1.0f : -1.0f;
