@@ -344,7 +344,7 @@ cudaError_t prepare_viscous_mixed(sd_mesh* m, sd::StageParams& P, const sd_backg
   struct Buf {
     float** p;
     size_t count;
-  } bufs[3] = {{&m->grad32, ne * sd::NGRAD * N3}, {&m->gtr32, ne * 6 * sd::NGRAD * N2}, {&m->rvis32, 7 * ne * N3}};
+  } bufs[3] = {{&m->grad32, ne * sd::MV_REC * N3}, {&m->gtr32, ne * 6 * sd::MV_REC * N2}, {&m->rvis32, 7 * ne * N3}};
   for (const Buf& b : bufs)
     if (!*b.p) {
       err = cudaMalloc((void**)b.p, b.count * sizeof(float));

@@ -223,6 +223,9 @@ constexpr int kWaitSpins = 1 << 16;
 constexpr int LAM_SLOTS = 256;
 // gradients the viscous fluxes need: 8 primitive variables x 3 directions, index 3 c + j
 constexpr int NGRAD = 24;
+// Values per point of the FP32-mixed viscous path's gradient record: the
+// viscous stress (6), the current (3), grad T' and grad S'.
+constexpr int MV_REC = 15;
 // kernels launched from the API (defined in the .cu files)
 cudaError_t launch_stage(const sd_mesh* m, int prec, const StageParams& P, cudaStream_t s);
 cudaError_t launch_traces(const sd_mesh* m, int prec, const StageParams& P, cudaStream_t s);

@@ -19,15 +19,23 @@
 //   quantities alone; q - q0 = -kappa (rho T grad S' + (p'/R) grad S0)
 //                              - kappa_r C_p (rho grad T' + rho' grad T0),
 //   exactly, since rho T - rho0 T0 = p'/R.
-// mgrad_kernel writes grad w' [e][24][N^3] and its face traces [e][F][24][N^2];
+// Of grad w' the fluxes need only the viscous stress tau (mu constant, so tau is
+// linear in grad U and may be formed at the solution points and extrapolated like
+// the gradients themselves), the current J = curl B, grad T' and grad S': the
+// gradient record, MV_REC = 15 values per point.
+// mgrad_kernel writes the record [e][15][N^3] and its face traces [e][F][15][N^2];
 // mvisc_kernel writes the viscous residual of the stage state (background's
 // included) [7][n_e N^3] (components rho U, E, B), which the stage kernel adds.
+// Both are line-blocked like the inviscid stage kernel: the 1D extrapolation and
+// derivative operators run along the lines of the element from registers, two
+// variables at a time in paired FP32 arithmetic, in the even-odd form.
 // Walls pass this side's own viscous flux (no wall conditions of the viscous
 // path); meshes with far-field faces are not taken.
 #pragma once
 
 #include "sd_internal.h"
 #include "sd_physics.cuh"
+#include "sd_physics2.cuh"
 #include "sd_stage.cuh"
 
 namespace sd {
@@ -78,42 +86,42 @@ __device__ __forceinline__ void mv_prim(const float* q, float r0, float p0, cons
   w[7] = q[7];
 }
 
+// The gradient record: tau (xx, yy, zz, xy, xz, yz), J (x, y, z), grad T',
+// grad S' at a point.
+enum { MV_TAU = 0, MV_J = 6, MV_GT = 9, MV_GS = 12 };
+static_assert(MV_GS + 3 == MV_REC, "record layout");
+
 // (F_vis(Q0 + q') - F_vis(Q0)) . n from q'(9), the background (r0, p0), the
-// perturbation gradients g[3 c + j] = d w'_c / d x_j and the background's
-// gT0 = grad T0, gS0 = grad S0, with the radiative diffusivity kr at the point.
-// F[0..6] = components rho U (3), E, B (3).
-__device__ __forceinline__ void mv_flux(const float* q, float r0, float p0, const float* g, const float* gT0,
+// gradient record rec[MV_REC] and the background's gT0 = grad T0, gS0 = grad S0,
+// with the radiative diffusivity kr at the point: F[0..6] = components rho U (3),
+// E, B (3).  n need not be a unit vector (F_vis . n is linear in n).
+__device__ __forceinline__ void mv_flux(const float* q, float r0, float p0, const float* rec, const float* gT0,
                                         const float* gS0, float nx, float ny, float nz, const MViscCoef& c, float kr,
                                         float* F) {
   const float rho = r0 + q[0];
   const float ir = 1.0f / rho;
-  const float U[3] = {q[1] * ir, q[2] * ir, q[3] * ir};
+  const float Ux = q[1] * ir, Uy = q[2] * ir, Uz = q[3] * ir;
   const float pp = mv_pprime(q, r0, c);
-  const float n[3] = {nx, ny, nz};
-  const float divu = g[0] + g[4] + g[8];
-  float tn[3] = {0.0f, 0.0f, 0.0f}, uT[3] = {0.0f, 0.0f, 0.0f};
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      const float t = c.mu * (g[3 * i + j] + g[3 * j + i]) + (i == j ? c.lam * divu : 0.0f);
-      tn[i] += t * n[j];
-      uT[j] += U[i] * t;
-    }
-  const float Jx = g[3 * 7 + 1] - g[3 * 6 + 2], Jy = g[3 * 5 + 2] - g[3 * 7 + 0], Jz = g[3 * 6 + 0] - g[3 * 5 + 1];
+  const float txx = rec[0], tyy = rec[1], tzz = rec[2], txy = rec[3], txz = rec[4], tyz = rec[5];
+  const float Jx = rec[MV_J], Jy = rec[MV_J + 1], Jz = rec[MV_J + 2];
+  F[0] = txx * nx + txy * ny + txz * nz;
+  F[1] = txy * nx + tyy * ny + tyz * nz;
+  F[2] = txz * nx + tyz * ny + tzz * nz;
+  const float uTx = Ux * txx + Uy * txy + Uz * txz;
+  const float uTy = Ux * txy + Uy * tyy + Uz * tyz;
+  const float uTz = Ux * txz + Uy * tyz + Uz * tzz;
   const float Bx = q[5], By = q[6], Bz = q[7];
-  const float BJ[3] = {By * Jz - Bz * Jy, Bz * Jx - Bx * Jz, Bx * Jy - By * Jx};
+  const float BJx = By * Jz - Bz * Jy, BJy = Bz * Jx - Bx * Jz, BJz = Bx * Jy - By * Jx;
   const float rT = (p0 + pp) * c.inv_R;  // rho T of the full state
   const float dRT = pp * c.inv_R;        // rho T - rho0 T0
+  const float krc = kr * c.cp;
+  const float n3[3] = {nx, ny, nz}, uT[3] = {uTx, uTy, uTz}, BJ[3] = {BJx, BJy, BJz};
   float e = 0.0f;
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
-    const float qh = -c.kappa * (rT * g[3 * 4 + j] + dRT * gS0[j]) - kr * c.cp * (rho * g[3 * 3 + j] + q[0] * gT0[j]);
-    e += (uT[j] - qh + c.eta * BJ[j]) * n[j];
+    const float qh = -c.kappa * (rT * rec[MV_GS + j] + dRT * gS0[j]) - krc * (rho * rec[MV_GT + j] + q[0] * gT0[j]);
+    e += (uT[j] - qh + c.eta * BJ[j]) * n3[j];
   }
-  F[0] = tn[0];
-  F[1] = tn[1];
-  F[2] = tn[2];
   F[3] = e;
   F[4] = c.eta * (Jy * nz - Jz * ny);
   F[5] = c.eta * (Jz * nx - Jx * nz);
@@ -159,251 +167,455 @@ __device__ __forceinline__ void mv_load_state(const StageParams& P, int64_t e, f
   }
 }
 
-template <int N>
-struct MVDims {
-  static constexpr int N2 = N * N, N3 = N2 * N, NF = N + 1;
-  static constexpr int MAXW = 6 * N2 > N3 ? 6 * N2 : N3;
-  static constexpr int T = ((MAXW + 31) / 32) * 32;
-};
-
-// BR1 gradients of w' and their face traces.
-template <int N>
-__global__ void __launch_bounds__(MVDims<N>::T) mgrad_kernel(const StageParams P, const Ops<float> ops) {
-  using MD = MVDims<N>;
-  constexpr int N2 = MD::N2, N3 = MD::N3, NF = MD::NF, T = MD::T;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  float* sQ = reinterpret_cast<float*>(smem_raw);  // [11][N3]
-  float* sW = sQ + 11 * N3;                          // [8][NF][N2] one family
-  float* sG = sW + 8 * NF * N2;                      // [24][N3]
-  const int tid = threadIdx.x;
-  const int64_t e = blockIdx.x;
-  const float* Sfam = reinterpret_cast<const float*>(P.Sfam) + e * (9 * N2 * NF);
-  const MViscCoef c = mvisc_coef(P);
-  mv_load_state<N>(P, e, sQ, T);
-  const int n = tid;
-  const int i0 = n % N, j0 = (n / N) % N, k0 = n / N2;
-  float acc[NGRAD];
-#pragma unroll
-  for (int k = 0; k < NGRAD; ++k) acc[k] = 0.0f;
+// Extrapolate NV variables (planes of `in` VS floats apart, solution point n at
+// n) along every line of the directions D0 <= d < D1 to the N+1 flux points of
+// the line's family, two variables at a time in paired FP32 arithmetic, in the
+// even-odd form (E[N-f][N-1-i] = E[f][i]): variable v at flux point f of line L
+// of direction d goes to out[f OF + v OV + (d - D0) OD + L].  The tasks
+// (variable pair, line), lines innermost, are spread over the T threads.
+template <int N, int T, int NV, int D0, int D1>
+__device__ __forceinline__ void mv_extrap(const float* in, int VS, float* out, int OF, int OV, int OD,
+                                          const Ops2& o2) {
+  constexpr int N2 = N * N, HP = N / 2, NL = (D1 - D0) * N2, NP = (NV + 1) / 2;
 #pragma unroll 1
-  for (int d = 0; d < 3; ++d) {
-    __syncthreads();
-    // w' at the flux points of family d, the BR1 common value at the two faces
-    for (int t = tid; t < NF * N2; t += T) {
-      const int f = t % NF, line = t / NF, a = line % N, b = line / N;
-      float Qf[11], w[8];
+  for (int t = threadIdx.x; t < NL * NP; t += T) {
+    const int pr = t / NL, l = t - pr * NL;
+    const int d = D0 + l / N2, L = l - (l / N2) * N2;
+    int base, stride;
+    line_geom<N>(d, L, base, stride);
+    const int v0 = 2 * pr, v1 = v0 + 1 < NV ? v0 + 1 : v0;
+    const float* a = in + v0 * VS + base;
+    const float* b = in + v1 * VS + base;
+    float2 ql[N];
 #pragma unroll
-      for (int v = 0; v < 11; ++v) {
-        float s = 0.0f;
+    for (int i = 0; i < N; ++i) ql[i] = make_float2(a[i * stride], b[i * stride]);
+    float2 sv[HP > 0 ? HP : 1], dv[HP > 0 ? HP : 1];
 #pragma unroll
-        for (int i = 0; i < N; ++i) s = fmaf(ops.E[f * N + i], sQ[v * N3 + sol_index<N>(d, i, a, b)], s);
-        Qf[v] = s;
-      }
-      mv_prim(Qf, Qf[9], Qf[10], c, w);
-      if (f == 0 || f == N) {
-        const int side = f == N, F = 2 * d + side;
-        const int64_t gidx = e * 6 + F;
-        const int nb = __ldg(P.nbr + gidx), mt = __ldg(P.meta + gidx);
-        float q2[9], w2[8], r2 = Qf[9], p2 = Qf[10];
-        if (nb >= 0) {
-          const int code = meta_code(mt);
-          const int u = (code & 4) ? b : a, ww = (code & 4) ? a : b;
-          const int a2 = (code & 2) ? N - 1 - u : u, b2 = (code & 1) ? N - 1 - ww : ww;
-          const float* Tn =
-              reinterpret_cast<const float*>(P.tr_in) + ((int64_t)nb * 6 + meta_nbF(mt)) * 9 * N2 + a2 + N * b2;
-#pragma unroll
-          for (int v = 0; v < 9; ++v) q2[v] = Tn[v * N2];
-          const int pt = a + N * b;
-          r2 += __ldg(P.bg_jump + (gidx * 2 + 0) * N2 + pt);
-          p2 += __ldg(P.bg_jump + (gidx * 2 + 1) * N2 + pt);
-        } else {
-          const float* Sp = Sfam + s32_index(N, d, f, 0, line);
-          const float Sx = Sp[0], Sy = Sp[N2], Sz = Sp[2 * N2];
-          const float im = rsqrtf(Sx * Sx + Sy * Sy + Sz * Sz), sg = side ? 1.0f : -1.0f;
-          wall_ghost<float>(Qf, sg * Sx * im, sg * Sy * im, sg * Sz * im, meta_bc(mt), q2);
-        }
-        mv_prim(q2, r2, p2, c, w2);
-#pragma unroll
-        for (int k = 0; k < 8; ++k) w[k] = 0.5f * (w[k] + w2[k]);
-      }
-#pragma unroll
-      for (int k = 0; k < 8; ++k) sW[(k * NF + f) * N2 + line] = w[k];
+    for (int i = 0; i < HP; ++i) {
+      sv[i] = add2(ql[i], ql[N - 1 - i]);
+      dv[i] = sub2(ql[i], ql[N - 1 - i]);
     }
-    __syncthreads();
-    // sum_f D[i][f] S^d_j w'_f at this thread's solution point
-    if (n < N3) {
-      const int id = d == 0 ? i0 : (d == 1 ? j0 : k0);
-      const int line = d == 0 ? j0 + N * k0 : (d == 1 ? i0 + N * k0 : i0 + N * j0);
-#pragma unroll 1
-      for (int f = 0; f <= N; ++f) {
-        const float* Sp = Sfam + s32_index(N, d, f, 0, line);
-        const float Df = ops.D[id * NF + f];
-        const float DS0 = Df * Sp[0], DS1 = Df * Sp[N2], DS2 = Df * Sp[2 * N2];
+    float* X = out + (d - D0) * OD + L;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          const float wv = sW[(k * NF + f) * N2 + line];
-          acc[3 * k + 0] = fmaf(DS0, wv, acc[3 * k + 0]);
-          acc[3 * k + 1] = fmaf(DS1, wv, acc[3 * k + 1]);
-          acc[3 * k + 2] = fmaf(DS2, wv, acc[3 * k + 2]);
-        }
+    for (int f = 0; 2 * f <= N; ++f) {
+      float2 s = (N & 1) ? mul2(o2.Es[f * N + HP], ql[HP]) : make_float2(0.0f, 0.0f);
+      float2 r = make_float2(0.0f, 0.0f);
+#pragma unroll
+      for (int i = 0; i < HP; ++i) {
+        s = fma2(o2.Es[f * N + i], sv[i], s);
+        r = fma2(o2.Ed[f * N + i], dv[i], r);
       }
-    }
-  }
-  if (n < N3) {
-    const float iJ = __ldg(reinterpret_cast<const float*>(P.invJ) + e * N3 + n);
-    float* Ge = P.mgrad_out + e * NGRAD * N3;
-#pragma unroll
-    for (int k = 0; k < NGRAD; ++k) {
-      const float gk = acc[k] * iJ;
-      sG[k * N3 + n] = gk;
-      Ge[k * N3 + n] = gk;
-    }
-  }
-  __syncthreads();
-  // face traces of the gradients
-  for (int t = tid; t < 6 * N2; t += T) {
-    const int F = t / N2, pt = t - F * N2, a = pt % N, b = pt / N;
-    const int d = F >> 1, f = (F & 1) ? N : 0;
-    float* Tr = P.mgtr_out + (e * 6 + F) * NGRAD * N2 + pt;
-#pragma unroll 4
-    for (int k = 0; k < NGRAD; ++k) {
-      float s = 0.0f;
-#pragma unroll
-      for (int i = 0; i < N; ++i) s = fmaf(ops.E[f * N + i], sG[k * N3 + sol_index<N>(d, i, a, b)], s);
-      Tr[k * N2] = s;
+      if (2 * f == N) {
+        X[f * OF + v0 * OV] = s.x;
+        X[f * OF + v1 * OV] = s.y;
+      } else {
+        const float2 lo = add2(s, r), hi = sub2(s, r);
+        X[f * OF + v0 * OV] = lo.x;
+        X[f * OF + v1 * OV] = lo.y;
+        X[(N - f) * OF + v0 * OV] = hi.x;
+        X[(N - f) * OF + v1 * OV] = hi.y;
+      }
     }
   }
 }
 
-// The viscous residual of the stage state, R_vis = div(S^d . F_vis)/|J| with
-// the face flux the average of both sides' (F_vis . n), background included:
-// out [7][n_e N^3] (components rho U, E, B).
+// Differentiate NV flux variables given at the N+1 flux points of every line of
+// direction D (variable v at flux point f of line L at in[f IF + v IV + L]) back
+// to the line's N solution points (even-odd form, D[N-1-i][f] = -D[i][N-f]) and
+// store (ADD false) or add (ADD true) the result into acc[v N^3 + n].  For one
+// direction the lines partition the solution points, so no two tasks touch the
+// same word.
+template <int N, int T, int NV, int D, bool ADD>
+__device__ __forceinline__ void mv_deriv(const float* in, int IF, int IV, float* acc, const Ops2& o2) {
+  constexpr int N2 = N * N, N3 = N2 * N, NF = N + 1, HF = NF / 2, NP = (NV + 1) / 2;
+#pragma unroll 1
+  for (int t = threadIdx.x; t < N2 * NP; t += T) {
+    const int pr = t / N2, L = t - pr * N2;
+    int base, stride;
+    line_geom<N>(D, L, base, stride);
+    const int v0 = 2 * pr, v1 = v0 + 1 < NV ? v0 + 1 : v0;
+    float2 fv[NF];
+#pragma unroll
+    for (int f = 0; f <= N; ++f) fv[f] = make_float2(in[f * IF + v0 * IV + L], in[f * IF + v1 * IV + L]);
+    float2 sf[HF], df[HF];
+#pragma unroll
+    for (int f = 0; f < HF; ++f) {
+      sf[f] = add2(fv[f], fv[N - f]);
+      df[f] = sub2(fv[f], fv[N - f]);
+    }
+    float* a = acc + v0 * N3 + base;
+    float* b = acc + v1 * N3 + base;
+    const bool two = v1 != v0;
+#pragma unroll
+    for (int i = 0; 2 * i <= N - 1; ++i) {
+      float2 p = (NF & 1) ? mul2(o2.Ds[i * NF + HF], fv[HF]) : make_float2(0.0f, 0.0f);
+      float2 r = make_float2(0.0f, 0.0f);
+#pragma unroll
+      for (int f = 0; f < HF; ++f) {
+        p = fma2(o2.Ds[i * NF + f], sf[f], p);
+        r = fma2(o2.Dd[i * NF + f], df[f], r);
+      }
+      float2 lo, hi;
+      const bool mid = 2 * i == N - 1;
+      if (mid) {
+        lo = r;
+        hi = r;
+      } else {
+        lo = add2(p, r);
+        hi = sub2(r, p);
+      }
+      const int ilo = i * stride, ihi = (N - 1 - i) * stride;
+      if (ADD) {
+        a[ilo] += lo.x;
+        if (two) b[ilo] += lo.y;
+        if (!mid) {
+          a[ihi] += hi.x;
+          if (two) b[ihi] += hi.y;
+        }
+      } else {
+        a[ilo] = lo.x;
+        if (two) b[ilo] = lo.y;
+        if (!mid) {
+          a[ihi] = hi.x;
+          if (two) b[ihi] = hi.y;
+        }
+      }
+    }
+  }
+}
+
+// The neighbour's side of point pt of a face with neighbour nb >= 0 and
+// metadata mt: its face nf = nb * 6 + (its face number) and the point p2 there.
 template <int N>
-__global__ void __launch_bounds__(MVDims<N>::T) mvisc_kernel(const StageParams P, const Ops<float> ops) {
+__device__ __forceinline__ void mv_partner(int nb, int mt, int pt, int64_t& nf, int& p2) {
+  const int code = meta_code(mt), a = pt % N, b = pt / N;
+  const int u = (code & 4) ? b : a, w = (code & 4) ? a : b;
+  const int a2 = (code & 2) ? N - 1 - u : u, b2 = (code & 1) ? N - 1 - w : w;
+  nf = (int64_t)nb * 6 + meta_nbF(mt);
+  p2 = a2 + N * b2;
+}
+
+template <int N>
+struct MVDims {
+  static constexpr int N2 = N * N, N3 = N2 * N, NF = N + 1;
+  static constexpr int T = N >= 6 ? 256 : 128;
+  // mgrad_kernel: the record [MV_REC][N3] (first the state [11][N3]), then the
+  // flux points of all three families [NF][11][3][N2] (the inviscid kernel's layout)
+  static constexpr int gO = 0, gX = (MV_REC * N3 + 3) / 4 * 4;
+  static constexpr int XD = N2, XV = 3 * N2, XF = 11 * 3 * N2;
+  static constexpr size_t gbytes = (size_t)(gX + NF * XF) * sizeof(float);
+  // mvisc_kernel: NQ values at the solution points [NQ][N3], one family's flux
+  // points [NF][NQ][N2], the residual [7][N3]
+  template <bool KR>
+  struct V {
+    static constexpr int NQ = 11 + MV_REC + 6 + (KR ? 3 : 0);
+    static constexpr int oQ = 0, oX = (NQ * N3 + 3) / 4 * 4, oR = oX + (NF * NQ * N2 + 3) / 4 * 4;
+    static constexpr size_t bytes = (size_t)(oR + 7 * N3) * sizeof(float);
+  };
+  static constexpr int minb(size_t bytes) {
+    const int s = (int)(233472 / (bytes + 1024 + 64)), r = 65536 / (T * 64);
+    const int m = s < r ? s : r;
+    return m < 1 ? 1 : m;
+  }
+};
+
+// BR1 gradients of w' and the record formed from them, with its face traces.
+template <int N>
+__global__ void __launch_bounds__(MVDims<N>::T, MVDims<N>::minb(MVDims<N>::gbytes))
+    mgrad_kernel(const StageParams P, const Ops<float> ops, const Ops2 o2) {
   using MD = MVDims<N>;
-  constexpr int N2 = MD::N2, N3 = MD::N3, NF = MD::NF, T = MD::T;
-  constexpr int NQ = 11 + NGRAD + 6 + 3;  // q', rho0, p0, grad w', grad T0, grad S0, x
+  constexpr int N2 = MD::N2, N3 = MD::N3, NF = MD::NF, T = MD::T, XD = MD::XD, XV = MD::XV, XF = MD::XF;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float* sQ = reinterpret_cast<float*>(smem_raw);  // [NQ][N3]
-  float* sF = sQ + NQ * N3;                          // [7][NF][N2] one family
+  float* sO = reinterpret_cast<float*>(smem_raw) + MD::gO;  // the state, then the record
+  float* sX = reinterpret_cast<float*>(smem_raw) + MD::gX;
+  __shared__ int sNb[6], sMt[6];
   const int tid = threadIdx.x;
   const int64_t e = blockIdx.x;
-  const int64_t n_e = P.n_e;
   const float* Sfam = reinterpret_cast<const float*>(P.Sfam) + e * (9 * N2 * NF);
   const MViscCoef c = mvisc_coef(P);
-  mv_load_state<N>(P, e, sQ, T);
-  for (int n = tid; n < N3; n += T) {
-#pragma unroll 4
-    for (int k = 0; k < NGRAD; ++k) sQ[(11 + k) * N3 + n] = __ldg(P.mgrad + (e * NGRAD + k) * N3 + n);
-#pragma unroll
-    for (int k = 0; k < 6; ++k) sQ[(11 + NGRAD + k) * N3 + n] = __ldg(P.bg_visc + (1 + k) * n_e * N3 + e * N3 + n);
-#pragma unroll
-    for (int k = 0; k < 3; ++k)
-      sQ[(11 + NGRAD + 6 + k) * N3 + n] = __ldg(reinterpret_cast<const float*>(P.X) + (e * 3 + k) * N3 + n);
+  if (tid < 6) {
+    sNb[tid] = __ldg(P.nbr + e * 6 + tid);
+    sMt[tid] = __ldg(P.meta + e * 6 + tid);
   }
-  const int n = tid;
-  const int i0 = n % N, j0 = (n / N) % N, k0 = n / N2;
-  float acc[7];
-#pragma unroll
-  for (int v = 0; v < 7; ++v) acc[v] = 0.0f;
+  mv_load_state<N>(P, e, sO, T);
+  __syncthreads();
+  // extrapolate q'(9), rho0, p0 along every line to its family's flux points
+  mv_extrap<N, T, 11, 0, 3>(sO, N3, sX, XF, XV, XD, o2);
+  __syncthreads();
+  // w' at every flux point, at the element faces the BR1 average with the other
+  // side's (the neighbour's trace about its own background, or the wall ghost)
 #pragma unroll 1
-  for (int d = 0; d < 3; ++d) {
-    __syncthreads();
-    for (int t = tid; t < NF * N2; t += T) {
-      const int f = t % NF, line = t / NF, a = line % N, b = line / N;
-      float x[NQ];
+  for (int t = tid; t < NF * 3 * N2; t += T) {
+    const int f = t / (3 * N2), r = t - f * (3 * N2), d = r / N2, L = r - d * N2;
+    float* X = sX + f * XF + d * XD + L;
+    float q[11], w[8];
 #pragma unroll
-      for (int v = 0; v < NQ; ++v) {
-        float s = 0.0f;
+    for (int v = 0; v < 11; ++v) q[v] = X[v * XV];
+    mv_prim(q, q[9], q[10], c, w);
+    if (f == 0 || f == N) {
+      const int F = 2 * d + (f == N);
+      const int nb = sNb[F], mt = sMt[F];
+      float q2[9], r2 = q[9], p2 = q[10];
+      if (nb >= 0) {
+        int64_t nf;
+        int pn;
+        mv_partner<N>(nb, mt, L, nf, pn);
+        const float* Tn = reinterpret_cast<const float*>(P.tr_in) + nf * 9 * N2 + pn;
 #pragma unroll
-        for (int i = 0; i < N; ++i) s = fmaf(ops.E[f * N + i], sQ[v * N3 + sol_index<N>(d, i, a, b)], s);
-        x[v] = s;
-      }
-      const float* Sp = Sfam + s32_index(N, d, f, 0, line);
-      const float Sx = Sp[0], Sy = Sp[N2], Sz = Sp[2 * N2];
-      const float kr = mv_kappa_r(c, x[NQ - 3], x[NQ - 2], x[NQ - 1]);
-      float Fv[7];
-      if (f > 0 && f < N) {
-        mv_flux(x, x[9], x[10], x + 11, x + 11 + NGRAD, x + 11 + NGRAD + 3, Sx, Sy, Sz, c, kr, Fv);
-      } else {
-        // the average of both sides' F_vis . n along this side's outward unit normal, times |S|
-        const int side = f == N, F = 2 * d + side;
-        const float mag = sqrtf(Sx * Sx + Sy * Sy + Sz * Sz), im = 1.0f / mag, sg = side ? 1.0f : -1.0f;
-        const float nx = sg * Sx * im, ny = sg * Sy * im, nz = sg * Sz * im;
-        mv_flux(x, x[9], x[10], x + 11, x + 11 + NGRAD, x + 11 + NGRAD + 3, nx, ny, nz, c, kr, Fv);
+        for (int v = 0; v < 9; ++v) q2[v] = Tn[v * N2];
         const int64_t gidx = e * 6 + F;
-        const int nb = __ldg(P.nbr + gidx), mt = __ldg(P.meta + gidx);
-        if (nb >= 0) {
-          const int code = meta_code(mt);
-          const int u = (code & 4) ? b : a, ww = (code & 4) ? a : b;
-          const int a2 = (code & 2) ? N - 1 - u : u, b2 = (code & 1) ? N - 1 - ww : ww;
-          const int64_t nf = (int64_t)nb * 6 + meta_nbF(mt);
-          float q2[9], g2[NGRAD], gT2[3], gS2[3], F2[7];
-          const float* Tn = reinterpret_cast<const float*>(P.tr_in) + nf * 9 * N2 + a2 + N * b2;
-#pragma unroll
-          for (int v = 0; v < 9; ++v) q2[v] = Tn[v * N2];
-          const float* Gn = P.mgtr_in + nf * NGRAD * N2 + a2 + N * b2;
-#pragma unroll
-          for (int k = 0; k < NGRAD; ++k) g2[k] = Gn[k * N2];
-          const float* Bn = P.bg_vtr + nf * 6 * N2 + a2 + N * b2;
-#pragma unroll
-          for (int k = 0; k < 3; ++k) {
-            gT2[k] = __ldg(Bn + k * N2);
-            gS2[k] = __ldg(Bn + (3 + k) * N2);
-          }
-          const int pt = a + N * b;
-          const float r2 = x[9] + __ldg(P.bg_jump + (gidx * 2 + 0) * N2 + pt);
-          const float p2 = x[10] + __ldg(P.bg_jump + (gidx * 2 + 1) * N2 + pt);
-          mv_flux(q2, r2, p2, g2, gT2, gS2, nx, ny, nz, c, kr, F2);
-#pragma unroll
-          for (int v = 0; v < 7; ++v) Fv[v] = 0.5f * (Fv[v] + F2[v]);
-        }
-        const float sm = sg * mag;
-#pragma unroll
-        for (int v = 0; v < 7; ++v) Fv[v] *= sm;
+        r2 += __ldg(P.bg_jump + (gidx * 2 + 0) * N2 + L);
+        p2 += __ldg(P.bg_jump + (gidx * 2 + 1) * N2 + L);
+      } else {
+        const float* Sp = Sfam + s32_index(N, d, f, 0, L);
+        const float Sx = __ldg(Sp), Sy = __ldg(Sp + N2), Sz = __ldg(Sp + 2 * N2);
+        const float im = rsqrtf(Sx * Sx + Sy * Sy + Sz * Sz), sg = (f == N) ? 1.0f : -1.0f;
+        wall_ghost<float>(q, sg * Sx * im, sg * Sy * im, sg * Sz * im, meta_bc(mt), q2);
       }
+      float w2[8];
+      mv_prim(q2, r2, p2, c, w2);
 #pragma unroll
-      for (int v = 0; v < 7; ++v) sF[(v * NF + f) * N2 + line] = Fv[v];
+      for (int k = 0; k < 8; ++k) w[k] = 0.5f * (w[k] + w2[k]);
     }
-    __syncthreads();
-    if (n < N3) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) X[k * XV] = w[k];
+  }
+  __syncthreads();
+  // |J| d w'_c / d x_j = sum_d D_d (S^d_j w'_c) at this thread's solution points,
+  // two components c at a time; then the record tau, J, grad T', grad S'
+#pragma unroll 1
+  for (int n = tid; n < N3; n += T) {
+    const int i0 = n % N, j0 = (n / N) % N, k0 = n / N2;
+    float2 acc[12];  // acc[4 j + p]: components (2p, j) and (2p + 1, j)
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] = make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
       const int id = d == 0 ? i0 : (d == 1 ? j0 : k0);
-      const int line = d == 0 ? j0 + N * k0 : (d == 1 ? i0 + N * k0 : i0 + N * j0);
+      const int L = d == 0 ? j0 + N * k0 : (d == 1 ? i0 + N * k0 : i0 + N * j0);
 #pragma unroll
       for (int f = 0; f <= N; ++f) {
         const float Df = ops.D[id * NF + f];
+        const float* Sp = Sfam + s32_index(N, d, f, 0, L);
+        const float2 DS[3] = {f2(Df * __ldg(Sp)), f2(Df * __ldg(Sp + N2)), f2(Df * __ldg(Sp + 2 * N2))};
+        const float* W = sX + f * XF + d * XD + L;
 #pragma unroll
-        for (int v = 0; v < 7; ++v) acc[v] = fmaf(Df, sF[(v * NF + f) * N2 + line], acc[v]);
+        for (int p = 0; p < 4; ++p) {
+          const float2 wp = make_float2(W[(2 * p) * XV], W[(2 * p + 1) * XV]);
+#pragma unroll
+          for (int j = 0; j < 3; ++j) acc[4 * j + p] = fma2(DS[j], wp, acc[4 * j + p]);
+        }
       }
     }
-  }
-  if (n < N3) {
     const float iJ = __ldg(reinterpret_cast<const float*>(P.invJ) + e * N3 + n);
-    const int64_t pl = n_e * N3, g = e * N3 + n;
+    float g[24];  // g[3 c + j] = d w'_c / d x_j
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+      for (int p = 0; p < 4; ++p) {
+        g[3 * (2 * p) + j] = acc[4 * j + p].x * iJ;
+        g[3 * (2 * p + 1) + j] = acc[4 * j + p].y * iJ;
+      }
+    const float divu = g[0] + g[4] + g[8];
+    float rec[MV_REC];
+    rec[0] = c.mu * (g[0] + g[0]) + c.lam * divu;
+    rec[1] = c.mu * (g[4] + g[4]) + c.lam * divu;
+    rec[2] = c.mu * (g[8] + g[8]) + c.lam * divu;
+    rec[3] = c.mu * (g[1] + g[3]);
+    rec[4] = c.mu * (g[2] + g[6]);
+    rec[5] = c.mu * (g[5] + g[7]);
+    rec[MV_J + 0] = g[3 * 7 + 1] - g[3 * 6 + 2];
+    rec[MV_J + 1] = g[3 * 5 + 2] - g[3 * 7 + 0];
+    rec[MV_J + 2] = g[3 * 6 + 0] - g[3 * 5 + 1];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      rec[MV_GT + j] = g[3 * 3 + j];
+      rec[MV_GS + j] = g[3 * 4 + j];
+    }
+    float* Ge = P.mgrad_out + e * MV_REC * N3 + n;
+#pragma unroll
+    for (int k = 0; k < MV_REC; ++k) {
+      sO[k * N3 + n] = rec[k];
+      Ge[k * N3] = rec[k];
+    }
+  }
+  __syncthreads();
+  // face traces of the record: both ends of every line, two values at a time
+  constexpr int NL = 3 * N2, NP = (MV_REC + 1) / 2;
+#pragma unroll 1
+  for (int t = tid; t < NL * NP; t += T) {
+    const int pr = t / NL, l = t - pr * NL, d = l / N2, L = l - d * N2;
+    int base, stride;
+    line_geom<N>(d, L, base, stride);
+    const int v0 = 2 * pr, v1 = v0 + 1 < MV_REC ? v0 + 1 : v0;
+    float2 s0 = make_float2(0.0f, 0.0f), s1 = make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      const float2 x = make_float2(sO[v0 * N3 + base + i * stride], sO[v1 * N3 + base + i * stride]);
+      s0 = fma2(o2.E0[i], x, s0);
+      s1 = fma2(o2.EN[i], x, s1);
+    }
+    float* Tr = P.mgtr_out + (e * 6 + 2 * d) * MV_REC * N2 + L;
+    Tr[v0 * N2] = s0.x;
+    Tr[MV_REC * N2 + v0 * N2] = s1.x;
+    if (v1 != v0) {
+      Tr[v1 * N2] = s0.y;
+      Tr[MV_REC * N2 + v1 * N2] = s1.y;
+    }
+  }
+}
+
+// One family of the viscous flux: S^d . F_vis at the flux points of family D
+// (values at flux point (f, L) read from X[f NQ N^2 + v N^2 + L], the flux
+// written over its first seven values).  At the element faces the common flux is
+// the average of both sides' F_vis . n (the neighbour's from its traces about its
+// own background), at a wall this side's alone.
+template <int N, bool KR, int D>
+__device__ __forceinline__ void mv_family_flux(const StageParams& P, const MViscCoef& c, int64_t e, const float* Sfam,
+                                               float* X, const int* sNb, const int* sMt) {
+  constexpr int N2 = N * N, NF = N + 1, T = MVDims<N>::T, NQ = MVDims<N>::template V<KR>::NQ;
+  constexpr int Q_R0 = 9, Q_P0 = 10, Q_REC = 11, Q_GT0 = Q_REC + MV_REC, Q_GS0 = Q_GT0 + 3, Q_X = Q_GS0 + 3;
+#pragma unroll 1
+  for (int t = threadIdx.x; t < NF * N2; t += T) {
+    const int f = t / N2, L = t - f * N2;
+    float* Xp = X + f * NQ * N2 + L;
+    float x[NQ];
+#pragma unroll
+    for (int v = 0; v < NQ; ++v) x[v] = Xp[v * N2];
+    const float* Sp = Sfam + s32_index(N, D, f, 0, L);
+    const float Sx = __ldg(Sp), Sy = __ldg(Sp + N2), Sz = __ldg(Sp + 2 * N2);
+    const float kr = KR ? mv_kappa_r(c, x[Q_X], x[Q_X + 1], x[Q_X + 2]) : c.kappa_r;
+    float Fv[7];
+    if (f > 0 && f < N) {
+      mv_flux(x, x[Q_R0], x[Q_P0], x + Q_REC, x + Q_GT0, x + Q_GS0, Sx, Sy, Sz, c, kr, Fv);
+    } else {
+      const int F = 2 * D + (f == N);
+      const float mag = sqrtf(Sx * Sx + Sy * Sy + Sz * Sz), im = 1.0f / mag, sg = (f == N) ? 1.0f : -1.0f;
+      const float nx = sg * Sx * im, ny = sg * Sy * im, nz = sg * Sz * im;
+      mv_flux(x, x[Q_R0], x[Q_P0], x + Q_REC, x + Q_GT0, x + Q_GS0, nx, ny, nz, c, kr, Fv);
+      const int nb = sNb[F], mt = sMt[F];
+      if (nb >= 0) {
+        int64_t nf;
+        int pn;
+        mv_partner<N>(nb, mt, L, nf, pn);
+        float q2[9], g2[MV_REC], gT2[3], gS2[3], F2[7];
+        const float* Tn = reinterpret_cast<const float*>(P.tr_in) + nf * 9 * N2 + pn;
+#pragma unroll
+        for (int v = 0; v < 9; ++v) q2[v] = Tn[v * N2];
+        const float* Gn = P.mgtr_in + nf * MV_REC * N2 + pn;
+#pragma unroll
+        for (int k = 0; k < MV_REC; ++k) g2[k] = Gn[k * N2];
+        const float* Bn = P.bg_vtr + nf * 6 * N2 + pn;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          gT2[k] = __ldg(Bn + k * N2);
+          gS2[k] = __ldg(Bn + (3 + k) * N2);
+        }
+        const int64_t gidx = e * 6 + F;
+        const float r2 = x[Q_R0] + __ldg(P.bg_jump + (gidx * 2 + 0) * N2 + L);
+        const float p2 = x[Q_P0] + __ldg(P.bg_jump + (gidx * 2 + 1) * N2 + L);
+        mv_flux(q2, r2, p2, g2, gT2, gS2, nx, ny, nz, c, kr, F2);
+#pragma unroll
+        for (int v = 0; v < 7; ++v) Fv[v] = 0.5f * (Fv[v] + F2[v]);
+      }
+      const float sm = sg * mag;
+#pragma unroll
+      for (int v = 0; v < 7; ++v) Fv[v] *= sm;
+    }
+#pragma unroll
+    for (int v = 0; v < 7; ++v) Xp[v * N2] = Fv[v];
+  }
+}
+
+// The viscous residual of the stage state, R_vis = div(S^d . F_vis)/|J|, the
+// background's included: out [7][n_e N^3] (components rho U, E, B).  Family by
+// family: extrapolate the NQ values (q'(9), rho0, p0, the record, grad T0,
+// grad S0 and, with KR, x for kappa_r(r)) along the lines of direction d, the flux
+// at the family's points, its derivative along the lines added to the residual.
+template <int N, bool KR>
+__global__ void __launch_bounds__(MVDims<N>::T, MVDims<N>::minb(MVDims<N>::template V<KR>::bytes))
+    mvisc_kernel(const StageParams P, const Ops2 o2) {
+  using MD = MVDims<N>;
+  using MV = typename MD::template V<KR>;
+  constexpr int N2 = MD::N2, N3 = MD::N3, T = MD::T, NQ = MV::NQ;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* sQ = reinterpret_cast<float*>(smem_raw) + MV::oQ;
+  float* sX = reinterpret_cast<float*>(smem_raw) + MV::oX;
+  float* sR = reinterpret_cast<float*>(smem_raw) + MV::oR;
+  __shared__ int sNb[6], sMt[6];
+  const int tid = threadIdx.x;
+  const int64_t e = blockIdx.x;
+  const int64_t n_e = P.n_e;
+  const float* Sfam = reinterpret_cast<const float*>(P.Sfam) + e * (9 * N2 * (N + 1));
+  const MViscCoef c = mvisc_coef(P);
+  if (tid < 6) {
+    sNb[tid] = __ldg(P.nbr + e * 6 + tid);
+    sMt[tid] = __ldg(P.meta + e * 6 + tid);
+  }
+  mv_load_state<N>(P, e, sQ, T);
+  for (int n = tid; n < N3; n += T) {
+    const float* G = P.mgrad + e * MV_REC * N3 + n;
+#pragma unroll
+    for (int k = 0; k < MV_REC; ++k) sQ[(11 + k) * N3 + n] = __ldg(G + k * N3);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) sQ[(11 + MV_REC + k) * N3 + n] = __ldg(P.bg_visc + (1 + k) * n_e * N3 + e * N3 + n);
+    if (KR) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        sQ[(11 + MV_REC + 6 + k) * N3 + n] = __ldg(reinterpret_cast<const float*>(P.X) + (e * 3 + k) * N3 + n);
+    }
+  }
+  constexpr int OF = NQ * N2;
+  __syncthreads();
+  mv_extrap<N, T, NQ, 0, 1>(sQ, N3, sX, OF, N2, 0, o2);
+  __syncthreads();
+  mv_family_flux<N, KR, 0>(P, c, e, Sfam, sX, sNb, sMt);
+  __syncthreads();
+  mv_deriv<N, T, 7, 0, false>(sX, OF, N2, sR, o2);
+  __syncthreads();
+  mv_extrap<N, T, NQ, 1, 2>(sQ, N3, sX, OF, N2, 0, o2);
+  __syncthreads();
+  mv_family_flux<N, KR, 1>(P, c, e, Sfam, sX, sNb, sMt);
+  __syncthreads();
+  mv_deriv<N, T, 7, 1, true>(sX, OF, N2, sR, o2);
+  __syncthreads();
+  mv_extrap<N, T, NQ, 2, 3>(sQ, N3, sX, OF, N2, 0, o2);
+  __syncthreads();
+  mv_family_flux<N, KR, 2>(P, c, e, Sfam, sX, sNb, sMt);
+  __syncthreads();
+  mv_deriv<N, T, 7, 2, true>(sX, OF, N2, sR, o2);
+  __syncthreads();
+  const int64_t pl = n_e * N3;
+  for (int n = tid; n < N3; n += T) {
+    const int64_t g = e * N3 + n;
+    const float iJ = __ldg(reinterpret_cast<const float*>(P.invJ) + g);
 #pragma unroll
     for (int v = 0; v < 7; ++v) {
-      float r = acc[v] * iJ;                                  // + div(S F_vis)/|J|
-      if (v == 3) r += __ldg(P.bg_visc + g);                  // the background's viscous residual (energy)
+      float r = sR[v * N3 + n] * iJ;            // + div(S F_vis)/|J|
+      if (v == 3) r += __ldg(P.bg_visc + g);  // the background's viscous residual (energy)
       P.rvis_out[v * pl + g] = r;
     }
   }
 }
 
 template <int N>
-cudaError_t launch_mixed_visc_t(const StageParams& Pg, const StageParams& Pv, const Ops<float>& ops, cudaStream_t s) {
+cudaError_t launch_mixed_visc_t(const StageParams& Pg, const StageParams& Pv, const Ops<float>& ops, const Ops2& o2,
+                                cudaStream_t s) {
   using MD = MVDims<N>;
-  constexpr size_t gbytes = (size_t)(11 * MD::N3 + 8 * MD::NF * MD::N2 + NGRAD * MD::N3) * sizeof(float);
-  constexpr size_t vbytes = (size_t)((11 + NGRAD + 6 + 3) * MD::N3 + 7 * MD::NF * MD::N2) * sizeof(float);
   if (Pg.n_e == 0) return cudaSuccess;
+  const bool kr = Pv.kappa_r1 != 0.0 || Pv.kappa_r2 != 0.0;
+  auto kv = kr ? mvisc_kernel<N, true> : mvisc_kernel<N, false>;
+  const size_t vbytes = kr ? MD::template V<true>::bytes : MD::template V<false>::bytes;
   cudaError_t err = cudaSuccess;
-  if (gbytes > 48 * 1024) err = cudaFuncSetAttribute(mgrad_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gbytes);
+  if (MD::gbytes > 48 * 1024)
+    err = cudaFuncSetAttribute(mgrad_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MD::gbytes);
   if (err == cudaSuccess && vbytes > 48 * 1024)
-    err = cudaFuncSetAttribute(mvisc_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vbytes);
+    err = cudaFuncSetAttribute(kv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vbytes);
   if (err != cudaSuccess) return err;
-  mgrad_kernel<N><<<(unsigned)Pg.n_e, MD::T, gbytes, s>>>(Pg, ops);
+  mgrad_kernel<N><<<(unsigned)Pg.n_e, MD::T, MD::gbytes, s>>>(Pg, ops, o2);
   err = cudaGetLastError();
   if (err != cudaSuccess) return err;
-  mvisc_kernel<N><<<(unsigned)Pv.n_e, MD::T, vbytes, s>>>(Pv, ops);
+  kv<<<(unsigned)Pv.n_e, MD::T, vbytes, s>>>(Pv, o2);
   return cudaGetLastError();
 }
 
