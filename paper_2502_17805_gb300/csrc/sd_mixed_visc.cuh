@@ -45,7 +45,9 @@ struct MViscCoef {
   bool kr_varies;
 };
 
-__device__ __forceinline__ MViscCoef mvisc_coef(const StageParams& P) {
+// The FP32 coefficients, converted once on the host (the FP64 pipe of an SM is
+// narrow: per-thread FP64 divisions cost more than a phase's point work).
+inline MViscCoef mvisc_coef(const StageParams& P) {
   MViscCoef c;
   c.gm1 = (float)(P.gamma - 1.0);
   c.mu = (float)P.mu;
@@ -63,12 +65,23 @@ __device__ __forceinline__ MViscCoef mvisc_coef(const StageParams& P) {
   return c;
 }
 
-// p' of a perturbation q'(9) about (rho0, p0): the pressure minus p0
-__device__ __forceinline__ float mv_pprime(const float* q, float r0, const MViscCoef& c) {
-  const float rho = r0 + q[0];
+// log(1 + x) for x > -1.  For |x| <= 1/32 (the perturbation ratios p'/p0 and
+// rho'/rho0 of the mixed path, as a rule) from log(1 + x) = 2 atanh(z),
+// z = x / (2 + x), by the Taylor series of atanh through z^7 (|z| <= 1/63: the
+// next term is below 1e-15 of the sum); elsewhere the library's log1pf.
+__device__ __forceinline__ float mv_log1p(float x) {
+  if (fabsf(x) > 0.03125f) return log1pf(x);
+  const float z = x / (2.0f + x), z2 = z * z;
+  const float s = fmaf(z2, fmaf(z2, fmaf(z2, 1.0f / 7.0f, 0.2f), 1.0f / 3.0f), 1.0f);
+  return 2.0f * z * s;
+}
+
+// p' of a perturbation q'(9) about (rho0, p0): the pressure minus p0, given
+// ir = 1 / (rho0 + rho')
+__device__ __forceinline__ float mv_pprime(const float* q, float ir, const MViscCoef& c) {
   const float m2 = q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
   const float B2 = q[5] * q[5] + q[6] * q[6] + q[7] * q[7];
-  return c.gm1 * (q[4] - 0.5f * (m2 / rho + B2 + q[8] * q[8]));
+  return c.gm1 * (q[4] - 0.5f * (m2 * ir + B2 + q[8] * q[8]));
 }
 
 // w' = (u, v, w, T', S', Bx, By, Bz) of the perturbation q'(9) about (r0, p0)
@@ -78,9 +91,28 @@ __device__ __forceinline__ void mv_prim(const float* q, float r0, float p0, cons
   w[0] = q[1] * ir;
   w[1] = q[2] * ir;
   w[2] = q[3] * ir;
-  const float pp = mv_pprime(q, r0, c);
-  w[3] = (pp * r0 - p0 * q[0]) * ir / (r0 * c.R);
-  w[4] = c.cp * (log1pf(pp / p0) * c.inv_gamma - log1pf(q[0] / r0));
+  const float pp = mv_pprime(q, ir, c);
+  w[3] = (pp * r0 - p0 * q[0]) * ir * (1.0f / (r0 * c.R));
+  w[4] = c.cp * (mv_log1p(pp * (1.0f / p0)) * c.inv_gamma - mv_log1p(q[0] * (1.0f / r0)));
+  w[5] = q[5];
+  w[6] = q[6];
+  w[7] = q[7];
+}
+
+// mv_prim for two points at once (paired FP32; reciprocals and log1p per lane)
+__device__ __forceinline__ void mv_prim2(const float2* q, float2 r0, float2 p0, const MViscCoef& c, float2* w) {
+  const float2 half = f2(0.5f);
+  const float2 rho = add2(r0, q[0]);
+  const float2 ir = rcp2(rho);
+  w[0] = mul2(q[1], ir);
+  w[1] = mul2(q[2], ir);
+  w[2] = mul2(q[3], ir);
+  const float2 m2 = dot3(q[1], q[2], q[3], q[1], q[2], q[3]);
+  const float2 B2 = dot3(q[5], q[6], q[7], q[5], q[6], q[7]);
+  const float2 pp = mul2(f2(c.gm1), sub2(q[4], mul2(half, fma2(q[8], q[8], add2(mul2(m2, ir), B2)))));
+  w[3] = mul2(mul2(sub2(mul2(pp, r0), mul2(p0, q[0])), ir), rcp2(mul2(r0, f2(c.R))));
+  const float2 a = mul2(pp, rcp2(p0)), b = mul2(q[0], rcp2(r0));
+  w[4] = mul2(f2(c.cp), make_float2(mv_log1p(a.x) * c.inv_gamma - mv_log1p(b.x), mv_log1p(a.y) * c.inv_gamma - mv_log1p(b.y)));
   w[5] = q[5];
   w[6] = q[6];
   w[7] = q[7];
@@ -101,7 +133,7 @@ __device__ __forceinline__ void mv_flux(const float* q, float r0, float p0, cons
   const float rho = r0 + q[0];
   const float ir = 1.0f / rho;
   const float Ux = q[1] * ir, Uy = q[2] * ir, Uz = q[3] * ir;
-  const float pp = mv_pprime(q, r0, c);
+  const float pp = mv_pprime(q, ir, c);
   const float txx = rec[0], tyy = rec[1], tzz = rec[2], txy = rec[3], txz = rec[4], tyz = rec[5];
   const float Jx = rec[MV_J], Jy = rec[MV_J + 1], Jz = rec[MV_J + 2];
   F[0] = txx * nx + txy * ny + txz * nz;
@@ -135,10 +167,11 @@ __device__ __forceinline__ float mv_kappa_r(const MViscCoef& c, float x, float y
 }
 
 // The stage state of the FP32-mixed path as q'(9), rho0, p0 at the solution
-// points, [11][N^3]: the increment form's stored q' of q^n plus the register D
-// (stages that read it), or the FP64 state q_in less the background.
+// points, [11][QS] (planes QS >= N^3 floats apart): the increment form's stored
+// q' of q^n plus the register D (stages that read it), or the FP64 state q_in
+// less the background.
 template <int N>
-__device__ __forceinline__ void mv_load_state(const StageParams& P, int64_t e, float* sQ, int T) {
+__device__ __forceinline__ void mv_load_state(const StageParams& P, int64_t e, float* sQ, int T, int QS) {
   constexpr int N3 = N * N * N;
   const int64_t n_e = P.n_e;
   for (int n = threadIdx.x; n < N3; n += T) {
@@ -150,20 +183,20 @@ __device__ __forceinline__ void mv_load_state(const StageParams& P, int64_t e, f
       for (int v = 0; v < 9; ++v) {
         float x = __ldg(P.qp_in + v * qplane + gd);
         if (P.lsr_read) x += __ldg(P.dreg + v * qplane + gd);
-        sQ[v * N3 + n] = x;
+        sQ[v * QS + n] = x;
       }
     } else {
       const int64_t g = e * P.stride + n;
       double qv[9];
 #pragma unroll
       for (int v = 0; v < 9; ++v) qv[v] = __ldg(P.q_in + v * P.plane + g);
-      sQ[0 * N3 + n] = f64_to_f32(qv[0] - f32_to_f64(r0));
+      sQ[0 * QS + n] = f64_to_f32(qv[0] - f32_to_f64(r0));
 #pragma unroll
-      for (int v = 1; v < 9; ++v) sQ[v * N3 + n] = f64_to_f32(qv[v]);
-      sQ[4 * N3 + n] = f64_to_f32(fma(-f32_to_f64(p0), P.inv_gm1, qv[4]));
+      for (int v = 1; v < 9; ++v) sQ[v * QS + n] = f64_to_f32(qv[v]);
+      sQ[4 * QS + n] = f64_to_f32(fma(-f32_to_f64(p0), P.inv_gm1, qv[4]));
     }
-    sQ[9 * N3 + n] = r0;
-    sQ[10 * N3 + n] = p0;
+    sQ[9 * QS + n] = r0;
+    sQ[10 * QS + n] = p0;
   }
 }
 
@@ -172,7 +205,8 @@ __device__ __forceinline__ void mv_load_state(const StageParams& P, int64_t e, f
 // the line's family, two variables at a time in paired FP32 arithmetic, in the
 // even-odd form (E[N-f][N-1-i] = E[f][i]): variable v at flux point f of line L
 // of direction d goes to out[f OF + v OV + (d - D0) OD + L].  The tasks
-// (variable pair, line), lines innermost, are spread over the T threads.
+// (variable pair, line), lines innermost, are spread over the T threads; the
+// lines of line_flip read their points in swapped pairs (fewer bank conflicts).
 template <int N, int T, int NV, int D0, int D1>
 __device__ __forceinline__ void mv_extrap(const float* in, int VS, float* out, int OF, int OV, int OD,
                                           const Ops2& o2) {
@@ -180,15 +214,12 @@ __device__ __forceinline__ void mv_extrap(const float* in, int VS, float* out, i
 #pragma unroll 1
   for (int t = threadIdx.x; t < NL * NP; t += T) {
     const int pr = t / NL, l = t - pr * NL;
-    const int d = D0 + l / N2, L = l - (l / N2) * N2;
+    const int d = D1 - D0 == 1 ? D0 : D0 + l / N2, L = D1 - D0 == 1 ? l : l - (l / N2) * N2;
     int base, stride;
     line_geom<N>(d, L, base, stride);
     const int v0 = 2 * pr, v1 = v0 + 1 < NV ? v0 + 1 : v0;
-    const float* a = in + v0 * VS + base;
-    const float* b = in + v1 * VS + base;
     float2 ql[N];
-#pragma unroll
-    for (int i = 0; i < N; ++i) ql[i] = make_float2(a[i * stride], b[i * stride]);
+    load_line<N>(in + v0 * VS, in + v1 * VS, base, stride, line_flip<N>(d, L), ql);
     float2 sv[HP > 0 ? HP : 1], dv[HP > 0 ? HP : 1];
 #pragma unroll
     for (int i = 0; i < HP; ++i) {
@@ -222,11 +253,11 @@ __device__ __forceinline__ void mv_extrap(const float* in, int VS, float* out, i
 // Differentiate NV flux variables given at the N+1 flux points of every line of
 // direction D (variable v at flux point f of line L at in[f IF + v IV + L]) back
 // to the line's N solution points (even-odd form, D[N-1-i][f] = -D[i][N-f]) and
-// store (ADD false) or add (ADD true) the result into acc[v N^3 + n].  For one
+// store (ADD false) or add (ADD true) the result into acc[v AS + n].  For one
 // direction the lines partition the solution points, so no two tasks touch the
 // same word.
 template <int N, int T, int NV, int D, bool ADD>
-__device__ __forceinline__ void mv_deriv(const float* in, int IF, int IV, float* acc, const Ops2& o2) {
+__device__ __forceinline__ void mv_deriv(const float* in, int IF, int IV, float* acc, int AS, const Ops2& o2) {
   constexpr int N2 = N * N, N3 = N2 * N, NF = N + 1, HF = NF / 2, NP = (NV + 1) / 2;
 #pragma unroll 1
   for (int t = threadIdx.x; t < N2 * NP; t += T) {
@@ -243,9 +274,7 @@ __device__ __forceinline__ void mv_deriv(const float* in, int IF, int IV, float*
       sf[f] = add2(fv[f], fv[N - f]);
       df[f] = sub2(fv[f], fv[N - f]);
     }
-    float* a = acc + v0 * N3 + base;
-    float* b = acc + v1 * N3 + base;
-    const bool two = v1 != v0;
+    float2 o[N];
 #pragma unroll
     for (int i = 0; 2 * i <= N - 1; ++i) {
       float2 p = (NF & 1) ? mul2(o2.Ds[i * NF + HF], fv[HF]) : make_float2(0.0f, 0.0f);
@@ -255,30 +284,25 @@ __device__ __forceinline__ void mv_deriv(const float* in, int IF, int IV, float*
         p = fma2(o2.Ds[i * NF + f], sf[f], p);
         r = fma2(o2.Dd[i * NF + f], df[f], r);
       }
-      float2 lo, hi;
-      const bool mid = 2 * i == N - 1;
-      if (mid) {
-        lo = r;
-        hi = r;
+      if (2 * i == N - 1) {
+        o[i] = r;
       } else {
-        lo = add2(p, r);
-        hi = sub2(r, p);
+        o[i] = add2(p, r);
+        o[N - 1 - i] = sub2(r, p);
       }
-      const int ilo = i * stride, ihi = (N - 1 - i) * stride;
+    }
+    float* a = acc + v0 * AS + base;
+    float* b = acc + v1 * AS + base;
+    const bool two = v1 != v0, flip = line_flip<N>(D, L);
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      const int k = ((i ^ 1) < N && flip) ? (i ^ 1) : i;
       if (ADD) {
-        a[ilo] += lo.x;
-        if (two) b[ilo] += lo.y;
-        if (!mid) {
-          a[ihi] += hi.x;
-          if (two) b[ihi] += hi.y;
-        }
+        a[k * stride] += o[k].x;
+        if (two) b[k * stride] += o[k].y;
       } else {
-        a[ilo] = lo.x;
-        if (two) b[ilo] = lo.y;
-        if (!mid) {
-          a[ihi] = hi.x;
-          if (two) b[ihi] = hi.y;
-        }
+        a[k * stride] = o[k].x;
+        if (two) b[k * stride] = o[k].y;
       }
     }
   }
@@ -298,22 +322,30 @@ __device__ __forceinline__ void mv_partner(int nb, int mt, int pt, int64_t& nf, 
 template <int N>
 struct MVDims {
   static constexpr int N2 = N * N, N3 = N2 * N, NF = N + 1;
+  // threads: mgrad_kernel T; mvisc_kernel TV, at N = 6 288 so that its line
+  // tasks (36 lines x 16 variable pairs per family) take two full rounds
   static constexpr int T = N >= 6 ? 256 : 128;
-  // mgrad_kernel: the record [MV_REC][N3] (first the state [11][N3]), then the
+  static constexpr int TV = N == 6 ? 288 : T;
+  // Plane stride of the solution-point arrays in shared memory: the least
+  // QS >= N^3 with QS = 2 (mod 16), so that the warps' line reads meet fewer
+  // bank conflicts where their lanes span two variable planes (modelled at N = 6:
+  // with line_flip, 1,680 -> 1,104 wavefronts for mvisc_kernel's line reads).
+  static constexpr int QS = N3 + ((18 - N3 % 16) % 16);
+  // mgrad_kernel: the record [MV_REC][QS] (first the state [11][QS]), then the
   // flux points of all three families [NF][11][3][N2] (the inviscid kernel's layout)
-  static constexpr int gO = 0, gX = (MV_REC * N3 + 3) / 4 * 4;
+  static constexpr int gO = 0, gX = (MV_REC * QS + 3) / 4 * 4;
   static constexpr int XD = N2, XV = 3 * N2, XF = 11 * 3 * N2;
   static constexpr size_t gbytes = (size_t)(gX + NF * XF) * sizeof(float);
-  // mvisc_kernel: NQ values at the solution points [NQ][N3], one family's flux
-  // points [NF][NQ][N2], the residual [7][N3]
+  // mvisc_kernel: NQ values at the solution points [NQ][QS], one family's flux
+  // points [NF][NQ][N2], the residual [7][QS]
   template <bool KR>
   struct V {
     static constexpr int NQ = 11 + MV_REC + 6 + (KR ? 3 : 0);
-    static constexpr int oQ = 0, oX = (NQ * N3 + 3) / 4 * 4, oR = oX + (NF * NQ * N2 + 3) / 4 * 4;
-    static constexpr size_t bytes = (size_t)(oR + 7 * N3) * sizeof(float);
+    static constexpr int oQ = 0, oX = (NQ * QS + 3) / 4 * 4, oR = oX + (NF * NQ * N2 + 3) / 4 * 4;
+    static constexpr size_t bytes = (size_t)(oR + 7 * QS) * sizeof(float);
   };
-  static constexpr int minb(size_t bytes) {
-    const int s = (int)(233472 / (bytes + 1024 + 64)), r = 65536 / (T * 64);
+  static constexpr int minb(size_t bytes, int threads) {
+    const int s = (int)(233472 / (bytes + 1024 + 64)), r = 65536 / (threads * 64);
     const int m = s < r ? s : r;
     return m < 1 ? 1 : m;
   }
@@ -321,10 +353,11 @@ struct MVDims {
 
 // BR1 gradients of w' and the record formed from them, with its face traces.
 template <int N>
-__global__ void __launch_bounds__(MVDims<N>::T, MVDims<N>::minb(MVDims<N>::gbytes))
-    mgrad_kernel(const StageParams P, const Ops<float> ops, const Ops2 o2) {
+__global__ void __launch_bounds__(MVDims<N>::T, MVDims<N>::minb(MVDims<N>::gbytes, MVDims<N>::T))
+    mgrad_kernel(const StageParams P, const Ops<float> ops, const Ops2 o2, const MViscCoef c) {
   using MD = MVDims<N>;
   constexpr int N2 = MD::N2, N3 = MD::N3, NF = MD::NF, T = MD::T, XD = MD::XD, XV = MD::XV, XF = MD::XF;
+  constexpr int QS = MD::QS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* sO = reinterpret_cast<float*>(smem_raw) + MD::gO;  // the state, then the record
   float* sX = reinterpret_cast<float*>(smem_raw) + MD::gX;
@@ -332,53 +365,78 @@ __global__ void __launch_bounds__(MVDims<N>::T, MVDims<N>::minb(MVDims<N>::gbyte
   const int tid = threadIdx.x;
   const int64_t e = blockIdx.x;
   const float* Sfam = reinterpret_cast<const float*>(P.Sfam) + e * (9 * N2 * NF);
-  const MViscCoef c = mvisc_coef(P);
   if (tid < 6) {
     sNb[tid] = __ldg(P.nbr + e * 6 + tid);
     sMt[tid] = __ldg(P.meta + e * 6 + tid);
+  } else if (tid >= 32 && tid < 32 + 6) {
+    // L2 prefetch of the neighbours' traces that the face points read
+    const int k = tid - 32;
+    const int nb = __ldg(P.nbr + e * 6 + k), mt = __ldg(P.meta + e * 6 + k);
+    if (nb >= 0)
+      l2_prefetch(reinterpret_cast<const float*>(P.tr_in) + ((int64_t)nb * 6 + meta_nbF(mt)) * 9 * N2,
+                  9 * N2 * sizeof(float));
   }
-  mv_load_state<N>(P, e, sO, T);
+  mv_load_state<N>(P, e, sO, T, QS);
   __syncthreads();
   // extrapolate q'(9), rho0, p0 along every line to its family's flux points
-  mv_extrap<N, T, 11, 0, 3>(sO, N3, sX, XF, XV, XD, o2);
+  mv_extrap<N, T, 11, 0, 3>(sO, QS, sX, XF, XV, XD, o2);
   __syncthreads();
-  // w' at every flux point, at the element faces the BR1 average with the other
-  // side's (the neighbour's trace about its own background, or the wall ghost)
+  // w' at every flux point: pairs of interior points (r, r + NINT/2) in the lanes
+  // of one paired evaluation, then the element faces one point at a time, with
+  // the BR1 average of this side's w' and the other side's (the neighbour's trace
+  // about its own background, or the wall ghost)
+  constexpr int NINT = 3 * (N - 1) * N2, NIP = NINT / 2, NIP_W = (NIP + 31) / 32 * 32;
 #pragma unroll 1
-  for (int t = tid; t < NF * 3 * N2; t += T) {
-    const int f = t / (3 * N2), r = t - f * (3 * N2), d = r / N2, L = r - d * N2;
+  for (int t = tid; t < NIP_W + 6 * N2; t += T) {
+    if (t < NIP_W) {
+      if (t >= NIP) continue;
+      float* Xp[2];
+      float2 q[11], w[8];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int r0 = t + h * NIP;
+        const int d = r0 / ((N - 1) * N2), r = r0 - d * ((N - 1) * N2);
+        const int f = 1 + r / N2, L = r - (f - 1) * N2;
+        Xp[h] = sX + f * XF + d * XD + L;
+#pragma unroll
+        for (int v = 0; v < 11; ++v) (h ? q[v].y : q[v].x) = Xp[h][v * XV];
+      }
+      mv_prim2(q, q[9], q[10], c, w);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        Xp[0][k * XV] = w[k].x;
+        Xp[1][k * XV] = w[k].y;
+      }
+      continue;
+    }
+    const int u = t - NIP_W, F = u / N2, L = u - F * N2, d = F >> 1, f = (F & 1) ? N : 0;
     float* X = sX + f * XF + d * XD + L;
     float q[11], w[8];
 #pragma unroll
     for (int v = 0; v < 11; ++v) q[v] = X[v * XV];
     mv_prim(q, q[9], q[10], c, w);
-    if (f == 0 || f == N) {
-      const int F = 2 * d + (f == N);
-      const int nb = sNb[F], mt = sMt[F];
-      float q2[9], r2 = q[9], p2 = q[10];
-      if (nb >= 0) {
-        int64_t nf;
-        int pn;
-        mv_partner<N>(nb, mt, L, nf, pn);
-        const float* Tn = reinterpret_cast<const float*>(P.tr_in) + nf * 9 * N2 + pn;
+    const int nb = sNb[F], mt = sMt[F];
+    float q2[9], r2 = q[9], p2 = q[10];
+    if (nb >= 0) {
+      int64_t nf;
+      int pn;
+      mv_partner<N>(nb, mt, L, nf, pn);
+      const float* Tn = reinterpret_cast<const float*>(P.tr_in) + nf * 9 * N2 + pn;
 #pragma unroll
-        for (int v = 0; v < 9; ++v) q2[v] = Tn[v * N2];
-        const int64_t gidx = e * 6 + F;
-        r2 += __ldg(P.bg_jump + (gidx * 2 + 0) * N2 + L);
-        p2 += __ldg(P.bg_jump + (gidx * 2 + 1) * N2 + L);
-      } else {
-        const float* Sp = Sfam + s32_index(N, d, f, 0, L);
-        const float Sx = __ldg(Sp), Sy = __ldg(Sp + N2), Sz = __ldg(Sp + 2 * N2);
-        const float im = rsqrtf(Sx * Sx + Sy * Sy + Sz * Sz), sg = (f == N) ? 1.0f : -1.0f;
-        wall_ghost<float>(q, sg * Sx * im, sg * Sy * im, sg * Sz * im, meta_bc(mt), q2);
-      }
-      float w2[8];
-      mv_prim(q2, r2, p2, c, w2);
-#pragma unroll
-      for (int k = 0; k < 8; ++k) w[k] = 0.5f * (w[k] + w2[k]);
+      for (int v = 0; v < 9; ++v) q2[v] = Tn[v * N2];
+      const int64_t gidx = e * 6 + F;
+      r2 += __ldg(P.bg_jump + (gidx * 2 + 0) * N2 + L);
+      p2 += __ldg(P.bg_jump + (gidx * 2 + 1) * N2 + L);
+    } else {
+      const float* Sp = Sfam + s32_index(N, d, f, 0, L);
+      const float Sx = __ldg(Sp), Sy = __ldg(Sp + N2), Sz = __ldg(Sp + 2 * N2);
+      const float im = rsqrtf(Sx * Sx + Sy * Sy + Sz * Sz), sg = (f == N) ? 1.0f : -1.0f;
+      wall_ghost<float>(q, sg * Sx * im, sg * Sy * im, sg * Sz * im, meta_bc(mt), q2);
     }
+    float w2[8];
+    mv_prim(q2, r2, p2, c, w2);
 #pragma unroll
-    for (int k = 0; k < 8; ++k) X[k * XV] = w[k];
+    for (int k = 0; k < 8; ++k) X[k * XV] = 0.5f * (w[k] + w2[k]);
   }
   __syncthreads();
   // |J| d w'_c / d x_j = sum_d D_d (S^d_j w'_c) at this thread's solution points,
@@ -435,7 +493,7 @@ __global__ void __launch_bounds__(MVDims<N>::T, MVDims<N>::minb(MVDims<N>::gbyte
     float* Ge = P.mgrad_out + e * MV_REC * N3 + n;
 #pragma unroll
     for (int k = 0; k < MV_REC; ++k) {
-      sO[k * N3 + n] = rec[k];
+      sO[k * QS + n] = rec[k];
       Ge[k * N3] = rec[k];
     }
   }
@@ -448,12 +506,13 @@ __global__ void __launch_bounds__(MVDims<N>::T, MVDims<N>::minb(MVDims<N>::gbyte
     int base, stride;
     line_geom<N>(d, L, base, stride);
     const int v0 = 2 * pr, v1 = v0 + 1 < MV_REC ? v0 + 1 : v0;
+    float2 x[N];
+    load_line<N>(sO + v0 * QS, sO + v1 * QS, base, stride, line_flip<N>(d, L), x);
     float2 s0 = make_float2(0.0f, 0.0f), s1 = make_float2(0.0f, 0.0f);
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-      const float2 x = make_float2(sO[v0 * N3 + base + i * stride], sO[v1 * N3 + base + i * stride]);
-      s0 = fma2(o2.E0[i], x, s0);
-      s1 = fma2(o2.EN[i], x, s1);
+      s0 = fma2(o2.E0[i], x[i], s0);
+      s1 = fma2(o2.EN[i], x[i], s1);
     }
     float* Tr = P.mgtr_out + (e * 6 + 2 * d) * MV_REC * N2 + L;
     Tr[v0 * N2] = s0.x;
@@ -473,7 +532,7 @@ __global__ void __launch_bounds__(MVDims<N>::T, MVDims<N>::minb(MVDims<N>::gbyte
 template <int N, bool KR, int D>
 __device__ __forceinline__ void mv_family_flux(const StageParams& P, const MViscCoef& c, int64_t e, const float* Sfam,
                                                float* X, const int* sNb, const int* sMt) {
-  constexpr int N2 = N * N, NF = N + 1, T = MVDims<N>::T, NQ = MVDims<N>::template V<KR>::NQ;
+  constexpr int N2 = N * N, NF = N + 1, T = MVDims<N>::TV, NQ = MVDims<N>::template V<KR>::NQ;
   constexpr int Q_R0 = 9, Q_P0 = 10, Q_REC = 11, Q_GT0 = Q_REC + MV_REC, Q_GS0 = Q_GT0 + 3, Q_X = Q_GS0 + 3;
 #pragma unroll 1
   for (int t = threadIdx.x; t < NF * N2; t += T) {
@@ -533,11 +592,11 @@ __device__ __forceinline__ void mv_family_flux(const StageParams& P, const MVisc
 // grad S0 and, with KR, x for kappa_r(r)) along the lines of direction d, the flux
 // at the family's points, its derivative along the lines added to the residual.
 template <int N, bool KR>
-__global__ void __launch_bounds__(MVDims<N>::T, MVDims<N>::minb(MVDims<N>::template V<KR>::bytes))
-    mvisc_kernel(const StageParams P, const Ops2 o2) {
+__global__ void __launch_bounds__(MVDims<N>::TV, MVDims<N>::minb(MVDims<N>::template V<KR>::bytes, MVDims<N>::TV))
+    mvisc_kernel(const StageParams P, const Ops2 o2, const MViscCoef c) {
   using MD = MVDims<N>;
   using MV = typename MD::template V<KR>;
-  constexpr int N2 = MD::N2, N3 = MD::N3, T = MD::T, NQ = MV::NQ;
+  constexpr int N2 = MD::N2, N3 = MD::N3, T = MD::TV, NQ = MV::NQ, QS = MD::QS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* sQ = reinterpret_cast<float*>(smem_raw) + MV::oQ;
   float* sX = reinterpret_cast<float*>(smem_raw) + MV::oX;
@@ -547,43 +606,56 @@ __global__ void __launch_bounds__(MVDims<N>::T, MVDims<N>::minb(MVDims<N>::templ
   const int64_t e = blockIdx.x;
   const int64_t n_e = P.n_e;
   const float* Sfam = reinterpret_cast<const float*>(P.Sfam) + e * (9 * N2 * (N + 1));
-  const MViscCoef c = mvisc_coef(P);
   if (tid < 6) {
     sNb[tid] = __ldg(P.nbr + e * 6 + tid);
     sMt[tid] = __ldg(P.meta + e * 6 + tid);
+  } else if (tid >= 32 && tid < 32 + 18) {
+    // L2 prefetch of what the face fluxes read from the neighbours: their traces
+    // of q', of the record and of the background gradients
+    const int k = (tid - 32) % 6, which = (tid - 32) / 6;
+    const int nb = __ldg(P.nbr + e * 6 + k), mt = __ldg(P.meta + e * 6 + k);
+    if (nb >= 0) {
+      const int64_t nf = (int64_t)nb * 6 + meta_nbF(mt);
+      if (which == 0)
+        l2_prefetch(reinterpret_cast<const float*>(P.tr_in) + nf * 9 * N2, 9 * N2 * sizeof(float));
+      else if (which == 1)
+        l2_prefetch(P.mgtr_in + nf * MV_REC * N2, MV_REC * N2 * sizeof(float));
+      else
+        l2_prefetch(P.bg_vtr + nf * 6 * N2, 6 * N2 * sizeof(float));
+    }
   }
-  mv_load_state<N>(P, e, sQ, T);
+  mv_load_state<N>(P, e, sQ, T, QS);
   for (int n = tid; n < N3; n += T) {
     const float* G = P.mgrad + e * MV_REC * N3 + n;
 #pragma unroll
-    for (int k = 0; k < MV_REC; ++k) sQ[(11 + k) * N3 + n] = __ldg(G + k * N3);
+    for (int k = 0; k < MV_REC; ++k) sQ[(11 + k) * QS + n] = __ldg(G + k * N3);
 #pragma unroll
-    for (int k = 0; k < 6; ++k) sQ[(11 + MV_REC + k) * N3 + n] = __ldg(P.bg_visc + (1 + k) * n_e * N3 + e * N3 + n);
+    for (int k = 0; k < 6; ++k) sQ[(11 + MV_REC + k) * QS + n] = __ldg(P.bg_visc + (1 + k) * n_e * N3 + e * N3 + n);
     if (KR) {
 #pragma unroll
       for (int k = 0; k < 3; ++k)
-        sQ[(11 + MV_REC + 6 + k) * N3 + n] = __ldg(reinterpret_cast<const float*>(P.X) + (e * 3 + k) * N3 + n);
+        sQ[(11 + MV_REC + 6 + k) * QS + n] = __ldg(reinterpret_cast<const float*>(P.X) + (e * 3 + k) * N3 + n);
     }
   }
   constexpr int OF = NQ * N2;
   __syncthreads();
-  mv_extrap<N, T, NQ, 0, 1>(sQ, N3, sX, OF, N2, 0, o2);
+  mv_extrap<N, T, NQ, 0, 1>(sQ, QS, sX, OF, N2, 0, o2);
   __syncthreads();
   mv_family_flux<N, KR, 0>(P, c, e, Sfam, sX, sNb, sMt);
   __syncthreads();
-  mv_deriv<N, T, 7, 0, false>(sX, OF, N2, sR, o2);
+  mv_deriv<N, T, 7, 0, false>(sX, OF, N2, sR, QS, o2);
   __syncthreads();
-  mv_extrap<N, T, NQ, 1, 2>(sQ, N3, sX, OF, N2, 0, o2);
+  mv_extrap<N, T, NQ, 1, 2>(sQ, QS, sX, OF, N2, 0, o2);
   __syncthreads();
   mv_family_flux<N, KR, 1>(P, c, e, Sfam, sX, sNb, sMt);
   __syncthreads();
-  mv_deriv<N, T, 7, 1, true>(sX, OF, N2, sR, o2);
+  mv_deriv<N, T, 7, 1, true>(sX, OF, N2, sR, QS, o2);
   __syncthreads();
-  mv_extrap<N, T, NQ, 2, 3>(sQ, N3, sX, OF, N2, 0, o2);
+  mv_extrap<N, T, NQ, 2, 3>(sQ, QS, sX, OF, N2, 0, o2);
   __syncthreads();
   mv_family_flux<N, KR, 2>(P, c, e, Sfam, sX, sNb, sMt);
   __syncthreads();
-  mv_deriv<N, T, 7, 2, true>(sX, OF, N2, sR, o2);
+  mv_deriv<N, T, 7, 2, true>(sX, OF, N2, sR, QS, o2);
   __syncthreads();
   const int64_t pl = n_e * N3;
   for (int n = tid; n < N3; n += T) {
@@ -591,7 +663,7 @@ __global__ void __launch_bounds__(MVDims<N>::T, MVDims<N>::minb(MVDims<N>::templ
     const float iJ = __ldg(reinterpret_cast<const float*>(P.invJ) + g);
 #pragma unroll
     for (int v = 0; v < 7; ++v) {
-      float r = sR[v * N3 + n] * iJ;            // + div(S F_vis)/|J|
+      float r = sR[v * QS + n] * iJ;            // + div(S F_vis)/|J|
       if (v == 3) r += __ldg(P.bg_visc + g);  // the background's viscous residual (energy)
       P.rvis_out[v * pl + g] = r;
     }
@@ -612,10 +684,11 @@ cudaError_t launch_mixed_visc_t(const StageParams& Pg, const StageParams& Pv, co
   if (err == cudaSuccess && vbytes > 48 * 1024)
     err = cudaFuncSetAttribute(kv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vbytes);
   if (err != cudaSuccess) return err;
-  mgrad_kernel<N><<<(unsigned)Pg.n_e, MD::T, MD::gbytes, s>>>(Pg, ops, o2);
+  const MViscCoef c = mvisc_coef(Pv);
+  mgrad_kernel<N><<<(unsigned)Pg.n_e, MD::T, MD::gbytes, s>>>(Pg, ops, o2, c);
   err = cudaGetLastError();
   if (err != cudaSuccess) return err;
-  kv<<<(unsigned)Pv.n_e, MD::T, vbytes, s>>>(Pv, o2);
+  kv<<<(unsigned)Pv.n_e, MD::TV, vbytes, s>>>(Pv, o2, c);
   return cudaGetLastError();
 }
 

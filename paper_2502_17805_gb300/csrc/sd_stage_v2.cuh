@@ -74,32 +74,6 @@ __device__ __forceinline__ float new_qprime(int v, double qo, float qo32, float 
   return qo32;
 }
 
-// Lines whose N values a thread reads with each pair of neighbours (i, i^1)
-// swapped: the lines along xi with (L mod 32) >= 16 (rows N floats apart, which
-// otherwise meet lines 16 further on in the same bank) and the lines along eta in
-// odd rows.  Modelled on the layout above, this removes about a sixth of the
-// bank conflicts of the line reads; the values reach the same registers.
-template <int N>
-__device__ __forceinline__ bool line_flip(int d, int L) {
-  return (d == 0 && (L & 31) >= 16) || (d == 1 && ((L / N) & 1));
-}
-
-// The N values of variables a (lane x) and b (lane y) along a line, read in the
-// order of line_flip and put back in order.
-template <int N>
-__device__ __forceinline__ void load_line(const float* a, const float* b, int base, int stride, bool flip,
-                                          float2* out) {
-  const int be = base + (flip ? stride : 0), bo = base - (flip ? stride : 0);
-  float2 x[N];
-#pragma unroll
-  for (int i = 0; i < N; ++i) {
-    const int o = ((i ^ 1) < N ? ((i & 1) ? bo : be) : base) + i * stride;
-    x[i] = make_float2(a[o], b[o]);
-  }
-#pragma unroll
-  for (int i = 0; i < N; ++i) out[i] = ((i ^ 1) < N && flip) ? x[i ^ 1] : x[i];
-}
-
 template <int N, bool EXACT, bool INCR>
 __device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops2& o2, const int64_t e,
                                               unsigned char* smem_raw) {
