@@ -154,3 +154,32 @@ def test_mixed_viscous_refusals():
     with pytest.raises(sdmhd.SDError) as exc:
         ff.background(visc, ff.empty_state())
     assert exc.value.code == 2
+
+
+VISC_R = dict(VISC, kappa_r=0.004, kappa_r1=0.012, kappa_r2=0.006)
+
+
+@pytest.mark.parametrize("N", [3, 6])
+def test_mixed_viscous_radius_dependent_kappa_r(N):
+    """kappa_r(r) = kappa_r + kappa_r1 r + kappa_r2 r^2 (reading V7) on the mixed path: the viscous
+    kernel's instance that extrapolates the coordinates to every flux point, on the stratified shell
+    with walls (the background's own viscous residual taken with the same kappa_r(r))."""
+    v, h = inputs.shell_mesh(3, 2)
+    gm, om = _pair(N, v, inputs.reorient(h, seed=5), geom=1, r_in=0.7, r_out=0.98,
+                   bc_in=sdref.BC_WALL_CONDUCTING, bc_out=sdref.BC_WALL_RADIAL)
+    gph, oph = _phys(powell=1, c_h=1.0, glm_alpha=0.5, gravity=1, GM=1.0, coriolis=1, omega=1.0, **VISC_R)
+    prm = [2.5, 0.7, 0.98, 1.0, 0.9, 1e-4, 1e-3]
+    q0, qb = om.state_init(oph, sdref.INIT_SHELL_POLYTROPE, prm, seed=6, background=True)
+    rng = np.random.default_rng(20 + N)
+    mom = rng.uniform(-1e-2, 1e-2, size=q0[1:4].shape) * q0[0]
+    q0[1:4] += mom
+    q0[4] += 0.5 * (mom ** 2).sum(axis=0) / q0[0]
+    bg = gm.background(gph, gm.to_device(qb))
+    R = gm.to_host(gm.residual(gph, gm.to_device(q0), prec=sdmhd.SD_FP32_MIXED, bg=bg))
+    Ro, _ = om.residual(oph, q0)
+    # the radius dependence is a visible part of this residual (0.7% of it at N = 6, 9% at N = 3),
+    # far above the 1e-5 tolerance
+    R1, _ = om.residual(sdref.Phys(**dict(vars(oph), kappa_r1=0.0, kappa_r2=0.0)), q0)
+    assert np.abs(Ro - R1).max() > 1e-3 * np.abs(Ro).max()
+    ok, err, ref = _strict(R, Ro, "kappa_r(r) shell N=%d" % N)
+    assert ok, (err, ref)
