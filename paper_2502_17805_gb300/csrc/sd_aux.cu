@@ -84,96 +84,147 @@ __device__ void tfi_d(const double* V, int geom, double u, double v, double w, d
   }
 }
 
-// Lagrange basis values and derivatives over the p1 nodes y at t
-__device__ void lagrange_1d(const double* y, int p1, double t, double* L, double* dL) {
-  for (int a = 0; a < p1; ++a) {
-    double v = 1.0, dv = 0.0;
-    for (int m = 0; m < p1; ++m) {
-      if (m == a) continue;
-      double prod = 1.0 / (y[a] - y[m]);
-      for (int s = 0; s < p1; ++s)
-        if (s != a && s != m) prod *= (t - y[s]) / (y[a] - y[s]);
-      dv += prod;
-      v *= (t - y[m]) / (y[a] - y[m]);
-    }
-    L[a] = v;
-    dL[a] = dv;
+// The 1D Lagrange bases of the map's p+1 nodes y (Chebyshev-Lobatto), tabulated
+// on the host: values A and derivatives B at the solution points (s) and the
+// flux points (f), row [point][node].
+struct GeoTab {
+  double y[kMaxGeoP1];
+  double As[kMaxN * kMaxGeoP1], Bs[kMaxN * kMaxGeoP1];
+  double Af[(kMaxN + 1) * kMaxGeoP1], Bf[(kMaxN + 1) * kMaxGeoP1];
+};
+
+// One tensor contraction of the map nodes, block-wide, its first two passes:
+//   out[c][k][j][i] = sum_{a,b,g} P[i][a] Q[j][b] R[k][g] X[c][g][b][a]
+// (c the coordinate; P, Q, R one 1D operator per direction, rows of p1 values).
+// Pass 1 T1[c][g][b][i] = sum_a P[i][a] X[c][g][b][a]; pass 2 T2[c][g][j][i] =
+// sum_b Q[j][b] T1[c][g][b][i].  The third pass (over g) is taken point by point
+// by geo_pass3 where the contraction is used.
+__device__ void geo_pass1(const double* X, const double* P, int ni, int p1, double* T1) {
+  const int n = 3 * p1 * p1 * ni;
+  for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    const int i = t % ni, r = t / ni;  // r = (c p1 + g) p1 + b
+    const double* x = X + r * p1;
+    const double* w = P + i * p1;
+    double s = 0.0;
+    for (int a = 0; a < p1; ++a) s += w[a] * x[a];
+    T1[t] = s;
   }
 }
 
-// dX/dxi, dX/deta, dX/dzeta and X at computational point (u, v, w)
-__device__ void map_jac(const double* Xp, const double* y, int p1, double u, double v, double w, double* J9, double* X) {
-  double Lu[5], dLu[5], Lv[5], dLv[5], Lw[5], dLw[5];
-  lagrange_1d(y, p1, u, Lu, dLu);
-  lagrange_1d(y, p1, v, Lv, dLv);
-  lagrange_1d(y, p1, w, Lw, dLw);
-  for (int i = 0; i < 9; ++i) J9[i] = 0.0;
-  if (X) X[0] = X[1] = X[2] = 0.0;
-  for (int c = 0; c < p1; ++c)
-    for (int b = 0; b < p1; ++b)
-      for (int a = 0; a < p1; ++a) {
-        const double* x = Xp + 3 * (a + p1 * (b + p1 * c));
-        const double w0 = dLu[a] * Lv[b] * Lw[c], w1 = Lu[a] * dLv[b] * Lw[c], w2 = Lu[a] * Lv[b] * dLw[c];
-        for (int d = 0; d < 3; ++d) {
-          J9[0 + d] += w0 * x[d];  // x_xi
-          J9[3 + d] += w1 * x[d];  // x_eta
-          J9[6 + d] += w2 * x[d];  // x_zeta
-        }
-        if (X) {
-          const double wv = Lu[a] * Lv[b] * Lw[c];
-          for (int d = 0; d < 3; ++d) X[d] += wv * x[d];
-        }
-      }
+__device__ void geo_pass2(const double* T1, const double* Q, int ni, int nj, int p1, double* T2) {
+  const int n = 3 * p1 * nj * ni;
+  for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    const int i = t % ni, j = (t / ni) % nj, cg = t / (ni * nj);  // cg = c p1 + g
+    const double* w = Q + j * p1;
+    const double* x = T1 + cg * p1 * ni + i;
+    double s = 0.0;
+    for (int b = 0; b < p1; ++b) s += w[b] * x[b * ni];
+    T2[t] = s;
+  }
 }
 
-__global__ void geometry_kernel(int N, int p, int geom, const double* __restrict__ corners, const Ops<double> ops,
+// the three coordinates of a contraction at point (i, j, k) from its T2
+__device__ __forceinline__ void geo_pass3(const double* T2, const double* R, int ni, int nj, int p1, int i, int j,
+                                          int k, double* out) {
+  const double* w = R + k * p1;
+  for (int c = 0; c < 3; ++c) {
+    const double* x = T2 + (c * p1 * nj + j) * ni + i;
+    double s = 0.0;
+    for (int g = 0; g < p1; ++g) s += w[g] * x[g * nj * ni];
+    out[c] = s;
+  }
+}
+
+// Shared memory of geometry_kernel, in doubles: the map nodes [3][p1^3], then
+// four (T1, T2) pairs of contraction buffers.
+__host__ __device__ inline int geo_t1_size(int N, int p1) { return 3 * p1 * p1 * (N + 1); }
+__host__ __device__ inline int geo_t2_size(int N, int p1) { return 3 * p1 * (N + 1) * (N + 1); }
+__host__ __device__ inline int geo_smem_doubles(int N, int p1) {
+  return 24 + 3 * p1 * p1 * p1 + 4 * (geo_t1_size(N, p1) + geo_t2_size(N, p1));
+}
+
+// Sum-factorised geometry of one element per CTA: the map nodes from the
+// transfinite map, then each derivative or value of the degree-p map at a
+// point set as three 1D contractions.  S^d = x_(d+1) x x_(d+2) at the flux points
+// of family d (flux points along d, solution points along the other two);
+// |J| = x_xi . (x_eta x x_zeta) and x at the solution points.
+__global__ void geometry_kernel(int N, int p, int geom, const double* __restrict__ corners, const GeoTab tab,
                                 double* Sfam64, double* invJ64, double* X64, float* Sfam32, float* invJ32, float* X32,
                                 int* flag) {
-  __shared__ double sV[24];
-  __shared__ double sXp[125 * 3];
-  __shared__ double y[5];
-  const int64_t e = blockIdx.x;
+  extern __shared__ double gsm[];
   const int p1 = p + 1, N2 = N * N, N3 = N2 * N, NF = N + 1;
+  double* sV = gsm;
+  double* sX = sV + 24;  // [c][g][b][a]
+  double* T1 = sX + 3 * p1 * p1 * p1;
+  const int t1 = geo_t1_size(N, p1), t2 = geo_t2_size(N, p1);
+  double* T2 = T1 + 4 * t1;
+  const int64_t e = blockIdx.x;
   for (int i = threadIdx.x; i < 24; i += blockDim.x) sV[i] = corners[e * 24 + i];
-  if (threadIdx.x < p1) y[threadIdx.x] = 0.5 * (1.0 - cos(M_PI * threadIdx.x / p));
   __syncthreads();
   for (int t = threadIdx.x; t < p1 * p1 * p1; t += blockDim.x) {
-    const int a = t % p1, b = (t / p1) % p1, c = t / (p1 * p1);
-    tfi_d(sV, geom, y[a], y[b], y[c], sXp + 3 * t);
+    const int a = t % p1, b = (t / p1) % p1, g = t / (p1 * p1);
+    double X[3];
+    tfi_d(sV, geom, tab.y[a], tab.y[b], tab.y[g], X);
+    for (int c = 0; c < 3; ++c) sX[c * p1 * p1 * p1 + t] = X[c];
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < 3 * NF * N2; t += blockDim.x) {
-    const int d = t / (NF * N2), r = t % (NF * N2), line = r / NF, f = r % NF, a = line % N, b = line / N;
-    double pt[3];
-    pt[d] = ops.xf[f];
-    pt[d == 0 ? 1 : 0] = ops.xs[a];
-    pt[d == 2 ? 1 : 2] = ops.xs[b];
-    double J9[9];
-    map_jac(sXp, y, p1, pt[0], pt[1], pt[2], J9, nullptr);
-    const double* t1 = J9 + 3 * ((d + 1) % 3);
-    const double* t2 = J9 + 3 * ((d + 2) % 3);
-    const double S[3] = {t1[1] * t2[2] - t1[2] * t2[1], t1[2] * t2[0] - t1[0] * t2[2], t1[0] * t2[1] - t1[1] * t2[0]};
-    for (int c = 0; c < 3; ++c) {
-      const int64_t idx = (((e * 3 + d) * 3 + c) * N2 + line) * NF + f;
-      Sfam64[idx] = S[c];
-      Sfam32[e * 9 * N2 * NF + s32_index(N, d, f, c, line)] = (float)S[c];
+  // family d: x_(d+1) and x_(d+2) at its points; operator per direction: the
+  // flux-point value along d, the solution-point derivative along the
+  // differentiated direction, the solution-point value along the third
+  for (int d = 0; d < 3; ++d) {
+    const int d1 = (d + 1) % 3, d2 = (d + 2) % 3;
+    const double* op[2][3];
+    int n[3];
+    for (int q = 0; q < 3; ++q) n[q] = q == d ? NF : N;
+    for (int h = 0; h < 2; ++h) {
+      const int dd = h == 0 ? d1 : d2;  // the direction differentiated
+      for (int q = 0; q < 3; ++q) op[h][q] = q == d ? tab.Af : (q == dd ? tab.Bs : tab.As);
     }
+    for (int h = 0; h < 2; ++h) geo_pass1(sX, op[h][0], n[0], p1, T1 + h * t1);
+    __syncthreads();
+    for (int h = 0; h < 2; ++h) geo_pass2(T1 + h * t1, op[h][1], n[0], n[1], p1, T2 + h * t2);
+    __syncthreads();
+    for (int t = threadIdx.x; t < NF * N2; t += blockDim.x) {
+      const int f = t % NF, line = t / NF, la = line % N, lb = line / N;
+      int ijk[3];
+      ijk[d] = f;
+      ijk[d == 0 ? 1 : 0] = la;
+      ijk[d == 2 ? 1 : 2] = lb;
+      double xa[3], xb[3];  // x_(d+1), x_(d+2)
+      geo_pass3(T2, op[0][2], n[0], n[1], p1, ijk[0], ijk[1], ijk[2], xa);
+      geo_pass3(T2 + t2, op[1][2], n[0], n[1], p1, ijk[0], ijk[1], ijk[2], xb);
+      const double S[3] = {xa[1] * xb[2] - xa[2] * xb[1], xa[2] * xb[0] - xa[0] * xb[2], xa[0] * xb[1] - xa[1] * xb[0]};
+      for (int c = 0; c < 3; ++c) {
+        const int64_t idx = (((e * 3 + d) * 3 + c) * N2 + line) * NF + f;
+        Sfam64[idx] = S[c];
+        Sfam32[e * 9 * N2 * NF + s32_index(N, d, f, c, line)] = (float)S[c];
+      }
+    }
+    __syncthreads();
   }
-  for (int n = threadIdx.x; n < N3; n += blockDim.x) {
-    const int i = n % N, j = (n / N) % N, k = n / N2;
-    double J9[9], X[3];
-    map_jac(sXp, y, p1, ops.xs[i], ops.xs[j], ops.xs[k], J9, X);
-    const double* xa = J9;
-    const double* xb = J9 + 3;
-    const double* xc = J9 + 6;
-    const double det = xa[0] * (xb[1] * xc[2] - xb[2] * xc[1]) + xa[1] * (xb[2] * xc[0] - xb[0] * xc[2]) +
-                       xa[2] * (xb[0] * xc[1] - xb[1] * xc[0]);
-    if (!(det > 0.0)) atomicExch(flag, 1);
-    invJ64[e * N3 + n] = 1.0 / det;
-    invJ32[e * N3 + n] = (float)(1.0 / det);
-    for (int c = 0; c < 3; ++c) {
-      X64[(e * 3 + c) * N3 + n] = X[c];
-      X32[(e * 3 + c) * N3 + n] = (float)X[c];
+  // solution points: x_xi, x_eta, x_zeta and x
+  {
+    for (int h = 0; h < 4; ++h) geo_pass1(sX, h == 0 ? tab.Bs : tab.As, N, p1, T1 + h * t1);
+    __syncthreads();
+    for (int h = 0; h < 4; ++h) geo_pass2(T1 + h * t1, h == 1 ? tab.Bs : tab.As, N, N, p1, T2 + h * t2);
+    __syncthreads();
+    for (int t = threadIdx.x; t < N3; t += blockDim.x) {
+      const int i = t % N, j = (t / N) % N, k = t / N2;
+      double J9[9], X[3];
+      for (int h = 0; h < 3; ++h) geo_pass3(T2 + h * t2, h == 2 ? tab.Bs : tab.As, N, N, p1, i, j, k, J9 + 3 * h);
+      geo_pass3(T2 + 3 * t2, tab.As, N, N, p1, i, j, k, X);
+      const double* xa = J9;
+      const double* xb = J9 + 3;
+      const double* xc = J9 + 6;
+      const double det = xa[0] * (xb[1] * xc[2] - xb[2] * xc[1]) + xa[1] * (xb[2] * xc[0] - xb[0] * xc[2]) +
+                         xa[2] * (xb[0] * xc[1] - xb[1] * xc[0]);
+      if (!(det > 0.0)) atomicExch(flag, 1);
+      invJ64[e * N3 + t] = 1.0 / det;
+      invJ32[e * N3 + t] = (float)(1.0 / det);
+      for (int c = 0; c < 3; ++c) {
+        X64[(e * 3 + c) * N3 + t] = X[c];
+        X32[(e * 3 + c) * N3 + t] = (float)X[c];
+      }
     }
   }
 }
@@ -204,10 +255,38 @@ __global__ void canonical_faces_kernel(int N, int64_t n_e, const int* __restrict
   }
 }
 
+// Lagrange basis l_a over nodes y (p1 of them) and its derivative, at t
+static void host_lagrange(const double* y, int p1, double t, double* L, double* dL) {
+  for (int a = 0; a < p1; ++a) {
+    double v = 1.0, dv = 0.0;
+    for (int m = 0; m < p1; ++m) {
+      if (m == a) continue;
+      double prod = 1.0 / (y[a] - y[m]);
+      for (int q = 0; q < p1; ++q)
+        if (q != a && q != m) prod *= (t - y[q]) / (y[a] - y[q]);
+      dv += prod;
+      v *= (t - y[m]) / (y[a] - y[m]);
+    }
+    L[a] = v;
+    dL[a] = dv;
+  }
+}
+
 cudaError_t launch_geometry(sd_mesh* m, const double* d_corners, int* d_flag, cudaStream_t s) {
   if (m->n_e == 0) return cudaSuccess;
-  geometry_kernel<<<(unsigned)m->n_e, 128, 0, s>>>(m->N, m->p, m->geom, d_corners, m->ops64, m->Sfam64, m->invJ64,
-                                                   m->X64, m->Sfam32, m->invJ32, m->X32, d_flag);
+  const int N = m->N, p = m->p, p1 = p + 1;
+  if (p1 > kMaxGeoP1) return cudaErrorInvalidValue;
+  GeoTab tab;
+  for (int a = 0; a < p1; ++a) tab.y[a] = 0.5 * (1.0 - cos(M_PI * a / p));
+  for (int i = 0; i < N; ++i) host_lagrange(tab.y, p1, m->ops64.xs[i], tab.As + i * p1, tab.Bs + i * p1);
+  for (int f = 0; f <= N; ++f) host_lagrange(tab.y, p1, m->ops64.xf[f], tab.Af + f * p1, tab.Bf + f * p1);
+  const size_t bytes = (size_t)geo_smem_doubles(N, p1) * sizeof(double);
+  if (bytes > 48 * 1024) {
+    cudaError_t err = cudaFuncSetAttribute(geometry_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (err != cudaSuccess) return err;
+  }
+  geometry_kernel<<<(unsigned)m->n_e, 128, bytes, s>>>(N, p, m->geom, d_corners, tab, m->Sfam64, m->invJ64, m->X64,
+                                                      m->Sfam32, m->invJ32, m->X32, d_flag);
   return cudaGetLastError();
 }
 

@@ -12,6 +12,8 @@
 namespace sd {
 
 constexpr int kMaxN = 8;
+// nodes per direction of the element map (degree floor(N/2) <= 4)
+constexpr int kMaxGeoP1 = kMaxN / 2 + 1;
 constexpr int kNV = 9;  // conserved variables
 
 // 1D operators of one order N (Sec. SD Method): solution points xs, flux points
