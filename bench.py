@@ -61,6 +61,7 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-rk53", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-viscous", action="store_true")
@@ -274,6 +275,38 @@ def time_steps(mesh, phys, q, work, prec, bg, steps, warmup, sampler=None, barri
     if barrier:
         barrier()
     return ms, prof, clocks
+
+
+def rk53_leg(mesh, phys, q0, bg, steps, warmup, cfl53=0.5):
+    """The five-stage third-order SSP method (SSPRK(5,3), SSP coefficient r = 2.65) on the FP32-mixed
+    path beside the three-stage method at the bench's CFL: the rate per step and the simulated time
+    per wall-clock second of each (sd_advance from the same state, device dt)."""
+    import torch
+
+    from paper_2502_17805_gb300 import sdmhd
+    out = {}
+    for name, scheme, cfl in (("ssp33", sdmhd.RK_SSP33, CFL), ("ssp53", sdmhd.RK_SSP53, cfl53)):
+        ph = sdmhd.Phys(**dict(vars(phys), rk_scheme=scheme))
+        q, work = q0.clone(), mesh.empty_state()
+        mesh.advance(ph, cfl, warmup, q, work, prec=sdmhd.SD_FP32_MIXED, bg=bg)
+        dts = torch.zeros(2 * steps, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        mesh.advance(ph, cfl, steps, q, work, prec=sdmhd.SD_FP32_MIXED, bg=bg, dt_out=dts)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        dt_mean = float(dts.view(steps, 2)[:, 0].mean())
+        out[name] = {"cfl": cfl, "stages": 3 if scheme == sdmhd.RK_SSP33 else 5, "steps": steps,
+                     "ms_per_step": ms / steps, "value": mesh.info["n_points"] * steps / (ms / 1e3),
+                     "dt_mean": dt_mean, "sim_time_per_s": dt_mean * steps / (ms / 1e3)}
+        del q, work
+    out["unit"] = UNIT
+    out["sim_time_ratio_ssp53_vs_ssp33"] = out["ssp53"]["sim_time_per_s"] / out["ssp33"]["sim_time_per_s"]
+    out["note"] = ("cfl 0.5 for the five-stage method: within r = 2.65 times the three-stage method's 0.2 "
+                   "(the same strong-stability bound per forward-Euler step)")
+    return out
 
 
 def time_e2e(mesh, phys, q_dev, work, bg, steps, warmup, chunks=16):
@@ -700,6 +733,10 @@ def run_ours(args):
                                                   "dq the change of the state over the steps"}}
         del qv, qm, bg_v
 
+    rk53 = None
+    if rank == 0 and world == 1 and not args.no_rk53:
+        rk53 = rk53_leg(mesh, phys, q0, bg, max(1, min(args.steps, 10)), min(args.warmup, 3))
+
     ms, ms64 = max_over_ranks([ms, ms64], device="cuda")
     value = whole_job_rate(n_pts, args.steps, world, ms)
     value64 = whole_job_rate(n_pts, k64, world, ms64)
@@ -727,6 +764,7 @@ def run_ours(args):
                  "stage_avg_ms": stage64_ms, "roofline": fp64_roofline(stage64_ms, clocks, n_pts)},
         "viscous_fp64": visc,
         "viscous_mixed": visc_mixed,
+        "ssprk53": rk53,
         "gpu_launches": int(prof["stage_launches"] + prof["trace_launches"] + prof["other_launches"]),
         "kernel_ms_per_step": {"stage": prof["stage_ms"] / args.steps, "trace_lambda": prof["trace_ms"] / args.steps,
                                "control": prof["other_ms"] / args.steps},

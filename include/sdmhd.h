@@ -59,6 +59,9 @@ typedef enum {
 
 typedef enum { SD_FP64 = 0, SD_FP32_MIXED = 1 } sd_precision;
 
+/* sd_phys.rk_scheme */
+enum { SD_RK_SSP33 = 0, SD_RK_SSP53 = 1 };
+
 /* Boundary conditions of unmatched faces (Sec. Problem Formulation and Boundary
  * Conditions).  Walls are impenetrable (U.n = 0); the inviscid ghost state
  * copies rho, p, psi and E, reflects U, and for the magnetic field either
@@ -115,7 +118,13 @@ typedef struct {
   int32_t powell;   /* 1: Powell terms -(div B)(B, U.B, U) in M */
   int32_t gravity;  /* 1: rho g and rho U.g in M */
   int32_t coriolis; /* 1: Coriolis force in M */
-  int32_t pad_;
+  /* Time integrator of sd_step and sd_advance: SD_RK_SSP33, the three-stage Shu-Osher SSP-RK3
+   * (0, the default), or SD_RK_SSP53, the five-stage third-order SSP method the paper names
+   * (Sec. SD Method, last paragraph: SSPRK(5,3)), with the coefficients of an optimal method of
+   * that class derived in the oracle (SSP coefficient r = 2.6506..., so cfl up to r times the
+   * three-stage method's for the same strong-stability bound).  sd_rk_stage and sd_step_packed
+   * run the three-stage stages only and refuse SD_RK_SSP53. */
+  int32_t rk_scheme;
   double farfield[9]; /* conserved ghost state of SD_BC_FARFIELD faces */
   /* Viscous, resistive and thermal fluxes F_vis (Sec. MHD Governing Equations; F = F_inv - F_vis),
    * with gradients of (U, T, S, B) by the BR1 scheme (Sec. SD Method), when viscous != 0 (both

@@ -1238,6 +1238,43 @@ int sdref_rk_stage(sdref_mesh* m, const sdref_phys* ph, int stage, double dt, co
   return 0;
 }
 
+/* One step of the five-stage third-order SSP method (Sec. SD Method, last paragraph: SSPRK(5,3);
+ * reading R23 -- Ruuth's table is not available, the coefficients are those derived by
+ * oracle/ssprk53.py: the optimal SSP coefficient r of explicit five-stage third-order methods,
+ * and of the family of methods attaining it the member of least principal error).  With c = 1/r
+ * and L the SD residual:
+ *   y1 = q,  y2 = y1 + c dt L(y1),  y3 = y2 + c dt L(y2),
+ *   y4 = (1 - a43) y1 + a43 (y3 + c dt L(y3)),  y5 = (1 - a54) y1 + a54 (y4 + c dt L(y4)),
+ *   q_out = a61 y2 + a62 y3 + a65 (y5 + c dt L(y5)). */
+int sdref_rk53_step(sdref_mesh* m, const sdref_phys* ph, double dt, const double* q, double* q_out) {
+  static const double r = 2.6506291914393882, a43 = 0.47329099097408517, a54 = 0.85150069298830050;
+  static const double a61 = 0.16614637524614647, a62 = 0.063691005655456475, a65 = 0.77016261909839706;
+  const double cdt = dt / r;
+  int64_t tot = 9LL * m->n_e * m->N * m->N * m->N;
+  double* R = (double*)malloc(sizeof(double) * tot);
+  double* y2 = (double*)malloc(sizeof(double) * tot);
+  double* y3 = (double*)malloc(sizeof(double) * tot);
+  double* y = (double*)malloc(sizeof(double) * tot);
+  int rc = 0;
+  if (!R || !y2 || !y3 || !y) { set_err("out of memory"); rc = 1; goto done; }
+  if ((rc = sdref_residual(m, ph, q, R, NULL, NULL))) goto done;
+  for (int64_t i = 0; i < tot; ++i) y2[i] = q[i] + cdt * R[i];
+  if ((rc = sdref_residual(m, ph, y2, R, NULL, NULL))) goto done;
+  for (int64_t i = 0; i < tot; ++i) y3[i] = y2[i] + cdt * R[i];
+  if ((rc = sdref_residual(m, ph, y3, R, NULL, NULL))) goto done;
+  for (int64_t i = 0; i < tot; ++i) y[i] = (1.0 - a43) * q[i] + a43 * (y3[i] + cdt * R[i]);
+  if ((rc = sdref_residual(m, ph, y, R, NULL, NULL))) goto done;
+  for (int64_t i = 0; i < tot; ++i) y[i] = (1.0 - a54) * q[i] + a54 * (y[i] + cdt * R[i]);
+  if ((rc = sdref_residual(m, ph, y, R, NULL, NULL))) goto done;
+  for (int64_t i = 0; i < tot; ++i) q_out[i] = a61 * y2[i] + a62 * y3[i] + a65 * (y[i] + cdt * R[i]);
+done:
+  free(R);
+  free(y2);
+  free(y3);
+  free(y);
+  return rc;
+}
+
 /* ------------------------------------------------------------------ */
 /* Diagnostics (Sec. Results: KE, E_B)                                 */
 /* ------------------------------------------------------------------ */

@@ -106,6 +106,9 @@ int sdref_residual_elements(sdref_mesh* m, const sdref_phys* ph, const double* q
 /* One Shu-Osher SSP-RK3 stage: q_out = a_s q_n + b_s (q_in + dt R(q_in)). */
 int sdref_rk_stage(sdref_mesh* m, const sdref_phys* ph, int stage, double dt, const double* q_n,
                    const double* q_in, double* q_out);
+/* One step of the five-stage third-order SSP method (SSPRK(5,3), coefficients of reading R23):
+ * q_out = q^(n+1) from q = q^n; q_out may not alias q. */
+int sdref_rk53_step(sdref_mesh* m, const sdref_phys* ph, double dt, const double* q, double* q_out);
 int sdref_diagnostics(sdref_mesh* m, const sdref_phys* ph, const double* q, sdref_diag* out);
 /* Initial state at the solution points; q_background (NULL allowed) receives the noise-free,
  * field-free hydrostatic background for SHELL_POLYTROPE. */

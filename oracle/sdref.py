@@ -96,6 +96,7 @@ def lib():
         L.sdref_spherical_averages.argtypes = [C.c_void_p, dp, C.c_int, C.c_int, dp]
         L.sdref_flux_balanced.argtypes = [dp, C.c_double, C.c_double, C.c_int, C.c_int, dp, dp, dp]
         L.sdref_rk_stage.argtypes = [C.c_void_p, C.POINTER(_Phys), C.c_int, C.c_double, dp, dp, dp]
+        L.sdref_rk53_step.argtypes = [C.c_void_p, C.POINTER(_Phys), C.c_double, dp, dp]
         L.sdref_diagnostics.argtypes = [C.c_void_p, C.POINTER(_Phys), dp, C.POINTER(_Diag)]
         L.sdref_state_init.argtypes = [C.c_void_p, C.POINTER(_Phys), C.c_int, dp, C.c_uint64, dp, dp]
         L.sdref_polytrope.argtypes = [C.c_double] * 8 + [dp, dp, dp]
@@ -287,6 +288,14 @@ class Mesh:
         q1 = self.rk_stage(phys, 0, dt, q, q)
         q2 = self.rk_stage(phys, 1, dt, q, q1)
         return self.rk_stage(phys, 2, dt, q, q2)
+
+    def rk53_step(self, phys: Phys, dt: float, q):
+        """one step of the five-stage third-order SSP method (SSPRK(5,3))"""
+        q = self._q(q)
+        out = np.zeros_like(q)
+        ph = phys._c()
+        _check(lib().sdref_rk53_step(self._h_ptr, C.byref(ph), dt, _dp(q), _dp(out)))
+        return out
 
     def diagnostics(self, phys: Phys, q) -> dict:
         q = self._q(q)

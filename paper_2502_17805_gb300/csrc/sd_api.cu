@@ -245,7 +245,7 @@ void free_mesh(sd_mesh* m) {
   void* ptrs[] = {m->own_faces, m->face_k, m->gface64, m->Sfam64, m->invJ64, m->X64, m->Sfam32, m->invJ32, m->X32,
                   m->nbr, m->meta,
                   m->tr64[0], m->tr64[1], m->tr32[0], m->tr32[1], m->dyn, m->diag_part, m->diag_out, m->divb,
-                  m->err, m->grad, m->gtr, m->grad32, m->gtr32, m->rvis32};
+                  m->err, m->grad, m->gtr, m->grad32, m->gtr32, m->rvis32, m->dyn_s, m->work2, m->wreg32};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (m->host_diag) cudaFreeHost(m->host_diag);
@@ -403,6 +403,8 @@ sd_status check_common(const sd_mesh* m, const sd_phys* ph, int prec, const sd_b
   if (!m) return fail(SD_ERR_INVALID_ARGUMENT, "mesh is NULL");
   if (!ph) return fail(SD_ERR_INVALID_ARGUMENT, "phys is NULL");
   if (prec != SD_FP64 && prec != SD_FP32_MIXED) return fail(SD_ERR_INVALID_ARGUMENT, "unknown precision");
+  if (ph->rk_scheme != SD_RK_SSP33 && ph->rk_scheme != SD_RK_SSP53)
+    return fail(SD_ERR_INVALID_ARGUMENT, "rk_scheme must be SD_RK_SSP33 or SD_RK_SSP53");
   if (!(ph->gamma > 1.0)) return fail(SD_ERR_INVALID_ARGUMENT, "gamma must exceed 1");
   if (ph->viscous) {
     if (prec == SD_FP32_MIXED) {
@@ -1056,6 +1058,8 @@ sd_status sd_rk_stage(const sd_mesh* m, const sd_phys* ph, sd_precision prec, in
   sd_status st = check_common(m, ph, prec, bg);
   if (st != SD_OK) return st;
   if (stage < 0 || stage > 2) return fail(SD_ERR_INVALID_ARGUMENT, "stage must be 0, 1 or 2");
+  if (ph->rk_scheme != SD_RK_SSP33)
+    return fail(SD_ERR_UNSUPPORTED, "sd_rk_stage runs the stages of the three-stage method (rk_scheme SD_RK_SSP33)");
   if ((st = check_state_ptr(q_in, "q_in")) != SD_OK) return st;
   if ((st = check_state_ptr(q_out, "q_out")) != SD_OK) return st;
   if (stage > 0 && (st = check_state_ptr(q_n, "q_n")) != SD_OK) return st;
@@ -1063,6 +1067,166 @@ sd_status sd_rk_stage(const sd_mesh* m, const sd_phys* ph, sd_precision prec, in
   DeviceGuard g(m->device);
   return rk_stage_impl(const_cast<sd_mesh*>(m), ph, prec, stage, dt, nullptr, stage > 0 ? q_n : q_in, q_in, q_out, bg,
                        stage < 2, (cudaStream_t)stream);
+}
+
+// The five-stage third-order SSP method (sd_phys.rk_scheme = SD_RK_SSP53; Sec. SD Method, last
+// paragraph: SSPRK(5,3)): an optimal method of that class (SSP coefficient r), the member of least
+// principal error of the family that attains r.  With c = 1/r and L the SD residual:
+//   y2 = y1 + c dt L(y1),  y3 = y2 + c dt L(y2),  y4 = (1 - a43) y1 + a43 (y3 + c dt L(y3)),
+//   y5 = (1 - a54) y1 + a54 (y4 + c dt L(y4)),  q^(n+1) = a61 y2 + a62 y3 + a65 (y5 + c dt L(y5)).
+namespace ssp53 {
+constexpr double r = 2.6506291914393882, a43 = 0.47329099097408517, a54 = 0.85150069298830050;
+constexpr double a61 = 0.16614637524614647, a62 = 0.063691005655456475, a65 = 0.77016261909839706;
+constexpr double c = 1.0 / r;
+}  // namespace ssp53
+
+// n_steps of the five-stage method, device-side step control as in advance_impl.
+// FP64: y2 -> work, y3 -> work2, then work = a61 y2 + a62 y3 and y4, y5 in place in work2;
+// every FP64 stage runs with dt / r (the step-control kernel's second pair), so each stage
+// is q_out = a q_n + b (q_in + (dt/r) R) with the coefficients above.  FP32-mixed, increment
+// form (D = y - q^n in FP32): stage 2 also leaves W = a61 D2 + a62 D3 in a second register,
+// and the last stage adds its D + t to q^n + W (formed in work, FP64).
+static sd_status advance53_impl(sd_mesh* mm, const sd_phys* ph, sd_precision prec, double cfl, int32_t n_steps,
+                                double* q, double* work, const sd_background* bg, double* dt_out, cudaStream_t s) {
+  using namespace ssp53;
+  const bool mixed = prec == SD_FP32_MIXED;
+  const size_t ne = (size_t)std::max<int64_t>(mm->n_e, 1);
+  if (!mm->dyn_s) {
+    SD_CUDA(cudaMalloc((void**)&mm->dyn_s, 2 * sizeof(double)));
+    mm->device_bytes += 2 * sizeof(double);
+  }
+  if (!mixed && !mm->work2) {
+    const size_t bytes = 9 * ne * (size_t)mm->stride * sizeof(double);
+    SD_CUDA(cudaMalloc((void**)&mm->work2, bytes));
+    mm->device_bytes += (int64_t)bytes;
+  }
+  if (mixed && !mm->wreg32) {
+    const size_t bytes = 9 * ne * (size_t)bg->dstride * sizeof(float);
+    SD_CUDA(cudaMalloc((void**)&mm->wreg32, bytes));
+    mm->device_bytes += (int64_t)bytes;
+  }
+  auto stage_params = [&]() {
+    sd::StageParams S = base_params(mm, ph, prec);
+    if (bg) {
+      S.bg = bg->rec;
+      S.bg_jump = bg->jump;
+    }
+    S.mode = sd::MODE_RK;
+    S.dyn = mixed ? mm->dyn : mm->dyn_s;
+    if (mixed) {
+      S.dreg = bg->dreg;
+      S.dstride = bg->dstride;
+      S.incr = 1;
+      S.qp_in = bg->qp;
+    }
+    return S;
+  };
+  auto run = [&](sd::StageParams& S) -> cudaError_t {
+    cudaError_t err = prepare_viscous(mm, S, s, prec, bg);
+    if (err != cudaSuccess) return err;
+    ProfScope ps(mm, PROF_STAGE, s);
+    return sd::launch_stage(mm, prec, S, s);
+  };
+  int a = 0, b = 1;
+  for (int32_t k = 0; k < n_steps; ++k) {
+    const bool last = k == n_steps - 1;
+    if (k == 0) {  // lambda_max of q fused with the traces of q (mixed: and q' of q)
+      sd::StageParams P = base_params(mm, ph, prec);
+      if (bg) {
+        P.bg = bg->rec;
+        P.bg_jump = bg->jump;
+      }
+      SD_CUDA(cudaMemsetAsync(mm->dyn + 4, 0, sd::LAM_SLOTS * sizeof(double), s));
+      P.mode = sd::MODE_RESIDUAL;
+      P.q_in = q;
+      P.tr_out = trace_buf(mm, prec, a);
+      P.lam_max = reinterpret_cast<unsigned long long*>(mm->dyn + 4);
+      P.lam_nslot = sd::LAM_SLOTS;
+      if (mixed) {
+        P.qp_out = bg->qp;
+        P.dstride = bg->dstride;
+      }
+      ProfScope ps(mm, PROF_TRACE, s);
+      SD_CUDA(sd::launch_traces(mm, prec, P, s));
+    }
+    {
+      ProfScope ps(mm, PROF_OTHER, s);
+      SD_CUDA(sd::launch_step_control(mm, cfl, ph->c_h, dt_out ? dt_out + 2 * (int64_t)k : nullptr, s, mm->dyn_s, c));
+    }
+    // stage 1: y2 = q + c dt L(q)
+    sd::StageParams S = stage_params();
+    S.q_in = S.q_n = q;
+    S.out = work;
+    S.rk_a = 0.0;
+    S.rk_b = mixed ? c : 1.0;
+    S.tr_in = trace_buf(mm, prec, a);
+    S.tr_out = trace_buf(mm, prec, b);
+    if (mixed) S.lsr_write = 1;
+    SD_CUDA(run(S));
+    // stage 2: y3 = y2 + c dt L(y2) (mixed: and W = a61 D2 + a62 D3)
+    S = stage_params();
+    S.q_in = mixed ? q : work;
+    S.q_n = q;
+    S.out = mixed ? work : mm->work2;
+    S.rk_a = 0.0;
+    S.rk_b = mixed ? c : 1.0;
+    S.tr_in = trace_buf(mm, prec, b);
+    S.tr_out = trace_buf(mm, prec, a);
+    if (mixed) {
+      S.lsr_read = 1;
+      S.lsr_write = 2;
+      S.wreg = mm->wreg32;
+      S.w_old = (float)a61;
+      S.w_new = (float)a62;
+    }
+    SD_CUDA(run(S));
+    if (!mixed) {  // work = W = a61 y2 + a62 y3
+      ProfScope ps(mm, PROF_OTHER, s);
+      SD_CUDA(sd::launch_axpby_f64(work, a61, work, a62, mm->work2, 9 * mm->n_e * mm->stride, s));
+    }
+    // stages 3 and 4: y4 = (1 - a43) q + a43 (y3 + c dt L(y3)), y5 likewise with a54
+    for (int st = 3; st <= 4; ++st) {
+      const double al = st == 3 ? a43 : a54;
+      S = stage_params();
+      S.q_in = mixed ? q : mm->work2;
+      S.q_n = q;
+      S.out = mixed ? work : mm->work2;
+      S.rk_a = 1.0 - al;
+      S.rk_b = mixed ? al * c : al;
+      S.tr_in = trace_buf(mm, prec, st == 3 ? a : b);
+      S.tr_out = trace_buf(mm, prec, st == 3 ? b : a);
+      if (mixed) {
+        S.lsr_read = 1;
+        S.lsr_write = 2;
+      }
+      SD_CUDA(run(S));
+    }
+    // stage 5: q = a61 y2 + a62 y3 + a65 (y5 + c dt L(y5)); with another step to come it
+    // also writes the traces and lambda_max of the new q (mixed: and its q')
+    if (mixed) {
+      ProfScope ps(mm, PROF_OTHER, s);
+      SD_CUDA(sd::launch_add_reg_f64(mm, work, q, mm->wreg32, bg->dstride, s));
+    }
+    S = stage_params();
+    S.q_in = mixed ? work : mm->work2;
+    S.q_n = mixed ? q : work;
+    S.out = q;
+    S.rk_a = mixed ? 1.0 - a65 : 1.0;
+    S.rk_b = mixed ? a65 * c : a65;
+    S.tr_in = trace_buf(mm, prec, a);
+    S.tr_out = last ? nullptr : trace_buf(mm, prec, b);
+    S.lam_max = last ? nullptr : reinterpret_cast<unsigned long long*>(mm->dyn + 4);
+    S.lam_nslot = sd::LAM_SLOTS;
+    if (mixed) {
+      S.lsr_read = 1;
+      S.lsr_write = 0;
+      S.qp_out = last ? nullptr : bg->qp;
+    }
+    SD_CUDA(run(S));
+    std::swap(a, b);
+  }
+  mm->tr_tag[0] = mm->tr_tag[1] = nullptr;
+  return SD_OK;
 }
 
 // n_steps SSP-RK3 steps with device-side step control.  Trace buffer `a` holds
@@ -1073,6 +1237,7 @@ sd_status sd_rk_stage(const sd_mesh* m, const sd_phys* ph, sd_precision prec, in
 // when another step follows); the buffers then swap roles.
 static sd_status advance_impl(sd_mesh* mm, const sd_phys* ph, sd_precision prec, double cfl, int32_t n_steps,
                               double* q, double* work, const sd_background* bg, double* dt_out, cudaStream_t s) {
+  if (ph->rk_scheme == SD_RK_SSP53) return advance53_impl(mm, ph, prec, cfl, n_steps, q, work, bg, dt_out, s);
   const bool mixed = prec == SD_FP32_MIXED;
   auto stage_params = [&]() {
     sd::StageParams S = base_params(mm, ph, prec);

@@ -1,5 +1,6 @@
 // sd_aux.cu -- geometry, initial state, diagnostics, background and step-control
 // kernels of the SD MHD+GLM library.
+#include <algorithm>
 #include <limits.h>
 #include <math.h>
 
@@ -760,7 +761,8 @@ cudaError_t launch_bg_finish(const sd_mesh* m, double gamma, const double* R0, f
 // (compared as bit patterns, as the atomics wrote them), which are cleared for
 // the next reduction; then dt and c_h.
 __global__ void __launch_bounds__(LAM_SLOTS) step_control_kernel(double* dyn, double cfl, double dx_min,
-                                                                 double ch_fixed, double* dt_out) {
+                                                                 double ch_fixed, double* dt_out, double* dyn_s,
+                                                                 double dt_scale) {
   __shared__ unsigned long long part[LAM_SLOTS / 32];
   unsigned long long* slots = reinterpret_cast<unsigned long long*>(dyn + 4);
   unsigned long long b = slots[threadIdx.x];
@@ -780,15 +782,55 @@ __global__ void __launch_bounds__(LAM_SLOTS) step_control_kernel(double* dyn, do
   dyn[0] = dt;
   dyn[1] = ch;
   dyn[2] = lam;
+  if (dyn_s) {  // the pair the FP64 stages of the five-stage method read: (dt / r, c_h)
+    dyn_s[0] = dt * dt_scale;
+    dyn_s[1] = ch;
+  }
   if (dt_out) {
     dt_out[0] = dt;
     dt_out[1] = ch;
   }
 }
 
-cudaError_t launch_step_control(const sd_mesh* m, double cfl, double c_h_fixed, double* dt_out, cudaStream_t s) {
+cudaError_t launch_step_control(const sd_mesh* m, double cfl, double c_h_fixed, double* dt_out, cudaStream_t s,
+                                double* dyn_s, double dt_scale) {
   const double dx_min = m->h_min * (m->ops64.xs[1] - m->ops64.xs[0]);
-  step_control_kernel<<<1, LAM_SLOTS, 0, s>>>(m->dyn, cfl, dx_min, c_h_fixed, dt_out);
+  step_control_kernel<<<1, LAM_SLOTS, 0, s>>>(m->dyn, cfl, dx_min, c_h_fixed, dt_out, dyn_s, dt_scale);
+  return cudaGetLastError();
+}
+
+// out = a x + b y over n FP64 values (the five-stage method's W = a61 y2 + a62 y3)
+__global__ void axpby_f64_kernel(double* out, double a, const double* __restrict__ x, double b,
+                                 const double* __restrict__ y, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = a * x[i] + b * y[i];
+}
+
+cudaError_t launch_axpby_f64(double* out, double a, const double* x, double b, const double* y, int64_t n,
+                             cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const int64_t blocks = std::min<int64_t>((n + 255) / 256, 152 * 16);
+  axpby_f64_kernel<<<(unsigned)blocks, 256, 0, s>>>(out, a, x, b, y, n);
+  return cudaGetLastError();
+}
+
+// out = q + W for an FP64 state q ([9][n_e stride]) and an FP32 register W ([9][n_e dstride]),
+// the padding of q copied
+__global__ void add_reg_f64_kernel(double* out, const double* __restrict__ q, const float* __restrict__ w,
+                                   int64_t n_e, int N3, int64_t stride, int64_t dstride) {
+  const int64_t per_v = n_e * stride, n = 9 * per_v;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = i / per_v, r = i - v * per_v, e = r / stride, k = r - e * stride;
+    out[i] = k < N3 ? q[i] + (double)w[(v * n_e + e) * dstride + k] : q[i];
+  }
+}
+
+cudaError_t launch_add_reg_f64(const sd_mesh* m, double* out, const double* q, const float* w, int64_t dstride,
+                               cudaStream_t s) {
+  const int64_t n = 9 * m->n_e * m->stride;
+  if (n == 0) return cudaSuccess;
+  const int64_t blocks = std::min<int64_t>((n + 255) / 256, 152 * 16);
+  add_reg_f64_kernel<<<(unsigned)blocks, 256, 0, s>>>(out, q, w, m->n_e, m->N * m->N * m->N, m->stride, dstride);
   return cudaGetLastError();
 }
 

@@ -106,6 +106,10 @@ struct StageParams {
   float* dreg;
   int64_t dstride;
   int lsr_read, lsr_write;
+  // five-stage method, increment form: a stage that advances D in place (lsr_write 2)
+  // also stores W = w_old D + w_new (D + t) here, [9][n_e * dstride] (nullptr: not)
+  float* wreg;
+  float w_old, w_new;
   // increment form (FP32-mixed sd_step): q_in is q^n in every stage and the stage's
   // state is q^n + D; stages with lsr_write only advance D, the last writes q^n + D + t
   int incr;
@@ -190,6 +194,11 @@ struct sd_mesh {
   float* grad32;            // viscous FP32-mixed path, allocated on first use: perturbation gradients,
   float* gtr32;             //   their face traces
   float* rvis32;            //   and the viscous residual [7][n_e N^3]
+  // five-stage time integrator (sd_phys.rk_scheme), allocated on first use: (dt/r, c_h)
+  // for the FP64 stages, a second FP64 stage state, the FP32 register W of the mixed path
+  double* dyn_s;
+  double* work2;
+  float* wreg32;
   int has_farfield;         // the mesh has far-field boundary faces
   int64_t device_bytes;
   sd::Ops<double> ops64;
@@ -259,5 +268,10 @@ cudaError_t launch_bg_prepare(const sd_mesh* m, double gamma, double inv_gm1, co
                               float* rec, cudaStream_t s);
 cudaError_t launch_bg_finish(const sd_mesh* m, double gamma, const double* R0, float* rec, float* jump,
                              const double* tr, cudaStream_t s);
-cudaError_t launch_step_control(const sd_mesh* m, double cfl, double c_h_fixed, double* dt_out, cudaStream_t s);
+cudaError_t launch_step_control(const sd_mesh* m, double cfl, double c_h_fixed, double* dt_out, cudaStream_t s,
+                                double* dyn_s = nullptr, double dt_scale = 1.0);
+cudaError_t launch_axpby_f64(double* out, double a, const double* x, double b, const double* y, int64_t n,
+                             cudaStream_t s);
+cudaError_t launch_add_reg_f64(const sd_mesh* m, double* out, const double* q, const float* w, int64_t dstride,
+                               cudaStream_t s);
 }  // namespace sd

@@ -172,6 +172,8 @@ sd_status sd_step_packed(sd_packer* pk, int32_t n, const sd_step_req* reqs, void
       return pk_fail(SD_ERR_INVALID_ARGUMENT, where + "q, work, traces must be distinct 16-byte aligned buffers, dyn non-NULL");
     if (!(r.cfl > 0.0)) return pk_fail(SD_ERR_INVALID_ARGUMENT, where + "cfl must be positive");
     if (r.phys.viscous) return pk_fail(SD_ERR_UNSUPPORTED, where + "sd_step_packed takes no viscous fluxes (sd_step runs them)");
+    if (r.phys.rk_scheme != SD_RK_SSP33)
+      return pk_fail(SD_ERR_UNSUPPORTED, where + "sd_step_packed runs the three-stage method (rk_scheme SD_RK_SSP33)");
     if (r.flags & ~(SD_REQ_KEEP_TRACES | SD_REQ_TRACES_READY))
       return pk_fail(SD_ERR_INVALID_ARGUMENT, where + "unknown flags");
   }

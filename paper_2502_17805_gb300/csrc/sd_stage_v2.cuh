@@ -507,6 +507,7 @@ __device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops2& 
       // t = -a D + b dt R; intermediate stages only advance D <- D + t (FP32),
       // the last writes q^n + (D + t) in FP64
       const int64_t gd = e * DV::DSTRIDE + n, dplane = n_e * DV::DSTRIDE;
+      float* const wreg = P.wreg;  // five-stage method: W = w_old D + w_new (D + t) beside D
       float qe[9];
 #pragma unroll
       for (int v = 0; v < 9; ++v) {
@@ -514,6 +515,7 @@ __device__ __forceinline__ void stage_body_v2(const StageParams& P, const Ops2& 
         const float t = fmaf(-rka, Dv, bdt * Rv[v]);
         if (lsr_write) {
           P.dreg[v * dplane + gd] = Dv + t;
+          if (wreg) wreg[v * dplane + gd] = fmaf(P.w_old, Dv, P.w_new * (Dv + t));
           sQ[v * N3 + n] = q[v] + t;
         } else {
           const double qo = qin9[v] + f32_to_f64(Dv + t);

@@ -19,6 +19,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libsdmhd.so")
 
 SD_FP64, SD_FP32_MIXED = 0, 1
+# time integrators of sd_step / sd_advance (sd_phys.rk_scheme)
+RK_SSP33, RK_SSP53 = 0, 1
 BC_PERIODIC, BC_WALL_CONDUCTING, BC_WALL_RADIAL, BC_FARFIELD = 0, 1, 2, 3
 INIT_UNIFORM, INIT_ALFVEN, INIT_SHELL_POLYTROPE, INIT_DIVB_PULSE, INIT_SHELL_FLUX_BALANCED = 0, 1, 2, 3, 4
 STATUS = {0: "SD_OK", 1: "SD_ERR_INVALID_ARGUMENT", 2: "SD_ERR_UNSUPPORTED", 3: "SD_ERR_MESH_TOPOLOGY",
@@ -49,7 +51,7 @@ class MeshDesc(C.Structure):
 class PhysC(C.Structure):
     _fields_ = [("gamma", C.c_double), ("GM", C.c_double), ("omega", C.c_double), ("glm_alpha", C.c_double),
                 ("c_h", C.c_double), ("powell", C.c_int32), ("gravity", C.c_int32), ("coriolis", C.c_int32),
-                ("pad_", C.c_int32), ("farfield", C.c_double * 9), ("mu", C.c_double), ("eta", C.c_double),
+                ("rk_scheme", C.c_int32), ("farfield", C.c_double * 9), ("mu", C.c_double), ("eta", C.c_double),
                 ("kappa", C.c_double), ("kappa_r", C.c_double), ("R_gas", C.c_double), ("viscous", C.c_int32),
                 ("pad2_", C.c_int32), ("q_bottom", C.c_double), ("T_top", C.c_double), ("visc_walls", C.c_int32),
                 ("pad3_", C.c_int32), ("kappa_r1", C.c_double), ("kappa_r2", C.c_double)]
@@ -112,6 +114,8 @@ class Phys:
     # radiative diffusivity kappa_r(r) = kappa_r + kappa_r1 r + kappa_r2 r^2
     kappa_r1: float = 0.0
     kappa_r2: float = 0.0
+    # time integrator of step / advance: RK_SSP33 (three-stage SSP-RK3) or RK_SSP53 (SSPRK(5,3))
+    rk_scheme: int = RK_SSP33
 
     def c(self) -> PhysC:
         p = PhysC()
@@ -123,6 +127,7 @@ class Phys:
         p.viscous = int(self.viscous)
         p.q_bottom, p.T_top, p.visc_walls = self.q_bottom, self.T_top, int(self.visc_walls)
         p.kappa_r1, p.kappa_r2 = self.kappa_r1, self.kappa_r2
+        p.rk_scheme = int(self.rk_scheme)
         return p
 
 
