@@ -280,6 +280,10 @@ sd_status sd_rk_stage(const sd_mesh* mesh, const sd_phys* phys, sd_precision pre
  * stage reads q' and the background's FP32 register D = q^(s) - q^n, and only
  * the last stage reads and writes q (work is then not written).  No host
  * synchronisation.
+ * With phys->rk_scheme = SD_RK_SSP53 the step is the five-stage SSPRK(5,3) (Sec. SD
+ * Method) instead: SD_FP64 then also uses a second stage state, and SD_FP32_MIXED a
+ * second FP32 register, both allocated by the mesh on first use, and work holds
+ * q^n plus that register's combination of stages 2 and 3 for the last stage.
  * Asynchronous. */
 sd_status sd_step(const sd_mesh* mesh, const sd_phys* phys, sd_precision prec, double cfl, double* q, double* work,
                   const sd_background* bg, double* dt_out, void* stream);
