@@ -158,3 +158,21 @@ def test_refusals():
     with pytest.raises(sdmhd.SDError) as exc:
         gm.step(bad, 0.2, q, gm.empty_state())
     assert exc.value.code == 1
+
+
+def test_fp64_viscous_walls_steps_follow_the_oracle():
+    """The FP64 path with the viscous fluxes and the wall conditions of the viscous path under the
+    five-stage method (its stages run with dt / r)."""
+    N = 4
+    v, h = inputs.shell_mesh(2, 2)
+    gm, om = _pair(N, v, inputs.reorient(h, seed=7), geom=1, r_in=0.7, r_out=0.98,
+                   bc_in=sdref.BC_WALL_CONDUCTING, bc_out=sdref.BC_WALL_RADIAL)
+    walls = dict(viscous=1, mu=0.03, eta=0.02, kappa=0.01, kappa_r=0.015, R_gas=0.9, visc_walls=1,
+                 q_bottom=0.05, T_top=0.6)
+    gph, oph = _phys(powell=1, c_h=0.0, glm_alpha=0.5, gravity=1, GM=1.0, coriolis=1, omega=1.0, **walls)
+    prm = [2.0, 0.7, 0.98, 1.0, 0.9, 1e-4, 1e-3]
+    q0 = om.state_init(oph, sdref.INIT_SHELL_POLYTROPE, prm, seed=8)
+    g, o = _follow(gm, om, gph, oph, q0, 2, 0.1)
+    err = np.abs(g - o).reshape(9, -1).max(axis=1) / np.abs(o - q0).reshape(9, -1).max(axis=1)
+    print("ssp53 fp64 viscous walls: max|g-o| / max|change| = %s" % err)
+    assert err.max() < 1e-9, err

@@ -299,3 +299,20 @@ def test_aged_policy_moves_a_long_waiting_request_forward():
     srv._now = 9.0
     assert srv.choose([big, run(1, 800, 2, 5.0)]) == [1]  # 1600 + 5000 < 9000 + 0
     assert srv.choose([big, run(1, 800, 2, 8.0)]) == [0]  # 1600 + 8000 > 9000: the early one first
+
+
+@gpu
+def test_five_stage_method_is_refused_in_packed_steps(torch_dev):
+    """sd_step_packed runs the three-stage stages; a request asking for SSPRK(5,3) is refused
+    (sd_step runs it)."""
+    import dataclasses
+
+    from paper_2502_17805_gb300 import sdmhd
+    srv = serve.Server(hbm_budget_bytes=1 << 34, max_running=4)
+    req = serve.Request(rid=0, nz=2, nr=1, N=4, n_rho=2.0, omega=1.0, seed=5, steps=1, arrival=0.0)
+    run = serve._Running(req, srv.mesh(req.nz, req.nr, req.N))
+    packed = list(run.as_packed())
+    packed[1] = dataclasses.replace(packed[1], rk_scheme=sdmhd.RK_SSP53)
+    with pytest.raises(sdmhd.SDError) as exc:
+        srv.packer.step([tuple(packed)])
+    assert exc.value.code == 2 and "three-stage" in str(exc.value)
