@@ -67,6 +67,9 @@ def parse():
     ap.add_argument("--no-viscous", action="store_true")
     ap.add_argument("--no-largest", action="store_true")
     ap.add_argument("--accuracy-steps", type=int, default=200)
+    ap.add_argument("--accuracy-oracle-steps", type=int, default=0,
+                    help="steps of the FP32-mixed path against the FP64 oracle itself on the workload's shell "
+                         "(off by default: the oracle takes about 0.9 s per step of the 41,472-element shell)")
     ap.add_argument("--largest-steps", type=int, default=50)
     ap.add_argument("--serve-requests", type=int, default=64)
     ap.add_argument("--serve-budget-gb", type=float, default=24.0)
@@ -541,6 +544,50 @@ def accuracy_report(steps: int = 20):
             "max_divb_mixed": dm["max_divb"], "max_divb_fp64": d64["max_divb"]}
 
 
+def accuracy_vs_oracle_shell(wl_key: str, steps: int):
+    """The FP32-mixed path against the FP64 oracle itself (OpenMP over elements on the host cores)
+    over `steps` SSP-RK3 steps of a workload's shell from the oracle's initial state: the mixed run
+    takes dt and c_h from its own lambda_max (one sd_advance call), the oracle repeats that sequence.
+    Per variable max|mixed - oracle| / max|oracle change|, and the relative drift of the total energy
+    of both (each by its own diagnostics).  Off by default: about 0.9 s of oracle per step of the
+    41,472-element shell on 16 cores."""
+    import time
+
+    import numpy as np
+    import torch
+
+    from oracle import sdref
+    from paper_2502_17805_gb300 import inputs, sdmhd
+    wl = WORKLOADS[wl_key]
+    mesh, phys, _, bg, params = make_case(wl)
+    v, h = inputs.shell_mesh(wl["nz"], wl["nr"])
+    om = sdref.Mesh(wl["N"], v, h, geom=1, r_in=0.70, r_out=0.98, bc_in=sdref.BC_WALL_CONDUCTING,
+                    bc_out=sdref.BC_WALL_RADIAL)
+    oph = sdref.Phys(gamma=phys.gamma, GM=phys.GM, omega=phys.omega, glm_alpha=phys.glm_alpha, c_h=0.0,
+                     powell=1, gravity=1, coriolis=1)
+    q_init = om.state_init(oph, sdref.INIT_SHELL_POLYTROPE, params, seed=0)
+    q, work = mesh.to_device(q_init), mesh.empty_state()
+    dts = torch.zeros(2 * steps, dtype=torch.float64, device="cuda")
+    mesh.advance(phys, CFL, steps, q, work, prec=sdmhd.SD_FP32_MIXED, bg=bg, dt_out=dts)
+    d = dts.cpu().numpy()
+    qm = mesh.to_host(q)
+    t0 = time.perf_counter()
+    qo = q_init
+    for k in range(steps):
+        oph.c_h = float(d[2 * k + 1])
+        qo = om.rk_step(oph, float(d[2 * k]), qo)
+    secs = time.perf_counter() - t0
+    err = np.abs(qm - qo).max(axis=(1, 2)) / np.maximum(np.abs(qo - q_init).max(axis=(1, 2)), 1e-300)
+    e0 = om.diagnostics(oph, q_init)["energy"]
+    names = ["rho", "mx", "my", "mz", "E", "Bx", "By", "Bz", "psi"]
+    return {"workload": wl["desc"], "steps": steps, "t_end": float(d[0::2].sum()),
+            "reference": "the FP64 oracle (OpenMP over elements, %d host threads, %.0f s)" % (os.cpu_count(), secs),
+            "mixed_vs_oracle_rel_err_of_change": {k: float(x) for k, x in zip(names, err)},
+            "max_rel_err_of_change": float(err.max()),
+            "energy_drift_mixed": mesh.diagnostics(phys, q)["energy"] / e0 - 1.0,
+            "energy_drift_oracle": om.diagnostics(oph, qo)["energy"] / e0 - 1.0}
+
+
 def accuracy_fp32_vs_fp64(mesh, phys, q0, bg, steps: int):
     """FP32-mixed against the FP64 path on the GPU (parity-checked against the oracle to 1e-12 per
     entry) over `steps` SSP-RK3 steps of the same shell: the mixed run takes dt and c_h from its own
@@ -783,6 +830,8 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_accuracy:
         out["accuracy_vs_oracle"] = accuracy_report()
         out["accuracy"] = accuracy_fp32_vs_fp64(mesh, phys, q0, bg, args.accuracy_steps)
+        if args.accuracy_oracle_steps > 0:
+            out["accuracy_oracle"] = accuracy_vs_oracle_shell(args.workload, args.accuracy_oracle_steps)
         out["accuracy"]["workload"] = wl["desc"]
     if rank == 0 and world == 1 and not args.no_largest:
         del q, work, q64, q2
