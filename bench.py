@@ -764,12 +764,32 @@ def run_ours(args):
         dv, dm = qv - q0, qm - q0
         rel = ((dm - dv).abs().amax(dim=(1, 2)) / dv.abs().amax(dim=(1, 2)).clamp_min(1e-300)).cpu().tolist()
         msv, msm = max_over_ranks([msv, msm], device="cuda")
+        # against the derived FP64 peak on the inviscid path's 1,300 flop per point and stage (the
+        # viscous terms' own flops on top): a lower bound of the FP64 pipe's share
+        import torch as _t
+        n_sm = _t.cuda.get_device_properties(_t.cuda.current_device()).multi_processor_count
+        peak64 = fp64_peak_tflops(n_sm, 2070.0)
+        visc64_roof = {"bound": "fp64", "basis": "1,300 flop per point and stage (the inviscid count)",
+                       "achieved": 3 * ALGORITHMIC_FLOP_PER_DOF_STAGE * n_pts * k64 / (msv / 1e3) / 1e12,
+                       "peak": peak64, "unit": "TFLOP/s",
+                       "peak_source": "derived: %d SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz" % n_sm}
+        visc64_roof["frac"] = visc64_roof["achieved"] / peak64
         visc = {"value": whole_job_rate(n_pts, k64, world, msv), "unit": UNIT, "steps": k64, "ms_per_step": msv / k64,
+                "roofline": visc64_roof,
                 "dtype": "f64", "coefficients": coef,
                 "kernel_ms_per_step": {"stage": profv["stage_ms"] / k64,
                                        "gradients_and_control": profv["other_ms"] / k64,
                                        "trace_lambda": profv["trace_ms"] / k64}}
+        peak_v, peak_kind_v = measured_peaks()
+        # against the HBM roofline on the state streams alone (the 648 B per DOF and step of the
+        # inviscid mixed path): the gradient record, its traces and the viscous residual are this
+        # design's own traffic on top
+        visc_roof = {"bound": "hbm", "basis": "algorithmic state streams, 648 B per DOF and step",
+                     "achieved": algorithmic_bytes_per_dof_step(True) * n_pts * k64 / (msm / 1e3) / 1e9,
+                     "peak": peak_v, "unit": "GB/s", "peak_source": peak_kind_v}
+        visc_roof["frac"] = visc_roof["achieved"] / peak_v
         visc_mixed = {"value": whole_job_rate(n_pts, k64, world, msm), "unit": UNIT, "steps": k64,
+                      "roofline": visc_roof,
                       "ms_per_step": msm / k64, "dtype": "f32 (perturbation) + f64 (background, RK state)",
                       "coefficients": coef,
                       "kernel_ms_per_step": {"stage": profm["stage_ms"] / k64,
