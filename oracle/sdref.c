@@ -56,7 +56,8 @@
  *  V7 the radiative diffusivity depends on the radius, kappa_r(r) = kappa_r + kappa_r1 r + kappa_r2 r^2
  *     (Sec. Benchmark Problem Definition gives it as a factor, left undefined, times a quadratic in
  *     r; the caller's three coefficients take both), evaluated at the point of the heat flux: the
- *     flux point, the face point or the wall.
+ *     flux point, the face point or the wall; at an interior face the owner's face point, so that
+ *     the common flux is one value where the two sides are periodic images.
  *  W1 viscous walls (visc_walls; Sec. Problem Formulation): stress-free and impenetrable, i.e. of
  *     the viscous stress only n.tau.n acts through a wall, on the face state (the average of the two
  *     sides, whose normal velocity vanishes), so the wall does no viscous work.
@@ -913,7 +914,15 @@ static void common_visc(const sdref_mesh* m, const sdref_phys* ph, const double*
                         double* Fvm) {
   int64_t k = 6 * e + F;
   double xf[3];
-  family_x(m, e, F / 2, (F & 1) ? m->N : 0, a, b, xf);
+  if (m->nb_e[k] >= 0 && !m->owner[k]) {
+    /* the owner's face point: one common flux per face point, also where the two sides are
+     * periodic images at different positions (readings V4, V7) */
+    int a2o, b2o;
+    map_point(m->code[k], m->N, a, b, &a2o, &b2o);
+    family_x(m, m->nb_e[k], m->nb_f[k] / 2, (m->nb_f[k] & 1) ? m->N : 0, a2o, b2o, xf);
+  } else {
+    family_x(m, e, F / 2, (F & 1) ? m->N : 0, a, b, xf);
+  }
   const double kr = kappa_r_at(ph, xf); /* both sides at this face point (reading V7) */
   if (m->nb_e[k] < 0 && ph->visc_walls) {
     wall_visc(m, ph, e, F, Qown, gown, n, kr, Fv, Fvm);

@@ -160,15 +160,18 @@ def test_gradients_exact_for_linear_fields(oracle):
                 assert np.abs(g[e, c, j] - ex[j]).max() < 1e-12, (e, c, j, g[e, c, j].min(), g[e, c, j].max())
 
 
-def test_viscous_fluxes_conserve_on_a_curved_periodic_box(oracle):
+@pytest.mark.parametrize("kr", [(0.02, 0.0, 0.0), (0.004, 0.012, 0.006)])
+def test_viscous_fluxes_conserve_on_a_curved_periodic_box(oracle, kr):
     """Random state on a jittered periodic box with every coefficient on: the face fluxes are averages
-    along the owner's normal, so sum w |J| R = 0 to round-off for mass, momentum, energy and B."""
+    along the owner's normal, so sum w |J| R = 0 to round-off for mass, momentum, energy and B.  With
+    kappa_r(r) the two sides of a periodic face lie at different radii: the common flux takes the
+    owner's face point (reading V7), one value per face point."""
     N = 4
     v, h, per = inputs.box_mesh(3, jitter=0.2, seed=8)
     m = oracle.Mesh(N, v, h, periodic=per, geom=0)
     q = inputs.random_state(m.n_e, N, seed=3)
     ph = oracle.Phys(gamma=GAMMA, powell=0, glm_alpha=0.0, c_h=0.5, viscous=1, mu=0.03, eta=0.02, kappa=0.01,
-                     kappa_r=0.02, R_gas=0.9)
+                     kappa_r=kr[0], kappa_r1=kr[1], kappa_r2=kr[2], R_gas=0.9)
     R, s = m.residual(ph, q)
     xs, xf, E, D, w = oracle.nodes(N)
     W = np.einsum("i,j,k->kji", w, w, w).ravel()
