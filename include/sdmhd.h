@@ -306,9 +306,15 @@ sd_status sd_advance(const sd_mesh* mesh, const sd_phys* phys, sd_precision prec
  * rho |U|^2/2) to the bin that holds it (points outside [r_min, r_max] go to the
  * nearest radial bin; on the rotation axis phi is taken as 0).  Dividing by the
  * first entry gives the bin means.  out: device double[n_r][n_theta][8],
- * overwritten.  The summation order is not fixed (atomic additions): results
- * agree with a fixed-order sum to round-off.  The paper's B^2 / 8 pi is B^2 / 2
- * in the library's units.  Asynchronous. */
+ * overwritten.  Reproducible: each quantity is summed exactly in a 128-bit
+ * fixed-point accumulator scaled to its largest |term| over the mesh (terms
+ * resolved to 2^-126 of that term), then converted to double within about one
+ * unit in the last place, so the result does not depend on the order of the
+ * points or of the elements (bitwise).  A quantity with a non-finite term sums
+ * to NaN.  Meshes of 2^31 points or more: SD_ERR_INVALID_ARGUMENT.  Scratch of
+ * 256 bytes per bin is allocated on the stream for the call
+ * (SD_ERR_OUT_OF_MEMORY when that fails).  The paper's B^2 / 8 pi is B^2 / 2 in
+ * the library's units.  Asynchronous. */
 sd_status sd_spherical_sums(const sd_mesh* mesh, const double* q, double r_min, double r_max, int32_t n_r,
                             int32_t n_theta, double* out, void* stream);
 

@@ -245,7 +245,7 @@ void free_mesh(sd_mesh* m) {
   void* ptrs[] = {m->own_faces, m->face_k, m->gface64, m->Sfam64, m->invJ64, m->X64, m->Sfam32, m->invJ32, m->X32,
                   m->nbr, m->meta,
                   m->tr64[0], m->tr64[1], m->tr32[0], m->tr32[1], m->dyn, m->diag_part, m->diag_out, m->divb,
-                  m->err, m->grad, m->gtr, m->grad32, m->gtr32, m->rvis32, m->dyn_s, m->work2, m->wreg32};
+                  m->err, m->grad, m->gtr, m->rvis64, m->grad32, m->gtr32, m->rvis32, m->dyn_s, m->work2, m->wreg32};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (m->host_diag) cudaFreeHost(m->host_diag);
@@ -367,35 +367,41 @@ cudaError_t prepare_viscous_mixed(sd_mesh* m, sd::StageParams& P, const sd_backg
   return err;
 }
 
-// Viscous FP64 path: the BR1 gradients of P.q_in (whose face traces are P.tr_in)
-// and their face traces, into the mesh's gradient buffers (allocated on first use);
-// P then points the stage kernel at them.  The FP32-mixed path goes through
-// prepare_viscous_mixed.  No-op without viscous fluxes.
+// Viscous FP64 path: the BR1 gradient record of P.q_in (whose face traces are
+// P.tr_in): its face traces and the interior viscous divergence into the mesh's
+// buffers (allocated on first use), the record itself too when `record` (the
+// background's viscous record); P then points the face-flux and element kernels at
+// them.  The FP32-mixed path goes through prepare_viscous_mixed.  No-op without
+// viscous fluxes.
 cudaError_t prepare_viscous(sd_mesh* m, sd::StageParams& P, cudaStream_t s, int prec = SD_FP64,
-                            const sd_background* bg = nullptr) {
+                            const sd_background* bg = nullptr, bool record = false) {
   if (!P.visc) return cudaSuccess;
   if (prec == SD_FP32_MIXED) return prepare_viscous_mixed(m, P, bg, s);
   const size_t N2 = (size_t)m->N * m->N, N3 = N2 * m->N, ne = (size_t)std::max<int64_t>(m->n_e, 1);
   cudaError_t err = cudaSuccess;
-  if (!m->grad) {
-    err = cudaMalloc((void**)&m->grad, ne * sd::NGRAD * N3 * sizeof(double));
-    if (err != cudaSuccess) return err;
-    m->device_bytes += (int64_t)(ne * sd::NGRAD * N3 * sizeof(double));
-  }
-  if (!m->gtr) {
-    err = cudaMalloc((void**)&m->gtr, ne * 6 * sd::NGRAD * N2 * sizeof(double));
-    if (err != cudaSuccess) return err;
-    m->device_bytes += (int64_t)(ne * 6 * sd::NGRAD * N2 * sizeof(double));
-  }
+  struct Buf {
+    double** p;
+    size_t count;
+    bool want;
+  } bufs[3] = {{&m->grad, ne * sd::MV_REC * N3, record},
+               {&m->gtr, ne * 6 * sd::MV_REC * N2, true},
+               {&m->rvis64, ne * 7 * N3, true}};
+  for (const Buf& b : bufs)
+    if (b.want && !*b.p) {
+      err = cudaMalloc((void**)b.p, b.count * sizeof(double));
+      if (err != cudaSuccess) return err;
+      m->device_bytes += (int64_t)(b.count * sizeof(double));
+    }
   sd::StageParams G = P;
-  G.grad_out = m->grad;
+  G.grad_out = record ? m->grad : nullptr;
   G.gtr_out = m->gtr;
+  G.rvis64_out = m->rvis64;
   {
     ProfScope ps(m, PROF_OTHER, s);
     err = sd::launch_grad(m, G, s);
   }
-  P.grad = m->grad;
   P.gtr_in = m->gtr;
+  P.rvis64 = m->rvis64;
   return err;
 }
 
@@ -919,7 +925,7 @@ sd_status sd_background_create(const sd_mesh* m, const sd_phys* ph, const double
       P.coriolis = 0;
       P.alpha = 0.0;
       P.out = R0v;
-      err = prepare_viscous(mm, P, s);  // FP64 BR1 gradients of Q0 into the mesh's buffers
+      err = prepare_viscous(mm, P, s, SD_FP64, nullptr, true);  // FP64 BR1 record of Q0 into the mesh's buffers
       if (err == cudaSuccess) err = sd::launch_stage(m, SD_FP64, P, s);
       if (err == cudaSuccess) err = sd::launch_bg_visc(m, R0, R0v, mm->grad, mm->gtr, bg->vrec, bg->vtr, s);
     }
@@ -1375,6 +1381,8 @@ sd_status sd_spherical_sums(const sd_mesh* m, const double* q, double r_min, dou
     return fail(SD_ERR_INVALID_ARGUMENT, "need finite r_min < r_max");
   if (n_r < 1 || n_theta < 1 || (int64_t)n_r * n_theta > (1 << 24))
     return fail(SD_ERR_INVALID_ARGUMENT, "n_r and n_theta must be >= 1 with n_r * n_theta <= 2^24");
+  if (m->n_e * (int64_t)m->N * m->N * m->N >= ((int64_t)1 << 31))
+    return fail(SD_ERR_INVALID_ARGUMENT, "the spherical sums take meshes of fewer than 2^31 points");
   DeviceGuard g(m->device);
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t err;
@@ -1382,6 +1390,7 @@ sd_status sd_spherical_sums(const sd_mesh* m, const double* q, double r_min, dou
     ProfScope ps(m, PROF_OTHER, s);
     err = sd::launch_spherical(m, q, r_min, r_max, n_r, n_theta, out, s);
   }
+  if (err == cudaErrorMemoryAllocation) return fail(SD_ERR_OUT_OF_MEMORY, "spherical sums: limb accumulators");
   if (err != cudaSuccess) return cuda_fail(err, "spherical sums kernel");
   return SD_OK;
 }

@@ -542,15 +542,27 @@ cudaError_t launch_diag(const sd_mesh* m, const sd_phys* ph, const double* q, cu
 // ---------------------------------------------------------------------------
 // Longitude averages on the shell (Sec. Results): volume sums over bins of
 // radius x colatitude of (1, V_r, V_theta, V_phi, (B_r^2 + B_theta^2)/2,
-// B_phi^2/2, rho, rho |U|^2 / 2), each weighted by w |J|.  One CTA per element:
-// its points touch a small window of bins, which the CTA sums in shared memory
-// before adding the window to the global table (one atomic per touched entry);
-// a window too large for shared memory adds point by point.  The summation
-// order is not fixed: results agree with a fixed-order sum to round-off.
+// B_phi^2/2, rho, rho |U|^2 / 2), each weighted by w |J|.
+//
+// The sums do not depend on the order of the points: each quantity c is scaled
+// by 2^s_c, with s_c chosen from the largest |term| of c over the mesh so that
+// every scaled term is below 2^126, and split exactly into four signed 32-bit
+// limbs of weights 2^0, 2^32, 2^64, 2^96 (the last one rounded to an integer).
+// Integer additions of the limbs are exact and associative, so atomic additions
+// give the same bits in any order; below 2^31 points per mesh no limb sum can
+// overflow 64 bits.  The finish kernel propagates the carries and converts the
+// four limbs to one double (within about one unit in its last place of the
+// exact sum of the scaled terms).  Kernels: the maxima (one CTA per element, a
+// block reduction, one atomicMax per quantity on the bits of a non-negative
+// double, whose order is the integers'), the limb sums (one CTA per element:
+// its points touch a small window of bins, summed in shared memory before one
+// atomic per touched limb; a window too large for shared memory adds point by
+// point), the finish (one thread per bin and quantity).
 // ---------------------------------------------------------------------------
 
 constexpr int kSphThreads = 256;
 constexpr int kSphVals = 8;
+constexpr int kSphLimbs = 4;
 constexpr int kSphWindow = 64;  // bins per element window in shared memory
 
 __device__ __forceinline__ void sph_point(const double* Q, const double* x, double wq, double r_min, double r_max,
@@ -583,60 +595,152 @@ __device__ __forceinline__ void sph_point(const double* Q, const double* x, doub
   val[7] = wq * 0.5 * Q[0] * (U[0] * U[0] + U[1] * U[1] + U[2] * U[2]);
 }
 
-__global__ void __launch_bounds__(kSphThreads) spherical_kernel(int N, int64_t stride, int64_t plane, const Ops<double> ops,
-                                                                const double* __restrict__ q,
+// the terms of point n of element e
+__device__ __forceinline__ void sph_terms(int N, int64_t stride, int64_t plane, const Ops<double>& ops,
+                                          const double* __restrict__ q, const double* __restrict__ X,
+                                          const double* __restrict__ invJ, double r_min, double r_max, int n_r,
+                                          int n_t, int64_t e, int n, int& bin, double* val) {
+  const int N3 = N * N * N;
+  const int i = n % N, j = (n / N) % N, k = n / (N * N);
+  double Q[9], x[3];
+  for (int c = 0; c < 9; ++c) Q[c] = q[c * plane + e * stride + n];
+  for (int c = 0; c < 3; ++c) x[c] = X[(e * 3 + c) * N3 + n];
+  sph_point(Q, x, ops.w[i] * ops.w[j] * ops.w[k] / invJ[e * N3 + n], r_min, r_max, n_r, n_t, bin, val);
+}
+
+__global__ void __launch_bounds__(kSphThreads) sph_max_kernel(int N, int64_t stride, int64_t plane,
+                                                              const Ops<double> ops, const double* __restrict__ q,
+                                                              const double* __restrict__ X,
+                                                              const double* __restrict__ invJ, double r_min,
+                                                              double r_max, int n_r, int n_t,
+                                                              unsigned long long* vmax) {
+  __shared__ double red[kSphThreads / 32][kSphVals];
+  const int64_t e = blockIdx.x;
+  const int N3 = N * N * N;
+  double m[kSphVals];
+  for (int c = 0; c < kSphVals; ++c) m[c] = 0.0;
+  for (int n = threadIdx.x; n < N3; n += kSphThreads) {
+    int bin;
+    double val[kSphVals];
+    sph_terms(N, stride, plane, ops, q, X, invJ, r_min, r_max, n_r, n_t, e, n, bin, val);
+    for (int c = 0; c < kSphVals; ++c) m[c] = isfinite(val[c]) ? fmax(m[c], fabs(val[c])) : INFINITY;
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int c = 0; c < kSphVals; ++c) {
+    double v = m[c];
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (lane == 0) red[w][c] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < kSphVals) {
+    double v = 0.0;
+    for (int k = 0; k < kSphThreads / 32; ++k) v = fmax(v, red[k][threadIdx.x]);
+    atomicMax(vmax + threadIdx.x, (unsigned long long)__double_as_longlong(v));
+  }
+}
+
+// s_c: the largest |term| of quantity c scaled by 2^s_c lies below 2^126 (0 when
+// every term is zero or some term is not finite: the sum is then NaN)
+__device__ __forceinline__ int sph_shift(unsigned long long bits) {
+  const double m = __longlong_as_double((long long)bits);
+  if (!(m > 0.0) || !isfinite(m)) return 0;
+  int ex;
+  frexp(m, &ex);  // m < 2^ex
+  return 126 - ex;
+}
+
+// x = t 2^s (|x| < 2^126) as l[0] + l[1] 2^32 + l[2] 2^64 + l[3] 2^96, |l[k]| < 2^32:
+// every step but the last rounding is exact (a power-of-two scaling, a truncation,
+// the subtraction of x's own leading bits)
+__device__ __forceinline__ void sph_limbs(double t, int s, long long* l) {
+  double x = ldexp(t, s);
+  const double w96 = 0x1p96, w64 = 0x1p64, w32 = 0x1p32;
+  const double a = trunc(x * 0x1p-96);
+  x -= a * w96;
+  const double b = trunc(x * 0x1p-64);
+  x -= b * w64;
+  const double c = trunc(x * 0x1p-32);
+  x -= c * w32;
+  l[3] = (long long)a;
+  l[2] = (long long)b;
+  l[1] = (long long)c;
+  l[0] = __double2ll_rn(x);
+}
+
+__global__ void __launch_bounds__(kSphThreads) spherical_kernel(int N, int64_t stride, int64_t plane,
+                                                                const Ops<double> ops, const double* __restrict__ q,
                                                                 const double* __restrict__ X,
                                                                 const double* __restrict__ invJ, double r_min,
-                                                                double r_max, int n_r, int n_t, double* out) {
-  __shared__ double win[kSphWindow * kSphVals];
+                                                                double r_max, int n_r, int n_t,
+                                                                const unsigned long long* __restrict__ vmax,
+                                                                unsigned long long* acc) {
+  __shared__ unsigned long long win[kSphWindow * kSphVals * kSphLimbs];
   __shared__ int lo_hi[2];
+  __shared__ int shift[kSphVals];
   const int64_t e = blockIdx.x;
   const int N3 = N * N * N;
   if (threadIdx.x == 0) {
     lo_hi[0] = INT_MAX;
     lo_hi[1] = -1;
   }
-  for (int i = threadIdx.x; i < kSphWindow * kSphVals; i += kSphThreads) win[i] = 0.0;
+  if (threadIdx.x < kSphVals) shift[threadIdx.x] = sph_shift(vmax[threadIdx.x]);
+  for (int i = threadIdx.x; i < kSphWindow * kSphVals * kSphLimbs; i += kSphThreads) win[i] = 0ull;
   __syncthreads();
   // pass 1: the range of bins this element touches
   for (int n = threadIdx.x; n < N3; n += kSphThreads) {
-    const int i = n % N, j = (n / N) % N, k = n / (N * N);
-    double Q[9], x[3], val[kSphVals];
-    for (int c = 0; c < 9; ++c) Q[c] = q[c * plane + e * stride + n];
-    for (int c = 0; c < 3; ++c) x[c] = X[(e * 3 + c) * N3 + n];
     int bin;
-    sph_point(Q, x, ops.w[i] * ops.w[j] * ops.w[k] / invJ[e * N3 + n], r_min, r_max, n_r, n_t, bin, val);
+    double val[kSphVals];
+    sph_terms(N, stride, plane, ops, q, X, invJ, r_min, r_max, n_r, n_t, e, n, bin, val);
     atomicMin(&lo_hi[0], bin);
     atomicMax(&lo_hi[1], bin);
   }
   __syncthreads();
   const int lo = lo_hi[0], span = lo_hi[1] - lo_hi[0] + 1;
   const bool local = span <= kSphWindow;
-  // pass 2: sums (in the window when it fits)
+  // pass 2: limb sums (two's complement: an unsigned addition adds the signed limbs)
   for (int n = threadIdx.x; n < N3; n += kSphThreads) {
-    const int i = n % N, j = (n / N) % N, k = n / (N * N);
-    double Q[9], x[3], val[kSphVals];
-    for (int c = 0; c < 9; ++c) Q[c] = q[c * plane + e * stride + n];
-    for (int c = 0; c < 3; ++c) x[c] = X[(e * 3 + c) * N3 + n];
     int bin;
-    sph_point(Q, x, ops.w[i] * ops.w[j] * ops.w[k] / invJ[e * N3 + n], r_min, r_max, n_r, n_t, bin, val);
-    if (local) {
-      for (int c = 0; c < kSphVals; ++c) atomicAdd(&win[(bin - lo) * kSphVals + c], val[c]);
-    } else {
-      for (int c = 0; c < kSphVals; ++c) atomicAdd(&out[(int64_t)bin * kSphVals + c], val[c]);
+    double val[kSphVals];
+    sph_terms(N, stride, plane, ops, q, X, invJ, r_min, r_max, n_r, n_t, e, n, bin, val);
+    for (int c = 0; c < kSphVals; ++c) {
+      if (!isfinite(val[c])) continue;  // the finish kernel writes NaN for this quantity
+      long long l[kSphLimbs];
+      sph_limbs(val[c], shift[c], l);
+      unsigned long long* dst =
+          local ? win + ((bin - lo) * kSphVals + c) * kSphLimbs : acc + ((int64_t)bin * kSphVals + c) * kSphLimbs;
+      for (int k = 0; k < kSphLimbs; ++k)
+        if (l[k] != 0) atomicAdd(dst + k, (unsigned long long)l[k]);
     }
   }
   __syncthreads();
   if (local)
-    for (int t = threadIdx.x; t < span * kSphVals; t += kSphThreads)
-      if (win[t] != 0.0) atomicAdd(&out[(int64_t)lo * kSphVals + t], win[t]);
+    for (int t = threadIdx.x; t < span * kSphVals * kSphLimbs; t += kSphThreads)
+      if (win[t] != 0ull) atomicAdd(acc + (int64_t)lo * kSphVals * kSphLimbs + t, win[t]);
+}
+
+__global__ void sph_finish_kernel(int64_t n_entries, const unsigned long long* __restrict__ vmax,
+                                  const unsigned long long* __restrict__ acc, double* __restrict__ out) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_entries) return;
+  const int c = (int)(t % kSphVals);
+  long long L[kSphLimbs];
+  for (int k = 0; k < kSphLimbs; ++k) L[k] = (long long)acc[t * kSphLimbs + k];
+  // carries: limbs 0..2 into [0, 2^32), the sign in limb 3
+  for (int k = 0; k < kSphLimbs - 1; ++k) {
+    const long long low = (long long)((unsigned long long)L[k] & 0xffffffffull);
+    L[k + 1] += (L[k] - low) / 4294967296ll;
+    L[k] = low;
+  }
+  const double r = ldexp((double)L[3], 96) + (ldexp((double)L[2], 64) + (ldexp((double)L[1], 32) + (double)L[0]));
+  const double m = __longlong_as_double((long long)vmax[c]);
+  out[t] = isfinite(m) ? ldexp(r, -sph_shift(vmax[c])) : __longlong_as_double(0x7ff8000000000000ll);
 }
 
 // ---------------------------------------------------------------------------
 // Viscous record of the FP32-mixed background: the energy component of the
 // background's viscous residual (its residual with viscous fluxes less the one
-// without, both FP64), grad T0 and grad S0 at the solution points (gradient
-// components 3 c + j, c = 3 for T and 4 for S) and their face traces, in FP32.
+// without, both FP64), grad T0 and grad S0 at the solution points (values 9..11
+// and 12..14 of the FP64 viscous record) and their face traces, in FP32.
 // ---------------------------------------------------------------------------
 
 __global__ void bg_visc_kernel(int N, int64_t n_e, int64_t stride, const double* __restrict__ R0,
@@ -650,12 +754,12 @@ __global__ void bg_visc_kernel(int N, int64_t n_e, int64_t stride, const double*
     const int n = (int)(t - e * N3);
     const int64_t g = e * stride + n;
     vrec[t] = (float)(R0v[4 * plane + g] - R0[4 * plane + g]);
-    for (int k = 0; k < 6; ++k) vrec[(1 + k) * n_e * N3 + t] = (float)grad[(e * NGRAD + 9 + k) * N3 + n];
+    for (int k = 0; k < 6; ++k) vrec[(1 + k) * n_e * N3 + t] = (float)grad[(e * MV_REC + 9 + k) * N3 + n];
   }
   if (t < n_e * 6 * N2) {
     const int64_t ef = t / N2;
     const int pt = (int)(t - ef * N2);
-    for (int k = 0; k < 6; ++k) vtr[(ef * 6 + k) * N2 + pt] = (float)gtr[(ef * NGRAD + 9 + k) * N2 + pt];
+    for (int k = 0; k < 6; ++k) vtr[(ef * 6 + k) * N2 + pt] = (float)gtr[(ef * MV_REC + 9 + k) * N2 + pt];
   }
 }
 
@@ -670,11 +774,31 @@ cudaError_t launch_bg_visc(const sd_mesh* m, const double* R0, const double* R0v
 
 cudaError_t launch_spherical(const sd_mesh* m, const double* q, double r_min, double r_max, int n_r, int n_t,
                              double* out, cudaStream_t s) {
-  cudaError_t err = cudaMemsetAsync(out, 0, (size_t)n_r * n_t * kSphVals * sizeof(double), s);
-  if (err != cudaSuccess || m->n_e == 0) return err;
-  spherical_kernel<<<(unsigned)m->n_e, kSphThreads, 0, s>>>(m->N, m->stride, m->n_e * m->stride, m->ops64, q, m->X64,
-                                                            m->invJ64, r_min, r_max, n_r, n_t, out);
-  return cudaGetLastError();
+  const int64_t n_entries = (int64_t)n_r * n_t * kSphVals;
+  const size_t acc_bytes = (size_t)n_entries * kSphLimbs * sizeof(unsigned long long);
+  unsigned long long* scratch = nullptr;  // [8] maxima, then the limbs [n_r * n_t][8][4]
+  cudaError_t err = cudaMallocAsync((void**)&scratch, acc_bytes + kSphVals * sizeof(unsigned long long), s);
+  if (err != cudaSuccess) return err;
+  unsigned long long* vmax = scratch;
+  unsigned long long* acc = scratch + kSphVals;
+  err = cudaMemsetAsync(scratch, 0, acc_bytes + kSphVals * sizeof(unsigned long long), s);
+  const int64_t plane = m->n_e * m->stride;
+  if (err == cudaSuccess && m->n_e > 0) {
+    sph_max_kernel<<<(unsigned)m->n_e, kSphThreads, 0, s>>>(m->N, m->stride, plane, m->ops64, q, m->X64, m->invJ64,
+                                                            r_min, r_max, n_r, n_t, vmax);
+    err = cudaGetLastError();
+    if (err == cudaSuccess) {
+      spherical_kernel<<<(unsigned)m->n_e, kSphThreads, 0, s>>>(m->N, m->stride, plane, m->ops64, q, m->X64,
+                                                                m->invJ64, r_min, r_max, n_r, n_t, vmax, acc);
+      err = cudaGetLastError();
+    }
+  }
+  if (err == cudaSuccess) {
+    sph_finish_kernel<<<(unsigned)((n_entries + 255) / 256), 256, 0, s>>>(n_entries, vmax, acc, out);
+    err = cudaGetLastError();
+  }
+  cudaError_t err2 = cudaFreeAsync(scratch, s);
+  return err != cudaSuccess ? err : err2;
 }
 
 // ---------------------------------------------------------------------------

@@ -129,17 +129,20 @@ struct StageParams {
   const int* own_faces;
   const int* face_k;
   void* gface;
-  // viscous, resistive and thermal fluxes (FP64 policy): coefficients, the gradients of
-  // (U, T, S, B) at the solution points [e][24][N^3] (grad[3c + j] = d w_c / d x_j) and their
-  // face traces [e][F][24][N^2]; the gradient kernel writes grad_out / gtr_out
+  // viscous, resistive and thermal fluxes (FP64 policy): coefficients; the viscous kernel
+  // writes the face traces [e][F][15][N^2] of the record (tau, J, grad T, grad S) to gtr_out,
+  // the record at the solution points [e][15][N^3] to grad_out when set, and the interior
+  // part of the viscous divergence [e][7][N^3] to rvis64_out; the face-flux kernel reads
+  // gtr_in, the element kernel rvis64
   int visc, visc_walls;
   double mu, eta, kappa, kappa_r, R_gas;
   double kappa_r1, kappa_r2;  // kappa_r(r) = kappa_r + kappa_r1 r + kappa_r2 r^2
   double q_bottom, T_top;  // wall conditions of the viscous path (visc_walls)
-  const double* grad;
   const double* gtr_in;
   double* grad_out;
   double* gtr_out;
+  const double* rvis64;
+  double* rvis64_out;
   // viscous fluxes on the FP32-mixed path: perturbation gradients [e][24][N^3] and their face
   // traces [e][F][24][N^2], the background's viscous record [7][n_e N^3] (its energy residual, grad T0,
   // grad S0) and its face traces [e][F][6][N^2], and the viscous residual of the stage state
@@ -189,8 +192,9 @@ struct sd_mesh {
   double* gface64;          // [n_own][10][N^2] FP64 common face fluxes of the current stage
   int* err;                 // device error word of the stage kernels
   int wait_spins;           // polls of a stage kernel's bounded wait before a time-out (sd_mesh_set_wait_limit)
-  double* grad;             // viscous path, allocated on first use: gradients [e][24][N^3]
-  double* gtr;              //   and their face traces [e][F][24][N^2]
+  double* grad;             // viscous FP64 path, allocated on first use: the record [e][15][N^3]
+  double* gtr;              //   (the background only), its face traces [e][F][15][N^2]
+  double* rvis64;           //   and the interior viscous divergence [e][7][N^3]
   float* grad32;            // viscous FP32-mixed path, allocated on first use: perturbation gradients,
   float* gtr32;             //   their face traces
   float* rvis32;            //   and the viscous residual [7][n_e N^3]
@@ -234,8 +238,8 @@ constexpr int kWaitSpins = 1 << 16;
 constexpr int LAM_SLOTS = 256;
 // gradients the viscous fluxes need: 8 primitive variables x 3 directions, index 3 c + j
 constexpr int NGRAD = 24;
-// Values per point of the FP32-mixed viscous path's gradient record: the
-// viscous stress (6), the current (3), grad T' and grad S'.
+// Values per point of the viscous paths' gradient record: the viscous stress (6),
+// the current (3), grad T and grad S (their perturbations on the FP32-mixed path).
 constexpr int MV_REC = 15;
 // kernels launched from the API (defined in the .cu files)
 cudaError_t launch_stage(const sd_mesh* m, int prec, const StageParams& P, cudaStream_t s);
@@ -243,7 +247,8 @@ cudaError_t launch_traces(const sd_mesh* m, int prec, const StageParams& P, cuda
 // longitude averages on the shell: volume sums per bin of radius x colatitude into out[n_r][n_t][8]
 cudaError_t launch_spherical(const sd_mesh* m, const double* q, double r_min, double r_max, int n_r, int n_t,
                              double* out, cudaStream_t s);
-// BR1 gradients of the primitive variables and their face traces (viscous FP64 path)
+// viscous FP64 path: the BR1 gradient record's face traces (and the record itself when
+// P.grad_out is set) and the interior viscous divergence of P.q_in
 cudaError_t launch_grad(const sd_mesh* m, const StageParams& P, cudaStream_t s);
 // viscous FP32-mixed path: perturbation gradients (Pg), then the viscous residual (Pv)
 cudaError_t launch_mixed_visc(const sd_mesh* m, const StageParams& Pg, const StageParams& Pv, cudaStream_t s);

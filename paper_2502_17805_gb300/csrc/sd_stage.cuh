@@ -1,36 +1,12 @@
-// sd_stage.cuh -- fused SD residual + SSP-RK stage kernel (one element per CTA).
-//
-// Per element (arXiv 2502.17805, Sec. Spectral Difference Method):
-//   load      Q at the N^3 solution points into shared memory
-//   faces     extrapolate Q to the 6 N^2 face points, read the neighbour's face
-//             trace (written by the previous stage), Rusanov common flux and
-//             BR1 normal field along the canonical face normal
-//   for each direction d:
-//     interior  extrapolate Q along the d-lines to the N-1 interior flux points,
-//               contravariant flux S^d . F(Q) and S^d . B
-//     derive    accumulate sum_f D[i][f] Ftilde^d_f at every solution point
-//   epilogue  R = -div/|J| + M(Q, div B), SSP-RK combination in FP64, and the
-//             face traces of the new state for the next stage.
-// Thread layout: BLK >= max(6 N^2, N^3) threads; thread n owns solution point n
-// in the derivative phase and epilogue (its accumulators stay in registers).
+// sd_stage.cuh -- pieces shared by the stage kernels of both policies: the line
+// and solution-point indexing of an element, the bound of the wave speeds and its
+// reduction, the element load (FP64 state, or the FP32 perturbation about the
+// background), the face-trace kernel (+lambda_max), and the sources M of the
+// governing equations (Sec. MHD Governing Equations).
 #pragma once
 
 #include "sd_internal.h"
 #include "sd_physics.cuh"
-
-namespace sd {
-
-template <int N>
-struct Dims;
-template <int N, class Pol>
-__device__ __forceinline__ void load_element(const StageParams& P, const double* q, int64_t e,
-                                             typename Pol::R* sQ, double* lam_out);
-template <int N>
-__device__ __forceinline__ int sol_index(int d, int i, int a, int b);
-
-}  // namespace sd
-
-#include "sd_viscous.cuh"
 
 namespace sd {
 
@@ -42,19 +18,12 @@ struct Dims {
   static constexpr int BLK = ((MAXW + 31) / 32) * 32;
 };
 
+// shared memory of the trace kernel: the state, then the extrapolation table
 template <int N, class Pol>
 struct Smem {
   using R = typename Pol::R;
   static constexpr int N2 = N * N, N3 = N2 * N, NF = N + 1, NV = Pol::NV;
   static constexpr int oQ = 0;
-  static constexpr int oF = oQ + NV * N3;     // [10][NF][N2]
-  static constexpr int oFace = oF + 10 * NF * N2;  // [6][10][N2]
-  static constexpr int oE = oFace + 60 * N2;  // [NF][N]
-  static constexpr int oD = oE + NF * N;      // [N][NF]
-  static constexpr int nR = oD + N * NF;
-  static constexpr size_t bytesR = ((nR * sizeof(R)) + 15) / 16 * 16;
-  static constexpr size_t bytes = bytesR;
-  // the trace kernel needs only the state and the extrapolation table
   static constexpr int oTE = NV * N3;
   static constexpr size_t trace_bytes = ((oTE + NF * N) * sizeof(R) + 15) / 16 * 16;
 };
@@ -345,239 +314,6 @@ __device__ __forceinline__ void sources_mixed(const MixedConsts& C, const float*
   M[8] -= C.alpha * q[8];
 }
 
-template <int N, class Pol, bool VISC>
-__global__ void __launch_bounds__(Dims<N>::BLK) stage_kernel(const StageParams P, const Ops<typename Pol::R> ops) {
-  using R = typename Pol::R;
-  using S = Smem<N, Pol>;
-  static_assert(!Pol::mixed, "the FP32-mixed stages run stage_kernel_v2");
-  constexpr int N2 = N * N, N3 = N2 * N, NF = N + 1, BLK = Dims<N>::BLK, NV = Pol::NV;
-  extern __shared__ __align__(16) unsigned char smem[];
-  R* sQ = reinterpret_cast<R*>(smem) + S::oQ;
-  R* sF = reinterpret_cast<R*>(smem) + S::oF;
-  R* sFace = reinterpret_cast<R*>(smem) + S::oFace;
-  R* sE = reinterpret_cast<R*>(smem) + S::oE;
-  R* sD = reinterpret_cast<R*>(smem) + S::oD;
-
-  const int tid = threadIdx.x;
-  for (int i = tid; i < NF * N; i += BLK) {
-    sE[i] = ops.E[i];
-    sD[i] = ops.D[i];
-  }
-  const int64_t e = blockIdx.x;
-  const R* Sfam = reinterpret_cast<const R*>(P.Sfam) + e * (9 * N2 * NF);
-  const R gamma = R(P.gamma);
-  const R gm1 = gamma - R(1);
-  double dt = P.dt, chd = P.c_h;
-  if (P.dyn) {
-    dt = P.dyn[0];
-    chd = P.dyn[1];
-  }
-  const R ch = R(chd);
-
-  load_element<N, Pol>(P, P.q_in, e, sQ, nullptr);
-  // viscous fluxes: this element's gradients [24][N3] after the state
-  [[maybe_unused]] double* sG = reinterpret_cast<double*>(smem + S::bytes);
-  [[maybe_unused]] ViscCoef vc{};  // set below in the viscous instances, the only ones that read it
-  // radiative diffusivity at point (f, a, b) of flux family d: the element's map is a polynomial
-  // of degree floor(N/2) < N, so E gives its position there exactly from the solution points
-  [[maybe_unused]] auto kr_at = [&](int d, int f, int a, int b) -> double {
-    if (!vc.kr_varies) return vc.kappa_r;
-    const double* Xe = reinterpret_cast<const double*>(P.X) + e * 3 * N3;
-    double x[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      double s = 0.0;
-#pragma unroll
-      for (int i = 0; i < N; ++i) s += sE[f * N + i] * __ldg(Xe + c * N3 + sol_index<N>(d, i, a, b));
-      x[c] = s;
-    }
-    return kappa_r_at(vc, x[0], x[1], x[2]);
-  };
-  if constexpr (VISC) {
-    vc = visc_coef(P);
-    const double* Ge = P.grad + e * NGRAD * N3;
-    for (int i = tid; i < NGRAD * N3; i += BLK) sG[i] = Ge[i];
-  }
-  __syncthreads();
-
-  // ---- element faces: common flux and BR1 normal field
-  for (int t = tid; t < 6 * N2; t += BLK) {
-    const int F = t / N2, pt = t - F * N2, a = pt % N, b = pt / N;
-    const int d = F >> 1, side = F & 1, f = side ? N : 0;
-    R qo[NV];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      R s = R(0);
-#pragma unroll
-      for (int i = 0; i < N; ++i) s += sE[f * N + i] * sQ[v * N3 + sol_index<N>(d, i, a, b)];
-      qo[v] = s;
-    }
-    const R* Sp = Sfam + (d * 3 * N2 + pt) * NF + f;
-    const R Sx = Sp[0], Sy = Sp[N2 * NF], Sz = Sp[2 * N2 * NF];
-    const R mag = sqrt(Sx * Sx + Sy * Sy + Sz * Sz);
-    const R im = R(1) / mag;
-    const R sg = side ? R(1) : R(-1);
-    const R nx = sg * Sx * im, ny = sg * Sy * im, nz = sg * Sz * im;
-    const int64_t gidx = e * 6 + F;
-    const int nb = P.nbr[gidx];
-    const int mt = P.meta[gidx];
-    R qn[9];
-    if (nb >= 0) {
-      const int code = meta_code(mt);
-      const int u = (code & 4) ? b : a, w = (code & 4) ? a : b;
-      const int a2 = (code & 2) ? N - 1 - u : u, b2 = (code & 1) ? N - 1 - w : w;
-      const R* T = reinterpret_cast<const R*>(P.tr_in) + ((int64_t)nb * 6 + meta_nbF(mt)) * 9 * N2 + a2 + N * b2;
-#pragma unroll
-      for (int v = 0; v < 9; ++v) qn[v] = T[v * N2];
-    } else {
-      const int bc = meta_bc(mt);
-      if (bc == SD_BC_FARFIELD) {
-#pragma unroll
-        for (int v = 0; v < 9; ++v) qn[v] = P.ff_own ? qo[v] : R(P.farfield[v]);
-      } else {
-        wall_ghost<R>(qo, nx, ny, nz, bc, qn);
-      }
-    }
-    R Fs[9];
-    riemann_fp64(qo, qn, nx, ny, nz, gamma, ch, P.central, Fs);
-    if constexpr (VISC) {
-      // average of both sides' F_vis . n (this side's alone at a wall or far-field face,
-      // or the wall conditions of visc_walls)
-      double g[NGRAD], Fv[9];
-      grad_face<N>(sG, sE, F, a, b, g);
-      const double kr = kr_at(d, f, a, b);  // both sides at this face point
-      if (nb < 0 && P.visc_walls)
-        wall_visc_flux(qo, qn, g, nx, ny, nz, meta_outer(mt) != 0, meta_bc(mt) == SD_BC_WALL_CONDUCTING, P.q_bottom,
-                       vc, kr, Fv);
-      else
-        visc_flux(qo, g, nx, ny, nz, vc, kr, Fv);
-      if (nb >= 0) {
-        const int code = meta_code(mt);
-        const int u = (code & 4) ? b : a, w = (code & 4) ? a : b;
-        const int a2 = (code & 2) ? N - 1 - u : u, b2 = (code & 1) ? N - 1 - w : w;
-        const double* Gt = P.gtr_in + ((int64_t)nb * 6 + meta_nbF(mt)) * NGRAD * N2 + a2 + N * b2;
-#pragma unroll
-        for (int k = 0; k < NGRAD; ++k) g[k] = Gt[k * N2];
-        double Fn[9];
-        visc_flux(qn, g, nx, ny, nz, vc, kr, Fn);
-#pragma unroll
-        for (int v = 0; v < 9; ++v) Fv[v] = 0.5 * (Fv[v] + Fn[v]);
-      }
-#pragma unroll
-      for (int v = 0; v < 9; ++v) Fs[v] -= Fv[v];
-    }
-    const R Bn = R(0.5) * ((qo[5] + qn[5]) * nx + (qo[6] + qn[6]) * ny + (qo[7] + qn[7]) * nz);
-    const R sm = sg * mag;
-#pragma unroll
-    for (int v = 0; v < 9; ++v) sFace[(F * 10 + v) * N2 + pt] = sm * Fs[v];
-    sFace[(F * 10 + 9) * N2 + pt] = sm * Bn;
-  }
-
-  // ---- three directions: interior contravariant fluxes, then derivative
-  R acc[10];
-#pragma unroll
-  for (int v = 0; v < 10; ++v) acc[v] = R(0);
-  const int n = tid;
-  const int i0 = n % N, j0 = (n / N) % N, k0 = n / N2;
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    __syncthreads();
-    for (int t = tid; t < (N - 1) * N2; t += BLK) {
-      const int fm = t % (N - 1), line = t / (N - 1), f = fm + 1, a = line % N, b = line / N;
-      R qf[NV];
-#pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        R s = R(0);
-#pragma unroll
-        for (int i = 0; i < N; ++i) s += sE[f * N + i] * sQ[v * N3 + sol_index<N>(d, i, a, b)];
-        qf[v] = s;
-      }
-      const R* Sp = Sfam + (d * 3 * N2 + line) * NF + f;
-      const R Sx = Sp[0], Sy = Sp[N2 * NF], Sz = Sp[2 * N2 * NF];
-      R Fv[9];
-      flux_full<R>(qf, Sx, Sy, Sz, gm1, ch, Fv);
-      if constexpr (VISC) {
-        double g[NGRAD], Fvis[9];
-#pragma unroll
-        for (int k = 0; k < NGRAD; ++k) {
-          double s = 0.0;
-#pragma unroll
-          for (int i = 0; i < N; ++i) s += sE[f * N + i] * sG[k * N3 + sol_index<N>(d, i, a, b)];
-          g[k] = s;
-        }
-        visc_flux(qf, g, Sx, Sy, Sz, vc, kr_at(d, f, a, b), Fvis);
-#pragma unroll
-        for (int v = 0; v < 9; ++v) Fv[v] -= Fvis[v];
-      }
-#pragma unroll
-      for (int v = 0; v < 9; ++v) sF[(v * NF + f) * N2 + line] = Fv[v];
-      sF[(9 * NF + f) * N2 + line] = Sx * qf[5] + Sy * qf[6] + Sz * qf[7];
-    }
-    __syncthreads();
-    if (n < N3) {
-      const int id = d == 0 ? i0 : (d == 1 ? j0 : k0);
-      const int line = d == 0 ? j0 + N * k0 : (d == 1 ? i0 + N * k0 : i0 + N * j0);
-      const R* Dr = sD + id * NF;
-#pragma unroll
-      for (int v = 0; v < 10; ++v) {
-        R s = Dr[0] * sFace[((2 * d) * 10 + v) * N2 + line];
-#pragma unroll
-        for (int f = 1; f < N; ++f) s += Dr[f] * sF[(v * NF + f) * N2 + line];
-        s += Dr[N] * sFace[((2 * d + 1) * 10 + v) * N2 + line];
-        acc[v] += s;
-      }
-    }
-  }
-
-  // ---- epilogue: residual, sources, RK combination q_out = a q_n + b (q_in + dt R)
-  double lam = 0.0;  // lambda_max of the new state (MODE_RK with P.lam_max)
-  if (n < N3) {
-    const R iJ = reinterpret_cast<const R*>(P.invJ)[e * N3 + n];
-    const R* Xe = reinterpret_cast<const R*>(P.X) + e * 3 * N3;
-    const R divB = acc[9] * iJ;
-    const int64_t g = e * P.stride + n;
-    double q[9], M[9], Rv[9];
-#pragma unroll
-    for (int v = 0; v < 9; ++v) q[v] = sQ[v * N3 + n];
-    sources_fp64(P, q, divB, Xe[n], Xe[N3 + n], Xe[2 * N3 + n], M);
-#pragma unroll
-    for (int v = 0; v < 9; ++v) Rv[v] = -acc[v] * iJ + M[v];
-    if (P.mode == MODE_RESIDUAL) {
-#pragma unroll
-      for (int v = 0; v < 9; ++v) P.out[v * P.plane + g] = Rv[v];
-    } else if (P.mode == MODE_DIVB) {
-      P.divb[e * N3 + n] = divB;
-    } else {
-      double qout[9];
-      if (P.rk_a != 0.0) {
-#pragma unroll
-        for (int v = 0; v < 9; ++v)
-          qout[v] = P.rk_a * __ldg(P.q_n + v * P.plane + g) + P.rk_b * (q[v] + dt * Rv[v]);
-      } else {
-#pragma unroll
-        for (int v = 0; v < 9; ++v) qout[v] = P.rk_b * (q[v] + dt * Rv[v]);
-      }
-#pragma unroll
-      for (int v = 0; v < 9; ++v) P.out[v * P.plane + g] = qout[v];
-      if (P.lam_max) lam = point_speed_fp64(qout, P.gamma);
-      if (P.tr_out) {
-#pragma unroll
-        for (int v = 0; v < 9; ++v) acc[v] = qout[v];  // kept for the traces below
-      }
-    }
-  }
-  if (P.mode == MODE_RK && P.lam_max) speed_reduce(lam, P.lam_max, P.lam_nslot);
-  if (P.mode == MODE_RK && P.tr_out) {
-    __syncthreads();
-    if (n < N3) {
-#pragma unroll
-      for (int v = 0; v < 9; ++v) sQ[v * N3 + n] = acc[v];
-    }
-    __syncthreads();
-    write_traces<N, Pol>(sQ, sE, reinterpret_cast<R*>(P.tr_out), e);
-  }
-}
-
 // The trace (+lambda_max) kernel of either policy.
 template <int N, class Pol>
 cudaError_t launch_traces_t(const StageParams& P, const Ops<typename Pol::R>& ops, cudaStream_t s) {
@@ -588,23 +324,6 @@ cudaError_t launch_traces_t(const StageParams& P, const Ops<typename Pol::R>& op
   }
   if (P.n_e == 0) return cudaSuccess;
   trace_kernel<N, Pol><<<(unsigned)P.n_e, Dims<N>::BLK, bytes, s>>>(P, ops);
-  return cudaGetLastError();
-}
-
-// The FP64 stage kernel, or its trace kernel.
-template <int N, class Pol, bool VISC = false>
-cudaError_t launch_stage_t(const StageParams& P, const Ops<typename Pol::R>& ops, bool traces_only, cudaStream_t s) {
-  static_assert(!Pol::mixed, "the FP32-mixed stages run stage_kernel_v2");
-  if (traces_only) return launch_traces_t<N, Pol>(P, ops, s);
-  using Sm = Smem<N, Pol>;
-  const size_t bytes = Sm::bytes + (VISC ? NGRAD * N * N * N * sizeof(double) : 0);
-  auto kern = stage_kernel<N, Pol, VISC>;
-  if (bytes > 48 * 1024) {
-    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (err != cudaSuccess) return err;
-  }
-  if (P.n_e == 0) return cudaSuccess;
-  kern<<<(unsigned)P.n_e, Dims<N>::BLK, bytes, s>>>(P, ops);
   return cudaGetLastError();
 }
 

@@ -25,6 +25,7 @@
 #include "sd_internal.h"
 #include "sd_physics.cuh"
 #include "sd_stage.cuh"
+#include "sd_viscous.cuh"
 
 namespace sd {
 
@@ -42,9 +43,11 @@ struct DimsF64 {
 // Common flux of one face point, computed by the face's owner: G[k][v][pt] =
 // |S| F*(q_own, q_other, n) for v < 9 and |S| (B_own + B_other) / 2 . n for v = 9,
 // n the owner's outward unit normal.  q_other is the neighbour's trace, the wall
-// ghost state or the far-field state.
-template <int N>
-__global__ void __launch_bounds__(256) face_flux_kernel(const StageParams P) {
+// ghost state or the far-field state.  VISC: less the common viscous flux, the
+// average of both sides' F_vis . n from their states and gradient records (this
+// side's alone at a boundary face; the wall conditions of visc_walls at a wall).
+template <int N, bool VISC>
+__global__ void __launch_bounds__(256, 2) face_flux_kernel(const StageParams P, const Ops<double> ops) {
   constexpr int N2 = N * N, NF = N + 1;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= P.n_own * N2) return;
@@ -86,6 +89,34 @@ __global__ void __launch_bounds__(256) face_flux_kernel(const StageParams P) {
   const double ch = P.dyn ? P.dyn[1] : P.c_h;
   double Fs[9];
   riemann_fp64(qo, qn, nx, ny, nz, P.gamma, ch, P.central, Fs);
+  if constexpr (VISC) {
+    const ViscCoef c = visc_coef(P);
+    const double kr = visc_kr<N>(c, ops, reinterpret_cast<const double*>(P.X), e, d, f, a, b);
+    double rec[MV_REC], Fv[7];
+    const double* Ro = P.gtr_in + (e * 6 + F) * MV_REC * N2 + pt;
+#pragma unroll
+    for (int k = 0; k < MV_REC; ++k) rec[k] = Ro[k * N2];
+    if (nb < 0 && P.visc_walls) {
+      wall_visc_flux_rec(qo, qn, rec, nx, ny, nz, meta_outer(mt) != 0, meta_bc(mt) == SD_BC_WALL_CONDUCTING,
+                         P.q_bottom, c, kr, Fv);
+    } else {
+      visc_flux_rec(qo, rec, nx, ny, nz, c, kr, Fv);
+      if (nb >= 0) {
+        const int code = meta_code(mt);
+        const int u = (code & 4) ? b : a, w = (code & 4) ? a : b;
+        const int a2 = (code & 2) ? N - 1 - u : u, b2 = (code & 1) ? N - 1 - w : w;
+        const double* Rn = P.gtr_in + ((int64_t)nb * 6 + meta_nbF(mt)) * MV_REC * N2 + a2 + N * b2;
+#pragma unroll
+        for (int k = 0; k < MV_REC; ++k) rec[k] = Rn[k * N2];
+        double Fn[7];
+        visc_flux_rec(qn, rec, nx, ny, nz, c, kr, Fn);
+#pragma unroll
+        for (int k = 0; k < 7; ++k) Fv[k] = 0.5 * (Fv[k] + Fn[k]);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 7; ++k) Fs[1 + k] -= Fv[k];
+  }
   const double Bn = 0.5 * ((qo[5] + qn[5]) * nx + (qo[6] + qn[6]) * ny + (qo[7] + qn[7]) * nz);
   double* G = reinterpret_cast<double*>(P.gface) + k * 10 * N2 + pt;
 #pragma unroll
@@ -246,6 +277,11 @@ __global__ void __launch_bounds__(DimsF64<N>::T) stage_kernel_f64(const StagePar
     double acc[10];
 #pragma unroll
     for (int v = 0; v < 10; ++v) acc[v] = (D0[v * N2] + D1[v * N2]) + D2[v * N2];
+    if (P.rvis64) {  // the viscous fluxes' divergence over the interior flux points (the faces' is in D)
+      const double* Rv = P.rvis64 + e * 7 * N3 + n;
+#pragma unroll
+      for (int k = 0; k < 7; ++k) acc[1 + k] -= __ldg(Rv + k * N3);
+    }
     const double iJ = __ldg(reinterpret_cast<const double*>(P.invJ) + e * N3 + n);
     const double* Xe = reinterpret_cast<const double*>(P.X) + e * 3 * N3;
     const double divB = acc[9] * iJ;
@@ -302,14 +338,19 @@ __global__ void __launch_bounds__(DimsF64<N>::T) stage_kernel_f64(const StagePar
   }
 }
 
-// The face-flux kernel, then the element kernel.
+// The face-flux kernel (with the common viscous flux when P.visc and the viscous
+// kernel has run: P.gtr_in set), then the element kernel.
 template <int N>
 cudaError_t launch_stage_f64_t(const StageParams& P, const Ops<double>& ops, cudaStream_t s) {
   using DV = DimsF64<N>;
   if (P.n_e == 0) return cudaSuccess;
   const int64_t pts = P.n_own * (int64_t)N * N;
   if (pts > 0) {
-    face_flux_kernel<N><<<(unsigned)((pts + 255) / 256), 256, 0, s>>>(P);
+    const unsigned blocks = (unsigned)((pts + 255) / 256);
+    if (P.visc && P.gtr_in)
+      face_flux_kernel<N, true><<<blocks, 256, 0, s>>>(P, ops);
+    else
+      face_flux_kernel<N, false><<<blocks, 256, 0, s>>>(P, ops);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
   }

@@ -1,16 +1,15 @@
-// Instantiations of the fused element kernels for the FP64 policy, N = 2..8:
-// the face-flux and line-blocked element kernels of the inviscid stages, the
-// viscous stage kernel, the trace kernel, and the BR1 gradient kernel.
+// Instantiations of the FP64 kernels, N = 2..8: the face-flux and line-blocked
+// element kernels of the stages, the trace kernel, and the viscous kernel (BR1
+// gradient record, its face traces, the interior viscous divergence).
 #include "sd_stage.cuh"
 #include "sd_stage_f64.cuh"
+#include "sd_viscous.cuh"
 
 namespace sd {
 
 template <int N>
 static cudaError_t launch_fp64_n(const sd_mesh* m, const StageParams& P, bool traces_only, cudaStream_t s) {
   if (traces_only) return launch_traces_t<N, PolFP64>(P, m->ops64, s);
-  // the viscous instantiation once the gradient pass has filled P.grad (not for MODE_DIVB)
-  if (P.visc && P.grad && P.mode != MODE_DIVB) return launch_stage_t<N, PolFP64, true>(P, m->ops64, false, s);
   return launch_stage_f64_t<N>(P, m->ops64, s);
 }
 
@@ -29,13 +28,13 @@ cudaError_t launch_stage_fp64(const sd_mesh* m, const StageParams& P, bool trace
 
 cudaError_t launch_grad(const sd_mesh* m, const StageParams& P, cudaStream_t s) {
   switch (m->N) {
-    case 2: return launch_grad_t<2>(P, m->ops64, s);
-    case 3: return launch_grad_t<3>(P, m->ops64, s);
-    case 4: return launch_grad_t<4>(P, m->ops64, s);
-    case 5: return launch_grad_t<5>(P, m->ops64, s);
-    case 6: return launch_grad_t<6>(P, m->ops64, s);
-    case 7: return launch_grad_t<7>(P, m->ops64, s);
-    case 8: return launch_grad_t<8>(P, m->ops64, s);
+    case 2: return launch_visc_f64_t<2>(P, m->ops64, s);
+    case 3: return launch_visc_f64_t<3>(P, m->ops64, s);
+    case 4: return launch_visc_f64_t<4>(P, m->ops64, s);
+    case 5: return launch_visc_f64_t<5>(P, m->ops64, s);
+    case 6: return launch_visc_f64_t<6>(P, m->ops64, s);
+    case 7: return launch_visc_f64_t<7>(P, m->ops64, s);
+    case 8: return launch_visc_f64_t<8>(P, m->ops64, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -205,3 +205,50 @@ def test_shell221k_mixed_residual_sampled():
     R = _gather(gm, gm.residual(gph, gm.to_device(q0), prec=sdmhd.SD_FP32_MIXED, bg=bg), elems)
     ok, err, bound = _mixed_bound(R, Ro, s, label="221k residual at rest", var_axis=1)
     assert ok, (err, bound)
+
+
+VISC = dict(viscous=1, mu=0.03, eta=0.02, kappa=0.01, kappa_r=0.015, R_gas=0.9)
+
+
+def _flow(q0, seed):
+    """a seeded flow U ~ 1e-2 U[-1, 1] added to a state at rest (in place)"""
+    rng = np.random.default_rng(seed)
+    mom = rng.uniform(-1e-2, 1e-2, size=q0[1:4].shape) * q0[0]
+    q0[1:4] += mom
+    q0[4] += 0.5 * (mom ** 2).sum(axis=0) / q0[0]
+
+
+def test_shell41k_fp64_viscous_residual_sampled():
+    """The viscous FP64 residual at full size, in the benchmark's launch configuration (the viscous
+    kernel, then the face-flux kernel with the common viscous flux and the element kernel over every
+    element), with the viscous wall conditions, kappa_r(r) and every source on."""
+    gm, om = _shell(24, 12)
+    kw = dict(gamma=5.0 / 3.0, GM=1.0, omega=1.0, glm_alpha=1.0, c_h=0.8, powell=1, gravity=1, coriolis=1,
+              visc_walls=1, q_bottom=0.05, T_top=0.6, kappa_r1=0.01, kappa_r2=0.005, **VISC)
+    gph, oph = sdmhd.Phys(**kw), sdref.Phys(**kw)
+    q0 = om.state_init(oph, sdref.INIT_SHELL_POLYTROPE, [3.0, 0.70, 0.98, 1.0, 1.0, 1e-4, 1e-3], seed=0)
+    _flow(q0, 43)
+    elems = _sample(gm.n_e, seed=4)
+    Ro, s = om.residual_elements(oph, q0, elems)
+    R = _gather(gm, gm.residual(gph, gm.to_device(q0)), elems)
+    err = (np.abs(R - Ro) / (np.abs(Ro) + s[None, :, None])).max()
+    assert err < TOL64, err
+
+
+def test_shell41k_mixed_viscous_residual_sampled():
+    """The viscous FP32-mixed residual at full size (background built with the viscous coefficients)
+    with a seeded flow: every variable within 1e-5 of its largest value over the sampled elements."""
+    gm, om = _shell(24, 12)
+    kw = dict(gamma=5.0 / 3.0, GM=1.0, omega=1.0, glm_alpha=1.0, c_h=0.8, powell=1, gravity=1, coriolis=1,
+              **VISC)
+    gph, oph = sdmhd.Phys(**kw), sdref.Phys(**kw)
+    prm = [3.0, 0.70, 0.98, 1.0, 1.0, 1e-4, 1e-3]
+    q0, qb = om.state_init(oph, sdref.INIT_SHELL_POLYTROPE, prm, seed=0, background=True)
+    _flow(q0, 44)
+    bg = gm.background(gph, gm.to_device(qb))
+    del qb
+    elems = _sample(gm.n_e, seed=5)
+    Ro, _ = om.residual_elements(oph, q0, elems)
+    R = _gather(gm, gm.residual(gph, gm.to_device(q0), prec=sdmhd.SD_FP32_MIXED, bg=bg), elems)
+    ok, err, bound = _mixed_bound(R, Ro, None, floor=(), label="41k viscous residual developed", var_axis=1)
+    assert ok, (err, bound)

@@ -1,6 +1,6 @@
 """Parity of sd_spherical_sums (longitude averages of Sec. Results) with the oracle's fixed-order sums
 on the shell, for bin tables that fit an element's window in shared memory and for tables that do not
-(point-by-point global additions)."""
+(point-by-point global additions); the sums' independence of the element order (bitwise)."""
 import numpy as np
 import pytest
 
@@ -49,14 +49,48 @@ def test_spherical_sums_reject_bad_arguments():
         gm.spherical_sums(q, 0.70, 0.98, 2, 2, out=torch.zeros(0, dtype=torch.float64, device="cuda"))
 
 
-def test_spherical_sums_repeat_to_round_off():
-    """The bin sums use atomic additions (no fixed order): two calls on the same state agree to
-    round-off of each bin's sum of magnitudes."""
+def test_spherical_sums_do_not_depend_on_the_element_order():
+    """The sums are exact in fixed point before one conversion: the same mesh with its elements
+    listed in another order (the same geometry per element, the state permuted alike) gives the
+    same bits, and so do repeated calls."""
     N = 5
     v, h = inputs.shell_mesh(8, 4)
-    gm = sdmhd.Mesh(N, v, h, geom=1, r_in=0.70, r_out=0.98)
-    q = gm.to_device(inputs.random_state(gm.n_e, N, seed=13))
-    a = gm.spherical_sums(q, 0.70, 0.98, 4, 16).cpu().numpy()
-    b = gm.spherical_sums(q, 0.70, 0.98, 4, 16).cpu().numpy()
-    scale = np.abs(a).reshape(-1, 8).max(axis=0)
-    assert np.all(np.abs(a - b).reshape(-1, 8).max(axis=0) <= 1e-13 * scale)
+    kw = dict(geom=1, r_in=0.70, r_out=0.98)
+    q0 = inputs.random_state(len(h), N, seed=13)
+    perm = np.random.default_rng(5).permutation(len(h))
+    ga, gb = sdmhd.Mesh(N, v, h, **kw), sdmhd.Mesh(N, v, np.ascontiguousarray(h[perm]), **kw)
+    qa, qb = ga.to_device(q0), gb.to_device(np.ascontiguousarray(q0[:, perm]))
+    for n_r, n_t in [(4, 16), (3, 300)]:  # element windows in shared memory; point-by-point additions
+        a = ga.spherical_sums(qa, 0.70, 0.98, n_r, n_t)
+        b = gb.spherical_sums(qb, 0.70, 0.98, n_r, n_t)
+        assert torch.equal(a, b), (n_r, n_t)
+        assert torch.equal(a, ga.spherical_sums(qa, 0.70, 0.98, n_r, n_t))
+
+
+def test_spherical_sums_of_terms_far_apart_in_size():
+    """Terms of very different size in one bin: the fixed-point sum keeps the small ones (the
+    density of one element raised by 1e12 leaves the other bins' mass sums as the oracle's)."""
+    N = 4
+    v, h = inputs.shell_mesh(4, 2)
+    kw = dict(geom=1, r_in=0.70, r_out=0.98)
+    gm, om = sdmhd.Mesh(N, v, h, **kw), sdref.Mesh(N, v, h, **kw)
+    q0 = inputs.random_state(gm.n_e, N, seed=21)
+    q0[:, 0] *= 1e12  # every component of element 0, so the velocities stay as they were
+    G = gm.spherical_sums(gm.to_device(q0), 0.70, 0.98, 2, 6).cpu().numpy()
+    O = om.spherical_sums(q0, 2, 6)
+    for c in (0, 4, 5, 6, 7):  # non-negative terms; per bin: round-off of that bin's own sum
+        mag = np.abs(O[..., c])
+        assert np.all(np.abs(G[..., c] - O[..., c]) <= 1e-12 * np.maximum(mag, 1e-300)), c
+
+
+def test_spherical_sums_nan_term():
+    """A NaN momentum at one point: the velocity quantities and the kinetic energy sum to NaN; the
+    volume, magnetic energies and mass stay finite."""
+    N = 3
+    v, h = inputs.shell_mesh(2, 1)
+    gm = sdmhd.Mesh(N, v, h, geom=1, r_in=0.7, r_out=0.98)
+    q0 = inputs.random_state(gm.n_e, N, seed=2)
+    q0[1, 3, 5] = np.nan
+    out = gm.spherical_sums(gm.to_device(q0), 0.70, 0.98, 2, 3).cpu().numpy().reshape(-1, 8)
+    assert np.all(np.isnan(out[:, [1, 2, 3, 7]]))
+    assert np.all(np.isfinite(out[:, [0, 4, 5, 6]]))

@@ -65,6 +65,20 @@ def test_viscous_residual_shell_with_walls_and_sources(N):
     assert _c19(R, Ro, s) < TOL64
 
 
+@pytest.mark.parametrize("N", [3, 5])
+def test_viscous_residual_shell_far_field(N):
+    """Far-field faces: the BR1 average against the far-field state, this side's viscous flux alone."""
+    v, h = inputs.shell_mesh(2, 2)
+    gm, om = _pair(N, v, inputs.reorient(h, seed=N), geom=1, r_in=0.7, r_out=0.98, bc_in=sdref.BC_FARFIELD,
+                   bc_out=sdref.BC_FARFIELD)
+    gph, oph = _phys(powell=1, c_h=0.8, glm_alpha=0.5, **VISC)
+    q0 = inputs.random_state(gm.n_e, N, seed=40 + N)
+    gph.farfield = oph.farfield = list(q0[:, 0, 0])
+    R = gm.to_host(gm.residual(gph, gm.to_device(q0)))
+    Ro, s = om.residual(oph, q0)
+    assert _c19(R, Ro, s) < TOL64
+
+
 def test_viscous_steps_follow_the_oracle():
     """Three SSP-RK3 steps through sd_step (device dt, c_h) against the oracle given them."""
     N = 4
