@@ -707,7 +707,8 @@ def fp64_roofline(stage_ms: float, clocks, n_pts: int, workload: str = COUNTER_W
     flops = ALGORITHMIC_FLOP_PER_DOF_STAGE * n_pts
     achieved = flops / (stage_ms / 1e3) / 1e12
     counted = committed_traffic("stage_fp64_N6_flops", FP64_SOURCES, workload)
-    return {"kernel": "face_flux_kernel<6> + stage_kernel_f64<6> (FP64 stage)", "bound": "fp64", "achieved": achieved,
+    return {"kernel": "face_flux_kernel<6> + stage_kernel_f64<6> (FP64 stage)", "bound": "alu", "pipe": "fp64",
+            "achieved": achieved,
             "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "peak_source": "derived: %d SMs x 2 FP64 FMA/clk x 2 flop x %.0f MHz" % (n_sm, mhz),
             "algorithmic_flops_per_launch": flops, "counted_flops_per_launch": counted,
@@ -773,7 +774,7 @@ def run_ours(args):
         import torch as _t
         n_sm = _t.cuda.get_device_properties(_t.cuda.current_device()).multi_processor_count
         peak64 = fp64_peak_tflops(n_sm, 2070.0)
-        visc64_roof = {"bound": "fp64", "basis": "1,300 flop per point and stage (the inviscid count)",
+        visc64_roof = {"bound": "alu", "pipe": "fp64", "basis": "1,300 flop per point and stage (the inviscid count)",
                        "achieved": 3 * ALGORITHMIC_FLOP_PER_DOF_STAGE * n_pts * k64 / (msv / 1e3) / 1e12,
                        "peak": peak64, "unit": "TFLOP/s",
                        "peak_source": "derived: %d SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz" % n_sm}
