@@ -245,7 +245,7 @@ void free_mesh(sd_mesh* m) {
   void* ptrs[] = {m->own_faces, m->face_k, m->gface64, m->Sfam64, m->invJ64, m->X64, m->Sfam32, m->invJ32, m->X32,
                   m->nbr, m->meta,
                   m->tr64[0], m->tr64[1], m->tr32[0], m->tr32[1], m->dyn, m->diag_part, m->diag_out, m->divb,
-                  m->err, m->grad, m->gtr, m->rvis64, m->grad32, m->gtr32, m->rvis32, m->dyn_s, m->work2, m->wreg32};
+                  m->err, m->grad, m->gtr, m->rvis64, m->grad32, m->mvf32, m->rvis32, m->dyn_s, m->work2, m->wreg32};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (m->host_diag) cudaFreeHost(m->host_diag);
@@ -344,20 +344,24 @@ cudaError_t prepare_viscous_mixed(sd_mesh* m, sd::StageParams& P, const sd_backg
   struct Buf {
     float** p;
     size_t count;
-  } bufs[3] = {{&m->grad32, ne * sd::MV_REC * N3}, {&m->gtr32, ne * 6 * sd::MV_REC * N2}, {&m->rvis32, 7 * ne * N3}};
+  } bufs[3] = {{&m->grad32, ne * sd::MV_REC * N3}, {&m->mvf32, ne * 6 * 7 * N2}, {&m->rvis32, 7 * ne * N3}};
   for (const Buf& b : bufs)
     if (!*b.p) {
       err = cudaMalloc((void**)b.p, b.count * sizeof(float));
       if (err != cudaSuccess) return err;
       m->device_bytes += (int64_t)(b.count * sizeof(float));
     }
-  sd::StageParams Pg = P, Pv = P;
+  if (!bg || !bg->vrec || !bg->vtr) return cudaErrorInvalidValue;
+  // both kernels read the background's viscous record: the gradient kernel its face
+  // traces (grad T0, grad S0 at this side's face points), the residual kernel all of it
+  sd::StageParams Pg = P;
+  Pg.bg_visc = bg->vrec;
+  Pg.bg_vtr = bg->vtr;
+  sd::StageParams Pv = Pg;
   Pg.mgrad_out = m->grad32;
-  Pg.mgtr_out = m->gtr32;
+  Pg.mvf_out = m->mvf32;
   Pv.mgrad = m->grad32;
-  Pv.mgtr_in = m->gtr32;
-  Pv.bg_visc = bg->vrec;
-  Pv.bg_vtr = bg->vtr;
+  Pv.mvf_in = m->mvf32;
   Pv.rvis_out = m->rvis32;
   {
     ProfScope ps(m, PROF_OTHER, s);

@@ -143,14 +143,15 @@ struct StageParams {
   double* gtr_out;
   const double* rvis64;
   double* rvis64_out;
-  // viscous fluxes on the FP32-mixed path: perturbation gradients [e][24][N^3] and their face
-  // traces [e][F][24][N^2], the background's viscous record [7][n_e N^3] (its energy residual, grad T0,
-  // grad S0) and its face traces [e][F][6][N^2], and the viscous residual of the stage state
-  // [7][n_e N^3] (components rho U, E, B) that the mixed stage kernel adds
+  // viscous fluxes on the FP32-mixed path: the perturbation gradient record [e][15][N^3], each
+  // element's own F_vis . n at its face points along its outward unit normal [e][F][7][N^2]
+  // (components rho U, E, B; mvf), the background's viscous record [7][n_e N^3] (its energy
+  // residual, grad T0, grad S0) and its face traces [e][F][6][N^2], and the viscous residual of the
+  // stage state [7][n_e N^3] (components rho U, E, B) that the mixed stage kernel adds
   const float* mgrad;
-  const float* mgtr_in;
+  const float* mvf_in;
   float* mgrad_out;
-  float* mgtr_out;
+  float* mvf_out;
   const float* bg_visc;
   const float* bg_vtr;
   float* rvis_out;
@@ -195,8 +196,8 @@ struct sd_mesh {
   double* grad;             // viscous FP64 path, allocated on first use: the record [e][15][N^3]
   double* gtr;              //   (the background only), its face traces [e][F][15][N^2]
   double* rvis64;           //   and the interior viscous divergence [e][7][N^3]
-  float* grad32;            // viscous FP32-mixed path, allocated on first use: perturbation gradients,
-  float* gtr32;             //   their face traces
+  float* grad32;            // viscous FP32-mixed path, allocated on first use: the gradient record,
+  float* mvf32;             //   each side's F_vis . n at the faces
   float* rvis32;            //   and the viscous residual [7][n_e N^3]
   // five-stage time integrator (sd_phys.rk_scheme), allocated on first use: (dt/r, c_h)
   // for the FP64 stages, a second FP64 stage state, the FP32 register W of the mixed path

@@ -23,9 +23,15 @@
 // linear in grad U and may be formed at the solution points and extrapolated like
 // the gradients themselves), the current J = curl B, grad T' and grad S': the
 // gradient record, MV_REC = 15 values per point.
-// mgrad_kernel writes the record [e][15][N^3] and its face traces [e][F][15][N^2];
+// mgrad_kernel writes the record [e][15][N^3] and, at every face point of the
+// element, its own F_vis . n along its outward unit normal [e][F][7][N^2] (the
+// record extrapolated there, its face trace of q', the background's values);
 // mvisc_kernel writes the viscous residual of the stage state (background's
-// included) [7][n_e N^3] (components rho U, E, B), which the stage kernel adds.
+// included) [7][n_e N^3] (components rho U, E, B), which the stage kernel adds:
+// at a face it averages its own F_vis . n with the neighbour's, whose outward
+// normal is exactly the opposite (the two sides share the owner's metric there).
+// The radiative diffusivity kappa_r(r) of a face point is taken at the owner's
+// face point by both sides.
 // Both are line-blocked like the inviscid stage kernel: the 1D extrapolation and
 // derivative operators run along the lines of the element from registers, two
 // variables at a time in paired FP32 arithmetic, in the even-odd form.
@@ -201,13 +207,14 @@ __device__ __forceinline__ void mv_load_state(const StageParams& P, int64_t e, f
 }
 
 // Extrapolate NV variables (planes of `in` VS floats apart, solution point n at
-// n) along every line of the directions D0 <= d < D1 to the N+1 flux points of
-// the line's family, two variables at a time in paired FP32 arithmetic, in the
+// n) along every line of the directions D0 <= d < D1 to the flux points
+// F0 <= f <= N - F0 of the line's family (F0 = 0: all N + 1; F0 = 1: the
+// interior ones), two variables at a time in paired FP32 arithmetic, in the
 // even-odd form (E[N-f][N-1-i] = E[f][i]): variable v at flux point f of line L
 // of direction d goes to out[f OF + v OV + (d - D0) OD + L].  The tasks
 // (variable pair, line), lines innermost, are spread over the T threads; the
 // lines of line_flip read their points in swapped pairs (fewer bank conflicts).
-template <int N, int T, int NV, int D0, int D1>
+template <int N, int T, int NV, int D0, int D1, int F0 = 0>
 __device__ __forceinline__ void mv_extrap(const float* in, int VS, float* out, int OF, int OV, int OD,
                                           const Ops2& o2) {
   constexpr int N2 = N * N, HP = N / 2, NL = (D1 - D0) * N2, NP = (NV + 1) / 2;
@@ -228,7 +235,7 @@ __device__ __forceinline__ void mv_extrap(const float* in, int VS, float* out, i
     }
     float* X = out + (d - D0) * OD + L;
 #pragma unroll
-    for (int f = 0; 2 * f <= N; ++f) {
+    for (int f = F0; 2 * f <= N; ++f) {
       float2 s = (N & 1) ? mul2(o2.Es[f * N + HP], ql[HP]) : make_float2(0.0f, 0.0f);
       float2 r = make_float2(0.0f, 0.0f);
 #pragma unroll
@@ -258,7 +265,7 @@ __device__ __forceinline__ void mv_extrap(const float* in, int VS, float* out, i
 // same word.
 template <int N, int T, int NV, int D, bool ADD>
 __device__ __forceinline__ void mv_deriv(const float* in, int IF, int IV, float* acc, int AS, const Ops2& o2) {
-  constexpr int N2 = N * N, N3 = N2 * N, NF = N + 1, HF = NF / 2, NP = (NV + 1) / 2;
+  constexpr int N2 = N * N, NF = N + 1, HF = NF / 2, NP = (NV + 1) / 2;
 #pragma unroll 1
   for (int t = threadIdx.x; t < N2 * NP; t += T) {
     const int pr = t / N2, L = t - pr * N2;
@@ -319,6 +326,34 @@ __device__ __forceinline__ void mv_partner(int nb, int mt, int pt, int64_t& nf, 
   p2 = a2 + N * b2;
 }
 
+// Position of point pt of face F of element e at the face's owner (the neighbour
+// nb >= 0 when this side does not own the face; the same point but for periodic
+// images): the map is a polynomial of degree floor(N/2) < N, so the end rows of E
+// give it exactly from the owner's solution points.
+template <int N>
+__device__ __forceinline__ void mv_face_position(const StageParams& P, const Ops2& o2, int64_t e, int F, int pt, int nb,
+                                                 int mt, float* x) {
+  constexpr int N3 = N * N * N;
+  int64_t eo = e;
+  int Fo = F, po = pt;
+  if (nb >= 0 && !meta_owner(mt)) {
+    int64_t nf;
+    mv_partner<N>(nb, mt, pt, nf, po);
+    eo = nb;
+    Fo = meta_nbF(mt);
+  }
+  const int d = Fo >> 1, a = po % N, b = po / N;
+  const float* X = reinterpret_cast<const float*>(P.X) + eo * 3 * N3;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    float s = 0.0f;
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+      s = fmaf((Fo & 1) ? o2.EN[i].x : o2.E0[i].x, __ldg(X + k * N3 + sol_index<N>(d, i, a, b)), s);
+    x[k] = s;
+  }
+}
+
 template <int N>
 struct MVDims {
   static constexpr int N2 = N * N, N3 = N2 * N, NF = N + 1;
@@ -332,10 +367,14 @@ struct MVDims {
   // with line_flip, 1,680 -> 1,104 wavefronts for mvisc_kernel's line reads).
   static constexpr int QS = N3 + ((18 - N3 % 16) % 16);
   // mgrad_kernel: the record [MV_REC][QS] (first the state [11][QS]), then the
-  // flux points of all three families [NF][11][3][N2] (the inviscid kernel's layout)
+  // flux points of all three families [NF][11][3][N2] (the inviscid kernel's layout);
+  // the record at the six faces [6][MV_REC][N2] over the interior flux points'
+  // slots where it fits between the two face blocks (N >= 4), else after them
   static constexpr int gO = 0, gX = (MV_REC * QS + 3) / 4 * 4;
   static constexpr int XD = N2, XV = 3 * N2, XF = 11 * 3 * N2;
-  static constexpr size_t gbytes = (size_t)(gX + NF * XF) * sizeof(float);
+  static constexpr int RF = 6 * MV_REC * N2;
+  static constexpr int gRF = XF + RF <= N * XF ? gX + XF : gX + NF * XF;
+  static constexpr size_t gbytes = (size_t)(gRF + RF > gX + NF * XF ? gRF + RF : gX + NF * XF) * sizeof(float);
   // mvisc_kernel: NQ values at the solution points [NQ][QS], one family's flux
   // points [NF][NQ][N2], the residual [7][QS]
   template <bool KR>
@@ -368,13 +407,20 @@ __global__ void __launch_bounds__(MVDims<N>::T, MVDims<N>::minb(MVDims<N>::gbyte
   if (tid < 6) {
     sNb[tid] = __ldg(P.nbr + e * 6 + tid);
     sMt[tid] = __ldg(P.meta + e * 6 + tid);
-  } else if (tid >= 32 && tid < 32 + 6) {
-    // L2 prefetch of the neighbours' traces that the face points read
+  } else if (tid >= 32 && tid < 32 + 8) {
+    // L2 prefetch of the neighbours' traces that the face points read, and of the
+    // element's own traces of q' and of grad T0, grad S0 (the face fluxes at the end)
     const int k = tid - 32;
-    const int nb = __ldg(P.nbr + e * 6 + k), mt = __ldg(P.meta + e * 6 + k);
-    if (nb >= 0)
-      l2_prefetch(reinterpret_cast<const float*>(P.tr_in) + ((int64_t)nb * 6 + meta_nbF(mt)) * 9 * N2,
-                  9 * N2 * sizeof(float));
+    if (k < 6) {
+      const int nb = __ldg(P.nbr + e * 6 + k), mt = __ldg(P.meta + e * 6 + k);
+      if (nb >= 0)
+        l2_prefetch(reinterpret_cast<const float*>(P.tr_in) + ((int64_t)nb * 6 + meta_nbF(mt)) * 9 * N2,
+                    9 * N2 * sizeof(float));
+    } else if (k == 6) {
+      l2_prefetch(reinterpret_cast<const float*>(P.tr_in) + e * 6 * 9 * N2, 6 * 9 * N2 * sizeof(float));
+    } else {
+      l2_prefetch(P.bg_vtr + e * 6 * 6 * N2, 6 * 6 * N2 * sizeof(float));
+    }
   }
   mv_load_state<N>(P, e, sO, T, QS);
   __syncthreads();
@@ -498,7 +544,8 @@ __global__ void __launch_bounds__(MVDims<N>::T, MVDims<N>::minb(MVDims<N>::gbyte
     }
   }
   __syncthreads();
-  // face traces of the record: both ends of every line, two values at a time
+  // the record at both ends of every line, two values at a time -> sRF[F][k][L]
+  float* sRF = reinterpret_cast<float*>(smem_raw) + MD::gRF;
   constexpr int NL = 3 * N2, NP = (MV_REC + 1) / 2;
 #pragma unroll 1
   for (int t = tid; t < NL * NP; t += T) {
@@ -514,7 +561,7 @@ __global__ void __launch_bounds__(MVDims<N>::T, MVDims<N>::minb(MVDims<N>::gbyte
       s0 = fma2(o2.E0[i], x[i], s0);
       s1 = fma2(o2.EN[i], x[i], s1);
     }
-    float* Tr = P.mgtr_out + (e * 6 + 2 * d) * MV_REC * N2 + L;
+    float* Tr = sRF + (2 * d) * MV_REC * N2 + L;
     Tr[v0 * N2] = s0.x;
     Tr[MV_REC * N2 + v0 * N2] = s1.x;
     if (v1 != v0) {
@@ -522,13 +569,49 @@ __global__ void __launch_bounds__(MVDims<N>::T, MVDims<N>::minb(MVDims<N>::gbyte
       Tr[MV_REC * N2 + v1 * N2] = s1.y;
     }
   }
+  __syncthreads();
+  // this side's F_vis . n at every face point, n its outward unit normal: its face
+  // trace of q', rho0 and p0 at the face flux point (sX slots 9 and 10, which the
+  // w' phase leaves), the record there, the background's grad T0 and grad S0
+#pragma unroll 1
+  for (int t = tid; t < 6 * N2; t += T) {
+    const int F = t / N2, L = t - F * N2, d = F >> 1, f = (F & 1) ? N : 0;
+    float q[9], rec[MV_REC], gT0[3], gS0[3], Fv[7];
+    const float* To = reinterpret_cast<const float*>(P.tr_in) + (e * 6 + F) * 9 * N2 + L;
+#pragma unroll
+    for (int v = 0; v < 9; ++v) q[v] = __ldg(To + v * N2);
+    const float* Xf = sX + f * XF + d * XD + L;
+    const float r0 = Xf[9 * XV], p0 = Xf[10 * XV];
+#pragma unroll
+    for (int k = 0; k < MV_REC; ++k) rec[k] = sRF[(F * MV_REC + k) * N2 + L];
+    const float* Bv = P.bg_vtr + (e * 6 + F) * 6 * N2 + L;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      gT0[k] = __ldg(Bv + k * N2);
+      gS0[k] = __ldg(Bv + (3 + k) * N2);
+    }
+    const float* Sp = Sfam + s32_index(N, d, f, 0, L);
+    const float Sx = __ldg(Sp), Sy = __ldg(Sp + N2), Sz = __ldg(Sp + 2 * N2);
+    const float im = 1.0f / sqrtf(Sx * Sx + Sy * Sy + Sz * Sz), sg = (f == N) ? 1.0f : -1.0f;
+    float kr = c.kappa_r;
+    if (c.kr_varies) {
+      float xo[3];
+      mv_face_position<N>(P, o2, e, F, L, sNb[F], sMt[F], xo);
+      kr = mv_kappa_r(c, xo[0], xo[1], xo[2]);
+    }
+    mv_flux(q, r0, p0, rec, gT0, gS0, sg * Sx * im, sg * Sy * im, sg * Sz * im, c, kr, Fv);
+    float* Out = P.mvf_out + (e * 6 + F) * 7 * N2 + L;
+#pragma unroll
+    for (int v = 0; v < 7; ++v) Out[v * N2] = Fv[v];
+  }
 }
 
 // One family of the viscous flux: S^d . F_vis at the flux points of family D
 // (values at flux point (f, L) read from X[f NQ N^2 + v N^2 + L], the flux
-// written over its first seven values).  At the element faces the common flux is
-// the average of both sides' F_vis . n (the neighbour's from its traces about its
-// own background), at a wall this side's alone.
+// written over its first seven values; the state is not extrapolated to the two
+// faces).  At the element faces the common flux is the average of both sides'
+// F_vis . n as their gradient kernels wrote them (each about its own
+// background), at a wall this side's alone.
 template <int N, bool KR, int D>
 __device__ __forceinline__ void mv_family_flux(const StageParams& P, const MViscCoef& c, int64_t e, const float* Sfam,
                                                float* X, const int* sNb, const int* sMt) {
@@ -538,46 +621,32 @@ __device__ __forceinline__ void mv_family_flux(const StageParams& P, const MVisc
   for (int t = threadIdx.x; t < NF * N2; t += T) {
     const int f = t / N2, L = t - f * N2;
     float* Xp = X + f * NQ * N2 + L;
-    float x[NQ];
-#pragma unroll
-    for (int v = 0; v < NQ; ++v) x[v] = Xp[v * N2];
     const float* Sp = Sfam + s32_index(N, D, f, 0, L);
     const float Sx = __ldg(Sp), Sy = __ldg(Sp + N2), Sz = __ldg(Sp + 2 * N2);
-    const float kr = KR ? mv_kappa_r(c, x[Q_X], x[Q_X + 1], x[Q_X + 2]) : c.kappa_r;
     float Fv[7];
     if (f > 0 && f < N) {
+      float x[NQ];
+#pragma unroll
+      for (int v = 0; v < NQ; ++v) x[v] = Xp[v * N2];
+      const float kr = KR ? mv_kappa_r(c, x[Q_X], x[Q_X + 1], x[Q_X + 2]) : c.kappa_r;
       mv_flux(x, x[Q_R0], x[Q_P0], x + Q_REC, x + Q_GT0, x + Q_GS0, Sx, Sy, Sz, c, kr, Fv);
     } else {
+      // this side's F_vis . n and the neighbour's F_vis . n_nb (n_nb = -n exactly), both as
+      // the gradient kernels wrote them; scaled to S^d along this side's direction
       const int F = 2 * D + (f == N);
-      const float mag = sqrtf(Sx * Sx + Sy * Sy + Sz * Sz), im = 1.0f / mag, sg = (f == N) ? 1.0f : -1.0f;
-      const float nx = sg * Sx * im, ny = sg * Sy * im, nz = sg * Sz * im;
-      mv_flux(x, x[Q_R0], x[Q_P0], x + Q_REC, x + Q_GT0, x + Q_GS0, nx, ny, nz, c, kr, Fv);
       const int nb = sNb[F], mt = sMt[F];
+      const float* Fo = P.mvf_in + (e * 6 + F) * 7 * N2 + L;
+#pragma unroll
+      for (int v = 0; v < 7; ++v) Fv[v] = Fo[v * N2];
       if (nb >= 0) {
         int64_t nf;
         int pn;
         mv_partner<N>(nb, mt, L, nf, pn);
-        float q2[9], g2[MV_REC], gT2[3], gS2[3], F2[7];
-        const float* Tn = reinterpret_cast<const float*>(P.tr_in) + nf * 9 * N2 + pn;
+        const float* Fn = P.mvf_in + nf * 7 * N2 + pn;
 #pragma unroll
-        for (int v = 0; v < 9; ++v) q2[v] = Tn[v * N2];
-        const float* Gn = P.mgtr_in + nf * MV_REC * N2 + pn;
-#pragma unroll
-        for (int k = 0; k < MV_REC; ++k) g2[k] = Gn[k * N2];
-        const float* Bn = P.bg_vtr + nf * 6 * N2 + pn;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          gT2[k] = __ldg(Bn + k * N2);
-          gS2[k] = __ldg(Bn + (3 + k) * N2);
-        }
-        const int64_t gidx = e * 6 + F;
-        const float r2 = x[Q_R0] + __ldg(P.bg_jump + (gidx * 2 + 0) * N2 + L);
-        const float p2 = x[Q_P0] + __ldg(P.bg_jump + (gidx * 2 + 1) * N2 + L);
-        mv_flux(q2, r2, p2, g2, gT2, gS2, nx, ny, nz, c, kr, F2);
-#pragma unroll
-        for (int v = 0; v < 7; ++v) Fv[v] = 0.5f * (Fv[v] + F2[v]);
+        for (int v = 0; v < 7; ++v) Fv[v] = 0.5f * (Fv[v] - Fn[v * N2]);
       }
-      const float sm = sg * mag;
+      const float sm = ((f == N) ? 1.0f : -1.0f) * sqrtf(Sx * Sx + Sy * Sy + Sz * Sz);
 #pragma unroll
       for (int v = 0; v < 7; ++v) Fv[v] *= sm;
     }
@@ -585,6 +654,7 @@ __device__ __forceinline__ void mv_family_flux(const StageParams& P, const MVisc
     for (int v = 0; v < 7; ++v) Xp[v * N2] = Fv[v];
   }
 }
+
 
 // The viscous residual of the stage state, R_vis = div(S^d . F_vis)/|J|, the
 // background's included: out [7][n_e N^3] (components rho U, E, B).  Family by
@@ -609,19 +679,15 @@ __global__ void __launch_bounds__(MVDims<N>::TV, MVDims<N>::minb(MVDims<N>::temp
   if (tid < 6) {
     sNb[tid] = __ldg(P.nbr + e * 6 + tid);
     sMt[tid] = __ldg(P.meta + e * 6 + tid);
-  } else if (tid >= 32 && tid < 32 + 18) {
-    // L2 prefetch of what the face fluxes read from the neighbours: their traces
-    // of q', of the record and of the background gradients
-    const int k = (tid - 32) % 6, which = (tid - 32) / 6;
-    const int nb = __ldg(P.nbr + e * 6 + k), mt = __ldg(P.meta + e * 6 + k);
-    if (nb >= 0) {
-      const int64_t nf = (int64_t)nb * 6 + meta_nbF(mt);
-      if (which == 0)
-        l2_prefetch(reinterpret_cast<const float*>(P.tr_in) + nf * 9 * N2, 9 * N2 * sizeof(float));
-      else if (which == 1)
-        l2_prefetch(P.mgtr_in + nf * MV_REC * N2, MV_REC * N2 * sizeof(float));
-      else
-        l2_prefetch(P.bg_vtr + nf * 6 * N2, 6 * N2 * sizeof(float));
+  } else if (tid >= 32 && tid < 32 + 7) {
+    // L2 prefetch of what the face fluxes read: the neighbours' own F_vis . n at
+    // the shared faces, and this element's
+    const int k = tid - 32;
+    if (k < 6) {
+      const int nb = __ldg(P.nbr + e * 6 + k), mt = __ldg(P.meta + e * 6 + k);
+      if (nb >= 0) l2_prefetch(P.mvf_in + ((int64_t)nb * 6 + meta_nbF(mt)) * 7 * N2, 7 * N2 * sizeof(float));
+    } else {
+      l2_prefetch(P.mvf_in + e * 6 * 7 * N2, 6 * 7 * N2 * sizeof(float));
     }
   }
   mv_load_state<N>(P, e, sQ, T, QS);
@@ -639,19 +705,19 @@ __global__ void __launch_bounds__(MVDims<N>::TV, MVDims<N>::minb(MVDims<N>::temp
   }
   constexpr int OF = NQ * N2;
   __syncthreads();
-  mv_extrap<N, T, NQ, 0, 1>(sQ, QS, sX, OF, N2, 0, o2);
+  mv_extrap<N, T, NQ, 0, 1, 1>(sQ, QS, sX, OF, N2, 0, o2);
   __syncthreads();
   mv_family_flux<N, KR, 0>(P, c, e, Sfam, sX, sNb, sMt);
   __syncthreads();
   mv_deriv<N, T, 7, 0, false>(sX, OF, N2, sR, QS, o2);
   __syncthreads();
-  mv_extrap<N, T, NQ, 1, 2>(sQ, QS, sX, OF, N2, 0, o2);
+  mv_extrap<N, T, NQ, 1, 2, 1>(sQ, QS, sX, OF, N2, 0, o2);
   __syncthreads();
   mv_family_flux<N, KR, 1>(P, c, e, Sfam, sX, sNb, sMt);
   __syncthreads();
   mv_deriv<N, T, 7, 1, true>(sX, OF, N2, sR, QS, o2);
   __syncthreads();
-  mv_extrap<N, T, NQ, 2, 3>(sQ, QS, sX, OF, N2, 0, o2);
+  mv_extrap<N, T, NQ, 2, 3, 1>(sQ, QS, sX, OF, N2, 0, o2);
   __syncthreads();
   mv_family_flux<N, KR, 2>(P, c, e, Sfam, sX, sNb, sMt);
   __syncthreads();
@@ -675,6 +741,10 @@ cudaError_t launch_mixed_visc_t(const StageParams& Pg, const StageParams& Pv, co
                                 cudaStream_t s) {
   using MD = MVDims<N>;
   if (Pg.n_e == 0) return cudaSuccess;
+  // every buffer the two kernels address (a missing one is a caller's error, not a fault)
+  if (!Pg.tr_in || !Pg.bg || !Pg.bg_jump || !Pg.bg_vtr || !Pg.mgrad_out || !Pg.mvf_out || !Pv.mgrad || !Pv.mvf_in ||
+      !Pv.bg_visc || !Pv.rvis_out)
+    return cudaErrorInvalidValue;
   const bool kr = Pv.kappa_r1 != 0.0 || Pv.kappa_r2 != 0.0;
   auto kv = kr ? mvisc_kernel<N, true> : mvisc_kernel<N, false>;
   const size_t vbytes = kr ? MD::template V<true>::bytes : MD::template V<false>::bytes;

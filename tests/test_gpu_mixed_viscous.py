@@ -183,3 +183,19 @@ def test_mixed_viscous_radius_dependent_kappa_r(N):
     assert np.abs(Ro - R1).max() > 1e-3 * np.abs(Ro).max()
     ok, err, ref = _strict(R, Ro, "kappa_r(r) shell N=%d" % N)
     assert ok, (err, ref)
+
+
+@pytest.mark.parametrize("N", [3, 5])
+def test_mixed_viscous_radius_dependent_kappa_r_periodic_box(N):
+    """kappa_r(r) on the jittered periodic box, whose periodic faces join points at different radii:
+    both sides take the owner's face point (reading V7), so the face flux is one value."""
+    gm, om, q0, qb = _box(N, 30 + N)
+    gph, oph = _phys(powell=1, c_h=0.7, glm_alpha=0.3, **VISC_R)
+    bg = gm.background(gph, gm.to_device(qb))
+    R = gm.to_host(gm.residual(gph, gm.to_device(q0), prec=sdmhd.SD_FP32_MIXED, bg=bg))
+    Ro, _ = om.residual(oph, q0)
+    R1, _ = om.residual(sdref.Phys(**dict(vars(oph), kappa_r1=0.0, kappa_r2=0.0)), q0)
+    assert np.abs(Ro - R1).max() > 1e-3 * np.abs(Ro).max()
+    ok, err, ref = _strict(R, Ro, "kappa_r(r) periodic box N=%d" % N)
+    assert ok, (err, ref)
+
