@@ -252,3 +252,60 @@ def test_shell41k_mixed_viscous_residual_sampled():
     R = _gather(gm, gm.residual(gph, gm.to_device(q0), prec=sdmhd.SD_FP32_MIXED, bg=bg), elems)
     ok, err, bound = _mixed_bound(R, Ro, None, floor=(), label="41k viscous residual developed", var_axis=1)
     assert ok, (err, bound)
+
+
+_last_dts = []  # (dt, c_h) of each step of the last _advance_vs_oracle call
+
+
+def _advance_vs_oracle(gm, om, gph, oph, q0, qb, steps, cfl, stepper):
+    """sd_advance of `steps` FP32-mixed steps against the oracle's steps (`stepper`) given each
+    step's dt and c_h; returns (gpu change, oracle change)"""
+    bg = gm.background(gph, gm.to_device(qb))
+    q, work = gm.to_device(q0), gm.empty_state()
+    dts = torch.zeros(2 * steps, dtype=torch.float64, device="cuda")
+    gm.advance(gph, cfl, steps, q, work, prec=sdmhd.SD_FP32_MIXED, bg=bg, dt_out=dts)
+    d = dts.cpu().numpy()
+    _last_dts[:] = [(float(d[2 * k]), float(d[2 * k + 1])) for k in range(steps)]
+    qo = q0
+    for k in range(steps):
+        oph.c_h = float(d[2 * k + 1])
+        qo = stepper(oph, float(d[2 * k]), qo)
+    return gm.to_host(q) - q0, qo - q0
+
+
+def test_shell41k_mixed_ssprk53_advance_developed_flow():
+    """The five-stage SSPRK(5,3) through sd_advance at full size and CFL 0.5 (the bench's ssprk53
+    leg), from the shell with a seeded flow: every variable's change within 1e-5 of its largest
+    value."""
+    gm, om = _shell(24, 12)
+    kw = dict(gamma=5.0 / 3.0, GM=1.0, omega=1.0, glm_alpha=1.0, c_h=0.0, powell=1, gravity=1, coriolis=1)
+    gph, oph = sdmhd.Phys(rk_scheme=sdmhd.RK_SSP53, **kw), sdref.Phys(**kw)
+    prm = [3.0, 0.70, 0.98, 1.0, 1.0, 1e-4, 1e-6]
+    q0, qb = om.state_init(oph, sdref.INIT_SHELL_POLYTROPE, prm, seed=0, background=True)
+    _flow(q0, 45)
+    g, o = _advance_vs_oracle(gm, om, gph, oph, q0, qb, 2, 0.5, om.rk53_step)
+    ok, err, bound = _mixed_bound(g, o, None, floor=(), label="41k ssprk53 x2 developed")
+    assert ok, (err, bound)
+
+
+def test_shell41k_mixed_viscous_advance_developed_flow():
+    """The viscous FP32-mixed path through sd_advance at full size, from the shell with a seeded flow,
+    at CFL 0.05 and mu = eta = kappa = kappa_r = 1e-4 (explicitly stable for the grid-scale modes of
+    the flow): every variable's change within 1e-5 of its largest value, the viscous terms a visible
+    part of it."""
+    gm, om = _shell(24, 12)
+    kw = dict(gamma=5.0 / 3.0, GM=1.0, omega=1.0, glm_alpha=1.0, c_h=0.0, powell=1, gravity=1, coriolis=1)
+    visc = dict(viscous=1, mu=1e-4, eta=1e-4, kappa=1e-4, kappa_r=1e-4, R_gas=1.0)
+    gph, oph = sdmhd.Phys(**kw, **visc), sdref.Phys(**kw, **visc)
+    prm = [3.0, 0.70, 0.98, 1.0, 1.0, 1e-4, 1e-3]
+    q0, qb = om.state_init(oph, sdref.INIT_SHELL_POLYTROPE, prm, seed=0, background=True)
+    _flow(q0, 46)
+    g, o = _advance_vs_oracle(gm, om, gph, oph, q0, qb, 2, 0.05, om.rk_step)
+    ok, err, bound = _mixed_bound(g, o, None, floor=(), label="41k viscous x2 developed")
+    assert ok, (err, bound)
+    # the same two steps without the viscous terms differ visibly in the momentum
+    qi = q0
+    for dt, ch in _last_dts:
+        qi = om.rk_step(sdref.Phys(**dict(kw, c_h=ch)), dt, qi)
+    dm = np.abs(o[1:4] - (qi - q0)[1:4]).max() / np.abs(o[1:4]).max()
+    assert dm > 1e-3, dm
