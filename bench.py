@@ -48,11 +48,12 @@ WORKLOADS = {
 CFL = 0.2
 GLM_ALPHA = 1.0
 # coefficients of the viscous legs, and their CFL number: the step control takes the advective limit
-# only, and with these coefficients the grid-scale diffusive modes near the top of the N_rho = 3 shell
-# (nu = mu / rho largest) grow without bound at CFL 0.2 (NaN within 10 steps) and 0.1 (slowly); 0.05
-# keeps them bounded.  The work of a step does not depend on dt, so neither does DOF-updates/s.
+# only, and with these coefficients the stiff diffusive modes of the viscous stress near the top of the
+# N_rho = 3 shell (nu = mu / rho largest) grow: at CFL 0.2 to NaN within 10 steps, at 0.05 and 0.02
+# slowly (over 200 steps the kinetic energy 200 and 6 times that of the inviscid run), at 0.01 barely
+# (1.5 times).  The work of a step does not depend on dt, so neither does DOF-updates/s.
 VISCOUS = dict(viscous=1, mu=1e-4, eta=1e-4, kappa=1e-4, kappa_r=1e-4, R_gas=1.0)
-VISCOUS_CFL = 0.05
+VISCOUS_CFL = 0.01
 
 
 def parse():
@@ -74,6 +75,10 @@ def parse():
     ap.add_argument("--accuracy-oracle-steps", type=int, default=0,
                     help="steps of the FP32-mixed path against the FP64 oracle itself on the workload's shell "
                          "(off by default: the oracle takes about 0.9 s per step of the 41,472-element shell)")
+    ap.add_argument("--viscous-accuracy-steps", type=int, default=0,
+                    help="steps of the viscous FP32-mixed path against the viscous FP64 path on the workload's "
+                         "shell at the viscous legs' CFL (off by default: about 0.14 s of FP64 per step of the "
+                         "41,472-element shell)")
     ap.add_argument("--largest-steps", type=int, default=50)
     ap.add_argument("--serve-requests", type=int, default=64)
     ap.add_argument("--serve-budget-gb", type=float, default=24.0)
@@ -552,6 +557,44 @@ def accuracy_report(steps: int = 20):
             "max_divb_mixed": dm["max_divb"], "max_divb_fp64": d64["max_divb"]}
 
 
+def accuracy_viscous_mixed_vs_fp64(mesh, phys, q0, params, steps: int):
+    """The viscous FP32-mixed path against the viscous FP64 path over `steps` SSP-RK3 steps at the
+    viscous legs' coefficients and CFL: the mixed run takes dt and c_h from its own lambda_max (one
+    sd_advance call), the FP64 run repeats that sequence with fixed-dt steps.  Per variable
+    max|dq_mixed - dq_fp64| / max|dq_fp64|, dq the change over the steps; energy, KE, magnetic
+    energy and max|div B| of both."""
+    import torch
+
+    from paper_2502_17805_gb300 import sdmhd
+    phys_v = sdmhd.Phys(**{k: getattr(phys, k) for k in ("gamma", "GM", "omega", "glm_alpha", "c_h", "powell",
+                                                        "gravity", "coriolis")}, **VISCOUS)
+    work, bgs = mesh.empty_state(), mesh.empty_state()
+    mesh.state_init(phys_v, sdmhd.INIT_SHELL_POLYTROPE, params, seed=0, q=work, background=bgs)
+    bg_v = mesh.background(phys_v, bgs)
+    del bgs
+    q = q0.clone()
+    dts = torch.zeros(2 * steps, dtype=torch.float64, device="cuda")
+    d0 = mesh.diagnostics(phys_v, q0)
+    mesh.advance(phys_v, VISCOUS_CFL, steps, q, work, prec=sdmhd.SD_FP32_MIXED, bg=bg_v, dt_out=dts)
+    d = dts.cpu().numpy()
+    q64 = q0.clone()
+    for k in range(steps):
+        mesh.rk_step(sdmhd.Phys(**dict(vars(phys_v), c_h=float(d[2 * k + 1]))), float(d[2 * k]), q64, work)
+    n3 = mesh.N ** 3
+    dm = (q - q0)[:, :, :n3].reshape(9, -1)
+    d64 = (q64 - q0)[:, :, :n3].reshape(9, -1)
+    err = ((dm - d64).abs().amax(dim=1) / d64.abs().amax(dim=1).clamp_min(1e-300)).cpu().tolist()
+    gm, g64 = mesh.diagnostics(phys_v, q), mesh.diagnostics(phys_v, q64)
+    names = ["rho", "mx", "my", "mz", "E", "Bx", "By", "Bz", "psi"]
+    return {"steps": steps, "cfl": VISCOUS_CFL, "t_end": float(d[0::2].sum()),
+            "coefficients": {k: v for k, v in VISCOUS.items() if k != "viscous"},
+            "mixed_vs_fp64_rel_err_of_change": dict(zip(names, err)), "max_rel_err_of_change": max(err),
+            "energy_drift_mixed": gm["energy"] / d0["energy"] - 1.0,
+            "energy_drift_fp64": g64["energy"] / d0["energy"] - 1.0,
+            "ke_mixed": gm["ke"], "ke_fp64": g64["ke"], "eb_mixed": gm["eb"], "eb_fp64": g64["eb"],
+            "max_divb_mixed": gm["max_divb"], "max_divb_fp64": g64["max_divb"]}
+
+
 def accuracy_vs_oracle_shell(wl_key: str, steps: int):
     """The FP32-mixed path against the FP64 oracle itself (OpenMP over elements on the host cores)
     over `steps` SSP-RK3 steps of a workload's shell from the oracle's initial state: the mixed run
@@ -870,6 +913,9 @@ def run_ours(args):
         out["accuracy"] = accuracy_fp32_vs_fp64(mesh, phys, q0, bg, args.accuracy_steps)
         if args.accuracy_oracle_steps > 0:
             out["accuracy_oracle"] = accuracy_vs_oracle_shell(args.workload, args.accuracy_oracle_steps)
+        if args.viscous_accuracy_steps > 0:
+            out["accuracy_viscous"] = accuracy_viscous_mixed_vs_fp64(mesh, phys, q0, params,
+                                                                   args.viscous_accuracy_steps)
         out["accuracy"]["workload"] = wl["desc"]
     if rank == 0 and world == 1 and not args.no_largest:
         del q, work, q64, q2
