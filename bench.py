@@ -47,13 +47,15 @@ WORKLOADS = {
 }
 CFL = 0.2
 GLM_ALPHA = 1.0
-# coefficients of the viscous legs, and their CFL number: the step control takes the advective limit
-# only, and with these coefficients the stiff diffusive modes of the viscous stress near the top of the
-# N_rho = 3 shell (nu = mu / rho largest) grow: at CFL 0.2 to NaN within 10 steps, at 0.05 and 0.02
-# slowly (over 200 steps the kinetic energy 200 and 6 times that of the inviscid run), at 0.01 barely
-# (1.5 times).  The work of a step does not depend on dt, so neither does DOF-updates/s.
-VISCOUS = dict(viscous=1, mu=1e-4, eta=1e-4, kappa=1e-4, kappa_r=1e-4, R_gas=1.0)
-VISCOUS_CFL = 0.01
+# coefficients of the viscous legs and their step limits: the advective CFL of the other legs and the
+# library's diffusive limit dt <= visc_cfl dx_min^2 / nu_max (sd_phys.visc_cfl).  With these coefficients
+# the stiff modes of the viscous stress near the top of the N_rho = 3 shell (nu = mu / rho largest) grow
+# under the advective limit alone: at CFL 0.2 to NaN within 10 steps, at 0.05 and 0.02 slowly (over
+# 200 steps the kinetic energy 200 and 6 times that of the inviscid run), at 0.01 barely (1.5 times);
+# visc_cfl 0.0157 gives the step of CFL 0.01 on this shell.  The work of a step does not depend on dt,
+# so neither does DOF-updates/s.
+VISCOUS = dict(viscous=1, mu=1e-4, eta=1e-4, kappa=1e-4, kappa_r=1e-4, R_gas=1.0, visc_cfl=0.015)
+VISCOUS_CFL = CFL
 
 
 def parse():
@@ -587,7 +589,8 @@ def accuracy_viscous_mixed_vs_fp64(mesh, phys, q0, params, steps: int):
     gm, g64 = mesh.diagnostics(phys_v, q), mesh.diagnostics(phys_v, q64)
     names = ["rho", "mx", "my", "mz", "E", "Bx", "By", "Bz", "psi"]
     return {"steps": steps, "cfl": VISCOUS_CFL, "t_end": float(d[0::2].sum()),
-            "coefficients": {k: v for k, v in VISCOUS.items() if k != "viscous"},
+            "coefficients": {k: v for k, v in VISCOUS.items() if k not in ("viscous", "visc_cfl")},
+            "visc_cfl": VISCOUS["visc_cfl"],
             "mixed_vs_fp64_rel_err_of_change": dict(zip(names, err)), "max_rel_err_of_change": max(err),
             "energy_drift_mixed": gm["energy"] / d0["energy"] - 1.0,
             "energy_drift_fp64": g64["energy"] / d0["energy"] - 1.0,
@@ -803,7 +806,7 @@ def run_ours(args):
     if not args.no_viscous:
         phys_v = sdmhd.Phys(**{k: getattr(phys, k) for k in ("gamma", "GM", "omega", "glm_alpha", "c_h", "powell",
                                                             "gravity", "coriolis")}, **VISCOUS)
-        coef = {k: v for k, v in VISCOUS.items() if k != "viscous"}
+        coef = {k: v for k, v in VISCOUS.items() if k not in ("viscous", "visc_cfl")}
         wv = min(args.warmup, 3)
         qv = q0.clone()
         msv, profv, _ = time_steps(mesh, phys_v, qv, work, sdmhd.SD_FP64, None, k64, wv, None, barrier,
@@ -837,7 +840,7 @@ def run_ours(args):
         visc64_roof["counted_frac"] = visc64_roof["counted_tflops"] / peak64 if counted_v else None
         visc = {"value": whole_job_rate(n_pts, k64, world, msv), "unit": UNIT, "steps": k64, "ms_per_step": msv / k64,
                 "roofline": visc64_roof,
-                "dtype": "f64", "coefficients": coef, "cfl": VISCOUS_CFL,
+                "dtype": "f64", "coefficients": coef, "cfl": VISCOUS_CFL, "visc_cfl": VISCOUS["visc_cfl"],
                 "kernel_ms_per_step": {"stage": profv["stage_ms"] / k64,
                                        "gradients_and_control": profv["other_ms"] / k64,
                                        "trace_lambda": profv["trace_ms"] / k64}}
@@ -852,7 +855,7 @@ def run_ours(args):
         visc_mixed = {"value": whole_job_rate(n_pts, k64, world, msm), "unit": UNIT, "steps": k64,
                       "roofline": visc_roof,
                       "ms_per_step": msm / k64, "dtype": "f32 (perturbation) + f64 (background, RK state)",
-                      "coefficients": coef, "cfl": VISCOUS_CFL,
+                      "coefficients": coef, "cfl": VISCOUS_CFL, "visc_cfl": VISCOUS["visc_cfl"],
                       "kernel_ms_per_step": {"stage": profm["stage_ms"] / k64,
                                              "viscous_gradients_fluxes_and_control": profm["other_ms"] / k64,
                                              "trace_lambda": profm["trace_ms"] / k64},

@@ -133,10 +133,10 @@ typedef struct {
    * term (constants), kappa_r radiative diffusivity (with kappa_r1 and kappa_r2 below: kappa_r(r) =
    * kappa_r + kappa_r1 r + kappa_r2 r^2, r = |x| at the point of the heat flux; the caller keeps it
    * non-negative on the mesh), R_gas specific gas constant (T = p / (rho R_gas), C_p = gamma R_gas /
-   * (gamma - 1)).  The time step of sd_step stays the inviscid one: the caller keeps cfl within the
-   * viscous limit (measured on the 41,472-element N = 6 shell, N_rho = 3, with mu = 1e-4 and SSP-RK3:
-   * the stiff modes of the viscous stress reach NaN within 10 steps at cfl 0.2 and stay near the
-   * inviscid run's level at 0.01; the limit scales as the grid spacing squared over mu / rho_min). */
+   * (gamma - 1)).  The time step of sd_step is the inviscid one unless visc_cfl (below) is set: the
+   * caller then keeps cfl within the viscous limit (measured on the 41,472-element N = 6 shell,
+   * N_rho = 3, with mu = 1e-4 and SSP-RK3: the stiff modes of the viscous stress reach NaN within 10
+   * steps at cfl 0.2 and stay near the inviscid run's level at 0.01). */
   double mu, eta, kappa, kappa_r, R_gas;
   int32_t viscous;
   int32_t pad2_;
@@ -151,6 +151,16 @@ typedef struct {
   int32_t visc_walls;
   int32_t pad3_;
   double kappa_r1, kappa_r2; /* radius dependence of kappa_r (Sec. Benchmark Problem Definition) */
+  /* Diffusive limit of the step (not in the paper; viscous != 0 only; 0 = off): sd_step and
+   * sd_advance take dt = min(cfl dx_min / lambda_max, visc_cfl dx_min^2 / nu_max), nu_max the
+   * largest diffusivity of the step's start state over the solution points,
+   * max(4/3 mu / rho, eta, kappa, gamma kappa_r(r)), dx_min the smallest solution-point spacing.
+   * One reduction over the state per step.  Measured with SSP-RK3 on the 41,472-element N = 6
+   * shell (N_rho = 3, mu = eta = kappa = kappa_r = 1e-4): 0.0157 gives the step at which the stiff
+   * modes of the viscous stress stay near the inviscid run's level over 200 steps; twice and four
+   * times that let them grow.  SSPRK(5,3)'s stability interval on the negative real axis is 2.47
+   * times SSP-RK3's. */
+  double visc_cfl;
 } sd_phys;
 
 typedef struct {
@@ -274,7 +284,8 @@ sd_status sd_rk_stage(const sd_mesh* mesh, const sd_phys* phys, sd_precision pre
 
 /* One full SSP-RK3 step with device-side step control: lambda_max of q (max of
  * |U| + fast speed over the solution points), dt = cfl * dx_min / lambda_max with
- * dx_min = h_min (X_s,2 - X_s,1) the smallest solution-point spacing,
+ * dx_min = h_min (X_s,2 - X_s,1) the smallest solution-point spacing (with
+ * the viscous terms and phys->visc_cfl > 0 at most visc_cfl dx_min^2 / nu_max),
  * c_h = lambda_max when phys->c_h <= 0 (else phys->c_h), then the three fused
  * stages.  q (in/out) and work: device states; dt_out: device double[2] or NULL,
  * receives (dt, c_h).  SD_FP32_MIXED keeps no FP64 intermediate state: the

@@ -415,6 +415,8 @@ sd_status check_common(const sd_mesh* m, const sd_phys* ph, int prec, const sd_b
   if (prec != SD_FP64 && prec != SD_FP32_MIXED) return fail(SD_ERR_INVALID_ARGUMENT, "unknown precision");
   if (ph->rk_scheme != SD_RK_SSP33 && ph->rk_scheme != SD_RK_SSP53)
     return fail(SD_ERR_INVALID_ARGUMENT, "rk_scheme must be SD_RK_SSP33 or SD_RK_SSP53");
+  if (!(ph->visc_cfl >= 0.0) || !isfinite(ph->visc_cfl))
+    return fail(SD_ERR_INVALID_ARGUMENT, "visc_cfl must be finite and not negative");
   if (!(ph->gamma > 1.0)) return fail(SD_ERR_INVALID_ARGUMENT, "gamma must exceed 1");
   if (ph->viscous) {
     if (prec == SD_FP32_MIXED) {
@@ -1161,7 +1163,9 @@ static sd_status advance53_impl(sd_mesh* mm, const sd_phys* ph, sd_precision pre
     }
     {
       ProfScope ps(mm, PROF_OTHER, s);
-      SD_CUDA(sd::launch_step_control(mm, cfl, ph->c_h, dt_out ? dt_out + 2 * (int64_t)k : nullptr, s, mm->dyn_s, c));
+      if (ph->viscous && ph->visc_cfl > 0.0) SD_CUDA(sd::launch_visc_numax(mm, ph, q, s));
+      SD_CUDA(sd::launch_step_control(mm, cfl, ph->c_h, dt_out ? dt_out + 2 * (int64_t)k : nullptr, s, mm->dyn_s, c,
+                                      ph->viscous ? ph->visc_cfl : 0.0));
     }
     // stage 1: y2 = q + c dt L(q)
     sd::StageParams S = stage_params();
@@ -1280,7 +1284,9 @@ static sd_status advance_impl(sd_mesh* mm, const sd_phys* ph, sd_precision prec,
     }
     {
       ProfScope ps(mm, PROF_OTHER, s);
-      SD_CUDA(sd::launch_step_control(mm, cfl, ph->c_h, dt_out ? dt_out + 2 * (int64_t)k : nullptr, s));
+      if (ph->viscous && ph->visc_cfl > 0.0) SD_CUDA(sd::launch_visc_numax(mm, ph, q, s));
+      SD_CUDA(sd::launch_step_control(mm, cfl, ph->c_h, dt_out ? dt_out + 2 * (int64_t)k : nullptr, s, nullptr, 1.0,
+                                      ph->viscous ? ph->visc_cfl : 0.0));
     }
     // stage 0: work = q + dt R(q).  The mixed path runs the increment form: it keeps
     // no FP64 intermediate state, only D = q^(s) - q^n in FP32 (D = dt R(q) here),

@@ -54,7 +54,7 @@ class PhysC(C.Structure):
                 ("rk_scheme", C.c_int32), ("farfield", C.c_double * 9), ("mu", C.c_double), ("eta", C.c_double),
                 ("kappa", C.c_double), ("kappa_r", C.c_double), ("R_gas", C.c_double), ("viscous", C.c_int32),
                 ("pad2_", C.c_int32), ("q_bottom", C.c_double), ("T_top", C.c_double), ("visc_walls", C.c_int32),
-                ("pad3_", C.c_int32), ("kappa_r1", C.c_double), ("kappa_r2", C.c_double)]
+                ("pad3_", C.c_int32), ("kappa_r1", C.c_double), ("kappa_r2", C.c_double), ("visc_cfl", C.c_double)]
 
 
 class InitC(C.Structure):
@@ -116,6 +116,8 @@ class Phys:
     kappa_r2: float = 0.0
     # time integrator of step / advance: RK_SSP33 (three-stage SSP-RK3) or RK_SSP53 (SSPRK(5,3))
     rk_scheme: int = RK_SSP33
+    # diffusive limit of the step with the viscous terms: dt <= visc_cfl dx_min^2 / nu_max (0 = off)
+    visc_cfl: float = 0.0
 
     def c(self) -> PhysC:
         p = PhysC()
@@ -128,6 +130,7 @@ class Phys:
         p.q_bottom, p.T_top, p.visc_walls = self.q_bottom, self.T_top, int(self.visc_walls)
         p.kappa_r1, p.kappa_r2 = self.kappa_r1, self.kappa_r2
         p.rk_scheme = int(self.rk_scheme)
+        p.visc_cfl = float(self.visc_cfl)
         return p
 
 

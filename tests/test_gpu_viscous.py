@@ -184,3 +184,58 @@ def test_radius_dependent_kappa_r_shell_walls(N):
     R = gm.to_host(gm.residual(gph, gm.to_device(q0)))
     Ro, s = om.residual(oph, q0)
     assert _c19(R, Ro, s) < TOL64
+
+
+def _nu_max(q0, ph, xyz=None):
+    """max over the solution points of (4/3 mu / rho, eta, kappa, gamma kappa_r(r))"""
+    nu = max(4.0 / 3.0 * ph.mu / q0[0].min(), ph.eta, ph.kappa, ph.gamma * ph.kappa_r)
+    if xyz is not None:
+        r = np.sqrt((xyz ** 2).sum(axis=-1))
+        nu = max(nu, float((ph.gamma * (ph.kappa_r + ph.kappa_r1 * r + ph.kappa_r2 * r * r)).max()))
+    return nu
+
+
+@pytest.mark.parametrize("radial", [False, True])
+def test_visc_cfl_limits_the_step(radial):
+    """With visc_cfl set, dt = min(cfl dx_min / lambda_max, visc_cfl dx_min^2 / nu_max), nu_max the
+    largest diffusivity of the step's start state (with kappa_r(r), at the points' radii)."""
+    N = 4
+    v, h = inputs.shell_mesh(2, 2)
+    kw = dict(geom=1, r_in=0.7, r_out=0.98, bc_in=sdref.BC_WALL_CONDUCTING, bc_out=sdref.BC_WALL_RADIAL)
+    gm, om = _pair(N, v, inputs.reorient(h, seed=9), **kw)
+    coef = dict(VISC_R, mu=1e-3) if radial else dict(VISC)  # radial: gamma kappa_r(r) the largest
+    base = dict(powell=1, c_h=0.0, glm_alpha=0.5, **coef)
+    q0 = inputs.random_state(gm.n_e, N, seed=77)
+    xyz = np.stack([om.geometry(e)[2] for e in range(gm.n_e)]) if radial else None
+    ph0 = sdmhd.Phys(**base)
+    nu = _nu_max(q0, ph0, xyz)
+    if radial:
+        assert nu > 1.5 * max(4.0 / 3.0 * ph0.mu / q0[0].min(), ph0.eta, ph0.kappa)
+    xs = sdref.nodes(N)[0]
+    dx_min = gm.info["h_min"] * (xs[1] - xs[0])
+
+    def dt_of(ph, prec=sdmhd.SD_FP64):
+        q, work = gm.to_device(q0), gm.empty_state()
+        dts = torch.zeros(2, dtype=torch.float64, device="cuda")
+        gm.step(ph, 0.2, q, work, dt_out=dts)
+        return float(dts[0])
+
+    dt_adv = dt_of(ph0)
+    c = 0.25 * dt_adv * nu / dx_min ** 2  # the diffusive limit at a quarter of the advective step
+    dt_v = dt_of(sdmhd.Phys(visc_cfl=c, **base))
+    assert abs(dt_v - c * dx_min ** 2 / nu) <= 1e-12 * dt_v, (dt_v, c * dx_min ** 2 / nu)
+    assert abs(dt_v / dt_adv - 0.25) < 1e-9
+    # a loose diffusive limit leaves the advective step; the five-stage method takes the same limit
+    assert dt_of(sdmhd.Phys(visc_cfl=100 * c, **base)) == dt_adv
+    dt53 = dt_of(sdmhd.Phys(visc_cfl=c, rk_scheme=sdmhd.RK_SSP53, **base))
+    assert abs(dt53 - dt_v) <= 1e-12 * dt_v
+
+
+def test_visc_cfl_refused_when_negative():
+    N = 3
+    v, h = inputs.shell_mesh(2, 1)
+    gm = sdmhd.Mesh(N, v, h, geom=1, r_in=0.7, r_out=0.98)
+    q = gm.to_device(inputs.random_state(gm.n_e, N, seed=3))
+    with pytest.raises(sdmhd.SDError, match="visc_cfl"):
+        gm.step(sdmhd.Phys(visc_cfl=-1.0, **VISC), 0.2, q, gm.empty_state())
+
