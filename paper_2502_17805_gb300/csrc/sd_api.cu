@@ -712,7 +712,7 @@ sd_status sd_mesh_create(const sd_mesh_desc* desc, void* stream, sd_mesh** out) 
   ALLOC(m->tr64[1], ne * 6 * 9 * N2);
   ALLOC(m->tr32[0], ne * 6 * 9 * N2);
   ALLOC(m->tr32[1], ne * 6 * 9 * N2);
-  ALLOC(m->dyn, 4 + sd::LAM_SLOTS);
+  ALLOC(m->dyn, 5 + sd::LAM_SLOTS);  // dt, c_h, lambda, rho_min | lambda slots | gamma kappa_r max
   ALLOC(m->diag_part, ne * 12);
   ALLOC(m->diag_out, 12);
   ALLOC(m->divb, ne * N3);
@@ -1164,8 +1164,7 @@ static sd_status advance53_impl(sd_mesh* mm, const sd_phys* ph, sd_precision pre
     {
       ProfScope ps(mm, PROF_OTHER, s);
       if (ph->viscous && ph->visc_cfl > 0.0) SD_CUDA(sd::launch_visc_numax(mm, ph, q, s));
-      SD_CUDA(sd::launch_step_control(mm, cfl, ph->c_h, dt_out ? dt_out + 2 * (int64_t)k : nullptr, s, mm->dyn_s, c,
-                                      ph->viscous ? ph->visc_cfl : 0.0));
+      SD_CUDA(sd::launch_step_control(mm, cfl, ph->c_h, dt_out ? dt_out + 2 * (int64_t)k : nullptr, s, mm->dyn_s, c, ph));
     }
     // stage 1: y2 = q + c dt L(q)
     sd::StageParams S = stage_params();
@@ -1285,8 +1284,7 @@ static sd_status advance_impl(sd_mesh* mm, const sd_phys* ph, sd_precision prec,
     {
       ProfScope ps(mm, PROF_OTHER, s);
       if (ph->viscous && ph->visc_cfl > 0.0) SD_CUDA(sd::launch_visc_numax(mm, ph, q, s));
-      SD_CUDA(sd::launch_step_control(mm, cfl, ph->c_h, dt_out ? dt_out + 2 * (int64_t)k : nullptr, s, nullptr, 1.0,
-                                      ph->viscous ? ph->visc_cfl : 0.0));
+      SD_CUDA(sd::launch_step_control(mm, cfl, ph->c_h, dt_out ? dt_out + 2 * (int64_t)k : nullptr, s, nullptr, 1.0, ph));
     }
     // stage 0: work = q + dt R(q).  The mixed path runs the increment form: it keeps
     // no FP64 intermediate state, only D = q^(s) - q^n in FP32 (D = dt R(q) here),

@@ -884,57 +884,63 @@ cudaError_t launch_bg_finish(const sd_mesh* m, double gamma, const double* R0, f
 // One block of LAM_SLOTS threads: lambda_max = largest of the partial maxima
 // (compared as bit patterns, as the atomics wrote them), which are cleared for
 // the next reduction; then dt and c_h.
-// Running maximum that keeps a NaN (a non-physical state must not pass unseen).
-__device__ __forceinline__ double max_keep_nan(double a, double b) { return (b > a || b != b) ? b : a; }
-
-// Largest diffusivity of the viscous terms over the solution points of the FP64
-// state q, max(nu_c, 4/3 mu / rho, gamma kappa_r(|x|) when kappa_r varies), nu_c =
-// max(eta, kappa, gamma kappa_r) for the constant ones, as the bits of a
-// non-negative double into *out (an atomicMax per warp; a NaN, above every finite
-// value, is kept).
-__global__ void visc_numax_kernel(int N3, int64_t n_e, int64_t stride, const double* __restrict__ q,
-                                  const double* __restrict__ X, double mu43, double nu_c, double gamma, double kr0,
-                                  double kr1, double kr2, unsigned long long* out) {
+// For the diffusive limit of the step: the smallest density over the solution
+// points of the FP64 state q (atomicMin on the bits of a positive double into
+// lo[0]; a NaN or a non-positive density, whose bits order above every positive
+// double, is passed over: the state's lambda_max is NaN then and so is dt) and,
+// when kappa_r varies, the largest gamma kappa_r(|x|) (atomicMax into hi[0]).
+// No division per point: the step control forms 4/3 mu / rho_min once.
+__global__ void visc_extrema_kernel(int N3, int64_t n_e, int64_t stride, const double* __restrict__ q,
+                                    const double* __restrict__ X, double gamma, double kr0, double kr1, double kr2,
+                                    unsigned long long* lo, unsigned long long* hi) {
   const bool kr_varies = kr1 != 0.0 || kr2 != 0.0;
-  double m = nu_c;
+  double rmin = INFINITY, kmax = 0.0;
   const int64_t n = n_e * N3;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t e = t / N3;
     const int k = (int)(t - e * N3);
-    double nu = mu43 / q[e * stride + k];
+    const double rho = q[e * stride + k];
+    rmin = rho > 0.0 && rho < rmin ? rho : rmin;
     if (kr_varies) {
       const double* x = X + e * 3 * N3 + k;
       const double r = sqrt(x[0] * x[0] + x[N3] * x[N3] + x[2 * N3] * x[2 * N3]);
       const double g = gamma * (kr0 + kr1 * r + kr2 * r * r);
-      nu = g > nu ? g : nu;
+      kmax = g > kmax ? g : kmax;
     }
-    m = max_keep_nan(m, nu);
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) m = max_keep_nan(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+  for (int o = 16; o > 0; o >>= 1) {
+    const double r2 = __shfl_xor_sync(0xffffffffu, rmin, o), k2 = __shfl_xor_sync(0xffffffffu, kmax, o);
+    rmin = r2 < rmin ? r2 : rmin;
+    kmax = k2 > kmax ? k2 : kmax;
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMin(lo, (unsigned long long)__double_as_longlong(rmin));
+    if (kr_varies) atomicMax(hi, (unsigned long long)__double_as_longlong(kmax));
+  }
 }
 
 cudaError_t launch_visc_numax(const sd_mesh* m, const sd_phys* ph, const double* q, cudaStream_t s) {
-  unsigned long long* out = reinterpret_cast<unsigned long long*>(m->dyn + 3);
-  cudaError_t err = cudaMemsetAsync(out, 0, sizeof(unsigned long long), s);
+  unsigned long long* lo = reinterpret_cast<unsigned long long*>(m->dyn + 3);
+  unsigned long long* hi = reinterpret_cast<unsigned long long*>(m->dyn + 4 + LAM_SLOTS);
+  cudaError_t err = cudaMemsetAsync(lo, 0xff, sizeof(unsigned long long), s);  // above every positive double
+  if (err == cudaSuccess) err = cudaMemsetAsync(hi, 0, sizeof(unsigned long long), s);
   if (err != cudaSuccess || m->n_e == 0) return err;
-  const double kr_c = (ph->kappa_r1 != 0.0 || ph->kappa_r2 != 0.0) ? 0.0 : ph->gamma * ph->kappa_r;
-  double nu_c = ph->eta > ph->kappa ? ph->eta : ph->kappa;
-  nu_c = kr_c > nu_c ? kr_c : nu_c;
   const int N3 = m->N * m->N * m->N;
   const int64_t n = m->n_e * N3;
   const int64_t blocks = std::min<int64_t>((n + 255) / 256, 152 * 8);
-  visc_numax_kernel<<<(unsigned)blocks, 256, 0, s>>>(N3, m->n_e, m->stride, q, m->X64, 4.0 / 3.0 * ph->mu, nu_c,
-                                                     ph->gamma, ph->kappa_r, ph->kappa_r1, ph->kappa_r2, out);
+  visc_extrema_kernel<<<(unsigned)blocks, 256, 0, s>>>(N3, m->n_e, m->stride, q, m->X64, ph->gamma, ph->kappa_r,
+                                                       ph->kappa_r1, ph->kappa_r2, lo, hi);
   return cudaGetLastError();
 }
 
-// The step-control kernel.  visc_dx2 > 0: also dt <= visc_dx2 / nu_max, nu_max
-// from dyn[3] (visc_numax_kernel), which is cleared.
+// The step-control kernel.  visc_dx2 > 0: also dt <= visc_dx2 / nu_max, nu_max =
+// max(mu43 / rho_min, nu_c, the largest gamma kappa_r(r)) from the extrema that
+// visc_extrema_kernel left in dyn[3] and dyn[4 + LAM_SLOTS].
 __global__ void __launch_bounds__(LAM_SLOTS) step_control_kernel(double* dyn, double cfl, double dx_min,
                                                                  double ch_fixed, double* dt_out, double* dyn_s,
-                                                                 double dt_scale, double visc_dx2) {
+                                                                 double dt_scale, double visc_dx2, double mu43,
+                                                                 double nu_c) {
   __shared__ unsigned long long part[LAM_SLOTS / 32];
   unsigned long long* slots = reinterpret_cast<unsigned long long*>(dyn + 4);
   unsigned long long b = slots[threadIdx.x];
@@ -951,9 +957,11 @@ __global__ void __launch_bounds__(LAM_SLOTS) step_control_kernel(double* dyn, do
   const double lam = __longlong_as_double((long long)b);
   double dt = cfl * dx_min / lam;
   if (visc_dx2 > 0.0) {
-    const double dtv = visc_dx2 / dyn[3];
+    double nu = mu43 / dyn[3];
+    nu = nu_c > nu ? nu_c : nu;
+    nu = dyn[4 + LAM_SLOTS] > nu ? dyn[4 + LAM_SLOTS] : nu;
+    const double dtv = visc_dx2 / nu;
     dt = (dtv < dt || dtv != dtv) ? dtv : dt;
-    dyn[3] = 0.0;
   }
   const double ch = ch_fixed > 0.0 ? ch_fixed : lam;
   dyn[0] = dt;
@@ -970,10 +978,18 @@ __global__ void __launch_bounds__(LAM_SLOTS) step_control_kernel(double* dyn, do
 }
 
 cudaError_t launch_step_control(const sd_mesh* m, double cfl, double c_h_fixed, double* dt_out, cudaStream_t s,
-                                double* dyn_s, double dt_scale, double visc_cfl) {
+                                double* dyn_s, double dt_scale, const sd_phys* visc) {
   const double dx_min = m->h_min * (m->ops64.xs[1] - m->ops64.xs[0]);
-  step_control_kernel<<<1, LAM_SLOTS, 0, s>>>(m->dyn, cfl, dx_min, c_h_fixed, dt_out, dyn_s, dt_scale,
-                                              visc_cfl * dx_min * dx_min);
+  double visc_dx2 = 0.0, mu43 = 0.0, nu_c = 0.0;
+  if (visc && visc->viscous && visc->visc_cfl > 0.0) {
+    visc_dx2 = visc->visc_cfl * dx_min * dx_min;
+    mu43 = 4.0 / 3.0 * visc->mu;
+    const double kr_c = (visc->kappa_r1 != 0.0 || visc->kappa_r2 != 0.0) ? 0.0 : visc->gamma * visc->kappa_r;
+    nu_c = visc->eta > visc->kappa ? visc->eta : visc->kappa;
+    nu_c = kr_c > nu_c ? kr_c : nu_c;
+  }
+  step_control_kernel<<<1, LAM_SLOTS, 0, s>>>(m->dyn, cfl, dx_min, c_h_fixed, dt_out, dyn_s, dt_scale, visc_dx2,
+                                              mu43, nu_c);
   return cudaGetLastError();
 }
 

@@ -274,11 +274,12 @@ cudaError_t launch_bg_prepare(const sd_mesh* m, double gamma, double inv_gm1, co
                               float* rec, cudaStream_t s);
 cudaError_t launch_bg_finish(const sd_mesh* m, double gamma, const double* R0, float* rec, float* jump,
                              const double* tr, cudaStream_t s);
-// visc_cfl > 0: also dt <= visc_cfl dx_min^2 / nu_max, nu_max from launch_visc_numax
+// visc with viscous != 0 and visc_cfl > 0: also dt <= visc_cfl dx_min^2 / nu_max, from the extrema
+// launch_visc_numax left
 cudaError_t launch_step_control(const sd_mesh* m, double cfl, double c_h_fixed, double* dt_out, cudaStream_t s,
-                                double* dyn_s = nullptr, double dt_scale = 1.0, double visc_cfl = 0.0);
-// the largest diffusivity of the viscous terms over the solution points of the FP64 state q, for
-// the step control of the next step
+                                double* dyn_s = nullptr, double dt_scale = 1.0, const sd_phys* visc = nullptr);
+// the extrema the diffusive limit of the step needs (the smallest density over the solution points
+// of the FP64 state q; the largest gamma kappa_r(r) when kappa_r varies), for the next step control
 cudaError_t launch_visc_numax(const sd_mesh* m, const sd_phys* ph, const double* q, cudaStream_t s);
 cudaError_t launch_axpby_f64(double* out, double a, const double* x, double b, const double* y, int64_t n,
                              cudaStream_t s);
