@@ -21,7 +21,7 @@ def _device():
     torch.cuda.set_device(0)
 
 
-@pytest.mark.parametrize("N,n_r,n_t", [(4, 3, 7), (6, 2, 5), (5, 4, 256)])
+@pytest.mark.parametrize("N,n_r,n_t", [(2, 2, 3), (3, 3, 4), (4, 3, 7), (6, 2, 5), (5, 4, 256), (7, 2, 6), (8, 3, 5)])
 def test_spherical_sums_match_the_oracle(N, n_r, n_t):
     v, h = inputs.shell_mesh(8, 4)
     kw = dict(geom=1, r_in=0.70, r_out=0.98)
