@@ -199,3 +199,27 @@ def test_mixed_viscous_radius_dependent_kappa_r_periodic_box(N):
     ok, err, ref = _strict(R, Ro, "kappa_r(r) periodic box N=%d" % N)
     assert ok, (err, ref)
 
+
+def test_mixed_visc_cfl_limits_the_step():
+    """sd_phys.visc_cfl on the mixed path: dt = min(cfl dx_min / lambda_max, visc_cfl dx_min^2 /
+    nu_max), nu_max from the step's FP64 start state, as on the FP64 path."""
+    N = 4
+    gm, om, q0, qb = _box(N, 41)
+    base = dict(powell=1, c_h=0.0, glm_alpha=0.3, **VISC)
+    bg = gm.background(sdmhd.Phys(**base), gm.to_device(qb))
+    nu = max(4.0 / 3.0 * VISC["mu"] / q0[0].min(), VISC["eta"], VISC["kappa"], 5.0 / 3.0 * VISC["kappa_r"])
+    xs = sdref.nodes(N)[0]
+    dx_min = gm.info["h_min"] * (xs[1] - xs[0])
+
+    def dt_of(ph):
+        q, work = gm.to_device(q0), gm.empty_state()
+        dts = torch.zeros(2, dtype=torch.float64, device="cuda")
+        gm.step(ph, 0.2, q, work, prec=sdmhd.SD_FP32_MIXED, bg=bg, dt_out=dts)
+        return float(dts[0])
+
+    dt_adv = dt_of(sdmhd.Phys(**base))
+    c = 0.5 * dt_adv * nu / dx_min ** 2
+    dt_v = dt_of(sdmhd.Phys(visc_cfl=c, **base))
+    assert abs(dt_v - c * dx_min ** 2 / nu) <= 1e-12 * dt_v, (dt_v, c * dx_min ** 2 / nu)
+    assert abs(dt_v / dt_adv - 0.5) < 1e-9
+
